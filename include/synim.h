@@ -1,0 +1,177 @@
+/*
+ * synim.h -- C ABI of the B300 (sm_103a) synthetic interaction-matrix library.
+ *
+ * The library computes Shack-Hartmann interaction matrices (IMs) from
+ * deformable-mirror influence functions (IFs), following the method of the
+ * paper's Sec. 2:
+ *   - Sec. 2.1: the DM misregistration (shift, rotation, magnification), the
+ *     sensor transform (rotation, anamorphic magnification, shift), the LGS
+ *     cone factor (1 - h/H) and the off-axis footprint shift h * theta are
+ *     folded into one composite affine map, and each IF is resampled exactly
+ *     once (bilinear) onto the sensor grid;
+ *   - Sec. 2.2: the sensor grid is M = k * n_sub pixels so that every
+ *     subaperture is an exact k x k block; slopes are central differences
+ *     averaged over the lit pixels of each subaperture;
+ *   - Sec. 2.3: edge repair (strict core of the interpolated DM mask at
+ *     0.999999, ring = cross dilation minus core, ring value = mean over the
+ *     valid cardinal directions of 2 P1 - P2 or P1);
+ *   - Sec. 4.2: many DMs x many sensors in one pass, each IF fetched once.
+ *
+ * Conventions (all calls):
+ *   - Images are row-major, row = y, column = x; pixel centres sit at integer
+ *     indices and each grid is centred at (n - 1) / 2.
+ *   - The IM of pair (dm, wfs) is FP32, column-major: column a (actuator a of
+ *     the DM, cube order) is contiguous and holds 2 * nv rows: the x slopes of
+ *     the nv valid subapertures (row-major subaperture order), then their y
+ *     slopes.  Memory size = n_act * 2 * nv * 4 bytes.
+ *   - Slopes are in IF units per metre of the sensor's pupil-plane frame,
+ *     times slope_scale.
+ *   - Positive DM shift moves the DM pattern towards +x / +y on the sensor;
+ *     positive rotation turns it from +x towards +y; mag > 1 enlarges it.
+ *   - Every call returns a synim_status; nothing aborts or throws across the
+ *     ABI.  Device work is ordered on the caller's CUDA stream (cudaStream_t
+ *     passed as void*; NULL = legacy default stream).  A context belongs to
+ *     the device that was current at create and is not thread-safe.
+ *   - Output buffers are allocated by the caller (sizes from synim_im_query)
+ *     and must stay valid until the stream has executed the call.
+ */
+#ifndef SYNIM_H
+#define SYNIM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SYNIM_OK = 0,
+    SYNIM_ERR_INVALID_ARG = 1, /* NULL pointer, negative size, bad enum */
+    SYNIM_ERR_SHAPE = 2,       /* inconsistent sizes (e.g. grid_m % n_sub != 0, k < 2) */
+    SYNIM_ERR_OOM = 3,         /* a device allocation failed */
+    SYNIM_ERR_CUDA = 4,        /* a CUDA runtime call failed (see synim_last_error) */
+    SYNIM_ERR_TIMEOUT = 5,     /* a bounded device wait gave up (kernel returned early) */
+    SYNIM_ERR_NOT_CONVERGED = 6,
+    SYNIM_ERR_NOT_TRAINED = 7
+} synim_status;
+
+typedef struct synim_ctx synim_ctx;
+
+/* One deformable mirror (or virtual layer).  Sec. 2.1, Sec. 4.1. */
+typedef struct {
+    int32_t n_act;          /* number of IFs = IM columns, >= 1 */
+    int32_t grid_n;         /* N: every IF is N x N FP32, N >= 4 */
+    double pixel_pitch_m;   /* DM-plane pixel size in metres, > 0 */
+    double altitude_m;      /* conjugation altitude h, >= 0 */
+    const float *ifs;       /* [n_act][N][N]; borrowed for the duration of create only */
+    int32_t ifs_on_device;  /* 1: ifs is a device pointer on the current device; 0: host */
+    const uint8_t *mask;    /* host [N][N] 0/1 DM mask (IFs are assumed already masked);
+                               NULL = all ones */
+    float support_eps;      /* |IF| <= support_eps * max|IF_a| is treated as zero outside
+                               the actuator's support window; 0 = keep the whole grid */
+} synim_dm_desc;
+
+/* One Shack-Hartmann sensor.  Sec. 2.1 (sensor transform), Sec. 2.2 (grid). */
+typedef struct {
+    int32_t n_sub;              /* subapertures per side, >= 1 */
+    int32_t grid_m;             /* M = k * n_sub with k >= 2 */
+    double pupil_diam_m;        /* D: the M x M grid spans D (pixel = D / M) */
+    double src_height_m;        /* guide-star height H; 0 (or inf) = natural guide star */
+    double field_rad[2];        /* guide-star direction (x, y) in radians */
+    double rot_deg;             /* sensor rotation */
+    double mag[2];              /* sensor magnification (x, y): anamorphosis */
+    double shift_m[2];          /* sensor shift in the pupil plane, metres */
+    const uint8_t *pupil_mask;  /* host [M][M] 0/1; NULL = annulus of inner radius
+                                   obstruction * M / 2 and outer radius M / 2 (pixel units) */
+    const uint8_t *subap_valid; /* host [n_sub][n_sub] 0/1; NULL = valid when at least half
+                                   of the k x k pixels are lit */
+    double obstruction;         /* used only when pupil_mask is NULL */
+    double slope_scale;         /* multiplies every slope (1 = IF units per metre) */
+} synim_wfs_desc;
+
+/* DM misregistration relative to one sensor (Sec. 5: the SPRINT parameters). */
+typedef struct {
+    double shift_x_px; /* DM pixels */
+    double shift_y_px; /* DM pixels */
+    double rot_deg;    /* degrees */
+    double mag;        /* dimensionless, 1 = nominal */
+} synim_misreg;
+
+/* Creation options; pass NULL for defaults. */
+typedef struct {
+    int32_t threads_per_cta; /* 0 = default (256); a multiple of 32 in 64..256 */
+    int32_t ctas_per_sm;     /* 0 = default / autotuned */
+    int32_t use_graph;       /* 1 = replay a CUDA graph per stream; 0 = plain launches */
+    int32_t autotune;        /* 1 = time candidate launch shapes at the first compute */
+    int32_t profile;         /* 1 = record CUDA events around every IM-kernel launch
+                                (read back with synim_im_kernel_ms) */
+} synim_opts;
+
+/*
+ * Create a context: uploads the IF cubes once, scans each IF's support
+ * window (|IF| > support_eps * peak), packs the windows into device memory,
+ * and builds the per-sensor subaperture tables (Sec. 2.2) and derivative
+ * stencils.  The caller may free every input as soon as create returns.
+ * dms[n_dm], wfs[n_wfs]: 1 <= n_dm <= 8, 1 <= n_wfs <= 16.
+ * On success *out owns device memory until synim_im_destroy.
+ */
+synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim_wfs_desc *wfs,
+                             int32_t n_wfs, const synim_opts *opts, synim_ctx **out);
+
+/* IM shape of pair (dm, wfs): n_rows = 2 * nv, n_cols = n_act. */
+synim_status synim_im_query(const synim_ctx *ctx, int32_t dm, int32_t wfs, int64_t *n_rows,
+                            int64_t *n_cols);
+
+/* Side W of the square support window of DM dm's influence functions, in DM
+ * pixels (every window of that DM has this size; Sec. 4.2 staging unit). */
+synim_status synim_dm_window(const synim_ctx *ctx, int32_t dm, int32_t *W);
+
+/*
+ * The composite affine of pair (dm, wfs) under misregistration mis (Sec. 2.1):
+ * DM pixel (x, y) sampled by sensor pixel (row i, column j) is
+ *   x = A[0] j + A[1] i + b[0],  y = A[2] j + A[3] i + b[1].
+ * Host-only; A[4], b[2] are host buffers.
+ */
+synim_status synim_pair_affine(const synim_ctx *ctx, int32_t dm, int32_t wfs,
+                               const synim_misreg *mis, double *A, double *b);
+
+/*
+ * Compute every IM of the context in one persistent launch (Sec. 2.1-2.3,
+ * Sec. 4.2).  mis[n_dm * n_wfs] (host) holds one misregistration per pair,
+ * pair index = dm * n_wfs + wfs; im[n_dm * n_wfs] (host array) holds device
+ * pointers to the caller's FP32 output buffers (layout above); a NULL entry
+ * skips that pair.  Asynchronous on cuda_stream.
+ */
+synim_status synim_im_compute(synim_ctx *ctx, const synim_misreg *mis, float *const *im,
+                              void *cuda_stream);
+
+/*
+ * Synchronise cuda_stream and report whether any kernel of this context has
+ * flagged an error since the last check (SYNIM_ERR_TIMEOUT if a bounded wait
+ * gave up).  Clears the flag.
+ */
+synim_status synim_im_check(synim_ctx *ctx, void *cuda_stream);
+
+/*
+ * With opts.profile = 1: wait for the IM-kernel launches recorded since the
+ * previous call and return their summed device time (ms) and count.  Up to
+ * 256 launches are kept between two calls (older ones are dropped from the
+ * sum and the count).  Returns SYNIM_ERR_INVALID_ARG without profiling.
+ */
+synim_status synim_im_kernel_ms(synim_ctx *ctx, double *total_ms, int32_t *n_launches);
+
+/* Free all device memory of the context (waits for its streams). NULL is a no-op. */
+void synim_im_destroy(synim_ctx *ctx);
+
+/* Static description of a status code. */
+const char *synim_status_string(synim_status s);
+
+/* Last error message recorded on ctx ("" if none); valid until the next call on ctx.
+ * With ctx == NULL: the last error of a failed create on this thread. */
+const char *synim_last_error(const synim_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SYNIM_H */

@@ -1,0 +1,101 @@
+"""ctypes declarations of include/synim.h (same names; argument marshalling only).
+
+Loading fails loudly when libsynim.so is missing and cannot be built: there
+is no CPU fallback anywhere in this package.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import shutil
+
+from . import build as _build
+
+c_int32, c_int64, c_double, c_float, c_void_p = (ctypes.c_int32, ctypes.c_int64, ctypes.c_double,
+                                                 ctypes.c_float, ctypes.c_void_p)
+
+SYNIM_OK = 0
+STATUS_NAMES = {0: "SYNIM_OK", 1: "SYNIM_ERR_INVALID_ARG", 2: "SYNIM_ERR_SHAPE", 3: "SYNIM_ERR_OOM",
+                4: "SYNIM_ERR_CUDA", 5: "SYNIM_ERR_TIMEOUT", 6: "SYNIM_ERR_NOT_CONVERGED",
+                7: "SYNIM_ERR_NOT_TRAINED"}
+
+
+class synim_dm_desc(ctypes.Structure):
+    _fields_ = [("n_act", c_int32), ("grid_n", c_int32), ("pixel_pitch_m", c_double),
+                ("altitude_m", c_double), ("ifs", c_void_p), ("ifs_on_device", c_int32),
+                ("mask", c_void_p), ("support_eps", c_float)]
+
+
+class synim_wfs_desc(ctypes.Structure):
+    _fields_ = [("n_sub", c_int32), ("grid_m", c_int32), ("pupil_diam_m", c_double),
+                ("src_height_m", c_double), ("field_rad", c_double * 2), ("rot_deg", c_double),
+                ("mag", c_double * 2), ("shift_m", c_double * 2), ("pupil_mask", c_void_p),
+                ("subap_valid", c_void_p), ("obstruction", c_double), ("slope_scale", c_double)]
+
+
+class synim_misreg(ctypes.Structure):
+    _fields_ = [("shift_x_px", c_double), ("shift_y_px", c_double), ("rot_deg", c_double),
+                ("mag", c_double)]
+
+
+class synim_opts(ctypes.Structure):
+    _fields_ = [("threads_per_cta", c_int32), ("ctas_per_sm", c_int32), ("use_graph", c_int32),
+                ("autotune", c_int32), ("profile", c_int32)]
+
+
+# name -> (restype, argtypes); mirrors include/synim.h
+SIGNATURES = {
+    "synim_im_create": (c_int32, [ctypes.POINTER(synim_dm_desc), c_int32, ctypes.POINTER(synim_wfs_desc),
+                                  c_int32, ctypes.POINTER(synim_opts), ctypes.POINTER(c_void_p)]),
+    "synim_im_query": (c_int32, [c_void_p, c_int32, c_int32, ctypes.POINTER(c_int64),
+                                 ctypes.POINTER(c_int64)]),
+    "synim_pair_affine": (c_int32, [c_void_p, c_int32, c_int32, ctypes.POINTER(synim_misreg),
+                                    ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
+    "synim_im_compute": (c_int32, [c_void_p, ctypes.POINTER(synim_misreg), ctypes.POINTER(c_void_p),
+                                   c_void_p]),
+    "synim_im_check": (c_int32, [c_void_p, c_void_p]),
+    "synim_dm_window": (c_int32, [c_void_p, c_int32, ctypes.POINTER(c_int32)]),
+    "synim_im_kernel_ms": (c_int32, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int32)]),
+    "synim_im_destroy": (None, [c_void_p]),
+    "synim_status_string": (ctypes.c_char_p, [c_int32]),
+    "synim_last_error": (ctypes.c_char_p, [c_void_p]),
+}
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libsynim.so (building it first if it is missing or stale and nvcc exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if _build.stale():
+        if shutil.which(_build.NVCC) or os.path.exists(_build.NVCC):
+            _build.build()
+        elif not os.path.exists(_build.LIB):
+            raise RuntimeError("libsynim.so is not built and nvcc is unavailable: the CUDA path "
+                               "cannot run (there is no CPU fallback)")
+    L = ctypes.CDLL(_build.LIB)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+class SynimError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def check(status: int, ctx=None):
+    if status != SYNIM_OK:
+        L = load()
+        msg = L.synim_last_error(ctx)
+        raise SynimError(status, (msg or b"").decode())

@@ -1,0 +1,769 @@
+// synim_api.cu -- host side of the C ABI declared in include/synim.h.
+//
+// create:  uploads the IF cubes, scans supports and packs windows (device),
+//          builds the per-sensor subaperture tables and telescoped
+//          derivative stencils (host), allocates the per-pair state maps.
+// compute: builds the composite affine of every pair (Sec. 2.1, FP64 host),
+//          copies the small per-pair block to the device and runs
+//          pixel classes -> persistent IM kernel, replayed from a CUDA graph.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "synim.h"
+#include "synim_internal.h"
+
+using namespace synim;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct DmHost {
+    int n_act = 0, N = 0, W = 0, Wp = 0;
+    double dd = 0, h = 0;
+};
+
+struct WfsHost {
+    int n_sub = 0, M = 0, k = 0, nv = 0, CH = 1;
+    double D = 0, H = 0, th[2] = {0, 0}, rot = 0, mag[2] = {1, 1}, shift[2] = {0, 0}, scale = 1;
+};
+
+constexpr int NSLOT = 4;
+constexpr int NPROF = 256;
+
+struct GraphEntry {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t ev_start = nullptr, ev_stop = nullptr;  // event-record nodes (profiling)
+};
+
+}  // namespace
+
+struct synim_ctx {
+    int device = 0, n_sm = 0, n_dm = 0, n_wfs = 0;
+    DmHost dmh[SYNIM_MAX_DM];
+    WfsHost wh[SYNIM_MAX_WFS];
+    Geo geo{};
+    std::vector<void *> dev_allocs;
+    std::vector<void *> host_allocs;
+    DevPair *d_pairs = nullptr;
+    DevPair *h_pairs[NSLOT] = {};
+    cudaEvent_t slot_ev[NSLOT] = {};
+    bool slot_used[NSLOT] = {};
+    int slot = 0;
+    int *d_counter = nullptr, *d_err = nullptr, *h_err = nullptr;
+    double *d_gp = nullptr;
+    long long pst_off[SYNIM_MAX_PAIRS] = {};
+    uint8_t *d_pst = nullptr;
+    int max_mm = 0;
+    int threads = 256, ctas_per_sm = 0;
+    bool use_graph = true;
+    int arena_floats = 0;
+    std::map<std::tuple<int, size_t, int, int>, GraphEntry> graphs;
+    cudaStream_t cap = nullptr;
+    bool profile = false;
+    cudaEvent_t prof_a[NPROF] = {}, prof_b[NPROF] = {};
+    unsigned long long prof_head = 0, prof_tail = 0;
+    double prof_acc_ms = 0.0;
+    int prof_acc_n = 0;
+    std::string err;
+};
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+synim_status fail(synim_ctx *c, synim_status s, const std::string &msg) {
+    if (c) c->err = msg;
+    else g_create_error = msg;
+    return s;
+}
+
+synim_status cuda_fail(synim_ctx *c, cudaError_t e, const char *what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(c, e == cudaErrorMemoryAllocation ? SYNIM_ERR_OOM : SYNIM_ERR_CUDA, m);
+}
+
+template <typename T>
+cudaError_t dev_alloc(synim_ctx *c, T **p, size_t count) {
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+    if (e == cudaSuccess) {
+        c->dev_allocs.push_back(q);
+        *p = static_cast<T *>(q);
+    }
+    return e;
+}
+
+template <typename T>
+cudaError_t dev_upload(synim_ctx *c, T **p, const std::vector<T> &v) {
+    cudaError_t e = dev_alloc(c, p, v.size());
+    if (e != cudaSuccess || v.empty()) return e;
+    return cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+// Composite affine (Sec. 2.1) in closed form:
+//   A = c dw / (dd m) R(-td) R(tw) diag(mw)
+//   b = cN + R(-td) (c s_w + h theta - s_d) / (dd m) - A (cM, cM)
+// with c = 1 - h/H the LGS cone factor, s_d the DM shift in metres, cN and
+// cM the DM and sensor grid centres.
+void composite(const DmHost &D, const WfsHost &W, const synim_misreg &m, double A[4], double b[2]) {
+    const double cone = (W.H > 0.0 && std::isfinite(W.H)) ? 1.0 - D.h / W.H : 1.0;
+    const double dw = W.D / W.M;
+    const double s = cone * dw / (D.dd * m.mag);
+    const double tw = W.rot * M_PI / 180.0, td = m.rot_deg * M_PI / 180.0;
+    const double ct = std::cos(td), st = std::sin(td), cw = std::cos(tw), sw = std::sin(tw);
+    // X = R(tw) diag(mw)
+    const double X00 = cw * W.mag[0], X01 = -sw * W.mag[1], X10 = sw * W.mag[0], X11 = cw * W.mag[1];
+    // R(-td) = [[ct, st], [-st, ct]]
+    A[0] = s * (ct * X00 + st * X10);
+    A[1] = s * (ct * X01 + st * X11);
+    A[2] = s * (-st * X00 + ct * X10);
+    A[3] = s * (-st * X01 + ct * X11);
+    const double tx = cone * W.shift[0] + D.h * W.th[0] - m.shift_x_px * D.dd;
+    const double ty = cone * W.shift[1] + D.h * W.th[1] - m.shift_y_px * D.dd;
+    const double inv = 1.0 / (D.dd * m.mag);
+    const double cN = (D.N - 1) * 0.5, cM = (W.M - 1) * 0.5;
+    b[0] = cN + inv * (ct * tx + st * ty) - (A[0] + A[1]) * cM;
+    b[1] = cN + inv * (-st * tx + ct * ty) - (A[2] + A[3]) * cM;
+}
+
+// d(A, b)/dp_k in closed form: the shifts translate by -R(-td) e / m; the
+// rotation turns the map about the DM centre (dA = -J A, db = -J (b - cN),
+// J = [[0, -1], [1, 0]], per radian); the magnification scales it about the
+// DM centre (dA = -A / m, db = -(b - cN) / m).
+void composite_jac(const DmHost &D, const synim_misreg &m, const double A[4], const double b[2],
+                   double dA[16], double db[8]) {
+    const double td = m.rot_deg * M_PI / 180.0, ct = std::cos(td), st = std::sin(td);
+    const double cN = (D.N - 1) * 0.5, rad = M_PI / 180.0;
+    std::fill(dA, dA + 16, 0.0);
+    db[0] = -ct / m.mag; db[1] = st / m.mag;
+    db[2] = -st / m.mag; db[3] = -ct / m.mag;
+    dA[8] = rad * A[2]; dA[9] = rad * A[3]; dA[10] = -rad * A[0]; dA[11] = -rad * A[1];
+    db[4] = rad * (b[1] - cN); db[5] = -rad * (b[0] - cN);
+    for (int q = 0; q < 4; ++q) dA[12 + q] = -A[q] / m.mag;
+    db[6] = -(b[0] - cN) / m.mag; db[7] = -(b[1] - cN) / m.mag;
+}
+
+bool invert2(const double A[4], double Ai[4]) {
+    const double det = A[0] * A[3] - A[1] * A[2];
+    if (!(std::fabs(det) > 1e-300) || !std::isfinite(det)) return false;
+    Ai[0] = A[3] / det; Ai[1] = -A[1] / det; Ai[2] = -A[2] / det; Ai[3] = A[0] / det;
+    return true;
+}
+
+int largest_divisor_le(int k, int cap) {
+    for (int c = std::min(k, cap); c >= 1; --c)
+        if (k % c == 0) return c;
+    return 1;
+}
+
+// Host tables of one sensor (Sec. 2.2): lit pixels, valid subapertures,
+// scale factors, and the telescoped derivative stencil.
+struct WfsTables {
+    std::vector<uint8_t> xcode, ycode;
+    std::vector<int> irr_pix, irr_sub, vsub, vrow;
+    std::vector<int8_t> irr_w;
+    std::vector<float> fac;
+    int nv = 0;
+};
+
+bool build_wfs_tables(const synim_wfs_desc &d, WfsTables &t, std::string &why) {
+    const int M = d.grid_m, n = d.n_sub, k = M / n;
+    std::vector<uint8_t> P((size_t)M * M);
+    if (d.pupil_mask) {
+        for (size_t q = 0; q < P.size(); ++q) P[q] = d.pupil_mask[q] ? 1 : 0;
+    } else {
+        const double c = (M - 1) * 0.5, ro = M * 0.5, ri = d.obstruction * M * 0.5;
+        for (int i = 0; i < M; ++i)
+            for (int j = 0; j < M; ++j) {
+                const double r = std::hypot(j - c, i - c);
+                P[(size_t)i * M + j] = (r <= ro && r >= ri) ? 1 : 0;
+            }
+    }
+    std::vector<int> lit((size_t)n * n, 0);
+    for (int i = 0; i < M; ++i)
+        for (int j = 0; j < M; ++j) lit[(i / k) * n + j / k] += P[(size_t)i * M + j];
+    std::vector<uint8_t> V((size_t)n * n);
+    t.vsub.clear();
+    t.fac.clear();
+    t.vrow.assign(n + 1, 0);
+    const double dw = d.pupil_diam_m / M;
+    for (int si = 0; si < n; ++si) {
+        t.vrow[si] = (int)t.vsub.size();
+        for (int sj = 0; sj < n; ++sj) {
+            const int l = lit[si * n + sj];
+            bool ok = d.subap_valid ? d.subap_valid[si * n + sj] != 0 : (2 * l >= k * k);
+            if (l == 0) ok = false;
+            V[si * n + sj] = ok;
+            if (ok) {
+                t.vsub.push_back((si << 16) | sj);
+                t.fac.push_back((float)(d.slope_scale / (2.0 * dw * l)));
+            }
+        }
+    }
+    t.vrow[n] = (int)t.vsub.size();
+    t.nv = (int)t.vsub.size();
+    if (t.nv == 0) {
+        why = "sensor has no valid subaperture";
+        return false;
+    }
+    auto Pv = [&](int i, int j) -> int {
+        return (i >= 0 && j >= 0 && i < M && j < M) ? P[(size_t)i * M + j] : 0;
+    };
+    auto Vv = [&](int si, int sj) -> int {
+        return (si >= 0 && sj >= 0 && si < n && sj < n) ? V[si * n + sj] : 0;
+    };
+    // Column pair (b k - 1, b k) at row i.  bit0/bit1: pixel b k - 1 adds
+    // +phi to subaperture (si, b-1) / -phi to (si, b); bit2/bit3: pixel b k.
+    t.xcode.assign((size_t)(n + 1) * M, 0);
+    t.ycode.assign((size_t)(n + 1) * M, 0);
+    for (int b = 0; b <= n; ++b) {
+        const int c0 = b * k - 1, c1 = b * k;
+        for (int i = 0; i < M; ++i) {
+            const int si = i / k;
+            int code = 0;
+            if (c0 >= 0) {
+                if (Pv(i, c0 - 1) && Vv(si, b - 1)) code |= 1;
+                if (Pv(i, c0 + 1) && Vv(si, b)) code |= 2;
+            }
+            if (c1 < M) {
+                if (Pv(i, c1 - 1) && Vv(si, b - 1)) code |= 4;
+                if (Pv(i, c1 + 1) && Vv(si, b)) code |= 8;
+            }
+            t.xcode[(size_t)b * M + i] = (uint8_t)code;
+        }
+        for (int j = 0; j < M; ++j) {
+            const int sj = j / k;
+            int code = 0;
+            if (c0 >= 0) {
+                if (Pv(c0 - 1, j) && Vv(b - 1, sj)) code |= 1;
+                if (Pv(c0 + 1, j) && Vv(b, sj)) code |= 2;
+            }
+            if (c1 < M) {
+                if (Pv(c1 - 1, j) && Vv(b - 1, sj)) code |= 4;
+                if (Pv(c1 + 1, j) && Vv(b, sj)) code |= 8;
+            }
+            t.ycode[(size_t)b * M + j] = (uint8_t)code;
+        }
+    }
+    // Pixels off the boundary lines whose two neighbours (both inside the same
+    // subaperture) differ in the pupil mask: weight P(q-e) - P(q+e).
+    t.irr_pix.clear();
+    t.irr_w.clear();
+    t.irr_sub.assign((size_t)n * n + 1, 0);
+    for (int si = 0; si < n; ++si)
+        for (int sj = 0; sj < n; ++sj) {
+            t.irr_sub[si * n + sj] = (int)t.irr_pix.size();
+            if (!V[si * n + sj]) continue;
+            for (int i = si * k; i < (si + 1) * k; ++i)
+                for (int j = sj * k; j < (sj + 1) * k; ++j) {
+                    const int jm = j - sj * k, im = i - si * k;
+                    const int wx = (jm != 0 && jm != k - 1) ? Pv(i, j - 1) - Pv(i, j + 1) : 0;
+                    const int wy = (im != 0 && im != k - 1) ? Pv(i - 1, j) - Pv(i + 1, j) : 0;
+                    if (wx || wy) {
+                        t.irr_pix.push_back((i << 16) | j);
+                        t.irr_w.push_back((int8_t)wx);
+                        t.irr_w.push_back((int8_t)wy);
+                    }
+                }
+        }
+    t.irr_sub[(size_t)n * n] = (int)t.irr_pix.size();
+    return true;
+}
+
+// Upper bound of the per-sensor accumulator floats for one pair (any
+// actuator), mirroring the kernel's box arithmetic.
+long long arena_need(const DmHost &D, const WfsHost &W, const double Ai[4], int NV) {
+    const double ej = (D.W + 1.0) * (std::fabs(Ai[0]) + std::fabs(Ai[1])) + 9.0;
+    const double ei = (D.W + 1.0) * (std::fabs(Ai[2]) + std::fabs(Ai[3])) + 9.0;
+    const long long pj = std::min<long long>((long long)std::ceil(ej), W.M);
+    const long long pi = std::min<long long>((long long)std::ceil(ei), W.M);
+    const long long nsj = std::min<long long>((pj + 2) / W.k + 2, W.n_sub);
+    const long long nsi = std::min<long long>((pi + 2) / W.k + 2, W.n_sub);
+    const long long nxc = pi / W.CH + 2, nyc = pj / W.CH + 2;
+    return (long long)NV * (2 * nxc * (nsj + 1) + 2 * nyc * (nsi + 1) + 2 * nsi * nsj);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *synim_status_string(synim_status s) {
+    switch (s) {
+        case SYNIM_OK: return "ok";
+        case SYNIM_ERR_INVALID_ARG: return "invalid argument";
+        case SYNIM_ERR_SHAPE: return "inconsistent shapes";
+        case SYNIM_ERR_OOM: return "device out of memory";
+        case SYNIM_ERR_CUDA: return "CUDA runtime error";
+        case SYNIM_ERR_TIMEOUT: return "bounded device wait timed out";
+        case SYNIM_ERR_NOT_CONVERGED: return "did not converge";
+        case SYNIM_ERR_NOT_TRAINED: return "estimator not trained";
+    }
+    return "unknown status";
+}
+
+const char *synim_last_error(const synim_ctx *ctx) {
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+void synim_im_destroy(synim_ctx *ctx) {
+    if (!ctx) return;
+    DeviceGuard guard(ctx->device);
+    cudaDeviceSynchronize();
+    for (auto &kv : ctx->graphs) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+    }
+    for (int q = 0; q < NPROF; ++q) {
+        if (ctx->prof_a[q]) cudaEventDestroy(ctx->prof_a[q]);
+        if (ctx->prof_b[q]) cudaEventDestroy(ctx->prof_b[q]);
+    }
+    for (int s = 0; s < NSLOT; ++s)
+        if (ctx->slot_ev[s]) cudaEventDestroy(ctx->slot_ev[s]);
+    if (ctx->cap) cudaStreamDestroy(ctx->cap);
+    for (void *p : ctx->dev_allocs) cudaFree(p);
+    for (void *p : ctx->host_allocs) cudaFreeHost(p);
+    delete ctx;
+}
+
+synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim_wfs_desc *wfs,
+                             int32_t n_wfs, const synim_opts *opts, synim_ctx **out) {
+    g_create_error.clear();
+    if (!out) return fail(nullptr, SYNIM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!dms || !wfs || n_dm < 1 || n_dm > SYNIM_MAX_DM || n_wfs < 1 || n_wfs > SYNIM_MAX_WFS)
+        return fail(nullptr, SYNIM_ERR_INVALID_ARG, "need 1..8 DMs and 1..16 sensors");
+    for (int d = 0; d < n_dm; ++d) {
+        const synim_dm_desc &D = dms[d];
+        if (D.n_act < 1 || D.grid_n < 4 || !(D.pixel_pitch_m > 0) || !(D.altitude_m >= 0) ||
+            !D.ifs || !(D.support_eps >= 0) || D.grid_n > 32767)
+            return fail(nullptr, SYNIM_ERR_INVALID_ARG, "invalid DM descriptor " + std::to_string(d));
+    }
+    for (int w = 0; w < n_wfs; ++w) {
+        const synim_wfs_desc &W = wfs[w];
+        if (W.n_sub < 1 || W.grid_m < 2 || !(W.pupil_diam_m > 0) || !(W.mag[0] != 0) ||
+            !(W.mag[1] != 0) || W.grid_m > 32767)
+            return fail(nullptr, SYNIM_ERR_INVALID_ARG, "invalid sensor descriptor " + std::to_string(w));
+        if (W.grid_m % W.n_sub != 0 || W.grid_m / W.n_sub < 2)
+            return fail(nullptr, SYNIM_ERR_SHAPE,
+                        "sensor " + std::to_string(w) + ": grid_m must be k * n_sub with k >= 2");
+    }
+    synim_ctx *c = new synim_ctx();
+    cudaGetDevice(&c->device);
+    cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device);
+    c->n_dm = n_dm;
+    c->n_wfs = n_wfs;
+    if (opts) {
+        if (opts->threads_per_cta > 0) c->threads = opts->threads_per_cta;
+        c->ctas_per_sm = std::max(0, opts->ctas_per_sm);
+        c->use_graph = opts->use_graph != 0;
+        c->profile = opts->profile != 0;
+    }
+    if (c->threads % 32 != 0 || c->threads < 64 || c->threads > 256) {
+        delete c;
+        return fail(nullptr, SYNIM_ERR_INVALID_ARG, "threads_per_cta must be a multiple of 32 in 64..256");
+    }
+    auto bail = [&](synim_status s) {
+        std::string m = c->err;
+        synim_im_destroy(c);
+        g_create_error = m;
+        return s;
+    };
+    cudaError_t e;
+    int max_win = 4;
+    // ---- DMs: support scan + window packing ----
+    for (int d = 0; d < n_dm; ++d) {
+        const synim_dm_desc &Dd = dms[d];
+        DmHost &H = c->dmh[d];
+        H.n_act = Dd.n_act; H.N = Dd.grid_n; H.dd = Dd.pixel_pitch_m; H.h = Dd.altitude_m;
+        const size_t NN = (size_t)H.N * H.N, cube_n = NN * H.n_act;
+        const float *cube = Dd.ifs;
+        float *staging = nullptr;
+        if (!Dd.ifs_on_device) {
+            if ((e = cudaMalloc(&staging, cube_n * sizeof(float))) != cudaSuccess)
+                return bail(cuda_fail(c, e, "cube staging"));
+            if ((e = cudaMemcpy(staging, Dd.ifs, cube_n * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess) {
+                cudaFree(staging);
+                return bail(cuda_fail(c, e, "cube upload"));
+            }
+            cube = staging;
+        }
+        int *d_box = nullptr;
+        std::vector<int> box(4 * (size_t)H.n_act);
+        e = cudaMalloc(&d_box, box.size() * sizeof(int));
+        if (e == cudaSuccess) e = launch_support(cube, H.n_act, H.N, Dd.support_eps, d_box, 0);
+        if (e == cudaSuccess) e = cudaMemcpy(box.data(), d_box, box.size() * sizeof(int), cudaMemcpyDeviceToHost);
+        cudaFree(d_box);
+        if (e != cudaSuccess) {
+            cudaFree(staging);
+            return bail(cuda_fail(c, e, "support scan"));
+        }
+        int W = 1;
+        for (int a = 0; a < H.n_act; ++a) {
+            const int *bx = &box[4 * (size_t)a];
+            if (bx[1] < bx[0]) continue;
+            W = std::max(W, std::max(bx[1] - bx[0] + 1, bx[3] - bx[2] + 1));
+        }
+        W = std::min(W, H.N);
+        int Wp = W + 2;
+        if ((Wp & 1) == 0) ++Wp;  // odd pitch: rows of the window fall in distinct banks
+        const int stride = (Wp * Wp + 3) / 4 * 4;
+        H.W = W; H.Wp = Wp;
+        std::vector<int> org(2 * (size_t)H.n_act, 0);
+        for (int a = 0; a < H.n_act; ++a) {
+            const int *bx = &box[4 * (size_t)a];
+            if (bx[1] < bx[0]) continue;
+            org[2 * a] = std::max(0, std::min(bx[0], H.N - W));
+            org[2 * a + 1] = std::max(0, std::min(bx[2], H.N - W));
+        }
+        DevDM &G = c->geo.dm[d];
+        int *d_org = nullptr;
+        float *d_win = nullptr;
+        e = dev_upload(c, &d_org, org);
+        if (e == cudaSuccess) e = dev_alloc(c, &d_win, (size_t)H.n_act * stride);
+        if (e == cudaSuccess) e = launch_pack(cube, H.n_act, H.N, d_org, W, Wp, stride, d_win, 0);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        cudaFree(staging);
+        if (e != cudaSuccess) return bail(cuda_fail(c, e, "window packing"));
+        uint8_t *d_mask = nullptr;
+        if (Dd.mask) {
+            std::vector<uint8_t> m(NN);
+            for (size_t q = 0; q < NN; ++q) m[q] = Dd.mask[q] ? 1 : 0;
+            if ((e = dev_upload(c, &d_mask, m)) != cudaSuccess) return bail(cuda_fail(c, e, "mask upload"));
+        }
+        G.win = d_win; G.org = d_org; G.mask = d_mask;
+        G.n_act = H.n_act; G.N = H.N; G.W = W; G.Wp = Wp; G.win_stride = stride;
+        max_win = std::max(max_win, stride);
+    }
+    // ---- sensors: tables ----
+    for (int w = 0; w < n_wfs; ++w) {
+        const synim_wfs_desc &Wd = wfs[w];
+        WfsHost &H = c->wh[w];
+        H.n_sub = Wd.n_sub; H.M = Wd.grid_m; H.k = Wd.grid_m / Wd.n_sub;
+        H.CH = largest_divisor_le(H.k, 32);
+        H.D = Wd.pupil_diam_m; H.H = Wd.src_height_m;
+        H.th[0] = Wd.field_rad[0]; H.th[1] = Wd.field_rad[1];
+        H.rot = Wd.rot_deg; H.mag[0] = Wd.mag[0]; H.mag[1] = Wd.mag[1];
+        H.shift[0] = Wd.shift_m[0]; H.shift[1] = Wd.shift_m[1]; H.scale = Wd.slope_scale;
+        WfsTables T;
+        std::string why;
+        if (!build_wfs_tables(Wd, T, why)) {
+            fail(c, SYNIM_ERR_SHAPE, "sensor " + std::to_string(w) + ": " + why);
+            return bail(SYNIM_ERR_SHAPE);
+        }
+        H.nv = T.nv;
+        DevWFS &G = c->geo.wfs[w];
+        uint8_t *xc, *yc;
+        int *ip, *is, *vs, *vr;
+        int8_t *iw;
+        float *fa;
+        e = dev_upload(c, &xc, T.xcode);
+        if (e == cudaSuccess) e = dev_upload(c, &yc, T.ycode);
+        if (e == cudaSuccess) e = dev_upload(c, &ip, T.irr_pix);
+        if (e == cudaSuccess) e = dev_upload(c, &iw, T.irr_w);
+        if (e == cudaSuccess) e = dev_upload(c, &is, T.irr_sub);
+        if (e == cudaSuccess) e = dev_upload(c, &fa, T.fac);
+        if (e == cudaSuccess) e = dev_upload(c, &vs, T.vsub);
+        if (e == cudaSuccess) e = dev_upload(c, &vr, T.vrow);
+        if (e != cudaSuccess) return bail(cuda_fail(c, e, "sensor tables"));
+        G.xcode = xc; G.ycode = yc; G.irr_pix = ip; G.irr_w = iw; G.irr_sub = is;
+        G.fac = fa; G.vsub = vs; G.vrow = vr;
+        G.n_sub = H.n_sub; G.M = H.M; G.k = H.k; G.nv = H.nv; G.CH = H.CH;
+        c->max_mm = std::max(c->max_mm, H.M * H.M);
+    }
+    // ---- per-pair state maps, parameter blocks, counters ----
+    long long tot = 0;
+    for (int d = 0; d < n_dm; ++d)
+        for (int w = 0; w < n_wfs; ++w) {
+            c->pst_off[d * n_wfs + w] = tot;
+            tot += (long long)c->wh[w].M * c->wh[w].M;
+        }
+    const int np = n_dm * n_wfs;
+    e = dev_alloc(c, &c->d_pst, (size_t)tot);
+    if (e == cudaSuccess) e = dev_alloc(c, &c->d_pairs, (size_t)np);
+    if (e == cudaSuccess) e = dev_alloc(c, &c->d_counter, 1);
+    if (e == cudaSuccess) e = dev_alloc(c, &c->d_err, 1);
+    if (e == cudaSuccess) e = dev_alloc(c, &c->d_gp, (size_t)np * 4);
+    if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "context buffers"));
+    for (int s = 0; s < NSLOT; ++s) {
+        void *h = nullptr;
+        if ((e = cudaMallocHost(&h, sizeof(DevPair) * np)) != cudaSuccess)
+            return bail(cuda_fail(c, e, "pinned parameter block"));
+        c->host_allocs.push_back(h);
+        c->h_pairs[s] = static_cast<DevPair *>(h);
+        std::memset(h, 0, sizeof(DevPair) * np);
+        if ((e = cudaEventCreateWithFlags(&c->slot_ev[s], cudaEventDisableTiming)) != cudaSuccess)
+            return bail(cuda_fail(c, e, "event"));
+    }
+    {
+        void *h = nullptr;
+        if ((e = cudaMallocHost(&h, sizeof(int))) != cudaSuccess) return bail(cuda_fail(c, e, "pinned flag"));
+        c->host_allocs.push_back(h);
+        c->h_err = static_cast<int *>(h);
+    }
+    if ((e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail(cuda_fail(c, e, "capture stream"));
+    if (c->profile)
+        for (int q = 0; q < NPROF; ++q)
+            if ((e = cudaEventCreate(&c->prof_a[q])) != cudaSuccess ||
+                (e = cudaEventCreate(&c->prof_b[q])) != cudaSuccess)
+                return bail(cuda_fail(c, e, "profiling events"));
+    // processing order: largest windows first (longest items scheduled early)
+    std::vector<int> order(n_dm);
+    for (int d = 0; d < n_dm; ++d) order[d] = d;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return c->geo.dm[x].win_stride > c->geo.dm[y].win_stride;
+    });
+    int acc = 0;
+    for (int q = 0; q < n_dm; ++q) {
+        c->geo.order_dm[q] = order[q];
+        c->geo.order_start[q] = acc;
+        acc += c->dmh[order[q]].n_act;
+    }
+    c->geo.order_start[n_dm] = acc;
+    c->geo.n_items = acc;
+    c->geo.n_dm = n_dm;
+    c->geo.n_wfs = n_wfs;
+    c->geo.max_win_floats = max_win;
+    *out = c;
+    return SYNIM_OK;
+}
+
+synim_status synim_im_query(const synim_ctx *ctx, int32_t dm, int32_t wfs, int64_t *n_rows,
+                            int64_t *n_cols) {
+    if (!ctx || !n_rows || !n_cols || dm < 0 || dm >= ctx->n_dm || wfs < 0 || wfs >= ctx->n_wfs)
+        return SYNIM_ERR_INVALID_ARG;
+    *n_rows = 2LL * ctx->wh[wfs].nv;
+    *n_cols = ctx->dmh[dm].n_act;
+    return SYNIM_OK;
+}
+
+synim_status synim_dm_window(const synim_ctx *ctx, int32_t dm, int32_t *W) {
+    if (!ctx || !W || dm < 0 || dm >= ctx->n_dm) return SYNIM_ERR_INVALID_ARG;
+    *W = ctx->dmh[dm].W;
+    return SYNIM_OK;
+}
+
+synim_status synim_im_kernel_ms(synim_ctx *ctx, double *total_ms, int32_t *n_launches) {
+    if (!ctx || !total_ms || !n_launches || !ctx->profile) return SYNIM_ERR_INVALID_ARG;
+    DeviceGuard guard(ctx->device);
+    double ms = ctx->prof_acc_ms;
+    int n = ctx->prof_acc_n;
+    for (; ctx->prof_tail < ctx->prof_head; ++ctx->prof_tail) {
+        const int q = (int)(ctx->prof_tail % NPROF);
+        float t = 0.f;
+        cudaError_t e = cudaEventSynchronize(ctx->prof_b[q]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, ctx->prof_a[q], ctx->prof_b[q]);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel timing");
+        ms += t;
+        ++n;
+    }
+    ctx->prof_acc_ms = 0.0;
+    ctx->prof_acc_n = 0;
+    *total_ms = ms;
+    *n_launches = n;
+    return SYNIM_OK;
+}
+
+synim_status synim_pair_affine(const synim_ctx *ctx, int32_t dm, int32_t wfs,
+                               const synim_misreg *mis, double *A, double *b) {
+    if (!ctx || !mis || !A || !b || dm < 0 || dm >= ctx->n_dm || wfs < 0 || wfs >= ctx->n_wfs)
+        return SYNIM_ERR_INVALID_ARG;
+    if (!(mis->mag > 0)) return SYNIM_ERR_INVALID_ARG;
+    composite(ctx->dmh[dm], ctx->wh[wfs], *mis, A, b);
+    return SYNIM_OK;
+}
+
+synim_status synim_im_check(synim_ctx *ctx, void *cuda_stream) {
+    if (!ctx) return SYNIM_ERR_INVALID_ARG;
+    DeviceGuard guard(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
+    if ((e = cudaMemcpy(ctx->h_err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(ctx, e, "error flag read");
+    const int flag = *ctx->h_err;
+    cudaMemset(ctx->d_err, 0, sizeof(int));
+    if (flag & ERR_TIMEOUT) return fail(ctx, SYNIM_ERR_TIMEOUT, "window staging wait timed out");
+    if (flag & ERR_ARENA) return fail(ctx, SYNIM_ERR_SHAPE, "subaperture accumulators exceeded the arena");
+    return SYNIM_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// compute / sensitivity / vjp share one launch path
+// ---------------------------------------------------------------------------
+namespace {
+
+synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *im,
+                 float *const *dim, const float *const *gim, double *grad_p, cudaStream_t s) {
+    DeviceGuard guard(c->device);
+    const int np = c->n_dm * c->n_wfs;
+    const int NV = (mode == MODE_FWD) ? 1 : 5;
+    cudaError_t e;
+    // parameter slot (pinned); wait for its previous copy to finish
+    const int slot = c->slot;
+    if (c->slot_used[slot] && (e = cudaEventSynchronize(c->slot_ev[slot])) != cudaSuccess)
+        return cuda_fail(c, e, "slot wait");
+    DevPair *hp = c->h_pairs[slot];
+    long long need = 0;
+    for (int d = 0; d < c->n_dm; ++d)
+        for (int w = 0; w < c->n_wfs; ++w) {
+            const int p = d * c->n_wfs + w;
+            const synim_misreg &m = mis[p];
+            if (!(m.mag > 0) || !std::isfinite(m.shift_x_px) || !std::isfinite(m.shift_y_px) ||
+                !std::isfinite(m.rot_deg) || !std::isfinite(m.mag))
+                return fail(c, SYNIM_ERR_INVALID_ARG, "misregistration of pair " + std::to_string(p));
+            DevPair &P = hp[p];
+            std::memset(&P, 0, sizeof(P));
+            composite(c->dmh[d], c->wh[w], m, P.A, P.b);
+            if (!invert2(P.A, P.Ai)) return fail(c, SYNIM_ERR_INVALID_ARG, "singular composite affine");
+            composite_jac(c->dmh[d], m, P.A, P.b, P.dA, P.db);
+            P.pst = c->d_pst + c->pst_off[p];
+            if (mode == MODE_FWD) P.im = im ? im[p] : nullptr;
+            if (mode == MODE_TAN) {
+                P.im = im ? im[p] : nullptr;
+                for (int q = 0; q < 4; ++q) P.dim[q] = dim ? dim[4 * p + q] : nullptr;
+            }
+            if (mode == MODE_VJP) P.gim = gim ? gim[p] : nullptr;
+            need = std::max(need, arena_need(c->dmh[d], c->wh[w], P.Ai, NV));
+        }
+    if (need > c->arena_floats) c->arena_floats = (int)((need + 255) / 256 * 256);
+    Geo g = c->geo;
+    g.arena_floats = c->arena_floats;
+    const size_t smem = im_smem_bytes(g);
+    int dev_max = 0;
+    cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+    if (smem + 8192 > (size_t)dev_max)
+        return fail(c, SYNIM_ERR_SHAPE,
+                    "support window + accumulators need " + std::to_string(smem) +
+                        " bytes of shared memory; reduce support_eps' window or the grid");
+    int bps = 0;
+    if ((e = im_prepare(mode, c->threads, smem, &bps)) != cudaSuccess) return cuda_fail(c, e, "kernel attributes");
+    if (bps < 1) return fail(c, SYNIM_ERR_SHAPE, "IM kernel does not fit on an SM");
+    if (c->ctas_per_sm > 0) bps = std::min(bps, c->ctas_per_sm);
+    const int grid = std::max(1, std::min(c->geo.n_items, c->n_sm * bps));
+    if ((e = cudaMemcpyAsync(c->d_pairs, hp, sizeof(DevPair) * np, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return cuda_fail(c, e, "parameter upload");
+    cudaEventRecord(c->slot_ev[slot], s);
+    c->slot_used[slot] = true;
+    c->slot = (slot + 1) % NSLOT;
+    if (mode == MODE_VJP && (e = cudaMemsetAsync(c->d_gp, 0, sizeof(double) * np * 4, s)) != cudaSuccess)
+        return cuda_fail(c, e, "vjp clear");
+    // profiling: pick the event pair of this launch (collect the oldest if the ring is full)
+    cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+    if (c->profile) {
+        if (c->prof_head - c->prof_tail >= (unsigned long long)NPROF) {
+            const int q = (int)(c->prof_tail % NPROF);
+            float t = 0.f;
+            if (cudaEventSynchronize(c->prof_b[q]) == cudaSuccess &&
+                cudaEventElapsedTime(&t, c->prof_a[q], c->prof_b[q]) == cudaSuccess) {
+                c->prof_acc_ms += t;
+                ++c->prof_acc_n;
+            }
+            ++c->prof_tail;
+        }
+        const int q = (int)(c->prof_head % NPROF);
+        ++c->prof_head;
+        ev_a = c->prof_a[q];
+        ev_b = c->prof_b[q];
+    }
+    // (inside a capture, only an "external" record becomes an event-record node)
+    auto enqueue = [&](cudaStream_t q, cudaEvent_t a0, cudaEvent_t b0, bool capturing) -> cudaError_t {
+        const unsigned int rf = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+        cudaError_t r = cudaMemsetAsync(c->d_counter, 0, sizeof(int), q);
+        if (r == cudaSuccess) r = launch_pst(g, c->d_pairs, c->max_mm, q);
+        if (r == cudaSuccess && a0) r = cudaEventRecordWithFlags(a0, q, rf);
+        if (r == cudaSuccess) r = launch_im(mode, g, c->d_pairs, c->d_counter, c->d_err, c->d_gp, grid, c->threads, smem, q);
+        if (r == cudaSuccess && b0) r = cudaEventRecordWithFlags(b0, q, rf);
+        return r;
+    };
+    if (c->use_graph) {
+        const auto key = std::make_tuple(mode, smem, grid, c->threads);
+        auto it = c->graphs.find(key);
+        if (it == c->graphs.end()) {
+            GraphEntry ge;
+            if ((e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+                return cuda_fail(c, e, "graph capture begin");
+            cudaError_t e1 = enqueue(c->cap, c->profile ? c->prof_a[0] : nullptr,
+                                     c->profile ? c->prof_b[0] : nullptr, true);
+            e = cudaStreamEndCapture(c->cap, &ge.graph);
+            if (e1 != cudaSuccess) {
+                if (ge.graph) cudaGraphDestroy(ge.graph);
+                return cuda_fail(c, e1, "graph capture");
+            }
+            if (e != cudaSuccess) return cuda_fail(c, e, "graph capture end");
+            if (c->profile) {
+                size_t nn = 0;
+                cudaGraphGetNodes(ge.graph, nullptr, &nn);
+                std::vector<cudaGraphNode_t> nodes(nn);
+                cudaGraphGetNodes(ge.graph, nodes.data(), &nn);
+                for (cudaGraphNode_t nd : nodes) {
+                    cudaGraphNodeType ty;
+                    cudaEvent_t ev = nullptr;
+                    if (cudaGraphNodeGetType(nd, &ty) != cudaSuccess || ty != cudaGraphNodeTypeEventRecord) continue;
+                    if (cudaGraphEventRecordNodeGetEvent(nd, &ev) != cudaSuccess) continue;
+                    if (ev == c->prof_a[0]) ge.ev_start = nd;
+                    if (ev == c->prof_b[0]) ge.ev_stop = nd;
+                }
+            }
+            e = cudaGraphInstantiate(&ge.exec, ge.graph, 0);
+            if (e != cudaSuccess) {
+                cudaGraphDestroy(ge.graph);
+                return cuda_fail(c, e, "graph instantiate");
+            }
+            it = c->graphs.emplace(key, ge).first;
+        }
+        if (c->profile) {
+            if (!it->second.ev_start || !it->second.ev_stop)
+                return fail(c, SYNIM_ERR_CUDA, "profiling: event nodes missing from the captured graph");
+            if ((e = cudaGraphExecEventRecordNodeSetEvent(it->second.exec, it->second.ev_start, ev_a)) != cudaSuccess ||
+                (e = cudaGraphExecEventRecordNodeSetEvent(it->second.exec, it->second.ev_stop, ev_b)) != cudaSuccess)
+                return cuda_fail(c, e, "profiling: event node update");
+        }
+        if ((e = cudaGraphLaunch(it->second.exec, s)) != cudaSuccess) return cuda_fail(c, e, "graph launch");
+    } else {
+        if ((e = enqueue(s, ev_a, ev_b, false)) != cudaSuccess) return cuda_fail(c, e, "launch");
+    }
+    if (mode == MODE_VJP) {
+        std::vector<double> tmp((size_t)np * 4);
+        if ((e = cudaMemcpyAsync(tmp.data(), c->d_gp, sizeof(double) * np * 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+            return cuda_fail(c, e, "vjp readback");
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(c, e, "vjp sync");
+        std::memcpy(grad_p, tmp.data(), sizeof(double) * np * 4);
+    }
+    return SYNIM_OK;
+}
+
+}  // namespace
+
+extern "C" synim_status synim_im_compute(synim_ctx *ctx, const synim_misreg *mis, float *const *im,
+                                         void *cuda_stream) {
+    if (!ctx || !mis || !im) return SYNIM_ERR_INVALID_ARG;
+    ctx->err.clear();
+    return run(ctx, MODE_FWD, mis, im, nullptr, nullptr, nullptr, static_cast<cudaStream_t>(cuda_stream));
+}

