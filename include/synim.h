@@ -163,11 +163,46 @@ synim_status synim_im_kernel_ms(synim_ctx *ctx, double *total_ms, int32_t *n_lau
 /* Free all device memory of the context (waits for its streams). NULL is a no-op. */
 void synim_im_destroy(synim_ctx *ctx);
 
+/*
+ * IM of one (DM, sensor) pair without allocating any memory.  The paper has
+ * no counterpart: this entry point exists for callers that must not allocate
+ * device memory while they run -- a real-time controller whose GPU memory is
+ * reserved once at start-up, or a host framework whose pooled allocator owns
+ * all device memory so that a direct cudaMalloc would fail or fragment it.
+ * It calls no cudaMalloc / cudaFree (nor any allocating library routine) and
+ * uses no host heap; all intermediates live in one fixed device array of
+ * SYNIM_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until
+ * the process exits.
+ *   dm:     dm->ifs must be a DEVICE pointer (ifs_on_device = 1), cube
+ *           [n_act][N][N] FP32; dm->mask is a host pointer or NULL.
+ *   wfs:    as for synim_im_create (host mask pointers).
+ *   mis:    the pair's misregistration (host).
+ *   im:     device output [n_act][2 nv] FP32 (column-major IM, layout above),
+ *           or NULL to only return the row count.
+ *   n_rows: if not NULL, receives 2 nv.
+ * Same results as synim_im_compute for the same pair.  The call synchronises
+ * cuda_stream and returns when the IM is written.  Inputs whose support
+ * windows, sensor tables and pixel maps do not fit the fixed array are
+ * rejected with SYNIM_ERR_SHAPE (message in synim_last_error(NULL)); the
+ * tables alone take about 8 M^2 + 30 n_act bytes, the windows
+ * 4 n_act (W + 3)^2 bytes for support side W.
+ * The first call on each device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.
+ * Every call shares the array and it keeps the previous call's contents:
+ * the call clears what must start at zero, but calls whose GPU work overlaps
+ * (other host threads or streams) race on it and must be serialised.
+ */
+#define SYNIM_NOALLOC_SCRATCH_BYTES (48u * 1024u * 1024u)
+synim_status synim_im_compute_noalloc(const synim_dm_desc *dm, const synim_wfs_desc *wfs,
+                                      const synim_misreg *mis, float *im, int64_t *n_rows,
+                                      void *cuda_stream);
+
 /* Static description of a status code. */
 const char *synim_status_string(synim_status s);
 
 /* Last error message recorded on ctx ("" if none); valid until the next call on ctx.
- * With ctx == NULL: the last error of a failed create on this thread. */
+ * With ctx == NULL: the last error of a failed synim_im_create or
+ * synim_im_compute_noalloc on this thread. */
 const char *synim_last_error(const synim_ctx *ctx);
 
 #ifdef __cplusplus

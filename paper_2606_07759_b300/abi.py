@@ -56,6 +56,9 @@ SIGNATURES = {
     "synim_im_check": (c_int32, [c_void_p, c_void_p]),
     "synim_dm_window": (c_int32, [c_void_p, c_int32, ctypes.POINTER(c_int32)]),
     "synim_im_kernel_ms": (c_int32, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int32)]),
+    "synim_im_compute_noalloc": (c_int32, [ctypes.POINTER(synim_dm_desc), ctypes.POINTER(synim_wfs_desc),
+                                           ctypes.POINTER(synim_misreg), c_void_p, ctypes.POINTER(c_int64),
+                                           c_void_p]),
     "synim_im_destroy": (None, [c_void_p]),
     "synim_status_string": (ctypes.c_char_p, [c_int32]),
     "synim_last_error": (ctypes.c_char_p, [c_void_p]),

@@ -24,16 +24,6 @@ namespace {
 
 thread_local std::string g_create_error;
 
-struct DmHost {
-    int n_act = 0, N = 0, W = 0, Wp = 0;
-    double dd = 0, h = 0;
-};
-
-struct WfsHost {
-    int n_sub = 0, M = 0, k = 0, nv = 0, CH = 1;
-    double D = 0, H = 0, th[2] = {0, 0}, rot = 0, mag[2] = {1, 1}, shift[2] = {0, 0}, scale = 1;
-};
-
 constexpr int NSLOT = 4;
 constexpr int NPROF = 256;
 
@@ -120,6 +110,12 @@ cudaError_t dev_upload(synim_ctx *c, T **p, const std::vector<T> &v) {
     return cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
 }
 
+}  // namespace
+
+namespace synim {
+
+void clear_create_error() { g_create_error.clear(); }
+
 // Composite affine (Sec. 2.1) in closed form:
 //   A = c dw / (dd m) R(-td) R(tw) diag(mw)
 //   b = cN + R(-td) (c s_w + h theta - s_d) / (dd m) - A (cM, cM)
@@ -175,6 +171,10 @@ int largest_divisor_le(int k, int cap) {
         if (k % c == 0) return c;
     return 1;
 }
+
+}  // namespace synim
+
+namespace {
 
 // Host tables of one sensor (Sec. 2.2): lit pixels, valid subapertures,
 // scale factors, and the telescoped derivative stencil.
@@ -290,6 +290,10 @@ bool build_wfs_tables(const synim_wfs_desc &d, WfsTables &t, std::string &why) {
     return true;
 }
 
+}  // namespace
+
+namespace synim {
+
 // Upper bound of the per-sensor accumulator floats for one pair (any
 // actuator), mirroring the kernel's box arithmetic.
 long long arena_need(const DmHost &D, const WfsHost &W, const double Ai[4], int NV) {
@@ -303,6 +307,9 @@ long long arena_need(const DmHost &D, const WfsHost &W, const double Ai[4], int 
     return (long long)NV * (2 * nxc * (nsj + 1) + 2 * nyc * (nsi + 1) + 2 * nsi * nsj);
 }
 
+}  // namespace synim
+
+namespace {
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -325,7 +332,8 @@ const char *synim_status_string(synim_status s) {
 }
 
 const char *synim_last_error(const synim_ctx *ctx) {
-    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+    if (ctx) return ctx->err.c_str();
+    return g_create_error.empty() ? synim::noalloc_last_error() : g_create_error.c_str();
 }
 
 void synim_im_destroy(synim_ctx *ctx) {

@@ -16,6 +16,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "synim.h"
+
 #define SYNIM_MAX_DM 8
 #define SYNIM_MAX_WFS 16
 #define SYNIM_MAX_PAIRS (SYNIM_MAX_DM * SYNIM_MAX_WFS)
@@ -63,9 +65,30 @@ struct Geo {
     int arena_floats;
 };
 
+// Host-side geometry of one DM and one sensor.
+struct DmHost {
+    int n_act = 0, N = 0, W = 0, Wp = 0;
+    double dd = 0, h = 0;
+};
+
+struct WfsHost {
+    int n_sub = 0, M = 0, k = 0, nv = 0, CH = 1;
+    double D = 0, H = 0, th[2] = {0, 0}, rot = 0, mag[2] = {1, 1}, shift[2] = {0, 0}, scale = 1;
+};
+
 enum { ERR_TIMEOUT = 1, ERR_ARENA = 2 };
 
 enum Mode { MODE_FWD = 0, MODE_TAN = 1, MODE_VJP = 2 };
+
+// Host helpers (synim_api.cu).
+void composite(const DmHost &D, const WfsHost &W, const synim_misreg &m, double A[4], double b[2]);
+void composite_jac(const DmHost &D, const synim_misreg &m, const double A[4], const double b[2],
+                   double dA[16], double db[8]);
+bool invert2(const double A[4], double Ai[4]);
+int largest_divisor_le(int k, int cap);
+long long arena_need(const DmHost &D, const WfsHost &W, const double Ai[4], int NV);
+void clear_create_error();         // synim_api.cu (no allocation)
+const char *noalloc_last_error();  // synim_noalloc.cu
 
 // Launch wrappers (synim_kernels.cu).
 cudaError_t launch_support(const float *cube, int n_act, int N, float eps, int *box,
