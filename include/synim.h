@@ -67,8 +67,9 @@ typedef struct {
     int32_t ifs_on_device;  /* 1: ifs is a device pointer on the current device; 0: host */
     const uint8_t *mask;    /* host [N][N] 0/1 DM mask (IFs are assumed already masked);
                                NULL = all ones */
-    float support_eps;      /* |IF| <= support_eps * max|IF_a| is treated as zero outside
-                               the actuator's support window; 0 = keep the whole grid */
+    float support_eps;      /* |IF| <= support_eps * (largest |IF| of this DM) is treated as
+                               zero outside each actuator's support window; 0 = keep the
+                               whole grid */
 } synim_dm_desc;
 
 /* One Shack-Hartmann sensor.  Sec. 2.1 (sensor transform), Sec. 2.2 (grid). */
@@ -109,7 +110,7 @@ typedef struct {
 
 /*
  * Create a context: uploads the IF cubes once, scans each IF's support
- * window (|IF| > support_eps * peak), packs the windows into device memory,
+ * window (|IF| > support_eps * the DM's largest |IF|), packs the windows into device memory,
  * and builds the per-sensor subaperture tables (Sec. 2.2) and derivative
  * stencils.  The caller may free every input as soon as create returns.
  * dms[n_dm], wfs[n_wfs]: 1 <= n_dm <= 8, 1 <= n_wfs <= 16.

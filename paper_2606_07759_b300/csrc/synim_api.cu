@@ -50,9 +50,10 @@ struct synim_ctx {
     int *d_counter = nullptr, *d_err = nullptr, *h_err = nullptr;
     double *d_gp = nullptr;
     long long pst_off[SYNIM_MAX_PAIRS] = {};
-    uint8_t *d_pst = nullptr;
-    int max_mm = 0;
-    int threads = 256, ctas_per_sm = 0;
+    long long line_off[SYNIM_MAX_PAIRS] = {};
+    uint8_t *d_pst = nullptr, *d_lines = nullptr;
+    int max_mm = 0, max_lines = 0;
+    int threads = 512, ctas_per_sm = 0;
     bool use_graph = true;
     int arena_floats = 0;
     std::map<std::tuple<int, size_t, int, int>, GraphEntry> graphs;
@@ -166,6 +167,18 @@ bool invert2(const double A[4], double Ai[4]) {
     return true;
 }
 
+void split_pair(DevPair &P) {
+    for (int q = 0; q < 4; ++q) {
+        P.Ahi[q] = (float)P.A[q];
+        P.Alo[q] = (float)(P.A[q] - (double)P.Ahi[q]);
+        P.Aif[q] = (float)P.Ai[q];
+    }
+    for (int q = 0; q < 2; ++q) {
+        P.bhi[q] = (float)P.b[q];
+        P.blo[q] = (float)(P.b[q] - (double)P.bhi[q]);
+    }
+}
+
 int largest_divisor_le(int k, int cap) {
     for (int c = std::min(k, cap); c >= 1; --c)
         if (k % c == 0) return c;
@@ -180,8 +193,10 @@ namespace {
 // scale factors, and the telescoped derivative stencil.
 struct WfsTables {
     std::vector<uint8_t> xcode, ycode;
-    std::vector<int> irr_pix, irr_sub, vsub, vrow;
+    std::vector<int> irr_pix, irr_sub, irr_sr, vsub, vrow, irrc_row, vidx;
+    std::vector<int4> irrc;
     std::vector<int8_t> irr_w;
+    std::vector<short> vsj;
     std::vector<float> fac;
     int nv = 0;
 };
@@ -222,6 +237,10 @@ bool build_wfs_tables(const synim_wfs_desc &d, WfsTables &t, std::string &why) {
     }
     t.vrow[n] = (int)t.vsub.size();
     t.nv = (int)t.vsub.size();
+    t.vidx.assign((size_t)n * n, -1);
+    for (int r = 0; r < t.nv; ++r) t.vidx[(t.vsub[r] >> 16) * n + (t.vsub[r] & 0xffff)] = r;
+    t.vsj.assign((size_t)t.nv + 4, (short)-1);
+    for (int r = 0; r < t.nv; ++r) t.vsj[r] = (short)(t.vsub[r] & 0xffff);
     if (t.nv == 0) {
         why = "sensor has no valid subaperture";
         return false;
@@ -270,11 +289,14 @@ bool build_wfs_tables(const synim_wfs_desc &d, WfsTables &t, std::string &why) {
     t.irr_pix.clear();
     t.irr_w.clear();
     t.irr_sub.assign((size_t)n * n + 1, 0);
+    t.irr_sr.assign((size_t)n * n * k + 1, 0);
     for (int si = 0; si < n; ++si)
         for (int sj = 0; sj < n; ++sj) {
             t.irr_sub[si * n + sj] = (int)t.irr_pix.size();
+            for (int r = 0; r < k; ++r) t.irr_sr[(size_t)(si * n + sj) * k + r] = (int)t.irr_pix.size();
             if (!V[si * n + sj]) continue;
-            for (int i = si * k; i < (si + 1) * k; ++i)
+            for (int i = si * k; i < (si + 1) * k; ++i) {
+                t.irr_sr[(size_t)(si * n + sj) * k + (i - si * k)] = (int)t.irr_pix.size();
                 for (int j = sj * k; j < (sj + 1) * k; ++j) {
                     const int jm = j - sj * k, im = i - si * k;
                     const int wx = (jm != 0 && jm != k - 1) ? Pv(i, j - 1) - Pv(i, j + 1) : 0;
@@ -285,8 +307,21 @@ bool build_wfs_tables(const synim_wfs_desc &d, WfsTables &t, std::string &why) {
                         t.irr_w.push_back((int8_t)wy);
                     }
                 }
+            }
         }
     t.irr_sub[(size_t)n * n] = (int)t.irr_pix.size();
+    t.irr_sr[(size_t)n * n * k] = (int)t.irr_pix.size();
+    // subapertures that have pupil-edge pixels, per subaperture row
+    t.irrc.clear();
+    t.irrc_row.assign(n + 1, 0);
+    for (int si = 0; si < n; ++si) {
+        t.irrc_row[si] = (int)t.irrc.size();
+        for (int sj = 0; sj < n; ++sj) {
+            const int e0 = t.irr_sub[si * n + sj], e1 = t.irr_sub[si * n + sj + 1];
+            if (e1 > e0) t.irrc.push_back(make_int4(sj, e0, e1, 0));
+        }
+    }
+    t.irrc_row[n] = (int)t.irrc.size();
     return true;
 }
 
@@ -389,9 +424,9 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
         c->use_graph = opts->use_graph != 0;
         c->profile = opts->profile != 0;
     }
-    if (c->threads % 32 != 0 || c->threads < 64 || c->threads > 256) {
+    if (c->threads % 32 != 0 || c->threads < 64 || c->threads > 512) {
         delete c;
-        return fail(nullptr, SYNIM_ERR_INVALID_ARG, "threads_per_cta must be a multiple of 32 in 64..256");
+        return fail(nullptr, SYNIM_ERR_INVALID_ARG, "threads_per_cta must be a multiple of 32 in 64..512");
     }
     auto bail = [&](synim_status s) {
         std::string m = c->err;
@@ -420,7 +455,7 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
         }
         int *d_box = nullptr;
         std::vector<int> box(4 * (size_t)H.n_act);
-        e = cudaMalloc(&d_box, box.size() * sizeof(int));
+        e = cudaMalloc(&d_box, (box.size() + 1) * sizeof(int));
         if (e == cudaSuccess) e = launch_support(cube, H.n_act, H.N, Dd.support_eps, d_box, 0);
         if (e == cudaSuccess) e = cudaMemcpy(box.data(), d_box, box.size() * sizeof(int), cudaMemcpyDeviceToHost);
         cudaFree(d_box);
@@ -461,7 +496,11 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
             for (size_t q = 0; q < NN; ++q) m[q] = Dd.mask[q] ? 1 : 0;
             if ((e = dev_upload(c, &d_mask, m)) != cudaSuccess) return bail(cuda_fail(c, e, "mask upload"));
         }
-        G.win = d_win; G.org = d_org; G.mask = d_mask;
+        uint8_t *d_mcls = nullptr;
+        e = dev_alloc(c, &d_mcls, (size_t)(H.N + 1) * (H.N + 1));
+        if (e == cudaSuccess) e = launch_mcls(d_mask, H.N, d_mcls, 0);
+        if (e != cudaSuccess) return bail(cuda_fail(c, e, "mask interior map"));
+        G.win = d_win; G.org = d_org; G.mask = d_mask; G.mcls = d_mcls;
         G.n_act = H.n_act; G.N = H.N; G.W = W; G.Wp = Wp; G.win_stride = stride;
         max_win = std::max(max_win, stride);
     }
@@ -496,20 +535,35 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
         if (e == cudaSuccess) e = dev_upload(c, &vs, T.vsub);
         if (e == cudaSuccess) e = dev_upload(c, &vr, T.vrow);
         if (e != cudaSuccess) return bail(cuda_fail(c, e, "sensor tables"));
+        int4 *cd = nullptr;
+        int *cr = nullptr, *sr = nullptr;
+        short *vj = nullptr;
+        int *vx = nullptr;
+        if (e == cudaSuccess) e = dev_upload(c, &vj, T.vsj);
+        if (e == cudaSuccess) e = dev_upload(c, &vx, T.vidx);
+        if (e == cudaSuccess) e = dev_upload(c, &sr, T.irr_sr);
+        if (e == cudaSuccess) e = dev_upload(c, &cd, T.irrc);
+        if (e == cudaSuccess) e = dev_upload(c, &cr, T.irrc_row);
+        if (e != cudaSuccess) return bail(cuda_fail(c, e, "sensor tables"));
+        G.irrc = cd; G.irrc_row = cr; G.irr_sr = sr; G.vsj = vj; G.vidx = vx;
         G.xcode = xc; G.ycode = yc; G.irr_pix = ip; G.irr_w = iw; G.irr_sub = is;
         G.fac = fa; G.vsub = vs; G.vrow = vr;
         G.n_sub = H.n_sub; G.M = H.M; G.k = H.k; G.nv = H.nv; G.CH = H.CH;
         c->max_mm = std::max(c->max_mm, H.M * H.M);
+        c->max_lines = std::max(c->max_lines, H.M * (H.n_sub + 1));
     }
     // ---- per-pair state maps, parameter blocks, counters ----
-    long long tot = 0;
+    long long tot = 0, tot_lines = 0;
     for (int d = 0; d < n_dm; ++d)
         for (int w = 0; w < n_wfs; ++w) {
             c->pst_off[d * n_wfs + w] = tot;
             tot += (long long)c->wh[w].M * c->wh[w].M;
+            c->line_off[d * n_wfs + w] = tot_lines;
+            tot_lines += 2LL * c->wh[w].M * (c->wh[w].n_sub + 1);
         }
     const int np = n_dm * n_wfs;
     e = dev_alloc(c, &c->d_pst, (size_t)tot);
+    if (e == cudaSuccess) e = dev_alloc(c, &c->d_lines, (size_t)tot_lines);
     if (e == cudaSuccess) e = dev_alloc(c, &c->d_pairs, (size_t)np);
     if (e == cudaSuccess) e = dev_alloc(c, &c->d_counter, 1);
     if (e == cudaSuccess) e = dev_alloc(c, &c->d_err, 1);
@@ -638,7 +692,7 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
     if (c->slot_used[slot] && (e = cudaEventSynchronize(c->slot_ev[slot])) != cudaSuccess)
         return cuda_fail(c, e, "slot wait");
     DevPair *hp = c->h_pairs[slot];
-    long long need = 0;
+    std::vector<long long> need((size_t)np);
     for (int d = 0; d < c->n_dm; ++d)
         for (int w = 0; w < c->n_wfs; ++w) {
             const int p = d * c->n_wfs + w;
@@ -651,25 +705,63 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
             composite(c->dmh[d], c->wh[w], m, P.A, P.b);
             if (!invert2(P.A, P.Ai)) return fail(c, SYNIM_ERR_INVALID_ARG, "singular composite affine");
             composite_jac(c->dmh[d], m, P.A, P.b, P.dA, P.db);
+            split_pair(P);
             P.pst = c->d_pst + c->pst_off[p];
+            P.xcc = c->d_lines + c->line_off[p];
+            P.ycc = P.xcc + (size_t)c->wh[w].M * (c->wh[w].n_sub + 1);
             if (mode == MODE_FWD) P.im = im ? im[p] : nullptr;
             if (mode == MODE_TAN) {
                 P.im = im ? im[p] : nullptr;
                 for (int q = 0; q < 4; ++q) P.dim[q] = dim ? dim[4 * p + q] : nullptr;
             }
             if (mode == MODE_VJP) P.gim = gim ? gim[p] : nullptr;
-            need = std::max(need, arena_need(c->dmh[d], c->wh[w], P.Ai, NV));
+            need[p] = (arena_need(c->dmh[d], c->wh[w], P.Ai, NV) + 31) / 32 * 32;
         }
-    if (need > c->arena_floats) c->arena_floats = (int)((need + 255) / 256 * 256);
+    // Accumulator arena: all sensors of a DM in one group when that fits the
+    // shared memory of 2 CTAs per SM (forward) or 1 CTA per SM (tangents).
     Geo g = c->geo;
-    g.arena_floats = c->arena_floats;
-    const size_t smem = im_smem_bytes(g);
-    int dev_max = 0;
+    int dev_max = 0, sm_max = 0;
     cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
-    if (smem + 8192 > (size_t)dev_max)
+    cudaDeviceGetAttribute(&sm_max, cudaDevAttrMaxSharedMemoryPerMultiprocessor, c->device);
+    g.arena_floats = 0;
+    const size_t fixed = im_smem_bytes(g) + (mode == MODE_VJP ? 8 * 4 * SYNIM_MAX_PAIRS : 64);
+    const int target = (mode == MODE_FWD) ? 2 : 1;
+    const long long budget =
+        std::min<long long>(dev_max, sm_max / target - 1024) - (long long)fixed;
+    long long cap = 0, single = 0;
+    for (int d = 0; d < c->n_dm; ++d) {
+        long long sum = 0;
+        for (int w = 0; w < c->n_wfs; ++w) {
+            sum += need[d * c->n_wfs + w];
+            single = std::max(single, need[d * c->n_wfs + w]);
+        }
+        cap = std::max(cap, sum);
+    }
+    cap = std::max(std::min(cap, budget / 4), single);
+    cap = std::max<long long>(cap, c->arena_floats);  // never shrink: keeps the captured graph
+    if ((long long)fixed + 4 * cap > dev_max)
         return fail(c, SYNIM_ERR_SHAPE,
-                    "support window + accumulators need " + std::to_string(smem) +
-                        " bytes of shared memory; reduce support_eps' window or the grid");
+                    "support window + accumulators need " + std::to_string(fixed + 4 * cap) +
+                        " bytes of shared memory; lower the grid or raise support_eps");
+    c->arena_floats = (int)cap;
+    g.arena_floats = c->arena_floats;
+    for (int d = 0; d < c->n_dm; ++d) {
+        int grp = 0;
+        long long used = 0;
+        for (int w = 0; w < c->n_wfs; ++w) {
+            const int p = d * c->n_wfs + w;
+            if (used + need[p] > cap && used > 0) {
+                ++grp;
+                used = 0;
+            }
+            hp[p].group = grp;
+            hp[p].arena_off = (int)used;
+            hp[p].arena_len = (int)need[p];
+            used += need[p];
+        }
+        g.n_groups[d] = grp + 1;
+    }
+    const size_t smem = im_smem_bytes(g);
     int bps = 0;
     if ((e = im_prepare(mode, c->threads, smem, &bps)) != cudaSuccess) return cuda_fail(c, e, "kernel attributes");
     if (bps < 1) return fail(c, SYNIM_ERR_SHAPE, "IM kernel does not fit on an SM");
@@ -704,7 +796,7 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
     auto enqueue = [&](cudaStream_t q, cudaEvent_t a0, cudaEvent_t b0, bool capturing) -> cudaError_t {
         const unsigned int rf = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
         cudaError_t r = cudaMemsetAsync(c->d_counter, 0, sizeof(int), q);
-        if (r == cudaSuccess) r = launch_pst(g, c->d_pairs, c->max_mm, q);
+        if (r == cudaSuccess) r = launch_pst(g, c->d_pairs, c->max_mm, c->max_lines, q);
         if (r == cudaSuccess && a0) r = cudaEventRecordWithFlags(a0, q, rf);
         if (r == cudaSuccess) r = launch_im(mode, g, c->d_pairs, c->d_counter, c->d_err, c->d_gp, grid, c->threads, smem, q);
         if (r == cudaSuccess && b0) r = cudaEventRecordWithFlags(b0, q, rf);

@@ -9,8 +9,12 @@
 //              telescoped derivative stencil: xcode/ycode per subaperture
 //              boundary line pair, and the irregular pixels where the pupil
 //              edge crosses a subaperture.
-//   per pair   pixel state map [M][M] (0 zero, 1 strict core, 2 repair ring),
-//              rebuilt every call because it depends on the misregistration.
+//   per pair   strict-core map [M][M] (0/1) and, for the two pixel lines at
+//              every subaperture boundary, one byte per (line pixel pair)
+//              holding the stencil bits and both pixels' classes (zero /
+//              core / ring), stored [pixel][boundary] so that the threads of
+//              a warp (consecutive boundaries) read consecutive bytes; both
+//              rebuilt every call because they depend on the misregistration.
 #pragma once
 
 #include <cstdint>
@@ -28,6 +32,8 @@ struct DevDM {
     const float *win;     // [n_act][win_stride]
     const int *org;       // [n_act][2] window origin (wx0, wy0), DM pixels
     const uint8_t *mask;  // [N][N] 0/1, or nullptr = all ones
+    const uint8_t *mcls;  // [(N+1)][(N+1)] taps of the 3x3 cells around cell (x-1, y-1):
+                          // 0 all zero, 1 all one, 2 mixed (interior test of the core)
     int n_act, N, W, Wp;
     int win_stride;       // floats per packed window, multiple of 4 (16-byte bulk copies)
 };
@@ -38,8 +44,13 @@ struct DevWFS {
     const int *irr_pix;    // [n_irr] (i << 16) | j, grouped by subaperture (row-major)
     const int8_t *irr_w;   // [n_irr][2] weights (wx, wy) in {-1, 0, 1}
     const int *irr_sub;    // [n_sub * n_sub + 1] first entry of each subaperture
+    const int *irr_sr;     // [n_sub * n_sub * k + 1] first entry of each (subaperture, pixel row)
+    const int4 *irrc;      // subapertures that have irregular pixels: (sj, e0, e1, 0)
+    const int *irrc_row;   // [n_sub + 1] first candidate of each subaperture row
     const float *fac;      // [nv] slope_scale / (2 dw lit)
     const int *vsub;       // [nv] (si << 16) | sj of each valid row
+    const short *vsj;      // [nv + 4] sj of each valid row (padded with -1: 4-row loads)
+    const int *vidx;       // [n_sub * n_sub] valid row of each subaperture, -1 if invalid
     const int *vrow;       // [n_sub + 1] first valid row of each subaperture row
     int n_sub, M, k, nv, CH;
 };
@@ -49,10 +60,16 @@ struct DevPair {
     double A[4], b[2];   // DM pixel = A (j, i) + b
     double Ai[4];        // inverse of A
     double dA[16], db[8];  // d(A, b)/dp_k, p = (shift x px, shift y px, rot deg, mag)
+    float Ahi[4], Alo[4], bhi[2], blo[2];  // A, b as float pairs (compensated origins)
+    float Aif[4];        // inverse of A, float (pixel boxes, with a margin)
+    int arena_off;       // shared-memory accumulator offset of this pair (floats)
+    int arena_len;       // floats reserved for it (upper bound over actuators)
+    int group;           // sensors of one DM are processed in groups that fit the arena
+    uint8_t *xcc, *ycc;  // [M][n_sub + 1] boundary-line bytes (see above)
     float *im;           // output [n_act][2 nv] or nullptr (skip)
     float *dim[4];       // tangent outputs or nullptr
     const float *gim;    // VJP input [n_act][2 nv] or nullptr
-    uint8_t *pst;        // [M][M] pixel state
+    uint8_t *pst;        // [M][M] strict core (0/1)
 };
 
 struct Geo {
@@ -63,6 +80,7 @@ struct Geo {
     int order_start[SYNIM_MAX_DM + 1];  // item prefix in processing order
     int max_win_floats;
     int arena_floats;
+    int n_groups[SYNIM_MAX_DM];
 };
 
 // Host-side geometry of one DM and one sensor.
@@ -87,15 +105,18 @@ void composite_jac(const DmHost &D, const synim_misreg &m, const double A[4], co
 bool invert2(const double A[4], double Ai[4]);
 int largest_divisor_le(int k, int cap);
 long long arena_need(const DmHost &D, const WfsHost &W, const double Ai[4], int NV);
+void split_pair(DevPair &P);  // float pairs of A, b and the float inverse
 void clear_create_error();         // synim_api.cu (no allocation)
 const char *noalloc_last_error();  // synim_noalloc.cu
 
 // Launch wrappers (synim_kernels.cu).
+// box: 4 * n_act + 1 ints (the extra one is scratch for the DM peak)
 cudaError_t launch_support(const float *cube, int n_act, int N, float eps, int *box,
                            cudaStream_t s);
 cudaError_t launch_pack(const float *cube, int n_act, int N, const int *org, int W, int Wp,
                         int stride, float *win, cudaStream_t s);
-cudaError_t launch_pst(const Geo &g, const DevPair *pairs, int max_mm, cudaStream_t s);
+cudaError_t launch_mcls(const uint8_t *mask, int N, uint8_t *mcls, cudaStream_t s);
+cudaError_t launch_pst(const Geo &g, const DevPair *pairs, int max_mm, int max_lines, cudaStream_t s);
 size_t im_smem_bytes(const Geo &g);
 cudaError_t im_prepare(int mode, int threads, size_t smem, int *blocks_per_sm);
 cudaError_t launch_im(int mode, const Geo &g, const DevPair *pairs, int *counter, int *err,

@@ -55,6 +55,9 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
         "l"(src), "r"(bytes), "r"(bar)
         : "memory");
 }
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -102,15 +105,25 @@ struct MaxI { __device__ int operator()(int a, int b) const { return max(a, b); 
 // ---------------------------------------------------------------------------
 // Create time: support box and window packing
 // ---------------------------------------------------------------------------
-// box[a] = {x0, x1, y0, y1} of |IF_a| > eps * max|IF_a| (x1 < x0 if empty).
-__global__ void k_support(const float *__restrict__ cube, int N, float eps, int *__restrict__ box) {
+// peak[a] = max |IF_a|; the DM's largest is folded into *dm_peak (float bits,
+// non-negative, so an integer max orders them).
+__global__ void k_peak(const float *__restrict__ cube, int N, unsigned *__restrict__ dm_peak) {
     const int a = blockIdx.x;
     const size_t NN = (size_t)N * N;
     const float *img = cube + (size_t)a * NN;
     float m = 0.f;
     for (size_t p = threadIdx.x; p < NN; p += blockDim.x) m = fmaxf(m, fabsf(img[p]));
     m = block_reduce(m, MaxF(), 0.f);
-    const float thr = eps * m;
+    if (threadIdx.x == 0) atomicMax(dm_peak, __float_as_uint(m));
+}
+
+// box[a] = {x0, x1, y0, y1} of |IF_a| > eps * (largest |IF| of the DM) (x1 < x0 if empty).
+__global__ void k_support(const float *__restrict__ cube, int N, float eps, const unsigned *__restrict__ dm_peak,
+                          int *__restrict__ box) {
+    const int a = blockIdx.x;
+    const size_t NN = (size_t)N * N;
+    const float *img = cube + (size_t)a * NN;
+    const float thr = eps * __uint_as_float(*dm_peak);
     int x0 = INT_MAX, x1 = -1, y0 = INT_MAX, y1 = -1;
     for (size_t p = threadIdx.x; p < NN; p += blockDim.x) {
         if (fabsf(img[p]) > thr) {
@@ -147,13 +160,40 @@ __global__ void k_pack(const float *__restrict__ cube, int N, const int *__restr
 
 cudaError_t launch_support(const float *cube, int n_act, int N, float eps, int *box,
                            cudaStream_t s) {
-    k_support<<<n_act, 256, 0, s>>>(cube, N, eps, box);
+    // box holds 4 * n_act + 1 ints: the last one is the DM peak
+    unsigned *peak = reinterpret_cast<unsigned *>(box + 4 * (size_t)n_act);
+    cudaError_t e = cudaMemsetAsync(peak, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    k_peak<<<n_act, 256, 0, s>>>(cube, N, peak);
+    k_support<<<n_act, 256, 0, s>>>(cube, N, eps, peak, box);
     return cudaGetLastError();
 }
 
 cudaError_t launch_pack(const float *cube, int n_act, int N, const int *org, int W, int Wp,
                         int stride, float *win, cudaStream_t s) {
     k_pack<<<n_act, 256, 0, s>>>(cube, N, org, W, Wp, stride, win);
+    return cudaGetLastError();
+}
+
+// Interior map of a DM mask for the strict-core test: for the bilinear cell
+// (cx, cy) (taps cx..cx+1, cy..cy+1; cx, cy in [-1, N-1]) record whether all
+// 16 taps of the 3 x 3 cells around it are 0, all 1, or mixed.  A FP32 cell
+// can be off by one, so a uniform neighbourhood settles the core decision.
+__global__ void k_mcls(const uint8_t *__restrict__ mask, int N, uint8_t *__restrict__ mcls) {
+    const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long N1 = N + 1;
+    if (q >= N1 * N1) return;
+    const int cy = (int)(q / N1) - 1, cx = (int)(q - (q / N1) * N1) - 1;
+    int ones = 0;
+    for (int y = cy - 1; y <= cy + 2; ++y)
+        for (int x = cx - 1; x <= cx + 2; ++x)
+            ones += (x >= 0 && y >= 0 && x < N && y < N) ? (mask ? (mask[(long)y * N + x] != 0) : 1) : 0;
+    mcls[q] = ones == 0 ? 0 : (ones == 16 ? 1 : 2);
+}
+
+cudaError_t launch_mcls(const uint8_t *mask, int N, uint8_t *mcls, cudaStream_t s) {
+    const long n = (long)(N + 1) * (N + 1);
+    k_mcls<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(mask, N, mcls);
     return cudaGetLastError();
 }
 
@@ -166,34 +206,48 @@ __device__ __forceinline__ int mask_tap(const uint8_t *__restrict__ mask, int N,
 }
 
 // Strict core: bilinear(DM mask) >= 0.999999 at the composite-affine image of
-// each sensor pixel.  The decision is taken in FP64 with the operations of
-// the definition (no contraction); an FP32 pre-test settles the cells whose
-// four taps agree and whose fractional position is far from an integer.
+// each sensor pixel.  The decision is the FP64 definition (no contraction);
+// FP32 pre-tests settle every pixel whose neighbourhood of mask taps is
+// uniform, and every pixel whose four taps agree and whose fractional position
+// is far from an integer, so FP64 runs only at mask edges near cell lines.
 __global__ void k_pst_core(const __grid_constant__ Geo g, const DevPair *__restrict__ pairs) {
     const int p = blockIdx.y;
     const int d = p / g.n_wfs, w = p - d * g.n_wfs;
     const int M = g.wfs[w].M;
     const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long)M * M) return;
-    uint8_t *pst = pairs[p].pst;
+    const DevPair &P = pairs[p];
+    uint8_t *pst = P.pst;
     if (!pst) return;
     const int i = (int)(idx / M), j = (int)(idx - (long)i * M);
     const int N = g.dm[d].N;
     const uint8_t *mask = g.dm[d].mask;
-    const double *A = pairs[p].A, *b = pairs[p].b;
-    const float xf = fmaf((float)A[0], (float)j, fmaf((float)A[1], (float)i, (float)b[0]));
-    const float yf = fmaf((float)A[2], (float)j, fmaf((float)A[3], (float)i, (float)b[1]));
-    const float fx0 = floorf(xf), fy0 = floorf(yf);
-    const float fxf = xf - fx0, fyf = yf - fy0;
-    int core;
-    if (fxf > 0.01f && fxf < 0.99f && fyf > 0.01f && fyf < 0.99f && fabsf(xf) < 1e6f &&
-        fabsf(yf) < 1e6f) {
-        // FP32 coordinate error < 1e-3 px here, so the cell is certain; every
-        // weight is > 1e-4, so any zero tap puts the mask below 0.999999.
-        const long ix = (long)fx0, iy = (long)fy0;
-        core = mask_tap(mask, N, ix, iy) & mask_tap(mask, N, ix + 1, iy) &
-               mask_tap(mask, N, ix, iy + 1) & mask_tap(mask, N, ix + 1, iy + 1);
+    const float xf = fmaf(P.Ahi[0], (float)j, fmaf(P.Ahi[1], (float)i, P.bhi[0]));
+    const float yf = fmaf(P.Ahi[2], (float)j, fmaf(P.Ahi[3], (float)i, P.bhi[1]));
+    int core = -1;
+    if (!(fabsf(xf) < 1e6f && fabsf(yf) < 1e6f)) {
+        core = 0;
     } else {
+        const float fx0 = floorf(xf), fy0 = floorf(yf);
+        const int ix = (int)fx0, iy = (int)fy0;
+        if (ix < -2 || iy < -2 || ix > N || iy > N) {
+            core = 0;  // every tap of every candidate cell is off the grid
+        } else if (ix >= -1 && iy >= -1 && ix <= N - 1 && iy <= N - 1) {
+            const int c = g.dm[d].mcls[(long)(iy + 1) * (N + 1) + (ix + 1)];
+            if (c != 2) core = c;
+        }
+        if (core < 0) {
+            const float fxf = xf - fx0, fyf = yf - fy0;
+            if (fxf > 0.01f && fxf < 0.99f && fyf > 0.01f && fyf < 0.99f) {
+                // FP32 coordinate error < 1e-3 px: the cell is certain; every
+                // weight is > 1e-4, so any zero tap puts the mask below 0.999999.
+                core = mask_tap(mask, N, ix, iy) & mask_tap(mask, N, ix + 1, iy) &
+                       mask_tap(mask, N, ix, iy + 1) & mask_tap(mask, N, ix + 1, iy + 1);
+            }
+        }
+    }
+    if (core < 0) {
+        const double *A = P.A, *b = P.b;
         const double x = __dadd_rn(__dadd_rn(__dmul_rn(A[0], (double)j), __dmul_rn(A[1], (double)i)), b[0]);
         const double y = __dadd_rn(__dadd_rn(__dmul_rn(A[2], (double)j), __dmul_rn(A[3], (double)i)), b[1]);
         const double x0 = floor(x), y0 = floor(y);
@@ -209,26 +263,52 @@ __global__ void k_pst_core(const __grid_constant__ Geo g, const DevPair *__restr
     pst[idx] = (uint8_t)core;
 }
 
-// Ring: non-core pixels with a core 4-neighbour.  Only 0 -> 2 transitions are
-// written and only "== 1" is read, so the in-place update is race-free.
-__global__ void k_pst_ring(const __grid_constant__ Geo g, const DevPair *__restrict__ pairs) {
-    const int p = blockIdx.y;
-    const int w = p % g.n_wfs;
-    const int M = g.wfs[w].M;
-    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long)M * M) return;
-    uint8_t *pst = pairs[p].pst;
-    if (!pst || pst[idx] != 0) return;
-    const int i = (int)(idx / M), j = (int)(idx - (long)i * M);
-    const bool ring = (j + 1 < M && pst[idx + 1] == 1) || (j >= 1 && pst[idx - 1] == 1) ||
-                      (i + 1 < M && pst[idx + M] == 1) || (i >= 1 && pst[idx - M] == 1);
-    if (ring) pst[idx] = 2;
+// Class of a sensor pixel from the core map: 1 core, 2 ring (Sec. 2.3 step 2:
+// a non-core pixel with a core 4-neighbour), 0 otherwise.
+__device__ __forceinline__ int pixel_class(const uint8_t *__restrict__ pst, int M, int i, int j) {
+    const long q = (long)i * M + j;
+    if (pst[q]) return 1;
+    const bool ring = (j + 1 < M && pst[q + 1]) || (j >= 1 && pst[q - 1]) ||
+                      (i + 1 < M && pst[q + M]) || (i >= 1 && pst[q - M]);
+    return ring ? 2 : 0;
 }
 
-cudaError_t launch_pst(const Geo &g, const DevPair *pairs, int max_mm, cudaStream_t s) {
+// Boundary-line bytes: for boundary b and pixel row i (x) / column j (y):
+// bits 0-3 = stencil bits of the sensor, bits 4-5 / 6-7 = classes of the two
+// line pixels (b k - 1 and b k).  Stored [i][b] so that consecutive b are
+// consecutive bytes.
+__global__ void k_pst_codes(const __grid_constant__ Geo g, const DevPair *__restrict__ pairs) {
+    const int p = blockIdx.y;
+    const int w = p % g.n_wfs;
+    const DevWFS &WF = g.wfs[w];
+    const int M = WF.M, n1 = WF.n_sub + 1, k = WF.k;
+    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 2L * M * n1) return;
+    const DevPair &P = pairs[p];
+    if (!P.pst) return;
+    const int dir = (int)(idx / ((long)M * n1));
+    const long r = idx - (long)dir * M * n1;
+    const int x = (int)(r / n1), b = (int)(r - (long)x * n1);
+    const int c0 = b * k - 1, c1 = b * k;
+    int code;
+    if (dir == 0) {
+        code = WF.xcode[(long)b * M + x];
+        const int k0 = (c0 >= 0) ? pixel_class(P.pst, M, x, c0) : 0;
+        const int k1 = (c1 < M) ? pixel_class(P.pst, M, x, c1) : 0;
+        P.xcc[r] = (uint8_t)(code | (k0 << 4) | (k1 << 6));
+    } else {
+        code = WF.ycode[(long)b * M + x];
+        const int k0 = (c0 >= 0) ? pixel_class(P.pst, M, c0, x) : 0;
+        const int k1 = (c1 < M) ? pixel_class(P.pst, M, c1, x) : 0;
+        P.ycc[r] = (uint8_t)(code | (k0 << 4) | (k1 << 6));
+    }
+}
+
+cudaError_t launch_pst(const Geo &g, const DevPair *pairs, int max_mm, int max_lines, cudaStream_t s) {
     dim3 grid((max_mm + 255) / 256, g.n_dm * g.n_wfs);
     k_pst_core<<<grid, 256, 0, s>>>(g, pairs);
-    k_pst_ring<<<grid, 256, 0, s>>>(g, pairs);
+    dim3 grid2((2 * max_lines + 255) / 256, g.n_dm * g.n_wfs);
+    k_pst_codes<<<grid2, 256, 0, s>>>(g, pairs);
     return cudaGetLastError();
 }
 
@@ -239,12 +319,26 @@ struct ItemWfs {
     int pi0, pi1, pj0, pj1;  // pixel box where phi may be non-zero (inclusive)
     int si0, si1, sj0, sj1;  // subapertures whose slopes may be non-zero (inclusive)
     int nxc, nb, nyc, nbr;   // row chunks x column boundaries; column chunks x row boundaries
-    int ntask, need, arena, empty;
+    int ntask, arena, group, empty;
+    int xcid0, ycid0;        // first row / column chunk ids (pi0 / CH, pj0 / CH)
+    float inv_nb, inv_nbr;   // 1 / nb, 1 / nbr (task decode without integer division)
     float xo, yo;            // padded-window coordinates of pixel (pi0, pj0)
     float a00, a01, a10, a11;
     float dxo[4], dyo[4], da[16];  // tangents of the coordinates (MODE_TAN / MODE_VJP)
-    const uint8_t *pst;
+    const uint8_t *pst, *xcc, *ycc;
 };
+
+// Bilinear sample of a zero-bordered window at padded coordinates (x, y);
+// zero when the cell does not touch the window.
+__device__ __forceinline__ float bil_xy(const float *__restrict__ win, int Wp, float Wf1, float x, float y) {
+    if (!(x > 0.f && x < Wf1 && y > 0.f && y < Wf1)) return 0.f;
+    const int ix = __float2int_rd(x), iy = __float2int_rd(y);
+    const float fx = x - (float)ix, fy = y - (float)iy;
+    const float *q = win + iy * Wp + ix;
+    const float v00 = q[0], v10 = q[1], v01 = q[Wp], v11 = q[Wp + 1];
+    const float top = fmaf(fx, v10 - v00, v00), bot = fmaf(fx, v11 - v01, v01);
+    return fmaf(fy, bot - top, top);
+}
 
 template <int NV>
 struct Eval {
@@ -296,8 +390,9 @@ struct Eval {
         }
     }
 
-    // Edge repair step 3 (Sec. 2.3) at a ring pixel.
-    __device__ void ring(int i, int j, float *v) const {
+    // Edge repair step 3 (Sec. 2.3) at a ring pixel: mean over the valid
+    // cardinal directions of 2 P1 - P2 (or P1); P1, P2 must be strict core.
+    __device__ __forceinline__ void ring(int i, int j, float *v) const {
         float acc[NV];
 #pragma unroll
         for (int t = 0; t < NV; ++t) acc[t] = 0.f;
@@ -308,11 +403,11 @@ struct Eval {
             const int dj = (d == 0) ? 1 : (d == 1 ? -1 : 0);
             const int i1 = i + di, j1 = j + dj;
             if (i1 < 0 || i1 >= M || j1 < 0 || j1 >= M) continue;
-            if (pst[i1 * M + j1] != 1) continue;
+            if (!pst[i1 * M + j1]) continue;
             float v1[NV];
             bil(i1, j1, v1);
             const int i2 = i1 + di, j2 = j1 + dj;
-            if (i2 >= 0 && i2 < M && j2 >= 0 && j2 < M && pst[i2 * M + j2] == 1) {
+            if (i2 >= 0 && i2 < M && j2 >= 0 && j2 < M && pst[i2 * M + j2]) {
                 float v2[NV];
                 bil(i2, j2, v2);
 #pragma unroll
@@ -328,19 +423,19 @@ struct Eval {
         for (int t = 0; t < NV; ++t) v[t] = acc[t] * inv;
     }
 
-    // Repaired phase (and tangents) at sensor pixel (i, j).
-    __device__ __forceinline__ void eval(int i, int j, float *v) const {
-        const int st = pst[i * M + j];
-        if (st == 1) {
+    // Repaired phase (and tangents) at (i, j) of known class (0 zero, 1 core, 2 ring).
+    __device__ __forceinline__ void eval_cls(int i, int j, int cls, float *v) const {
+        if (cls == 1) {
             bil(i, j, v);
-            return;
-        }
-        if (st == 0) {
+        } else if (cls == 0) {
 #pragma unroll
             for (int t = 0; t < NV; ++t) v[t] = 0.f;
-            return;
+        } else {
+            ring(i, j, v);
         }
-        ring(i, j, v);
+    }
+    __device__ __forceinline__ void eval(int i, int j, float *v) const {
+        eval_cls(i, j, pixel_class(pst, M, i, j), v);
     }
 };
 
@@ -349,6 +444,13 @@ __device__ __forceinline__ void decode_item(const Geo &g, int item, int &d, int 
     while (pos + 1 < g.n_dm && item >= g.order_start[pos + 1]) ++pos;
     d = g.order_dm[pos];
     a = item - g.order_start[pos];
+}
+
+__device__ __forceinline__ void prefetch_window(const Geo &g, int item) {
+    int d, a;
+    decode_item(g, item, d, a);
+    const DevDM &D = g.dm[d];
+    bulk_prefetch_l2(D.win + (size_t)a * D.win_stride, (uint32_t)D.win_stride * 4u);
 }
 
 __device__ __forceinline__ void issue_window(const Geo &g, int item, float *s_win, uint32_t bar) {
@@ -368,56 +470,87 @@ __device__ __forceinline__ bool pair_active(const DevPair &P) {
     return P.gim != nullptr;
 }
 
+// a + b with the rounding error added to err (Knuth's two-sum; exact).
+__device__ __forceinline__ float two_sum(float a, float b, float &err) {
+    const float s = __fadd_rn(a, b);
+    const float z = __fsub_rn(s, a);
+    err = __fadd_rn(err, __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z)));
+    return s;
+}
+
+// (Ah + Al) j + (Bh + Bl) i + (ch + cl) - off, evaluated with error-free
+// products and sums so that the only rounding is the final one.
+__device__ __forceinline__ float exact_affine(float Ah, float Al, float Bh, float Bl, float ch, float cl,
+                                              int j, int i, int off) {
+    const float fj = (float)j, fi = (float)i;
+    const float p1 = __fmul_rn(Ah, fj), p2 = __fmul_rn(Bh, fi);
+    float err = __fadd_rn(__fadd_rn(fmaf(Ah, fj, -p1), fmaf(Bh, fi, -p2)),
+                          __fadd_rn(fmaf(Al, fj, __fmul_rn(Bl, fi)), cl));
+    float sum = two_sum(p1, p2, err);
+    sum = two_sum(sum, ch, err);
+    sum = two_sum(sum, (float)(-off), err);
+    return __fadd_rn(sum, err);
+}
+
 // Pixel box of actuator a on sensor w, task counts and local coordinates.
 template <int MODE, int NV>
 __device__ void make_info(const Geo &g, const DevPair *__restrict__ pairs, int d, int a, int w,
-                          ItemWfs &s) {
+                          ItemWfs &s, int *err) {
     const DevPair &P = pairs[d * g.n_wfs + w];
     const DevWFS &WF = g.wfs[w];
     const DevDM &D = g.dm[d];
     const int M = WF.M, k = WF.k, CH = WF.CH;
-    s.pst = P.pst;
+    s.pst = P.pst; s.xcc = P.xcc; s.ycc = P.ycc;
+    s.arena = P.arena_off;
+    s.group = P.group;
     s.empty = 1;
     s.ntask = 0;
-    s.need = 0;
     s.si0 = 1; s.si1 = 0; s.sj0 = 1; s.sj1 = 0;
     s.pi0 = 1; s.pi1 = 0; s.pj0 = 1; s.pj1 = 0;
     if (!pair_active<MODE>(P)) return;
     const int wx0 = D.org[2 * a], wy0 = D.org[2 * a + 1];
-    // Cells that touch the window: x in (wx0 - 1, wx0 + W), y likewise.
-    double jmin = 1e300, jmax = -1e300, imin = 1e300, imax = -1e300;
+    // cells that touch the window: x in (wx0 - 1, wx0 + W), y likewise
+    float jmin = 3e38f, jmax = -3e38f, imin = 3e38f, imax = -3e38f;
 #pragma unroll
     for (int cx = 0; cx < 2; ++cx)
 #pragma unroll
         for (int cy = 0; cy < 2; ++cy) {
-            const double dx = (cx ? (double)(wx0 + D.W) : (double)(wx0 - 1)) - P.b[0];
-            const double dy = (cy ? (double)(wy0 + D.W) : (double)(wy0 - 1)) - P.b[1];
-            const double jj = P.Ai[0] * dx + P.Ai[1] * dy;
-            const double ii = P.Ai[2] * dx + P.Ai[3] * dy;
-            jmin = fmin(jmin, jj); jmax = fmax(jmax, jj);
-            imin = fmin(imin, ii); imax = fmax(imax, ii);
+            const float dx = (float)(cx ? wx0 + D.W : wx0 - 1) - P.bhi[0];
+            const float dy = (float)(cy ? wy0 + D.W : wy0 - 1) - P.bhi[1];
+            const float jj = fmaf(P.Aif[0], dx, P.Aif[1] * dy);
+            const float ii = fmaf(P.Aif[2], dx, P.Aif[3] * dy);
+            jmin = fminf(jmin, jj); jmax = fmaxf(jmax, jj);
+            imin = fminf(imin, ii); imax = fmaxf(imax, ii);
         }
+    const float lo = -8.f, hi = (float)M + 8.f;
+    jmin = fmaxf(jmin, lo); imin = fmaxf(imin, lo); jmax = fminf(jmax, hi); imax = fminf(imax, hi);
     // ring reach 2 + 1 pixel of rounding margin
-    const double lo = -8.0, hi = (double)M + 8.0;
-    jmin = fmax(jmin, lo); imin = fmax(imin, lo); jmax = fmin(jmax, hi); imax = fmin(imax, hi);
-    const int pj0 = max(0, (int)floor(jmin) - 3), pj1 = min(M - 1, (int)ceil(jmax) + 3);
-    const int pi0 = max(0, (int)floor(imin) - 3), pi1 = min(M - 1, (int)ceil(imax) + 3);
+    const int pj0 = max(0, (int)floorf(jmin) - 3), pj1 = min(M - 1, (int)ceilf(jmax) + 3);
+    const int pi0 = max(0, (int)floorf(imin) - 3), pi1 = min(M - 1, (int)ceilf(imax) + 3);
     if (pj0 > pj1 || pi0 > pi1) return;
+    // slopes reach one pixel further (the central difference)
+    const int si0 = max(pi0 - 1, 0) / k, si1 = min(pi1 + 1, M - 1) / k;
+    const int sj0 = max(pj0 - 1, 0) / k, sj1 = min(pj1 + 1, M - 1) / k;
+    const int nxc = pi1 / CH - pi0 / CH + 1, nb = sj1 - sj0 + 2;
+    const int nyc = pj1 / CH - pj0 / CH + 1, nbr = si1 - si0 + 2;
+    const int nsub = (si1 - si0 + 1) * (sj1 - sj0 + 1);
+    const int need = NV * (2 * nxc * nb + 2 * nyc * nbr + 2 * nsub);
+    if (need > P.arena_len) {
+        atomicOr(err, ERR_ARENA);
+        return;
+    }
     s.empty = 0;
     s.pi0 = pi0; s.pi1 = pi1; s.pj0 = pj0; s.pj1 = pj1;
-    // slopes reach one pixel further (the central difference)
-    s.si0 = max(pi0 - 1, 0) / k; s.si1 = min(pi1 + 1, M - 1) / k;
-    s.sj0 = max(pj0 - 1, 0) / k; s.sj1 = min(pj1 + 1, M - 1) / k;
-    s.nxc = pi1 / CH - pi0 / CH + 1;
-    s.nb = s.sj1 - s.sj0 + 2;
-    s.nyc = pj1 / CH - pj0 / CH + 1;
-    s.nbr = s.si1 - s.si0 + 2;
-    const int nsub = (s.si1 - s.si0 + 1) * (s.sj1 - s.sj0 + 1);
-    s.ntask = s.nxc * s.nb + s.nyc * s.nbr;
-    s.need = NV * (2 * s.nxc * s.nb + 2 * s.nyc * s.nbr + 2 * nsub);
-    s.xo = (float)(P.A[0] * pj0 + P.A[1] * pi0 + P.b[0] - (double)(wx0 - 1));
-    s.yo = (float)(P.A[2] * pj0 + P.A[3] * pi0 + P.b[1] - (double)(wy0 - 1));
-    s.a00 = (float)P.A[0]; s.a01 = (float)P.A[1]; s.a10 = (float)P.A[2]; s.a11 = (float)P.A[3];
+    s.si0 = si0; s.si1 = si1; s.sj0 = sj0; s.sj1 = sj1;
+    s.nxc = nxc; s.nb = nb; s.nyc = nyc; s.nbr = nbr;
+    s.ntask = nxc * nb + nyc * nbr;
+    s.xcid0 = pi0 / CH;
+    s.ycid0 = pj0 / CH;
+    s.inv_nb = 1.f / (float)nb;
+    s.inv_nbr = 1.f / (float)nbr;
+    s.xo = exact_affine(P.Ahi[0], P.Alo[0], P.Ahi[1], P.Alo[1], P.bhi[0], P.blo[0], pj0, pi0, wx0 - 1);
+    s.yo = exact_affine(P.Ahi[2], P.Alo[2], P.Ahi[3], P.Alo[3], P.bhi[1], P.blo[1], pj0, pi0, wy0 - 1);
+    s.a00 = P.Ahi[0]; s.a01 = P.Ahi[1]; s.a10 = P.Ahi[2]; s.a11 = P.Ahi[3];
     if (NV == 5) {
         for (int q = 0; q < 4; ++q) {
             s.dxo[q] = (float)(P.dA[4 * q + 0] * pj0 + P.dA[4 * q + 1] * pi0 + P.db[2 * q + 0]);
@@ -427,74 +560,197 @@ __device__ void make_info(const Geo &g, const DevPair *__restrict__ pairs, int d
     }
 }
 
-// One telescoped line task: a column pair (XB) over a chunk of rows, or a row
-// pair (YB) over a chunk of columns.
+// floor(u / n) for 0 <= u < 2^24 from a float reciprocal, corrected to exact.
+__device__ __forceinline__ int fast_div(int u, int n, float inv) {
+    int c = __float2int_rz((float)u * inv);
+    if (c * n > u) --c;
+    else if ((c + 1) * n <= u) ++c;
+    return c;
+}
+
+// One telescoped line task: a column pair (b k - 1, b k) over a chunk of
+// rows (x slopes) or a row pair over a chunk of columns (y slopes).
+struct LineTask {
+    int lo, hi, l0, slot;  // line range, first line pixel, accumulator slot
+    bool xdir, use0, use1;
+    const uint8_t *cc;     // boundary-line bytes of this boundary (stride n_sub + 1)
+};
+
+__device__ __forceinline__ LineTask decode_task(const DevWFS &WF, const ItemWfs &s, int u) {
+    const int k = WF.k, CH = WF.CH;
+    const int nxb = s.nxc * s.nb;
+    LineTask T;
+    T.xdir = u < nxb;
+    if (T.xdir) {
+        const int c = fast_div(u, s.nb, s.inv_nb), bq = u - c * s.nb;
+        const int b = s.sj0 + bq, cid = s.xcid0 + c;
+        T.lo = max(cid * CH, s.pi0);
+        T.hi = min(cid * CH + CH - 1, s.pi1);
+        T.l0 = b * k - 1;
+        T.use0 = T.l0 >= s.pj0 && T.l0 <= s.pj1;
+        T.use1 = T.l0 + 1 >= s.pj0 && T.l0 + 1 <= s.pj1;
+        T.cc = s.xcc + b;
+        T.slot = c * s.nb + bq;
+    } else {
+        u -= nxb;
+        const int c = fast_div(u, s.nbr, s.inv_nbr), bq = u - c * s.nbr;
+        const int b = s.si0 + bq, cid = s.ycid0 + c;
+        T.lo = max(cid * CH, s.pj0);
+        T.hi = min(cid * CH + CH - 1, s.pj1);
+        T.l0 = b * k - 1;
+        T.use0 = T.l0 >= s.pi0 && T.l0 <= s.pi1;
+        T.use1 = T.l0 + 1 >= s.pi0 && T.l0 + 1 <= s.pi1;
+        T.cc = s.ycc + b;
+        T.slot = c * s.nbr + bq;
+    }
+    return T;
+}
+
+// Up to 8 boundary-line bytes (rows r0 .. r0 + 7 of the task) in one register.
+__device__ __forceinline__ unsigned long long load_codes(const LineTask &T, int n1, int r0) {
+    const int cnt = min(8, T.hi - r0 + 1);
+    unsigned long long pack = 0ull;
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        if (q < cnt) pack |= (unsigned long long)__ldg(T.cc + (long)(r0 + q) * n1) << (8 * q);
+    return pack;
+}
+
+// Resample the task's line pixels (the first 8 rows' bytes are given) and
+// store its two telescoped partial sums.
 template <int NV>
-__device__ void line_task(const DevWFS &WF, const ItemWfs &s, int u, const Eval<NV> &ev,
-                          float *base) {
-    const int k = WF.k, M = WF.M, CH = WF.CH;
+__device__ __forceinline__ void run_task(const DevWFS &WF, const ItemWfs &s, const LineTask &T,
+                                         unsigned long long pack, const Eval<NV> &ev, float *base) {
+    const int n1 = WF.n_sub + 1;
     const int nxb = s.nxc * s.nb, nyb = s.nyc * s.nbr;
     float L[NV], R[NV], v[NV];
 #pragma unroll
     for (int t = 0; t < NV; ++t) L[t] = R[t] = 0.f;
-    if (u < nxb) {
-        const int c = u / s.nb, bq = u - c * s.nb, b = s.sj0 + bq;
-        const int cid = s.pi0 / CH + c;
-        const int r_lo = max(cid * CH, s.pi0), r_hi = min(cid * CH + CH - 1, s.pi1);
-        const int c0 = b * k - 1, c1 = b * k;
-        const bool use0 = c0 >= s.pj0 && c0 <= s.pj1, use1 = c1 >= s.pj0 && c1 <= s.pj1;
-        const uint8_t *xc = WF.xcode + (size_t)b * M;
-        for (int r = r_lo; r <= r_hi; ++r) {
-            const int code = xc[r];
-            if (use0 && (code & 3)) {
-                ev.eval(r, c0, v);
-                if (code & 1) for (int t = 0; t < NV; ++t) L[t] += v[t];
-                if (code & 2) for (int t = 0; t < NV; ++t) R[t] += v[t];
-            }
-            if (use1 && (code & 12)) {
-                ev.eval(r, c1, v);
-                if (code & 4) for (int t = 0; t < NV; ++t) L[t] += v[t];
-                if (code & 8) for (int t = 0; t < NV; ++t) R[t] += v[t];
-            }
+    const bool xdir = T.xdir;
+    const int lo = T.lo, hi = T.hi, l0 = T.l0;
+    if constexpr (NV == 1) {
+        // along a line the sampled DM point moves by a constant step: one FMA
+        // per coordinate from the line's first pixel
+        float x0, y0, x1, y1, sx, sy;
+        if (xdir) {
+            const float di = (float)(lo - ev.pi0), dj = (float)(l0 - ev.pj0);
+            x0 = fmaf(ev.a00, dj, fmaf(ev.a01, di, ev.xo));
+            y0 = fmaf(ev.a10, dj, fmaf(ev.a11, di, ev.yo));
+            x1 = fmaf(ev.a00, dj + 1.f, fmaf(ev.a01, di, ev.xo));
+            y1 = fmaf(ev.a10, dj + 1.f, fmaf(ev.a11, di, ev.yo));
+            sx = ev.a01;
+            sy = ev.a11;
+        } else {
+            const float di = (float)(l0 - ev.pi0), dj = (float)(lo - ev.pj0);
+            x0 = fmaf(ev.a00, dj, fmaf(ev.a01, di, ev.xo));
+            y0 = fmaf(ev.a10, dj, fmaf(ev.a11, di, ev.yo));
+            x1 = fmaf(ev.a00, dj, fmaf(ev.a01, di + 1.f, ev.xo));
+            y1 = fmaf(ev.a10, dj, fmaf(ev.a11, di + 1.f, ev.yo));
+            sx = ev.a00;
+            sy = ev.a10;
         }
-        float *CBL = base, *CBR = base + NV * nxb;
-#pragma unroll
-        for (int t = 0; t < NV; ++t) {
-            CBL[(c * s.nb + bq) * NV + t] = L[t];
-            CBR[(c * s.nb + bq) * NV + t] = R[t];
+        for (int rb = lo; rb <= hi; rb += 8) {
+            if (rb != lo) pack = load_codes(T, n1, rb);
+            const int cnt = min(8, hi - rb + 1);
+            for (int q = 0; q < cnt; ++q) {
+                const int r = rb + q;
+                const float m = (float)(r - lo);
+                const int code = (int)((pack >> (8 * q)) & 0xffull);
+                if (T.use0 && (code & 3)) {
+                    const int cls = (code >> 4) & 3;
+                    float vv = 0.f;
+                    if (cls == 1) vv = bil_xy(ev.win, ev.Wp, ev.Wf1, fmaf(sx, m, x0), fmaf(sy, m, y0));
+                    else if (cls == 2) { if (xdir) ev.ring(r, l0, &vv); else ev.ring(l0, r, &vv); }
+                    L[0] += (code & 1) ? vv : 0.f;
+                    R[0] += (code & 2) ? vv : 0.f;
+                }
+                if (T.use1 && (code & 12)) {
+                    const int cls = code >> 6;
+                    float vv = 0.f;
+                    if (cls == 1) vv = bil_xy(ev.win, ev.Wp, ev.Wf1, fmaf(sx, m, x1), fmaf(sy, m, y1));
+                    else if (cls == 2) { if (xdir) ev.ring(r, l0 + 1, &vv); else ev.ring(l0 + 1, r, &vv); }
+                    L[0] += (code & 4) ? vv : 0.f;
+                    R[0] += (code & 8) ? vv : 0.f;
+                }
+            }
         }
     } else {
-        u -= nxb;
-        const int c = u / s.nbr, bq = u - c * s.nbr, b = s.si0 + bq;
-        const int cid = s.pj0 / CH + c;
-        const int c_lo = max(cid * CH, s.pj0), c_hi = min(cid * CH + CH - 1, s.pj1);
-        const int r0 = b * k - 1, r1 = b * k;
-        const bool use0 = r0 >= s.pi0 && r0 <= s.pi1, use1 = r1 >= s.pi0 && r1 <= s.pi1;
-        const uint8_t *yc = WF.ycode + (size_t)b * M;
-        for (int col = c_lo; col <= c_hi; ++col) {
-            const int code = yc[col];
-            if (use0 && (code & 3)) {
-                ev.eval(r0, col, v);
-                if (code & 1) for (int t = 0; t < NV; ++t) L[t] += v[t];
-                if (code & 2) for (int t = 0; t < NV; ++t) R[t] += v[t];
-            }
-            if (use1 && (code & 12)) {
-                ev.eval(r1, col, v);
-                if (code & 4) for (int t = 0; t < NV; ++t) L[t] += v[t];
-                if (code & 8) for (int t = 0; t < NV; ++t) R[t] += v[t];
-            }
-        }
-        float *RBU = base + 2 * NV * nxb, *RBD = RBU + NV * nyb;
+        for (int rb = lo; rb <= hi; rb += 8) {
+            if (rb != lo) pack = load_codes(T, n1, rb);
+            const int cnt = min(8, hi - rb + 1);
+            for (int q = 0; q < cnt; ++q) {
+                const int r = rb + q;
+                const int code = (int)((pack >> (8 * q)) & 0xffull);
+#pragma unroll 1
+                for (int px = 0; px < 2; ++px) {
+                    const int bits = (code >> (2 * px)) & 3;
+                    if (!bits || !(px ? T.use1 : T.use0)) continue;
+                    const int line = l0 + px;
+                    if (xdir) ev.eval_cls(r, line, (code >> (4 + 2 * px)) & 3, v);
+                    else ev.eval_cls(line, r, (code >> (4 + 2 * px)) & 3, v);
+                    if (bits & 1)
 #pragma unroll
-        for (int t = 0; t < NV; ++t) {
-            RBU[(c * s.nbr + bq) * NV + t] = L[t];
-            RBD[(c * s.nbr + bq) * NV + t] = R[t];
+                        for (int t = 0; t < NV; ++t) L[t] += v[t];
+                    if (bits & 2)
+#pragma unroll
+                        for (int t = 0; t < NV; ++t) R[t] += v[t];
+                }
+            }
         }
+    }
+    float *lp, *rp;
+    if (xdir) {
+        lp = base + T.slot * NV;
+        rp = base + NV * nxb + T.slot * NV;
+    } else {
+        lp = base + 2 * NV * nxb + T.slot * NV;
+        rp = base + 2 * NV * nxb + NV * nyb + T.slot * NV;
+    }
+#pragma unroll
+    for (int t = 0; t < NV; ++t) {
+        lp[t] = L[t];
+        rp[t] = R[t];
     }
 }
 
+// Subaperture sums of one sensor (x block, then y block): add the telescoped
+// boundary-line sums of every chunk to the pupil-edge sums already in S.
+template <int NV>
+__device__ __forceinline__ void finalize_sub(const ItemWfs &s, const DevWFS &WF, float *base, int q) {
+    const int k = WF.k, CH = WF.CH;
+    const int nsj = s.sj1 - s.sj0 + 1, nsub = (s.si1 - s.si0 + 1) * nsj;
+    const int nxb = s.nxc * s.nb, nyb = s.nyc * s.nbr;
+    float *S = base + NV * (2 * nxb + 2 * nyb);
+    const int comp = q >= nsub ? 1 : 0, idx = q - comp * nsub;
+    const int si = s.si0 + idx / nsj, sj = s.sj0 + idx % nsj;
+    float v[NV];
+#pragma unroll
+    for (int t = 0; t < NV; ++t) v[t] = S[q * NV + t];
+    if (comp == 0) {
+        const float *CBL = base, *CBR = base + NV * nxb;
+        const int lo = max(si * k / CH, s.pi0 / CH), hi = min(((si + 1) * k - 1) / CH, s.pi1 / CH);
+        for (int cid = lo; cid <= hi; ++cid) {
+            const int c = cid - s.pi0 / CH;
+#pragma unroll
+            for (int t = 0; t < NV; ++t)
+                v[t] += CBL[(c * s.nb + sj + 1 - s.sj0) * NV + t] - CBR[(c * s.nb + sj - s.sj0) * NV + t];
+        }
+    } else {
+        const float *RBU = base + 2 * NV * nxb, *RBD = RBU + NV * nyb;
+        const int lo = max(sj * k / CH, s.pj0 / CH), hi = min(((sj + 1) * k - 1) / CH, s.pj1 / CH);
+        for (int cid = lo; cid <= hi; ++cid) {
+            const int c = cid - s.pj0 / CH;
+#pragma unroll
+            for (int t = 0; t < NV; ++t)
+                v[t] += RBU[(c * s.nbr + si + 1 - s.si0) * NV + t] - RBD[(c * s.nbr + si - s.si0) * NV + t];
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < NV; ++t) S[q * NV + t] = v[t];
+}
+
 template <int MODE>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(512, (MODE == MODE_FWD) ? 2 : 1)
     k_im(const __grid_constant__ Geo g, const DevPair *__restrict__ pairs, int *__restrict__ counter,
          int *__restrict__ err, double *__restrict__ gp) {
     constexpr int NV = (MODE == MODE_FWD) ? 1 : 5;
@@ -503,12 +759,11 @@ __global__ void __launch_bounds__(256)
     uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem + (size_t)g.max_win_floats * 4);
     ItemWfs *s_info = reinterpret_cast<ItemWfs *>(s_bar + 2);
     float *s_arena = reinterpret_cast<float *>(s_info + SYNIM_MAX_WFS);
-    __shared__ int s_item, s_next, s_abort, s_ng;
-    __shared__ int s_tpre[SYNIM_MAX_WFS + 1];
-    __shared__ int s_gbeg[SYNIM_MAX_WFS + 1];
+    __shared__ int s_item, s_next, s_abort;
     __shared__ double s_gp[MODE == MODE_VJP ? SYNIM_MAX_PAIRS * 4 : 1];
 
     const int tid = threadIdx.x, nth = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nwarps = nth >> 5;
     const uint32_t bar = smem_u32(s_bar);
     if (MODE == MODE_VJP)
         for (int q = tid; q < SYNIM_MAX_PAIRS * 4; q += nth) s_gp[q] = 0.0;
@@ -527,34 +782,13 @@ __global__ void __launch_bounds__(256)
         int d, a;
         decode_item(g, item, d, a);
         const DevDM &D = g.dm[d];
-        for (int w = tid; w < g.n_wfs; w += nth) make_info<MODE, NV>(g, pairs, d, a, w, s_info[w]);
-        __syncthreads();
         if (tid == 0) {
-            // group sensors so that their accumulators fit the arena
-            int used = 0, ng = 0, tp = 0;
-            s_gbeg[0] = 0;
-            for (int w = 0; w < g.n_wfs; ++w) {
-                ItemWfs &s = s_info[w];
-                if (s.need > g.arena_floats) {
-                    atomicOr(err, ERR_ARENA);
-                    s.empty = 1; s.ntask = 0; s.need = 0;
-                    s.si0 = 1; s.si1 = 0; s.sj0 = 1; s.sj1 = 0;
-                }
-                if (used + s.need > g.arena_floats && w > s_gbeg[ng]) {
-                    ++ng;
-                    s_gbeg[ng] = w;
-                    used = 0;
-                }
-                s.arena = used;
-                used += s.need;
-                s_tpre[w] = tp;
-                tp += s.ntask;
-            }
-            s_tpre[g.n_wfs] = tp;
-            ++ng;
-            s_gbeg[ng] = g.n_wfs;
-            s_ng = ng;
+            // claim the next actuator now and pull its window towards L2
+            const int nx = atomicAdd(counter, 1);
+            s_next = nx;
+            if (nx < g.n_items) prefetch_window(g, nx);
         }
+        for (int w = tid; w < g.n_wfs; w += nth) make_info<MODE, NV>(g, pairs, d, a, w, s_info[w], err);
         if (!mbar_wait_bounded(bar, phase)) {
             s_abort = 1;
             atomicOr(err, ERR_TIMEOUT);
@@ -562,47 +796,91 @@ __global__ void __launch_bounds__(256)
         __syncthreads();
         if (s_abort) break;
         phase ^= 1u;
-        const int ng = s_ng;
+        const int next_item = s_next;  // read before tid 0 can claim again
+        const int ng = g.n_groups[d];
         for (int gi = 0; gi < ng; ++gi) {
-            const int w0 = s_gbeg[gi], w1 = s_gbeg[gi + 1];
-            const int z0 = s_info[w0].arena, z1 = s_info[w1 - 1].arena + s_info[w1 - 1].need;
-            for (int q = z0 + tid; q < z1; q += nth) s_arena[q] = 0.f;
-            __syncthreads();
-            // telescoped boundary lines
-            const int t0 = s_tpre[w0], t1 = s_tpre[w1];
-            for (int t = t0 + tid; t < t1; t += nth) {
-                int w = w0;
-                while (s_tpre[w + 1] <= t) ++w;
-                const ItemWfs &s = s_info[w];
-                Eval<NV> ev;
-                ev.load(s, s_win, D.Wp, D.W, g.wfs[w].M);
-                line_task<NV>(g.wfs[w], s, t - s_tpre[w], ev, s_arena + s.arena);
-            }
-            // pixels where the pupil edge cuts a subaperture: one warp per
-            // subaperture, lane-strided in entry order + butterfly reduction,
-            // so the sums are deterministic
+            // telescoped boundary lines: the tasks of every sensor of the group
+            // form one sequence dealt round-robin to the threads; each thread
+            // loads the next task's line bytes before resampling the current one
             {
-                const int warp = tid >> 5, lane = tid & 31, nwarps = nth >> 5;
-                for (int w = w0; w < w1; ++w) {
+                auto find = [&](int gq, int &w, int &basew) -> bool {
+                    while (true) {
+                        if (w >= 0) {
+                            if (gq < basew + s_info[w].ntask) return true;
+                            basew += s_info[w].ntask;
+                        }
+                        do { ++w; } while (w < g.n_wfs && (s_info[w].group != gi || s_info[w].empty));
+                        if (w >= g.n_wfs) return false;
+                    }
+                };
+                int gq = tid, w = -1, basew = 0;
+                if (find(gq, w, basew)) {
+                    LineTask T = decode_task(g.wfs[w], s_info[w], gq - basew);
+                    unsigned long long pack = load_codes(T, g.wfs[w].n_sub + 1, T.lo);
+                    Eval<NV> ev;
+                    ev.load(s_info[w], s_win, D.Wp, D.W, g.wfs[w].M);
+                    int ev_w = w;
+                    while (true) {
+                        int gn = gq + nth, wn = w, bn = basew;
+                        const bool more = find(gn, wn, bn);
+                        LineTask Tn;
+                        unsigned long long packn = 0ull;
+                        if (more) {
+                            Tn = decode_task(g.wfs[wn], s_info[wn], gn - bn);
+                            packn = load_codes(Tn, g.wfs[wn].n_sub + 1, Tn.lo);
+                        }
+                        if (ev_w != w) {
+                            ev.load(s_info[w], s_win, D.Wp, D.W, g.wfs[w].M);
+                            ev_w = w;
+                        }
+                        run_task<NV>(g.wfs[w], s_info[w], T, pack, ev, s_arena + s_info[w].arena);
+                        if (!more) break;
+                        gq = gn; w = wn; basew = bn; T = Tn; pack = packn;
+                    }
+                }
+            }
+            // pupil-edge pixels: one warp per (sensor, subaperture row) writes the
+            // edge sum of every subaperture of that row (zero where there is none);
+            // only the entries on pixel rows inside the box are visited
+            for (int rr = warp;; rr += nwarps) {
+                int w = 0, acc = 0;
+                for (; w < g.n_wfs; ++w) {
                     const ItemWfs &s = s_info[w];
-                    if (s.empty) continue;
-                    const DevWFS &WF = g.wfs[w];
+                    if (s.group != gi || s.empty) continue;
+                    const int nr = s.si1 - s.si0 + 1;
+                    if (rr < acc + nr) break;
+                    acc += nr;
+                }
+                if (w >= g.n_wfs) break;
+                const ItemWfs &s = s_info[w];
+                const DevWFS &WF = g.wfs[w];
+                const int k = WF.k;
+                const int si = s.si0 + rr - acc;
+                const int nsj = s.sj1 - s.sj0 + 1, nsub = (s.si1 - s.si0 + 1) * nsj;
+                float *S = s_arena + s.arena + NV * (2 * s.nxc * s.nb + 2 * s.nyc * s.nbr);
+                const int row = (si - s.si0) * nsj;
+                for (int q = lane; q < nsj * NV; q += 32) {
+                    S[row * NV + q] = 0.f;
+                    S[(nsub + row) * NV + q] = 0.f;
+                }
+                __syncwarp();
+                const int ra = max(s.pi0, si * k) - si * k, rb = min(s.pi1, si * k + k - 1) - si * k;
+                const int c1 = WF.irrc_row[si + 1];
+                if (ra <= rb && c1 > WF.irrc_row[si]) {
                     Eval<NV> ev;
                     ev.load(s, s_win, D.Wp, D.W, WF.M);
-                    const int nsj = s.sj1 - s.sj0 + 1, nsub = (s.si1 - s.si0 + 1) * nsj;
-                    float *S = s_arena + s.arena + NV * (2 * s.nxc * s.nb + 2 * s.nyc * s.nbr);
-                    for (int idx = warp; idx < nsub; idx += nwarps) {
-                        const int si = s.si0 + idx / nsj, sj = s.sj0 + idx % nsj;
-                        const int e0 = WF.irr_sub[si * WF.n_sub + sj];
-                        const int e1 = WF.irr_sub[si * WF.n_sub + sj + 1];
-                        if (e0 == e1) continue;
+                    for (int c = WF.irrc_row[si]; c < c1; ++c) {
+                        const int sj = WF.irrc[c].x;
+                        if (sj < s.sj0 || sj > s.sj1) continue;
+                        const long sr = (long)(si * WF.n_sub + sj) * k;
+                        const int e0 = WF.irr_sr[sr + ra], e1 = WF.irr_sr[sr + rb + 1];
                         float ax[NV], ay[NV], v[NV];
 #pragma unroll
                         for (int t = 0; t < NV; ++t) ax[t] = ay[t] = 0.f;
                         for (int e = e0 + lane; e < e1; e += 32) {
                             const int pix = WF.irr_pix[e];
                             const int i = pix >> 16, j = pix & 0xffff;
-                            if (i < s.pi0 || i > s.pi1 || j < s.pj0 || j > s.pj1) continue;
+                            if (j < s.pj0 || j > s.pj1) continue;
                             ev.eval(i, j, v);
                             const float wx = WF.irr_w[2 * e], wy = WF.irr_w[2 * e + 1];
 #pragma unroll
@@ -618,6 +896,7 @@ __global__ void __launch_bounds__(256)
                                 ay[t] += __shfl_xor_sync(0xffffffffu, ay[t], o);
                             }
                         if (lane == 0) {
+                            const int idx = row + sj - s.sj0;
 #pragma unroll
                             for (int t = 0; t < NV; ++t) {
                                 S[idx * NV + t] = ax[t];
@@ -626,124 +905,100 @@ __global__ void __launch_bounds__(256)
                         }
                     }
                 }
+                __syncwarp();
             }
             __syncthreads();
-            if (gi == ng - 1 && tid == 0) {
-                // the window is no longer read: prefetch the next actuator
-                const int nx = atomicAdd(counter, 1);
-                s_next = nx;
-                if (nx < g.n_items) {
-                    fence_proxy_async_smem();
-                    issue_window(g, nx, s_win, bar);
-                }
+            if (gi == ng - 1 && tid == 0 && next_item < g.n_items) {
+                // the window is no longer read: stage the next actuator's
+                fence_proxy_async_smem();
+                issue_window(g, next_item, s_win, bar);
             }
-            // finalize: add the telescoped line sums into each subaperture
-            for (int w = w0; w < w1; ++w) {
-                const ItemWfs &s = s_info[w];
-                if (s.empty) continue;
-                const DevWFS &WF = g.wfs[w];
-                const int k = WF.k, CH = WF.CH;
-                const int nsj = s.sj1 - s.sj0 + 1, nsub = (s.si1 - s.si0 + 1) * nsj;
-                const int nxb = s.nxc * s.nb, nyb = s.nyc * s.nbr;
-                float *base = s_arena + s.arena;
-                const float *CBL = base, *CBR = base + NV * nxb;
-                const float *RBU = base + 2 * NV * nxb, *RBD = RBU + NV * nyb;
-                float *S = base + NV * (2 * nxb + 2 * nyb);
-                for (int idx = tid; idx < nsub; idx += nth) {
-                    const int si = s.si0 + idx / nsj, sj = s.sj0 + idx % nsj;
-                    float sx[NV], sy[NV];
-#pragma unroll
-                    for (int t = 0; t < NV; ++t) { sx[t] = S[idx * NV + t]; sy[t] = S[(nsub + idx) * NV + t]; }
-                    const int cx_lo = max(si * k / CH, s.pi0 / CH), cx_hi = min(((si + 1) * k - 1) / CH, s.pi1 / CH);
-                    for (int cid = cx_lo; cid <= cx_hi; ++cid) {
-                        const int c = cid - s.pi0 / CH;
-#pragma unroll
-                        for (int t = 0; t < NV; ++t)
-                            sx[t] += CBL[(c * s.nb + sj + 1 - s.sj0) * NV + t] - CBR[(c * s.nb + sj - s.sj0) * NV + t];
-                    }
-                    const int cy_lo = max(sj * k / CH, s.pj0 / CH), cy_hi = min(((sj + 1) * k - 1) / CH, s.pj1 / CH);
-                    for (int cid = cy_lo; cid <= cy_hi; ++cid) {
-                        const int c = cid - s.pj0 / CH;
-#pragma unroll
-                        for (int t = 0; t < NV; ++t)
-                            sy[t] += RBU[(c * s.nbr + si + 1 - s.si0) * NV + t] - RBD[(c * s.nbr + si - s.si0) * NV + t];
-                    }
-#pragma unroll
-                    for (int t = 0; t < NV; ++t) { S[idx * NV + t] = sx[t]; S[(nsub + idx) * NV + t] = sy[t]; }
+            // finalize the subaperture sums of every sensor of the group, and
+            // stream zeros over every output column of the group (no loads)
+            {
+                int seq = 0;
+                for (int w = 0; w < g.n_wfs; ++w) {
+                    const ItemWfs &s = s_info[w];
+                    if (s.group != gi || s.empty) continue;
+                    const int nq = 2 * (s.si1 - s.si0 + 1) * (s.sj1 - s.sj0 + 1);
+                    int q = tid - seq % nth;
+                    if (q < 0) q += nth;
+                    for (; q < nq; q += nth) finalize_sub<NV>(s, g.wfs[w], s_arena + s.arena, q);
+                    seq += nq;
                 }
-            }
-            __syncthreads();
-            // output: dense columns (MODE_FWD / MODE_TAN) or the VJP reduction
-            for (int w = w0; w < w1; ++w) {
-                const ItemWfs &s = s_info[w];
-                const DevWFS &WF = g.wfs[w];
-                const int pidx = d * g.n_wfs + w;
-                const DevPair &P = pairs[pidx];
-                const int nv = WF.nv, n2 = 2 * nv;
-                const int nsj = s.sj1 - s.sj0 + 1, nsub = (s.si1 - s.si0 + 1) * nsj;
-                const float *S = s_arena + s.arena + NV * (2 * s.nxc * s.nb + 2 * s.nyc * s.nbr);
-                const int x_lo = s.empty ? 0 : WF.vrow[s.si0];
-                const int x_hi = s.empty ? 0 : WF.vrow[s.si1 + 1];
-                auto value = [&](int r, int t) -> float {
-                    const int comp = r >= nv ? 1 : 0;
-                    const int rr = r - comp * nv;
-                    const int sub = WF.vsub[rr];
-                    const int si = sub >> 16, sj = sub & 0xffff;
-                    if (si < s.si0 || si > s.si1 || sj < s.sj0 || sj > s.sj1) return 0.f;
-                    return S[(comp * nsub + (si - s.si0) * nsj + (sj - s.sj0)) * NV + t] * WF.fac[rr];
-                };
-                if (MODE == MODE_VJP) {
-                    if (!P.gim || s.empty) continue;
-                    const float *src = P.gim + (size_t)a * n2;
-                    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-                    const int span = x_hi - x_lo;
-                    for (int q = tid; q < 2 * span; q += nth) {
-                        const int r = (q < span) ? x_lo + q : nv + x_lo + (q - span);
-                        const float gv = src[r];
-                        if (gv != 0.f)
-#pragma unroll
-                            for (int t = 0; t < 4; ++t) acc[t] = fmaf(gv, value(r, t + 1), acc[t]);
-                    }
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        float vsum = acc[t];
-                        for (int o = 16; o > 0; o >>= 1) vsum += __shfl_xor_sync(0xffffffffu, vsum, o);
-                        if ((tid & 31) == 0 && vsum != 0.f) atomicAdd(&s_gp[pidx * 4 + t], (double)vsum);
-                    }
-                    continue;
-                }
-                const int nout = (MODE == MODE_FWD) ? 1 : 5;
-                for (int t = 0; t < nout; ++t) {
-                    float *dst = (t == 0) ? P.im : P.dim[t - 1];
-                    if (!dst) continue;
-                    dst += (size_t)a * n2;
-                    if ((nv & 1) == 0) {
-                        for (int q = tid; q < n2 / 4; q += nth) {
-                            const int r0 = 4 * q;
-                            float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
-                            const bool hit = (r0 + 4 > x_lo && r0 < x_hi) ||
-                                             (r0 + 4 > nv + x_lo && r0 < nv + x_hi);
-                            if (hit) {
-                                o.x = value(r0, t); o.y = value(r0 + 1, t);
-                                o.z = value(r0 + 2, t); o.w = value(r0 + 3, t);
+                if (MODE != MODE_VJP) {
+                    for (int w = 0; w < g.n_wfs; ++w) {
+                        if (s_info[w].group != gi) continue;
+                        const DevPair &P = pairs[d * g.n_wfs + w];
+                        const int nv = g.wfs[w].nv, n2 = 2 * nv;
+                        const int nout = (MODE == MODE_FWD) ? 1 : 5;
+                        for (int t = 0; t < nout; ++t) {
+                            float *dst = (t == 0) ? P.im : P.dim[t - 1];
+                            if (!dst) continue;
+                            dst += (size_t)a * n2;
+                            if ((nv & 1) == 0) {
+                                const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+                                for (int q = tid; q < n2 / 4; q += nth) reinterpret_cast<float4 *>(dst)[q] = z;
+                            } else {
+                                const float2 z = make_float2(0.f, 0.f);
+                                for (int q = tid; q < nv; q += nth) reinterpret_cast<float2 *>(dst)[q] = z;
                             }
-                            __stcs(reinterpret_cast<float4 *>(dst + r0), o);
                         }
-                    } else {
-                        for (int q = tid; q < nv; q += nth) {
-                            const int r0 = 2 * q;
-                            float2 o = make_float2(0.f, 0.f);
-                            const bool hit = (r0 + 2 > x_lo && r0 < x_hi) ||
-                                             (r0 + 2 > nv + x_lo && r0 < nv + x_hi);
-                            if (hit) { o.x = value(r0, t); o.y = value(r0 + 1, t); }
-                            __stcs(reinterpret_cast<float2 *>(dst + r0), o);
+                    }
+                }
+            }
+            __syncthreads();
+            // the box subapertures' slopes: scattered stores over the zeroed
+            // columns (MODE_FWD / MODE_TAN) or the VJP dot product
+            {
+                int seq = 0;
+                for (int w = 0; w < g.n_wfs; ++w) {
+                    const ItemWfs &s = s_info[w];
+                    if (s.group != gi) continue;
+                    const int pidx = d * g.n_wfs + w;
+                    const DevPair &P = pairs[pidx];
+                    if (MODE == MODE_VJP && !P.gim) continue;
+                    const DevWFS &WF = g.wfs[w];
+                    const int nv = WF.nv, n2 = 2 * nv;
+                    const int nsj = s.sj1 - s.sj0 + 1, nsub = (s.si1 - s.si0 + 1) * nsj;
+                    const int nq = s.empty ? 0 : 2 * nsub;
+                    const float *S = s_arena + s.arena + NV * (2 * s.nxc * s.nb + 2 * s.nyc * s.nbr);
+                    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+                    int q = tid - seq % nth;
+                    if (q < 0) q += nth;
+                    for (; q < nq; q += nth) {
+                        const int comp = q >= nsub ? 1 : 0, idx = q - comp * nsub;
+                        const int si = s.si0 + idx / nsj, sj = s.sj0 + idx % nsj;
+                        const int row = WF.vidx[si * WF.n_sub + sj];
+                        if (row < 0) continue;
+                        const float f = WF.fac[row];
+                        const size_t at = (size_t)a * n2 + comp * nv + row;
+                        if (MODE == MODE_VJP) {
+                            const float gv = P.gim[at];
+#pragma unroll
+                            for (int t = 0; t < 4; ++t) acc[t] = fmaf(gv, S[q * NV + t + 1] * f, acc[t]);
+                        } else {
+                            if (P.im) P.im[at] = S[q * NV] * f;
+                            if (MODE == MODE_TAN)
+#pragma unroll
+                                for (int t = 0; t < 4; ++t)
+                                    if (P.dim[t]) P.dim[t][at] = S[q * NV + t + 1] * f;
+                        }
+                    }
+                    seq += nq;
+                    if (MODE == MODE_VJP) {
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) {
+                            float vsum = acc[t];
+                            for (int o = 16; o > 0; o >>= 1) vsum += __shfl_xor_sync(0xffffffffu, vsum, o);
+                            if (lane == 0 && vsum != 0.f) atomicAdd(&s_gp[pidx * 4 + t], (double)vsum);
                         }
                     }
                 }
             }
             __syncthreads();
         }
-        item = s_next;
+        item = next_item;
     }
     if (MODE == MODE_VJP) {
         __syncthreads();

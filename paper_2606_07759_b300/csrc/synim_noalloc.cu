@@ -66,8 +66,8 @@ size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 enum { H_COUNTER = 0, H_ERR = 1, H_W = 2, H_NV = 3, H_NIRR = 4, H_WORDS = 64 };
 
 struct Layout {
-    size_t pair, box, org, dmmask, P, vin, lit, ros, vsub, fac, vrow, xcode, ycode, irrsr, irrsub,
-        irrpix, irrw, pst, win, fixed_end;
+    size_t pair, box, org, dmmask, mcls, P, vin, lit, ros, vsub, vsj, fac, vrow, xcode, ycode, irrsr, irrsub,
+        irrpix, irrw, irrc, irrcrow, pst, lines, win, fixed_end;
 };
 
 Layout make_layout(int n_act, int N, int M, int n, bool has_mask, bool has_vin) {
@@ -76,23 +76,28 @@ Layout make_layout(int n_act, int N, int M, int n, bool has_mask, bool has_vin) 
     size_t o = up256(sizeof(int) * H_WORDS);
     auto take = [&](size_t bytes) { const size_t at = o; o = up256(o + bytes); return at; };
     L.pair = take(sizeof(DevPair));
-    L.box = take(sizeof(int) * 4 * (size_t)n_act);
+    L.box = take(sizeof(int) * (4 * (size_t)n_act + 1));
     L.org = take(sizeof(int) * 2 * (size_t)n_act);
     L.dmmask = has_mask ? take((size_t)N * N) : 0;
+    L.mcls = take((size_t)(N + 1) * (N + 1));
     L.P = take((size_t)M * M);
     L.vin = has_vin ? take((size_t)n * n) : 0;
     L.lit = take(sizeof(int) * (size_t)n * n);
     L.ros = take(sizeof(int) * (size_t)n * n);
     L.vsub = take(sizeof(int) * (size_t)n * n);
+    L.vsj = take(sizeof(short) * ((size_t)n * n + 4));
     L.fac = take(sizeof(float) * (size_t)n * n);
     L.vrow = take(sizeof(int) * (size_t)(n + 1));
     L.xcode = take((size_t)(n + 1) * M);
     L.ycode = take((size_t)(n + 1) * M);
-    L.irrsr = take(sizeof(int) * (size_t)n * n * k);
+    L.irrsr = take(sizeof(int) * ((size_t)n * n * k + 1));
     L.irrsub = take(sizeof(int) * ((size_t)n * n + 1));
     L.irrpix = take(sizeof(int) * (size_t)M * M);
     L.irrw = take(2 * (size_t)M * M);
+    L.irrc = take(sizeof(int4) * (size_t)n * n);
+    L.irrcrow = take(sizeof(int) * (size_t)(n + 1));
     L.pst = take((size_t)M * M);
+    L.lines = take(2 * (size_t)M * (n + 1));
     L.win = o;
     L.fixed_end = o;
     return L;
@@ -118,7 +123,7 @@ __global__ void k_na_lit(const uint8_t *P, int M, int n, int k, int *lit) {
 
 // One CTA: validity, row ranks (row-major), scale factors, first row per subaperture row.
 __global__ void k_na_valid(const int *lit, const uint8_t *vin, int n, int k, double scale, double dw,
-                           int *ros, int *vsub, float *fac, int *vrow, int *hdr) {
+                           int *ros, int *vsub, short *vsj, float *fac, int *vrow, int *hdr) {
     __shared__ int cnt[1024];
     const int ns = n * n, T = blockDim.x, t = threadIdx.x;
     const int C = (ns + T - 1) / T, a = t * C, b = min(ns, a + C);
@@ -136,6 +141,7 @@ __global__ void k_na_valid(const int *lit, const uint8_t *vin, int n, int k, dou
         for (int q = 0; q < T; ++q) { const int v = cnt[q]; cnt[q] = run; run += v; }
         vrow[n] = run;
         hdr[H_NV] = run;
+        for (int q = 0; q < 4; ++q) vsj[run + q] = -1;
     }
     __syncthreads();
     int r = cnt[t];
@@ -148,6 +154,7 @@ __global__ void k_na_valid(const int *lit, const uint8_t *vin, int n, int k, dou
         ros[s] = ok ? r : -1;
         if (ok) {
             vsub[r] = (si << 16) | sj;
+            vsj[r] = (short)sj;
             fac[r] = (float)(scale / (2.0 * dw * l));
             ++r;
         }
@@ -233,6 +240,7 @@ __global__ void k_na_irr_scan(int *irrsr, int n, int k, int *irr_sub, int *hdr) 
         int run = 0;
         for (int q = 0; q < T; ++q) { const int v = cnt[q]; cnt[q] = run; run += v; }
         irr_sub[n * n] = run;
+        irrsr[tot] = run;
         hdr[H_NIRR] = run;
     }
     __syncthreads();
@@ -263,6 +271,20 @@ __global__ void k_na_irr_fill(const uint8_t *P, const int *ros, int M, int n, in
             ++at;
         }
     }
+}
+
+// One thread: subapertures with pupil-edge pixels, grouped by subaperture row.
+__global__ void k_na_irr_cand(const int *irr_sub, int n, int4 *irrc, int *irrc_row) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int q = 0;
+    for (int si = 0; si < n; ++si) {
+        irrc_row[si] = q;
+        for (int sj = 0; sj < n; ++sj) {
+            const int e0 = irr_sub[si * n + sj], e1 = irr_sub[si * n + sj + 1];
+            if (e1 > e0) irrc[q++] = make_int4(sj, e0, e1, 0);
+        }
+    }
+    irrc_row[n] = q;
 }
 
 // ---- support windows ----
@@ -349,6 +371,7 @@ extern "C" synim_status synim_im_compute_noalloc(const synim_dm_desc *dm, const 
     uint8_t *P = reinterpret_cast<uint8_t *>(ptr(L.P));
     int *lit = reinterpret_cast<int *>(ptr(L.lit)), *ros = reinterpret_cast<int *>(ptr(L.ros));
     int *vsub = reinterpret_cast<int *>(ptr(L.vsub)), *vrow = reinterpret_cast<int *>(ptr(L.vrow));
+    short *vsj = reinterpret_cast<short *>(ptr(L.vsj));
     float *fac = reinterpret_cast<float *>(ptr(L.fac));
     uint8_t *xcode = ptr(L.xcode), *ycode = ptr(L.ycode);
     int *irrsr = reinterpret_cast<int *>(ptr(L.irrsr)), *irrsub = reinterpret_cast<int *>(ptr(L.irrsub));
@@ -362,11 +385,17 @@ extern "C" synim_status synim_im_compute_noalloc(const synim_dm_desc *dm, const 
     if (dm->mask) k_na_binarize<<<grid_for((long)N * N, 256), 256, 0, st>>>(ptr(L.dmmask), (long)N * N);
     k_na_lit<<<grid_for(MM, 256), 256, 0, st>>>(P, M, n, k, lit);
     k_na_valid<<<1, 1024, 0, st>>>(lit, wfs->subap_valid ? ptr(L.vin) : nullptr, n, k, wfs->slope_scale, dw,
-                                   ros, vsub, fac, vrow, hdr);
+                                   ros, vsub, vsj, fac, vrow, hdr);
     k_na_codes<<<grid_for((long)(n + 1) * M, 256), 256, 0, st>>>(P, ros, M, n, k, xcode, ycode);
     k_na_irr_count<<<grid_for((long)n * n * k, 256), 256, 0, st>>>(P, ros, M, n, k, irrsr);
     k_na_irr_scan<<<1, 1024, 0, st>>>(irrsr, n, k, irrsub, hdr);
     k_na_irr_fill<<<grid_for((long)n * n * k, 256), 256, 0, st>>>(P, ros, M, n, k, irrsr, irrpix, irrw);
+    int4 *irrc = reinterpret_cast<int4 *>(ptr(L.irrc));
+    int *irrcrow = reinterpret_cast<int *>(ptr(L.irrcrow));
+    k_na_irr_cand<<<1, 32, 0, st>>>(irrsub, n, irrc, irrcrow);
+    uint8_t *mcls = ptr(L.mcls);
+    if ((e = launch_mcls(dm->mask ? ptr(L.dmmask) : nullptr, N, mcls, st)) != cudaSuccess)
+        return na_fail(SYNIM_ERR_CUDA, "mask interior map launch failed");
     // support windows
     if ((e = launch_support(dm->ifs, n_act, N, dm->support_eps, box, st)) != cudaSuccess)
         return na_fail(SYNIM_ERR_CUDA, "support scan launch failed");
@@ -409,8 +438,15 @@ extern "C" synim_status synim_im_compute_noalloc(const synim_dm_desc *dm, const 
     composite(Dh, Wh, *mis, pair.A, pair.b);
     if (!invert2(pair.A, pair.Ai)) return na_fail(SYNIM_ERR_INVALID_ARG, "singular composite affine");
     composite_jac(Dh, *mis, pair.A, pair.b, pair.dA, pair.db);
+    split_pair(pair);
     pair.im = im;
     pair.pst = ptr(L.pst);
+    pair.xcc = ptr(L.lines);
+    pair.ycc = pair.xcc + (size_t)M * (n + 1);
+    const long long arena = (arena_need(Dh, Wh, pair.Ai, 1) + 31) / 32 * 32;
+    pair.arena_off = 0;
+    pair.arena_len = (int)arena;
+    pair.group = 0;
     DevPair *d_pair = reinterpret_cast<DevPair *>(ptr(L.pair));
     // pageable source: the copy is staged before cudaMemcpyAsync returns
     if ((e = cudaMemcpyAsync(d_pair, &pair, sizeof(pair), cudaMemcpyHostToDevice, st)) != cudaSuccess)
@@ -418,27 +454,28 @@ extern "C" synim_status synim_im_compute_noalloc(const synim_dm_desc *dm, const 
     Geo g;
     std::memset(&g, 0, sizeof(g));
     DevDM &G = g.dm[0];
-    G.win = win; G.org = org; G.mask = dm->mask ? ptr(L.dmmask) : nullptr;
+    G.win = win; G.org = org; G.mask = dm->mask ? ptr(L.dmmask) : nullptr; G.mcls = mcls;
     G.n_act = n_act; G.N = N; G.W = W; G.Wp = Wp; G.win_stride = stride;
     DevWFS &F = g.wfs[0];
     F.xcode = xcode; F.ycode = ycode; F.irr_pix = irrpix; F.irr_w = irrw; F.irr_sub = irrsub;
-    F.fac = fac; F.vsub = vsub; F.vrow = vrow;
+    F.fac = fac; F.vsub = vsub; F.vrow = vrow; F.irrc = irrc; F.irrc_row = irrcrow; F.irr_sr = irrsr; F.vsj = vsj; F.vidx = ros;
     F.n_sub = n; F.M = M; F.k = k; F.nv = nv; F.CH = Wh.CH;
     g.n_dm = 1; g.n_wfs = 1; g.n_items = n_act;
     g.order_dm[0] = 0; g.order_start[0] = 0; g.order_start[1] = n_act;
     g.max_win_floats = stride;
-    g.arena_floats = (int)((arena_need(Dh, Wh, pair.Ai, 1) + 255) / 256 * 256);
+    g.arena_floats = (int)arena;
+    g.n_groups[0] = 1;
     const size_t smem = im_smem_bytes(g);
     int dev_max = 0, n_sm = 0, bps = 0;
     cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     if (smem + 8192 > (size_t)dev_max) return na_fail(SYNIM_ERR_SHAPE, "support window too large for shared memory");
-    if ((e = im_prepare(MODE_FWD, 256, smem, &bps)) != cudaSuccess || bps < 1)
+    if ((e = im_prepare(MODE_FWD, 512, smem, &bps)) != cudaSuccess || bps < 1)
         return na_fail(SYNIM_ERR_CUDA, "IM kernel attributes");
     const int grid = std::max(1, std::min(n_act, n_sm * bps));
     if ((e = cudaMemsetAsync(hdr, 0, 2 * sizeof(int), st)) != cudaSuccess ||
-        (e = launch_pst(g, d_pair, M * M, st)) != cudaSuccess ||
-        (e = launch_im(MODE_FWD, g, d_pair, hdr + H_COUNTER, hdr + H_ERR, nullptr, grid, 256, smem, st)) != cudaSuccess)
+        (e = launch_pst(g, d_pair, M * M, M * (n + 1), st)) != cudaSuccess ||
+        (e = launch_im(MODE_FWD, g, d_pair, hdr + H_COUNTER, hdr + H_ERR, nullptr, grid, 512, smem, st)) != cudaSuccess)
         return na_fail(SYNIM_ERR_CUDA, cudaGetErrorString(e));
     int err_flag = 0;
     if ((e = cudaMemcpyAsync(&err_flag, hdr + H_ERR, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
