@@ -147,6 +147,28 @@ synim_status synim_im_compute(synim_ctx *ctx, const synim_misreg *mis, float *co
                               void *cuda_stream);
 
 /*
+ * IM and its tangents with respect to the four misregistration parameters
+ * p = (shift_x_px, shift_y_px, rot_deg, mag) of every pair, in one pass
+ * (forward-mode derivative of Sec. 2.1-2.3 with the edge-repair core set held
+ * fixed; the bilinear derivative is that of the floor cell).
+ * im[n_pairs] (may be NULL, or hold NULL entries) receives the IMs;
+ * d_im[4 * n_pairs] holds device pointers, d_im[4 p + k] = dIM_p / dp_k
+ * (same layout as the IM; NULL entries are skipped).  Asynchronous.
+ */
+synim_status synim_im_sensitivity(synim_ctx *ctx, const synim_misreg *mis, float *const *im,
+                                  float *const *d_im, void *cuda_stream);
+
+/*
+ * Vector-Jacobian product of the IMs: grad_p[4 p + k] = sum over the IM of
+ * pair p of grad_im[p] * dIM_p / dp_k, without forming the tangents (the
+ * adjoint of synim_im_sensitivity).  grad_im[n_pairs]: device pointers (NULL
+ * = zero cotangent); grad_p: host [4 * n_pairs] doubles, written when the call
+ * returns (it synchronises cuda_stream).
+ */
+synim_status synim_im_vjp(synim_ctx *ctx, const synim_misreg *mis, const float *const *grad_im,
+                          double *grad_p, void *cuda_stream);
+
+/*
  * Synchronise cuda_stream and report whether any kernel of this context has
  * flagged an error since the last check (SYNIM_ERR_TIMEOUT if a bounded wait
  * gave up).  Clears the flag.

@@ -53,6 +53,10 @@ SIGNATURES = {
                                     ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
     "synim_im_compute": (c_int32, [c_void_p, ctypes.POINTER(synim_misreg), ctypes.POINTER(c_void_p),
                                    c_void_p]),
+    "synim_im_sensitivity": (c_int32, [c_void_p, ctypes.POINTER(synim_misreg), ctypes.POINTER(c_void_p),
+                                       ctypes.POINTER(c_void_p), c_void_p]),
+    "synim_im_vjp": (c_int32, [c_void_p, ctypes.POINTER(synim_misreg), ctypes.POINTER(c_void_p),
+                               ctypes.POINTER(c_double), c_void_p]),
     "synim_im_check": (c_int32, [c_void_p, c_void_p]),
     "synim_dm_window": (c_int32, [c_void_p, c_int32, ctypes.POINTER(c_int32)]),
     "synim_im_kernel_ms": (c_int32, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int32)]),

@@ -867,3 +867,17 @@ extern "C" synim_status synim_im_compute(synim_ctx *ctx, const synim_misreg *mis
     ctx->err.clear();
     return run(ctx, MODE_FWD, mis, im, nullptr, nullptr, nullptr, static_cast<cudaStream_t>(cuda_stream));
 }
+
+extern "C" synim_status synim_im_sensitivity(synim_ctx *ctx, const synim_misreg *mis, float *const *im,
+                                             float *const *d_im, void *cuda_stream) {
+    if (!ctx || !mis || !d_im) return SYNIM_ERR_INVALID_ARG;
+    ctx->err.clear();
+    return run(ctx, MODE_TAN, mis, im, d_im, nullptr, nullptr, static_cast<cudaStream_t>(cuda_stream));
+}
+
+extern "C" synim_status synim_im_vjp(synim_ctx *ctx, const synim_misreg *mis, const float *const *grad_im,
+                                     double *grad_p, void *cuda_stream) {
+    if (!ctx || !mis || !grad_im || !grad_p) return SYNIM_ERR_INVALID_ARG;
+    ctx->err.clear();
+    return run(ctx, MODE_VJP, mis, nullptr, nullptr, grad_im, grad_p, static_cast<cudaStream_t>(cuda_stream));
+}

@@ -151,3 +151,47 @@ class SynIM:
 
     def check(self, stream=None):
         abi.check(self._L.synim_im_check(self._ctx, self._stream(stream)), self._ctx)
+
+    def sensitivity(self, misregs, out=None, d_out=None, stream=None):
+        """IMs and their tangents dIM/dp_k, p = (shift_x_px, shift_y_px, rot_deg, mag).
+
+        Returns (ims, tangents) with tangents[p][k] shaped like ims[p].
+        """
+        np_ = self.n_dm * self.n_wfs
+        out = self.alloc_outputs() if out is None else out
+        if d_out is None:
+            d_out = [[torch.empty_like(t) for _ in range(4)] for t in out]
+        ptrs = (ctypes.c_void_p * np_)(*[None if t is None else t.data_ptr() for t in out])
+        dptrs = (ctypes.c_void_p * (4 * np_))(*[None if t is None else t.data_ptr() for ts in d_out for t in ts])
+        abi.check(self._L.synim_im_sensitivity(self._ctx, _misreg_array(misregs), ptrs, dptrs,
+                                               self._stream(stream)), self._ctx)
+        return out, d_out
+
+    def vjp(self, misregs, grad_ims, stream=None):
+        """grad_p[p, k] = sum(grad_ims[p] * dIM_p / dp_k) as a float64 numpy array [n_pairs, 4]."""
+        np_ = self.n_dm * self.n_wfs
+        keep = [None if g is None else g.contiguous().float() for g in grad_ims]
+        gptrs = (ctypes.c_void_p * np_)(*[None if g is None else g.data_ptr() for g in keep])
+        gp = (ctypes.c_double * (4 * np_))()
+        abi.check(self._L.synim_im_vjp(self._ctx, _misreg_array(misregs), gptrs, gp, self._stream(stream)),
+                  self._ctx)
+        return np.array(gp[:]).reshape(np_, 4)
+
+
+class IMFunction(torch.autograd.Function):
+    """IMs as a differentiable function of the misregistrations.
+
+    forward(params [n_pairs, 4] float64 CPU tensor, synim) -> tuple of IMs;
+    backward uses the library's adjoint kernel (synim_im_vjp).
+    """
+
+    @staticmethod
+    def forward(ctx, params, synim):
+        mis = params.detach().cpu().double().tolist()
+        ctx.synim, ctx.mis, ctx.pdtype = synim, mis, params.dtype
+        return tuple(synim.compute(mis))
+
+    @staticmethod
+    def backward(ctx, *grads):
+        gp = ctx.synim.vjp(ctx.mis, list(grads))
+        return torch.from_numpy(gp).to(ctx.pdtype), None
