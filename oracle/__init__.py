@@ -10,6 +10,10 @@ derivative and subaperture mean, Sec. 2.3 edge repair).
 ``build()`` compiles ``synim_oracle.c`` with gcc (FP64, no FMA contraction,
 OpenMP over independent columns).
 
+Probe responses (the learned estimator's input) are the method applied to
+modal screens; their counter-based noise is Philox4x32-10 with a Box-Muller
+transform, both written from their published definitions.
+
 Parity status: the forward IM, the composite affine and its Jacobian, the
 tangents, the edge repair and the valid-subaperture rule are pinned by the
 ``-m "not gpu"`` tests (closed forms, invariants, telescoping identity,
@@ -60,6 +64,12 @@ def lib():
         L.synor_im_tangent.argtypes = [fp, ci, ci, u8p, ci, ci, u8p, u8p, dp, dp, dp, dp, cd, cd,
                                        i32p, ci, dp, ci]
         L.synor_im_tangent.restype = ci
+        L.synor_probe.argtypes = [dp, ci, ci, u8p, ci, ci, u8p, u8p, dp, dp, dp, dp, cd, cd, dp, dp]
+        L.synor_probe.restype = ci
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        L.synor_philox4x32_10.argtypes = [u32p, u32p, u32p]
+        L.synor_gauss.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int64),
+                                  ctypes.c_long, dp]
         _lib = L
     return _lib
 
@@ -205,3 +215,98 @@ def pair_tangent(workload, d: int, w: int, cols=None, misreg=None, nthreads: int
     dA, db = composite_jac(g, p)
     return im_tangent(dm.ifs, dm.mask, wfs.grid_m, wfs.n_sub, wfs.pupil_mask, wfs.subap_valid,
                       A, b, dA, db, wfs.pupil_diam_m / wfs.grid_m, wfs.slope_scale, cols, nthreads)
+
+
+# ---------------------------------------------------------------------------
+# Probe responses of the learned estimator
+# ---------------------------------------------------------------------------
+def probe_screens(dm, cmd: np.ndarray) -> np.ndarray:
+    """Modal screens S_m = sum_a cmd[m, a] IF_a in double precision, [n_modes, N, N]."""
+    flat = np.asarray(dm.ifs, np.float64).reshape(dm.n_act, -1)
+    return (np.asarray(cmd, np.float64) @ flat).reshape(len(cmd), dm.grid_n, dm.grid_n)
+
+
+def probe(screens: np.ndarray, dm_mask, wfs, A, b, dA=None, db=None):
+    """Responses [n_modes, 2 nv] of the screens at (A, b) and, with dA/db, the
+    tangents [4, n_modes, 2 nv] (core set fixed)."""
+    screens = np.ascontiguousarray(screens, np.float64)
+    n_modes, N = screens.shape[0], screens.shape[1]
+    P = _u8(wfs.pupil_mask)
+    _, _, nv = valid_subaps(P, wfs.n_sub, wfs.subap_valid)
+    out = np.zeros((n_modes, 2 * nv))
+    tan = dA is not None
+    dout = np.zeros((4, n_modes, 2 * nv)) if tan else None
+    dA_ = _f64(dA).ravel() if tan else None
+    db_ = _f64(db).ravel() if tan else None
+    m, vi = _u8(dm_mask), _u8(wfs.subap_valid)
+    A, b = _f64(A), _f64(b)
+    lib().synor_probe(_p(screens, ctypes.c_double), n_modes, N, _p(m, ctypes.c_uint8),
+                      wfs.grid_m, wfs.n_sub, _p(P, ctypes.c_uint8), _p(vi, ctypes.c_uint8),
+                      _p(A, ctypes.c_double), _p(b, ctypes.c_double), _p(dA_, ctypes.c_double),
+                      _p(db_, ctypes.c_double), wfs.pupil_diam_m / wfs.grid_m, wfs.slope_scale,
+                      _p(out, ctypes.c_double), _p(dout, ctypes.c_double))
+    return (out, dout) if tan else out
+
+
+def to_maps(rows: np.ndarray, wfs) -> np.ndarray:
+    """Scatter response rows [n_modes, 2 nv] into slope maps [n_sub, n_sub, 2 n_modes]
+    (channel 2 m + 0 = x slope of mode m, 2 m + 1 = y slope; invalid subapertures 0)."""
+    rows = np.asarray(rows)
+    ros, _, nv = valid_subaps(wfs.pupil_mask, wfs.n_sub, wfs.subap_valid)
+    n_modes = rows.shape[0]
+    maps = np.zeros((wfs.n_sub, wfs.n_sub, 2 * n_modes))
+    si, sj = np.nonzero(ros >= 0)
+    r = ros[si, sj]
+    maps[si, sj, 0::2] = rows[:, r].T
+    maps[si, sj, 1::2] = rows[:, nv + r].T
+    return maps
+
+
+def probe_maps(screens, dm, wfs, p, tangents: bool = False):
+    """Slope maps of one sample at misregistration p = (sx, sy, rot_deg, mag)."""
+    g = pair_geom(dm, wfs)
+    A, b = composite(g, p)
+    if not tangents:
+        return to_maps(probe(screens, dm.mask, wfs, A, b), wfs)
+    dA, db = composite_jac(g, p)
+    out, dout = probe(screens, dm.mask, wfs, A, b, dA, db)
+    return to_maps(out, wfs), np.stack([to_maps(dout[k], wfs) for k in range(4)])
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, np.uint32)
+    k = np.ascontiguousarray(key, np.uint32)
+    out = np.zeros(4, np.uint32)
+    u32 = ctypes.POINTER(ctypes.c_uint32)
+    lib().synor_philox4x32_10(c.ctypes.data_as(u32), k.ctypes.data_as(u32), out.ctypes.data_as(u32))
+    return out
+
+
+def gauss(seed: int, sample: int, elems) -> np.ndarray:
+    """Standard normal deviates of the given noise elements of one sample."""
+    e = np.ascontiguousarray(elems, np.int64)
+    z = np.zeros(len(e))
+    lib().synor_gauss(ctypes.c_uint64(seed), ctypes.c_uint64(sample),
+                      e.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), len(e),
+                      z.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return z
+
+
+def bf16_round(x: np.ndarray) -> np.ndarray:
+    """Round to the nearest bfloat16 (ties to even), via float32; returned as float32."""
+    f = np.ascontiguousarray(x, np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32)
+
+
+def noisy_maps(clean: np.ndarray, valid: np.ndarray, seed: int, sample: int,
+               noise_rel: float) -> np.ndarray:
+    """Probe input of one sample: clean maps [n_sub, n_sub, C] plus Gaussian
+    noise of standard deviation noise_rel * (peak |slope| of the sample) on the
+    valid subapertures (invalid ones stay 0), rounded to bfloat16."""
+    clean = np.asarray(clean, np.float64)
+    sigma = noise_rel * np.abs(clean).max()
+    z = gauss(seed, sample, np.arange(clean.size)).reshape(clean.shape)
+    out = np.where(valid[:, :, None], clean + sigma * z, 0.0)
+    return bf16_round(out)

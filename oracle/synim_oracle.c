@@ -443,3 +443,149 @@ int synor_im_tangent(const float *ifs, int n_act, int N, const uint8_t *dm_mask,
     free(lit);
     return nv;
 }
+
+/* ---------------------------------------------------------------------------
+ * Probe responses (training data of the learned misregistration estimator).
+ *
+ * A probe mode m is the DM shape S_m = sum_a cmd[m][a] IF_a (a "modal
+ * screen", formed by the caller in double precision).  Its response at
+ * misregistration p is the slope vector the method (Sec. 2.1-2.3) gives for
+ * S_m: one bilinear resample through the composite transform, edge repair
+ * with the core set of the DM mask, central differences, pupil-weighted
+ * subaperture mean.  Every step is linear in the phase for a fixed core set,
+ * so the response equals cmd[m] . IM(p); the tests pin this function to the
+ * already pinned IM oracle that way.
+ * ------------------------------------------------------------------------- */
+static inline double tap_d(const double *img, int N, long x, long y) {
+    if (x < 0 || y < 0 || x >= N || y >= N) return 0.0;
+    return img[y * (long)N + x];
+}
+
+static double bilinear_d(const double *img, int N, double x, double y, double *dx, double *dy) {
+    const double x0 = floor(x), y0 = floor(y);
+    const double fx = x - x0, fy = y - y0;
+    const long ix = (long)x0, iy = (long)y0;
+    const double v00 = tap_d(img, N, ix, iy), v10 = tap_d(img, N, ix + 1, iy);
+    const double v01 = tap_d(img, N, ix, iy + 1), v11 = tap_d(img, N, ix + 1, iy + 1);
+    if (dx) *dx = (1.0 - fy) * (v10 - v00) + fy * (v11 - v01);
+    if (dy) *dy = (1.0 - fx) * (v01 - v00) + fx * (v11 - v10);
+    return (1.0 - fx) * (1.0 - fy) * v00 + fx * (1.0 - fy) * v10 + (1.0 - fx) * fy * v01 +
+           fx * fy * v11;
+}
+
+/*
+ * Responses of n_modes screens [n_modes][N][N] (double) at one composite
+ * transform.  out is [n_modes][2 nv]; when dA/db are given, dout receives the
+ * tangents [4][n_modes][2 nv] (core set held fixed, floor-cell derivative, as
+ * synor_im_tangent).  Returns nv, or -1 on a shape error.
+ */
+int synor_probe(const double *screens, int n_modes, int N, const uint8_t *dm_mask, int M,
+                int n_sub, const uint8_t *P, const uint8_t *valid_in, const double A[4],
+                const double b[2], const double *dA, const double *db, double dw,
+                double slope_scale, double *out, double *dout) {
+    if (n_sub <= 0 || M % n_sub != 0) return -1;
+    const int ns = n_sub * n_sub;
+    const long MM = (long)M * M;
+    int32_t *row_of_sub = (int32_t *)malloc(sizeof(int32_t) * ns);
+    int32_t *lit = (int32_t *)malloc(sizeof(int32_t) * ns);
+    const int nv = synor_valid_subaps(M, n_sub, P, valid_in, row_of_sub, lit);
+    uint8_t *core = (uint8_t *)malloc((size_t)MM);
+    double *phic = (double *)malloc(sizeof(double) * MM * 5);
+    double *phi = (double *)malloc(sizeof(double) * MM);
+    double *sx = (double *)malloc(sizeof(double) * ns);
+    double *sy = (double *)malloc(sizeof(double) * ns);
+    synor_core(N, dm_mask, M, A, b, core, NULL);
+    const int nq = (dA && db && dout) ? 5 : 1;
+    for (int m = 0; m < n_modes; ++m) {
+        const double *img = screens + (long)m * N * N;
+        for (long i = 0; i < M; ++i)
+            for (long j = 0; j < M; ++j) {
+                const long p = i * M + j;
+                if (!core[p]) {
+                    for (int q = 0; q < nq; ++q) phic[q * MM + p] = 0.0;
+                    continue;
+                }
+                double gx, gy;
+                phic[p] = bilinear_d(img, N, A[0] * j + A[1] * i + b[0],
+                                     A[2] * j + A[3] * i + b[1], &gx, &gy);
+                for (int q = 1; q < nq; ++q) {
+                    const int k = q - 1;
+                    const double ddx = dA[4 * k + 0] * j + dA[4 * k + 1] * i + db[2 * k + 0];
+                    const double ddy = dA[4 * k + 2] * j + dA[4 * k + 3] * i + db[2 * k + 1];
+                    phic[q * MM + p] = gx * ddx + gy * ddy;
+                }
+            }
+        for (int q = 0; q < nq; ++q) {
+            double *col = (q == 0) ? out + (long)m * 2 * nv
+                                   : dout + ((long)(q - 1) * n_modes + m) * 2 * nv;
+            edge_repair(phic + q * MM, core, M, phi, NULL);
+            slopes_from_phase(phi, M, n_sub, P, row_of_sub, lit, nv, dw, slope_scale, col, sx,
+                              sy);
+        }
+    }
+    free(core);
+    free(phic);
+    free(phi);
+    free(sx);
+    free(sy);
+    free(row_of_sub);
+    free(lit);
+    return nv;
+}
+
+/* ---------------------------------------------------------------------------
+ * Counter-based random numbers for the probe noise: Philox4x32 with 10
+ * rounds (Salmon, Moraes, Dror and Shaw, "Parallel random numbers: as easy
+ * as 1, 2, 3", SC 2011), written from its published definition.  Each round
+ * multiplies counter words 0 and 2 by the two round constants, takes the
+ * 64-bit products apart and mixes the high halves with the other counter
+ * words and the key; the key is bumped by the two Weyl constants between
+ * rounds.
+ * ------------------------------------------------------------------------- */
+void synor_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += W0;
+            k1 += W1;
+        }
+        const uint64_t p0 = (uint64_t)M0 * c[0], p1 = (uint64_t)M1 * c[2];
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+    }
+    memcpy(out, c, sizeof(c));
+}
+
+/*
+ * Standard normal deviates of probe-noise element e[0..n) of one sample.
+ * Element e takes Philox block ctr = (e / 4, sample low, sample high, 0)
+ * under key (seed low, seed high); its lane pair (words 2t, 2t+1, t = (e % 4)
+ * / 2) gives u1 = (w0 + 1) 2^-32 and u2 = w1 2^-32, and the Box-Muller
+ * transform (Box and Muller 1958) turns them into sqrt(-2 ln u1) times
+ * cos(2 pi u2) for even e, sin(2 pi u2) for odd e.
+ */
+void synor_gauss(uint64_t seed, uint64_t sample, const int64_t *e, long n, double *z) {
+    const double two32 = 4294967296.0;
+    const double pi = 3.14159265358979323846;
+    for (long q = 0; q < n; ++q) {
+        const uint64_t blk = (uint64_t)e[q] / 4;
+        const int lane = (int)(e[q] % 4);
+        const uint32_t ctr[4] = {(uint32_t)blk, (uint32_t)sample, (uint32_t)(sample >> 32), 0u};
+        const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+        uint32_t w[4];
+        synor_philox4x32_10(ctr, key, w);
+        const int t = lane / 2;
+        const double u1 = ((double)w[2 * t] + 1.0) / two32;
+        const double u2 = (double)w[2 * t + 1] / two32;
+        const double r = sqrt(-2.0 * log(u1));
+        z[q] = (lane % 2 == 0) ? r * cos(2.0 * pi * u2) : r * sin(2.0 * pi * u2);
+    }
+}
