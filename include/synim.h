@@ -183,6 +183,100 @@ synim_status synim_im_check(synim_ctx *ctx, void *cuda_stream);
  */
 synim_status synim_im_kernel_ms(synim_ctx *ctx, double *total_ms, int32_t *n_launches);
 
+/* ------------------------------------------------------------------------
+ * Probe responses.  The paper's Sec. 5 drives the IM generator from online
+ * estimates of slowly drifting misregistrations; the estimators of this
+ * library (below) read the misregistration of one (DM, sensor) pair from the
+ * sensor's response to a few probe commands.  A probe mode m is the DM shape
+ * S_m = sum_a cmd[m][a] IF_a; its response is the slope vector that the
+ * method of Sec. 2.1-2.3 gives for S_m.  For a fixed edge-repair core set
+ * every step is linear, so the response equals cmd[m] . IM.
+ *
+ * Slope maps: [n_sub][n_sub][C] FP32 (or bfloat16), C = 2 n_modes, channel
+ * 2 m = x slope of mode m, 2 m + 1 = its y slope; invalid subapertures hold 0.
+ * A sample's parameters are a synim_misreg as 4 doubles
+ * (shift_x_px, shift_y_px, rot_deg, mag) and replace the pair's
+ * misregistration.
+ * ---------------------------------------------------------------------- */
+
+/*
+ * Attach probe modes to pair (dm, wfs): cmd is host [n_modes][n_act] doubles
+ * (mode m's command on actuator a, cube order), 1 <= n_modes <= 32.  Forms
+ * the modal screens once on the device from the packed supports (FP64 sums,
+ * stored FP32 [N + 2][N + 2][modes rounded up to 4], zero border).  The
+ * per-row working tile needs 4 (k + 2)(k + 2) (n_modes rounded up to 4) bytes
+ * of shared memory for tangents x 5; sensors whose k makes even one
+ * subaperture too large are refused (SYNIM_ERR_SHAPE).  Replaces a previous
+ * attachment; synchronous.
+ */
+synim_status synim_probe_attach(synim_ctx *ctx, int32_t dm, int32_t wfs, const double *cmd,
+                                int32_t n_modes);
+
+/* Map shape of the attached probes; valid (host [n_sub][n_sub], may be NULL)
+ * receives 1 for valid subapertures. */
+synim_status synim_probe_query(const synim_ctx *ctx, int32_t *n_sub, int32_t *n_channels,
+                               uint8_t *valid);
+
+/*
+ * Clean probe responses of n samples.  params: device [n][4] doubles.
+ * maps: device [n][n_sub][n_sub][C] FP32.  d_maps: NULL, or device
+ * [4][n][n_sub][n_sub][C] FP32 tangents with respect to the four parameters
+ * (core set held fixed, floor-cell bilinear derivative, as
+ * synim_im_sensitivity).  Asynchronous on cuda_stream.
+ */
+synim_status synim_probe_response(synim_ctx *ctx, const double *params, int64_t n, float *maps,
+                                  float *d_maps, void *cuda_stream);
+
+/*
+ * Noisy bfloat16 probe inputs (training data of the learned estimator).
+ * Sample q gets its clean maps plus Gaussian noise of standard deviation
+ * noise_rel x (largest |slope| of its maps) on valid subapertures (invalid
+ * ones stay 0), rounded to the nearest bfloat16 (ties to even).  Noise of
+ * element e of the sample's maps: Philox4x32-10 (Salmon et al., SC 2011)
+ * under key (seed low, seed high) at counter (e / 4, s low, s high, 0),
+ * s = sample0 + q; words (2t, 2t + 1), t = (e mod 4) / 2, give
+ * u1 = (w + 1) 2^-32 and u2 = w' 2^-32, and the Box-Muller transform gives
+ * sqrt(-2 ln u1) cos(2 pi u2) for even e, sqrt(-2 ln u1) sin(2 pi u2) for
+ * odd e.  params: device [n][4]; out: device [n][n_sub][n_sub][C] bfloat16
+ * bits.  Asynchronous; works in batches with context-owned scratch.
+ */
+synim_status synim_probe_generate(synim_ctx *ctx, const double *params, int64_t n, uint64_t seed,
+                                  uint64_t sample0, float noise_rel, uint16_t *out,
+                                  void *cuda_stream);
+
+/*
+ * Misregistration of the probed pair from measured probe responses.
+ *   probe_slopes: device [n][n_sub][n_sub][C] FP32 slope maps (layout above).
+ *   method: 0 = Gauss-Newton fit from the initial guesses in inout;
+ *           1 = the trained network alone (synim_cnn_train / synim_cnn_load);
+ *           2 = the network's estimate refined by the fit.
+ *   inout: host [n]: initial guesses (method 0; ignored otherwise), then the
+ *          estimates.
+ *   residual_out: host [n] or NULL: ||y - s(p)|| / ||y|| at the estimate, with
+ *          s regenerated by Sec. 2.1-2.3 (the judge of the estimate).
+ * Fit: r = y - s(p) over all map entries, Jacobian J from the probe tangents,
+ * step (J^T J + mu diag(J^T J)) dp = J^T r solved in FP64 (Cholesky); mu = 0
+ * at first, x10 when the cost rises (the step is rejected), /10 after an
+ * accepted step; stops when an accepted step, divided component-wise by
+ * the scale (default 8 px, 8 px, 2 deg, 0.02), has norm below tol (default
+ * 1e-4), or after max_iter steps (default 30).  The cost is only piecewise
+ * smooth (bilinear cells, core changes), so the step test stops at a step
+ * size well below the estimate's noise rather than at rounding level.  An
+ * initial guess should not put the sensor grid exactly on the DM grid (the
+ * identity when N = M): there every sample lies on a cell line and the
+ * floor-cell Jacobian is one-sided.  SYNIM_ERR_NOT_TRAINED for methods 1-2
+ * without a network.  Synchronous.
+ */
+synim_status synim_misreg_estimate(synim_ctx *ctx, const float *probe_slopes, int64_t n, int32_t method,
+                                   synim_misreg *inout, double *residual_out, void *cuda_stream);
+
+/* Fit settings: max_iter in 1..1000, tol > 0, scale (4 positive doubles) or NULL to keep. */
+synim_status synim_gn_config(synim_ctx *ctx, int32_t max_iter, double tol, const double *scale);
+
+/* Steps taken and convergence flag (1 = stopped on the step test) of each
+ * sample of the last synim_misreg_estimate; host [n] each, either may be NULL. */
+synim_status synim_misreg_estimate_stats(const synim_ctx *ctx, int32_t *iters, int32_t *converged);
+
 /* Free all device memory of the context (waits for its streams). NULL is a no-op. */
 void synim_im_destroy(synim_ctx *ctx);
 

@@ -310,3 +310,50 @@ def noisy_maps(clean: np.ndarray, valid: np.ndarray, seed: int, sample: int,
     z = gauss(seed, sample, np.arange(clean.size)).reshape(clean.shape)
     out = np.where(valid[:, :, None], clean + sigma * z, 0.0)
     return bf16_round(out)
+
+
+def gn_fit(screens, dm, wfs, y, p0, max_iter: int = 30, tol: float = 1e-4,
+           scale=(8.0, 8.0, 2.0, 0.02)):
+    """Levenberg-Marquardt fit of a probe measurement y [n_sub, n_sub, C] (FP64).
+
+    Residual r = y - s(p) over all map entries, Jacobian from the probe
+    tangents; each step solves (J^T J + mu diag(J^T J)) dp = J^T r (Cholesky);
+    mu starts at 0, becomes 1e-3 (or x10) when the cost rises and the step is
+    rejected, /10 (0 below 1e-7) after an accepted step; stop when an accepted
+    step, divided by `scale`, has norm below tol, or after max_iter steps.
+    Returns (p, ||y - s(p)|| / ||y||, steps, converged).
+    """
+    y = np.asarray(y, np.float64)
+    sc = np.asarray(scale, np.float64)
+
+    def evaluate(p):
+        s, T = probe_maps(screens, dm, wfs, p, tangents=True)
+        r = (y - s).ravel()
+        J = T.reshape(4, -1).T
+        return r @ r, J.T @ J, J.T @ r
+
+    p = np.asarray(p0, np.float64).copy()
+    c, H, g = evaluate(p)
+    mu, it, conv = 0.0, 0, False
+    while it < max_iter:
+        try:
+            L = np.linalg.cholesky(H + mu * np.diag(np.diag(H)))
+        except np.linalg.LinAlgError:
+            mu = 1e-3 if mu == 0.0 else mu * 10.0
+            it += 1
+            continue
+        dp = np.linalg.solve(L.T, np.linalg.solve(L, g))
+        it += 1
+        pt = p + dp
+        ct, Ht, gt = evaluate(pt)
+        if ct <= c:
+            p, c, H, g = pt, ct, Ht, gt
+            mu = 0.0 if mu * 0.1 < 1e-7 else mu * 0.1
+            if np.linalg.norm(dp / sc) < tol:
+                conv = True
+                break
+        else:
+            mu = 1e-3 if mu == 0.0 else mu * 10.0
+            if mu > 1e12:
+                break
+    return p, float(np.sqrt(c / (y.ravel() @ y.ravel()))), it, conv

@@ -63,6 +63,15 @@ SIGNATURES = {
     "synim_im_compute_noalloc": (c_int32, [ctypes.POINTER(synim_dm_desc), ctypes.POINTER(synim_wfs_desc),
                                            ctypes.POINTER(synim_misreg), c_void_p, ctypes.POINTER(c_int64),
                                            c_void_p]),
+    "synim_probe_attach": (c_int32, [c_void_p, c_int32, c_int32, ctypes.POINTER(c_double), c_int32]),
+    "synim_probe_query": (c_int32, [c_void_p, ctypes.POINTER(c_int32), ctypes.POINTER(c_int32), c_void_p]),
+    "synim_probe_response": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),
+    "synim_probe_generate": (c_int32, [c_void_p, c_void_p, c_int64, ctypes.c_uint64, ctypes.c_uint64, c_float,
+                                       c_void_p, c_void_p]),
+    "synim_misreg_estimate": (c_int32, [c_void_p, c_void_p, c_int64, c_int32, ctypes.POINTER(synim_misreg),
+                                        ctypes.POINTER(c_double), c_void_p]),
+    "synim_gn_config": (c_int32, [c_void_p, c_int32, c_double, ctypes.POINTER(c_double)]),
+    "synim_misreg_estimate_stats": (c_int32, [c_void_p, ctypes.POINTER(c_int32), ctypes.POINTER(c_int32)]),
     "synim_im_destroy": (None, [c_void_p]),
     "synim_status_string": (ctypes.c_char_p, [c_int32]),
     "synim_last_error": (ctypes.c_char_p, [c_void_p]),

@@ -24,47 +24,8 @@ namespace {
 
 thread_local std::string g_create_error;
 
-constexpr int NSLOT = 4;
-constexpr int NPROF = 256;
-
-struct GraphEntry {
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    cudaGraphNode_t ev_start = nullptr, ev_stop = nullptr;  // event-record nodes (profiling)
-};
-
 }  // namespace
 
-struct synim_ctx {
-    int device = 0, n_sm = 0, n_dm = 0, n_wfs = 0;
-    DmHost dmh[SYNIM_MAX_DM];
-    WfsHost wh[SYNIM_MAX_WFS];
-    Geo geo{};
-    std::vector<void *> dev_allocs;
-    std::vector<void *> host_allocs;
-    DevPair *d_pairs = nullptr;
-    DevPair *h_pairs[NSLOT] = {};
-    cudaEvent_t slot_ev[NSLOT] = {};
-    bool slot_used[NSLOT] = {};
-    int slot = 0;
-    int *d_counter = nullptr, *d_err = nullptr, *h_err = nullptr;
-    double *d_gp = nullptr;
-    long long pst_off[SYNIM_MAX_PAIRS] = {};
-    long long line_off[SYNIM_MAX_PAIRS] = {};
-    uint8_t *d_pst = nullptr, *d_lines = nullptr;
-    int max_mm = 0, max_lines = 0;
-    int threads = 512, ctas_per_sm = 0;
-    bool use_graph = true;
-    int arena_floats = 0;
-    std::map<std::tuple<int, size_t, int, int>, GraphEntry> graphs;
-    cudaStream_t cap = nullptr;
-    bool profile = false;
-    cudaEvent_t prof_a[NPROF] = {}, prof_b[NPROF] = {};
-    unsigned long long prof_head = 0, prof_tail = 0;
-    double prof_acc_ms = 0.0;
-    int prof_acc_n = 0;
-    std::string err;
-};
 
 // ---------------------------------------------------------------------------
 // helpers
@@ -117,49 +78,17 @@ namespace synim {
 
 void clear_create_error() { g_create_error.clear(); }
 
+int ctx_valid_rows(const synim_ctx *ctx, int w, const int **vsub, int *n_sub) {
+    *vsub = ctx->geo.wfs[w].vsub;
+    *n_sub = ctx->geo.wfs[w].n_sub;
+    return ctx->geo.wfs[w].nv;
+}
+
 // Composite affine (Sec. 2.1) in closed form:
 //   A = c dw / (dd m) R(-td) R(tw) diag(mw)
 //   b = cN + R(-td) (c s_w + h theta - s_d) / (dd m) - A (cM, cM)
 // with c = 1 - h/H the LGS cone factor, s_d the DM shift in metres, cN and
 // cM the DM and sensor grid centres.
-void composite(const DmHost &D, const WfsHost &W, const synim_misreg &m, double A[4], double b[2]) {
-    const double cone = (W.H > 0.0 && std::isfinite(W.H)) ? 1.0 - D.h / W.H : 1.0;
-    const double dw = W.D / W.M;
-    const double s = cone * dw / (D.dd * m.mag);
-    const double tw = W.rot * M_PI / 180.0, td = m.rot_deg * M_PI / 180.0;
-    const double ct = std::cos(td), st = std::sin(td), cw = std::cos(tw), sw = std::sin(tw);
-    // X = R(tw) diag(mw)
-    const double X00 = cw * W.mag[0], X01 = -sw * W.mag[1], X10 = sw * W.mag[0], X11 = cw * W.mag[1];
-    // R(-td) = [[ct, st], [-st, ct]]
-    A[0] = s * (ct * X00 + st * X10);
-    A[1] = s * (ct * X01 + st * X11);
-    A[2] = s * (-st * X00 + ct * X10);
-    A[3] = s * (-st * X01 + ct * X11);
-    const double tx = cone * W.shift[0] + D.h * W.th[0] - m.shift_x_px * D.dd;
-    const double ty = cone * W.shift[1] + D.h * W.th[1] - m.shift_y_px * D.dd;
-    const double inv = 1.0 / (D.dd * m.mag);
-    const double cN = (D.N - 1) * 0.5, cM = (W.M - 1) * 0.5;
-    b[0] = cN + inv * (ct * tx + st * ty) - (A[0] + A[1]) * cM;
-    b[1] = cN + inv * (-st * tx + ct * ty) - (A[2] + A[3]) * cM;
-}
-
-// d(A, b)/dp_k in closed form: the shifts translate by -R(-td) e / m; the
-// rotation turns the map about the DM centre (dA = -J A, db = -J (b - cN),
-// J = [[0, -1], [1, 0]], per radian); the magnification scales it about the
-// DM centre (dA = -A / m, db = -(b - cN) / m).
-void composite_jac(const DmHost &D, const synim_misreg &m, const double A[4], const double b[2],
-                   double dA[16], double db[8]) {
-    const double td = m.rot_deg * M_PI / 180.0, ct = std::cos(td), st = std::sin(td);
-    const double cN = (D.N - 1) * 0.5, rad = M_PI / 180.0;
-    std::fill(dA, dA + 16, 0.0);
-    db[0] = -ct / m.mag; db[1] = st / m.mag;
-    db[2] = -st / m.mag; db[3] = -ct / m.mag;
-    dA[8] = rad * A[2]; dA[9] = rad * A[3]; dA[10] = -rad * A[0]; dA[11] = -rad * A[1];
-    db[4] = rad * (b[1] - cN); db[5] = -rad * (b[0] - cN);
-    for (int q = 0; q < 4; ++q) dA[12 + q] = -A[q] / m.mag;
-    db[6] = -(b[0] - cN) / m.mag; db[7] = -(b[1] - cN) / m.mag;
-}
-
 bool invert2(const double A[4], double Ai[4]) {
     const double det = A[0] * A[3] - A[1] * A[2];
     if (!(std::fabs(det) > 1e-300) || !std::isfinite(det)) return false;
@@ -198,6 +127,7 @@ struct WfsTables {
     std::vector<int8_t> irr_w;
     std::vector<short> vsj;
     std::vector<float> fac;
+    std::vector<uint8_t> P;
     int nv = 0;
 };
 
@@ -322,6 +252,7 @@ bool build_wfs_tables(const synim_wfs_desc &d, WfsTables &t, std::string &why) {
         }
     }
     t.irrc_row[n] = (int)t.irrc.size();
+    t.P = std::move(P);
     return true;
 }
 
@@ -386,6 +317,8 @@ void synim_im_destroy(synim_ctx *ctx) {
     for (int s = 0; s < NSLOT; ++s)
         if (ctx->slot_ev[s]) cudaEventDestroy(ctx->slot_ev[s]);
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
+    est_destroy(ctx->est);
+    probe_destroy(ctx->probe);
     for (void *p : ctx->dev_allocs) cudaFree(p);
     for (void *p : ctx->host_allocs) cudaFreeHost(p);
     delete ctx;
@@ -521,6 +454,8 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
             return bail(SYNIM_ERR_SHAPE);
         }
         H.nv = T.nv;
+        c->pupil[w] = T.P;
+        c->vidx_h[w] = T.vidx;
         DevWFS &G = c->geo.wfs[w];
         uint8_t *xc, *yc;
         int *ip, *is, *vs, *vr;

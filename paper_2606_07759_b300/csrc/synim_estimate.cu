@@ -1,0 +1,397 @@
+// synim_estimate.cu -- misregistration estimators of one (DM, sensor) pair
+// from measured probe responses: a batched Gauss-Newton / Levenberg-
+// Marquardt fit whose Jacobian comes from the probe tangents, the learned
+// network (synim_cnn.cu), and the network's estimate refined by the fit.
+//
+// One fit pass over a batch of samples:
+//   probe_launch  responses s(p_t) and tangents ds/dp at every sample's trial
+//                 point p_t (Sec. 2.1-2.3, forward mode);
+//   k_gn_reduce   one CTA per sample: r = y - s, sums r.r, J^T J (10), J^T r,
+//                 y.y in FP64 over all map entries (fixed order: per-thread
+//                 strided sums, then a fixed tree);
+//   k_gn_step     one thread per sample: accept / reject the trial point,
+//                 update the damping, solve (J^T J + mu diag) dp = J^T r by
+//                 Cholesky in FP64, next trial point.
+// The host repeats passes until every sample has stopped.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "synim_internal.h"
+
+namespace synim {
+
+constexpr int kRedThreads = 256;
+constexpr int kRed = 16;  // c, H (10), g (4), y.y
+
+enum : int { GN_DONE = 1, GN_CONV = 2, GN_FIRST = 4 };
+
+struct GnState {
+    double p[4], pt[4], c, yy, H[10], g[4], mu, dnorm;
+    int it, flags;
+};
+
+struct EstState {
+    int max_iter = 30;
+    double tol = 1e-4;
+    double scale[4] = {8.0, 8.0, 2.0, 0.02};
+    long long cap = 0;          // samples the buffers hold
+    float *maps = nullptr;      // [cap][per_sample]
+    float *dmaps = nullptr;     // [4][cap][per_sample]
+    double *red = nullptr;      // [cap][kRed]
+    double *pt = nullptr;       // [cap][4]
+    GnState *st = nullptr;      // [cap]
+    int *n_active = nullptr;    // device counter
+    int *h_active = nullptr;    // pinned
+    std::vector<int> iters, conv;  // of the last estimate
+};
+
+void est_destroy(EstState *e) {
+    if (!e) return;
+    cudaFree(e->maps);
+    cudaFree(e->dmaps);
+    cudaFree(e->red);
+    cudaFree(e->pt);
+    cudaFree(e->st);
+    cudaFree(e->n_active);
+    cudaFreeHost(e->h_active);
+    delete e;
+}
+
+// Index of (a, b), a <= b, in the packed upper triangle of a 4x4 matrix.
+__host__ __device__ __forceinline__ int tri(int a, int b) {
+    return a * 4 - a * (a - 1) / 2 + (b - a);
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+k_gn_reduce(const float *__restrict__ y, const float *__restrict__ s, const float *__restrict__ ds,
+            long n, int per_sample, double *__restrict__ red) {
+    const long q = blockIdx.x;
+    const float *yq = y + q * per_sample, *sq = s + q * per_sample;
+    const size_t plane = (size_t)n * per_sample;
+    double acc[kRed];
+#pragma unroll
+    for (int t = 0; t < kRed; ++t) acc[t] = 0.0;
+    for (int e = threadIdx.x; e < per_sample; e += blockDim.x) {
+        const double yv = yq[e];
+        const double r = yv - (double)sq[e];
+        double j[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) j[k] = ds[(size_t)k * plane + (size_t)q * per_sample + e];
+        acc[0] += r * r;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+#pragma unroll
+            for (int b = a; b < 4; ++b) acc[1 + tri(a, b)] += j[a] * j[b];
+            acc[11 + a] += j[a] * r;
+        }
+        acc[15] += yv * yv;
+    }
+    __shared__ double sh[kRedThreads / 32][kRed];
+#pragma unroll
+    for (int t = 0; t < kRed; ++t) {
+        double v = acc[t];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        acc[t] = v;
+    }
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int t = 0; t < kRed; ++t) sh[threadIdx.x >> 5][t] = acc[t];
+    __syncthreads();
+    if (threadIdx.x < kRed) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sh[w][threadIdx.x];
+        red[q * kRed + threadIdx.x] = v;
+    }
+}
+
+// Cholesky solve of the 4x4 SPD system (packed upper triangle); false if a
+// pivot is not positive.
+__device__ bool chol_solve4(const double *Hp, const double *g, double mu, double *x) {
+    double L[4][4] = {};
+    for (int a = 0; a < 4; ++a)
+        for (int b = 0; b <= a; ++b) {
+            double v = Hp[tri(b, a)];
+            if (a == b) v += mu * Hp[tri(a, a)];
+            for (int k = 0; k < b; ++k) v -= L[a][k] * L[b][k];
+            if (a == b) {
+                if (!(v > 0.0)) return false;
+                L[a][a] = sqrt(v);
+            } else {
+                L[a][b] = v / L[b][b];
+            }
+        }
+    double z[4];
+    for (int a = 0; a < 4; ++a) {
+        double v = g[a];
+        for (int k = 0; k < a; ++k) v -= L[a][k] * z[k];
+        z[a] = v / L[a][a];
+    }
+    for (int a = 3; a >= 0; --a) {
+        double v = z[a];
+        for (int k = a + 1; k < 4; ++k) v -= L[k][a] * x[k];
+        x[a] = v / L[a][a];
+    }
+    return true;
+}
+
+struct GnCfg {
+    int max_iter;
+    double tol, scale[4];
+};
+
+__global__ void k_gn_step(GnState *__restrict__ S, const double *__restrict__ red, long n, const GnCfg cfg,
+                          double *__restrict__ pt, int *__restrict__ n_active) {
+    const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    GnState s = S[q];
+    if (!(s.flags & GN_DONE)) {
+        const double *R = red + q * kRed;
+        const double ct = R[0];
+        bool accept = false;
+        if (s.flags & GN_FIRST) {
+            accept = true;
+            s.flags &= ~GN_FIRST;
+        } else if (ct <= s.c) {
+            accept = true;
+            if (s.dnorm < cfg.tol) s.flags |= GN_DONE | GN_CONV;
+            s.mu = (s.mu * 0.1 < 1e-7) ? 0.0 : s.mu * 0.1;
+        } else {
+            s.mu = (s.mu == 0.0) ? 1e-3 : s.mu * 10.0;
+            if (s.mu > 1e12) s.flags |= GN_DONE;
+        }
+        if (accept) {
+            for (int k = 0; k < 4; ++k) s.p[k] = s.pt[k];
+            s.c = ct;
+            s.yy = R[15];
+            for (int t = 0; t < 10; ++t) s.H[t] = R[1 + t];
+            for (int k = 0; k < 4; ++k) s.g[k] = R[11 + k];
+        }
+        if (!(s.flags & GN_DONE) && s.it >= cfg.max_iter) s.flags |= GN_DONE;
+        if (!(s.flags & GN_DONE)) {
+            double dp[4];
+            if (chol_solve4(s.H, s.g, s.mu, dp)) {
+                double d2 = 0.0;
+                for (int k = 0; k < 4; ++k) {
+                    s.pt[k] = s.p[k] + dp[k];
+                    const double u = dp[k] / cfg.scale[k];
+                    d2 += u * u;
+                }
+                s.dnorm = sqrt(d2);
+            } else {
+                // singular normal matrix: stay, damp harder
+                for (int k = 0; k < 4; ++k) s.pt[k] = s.p[k];
+                s.dnorm = 0.0;
+                s.mu = (s.mu == 0.0) ? 1e-3 : s.mu * 10.0;
+                s.flags |= GN_FIRST;  // re-evaluate at p, accepted as is
+            }
+            ++s.it;
+            atomicAdd(n_active, 1);
+        } else {
+            for (int k = 0; k < 4; ++k) s.pt[k] = s.p[k];
+        }
+    }
+    for (int k = 0; k < 4; ++k) pt[4 * q + k] = s.pt[k];
+    S[q] = s;
+}
+
+__global__ void k_gn_init(GnState *__restrict__ S, const double *__restrict__ p0, long n,
+                          double *__restrict__ pt) {
+    const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    GnState s;
+    memset(&s, 0, sizeof(s));
+    for (int k = 0; k < 4; ++k) s.p[k] = s.pt[k] = pt[4 * q + k] = p0[4 * q + k];
+    s.flags = GN_FIRST;
+    S[q] = s;
+}
+
+namespace {
+
+synim_status efail(synim_ctx *c, synim_status s, const std::string &m) {
+    c->err = m;
+    return s;
+}
+
+synim_status ecuda(synim_ctx *c, cudaError_t e, const char *what) {
+    return efail(c, e == cudaErrorMemoryAllocation ? SYNIM_ERR_OOM : SYNIM_ERR_CUDA,
+                 std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+EstState *est_get(synim_ctx *c) {
+    if (!c->est) c->est = new EstState();
+    return c->est;
+}
+
+cudaError_t est_reserve(EstState *E, long long cap, int per_sample) {
+    if (cap <= E->cap) return cudaSuccess;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return e;
+    cudaFree(E->maps);
+    cudaFree(E->dmaps);
+    cudaFree(E->red);
+    cudaFree(E->pt);
+    cudaFree(E->st);
+    E->maps = E->dmaps = nullptr;
+    E->red = E->pt = nullptr;
+    E->st = nullptr;
+    E->cap = 0;
+    if ((e = cudaMalloc(&E->maps, sizeof(float) * per_sample * cap)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&E->dmaps, sizeof(float) * 4 * per_sample * cap)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&E->red, sizeof(double) * kRed * cap)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&E->pt, sizeof(double) * 4 * cap)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&E->st, sizeof(GnState) * cap)) != cudaSuccess) return e;
+    if (!E->n_active && (e = cudaMalloc(&E->n_active, sizeof(int))) != cudaSuccess) return e;
+    if (!E->h_active && (e = cudaMallocHost(&E->h_active, sizeof(int))) != cudaSuccess) return e;
+    E->cap = cap;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+// Fit n samples (n <= E->cap) from initial points p0 (device [n][4]); writes
+// the estimates to p_out (host [n][4]), the relative residual to res (host
+// [n], may be null) and the per-sample statistics.
+cudaError_t gn_fit(synim_ctx *c, const float *y, long long n, const double *p0, double *p_out, double *res,
+                   int *iters, int *conv, cudaStream_t st) {
+    EstState *E = c->est;
+    const int per_sample = probe_per_sample(c->probe);
+    GnCfg cfg;
+    cfg.max_iter = E->max_iter;
+    cfg.tol = E->tol;
+    for (int k = 0; k < 4; ++k) cfg.scale[k] = E->scale[k];
+    const unsigned nb = (unsigned)((n + 63) / 64);
+    k_gn_init<<<nb, 64, 0, st>>>(E->st, p0, n, E->pt);
+    cudaError_t e = cudaGetLastError();
+    for (int pass = 0; pass <= E->max_iter + 16 && e == cudaSuccess; ++pass) {
+        if ((e = probe_launch(c, E->pt, n, E->maps, E->dmaps, nullptr, st)) != cudaSuccess) break;
+        k_gn_reduce<<<(unsigned)n, kRedThreads, 0, st>>>(y, E->maps, E->dmaps, n, per_sample, E->red);
+        if ((e = cudaMemsetAsync(E->n_active, 0, sizeof(int), st)) != cudaSuccess) break;
+        k_gn_step<<<nb, 64, 0, st>>>(E->st, E->red, n, cfg, E->pt, E->n_active);
+        if ((e = cudaMemcpyAsync(E->h_active, E->n_active, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            break;
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) break;
+        if (*E->h_active == 0) break;
+    }
+    if (e != cudaSuccess) return e;
+    std::vector<GnState> hs((size_t)n);
+    if ((e = cudaMemcpyAsync(hs.data(), E->st, sizeof(GnState) * n, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return e;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+    for (long long q = 0; q < n; ++q) {
+        for (int k = 0; k < 4; ++k) p_out[4 * q + k] = hs[q].p[k];
+        if (res) res[q] = hs[q].yy > 0 ? std::sqrt(hs[q].c / hs[q].yy) : 0.0;
+        if (iters) iters[q] = hs[q].it;
+        if (conv) conv[q] = (hs[q].flags & GN_CONV) ? 1 : 0;
+    }
+    return cudaSuccess;
+}
+
+// CNN estimate of n samples (synim_cnn.cu): params_out device [n][4].
+cudaError_t cnn_predict_slopes(synim_ctx *c, const float *y, long long n, double *params_out, cudaStream_t st,
+                               std::string &why);
+
+}  // namespace synim
+
+using namespace synim;
+
+extern "C" {
+
+synim_status synim_gn_config(synim_ctx *ctx, int32_t max_iter, double tol, const double *scale) {
+    if (!ctx) return SYNIM_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (max_iter < 1 || max_iter > 1000 || !(tol > 0.0))
+        return efail(ctx, SYNIM_ERR_INVALID_ARG, "gn_config: max_iter in 1..1000, tol > 0");
+    EstState *E = est_get(ctx);
+    E->max_iter = max_iter;
+    E->tol = tol;
+    if (scale)
+        for (int k = 0; k < 4; ++k) {
+            if (!(scale[k] > 0.0)) return efail(ctx, SYNIM_ERR_INVALID_ARG, "gn_config: scale must be > 0");
+            E->scale[k] = scale[k];
+        }
+    return SYNIM_OK;
+}
+
+synim_status synim_misreg_estimate(synim_ctx *ctx, const float *probe_slopes, int64_t n, int32_t method,
+                                   synim_misreg *inout, double *residual_out, void *cuda_stream) {
+    if (!ctx) return SYNIM_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (!ctx->probe) return efail(ctx, SYNIM_ERR_INVALID_ARG, "misreg_estimate: no probes attached");
+    if (n < 0 || (n > 0 && (!probe_slopes || !inout)) || method < 0 || method > 2)
+        return efail(ctx, SYNIM_ERR_INVALID_ARG, "misreg_estimate: bad n, probe_slopes, inout or method");
+    EstState *E = est_get(ctx);
+    E->iters.assign((size_t)n, 0);
+    E->conv.assign((size_t)n, 0);
+    if (n == 0) return SYNIM_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const int per_sample = probe_per_sample(ctx->probe);
+    const long long chunk = std::min<long long>(n, 512);
+    cudaError_t e = est_reserve(E, chunk, per_sample);
+    if (e != cudaSuccess) return ecuda(ctx, e, "misreg_estimate scratch");
+    double *p0 = nullptr;
+    if ((e = cudaMalloc(&p0, sizeof(double) * 4 * chunk)) != cudaSuccess) return ecuda(ctx, e, "misreg_estimate");
+    std::vector<double> hp((size_t)4 * chunk), hout((size_t)4 * chunk);
+    synim_status status = SYNIM_OK;
+    for (long long s0 = 0; s0 < n && status == SYNIM_OK; s0 += chunk) {
+        const long long b = std::min(chunk, n - s0);
+        const float *y = probe_slopes + (size_t)s0 * per_sample;
+        if (method == 0) {
+            for (long long q = 0; q < b; ++q) {
+                const synim_misreg &m = inout[s0 + q];
+                hp[4 * q + 0] = m.shift_x_px;
+                hp[4 * q + 1] = m.shift_y_px;
+                hp[4 * q + 2] = m.rot_deg;
+                hp[4 * q + 3] = m.mag;
+            }
+            e = cudaMemcpyAsync(p0, hp.data(), sizeof(double) * 4 * b, cudaMemcpyHostToDevice, st);
+        } else {
+            std::string why;
+            e = cnn_predict_slopes(ctx, y, b, p0, st, why);
+            if (e == cudaErrorNotReady) {
+                status = efail(ctx, SYNIM_ERR_NOT_TRAINED, "misreg_estimate: " + why);
+                break;
+            }
+        }
+        if (e != cudaSuccess) {
+            status = ecuda(ctx, e, "misreg_estimate");
+            break;
+        }
+        if (method == 1) {
+            // network only: the judge is the residual of the regenerated responses
+            const int save = E->max_iter;
+            E->max_iter = 0;
+            e = gn_fit(ctx, y, b, p0, hout.data(), residual_out ? residual_out + s0 : nullptr, nullptr, nullptr, st);
+            E->max_iter = save;
+        } else {
+            e = gn_fit(ctx, y, b, p0, hout.data(), residual_out ? residual_out + s0 : nullptr,
+                       E->iters.data() + s0, E->conv.data() + s0, st);
+        }
+        if (e != cudaSuccess) {
+            status = ecuda(ctx, e, "misreg_estimate fit");
+            break;
+        }
+        for (long long q = 0; q < b; ++q) {
+            synim_misreg &m = inout[s0 + q];
+            m.shift_x_px = hout[4 * q + 0];
+            m.shift_y_px = hout[4 * q + 1];
+            m.rot_deg = hout[4 * q + 2];
+            m.mag = hout[4 * q + 3];
+        }
+    }
+    cudaFree(p0);
+    return status;
+}
+
+synim_status synim_misreg_estimate_stats(const synim_ctx *ctx, int32_t *iters, int32_t *converged) {
+    if (!ctx || !ctx->est) return SYNIM_ERR_INVALID_ARG;
+    const EstState *E = ctx->est;
+    for (size_t q = 0; q < E->iters.size(); ++q) {
+        if (iters) iters[q] = E->iters[q];
+        if (converged) converged[q] = E->conv[q];
+    }
+    return SYNIM_OK;
+}
+
+}  // extern "C"

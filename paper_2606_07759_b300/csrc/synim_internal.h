@@ -18,9 +18,15 @@
 #pragma once
 
 #include <cstdint>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
 #include <cuda_runtime.h>
 
 #include "synim.h"
+#include "synim_geom.h"
 
 #define SYNIM_MAX_DM 8
 #define SYNIM_MAX_WFS 16
@@ -83,30 +89,19 @@ struct Geo {
     int n_groups[SYNIM_MAX_DM];
 };
 
-// Host-side geometry of one DM and one sensor.
-struct DmHost {
-    int n_act = 0, N = 0, W = 0, Wp = 0;
-    double dd = 0, h = 0;
-};
-
-struct WfsHost {
-    int n_sub = 0, M = 0, k = 0, nv = 0, CH = 1;
-    double D = 0, H = 0, th[2] = {0, 0}, rot = 0, mag[2] = {1, 1}, shift[2] = {0, 0}, scale = 1;
-};
-
 enum { ERR_TIMEOUT = 1, ERR_ARENA = 2 };
 
 enum Mode { MODE_FWD = 0, MODE_TAN = 1, MODE_VJP = 2 };
 
 // Host helpers (synim_api.cu).
-void composite(const DmHost &D, const WfsHost &W, const synim_misreg &m, double A[4], double b[2]);
-void composite_jac(const DmHost &D, const synim_misreg &m, const double A[4], const double b[2],
-                   double dA[16], double db[8]);
 bool invert2(const double A[4], double Ai[4]);
 int largest_divisor_le(int k, int cap);
 long long arena_need(const DmHost &D, const WfsHost &W, const double Ai[4], int NV);
 void split_pair(DevPair &P);  // float pairs of A, b and the float inverse
 void clear_create_error();         // synim_api.cu (no allocation)
+// Valid-row tables of sensor w of a context (device pointers): vsub[r] =
+// (si << 16) | sj of valid row r; returns nv.
+int ctx_valid_rows(const synim_ctx *ctx, int w, const int **vsub, int *n_sub);
 const char *noalloc_last_error();  // synim_noalloc.cu
 
 // Launch wrappers (synim_kernels.cu).
@@ -122,4 +117,62 @@ cudaError_t im_prepare(int mode, int threads, size_t smem, int *blocks_per_sm);
 cudaError_t launch_im(int mode, const Geo &g, const DevPair *pairs, int *counter, int *err,
                       double *gp, int grid, int threads, size_t smem, cudaStream_t s);
 
+struct ProbeSet;   // synim_probe.cu
+void probe_destroy(ProbeSet *p);
+// Probe responses of n samples (params device [n][4]): maps [n][per_sample],
+// tangents dmaps [4][n][per_sample] when not null, per-sample peak |slope|
+// (float bits) when peak is not null.
+cudaError_t probe_launch(synim_ctx *c, const double *params, long long n, float *maps, float *dmaps,
+                         unsigned *peak, cudaStream_t st);
+int probe_per_sample(const ProbeSet *p);   // n_sub^2 x channels
+struct EstState;   // synim_estimate.cu
+void est_destroy(EstState *e);
+
+constexpr int NSLOT = 4;
+constexpr int NPROF = 256;
+
+struct GraphEntry {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t ev_start = nullptr, ev_stop = nullptr;  // event-record nodes (profiling)
+};
+
 }  // namespace synim
+
+// One context (opaque to callers): everything create() packed, the per-call
+// parameter slots, captured graphs and profiling events.
+struct synim_ctx {
+    int device = 0, n_sm = 0, n_dm = 0, n_wfs = 0;
+    synim::DmHost dmh[SYNIM_MAX_DM];
+    synim::WfsHost wh[SYNIM_MAX_WFS];
+    synim::Geo geo{};
+    std::vector<void *> dev_allocs;
+    std::vector<void *> host_allocs;
+    synim::DevPair *d_pairs = nullptr;
+    synim::DevPair *h_pairs[synim::NSLOT] = {};
+    cudaEvent_t slot_ev[synim::NSLOT] = {};
+    bool slot_used[synim::NSLOT] = {};
+    int slot = 0;
+    int *d_counter = nullptr, *d_err = nullptr, *h_err = nullptr;
+    double *d_gp = nullptr;
+    long long pst_off[SYNIM_MAX_PAIRS] = {};
+    long long line_off[SYNIM_MAX_PAIRS] = {};
+    uint8_t *d_pst = nullptr, *d_lines = nullptr;
+    int max_mm = 0, max_lines = 0;
+    int threads = 512, ctas_per_sm = 0;
+    bool use_graph = true;
+    int arena_floats = 0;
+    std::map<std::tuple<int, size_t, int, int>, synim::GraphEntry> graphs;
+    cudaStream_t cap = nullptr;
+    bool profile = false;
+    cudaEvent_t prof_a[synim::NPROF] = {}, prof_b[synim::NPROF] = {};
+    unsigned long long prof_head = 0, prof_tail = 0;
+    double prof_acc_ms = 0.0;
+    int prof_acc_n = 0;
+    std::string err;
+    // host copies of each sensor's pupil and valid-row index (probe responses)
+    std::vector<uint8_t> pupil[SYNIM_MAX_WFS];
+    std::vector<int> vidx_h[SYNIM_MAX_WFS];
+    synim::ProbeSet *probe = nullptr;
+    synim::EstState *est = nullptr;
+};

@@ -177,6 +177,77 @@ class SynIM:
                   self._ctx)
         return np.array(gp[:]).reshape(np_, 4)
 
+    # ---- probe responses (input of the misregistration estimators) ----
+    def probe_attach(self, d: int, w: int, cmd):
+        """Attach probe commands cmd [n_modes, n_act] (float64) to pair (d, w)."""
+        c = np.ascontiguousarray(cmd, dtype=np.float64)
+        abi.check(self._L.synim_probe_attach(self._ctx, d, w, c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                             c.shape[0]), self._ctx)
+        n_sub, C = ctypes.c_int32(), ctypes.c_int32()
+        abi.check(self._L.synim_probe_query(self._ctx, ctypes.byref(n_sub), ctypes.byref(C), None), self._ctx)
+        self.probe_shape = (int(n_sub.value), int(n_sub.value), int(C.value))
+        valid = np.zeros((n_sub.value, n_sub.value), np.uint8)
+        abi.check(self._L.synim_probe_query(self._ctx, None, None, valid.ctypes.data), self._ctx)
+        self.probe_valid = valid.astype(bool)
+
+    @staticmethod
+    def _params(params, device):
+        t = torch.as_tensor(params, dtype=torch.float64)
+        return t.to(device).contiguous().reshape(-1, 4)
+
+    def probe_response(self, params, tangents: bool = False, stream=None):
+        """Clean slope maps [n, n_sub, n_sub, C] (and tangents [4, n, ...]) for params [n, 4]."""
+        p = self._params(params, self.device)
+        n = p.shape[0]
+        maps = torch.empty((n, *self.probe_shape), dtype=torch.float32, device=self.device)
+        dmaps = torch.empty((4, n, *self.probe_shape), dtype=torch.float32, device=self.device) if tangents else None
+        abi.check(self._L.synim_probe_response(self._ctx, ctypes.c_void_p(p.data_ptr()), n,
+                                               ctypes.c_void_p(maps.data_ptr()),
+                                               None if dmaps is None else ctypes.c_void_p(dmaps.data_ptr()),
+                                               self._stream(stream)), self._ctx)
+        return (maps, dmaps) if tangents else maps
+
+    def probe_generate(self, params, seed: int, sample0: int = 0, noise_rel: float = 0.01, out=None,
+                       stream=None):
+        """Noisy bfloat16 probe inputs [n, n_sub, n_sub, C] for params [n, 4]."""
+        p = self._params(params, self.device)
+        n = p.shape[0]
+        if out is None:
+            out = torch.empty((n, *self.probe_shape), dtype=torch.bfloat16, device=self.device)
+        abi.check(self._L.synim_probe_generate(self._ctx, ctypes.c_void_p(p.data_ptr()), n, seed, sample0,
+                                               float(noise_rel), ctypes.c_void_p(out.data_ptr()),
+                                               self._stream(stream)), self._ctx)
+        return out
+
+    # ---- misregistration estimators ----
+    METHODS = {"gn": 0, "cnn": 1, "cnn+gn": 2}
+
+    def gn_config(self, max_iter: int = 30, tol: float = 1e-4, scale=None):
+        sc = None if scale is None else (ctypes.c_double * 4)(*[float(v) for v in scale])
+        abi.check(self._L.synim_gn_config(self._ctx, int(max_iter), float(tol), sc), self._ctx)
+
+    def estimate(self, slopes, method: str = "gn", init=None, stream=None):
+        """Estimate the probed pair's misregistration from slope maps [n, n_sub, n_sub, C].
+
+        Returns (params [n, 4] float64, relative residual [n], iterations [n], converged [n]).
+        """
+        y = torch.as_tensor(slopes).to(self.device, torch.float32).contiguous()
+        n = y.shape[0]
+        arr = (abi.synim_misreg * n)()
+        # default start: the prior centre nudged off the exact grid alignment
+        init = (np.tile([1e-3, 1e-3, 1e-3, 1.0 + 1e-5], (n, 1)) if init is None
+                else np.asarray(init, np.float64).reshape(n, 4))
+        for q in range(n):
+            arr[q] = abi.synim_misreg(*[float(v) for v in init[q]])
+        res = (ctypes.c_double * max(n, 1))()
+        abi.check(self._L.synim_misreg_estimate(self._ctx, ctypes.c_void_p(y.data_ptr()), n,
+                                                self.METHODS[method], arr, res, self._stream(stream)), self._ctx)
+        it = (ctypes.c_int32 * max(n, 1))()
+        cv = (ctypes.c_int32 * max(n, 1))()
+        abi.check(self._L.synim_misreg_estimate_stats(self._ctx, it, cv), self._ctx)
+        p = np.array([[a.shift_x_px, a.shift_y_px, a.rot_deg, a.mag] for a in arr]).reshape(n, 4)
+        return p, np.array(res[:n]), np.array(it[:n]), np.array(cv[:n], bool)
+
 
 class IMFunction(torch.autograd.Function):
     """IMs as a differentiable function of the misregistrations.

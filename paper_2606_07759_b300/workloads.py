@@ -251,16 +251,24 @@ def modal_screens(dm: DM, cmd: np.ndarray) -> np.ndarray:
 
 
 def learned(seed: int = 5):
-    """40x40 SH (k = 8, M = 320, no obstruction), 41x41 DM (p = 8 px, N = 320), 16 probes."""
-    D, N, n_side = 8.0, 320, 41
-    dd = D / N
-    mask = disc_mask(N, N / 2.0)
+    """40x40 SH (k = 8, M = 320, no obstruction), 41x41 DM (p = 8 px), 16 probes.
+
+    The DM grid is N = 352 px (the 320 px pupil plus two pitches on each side)
+    with no DM mask, so that a sensor misregistered by up to one subaperture
+    and 2 % still sees only the DM's active area: a mask edge inside the
+    pupil would make the probe responses jump with the misregistration
+    (pixels entering and leaving the edge-repair ring) and no local fit
+    could follow them.
+    """
+    D, M, n_side = 8.0, 320, 41
+    dd = D / M
+    N = M + 32
     xy, r, pitch_m = actuator_lattice(n_side, D, N, dd)
     keep = r <= D / 2.0 + pitch_m + 1e-9
     xy = xy[keep]
     pitch_px = pitch_m / dd
-    dm = DM(gaussian_cube(xy, coupling_sigma(pitch_px), N, mask), mask, dd, 0.0, xy, pitch_px)
-    wfs = WFS(40, 320, D, 0.0, (0.0, 0.0), disc_mask(320, 160.0), obstruction=0.0)
+    dm = DM(gaussian_cube(xy, coupling_sigma(pitch_px), N, None), None, dd, 0.0, xy, pitch_px)
+    wfs = WFS(40, M, D, 0.0, (0.0, 0.0), disc_mask(M, M / 2.0), obstruction=0.0)
     cmd = probe_modes(dm, D, 16)
     return Workload("learned", [dm], [wfs], [Misreg()]), cmd
 

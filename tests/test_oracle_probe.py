@@ -19,6 +19,7 @@ from paper_2606_07759_b300 import workloads as W
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 MIS = [(0.3, -0.2, 0.5, 1.01), (-0.7, 0.45, -1.3, 0.985)]
+P0 = (1e-3, 1e-3, 1e-3, 1.0 + 1e-5)   # fit start: prior centre, off the exact grid alignment
 
 
 def _scao_with_probes():
@@ -136,3 +137,34 @@ def test_noisy_maps():
     sigma = 0.05 * np.abs(clean).max()
     z = (noisy[valid] - clean[valid]) / sigma
     assert abs(z.std() - 1.0) < 0.05 and abs(z.mean()) < 0.05
+
+
+def test_gn_fit_recovers_noise_free_truth():
+    # zero residual at the truth: the fit must land on it (the minimum is exact).
+    # The start is the prior centre nudged off the exact grid alignment: at
+    # the identity with N = M every sample sits on a bilinear cell line, where
+    # the floor-cell Jacobian is one-sided.
+    wl, dm, wfs, cmd = _scao_with_probes()
+    screens = oracle.probe_screens(dm, cmd)
+    truth = np.array([0.6, -0.4, 0.8, 1.012])
+    y = oracle.probe_maps(screens, dm, wfs, truth)
+    p, res, it, conv = oracle.gn_fit(screens, dm, wfs, y, P0, tol=1e-7)
+    assert conv and it <= 20
+    assert np.all(np.abs(p - truth) / np.array([8, 8, 2, 0.02]) < 1e-10), p - truth
+    assert res < 1e-9
+
+
+def test_gn_fit_is_a_minimiser_under_noise():
+    wl, dm, wfs, cmd = _scao_with_probes()
+    screens = oracle.probe_screens(dm, cmd)
+    truth = np.array([-0.3, 0.5, -0.6, 0.991])
+    clean = oracle.probe_maps(screens, dm, wfs, truth)
+    ros, _, _ = oracle.valid_subaps(wfs.pupil_mask, wfs.n_sub)
+    y = oracle.noisy_maps(clean, ros >= 0, 9, 0, 0.01).astype(np.float64)
+    p, res, it, conv = oracle.gn_fit(screens, dm, wfs, y, P0, max_iter=50)
+    assert conv
+    r_truth = np.linalg.norm(y - clean) / np.linalg.norm(y)
+    assert res <= r_truth * (1 + 1e-12)
+    # and the fit sits near the truth (noise of 1% of the peak; a 10x10
+    # sensor constrains rotation and magnification only loosely)
+    assert np.all(np.abs(p - truth) / np.array([8, 8, 2, 0.02]) < 0.1)
