@@ -56,3 +56,45 @@ def loss_grad(params, x, target, n_channels: int):
     loss = ((out - torch.as_tensor(np.asarray(target, np.float64))) ** 2).mean()
     loss.backward()
     return float(loss.detach()), pack([v.grad for v in t])
+
+
+def _bf16(t):
+    """Round a float64 tensor to the nearest bfloat16 (ties to even), via float32."""
+    f = t.to(torch.float32).contiguous()
+    u = f.view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    u = torch.where(u >= 2 ** 31, u - 2 ** 32, u).to(torch.int32)
+    return u.view(torch.float32).to(torch.float64)
+
+
+def loss_grad_rounded(params, x, target, n_channels: int, rounded: bool = True):
+    """Loss and gradient with the backward pass written out layer by layer and,
+    when `rounded`, every stored activation (a1, a2, a3) and activation
+    gradient (dz3, dz2, dz1) rounded to bfloat16: the precision model of a
+    BF16 training step, all arithmetic in between in float64.  With
+    rounded=False this is the exact gradient (a test checks it against
+    loss_grad)."""
+    R = _bf16 if rounded else (lambda v: v)
+    W1, b1, W2, b2, W3, b3, Wfc, bfc = unpack(params, n_channels)
+    x = torch.as_tensor(np.asarray(x, np.float64))
+    t = torch.as_tensor(np.asarray(target, np.float64))
+    h = x.permute(0, 3, 1, 2)
+    Wc = [w.permute(0, 3, 1, 2) for w in (W1, W2, W3)]
+    a1 = R(F.relu(F.conv2d(h, Wc[0], b1, stride=1, padding=1)))
+    a2 = R(F.relu(F.conv2d(a1, Wc[1], b2, stride=2, padding=1)))
+    a3 = R(F.relu(F.conv2d(a2, Wc[2], b3, stride=2, padding=1)))
+    g = a3.mean(dim=(2, 3))
+    out = g @ Wfc.T + bfc
+    B = x.shape[0]
+    dout = 2.0 * (out - t) / (4.0 * B)
+    dWfc, dbfc = dout.T @ g, dout.sum(0)
+    P3 = a3.shape[2] * a3.shape[3]
+    dz3 = R((dout @ Wfc)[:, :, None, None].expand_as(a3) / P3 * (a3 > 0))
+    dW3 = torch.nn.grad.conv2d_weight(a2, Wc[2].shape, dz3, stride=2, padding=1)
+    dz2 = R(torch.nn.grad.conv2d_input(a2.shape, Wc[2], dz3, stride=2, padding=1) * (a2 > 0))
+    dW2 = torch.nn.grad.conv2d_weight(a1, Wc[1].shape, dz2, stride=2, padding=1)
+    dz1 = R(torch.nn.grad.conv2d_input(a1.shape, Wc[1], dz2, stride=2, padding=1) * (a1 > 0))
+    dW1 = torch.nn.grad.conv2d_weight(h, Wc[0].shape, dz1, stride=1, padding=1)
+    grads = [dW1.permute(0, 2, 3, 1), dz1.sum((0, 2, 3)), dW2.permute(0, 2, 3, 1), dz2.sum((0, 2, 3)),
+             dW3.permute(0, 2, 3, 1), dz3.sum((0, 2, 3)), dWfc, dbfc]
+    return float(((out - t) ** 2).mean()), pack(grads)

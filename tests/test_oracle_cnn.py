@@ -68,3 +68,21 @@ def test_gradient_matches_central_differences():
         e[i] = h
         fd = (oc.loss_grad(p + e, x, tgt, 32)[0] - oc.loss_grad(p - e, x, tgt, 32)[0]) / (2 * h)
         assert abs(fd - g[i]) <= 1e-6 * max(abs(g[i]), 1e-3), (i, fd, g[i])
+
+
+def test_written_out_backward_equals_autograd():
+    rng = np.random.default_rng(7)
+    p = cnn_init_params(32, seed=8).astype(np.float64) + rng.normal(0, 0.02, 92612)
+    x = rng.standard_normal((3, 8, 8, 32))
+    tgt = rng.uniform(-1, 1, (3, 4))
+    l0, g0 = oc.loss_grad(p, x, tgt, 32)
+    l1, g1 = oc.loss_grad_rounded(p, x, tgt, 32, rounded=False)
+    assert abs(l0 - l1) <= 1e-14 * l0
+    np.testing.assert_allclose(g1, g0, rtol=0, atol=1e-12 * np.abs(g0).max())
+
+
+def test_bf16_rounding_helper_matches_torch():
+    import torch
+    from oracle.cnn import _bf16
+    v = torch.as_tensor(np.random.default_rng(0).standard_normal(5000) * 1e3)
+    np.testing.assert_array_equal(_bf16(v).numpy(), v.to(torch.bfloat16).to(torch.float64).numpy())
