@@ -1,11 +1,12 @@
 """FP64 CPU oracle of the learned estimator's network (test infrastructure).
 
 The network (conv 3x3 stride 1 C->64, conv 3x3 stride 2 64->64, conv 3x3
-stride 2 64->64, each with bias and ReLU; global average pooling; dense
-64->4; mean squared error) written with PyTorch CPU operators in float64,
+stride 2 64->64, each with bias and ReLU; dense layer from the flattened
+last feature map (H3 x H3 x 64, NHWC order) to 4 outputs; mean squared
+error) written with PyTorch CPU operators in float64,
 the gradient by PyTorch's automatic differentiation.  Parameters come as the
 flat FP32 vector of the library (W[co][ky][kx][ci] per layer, then biases;
-Wfc[j][c]); inputs are NHWC.  Tests pin the convolution layout against an
+Wfc[j][y][x][c]); inputs are NHWC.  Tests pin the convolution layout against an
 explicit sum and the gradient against central differences.
 """
 from __future__ import annotations
@@ -15,9 +16,16 @@ import torch
 import torch.nn.functional as F
 
 
-def unpack(params, n_channels: int):
+def feature_side(h0: int) -> int:
+    """Side of the last feature map: two stride-2 convolutions of an h0 map."""
+    h = (h0 - 1) // 2 + 1
+    return (h - 1) // 2 + 1
+
+
+def unpack(params, n_channels: int, h0: int = 40):
     p = torch.as_tensor(np.asarray(params, np.float64))
-    shapes = [(64, 3, 3, n_channels), (64,), (64, 3, 3, 64), (64,), (64, 3, 3, 64), (64,), (4, 64), (4,)]
+    h3 = feature_side(h0)
+    shapes = [(64, 3, 3, n_channels), (64,), (64, 3, 3, 64), (64,), (64, 3, 3, 64), (64,), (4, h3, h3, 64), (4,)]
     out, o = [], 0
     for s in shapes:
         n = int(np.prod(s))
@@ -32,26 +40,27 @@ def pack(tensors) -> np.ndarray:
 
 
 def layers(tensors, x):
-    """Activations (a1, a2, a3 NHWC, pooled g, output) of float64 input x [B, H, H, C]."""
+    """Activations (a1, a2, a3 NHWC, flattened features g, output) of float64 input x [B, H, H, C]."""
     W1, b1, W2, b2, W3, b3, Wfc, bfc = tensors
     h = x.permute(0, 3, 1, 2)
     a1 = F.relu(F.conv2d(h, W1.permute(0, 3, 1, 2), b1, stride=1, padding=1))
     a2 = F.relu(F.conv2d(a1, W2.permute(0, 3, 1, 2), b2, stride=2, padding=1))
     a3 = F.relu(F.conv2d(a2, W3.permute(0, 3, 1, 2), b3, stride=2, padding=1))
-    g = a3.mean(dim=(2, 3))
-    out = g @ Wfc.T + bfc
-    return a1.permute(0, 2, 3, 1), a2.permute(0, 2, 3, 1), a3.permute(0, 2, 3, 1), g, out
+    a3h = a3.permute(0, 2, 3, 1)
+    g = a3h.reshape(a3h.shape[0], -1)
+    out = g @ Wfc.reshape(4, -1).T + bfc
+    return a1.permute(0, 2, 3, 1), a2.permute(0, 2, 3, 1), a3h, g, out
 
 
 def forward(params, x, n_channels: int) -> np.ndarray:
-    t = unpack(params, n_channels)
+    t = unpack(params, n_channels, np.shape(x)[1])
     with torch.no_grad():
         return layers(t, torch.as_tensor(np.asarray(x, np.float64)))[-1].numpy()
 
 
 def loss_grad(params, x, target, n_channels: int):
     """(mean squared error over the B x 4 outputs, gradient as a flat float64 vector)."""
-    t = [v.clone().requires_grad_(True) for v in unpack(params, n_channels)]
+    t = [v.clone().requires_grad_(True) for v in unpack(params, n_channels, np.shape(x)[1])]
     out = layers(t, torch.as_tensor(np.asarray(x, np.float64)))[-1]
     loss = ((out - torch.as_tensor(np.asarray(target, np.float64))) ** 2).mean()
     loss.backward()
@@ -75,7 +84,7 @@ def loss_grad_rounded(params, x, target, n_channels: int, rounded: bool = True):
     rounded=False this is the exact gradient (a test checks it against
     loss_grad)."""
     R = _bf16 if rounded else (lambda v: v)
-    W1, b1, W2, b2, W3, b3, Wfc, bfc = unpack(params, n_channels)
+    W1, b1, W2, b2, W3, b3, Wfc, bfc = unpack(params, n_channels, np.shape(x)[1])
     x = torch.as_tensor(np.asarray(x, np.float64))
     t = torch.as_tensor(np.asarray(target, np.float64))
     h = x.permute(0, 3, 1, 2)
@@ -83,13 +92,14 @@ def loss_grad_rounded(params, x, target, n_channels: int, rounded: bool = True):
     a1 = R(F.relu(F.conv2d(h, Wc[0], b1, stride=1, padding=1)))
     a2 = R(F.relu(F.conv2d(a1, Wc[1], b2, stride=2, padding=1)))
     a3 = R(F.relu(F.conv2d(a2, Wc[2], b3, stride=2, padding=1)))
-    g = a3.mean(dim=(2, 3))
-    out = g @ Wfc.T + bfc
+    a3h = a3.permute(0, 2, 3, 1)
+    g = a3h.reshape(a3h.shape[0], -1)
+    Wf = Wfc.reshape(4, -1)
+    out = g @ Wf.T + bfc
     B = x.shape[0]
     dout = 2.0 * (out - t) / (4.0 * B)
-    dWfc, dbfc = dout.T @ g, dout.sum(0)
-    P3 = a3.shape[2] * a3.shape[3]
-    dz3 = R((dout @ Wfc)[:, :, None, None].expand_as(a3) / P3 * (a3 > 0))
+    dWfc, dbfc = (dout.T @ g).reshape(Wfc.shape), dout.sum(0)
+    dz3 = R((dout @ Wf).reshape(a3h.shape).permute(0, 3, 1, 2) * (a3 > 0))
     dW3 = torch.nn.grad.conv2d_weight(a2, Wc[2].shape, dz3, stride=2, padding=1)
     dz2 = R(torch.nn.grad.conv2d_input(a2.shape, Wc[2], dz3, stride=2, padding=1) * (a2 > 0))
     dW2 = torch.nn.grad.conv2d_weight(a1, Wc[1].shape, dz2, stride=2, padding=1)

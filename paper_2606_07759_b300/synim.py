@@ -248,6 +248,72 @@ class SynIM:
         p = np.array([[a.shift_x_px, a.shift_y_px, a.rot_deg, a.mag] for a in arr]).reshape(n, 4)
         return p, np.array(res[:n]), np.array(it[:n]), np.array(cv[:n], bool)
 
+    # ---- the learned estimator ----
+    def cnn_n_params(self) -> int:
+        return int(self._L.synim_cnn_n_params(self.probe_shape[2]))
+
+    def cnn_init(self, params, center, range_):
+        """Create the network with initial parameters (float32 [n_params]) and the
+        output normalisation (p - center) / range."""
+        w = np.ascontiguousarray(params, np.float32)
+        norm = np.ascontiguousarray(list(center) + list(range_), np.float64)
+        abi.check(self._L.synim_cnn_init(self._ctx, w.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                         norm.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), self._ctx)
+
+    def cnn_get(self):
+        w = np.zeros(self.cnn_n_params(), np.float32)
+        norm = np.zeros(8)
+        abi.check(self._L.synim_cnn_get(self._ctx, w.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                        norm.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), self._ctx)
+        return w, norm[:4], norm[4:]
+
+    def cnn_forward(self, x, stream=None):
+        """Normalised outputs [n, 4] for bfloat16 maps x [n, n_sub, n_sub, C]."""
+        x = x.to(self.device, torch.bfloat16).contiguous()
+        out = torch.empty((x.shape[0], 4), dtype=torch.float32, device=self.device)
+        abi.check(self._L.synim_cnn_forward(self._ctx, ctypes.c_void_p(x.data_ptr()), x.shape[0],
+                                            ctypes.c_void_p(out.data_ptr()), self._stream(stream)), self._ctx)
+        return out
+
+    def cnn_grad(self, x, target, stream=None):
+        """(loss, gradient [n_params]) of one forward/backward pass without an update."""
+        x = x.to(self.device, torch.bfloat16).contiguous()
+        t = torch.as_tensor(target, dtype=torch.float32).to(self.device).contiguous()
+        loss = ctypes.c_double()
+        g = np.zeros(self.cnn_n_params(), np.float32)
+        abi.check(self._L.synim_cnn_grad(self._ctx, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                                         x.shape[0], ctypes.byref(loss),
+                                         g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), self._stream(stream)),
+                  self._ctx)
+        return float(loss.value), g
+
+    def cnn_train(self, params, epochs: int = 10, batch: int = 256, lr: float = 1e-3, lr_final: float = 0.0,
+                  noise_rel: float = 0.01, seed: int = 0, sample0: int = 0, stream=None):
+        """Train on samples with misregistrations params [n, 4]; returns the per-epoch loss."""
+        p = self._params(params, self.device)
+        o = abi.synim_train_opts(int(epochs), int(batch), float(lr), float(lr_final), 0.0, 0.0, 0.0,
+                                 float(noise_rel), int(seed), int(sample0))
+        loss = (ctypes.c_double * int(epochs))()
+        abi.check(self._L.synim_cnn_train(self._ctx, ctypes.c_void_p(p.data_ptr()), p.shape[0], ctypes.byref(o),
+                                          loss, self._stream(stream)), self._ctx)
+        return np.array(loss[:])
+
+
+def cnn_init_params(n_channels: int, seed: int = 0, input_scale: float = 1.0, side: int = 40) -> np.ndarray:
+    """He-uniform initial parameters of the estimator network (seeded) for side x side
+    maps, the first layer scaled by input_scale (1 / typical input magnitude), the
+    dense layer Glorot-uniform; biases zero."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for cin, fan, sc in ((n_channels, 9 * n_channels, input_scale), (64, 576, 1.0), (64, 576, 1.0)):
+        lim = np.sqrt(6.0 / fan) * sc
+        out += [rng.uniform(-lim, lim, 64 * 9 * cin), np.zeros(64)]
+    h3 = ((side - 1) // 2) // 2 + 1
+    nf = h3 * h3 * 64
+    lim = np.sqrt(6.0 / (nf + 4))
+    out += [rng.uniform(-lim, lim, 4 * nf), np.zeros(4)]
+    return np.concatenate(out).astype(np.float32)
+
 
 class IMFunction(torch.autograd.Function):
     """IMs as a differentiable function of the misregistrations.

@@ -26,10 +26,10 @@ def _explicit_conv(x, W, b, stride):
 
 def test_convolution_layout_matches_explicit_sum():
     rng = np.random.default_rng(0)
-    p = cnn_init_params(32, seed=1).astype(np.float64)
+    p = cnn_init_params(32, seed=1, side=5).astype(np.float64)
     p += rng.normal(0, 0.01, p.shape)        # non-zero biases too
     x = rng.standard_normal((2, 5, 5, 32))
-    t = oc.unpack(p, 32)
+    t = oc.unpack(p, 32, 5)
     import torch
     a1, a2, a3, g, out = [v.numpy() for v in oc.layers(t, torch.as_tensor(x))]
     W1, b1, W2, b2, W3, b3, Wfc, bfc = [v.numpy() for v in t]
@@ -40,20 +40,20 @@ def test_convolution_layout_matches_explicit_sum():
     np.testing.assert_allclose(a2, e2, rtol=0, atol=1e-12)
     np.testing.assert_allclose(a3, e3, rtol=0, atol=1e-12)
     assert a2.shape[1] == 3 and a3.shape[1] == 2
-    np.testing.assert_allclose(out, e3.mean(axis=(1, 2)) @ Wfc.T + bfc, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(out, e3.reshape(2, -1) @ Wfc.reshape(4, -1).T + bfc, rtol=0, atol=1e-12)
 
 
 def test_output_sizes_of_the_learned_geometry():
     import torch
     p = cnn_init_params(32)
-    a1, a2, a3, g, out = oc.layers(oc.unpack(p, 32), torch.zeros((1, 40, 40, 32), dtype=torch.float64))
+    a1, a2, a3, g, out = oc.layers(oc.unpack(p, 32, 40), torch.zeros((1, 40, 40, 32), dtype=torch.float64))
     assert a1.shape == (1, 40, 40, 64) and a2.shape == (1, 20, 20, 64) and a3.shape == (1, 10, 10, 64)
     assert out.shape == (1, 4)
 
 
 def test_gradient_matches_central_differences():
     rng = np.random.default_rng(2)
-    p = cnn_init_params(32, seed=3).astype(np.float64)
+    p = cnn_init_params(32, seed=3, side=6).astype(np.float64)
     p += rng.normal(0, 0.02, p.shape)
     x = rng.standard_normal((2, 6, 6, 32))
     tgt = rng.uniform(-1, 1, (2, 4))
@@ -61,7 +61,7 @@ def test_gradient_matches_central_differences():
     n1 = 64 * 9 * 32
     # entries of every tensor: W1, b1, W2, b2, W3, b3, Wfc, bfc
     idx = [5, 1000, n1 + 3, n1 + 64 + 77, n1 + 64 + 36864 + 10, n1 + 64 + 36864 + 64 + 999,
-           n1 + 2 * (64 + 36864) + 5, len(p) - 256 - 4 + 17, len(p) - 2]
+           n1 + 2 * (64 + 36864) + 5, len(p) - 4 * 2 * 2 * 64 - 4 + 17, len(p) - 2]
     h = 1e-6
     for i in idx:
         e = np.zeros_like(p)
@@ -72,7 +72,8 @@ def test_gradient_matches_central_differences():
 
 def test_written_out_backward_equals_autograd():
     rng = np.random.default_rng(7)
-    p = cnn_init_params(32, seed=8).astype(np.float64) + rng.normal(0, 0.02, 92612)
+    p = cnn_init_params(32, seed=8, side=8).astype(np.float64)
+    p += rng.normal(0, 0.02, p.shape)
     x = rng.standard_normal((3, 8, 8, 32))
     tgt = rng.uniform(-1, 1, (3, 4))
     l0, g0 = oc.loss_grad(p, x, tgt, 32)
