@@ -277,6 +277,58 @@ synim_status synim_gn_config(synim_ctx *ctx, int32_t max_iter, double tol, const
  * sample of the last synim_misreg_estimate; host [n] each, either may be NULL. */
 synim_status synim_misreg_estimate_stats(const synim_ctx *ctx, int32_t *iters, int32_t *converged);
 
+/* ------------------------------------------------------------------------
+ * The learned estimator: a small BF16 convolutional network (tensor cores,
+ * FP32 accumulation) on the probe slope maps, trained on the GPU on probe
+ * responses the library generates.  Layers: conv 3x3 stride 1 (C -> 64),
+ * conv 3x3 stride 2 (64 -> 64), conv 3x3 stride 2 (64 -> 64), each with
+ * bias and ReLU, then a dense layer from the flattened H3 x H3 x 64 map
+ * (H3 = side after the two stride-2 layers, 10 for 40x40 maps) to 4 outputs.  Output: the
+ * misregistration normalised as (p - center) / range per component.
+ * Parameters (FP32, this order): W1 [64][3][3][C], b1 [64], W2 [64][3][3][64],
+ * b2, W3 [64][3][3][64], b3, Wfc [4][H3][H3][64], bfc [4]; C = 2 n_modes must be a
+ * multiple of 32.
+ * ---------------------------------------------------------------------- */
+
+/* Number of parameters for n_sub x n_sub maps with n_channels channels. */
+int32_t synim_cnn_n_params(int32_t n_sub, int32_t n_channels);
+
+/* Create the network of the attached probes with initial parameters (host
+ * [n_params]) and normalisation norm = {center[4], range[4]} (host). */
+synim_status synim_cnn_init(synim_ctx *ctx, const float *params, const double *norm);
+
+/* Copy the current parameters (host [n_params]) and normalisation (host [8]); either may be NULL. */
+synim_status synim_cnn_get(const synim_ctx *ctx, float *params, double *norm);
+
+/* Normalised outputs (device [n][4] FP32) for bfloat16 maps x (device [n][n_sub][n_sub][C]). */
+synim_status synim_cnn_forward(synim_ctx *ctx, const uint16_t *x, int64_t n, float *out, void *cuda_stream);
+
+/* One forward and backward pass without an update, 1 <= n <= 256: loss_out
+ * (host, may be NULL) = mean squared error over the n x 4 outputs against
+ * target (device [n][4], normalised); grad_out (host [n_params], may be
+ * NULL) = its gradient.  Synchronous. */
+synim_status synim_cnn_grad(synim_ctx *ctx, const uint16_t *x, const float *target, int64_t n,
+                            double *loss_out, float *grad_out, void *cuda_stream);
+
+typedef struct {
+    int32_t epochs, batch;   /* batch <= 256 */
+    float lr, lr_final;      /* Adam step, decayed geometrically to lr_final (0 = constant) */
+    float beta1, beta2, eps; /* 0 = defaults 0.9, 0.999, 1e-8 */
+    float noise_rel;         /* probe noise, as synim_probe_generate */
+    uint64_t seed, sample0;  /* noise stream and shuffling seed, first sample index */
+} synim_train_opts;
+
+/* Train on n samples with misregistrations params (device [n][4]): the
+ * library generates one noisy bfloat16 probe response per sample
+ * (synim_probe_generate), then runs opts->epochs epochs of shuffled
+ * minibatches (std::mt19937_64 permutation seeded from opts->seed) with Adam
+ * on the mean squared error of the normalised outputs.  loss_out (host
+ * [epochs], may be NULL): the loss of the last batch of each epoch.  Keeps
+ * the generated inputs (n x n_sub^2 x C x 2 bytes of device memory).
+ * Synchronous. */
+synim_status synim_cnn_train(synim_ctx *ctx, const double *params, int64_t n, const synim_train_opts *opts,
+                             double *loss_out, void *cuda_stream);
+
 /* Free all device memory of the context (waits for its streams). NULL is a no-op. */
 void synim_im_destroy(synim_ctx *ctx);
 

@@ -43,6 +43,12 @@ class synim_opts(ctypes.Structure):
                 ("autotune", c_int32), ("profile", c_int32)]
 
 
+class synim_train_opts(ctypes.Structure):
+    _fields_ = [("epochs", c_int32), ("batch", c_int32), ("lr", c_float), ("lr_final", c_float),
+                ("beta1", c_float), ("beta2", c_float), ("eps", c_float), ("noise_rel", c_float),
+                ("seed", ctypes.c_uint64), ("sample0", ctypes.c_uint64)]
+
+
 # name -> (restype, argtypes); mirrors include/synim.h
 SIGNATURES = {
     "synim_im_create": (c_int32, [ctypes.POINTER(synim_dm_desc), c_int32, ctypes.POINTER(synim_wfs_desc),
@@ -72,6 +78,14 @@ SIGNATURES = {
                                         ctypes.POINTER(c_double), c_void_p]),
     "synim_gn_config": (c_int32, [c_void_p, c_int32, c_double, ctypes.POINTER(c_double)]),
     "synim_misreg_estimate_stats": (c_int32, [c_void_p, ctypes.POINTER(c_int32), ctypes.POINTER(c_int32)]),
+    "synim_cnn_n_params": (c_int32, [c_int32, c_int32]),
+    "synim_cnn_init": (c_int32, [c_void_p, ctypes.POINTER(c_float), ctypes.POINTER(c_double)]),
+    "synim_cnn_get": (c_int32, [c_void_p, ctypes.POINTER(c_float), ctypes.POINTER(c_double)]),
+    "synim_cnn_forward": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
+    "synim_cnn_grad": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, ctypes.POINTER(c_double),
+                                 ctypes.POINTER(c_float), c_void_p]),
+    "synim_cnn_train": (c_int32, [c_void_p, c_void_p, c_int64, ctypes.POINTER(synim_train_opts),
+                                  ctypes.POINTER(c_double), c_void_p]),
     "synim_im_destroy": (None, [c_void_p]),
     "synim_status_string": (ctypes.c_char_p, [c_int32]),
     "synim_last_error": (ctypes.c_char_p, [c_void_p]),

@@ -317,6 +317,7 @@ void synim_im_destroy(synim_ctx *ctx) {
     for (int s = 0; s < NSLOT; ++s)
         if (ctx->slot_ev[s]) cudaEventDestroy(ctx->slot_ev[s]);
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
+    cnn_destroy(ctx->cnn);
     est_destroy(ctx->est);
     probe_destroy(ctx->probe);
     for (void *p : ctx->dev_allocs) cudaFree(p);

@@ -127,6 +127,8 @@ cudaError_t probe_launch(synim_ctx *c, const double *params, long long n, float 
 int probe_per_sample(const ProbeSet *p);   // n_sub^2 x channels
 struct EstState;   // synim_estimate.cu
 void est_destroy(EstState *e);
+struct CnnState;   // synim_cnn.cu
+void cnn_destroy(CnnState *s);
 
 constexpr int NSLOT = 4;
 constexpr int NPROF = 256;
@@ -175,4 +177,5 @@ struct synim_ctx {
     std::vector<int> vidx_h[SYNIM_MAX_WFS];
     synim::ProbeSet *probe = nullptr;
     synim::EstState *est = nullptr;
+    synim::CnnState *cnn = nullptr;
 };

@@ -250,7 +250,7 @@ class SynIM:
 
     # ---- the learned estimator ----
     def cnn_n_params(self) -> int:
-        return int(self._L.synim_cnn_n_params(self.probe_shape[2]))
+        return int(self._L.synim_cnn_n_params(self.probe_shape[0], self.probe_shape[2]))
 
     def cnn_init(self, params, center, range_):
         """Create the network with initial parameters (float32 [n_params]) and the
