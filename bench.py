@@ -146,7 +146,7 @@ def cpu_oracle_sample(wl, seconds: float, seed: int = 0):
 
 
 def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
+    _, rank, _ = rank_env()
     if rank != 0:
         return 0
     wl = make_workload(args.workload)
@@ -174,14 +174,110 @@ def run_reference(args):
     return 0
 
 
+def rank_env():
+    """(world, rank, local rank) from the torchrun environment (1, 0, 0 without it)."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(x: float, world: int, device="cuda") -> float:
+    """The largest x over all ranks (the job's time is its slowest rank's)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank: float, seconds_max: float, world: int) -> float:
+    """Whole-job throughput of independent replicas: every rank processes
+    units_per_rank, the job ends with its slowest rank."""
+    return world * units_per_rank / seconds_max
+
+
+def learned_flops_per_sample(h0: int = 40, c0: int = 32):
+    """(forward, training-step) FLOPs of the estimator network per sample."""
+    h1 = h0
+    h2 = (h1 - 1) // 2 + 1
+    h3 = (h2 - 1) // 2 + 1
+    l1 = 2 * h1 * h1 * 64 * 9 * c0
+    l2 = 2 * h2 * h2 * 64 * 9 * 64
+    l3 = 2 * h3 * h3 * 64 * 9 * 64
+    head = 2 * h3 * h3 * 64 * 4
+    fwd = l1 + l2 + l3 + head
+    # backward: weight gradients of all layers, input gradients of layers 2-3 and the head
+    bwd = (l1 + l2 + l3 + head) + (l2 + l3 + head)
+    return fwd, fwd + bwd
+
+
+def run_learned(args):
+    """Training throughput, accuracy and batch-1 latency of the misregistration estimators."""
+    import torch
+    from paper_2606_07759_b300.synim import SynIM, cnn_init_params
+    wl, cmd = W.learned()
+    s = SynIM(wl.dms, wl.wfss)
+    s.probe_attach(0, 0, cmd)
+    center, rng_ = (0.0, 0.0, 0.0, 1.0), (8.0, 8.0, 2.0, 0.02)
+    rng = np.random.default_rng(5)
+    ptr = W.random_misregs(rng, args.learned_train, 8.0, 2.0, 0.02)
+    # probe generation alone
+    gen = torch.empty((args.learned_train, *s.probe_shape), dtype=torch.bfloat16, device="cuda")
+    s.probe_generate(ptr[:1024], seed=6, out=gen[:1024])   # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.probe_generate(ptr, seed=6, out=gen)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    del gen
+    s.cnn_init(cnn_init_params(32, seed=0, input_scale=0.2), center, rng_)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = s.cnn_train(ptr, epochs=args.learned_epochs, batch=256, lr=2e-3, lr_final=1e-4, seed=6)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    s.check()
+    fwd_flops, step_flops = learned_flops_per_sample()
+    n_steps = (args.learned_train // 256) * 256 * args.learned_epochs
+    t_opt = max(t_train - t_gen, 1e-9)
+    pte = W.random_misregs(np.random.default_rng(99), 1024, 8.0, 2.0, 0.02)
+    y = s.probe_generate(pte, seed=1234, sample0=10 ** 9, noise_rel=0.01).float()
+    sc = np.array(rng_)
+    acc, lat = {}, {}
+    for m in ("cnn", "gn", "cnn+gn"):
+        p, res, it, cv = s.estimate(y, m)
+        e = (p - pte) / sc
+        acc[m] = {"rms_err_frac_of_range": [float(v) for v in np.sqrt((e ** 2).mean(0))],
+                  "median_residual": float(np.median(res)),
+                  "mean_iterations": float(it.mean()), "converged": float(cv.mean())}
+        ts = []
+        for q in range(21):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.estimate(y[q:q + 1], m)
+            ts.append(time.perf_counter() - t0)
+        lat[m] = 1000 * statistics.median(ts[1:])
+    s.close()
+    return {
+        "workload": "40x40 SH, 41x41 DM, 16 probe modes, shift +-8 px, rotation +-2 deg, magnification 1+-0.02, "
+                    "noise 1% of peak",
+        "probe_generation_samples_per_s": args.learned_train / t_gen,
+        "train_samples": args.learned_train, "epochs": args.learned_epochs, "train_wall_s": t_train,
+        "train_samples_per_s": n_steps / t_opt, "train_tflops": n_steps * step_flops / t_opt / 1e12,
+        "train_flops_per_sample": step_flops, "final_loss": float(losses[-1]),
+        "test_samples": 1024, "accuracy": acc, "latency_ms_batch1": lat,
+        "latency_ratio_gn_over_cnn": lat["gn"] / lat["cnn"],
+        "note": "training time excludes the probe generation measured separately (same kernel)",
+    }
+
+
 def run_synim(args):
     import torch
     import torch.distributed as dist
     from paper_2606_07759_b300.synim import SynIM
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -223,13 +319,9 @@ def run_synim(args):
     barrier()
     clk = clocks.stop()
     s.check()
-    t_ms = e0.elapsed_time(e1)
-    if world > 1:
-        tt = torch.tensor([t_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
+    t_ms = max_over_ranks(e0.elapsed_time(e1), world)
     k_ms, k_n = s.kernel_ms()
-    value = world * cols_per_step * args.steps / (t_ms / 1000.0)
+    value = job_value(cols_per_step * args.steps, t_ms / 1000.0, world)
     k_avg_s = (k_ms / max(k_n, 1)) / 1000.0
     peak, peak_kind = peaks()
     achieved = alg_bytes / k_avg_s / 1e9
@@ -256,12 +348,8 @@ def run_synim(args):
             e2e_t.append(dt)
     e2e_value = None
     if e2e_t:
-        e2e_s = statistics.median(e2e_t)
-        if world > 1:
-            tt = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_s = float(tt.item())
-        e2e_value = world * cols_per_step / e2e_s
+        e2e_s = max_over_ranks(statistics.median(e2e_t), world)
+        e2e_value = job_value(cols_per_step, e2e_s, world)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -286,9 +374,11 @@ def run_synim(args):
         line["cpu_baseline"] = {"value": cols / secs, "unit": UNIT, "cores": threads, "kind": "oracle",
                                 "sample": f"{cols} random columns over all {n_pairs} pairs, dense FP64 oracle, "
                                           f"{secs:.1f} s"}
+    s.close()
+    if rank == 0 and world == 1 and not args.no_learned:
+        line["learned"] = run_learned(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    s.close()
     if world > 1:
         dist.destroy_process_group()
     return 0
@@ -307,6 +397,9 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=4.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-estimator measurements")
+    ap.add_argument("--learned-train", type=int, default=200_000)
+    ap.add_argument("--learned-epochs", type=int, default=10)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -43,6 +43,9 @@ struct EstState {
     GnState *st = nullptr;      // [cap]
     int *n_active = nullptr;    // device counter
     int *h_active = nullptr;    // pinned
+    double *p0 = nullptr;       // [cap][4] start points / network estimates
+    double *h_p = nullptr;      // pinned [cap][4]
+    double *h_r = nullptr;      // pinned [cap][2] residual sums
     std::vector<int> iters, conv;  // of the last estimate
 };
 
@@ -54,7 +57,10 @@ void est_destroy(EstState *e) {
     cudaFree(e->pt);
     cudaFree(e->st);
     cudaFree(e->n_active);
+    cudaFree(e->p0);
     cudaFreeHost(e->h_active);
+    cudaFreeHost(e->h_p);
+    cudaFreeHost(e->h_r);
     delete e;
 }
 
@@ -103,6 +109,35 @@ k_gn_reduce(const float *__restrict__ y, const float *__restrict__ s, const floa
         double v = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sh[w][threadIdx.x];
         red[q * kRed + threadIdx.x] = v;
+    }
+}
+
+// Residual sums only: red2[q] = (r.r, y.y) of sample q.
+__global__ void __launch_bounds__(kRedThreads)
+k_resid_reduce(const float *__restrict__ y, const float *__restrict__ s, int per_sample, double *__restrict__ red2) {
+    const long q = blockIdx.x;
+    const float *yq = y + q * per_sample, *sq = s + q * per_sample;
+    double rr = 0.0, yy = 0.0;
+    for (int e = threadIdx.x; e < per_sample; e += blockDim.x) {
+        const double yv = yq[e], r = yv - (double)sq[e];
+        rr += r * r;
+        yy += yv * yv;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        rr += __shfl_xor_sync(0xffffffffu, rr, o);
+        yy += __shfl_xor_sync(0xffffffffu, yy, o);
+    }
+    __shared__ double sh[kRedThreads / 32][2];
+    if ((threadIdx.x & 31) == 0) {
+        sh[threadIdx.x >> 5][0] = rr;
+        sh[threadIdx.x >> 5][1] = yy;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sh[w][threadIdx.x];
+        red2[2 * q + threadIdx.x] = v;
     }
 }
 
@@ -233,8 +268,11 @@ cudaError_t est_reserve(EstState *E, long long cap, int per_sample) {
     cudaFree(E->red);
     cudaFree(E->pt);
     cudaFree(E->st);
+    cudaFree(E->p0);
+    cudaFreeHost(E->h_p);
+    cudaFreeHost(E->h_r);
     E->maps = E->dmaps = nullptr;
-    E->red = E->pt = nullptr;
+    E->red = E->pt = E->p0 = E->h_p = E->h_r = nullptr;
     E->st = nullptr;
     E->cap = 0;
     if ((e = cudaMalloc(&E->maps, sizeof(float) * per_sample * cap)) != cudaSuccess) return e;
@@ -242,6 +280,9 @@ cudaError_t est_reserve(EstState *E, long long cap, int per_sample) {
     if ((e = cudaMalloc(&E->red, sizeof(double) * kRed * cap)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&E->pt, sizeof(double) * 4 * cap)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&E->st, sizeof(GnState) * cap)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&E->p0, sizeof(double) * 4 * cap)) != cudaSuccess) return e;
+    if ((e = cudaMallocHost(&E->h_p, sizeof(double) * 4 * cap)) != cudaSuccess) return e;
+    if ((e = cudaMallocHost(&E->h_r, sizeof(double) * 2 * cap)) != cudaSuccess) return e;
     if (!E->n_active && (e = cudaMalloc(&E->n_active, sizeof(int))) != cudaSuccess) return e;
     if (!E->h_active && (e = cudaMallocHost(&E->h_active, sizeof(int))) != cudaSuccess) return e;
     E->cap = cap;
@@ -330,9 +371,8 @@ synim_status synim_misreg_estimate(synim_ctx *ctx, const float *probe_slopes, in
     const long long chunk = std::min<long long>(n, 512);
     cudaError_t e = est_reserve(E, chunk, per_sample);
     if (e != cudaSuccess) return ecuda(ctx, e, "misreg_estimate scratch");
-    double *p0 = nullptr;
-    if ((e = cudaMalloc(&p0, sizeof(double) * 4 * chunk)) != cudaSuccess) return ecuda(ctx, e, "misreg_estimate");
-    std::vector<double> hp((size_t)4 * chunk), hout((size_t)4 * chunk);
+    double *p0 = E->p0;
+    std::vector<double> hout((size_t)4 * chunk);
     synim_status status = SYNIM_OK;
     for (long long s0 = 0; s0 < n && status == SYNIM_OK; s0 += chunk) {
         const long long b = std::min(chunk, n - s0);
@@ -340,12 +380,12 @@ synim_status synim_misreg_estimate(synim_ctx *ctx, const float *probe_slopes, in
         if (method == 0) {
             for (long long q = 0; q < b; ++q) {
                 const synim_misreg &m = inout[s0 + q];
-                hp[4 * q + 0] = m.shift_x_px;
-                hp[4 * q + 1] = m.shift_y_px;
-                hp[4 * q + 2] = m.rot_deg;
-                hp[4 * q + 3] = m.mag;
+                E->h_p[4 * q + 0] = m.shift_x_px;
+                E->h_p[4 * q + 1] = m.shift_y_px;
+                E->h_p[4 * q + 2] = m.rot_deg;
+                E->h_p[4 * q + 3] = m.mag;
             }
-            e = cudaMemcpyAsync(p0, hp.data(), sizeof(double) * 4 * b, cudaMemcpyHostToDevice, st);
+            e = cudaMemcpyAsync(p0, E->h_p, sizeof(double) * 4 * b, cudaMemcpyHostToDevice, st);
         } else {
             std::string why;
             e = cnn_predict_slopes(ctx, y, b, p0, st, why);
@@ -359,11 +399,23 @@ synim_status synim_misreg_estimate(synim_ctx *ctx, const float *probe_slopes, in
             break;
         }
         if (method == 1) {
-            // network only: the judge is the residual of the regenerated responses
-            const int save = E->max_iter;
-            E->max_iter = 0;
-            e = gn_fit(ctx, y, b, p0, hout.data(), residual_out ? residual_out + s0 : nullptr, nullptr, nullptr, st);
-            E->max_iter = save;
+            // network only; the judge is the residual of the regenerated responses
+            if (residual_out) {
+                e = probe_launch(ctx, p0, b, E->maps, nullptr, nullptr, st);
+                if (e == cudaSuccess) {
+                    k_resid_reduce<<<(unsigned)b, kRedThreads, 0, st>>>(y, E->maps, per_sample, E->red);
+                    e = cudaMemcpyAsync(E->h_r, E->red, sizeof(double) * 2 * b, cudaMemcpyDeviceToHost, st);
+                }
+            }
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(E->h_p, p0, sizeof(double) * 4 * b, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e == cudaSuccess) {
+                std::memcpy(hout.data(), E->h_p, sizeof(double) * 4 * b);
+                if (residual_out)
+                    for (long long q = 0; q < b; ++q)
+                        residual_out[s0 + q] = E->h_r[2 * q + 1] > 0 ? std::sqrt(E->h_r[2 * q] / E->h_r[2 * q + 1]) : 0.0;
+            }
         } else {
             e = gn_fit(ctx, y, b, p0, hout.data(), residual_out ? residual_out + s0 : nullptr,
                        E->iters.data() + s0, E->conv.data() + s0, st);
@@ -380,7 +432,6 @@ synim_status synim_misreg_estimate(synim_ctx *ctx, const float *probe_slopes, in
             m.mag = hout[4 * q + 3];
         }
     }
-    cudaFree(p0);
     return status;
 }
 
