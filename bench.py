@@ -400,11 +400,16 @@ def main(argv=None):
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-estimator measurements")
     ap.add_argument("--learned-train", type=int, default=200_000)
     ap.add_argument("--learned-epochs", type=int, default=10)
+    ap.add_argument("--learned-only", action="store_true",
+                    help="diagnostic: run only the learned-estimator measurements and print them")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.learned_only:
+        print(json.dumps({"learned": run_learned(args)}), flush=True)
+        return 0
     return run_synim(args)
 
 

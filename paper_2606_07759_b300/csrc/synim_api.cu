@@ -262,15 +262,17 @@ namespace synim {
 
 // Upper bound of the per-sensor accumulator floats for one pair (any
 // actuator), mirroring the kernel's box arithmetic.
-long long arena_need(const DmHost &D, const WfsHost &W, const double Ai[4], int NV) {
+long long seg_need(const DmHost &D, const WfsHost &W, const double Ai[4], int NV) {
     const double ej = (D.W + 1.0) * (std::fabs(Ai[0]) + std::fabs(Ai[1])) + 9.0;
     const double ei = (D.W + 1.0) * (std::fabs(Ai[2]) + std::fabs(Ai[3])) + 9.0;
     const long long pj = std::min<long long>((long long)std::ceil(ej), W.M);
     const long long pi = std::min<long long>((long long)std::ceil(ei), W.M);
     const long long nsj = std::min<long long>((pj + 2) / W.k + 2, W.n_sub);
     const long long nsi = std::min<long long>((pi + 2) / W.k + 2, W.n_sub);
-    const long long nxc = pi / W.CH + 2, nyc = pj / W.CH + 2;
-    return (long long)NV * (2 * nxc * (nsj + 1) + 2 * nyc * (nsi + 1) + 2 * nsi * nsj);
+    // one box row: nsj + 1 x segments, two rows of nsj y segments, nsj pupil-edge
+    // sums, two values each
+    (void)nsi;
+    return (long long)NV * 2 * (4 * nsj + 1);
 }
 
 }  // namespace synim
@@ -358,9 +360,9 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
         c->use_graph = opts->use_graph != 0;
         c->profile = opts->profile != 0;
     }
-    if (c->threads % 32 != 0 || c->threads < 64 || c->threads > 512) {
+    if (c->threads % 32 != 0 || c->threads < 64 || c->threads > 256) {
         delete c;
-        return fail(nullptr, SYNIM_ERR_INVALID_ARG, "threads_per_cta must be a multiple of 32 in 64..512");
+        return fail(nullptr, SYNIM_ERR_INVALID_ARG, "threads_per_cta must be a multiple of 32 in 64..256");
     }
     auto bail = [&](synim_status s) {
         std::string m = c->err;
@@ -369,7 +371,6 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
         return s;
     };
     cudaError_t e;
-    int max_win = 4;
     // ---- DMs: support scan + window packing ----
     for (int d = 0; d < n_dm; ++d) {
         const synim_dm_desc &Dd = dms[d];
@@ -436,7 +437,6 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
         if (e != cudaSuccess) return bail(cuda_fail(c, e, "mask interior map"));
         G.win = d_win; G.org = d_org; G.mask = d_mask; G.mcls = d_mcls;
         G.n_act = H.n_act; G.N = H.N; G.W = W; G.Wp = Wp; G.win_stride = stride;
-        max_win = std::max(max_win, stride);
     }
     // ---- sensors: tables ----
     for (int w = 0; w < n_wfs; ++w) {
@@ -545,7 +545,6 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
     c->geo.n_items = acc;
     c->geo.n_dm = n_dm;
     c->geo.n_wfs = n_wfs;
-    c->geo.max_win_floats = max_win;
     *out = c;
     return SYNIM_OK;
 }
@@ -606,7 +605,7 @@ synim_status synim_im_check(synim_ctx *ctx, void *cuda_stream) {
     const int flag = *ctx->h_err;
     cudaMemset(ctx->d_err, 0, sizeof(int));
     if (flag & ERR_TIMEOUT) return fail(ctx, SYNIM_ERR_TIMEOUT, "window staging wait timed out");
-    if (flag & ERR_ARENA) return fail(ctx, SYNIM_ERR_SHAPE, "subaperture accumulators exceeded the arena");
+    if (flag & ERR_ARENA) return fail(ctx, SYNIM_ERR_SHAPE, "slope values exceeded their shared-memory buffer");
     return SYNIM_OK;
 }
 
@@ -651,58 +650,36 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
                 for (int q = 0; q < 4; ++q) P.dim[q] = dim ? dim[4 * p + q] : nullptr;
             }
             if (mode == MODE_VJP) P.gim = gim ? gim[p] : nullptr;
-            need[p] = (arena_need(c->dmh[d], c->wh[w], P.Ai, NV) + 31) / 32 * 32;
-        }
-    // Accumulator arena: all sensors of a DM in one group when that fits the
-    // shared memory of 2 CTAs per SM (forward) or 1 CTA per SM (tangents).
-    Geo g = c->geo;
-    int dev_max = 0, sm_max = 0;
-    cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
-    cudaDeviceGetAttribute(&sm_max, cudaDevAttrMaxSharedMemoryPerMultiprocessor, c->device);
-    g.arena_floats = 0;
-    const size_t fixed = im_smem_bytes(g) + (mode == MODE_VJP ? 8 * 4 * SYNIM_MAX_PAIRS : 64);
-    const int target = (mode == MODE_FWD) ? 2 : 1;
-    const long long budget =
-        std::min<long long>(dev_max, sm_max / target - 1024) - (long long)fixed;
-    long long cap = 0, single = 0;
-    for (int d = 0; d < c->n_dm; ++d) {
-        long long sum = 0;
-        for (int w = 0; w < c->n_wfs; ++w) {
-            sum += need[d * c->n_wfs + w];
-            single = std::max(single, need[d * c->n_wfs + w]);
-        }
-        cap = std::max(cap, sum);
-    }
-    cap = std::max(std::min(cap, budget / 4), single);
-    cap = std::max<long long>(cap, c->arena_floats);  // never shrink: keeps the captured graph
-    if ((long long)fixed + 4 * cap > dev_max)
-        return fail(c, SYNIM_ERR_SHAPE,
-                    "support window + accumulators need " + std::to_string(fixed + 4 * cap) +
-                        " bytes of shared memory; lower the grid or raise support_eps");
-    c->arena_floats = (int)cap;
-    g.arena_floats = c->arena_floats;
-    for (int d = 0; d < c->n_dm; ++d) {
-        int grp = 0;
-        long long used = 0;
-        for (int w = 0; w < c->n_wfs; ++w) {
-            const int p = d * c->n_wfs + w;
-            if (used + need[p] > cap && used > 0) {
-                ++grp;
-                used = 0;
+            {
+                // 16-byte column stores need aligned outputs and 2 nv % 4 == 0
+                auto al = [](const void *q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; };
+                bool v4 = (2 * c->wh[w].nv) % 4 == 0;
+                if (P.im && !al(P.im)) v4 = false;
+                for (int q = 0; q < 4; ++q)
+                    if (P.dim[q] && !al(P.dim[q])) v4 = false;
+                P.vec4 = v4 ? 1 : 0;
             }
-            hp[p].group = grp;
-            hp[p].arena_off = (int)used;
-            hp[p].arena_len = (int)need[p];
-            used += need[p];
+            need[p] = (seg_need(c->dmh[d], c->wh[w], P.Ai, NV) + 3) / 4 * 4;
         }
-        g.n_groups[d] = grp + 1;
-    }
+    // Per-warp segment buffer (one warp per column): the largest need over the pairs.
+    Geo g = c->geo;
+    long long cap = 4;
+    for (int p = 0; p < np; ++p) cap = std::max(cap, need[p]);
+    cap = std::max<long long>(cap, c->seg_floats);  // never shrink: keeps the captured graph
+    int dev_max = 0;
+    cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+    if ((long long)8 * 4 * cap > dev_max)
+        return fail(c, SYNIM_ERR_SHAPE,
+                    "boundary segments need " + std::to_string(8 * 4 * cap) +
+                        " bytes of shared memory per CTA; lower the grid or raise support_eps");
+    c->seg_floats = (int)cap;
+    g.seg_floats = c->seg_floats;
     const size_t smem = im_smem_bytes(g);
     int bps = 0;
     if ((e = im_prepare(mode, c->threads, smem, &bps)) != cudaSuccess) return cuda_fail(c, e, "kernel attributes");
     if (bps < 1) return fail(c, SYNIM_ERR_SHAPE, "IM kernel does not fit on an SM");
-    if (c->ctas_per_sm > 0) bps = std::min(bps, c->ctas_per_sm);
-    const int grid = std::max(1, std::min(c->geo.n_items, c->n_sm * bps));
+    const long long units = (long long)c->geo.n_items * c->n_wfs, warps = c->threads / 32;
+    const int grid = (int)std::max<long long>(1, std::min<long long>((units + warps - 1) / warps, 1LL << 30));
     if ((e = cudaMemcpyAsync(c->d_pairs, hp, sizeof(DevPair) * np, cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return cuda_fail(c, e, "parameter upload");
     cudaEventRecord(c->slot_ev[slot], s);

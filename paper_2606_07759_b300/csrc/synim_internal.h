@@ -13,7 +13,7 @@
 //              every subaperture boundary, one byte per (line pixel pair)
 //              holding the stencil bits and both pixels' classes (zero /
 //              core / ring), stored [pixel][boundary] so that the threads of
-//              a warp (consecutive boundaries) read consecutive bytes; both
+//              a warp (consecutive subapertures) read consecutive bytes; both
 //              rebuilt every call because they depend on the misregistration.
 #pragma once
 
@@ -68,10 +68,8 @@ struct DevPair {
     double dA[16], db[8];  // d(A, b)/dp_k, p = (shift x px, shift y px, rot deg, mag)
     float Ahi[4], Alo[4], bhi[2], blo[2];  // A, b as float pairs (compensated origins)
     float Aif[4];        // inverse of A, float (pixel boxes, with a margin)
-    int arena_off;       // shared-memory accumulator offset of this pair (floats)
-    int arena_len;       // floats reserved for it (upper bound over actuators)
-    int group;           // sensors of one DM are processed in groups that fit the arena
     uint8_t *xcc, *ycc;  // [M][n_sub + 1] boundary-line bytes (see above)
+    int vec4;            // output columns are 16-byte aligned and a multiple of 4 floats
     float *im;           // output [n_act][2 nv] or nullptr (skip)
     float *dim[4];       // tangent outputs or nullptr
     const float *gim;    // VJP input [n_act][2 nv] or nullptr
@@ -84,9 +82,7 @@ struct Geo {
     int n_dm, n_wfs, n_items;
     int order_dm[SYNIM_MAX_DM];         // DM processed at each position (costliest first)
     int order_start[SYNIM_MAX_DM + 1];  // item prefix in processing order
-    int max_win_floats;
-    int arena_floats;
-    int n_groups[SYNIM_MAX_DM];
+    int seg_floats;      // per-warp shared-memory buffer of the IM kernel (floats)
 };
 
 enum { ERR_TIMEOUT = 1, ERR_ARENA = 2 };
@@ -96,7 +92,9 @@ enum Mode { MODE_FWD = 0, MODE_TAN = 1, MODE_VJP = 2 };
 // Host helpers (synim_api.cu).
 bool invert2(const double A[4], double Ai[4]);
 int largest_divisor_le(int k, int cap);
-long long arena_need(const DmHost &D, const WfsHost &W, const double Ai[4], int NV);
+// Per-warp buffer (floats) of the IM kernel for the pair: one box row's
+// boundary segments and pupil-edge sums, NV values each.
+long long seg_need(const DmHost &D, const WfsHost &W, const double Ai[4], int NV);
 void split_pair(DevPair &P);  // float pairs of A, b and the float inverse
 void clear_create_error();         // synim_api.cu (no allocation)
 // Valid-row tables of sensor w of a context (device pointers): vsub[r] =
@@ -161,9 +159,9 @@ struct synim_ctx {
     long long line_off[SYNIM_MAX_PAIRS] = {};
     uint8_t *d_pst = nullptr, *d_lines = nullptr;
     int max_mm = 0, max_lines = 0;
-    int threads = 512, ctas_per_sm = 0;
+    int threads = 256, ctas_per_sm = 0;
     bool use_graph = true;
-    int arena_floats = 0;
+    int seg_floats = 0;
     std::map<std::tuple<int, size_t, int, int>, synim::GraphEntry> graphs;
     cudaStream_t cap = nullptr;
     bool profile = false;

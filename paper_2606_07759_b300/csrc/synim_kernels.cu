@@ -2,18 +2,21 @@
 //
 // k_support / k_pack  (create time) scan each influence function for its
 //                     support box and pack it into a zero-bordered window.
-// k_pst_core / _ring  (every call) edge-repair pixel classes per pair,
+// k_pst_core / _codes (every call) edge-repair pixel classes per pair,
 //                     Sec. 2.3 steps 1-2: the DM mask carried by the composite
 //                     affine, strictly binarised at 0.999999 (decided in FP64,
 //                     exactly as the definition), and the cross-dilated ring.
-// k_im<MODE>          (every call) one persistent launch over all actuators of
-//                     all DMs; each CTA stages one actuator's window into
-//                     shared memory with a 1-D bulk copy (TMA) and reuses it
-//                     for every sensor (Sec. 4.2: each IF fetched once).  For
-//                     each sensor it resamples the IF (Sec. 2.1), repairs the
-//                     ring (Sec. 2.3) and forms the subaperture means of the
-//                     central differences (Sec. 2.2), then streams the full
-//                     dense column out with 16-byte stores.
+// k_im<MODE>          (every call) one launch over every (actuator, sensor)
+//                     column of every DM (Sec. 4.2: all sensors in one pass);
+//                     one warp per column, the columns of one actuator in
+//                     consecutive warps of a CTA so that its packed window is
+//                     fetched from HBM once and served to the others from L1.
+//                     Box row by box row the warp resamples the IF at the
+//                     boundary line pixels (Sec. 2.1), repairs ring pixels
+//                     (Sec. 2.3), forms the telescoped boundary segments and
+//                     the subaperture means of the central differences (Sec.
+//                     2.2), and writes the column once (16-byte stores for the
+//                     zero runs).  No warp ever waits for another.
 //
 // The subaperture sum of central differences is evaluated in telescoped
 // form: sum_{p in s} P(p) (phi(p+x) - phi(p-x)) = sum_q phi(q) w_s(q) where
@@ -28,55 +31,6 @@
 #include "synim_device.cuh"
 
 namespace synim {
-
-// ---------------------------------------------------------------------------
-// PTX helpers: mbarrier + 1-D bulk copy global -> shared (TMA unit)
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,
-                                         uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            dst),
-        "l"(src), "r"(bytes), "r"(bar)
-        : "memory");
-}
-__device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait: gives up after ~2^31 clocks (about a second) instead of hanging.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > (1LL << 31)) return false;
-    }
-    return true;
-}
 
 // ---------------------------------------------------------------------------
 // Block reductions
@@ -316,38 +270,28 @@ cudaError_t launch_pst(const Geo &g, const DevPair *pairs, int max_mm, int max_l
 // ---------------------------------------------------------------------------
 // The IM kernel
 // ---------------------------------------------------------------------------
+// Per (actuator, sensor): the pixel box where the resampled, repaired IF can
+// be non-zero, the subaperture box whose slopes can be non-zero, and the
+// local coordinates of the box origin in the staged window.
 struct ItemWfs {
-    int pi0, pi1, pj0, pj1;  // pixel box where phi may be non-zero (inclusive)
-    int si0, si1, sj0, sj1;  // subapertures whose slopes may be non-zero (inclusive)
-    int nxc, nb, nyc, nbr;   // row chunks x column boundaries; column chunks x row boundaries
-    int ntask, arena, group, empty;
-    int xcid0, ycid0;        // first row / column chunk ids (pi0 / CH, pj0 / CH)
-    float inv_nb, inv_nbr;   // 1 / nb, 1 / nbr (task decode without integer division)
+    int pi0, pi1, pj0, pj1;  // pixel box (inclusive)
+    int si0, si1, sj0, sj1;  // subaperture box (inclusive)
+    int nsj, nsub;           // box width and size in subapertures
+    int empty;
     float xo, yo;            // padded-window coordinates of pixel (pi0, pj0)
     float a00, a01, a10, a11;
     float dxo[4], dyo[4], da[16];  // tangents of the coordinates (MODE_TAN / MODE_VJP)
     const uint8_t *pst, *xcc, *ycc;
 };
 
-// Bilinear sample of a zero-bordered window at padded coordinates (x, y);
-// zero when the cell does not touch the window.
-__device__ __forceinline__ float bil_xy(const float *__restrict__ win, int Wp, float Wf1, float x, float y) {
-    if (!(x > 0.f && x < Wf1 && y > 0.f && y < Wf1)) return 0.f;
-    const int ix = __float2int_rd(x), iy = __float2int_rd(y);
-    const float fx = x - (float)ix, fy = y - (float)iy;
-    const float *q = win + iy * Wp + ix;
-    const float v00 = q[0], v10 = q[1], v01 = q[Wp], v11 = q[Wp + 1];
-    const float top = fmaf(fx, v10 - v00, v00), bot = fmaf(fx, v11 - v01, v01);
-    return fmaf(fy, bot - top, top);
-}
-
 template <int NV>
 struct Eval {
+    static constexpr int NT = (NV == 5) ? 4 : 1;  // tangent parameters held
     const float *win;
     const uint8_t *pst;
     int Wp, M, pi0, pj0;
     float Wf1, xo, yo, a00, a01, a10, a11;
-    float dxo[4], dyo[4], da[16];
+    float dxo[NT], dyo[NT], da[4 * NT];
 
     __device__ __forceinline__ void load(const ItemWfs &s, const float *w, int wp, int W, int m) {
         win = w; pst = s.pst; Wp = wp; M = m; pi0 = s.pi0; pj0 = s.pj0;
@@ -398,7 +342,7 @@ struct Eval {
 #pragma unroll
         for (int t = 0; t < NV; ++t) acc[t] = 0.f;
         int n = 0;
-#pragma unroll
+#pragma unroll 1
         for (int d = 0; d < 4; ++d) {
             const int di = (d == 2) ? 1 : (d == 3 ? -1 : 0);
             const int dj = (d == 0) ? 1 : (d == 1 ? -1 : 0);
@@ -424,19 +368,15 @@ struct Eval {
         for (int t = 0; t < NV; ++t) v[t] = acc[t] * inv;
     }
 
-    // Repaired phase (and tangents) at (i, j) of known class (0 zero, 1 core, 2 ring).
-    __device__ __forceinline__ void eval_cls(int i, int j, int cls, float *v) const {
-        if (cls == 1) {
-            bil(i, j, v);
-        } else if (cls == 0) {
+    // acc += wgt * (repaired phase and tangents at (i, j) of class c: 0 zero,
+    // 1 core, 2 ring).
+    __device__ __forceinline__ void add(int i, int j, int c, float wgt, float *acc) const {
+        if (c == 0) return;
+        float v[NV];
+        if (c == 1) bil(i, j, v);
+        else ring(i, j, v);
 #pragma unroll
-            for (int t = 0; t < NV; ++t) v[t] = 0.f;
-        } else {
-            ring(i, j, v);
-        }
-    }
-    __device__ __forceinline__ void eval(int i, int j, float *v) const {
-        eval_cls(i, j, pixel_class(pst, M, i, j), v);
+        for (int t = 0; t < NV; ++t) acc[t] = fmaf(wgt, v[t], acc[t]);
     }
 };
 
@@ -447,22 +387,6 @@ __device__ __forceinline__ void decode_item(const Geo &g, int item, int &d, int 
     a = item - g.order_start[pos];
 }
 
-__device__ __forceinline__ void prefetch_window(const Geo &g, int item) {
-    int d, a;
-    decode_item(g, item, d, a);
-    const DevDM &D = g.dm[d];
-    bulk_prefetch_l2(D.win + (size_t)a * D.win_stride, (uint32_t)D.win_stride * 4u);
-}
-
-__device__ __forceinline__ void issue_window(const Geo &g, int item, float *s_win, uint32_t bar) {
-    int d, a;
-    decode_item(g, item, d, a);
-    const DevDM &D = g.dm[d];
-    const uint32_t bytes = (uint32_t)D.win_stride * 4u;
-    mbar_expect_tx(bar, bytes);
-    bulk_g2s(smem_u32(s_win), D.win + (size_t)a * D.win_stride, bytes, bar);
-}
-
 template <int MODE>
 __device__ __forceinline__ bool pair_active(const DevPair &P) {
     if (MODE == MODE_FWD) return P.im != nullptr;
@@ -471,19 +395,20 @@ __device__ __forceinline__ bool pair_active(const DevPair &P) {
     return P.gim != nullptr;
 }
 
-// Pixel box of actuator a on sensor w, task counts and local coordinates.
+// Pixel and subaperture boxes of actuator a on sensor w, local coordinates.
 template <int MODE, int NV>
 __device__ void make_info(const Geo &g, const DevPair *__restrict__ pairs, int d, int a, int w,
                           ItemWfs &s, int *err) {
     const DevPair &P = pairs[d * g.n_wfs + w];
     const DevWFS &WF = g.wfs[w];
     const DevDM &D = g.dm[d];
-    const int M = WF.M, k = WF.k, CH = WF.CH;
-    s.pst = P.pst; s.xcc = P.xcc; s.ycc = P.ycc;
-    s.arena = P.arena_off;
-    s.group = P.group;
+    const int M = WF.M, k = WF.k;
+    s.pst = P.pst;
+    s.xcc = P.xcc;
+    s.ycc = P.ycc;
     s.empty = 1;
-    s.ntask = 0;
+    s.nsub = 0;
+    s.nsj = 1;
     s.si0 = 1; s.si1 = 0; s.sj0 = 1; s.sj1 = 0;
     s.pi0 = 1; s.pi1 = 0; s.pj0 = 1; s.pj1 = 0;
     if (!pair_active<MODE>(P)) return;
@@ -510,23 +435,13 @@ __device__ void make_info(const Geo &g, const DevPair *__restrict__ pairs, int d
     // slopes reach one pixel further (the central difference)
     const int si0 = max(pi0 - 1, 0) / k, si1 = min(pi1 + 1, M - 1) / k;
     const int sj0 = max(pj0 - 1, 0) / k, sj1 = min(pj1 + 1, M - 1) / k;
-    const int nxc = pi1 / CH - pi0 / CH + 1, nb = sj1 - sj0 + 2;
-    const int nyc = pj1 / CH - pj0 / CH + 1, nbr = si1 - si0 + 2;
-    const int nsub = (si1 - si0 + 1) * (sj1 - sj0 + 1);
-    const int need = NV * (2 * nxc * nb + 2 * nyc * nbr + 2 * nsub);
-    if (need > P.arena_len) {
-        atomicOr(err, ERR_ARENA);
-        return;
-    }
+    const int nsj = sj1 - sj0 + 1, nsub = (si1 - si0 + 1) * nsj;
+    (void)err;
     s.empty = 0;
     s.pi0 = pi0; s.pi1 = pi1; s.pj0 = pj0; s.pj1 = pj1;
     s.si0 = si0; s.si1 = si1; s.sj0 = sj0; s.sj1 = sj1;
-    s.nxc = nxc; s.nb = nb; s.nyc = nyc; s.nbr = nbr;
-    s.ntask = nxc * nb + nyc * nbr;
-    s.xcid0 = pi0 / CH;
-    s.ycid0 = pj0 / CH;
-    s.inv_nb = 1.f / (float)nb;
-    s.inv_nbr = 1.f / (float)nbr;
+    s.nsj = nsj;
+    s.nsub = nsub;
     s.xo = exact_affine(P.Ahi[0], P.Alo[0], P.Ahi[1], P.Alo[1], P.bhi[0], P.blo[0], pj0, pi0, wx0 - 1);
     s.yo = exact_affine(P.Ahi[2], P.Alo[2], P.Ahi[3], P.Alo[3], P.bhi[1], P.blo[1], pj0, pi0, wy0 - 1);
     s.a00 = P.Ahi[0]; s.a01 = P.Ahi[1]; s.a10 = P.Ahi[2]; s.a11 = P.Ahi[3];
@@ -539,458 +454,343 @@ __device__ void make_info(const Geo &g, const DevPair *__restrict__ pairs, int d
     }
 }
 
-// floor(u / n) for 0 <= u < 2^24 from a float reciprocal, corrected to exact.
-__device__ __forceinline__ int fast_div(int u, int n, float inv) {
-    int c = __float2int_rz((float)u * inv);
-    if (c * n > u) --c;
-    else if ((c + 1) * n <= u) ++c;
-    return c;
-}
-
-// One telescoped line task: a column pair (b k - 1, b k) over a chunk of
-// rows (x slopes) or a row pair over a chunk of columns (y slopes).
-struct LineTask {
-    int lo, hi, l0, slot;  // line range, first line pixel, accumulator slot
-    bool xdir, use0, use1;
-    const uint8_t *cc;     // boundary-line bytes of this boundary (stride n_sub + 1)
+// One boundary segment (Sec. 2.2, telescoped): the two pixel lines at
+// boundary b (pixels b k - 1 and b k) over one subaperture row (x) or column
+// (y), restricted to the pixel box.  A collects their contributions to the
+// subaperture before the boundary (bits 0 and 2 of the boundary byte), B to
+// the one after (bits 1 and 3); the slope of subaperture s along x is then
+// A(b = sj + 1) - B(b = sj) plus its pupil-edge pixels.
+struct SegRows {
+    int ua, ub, l0, inmask;
+    const uint8_t *cc;
 };
 
-__device__ __forceinline__ LineTask decode_task(const DevWFS &WF, const ItemWfs &s, int u) {
-    const int k = WF.k, CH = WF.CH;
-    const int nxb = s.nxc * s.nb;
-    LineTask T;
-    T.xdir = u < nxb;
-    if (T.xdir) {
-        const int c = fast_div(u, s.nb, s.inv_nb), bq = u - c * s.nb;
-        const int b = s.sj0 + bq, cid = s.xcid0 + c;
-        T.lo = max(cid * CH, s.pi0);
-        T.hi = min(cid * CH + CH - 1, s.pi1);
-        T.l0 = b * k - 1;
-        T.use0 = T.l0 >= s.pj0 && T.l0 <= s.pj1;
-        T.use1 = T.l0 + 1 >= s.pj0 && T.l0 + 1 <= s.pj1;
-        T.cc = s.xcc + b;
-        T.slot = c * s.nb + bq;
-    } else {
-        u -= nxb;
-        const int c = fast_div(u, s.nbr, s.inv_nbr), bq = u - c * s.nbr;
-        const int b = s.si0 + bq, cid = s.ycid0 + c;
-        T.lo = max(cid * CH, s.pj0);
-        T.hi = min(cid * CH + CH - 1, s.pj1);
-        T.l0 = b * k - 1;
-        T.use0 = T.l0 >= s.pi0 && T.l0 <= s.pi1;
-        T.use1 = T.l0 + 1 >= s.pi0 && T.l0 + 1 <= s.pi1;
-        T.cc = s.ycc + b;
-        T.slot = c * s.nbr + bq;
-    }
-    return T;
+__device__ __forceinline__ SegRows seg_rows(const DevWFS &WF, const ItemWfs &s, int axis, int b, int sq) {
+    const int k = WF.k;
+    SegRows r;
+    const int u0 = sq * k;
+    r.ua = max(u0, axis ? s.pj0 : s.pi0);
+    r.ub = min(u0 + k - 1, axis ? s.pj1 : s.pi1);
+    r.l0 = b * k - 1;
+    const int c0 = axis ? s.pi0 : s.pj0, c1 = axis ? s.pi1 : s.pj1;
+    r.inmask = ((r.l0 >= c0 && r.l0 <= c1) ? 1 : 0) | ((r.l0 + 1 >= c0 && r.l0 + 1 <= c1) ? 2 : 0);
+    r.cc = (axis ? s.ycc : s.xcc) + b;
+    return r;
 }
 
-// Up to 8 boundary-line bytes (rows r0 .. r0 + 7 of the task) in one register.
-__device__ __forceinline__ unsigned long long load_codes(const LineTask &T, int n1, int r0) {
-    const int cnt = min(8, T.hi - r0 + 1);
-    unsigned long long pack = 0ull;
-#pragma unroll
-    for (int q = 0; q < 8; ++q)
-        if (q < cnt) pack |= (unsigned long long)__ldg(T.cc + (long)(r0 + q) * n1) << (8 * q);
-    return pack;
-}
-
-// Resample the task's line pixels (the first 8 rows' bytes are given) and
-// store its two telescoped partial sums.
+// This lane's share of a segment: pixel rows ua + lane0, ua + lane0 + lstep, ...
 template <int NV>
-__device__ __forceinline__ void run_task(const DevWFS &WF, const ItemWfs &s, const LineTask &T,
-                                         unsigned long long pack, const Eval<NV> &ev, float *base) {
-    const int n1 = WF.n_sub + 1;
-    const int nxb = s.nxc * s.nb, nyb = s.nyc * s.nbr;
-    float L[NV], R[NV], v[NV];
+__device__ __forceinline__ void seg_compute(const DevWFS &WF, const SegRows &r, const Eval<NV> &ev, int axis,
+                                            int lane0, int lstep, float *A, float *B) {
+    if (!r.inmask) return;
+    const int n1 = WF.n_sub + 1, l0 = r.l0, inmask = r.inmask;
+    for (int u = r.ua + lane0; u <= r.ub; u += lstep) {
+        const int c = __ldg(r.cc + (long)u * n1);
+        const int cl0 = (inmask & 1) ? (c >> 4) & 3 : 0, cl1 = (inmask & 2) ? (c >> 6) & 3 : 0;
+        const float wa0 = (float)(c & 1), wb0 = (float)((c >> 1) & 1);
+        const float wa1 = (float)((c >> 2) & 1), wb1 = (float)((c >> 3) & 1);
+        float v0[NV], v1[NV];
+        if (cl0 == 2 || cl1 == 2) {
 #pragma unroll
-    for (int t = 0; t < NV; ++t) L[t] = R[t] = 0.f;
-    const bool xdir = T.xdir;
-    const int lo = T.lo, hi = T.hi, l0 = T.l0;
-    if constexpr (NV == 1) {
-        // along a line the sampled DM point moves by a constant step: one FMA
-        // per coordinate from the line's first pixel
-        float x0, y0, x1, y1, sx, sy;
-        if (xdir) {
-            const float di = (float)(lo - ev.pi0), dj = (float)(l0 - ev.pj0);
-            x0 = fmaf(ev.a00, dj, fmaf(ev.a01, di, ev.xo));
-            y0 = fmaf(ev.a10, dj, fmaf(ev.a11, di, ev.yo));
-            x1 = fmaf(ev.a00, dj + 1.f, fmaf(ev.a01, di, ev.xo));
-            y1 = fmaf(ev.a10, dj + 1.f, fmaf(ev.a11, di, ev.yo));
-            sx = ev.a01;
-            sy = ev.a11;
+            for (int t = 0; t < NV; ++t) v0[t] = v1[t] = 0.f;
+            if (cl0 == 1) ev.bil(axis ? l0 : u, axis ? u : l0, v0);
+            else if (cl0 == 2) ev.ring(axis ? l0 : u, axis ? u : l0, v0);
+            if (cl1 == 1) ev.bil(axis ? l0 + 1 : u, axis ? u : l0 + 1, v1);
+            else if (cl1 == 2) ev.ring(axis ? l0 + 1 : u, axis ? u : l0 + 1, v1);
         } else {
-            const float di = (float)(l0 - ev.pi0), dj = (float)(lo - ev.pj0);
-            x0 = fmaf(ev.a00, dj, fmaf(ev.a01, di, ev.xo));
-            y0 = fmaf(ev.a10, dj, fmaf(ev.a11, di, ev.yo));
-            x1 = fmaf(ev.a00, dj, fmaf(ev.a01, di + 1.f, ev.xo));
-            y1 = fmaf(ev.a10, dj, fmaf(ev.a11, di + 1.f, ev.yo));
-            sx = ev.a00;
-            sy = ev.a10;
-        }
-        for (int rb = lo; rb <= hi; rb += 8) {
-            if (rb != lo) pack = load_codes(T, n1, rb);
-            const int cnt = min(8, hi - rb + 1);
-            for (int q = 0; q < cnt; ++q) {
-                const int r = rb + q;
-                const float m = (float)(r - lo);
-                const int code = (int)((pack >> (8 * q)) & 0xffull);
-                if (T.use0 && (code & 3)) {
-                    const int cls = (code >> 4) & 3;
-                    float vv = 0.f;
-                    if (cls == 1) vv = bil_xy(ev.win, ev.Wp, ev.Wf1, fmaf(sx, m, x0), fmaf(sy, m, y0));
-                    else if (cls == 2) { if (xdir) ev.ring(r, l0, &vv); else ev.ring(l0, r, &vv); }
-                    L[0] += (code & 1) ? vv : 0.f;
-                    R[0] += (code & 2) ? vv : 0.f;
-                }
-                if (T.use1 && (code & 12)) {
-                    const int cls = code >> 6;
-                    float vv = 0.f;
-                    if (cls == 1) vv = bil_xy(ev.win, ev.Wp, ev.Wf1, fmaf(sx, m, x1), fmaf(sy, m, y1));
-                    else if (cls == 2) { if (xdir) ev.ring(r, l0 + 1, &vv); else ev.ring(l0 + 1, r, &vv); }
-                    L[0] += (code & 4) ? vv : 0.f;
-                    R[0] += (code & 8) ? vv : 0.f;
-                }
-            }
-        }
-    } else {
-        for (int rb = lo; rb <= hi; rb += 8) {
-            if (rb != lo) pack = load_codes(T, n1, rb);
-            const int cnt = min(8, hi - rb + 1);
-            for (int q = 0; q < cnt; ++q) {
-                const int r = rb + q;
-                const int code = (int)((pack >> (8 * q)) & 0xffull);
-#pragma unroll 1
-                for (int px = 0; px < 2; ++px) {
-                    const int bits = (code >> (2 * px)) & 3;
-                    if (!bits || !(px ? T.use1 : T.use0)) continue;
-                    const int line = l0 + px;
-                    if (xdir) ev.eval_cls(r, line, (code >> (4 + 2 * px)) & 3, v);
-                    else ev.eval_cls(line, r, (code >> (4 + 2 * px)) & 3, v);
-                    if (bits & 1)
+            // both pixels core or zero: two independent gathers, zero weight
+            // for a zero-class pixel
+            ev.bil(axis ? l0 : u, axis ? u : l0, v0);
+            ev.bil(axis ? l0 + 1 : u, axis ? u : l0 + 1, v1);
+            if (cl0 == 0)
 #pragma unroll
-                        for (int t = 0; t < NV; ++t) L[t] += v[t];
-                    if (bits & 2)
+                for (int t = 0; t < NV; ++t) v0[t] = 0.f;
+            if (cl1 == 0)
 #pragma unroll
-                        for (int t = 0; t < NV; ++t) R[t] += v[t];
-                }
-            }
+                for (int t = 0; t < NV; ++t) v1[t] = 0.f;
         }
-    }
-    float *lp, *rp;
-    if (xdir) {
-        lp = base + T.slot * NV;
-        rp = base + NV * nxb + T.slot * NV;
-    } else {
-        lp = base + 2 * NV * nxb + T.slot * NV;
-        rp = base + 2 * NV * nxb + NV * nyb + T.slot * NV;
-    }
 #pragma unroll
-    for (int t = 0; t < NV; ++t) {
-        lp[t] = L[t];
-        rp[t] = R[t];
+        for (int t = 0; t < NV; ++t) {
+            A[t] = fmaf(wa0, v0[t], fmaf(wa1, v1[t], A[t]));
+            B[t] = fmaf(wb0, v0[t], fmaf(wb1, v1[t], B[t]));
+        }
     }
 }
 
-// Subaperture sums of one sensor (x block, then y block): add the telescoped
-// boundary-line sums of every chunk to the pupil-edge sums already in S.
+// Pupil-edge pixels of subaperture (si, sj) inside the pixel box, both axes
+// at once: ax += wx(q) phi(q), ay += wy(q) phi(q); the warp's lanes split the
+// entries (lane0, lstep) and the caller reduces.
 template <int NV>
-__device__ __forceinline__ void finalize_sub(const ItemWfs &s, const DevWFS &WF, float *base, int q) {
-    const int k = WF.k, CH = WF.CH;
-    const int nsj = s.sj1 - s.sj0 + 1, nsub = (s.si1 - s.si0 + 1) * nsj;
-    const int nxb = s.nxc * s.nb, nyb = s.nyc * s.nbr;
-    float *S = base + NV * (2 * nxb + 2 * nyb);
-    const int comp = q >= nsub ? 1 : 0, idx = q - comp * nsub;
-    const int si = s.si0 + idx / nsj, sj = s.sj0 + idx % nsj;
-    float v[NV];
+__device__ __forceinline__ void edge_sum(const DevWFS &WF, const ItemWfs &s, const Eval<NV> &ev, int si, int sj,
+                                         int lane0, int lstep, float *ax, float *ay) {
+    const int k = WF.k;
+    const int ra = max(si * k, s.pi0), rb = min(si * k + k - 1, s.pi1);
+    if (ra > rb) return;
+    const long sr = (long)(si * WF.n_sub + sj) * k - (long)si * k;
+    const int e0 = WF.irr_sr[sr + ra], e1 = WF.irr_sr[sr + rb + 1];
+    for (int e = e0 + lane0; e < e1; e += lstep) {
+        const int pix = WF.irr_pix[e];
+        const int i = pix >> 16, j = pix & 0xffff;
+        if (j < s.pj0 || j > s.pj1) continue;
+        const float wx = WF.irr_w[2 * e], wy = WF.irr_w[2 * e + 1];
+        float v[NV];
 #pragma unroll
-    for (int t = 0; t < NV; ++t) v[t] = S[q * NV + t];
-    if (comp == 0) {
-        const float *CBL = base, *CBR = base + NV * nxb;
-        const int lo = max(si * k / CH, s.pi0 / CH), hi = min(((si + 1) * k - 1) / CH, s.pi1 / CH);
-        for (int cid = lo; cid <= hi; ++cid) {
-            const int c = cid - s.pi0 / CH;
+        for (int t = 0; t < NV; ++t) v[t] = 0.f;
+        const int c = pixel_class(s.pst, WF.M, i, j);
+        if (c == 1) ev.bil(i, j, v);
+        else if (c == 2) ev.ring(i, j, v);
 #pragma unroll
-            for (int t = 0; t < NV; ++t)
-                v[t] += CBL[(c * s.nb + sj + 1 - s.sj0) * NV + t] - CBR[(c * s.nb + sj - s.sj0) * NV + t];
-        }
-    } else {
-        const float *RBU = base + 2 * NV * nxb, *RBD = RBU + NV * nyb;
-        const int lo = max(sj * k / CH, s.pj0 / CH), hi = min(((sj + 1) * k - 1) / CH, s.pj1 / CH);
-        for (int cid = lo; cid <= hi; ++cid) {
-            const int c = cid - s.pj0 / CH;
-#pragma unroll
-            for (int t = 0; t < NV; ++t)
-                v[t] += RBU[(c * s.nbr + si + 1 - s.si0) * NV + t] - RBD[(c * s.nbr + si - s.si0) * NV + t];
+        for (int t = 0; t < NV; ++t) {
+            ax[t] = fmaf(wx, v[t], ax[t]);
+            ay[t] = fmaf(wy, v[t], ay[t]);
         }
     }
-#pragma unroll
-    for (int t = 0; t < NV; ++t) S[q * NV + t] = v[t];
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(512, (MODE == MODE_FWD) ? 2 : 1)
-    k_im(const __grid_constant__ Geo g, const DevPair *__restrict__ pairs, int *__restrict__ counter,
-         int *__restrict__ err, double *__restrict__ gp) {
-    constexpr int NV = (MODE == MODE_FWD) ? 1 : 5;
-    extern __shared__ __align__(128) unsigned char smem[];
-    float *s_win = reinterpret_cast<float *>(smem);
-    uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem + (size_t)g.max_win_floats * 4);
-    ItemWfs *s_info = reinterpret_cast<ItemWfs *>(s_bar + 2);
-    float *s_arena = reinterpret_cast<float *>(s_info + SYNIM_MAX_WFS);
-    __shared__ int s_item, s_next, s_abort;
-    __shared__ double s_gp[MODE == MODE_VJP ? SYNIM_MAX_PAIRS * 4 : 1];
-
-    const int tid = threadIdx.x, nth = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5, nwarps = nth >> 5;
-    const uint32_t bar = smem_u32(s_bar);
-    if (MODE == MODE_VJP)
-        for (int q = tid; q < SYNIM_MAX_PAIRS * 4; q += nth) s_gp[q] = 0.0;
-    if (tid == 0) {
-        mbar_init(bar, 1);
-        fence_mbar_init();
-        s_abort = 0;
-        const int it = atomicAdd(counter, 1);
-        s_item = it;
-        if (it < g.n_items) issue_window(g, it, s_win, bar);
+// Zero rows [r0, r1) of one output column (16-byte stores where aligned).
+__device__ __forceinline__ void zero_rows(float *col, int r0, int r1, bool vec4, int lane) {
+    if (r0 >= r1) return;
+    if (!vec4) {
+        for (int r = r0 + lane; r < r1; r += 32) col[r] = 0.f;
+        return;
     }
-    __syncthreads();
-    int item = s_item;
-    uint32_t phase = 0;
-    while (item < g.n_items) {
-        int d, a;
-        decode_item(g, item, d, a);
-        const DevDM &D = g.dm[d];
-        if (tid == 0) {
-            // claim the next actuator now and pull its window towards L2
-            const int nx = atomicAdd(counter, 1);
-            s_next = nx;
-            if (nx < g.n_items) prefetch_window(g, nx);
+    const int h = min(r1, (r0 + 3) & ~3), t = max(h, r1 & ~3);
+    if (lane < h - r0) col[r0 + lane] = 0.f;
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int c = h / 4 + lane; c < t / 4; c += 32) reinterpret_cast<float4 *>(col)[c] = z;
+    if (lane < r1 - t) col[t + lane] = 0.f;
+}
+
+// Boundary segments of one box row (x, boundaries sj0 .. sj1 + 1 over the
+// subaperture row si) or one row boundary (y, boundary b over the box's
+// subaperture columns), warp-cooperative: groups of L lanes share a segment
+// and split its pixel rows / columns, then reduce (fixed butterfly order).
+// seg[(q) * 2 NV + v] = A, seg[(q) * 2 NV + NV + v] = B of the q-th segment.
+template <int NV>
+__device__ __forceinline__ void warp_segments(const DevWFS &WF, const ItemWfs &s, const Eval<NV> &ev, int axis,
+                                              int fixed, int first, int count, float *seg, int lane) {
+    const int L = (WF.k > 32) ? 32 : (WF.k > 16 ? 8 : 4);   // lanes per segment
+    const int per = 32 / L;
+    const int grp = lane / L, q = lane - grp * L;
+    // x: boundary first + idx over subaperture row `fixed`; y: boundary
+    // `fixed` over subaperture column first + idx
+    for (int base = 0; base < count; base += per) {
+        const int idx = base + grp;
+        float A[NV], B[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) A[v] = B[v] = 0.f;
+        if (idx < count) {
+            const SegRows r = seg_rows(WF, s, axis, axis ? fixed : first + idx, axis ? first + idx : fixed);
+            seg_compute<NV>(WF, r, ev, axis, q, L, A, B);
         }
-        for (int w = tid; w < g.n_wfs; w += nth) make_info<MODE, NV>(g, pairs, d, a, w, s_info[w], err);
-        if (!mbar_wait_bounded(bar, phase)) {
-            s_abort = 1;
-            atomicOr(err, ERR_TIMEOUT);
+        if (L == 4) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+#pragma unroll
+                for (int o = 2; o > 0; o >>= 1) {
+                    A[v] += __shfl_xor_sync(0xffffffffu, A[v], o);
+                    B[v] += __shfl_xor_sync(0xffffffffu, B[v], o);
+                }
+        } else if (L == 8) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+#pragma unroll
+                for (int o = 4; o > 0; o >>= 1) {
+                    A[v] += __shfl_xor_sync(0xffffffffu, A[v], o);
+                    B[v] += __shfl_xor_sync(0xffffffffu, B[v], o);
+                }
+        } else {
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    A[v] += __shfl_xor_sync(0xffffffffu, A[v], o);
+                    B[v] += __shfl_xor_sync(0xffffffffu, B[v], o);
+                }
         }
-        __syncthreads();
-        if (s_abort) break;
-        phase ^= 1u;
-        const int next_item = s_next;  // read before tid 0 can claim again
-        const int ng = g.n_groups[d];
-        for (int gi = 0; gi < ng; ++gi) {
-            // telescoped boundary lines: the tasks of every sensor of the group
-            // form one sequence dealt round-robin to the threads; each thread
-            // loads the next task's line bytes before resampling the current one
-            {
-                auto find = [&](int gq, int &w, int &basew) -> bool {
-                    while (true) {
-                        if (w >= 0) {
-                            if (gq < basew + s_info[w].ntask) return true;
-                            basew += s_info[w].ntask;
-                        }
-                        do { ++w; } while (w < g.n_wfs && (s_info[w].group != gi || s_info[w].empty));
-                        if (w >= g.n_wfs) return false;
-                    }
-                };
-                int gq = tid, w = -1, basew = 0;
-                if (find(gq, w, basew)) {
-                    LineTask T = decode_task(g.wfs[w], s_info[w], gq - basew);
-                    unsigned long long pack = load_codes(T, g.wfs[w].n_sub + 1, T.lo);
-                    Eval<NV> ev;
-                    ev.load(s_info[w], s_win, D.Wp, D.W, g.wfs[w].M);
-                    int ev_w = w;
-                    while (true) {
-                        int gn = gq + nth, wn = w, bn = basew;
-                        const bool more = find(gn, wn, bn);
-                        LineTask Tn;
-                        unsigned long long packn = 0ull;
-                        if (more) {
-                            Tn = decode_task(g.wfs[wn], s_info[wn], gn - bn);
-                            packn = load_codes(Tn, g.wfs[wn].n_sub + 1, Tn.lo);
-                        }
-                        if (ev_w != w) {
-                            ev.load(s_info[w], s_win, D.Wp, D.W, g.wfs[w].M);
-                            ev_w = w;
-                        }
-                        run_task<NV>(g.wfs[w], s_info[w], T, pack, ev, s_arena + s_info[w].arena);
-                        if (!more) break;
-                        gq = gn; w = wn; basew = bn; T = Tn; pack = packn;
-                    }
-                }
+        if (q == 0 && idx < count)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                seg[(size_t)idx * 2 * NV + v] = A[v];
+                seg[(size_t)idx * 2 * NV + NV + v] = B[v];
             }
-            // pupil-edge pixels: one warp per (sensor, subaperture row) writes the
-            // edge sum of every subaperture of that row (zero where there is none);
-            // only the entries on pixel rows inside the box are visited
-            for (int rr = warp;; rr += nwarps) {
-                int w = 0, acc = 0;
-                for (; w < g.n_wfs; ++w) {
-                    const ItemWfs &s = s_info[w];
-                    if (s.group != gi || s.empty) continue;
-                    const int nr = s.si1 - s.si0 + 1;
-                    if (rr < acc + nr) break;
-                    acc += nr;
-                }
-                if (w >= g.n_wfs) break;
-                const ItemWfs &s = s_info[w];
-                const DevWFS &WF = g.wfs[w];
-                const int k = WF.k;
-                const int si = s.si0 + rr - acc;
-                const int nsj = s.sj1 - s.sj0 + 1, nsub = (s.si1 - s.si0 + 1) * nsj;
-                float *S = s_arena + s.arena + NV * (2 * s.nxc * s.nb + 2 * s.nyc * s.nbr);
-                const int row = (si - s.si0) * nsj;
-                for (int q = lane; q < nsj * NV; q += 32) {
-                    S[row * NV + q] = 0.f;
-                    S[(nsub + row) * NV + q] = 0.f;
-                }
-                __syncwarp();
-                const int ra = max(s.pi0, si * k) - si * k, rb = min(s.pi1, si * k + k - 1) - si * k;
-                const int c1 = WF.irrc_row[si + 1];
-                if (ra <= rb && c1 > WF.irrc_row[si]) {
-                    Eval<NV> ev;
-                    ev.load(s, s_win, D.Wp, D.W, WF.M);
-                    for (int c = WF.irrc_row[si]; c < c1; ++c) {
-                        const int sj = WF.irrc[c].x;
-                        if (sj < s.sj0 || sj > s.sj1) continue;
-                        const long sr = (long)(si * WF.n_sub + sj) * k;
-                        const int e0 = WF.irr_sr[sr + ra], e1 = WF.irr_sr[sr + rb + 1];
-                        float ax[NV], ay[NV], v[NV];
+    }
+}
+
+// One IM column (actuator a of DM d on sensor w) by one warp: zeros outside
+// the rows of the subaperture box, and, box row by box row, the boundary
+// segments, the slopes (segment differences plus pupil-edge pixels, times
+// slope_scale / (2 dw lit)) and their stores; or the cotangent dot products.
+template <int MODE, int NV>
+__device__ __forceinline__ void warp_column(const Geo &g, const DevPair *__restrict__ pairs, int d, int a, int w,
+                                            float *wbuf, int cap, int lane, int *err, double *gp) {
+    const int pidx = d * g.n_wfs + w;
+    const DevPair &P = pairs[pidx];
+    if (!pair_active<MODE>(P)) return;
+    const DevWFS &WF = g.wfs[w];
+    const DevDM &D = g.dm[d];
+    ItemWfs s;
+    make_info<MODE, NV>(g, pairs, d, a, w, s, err);
+    const int nv = WF.nv, n2 = 2 * nv;
+    const int nsj = s.empty ? 0 : s.nsj;
+    if (!s.empty && NV * 2 * (4 * nsj + 1) > cap) {
+        if (lane == 0) atomicOr(err, ERR_ARENA);
+        s.empty = 1;
+    }
+    const bool vec4 = P.vec4 != 0;
+    const int vr0 = s.empty ? 0 : WF.vrow[s.si0], vr1 = s.empty ? 0 : WF.vrow[s.si1 + 1];
+    constexpr int NOUT = (MODE == MODE_FWD) ? 1 : (MODE == MODE_TAN ? 5 : 0);
+    float *cols[NOUT > 0 ? NOUT : 1];
+    if (MODE != MODE_VJP) {
 #pragma unroll
-                        for (int t = 0; t < NV; ++t) ax[t] = ay[t] = 0.f;
-                        for (int e = e0 + lane; e < e1; e += 32) {
-                            const int pix = WF.irr_pix[e];
-                            const int i = pix >> 16, j = pix & 0xffff;
-                            if (j < s.pj0 || j > s.pj1) continue;
-                            ev.eval(i, j, v);
-                            const float wx = WF.irr_w[2 * e], wy = WF.irr_w[2 * e + 1];
-#pragma unroll
-                            for (int t = 0; t < NV; ++t) {
-                                ax[t] = fmaf(wx, v[t], ax[t]);
-                                ay[t] = fmaf(wy, v[t], ay[t]);
-                            }
-                        }
-#pragma unroll
-                        for (int t = 0; t < NV; ++t)
-                            for (int o = 16; o > 0; o >>= 1) {
-                                ax[t] += __shfl_xor_sync(0xffffffffu, ax[t], o);
-                                ay[t] += __shfl_xor_sync(0xffffffffu, ay[t], o);
-                            }
-                        if (lane == 0) {
-                            const int idx = row + sj - s.sj0;
-#pragma unroll
-                            for (int t = 0; t < NV; ++t) {
-                                S[idx * NV + t] = ax[t];
-                                S[(nsub + idx) * NV + t] = ay[t];
-                            }
-                        }
-                    }
-                }
-                __syncwarp();
-            }
-            __syncthreads();
-            if (gi == ng - 1 && tid == 0 && next_item < g.n_items) {
-                // the window is no longer read: stage the next actuator's
-                fence_proxy_async_smem();
-                issue_window(g, next_item, s_win, bar);
-            }
-            // finalize the subaperture sums of every sensor of the group, and
-            // stream zeros over every output column of the group (no loads)
-            {
-                int seq = 0;
-                for (int w = 0; w < g.n_wfs; ++w) {
-                    const ItemWfs &s = s_info[w];
-                    if (s.group != gi || s.empty) continue;
-                    const int nq = 2 * (s.si1 - s.si0 + 1) * (s.sj1 - s.sj0 + 1);
-                    int q = tid - seq % nth;
-                    if (q < 0) q += nth;
-                    for (; q < nq; q += nth) finalize_sub<NV>(s, g.wfs[w], s_arena + s.arena, q);
-                    seq += nq;
-                }
-                if (MODE != MODE_VJP) {
-                    for (int w = 0; w < g.n_wfs; ++w) {
-                        if (s_info[w].group != gi) continue;
-                        const DevPair &P = pairs[d * g.n_wfs + w];
-                        const int nv = g.wfs[w].nv, n2 = 2 * nv;
-                        const int nout = (MODE == MODE_FWD) ? 1 : 5;
-                        for (int t = 0; t < nout; ++t) {
-                            float *dst = (t == 0) ? P.im : P.dim[t - 1];
-                            if (!dst) continue;
-                            dst += (size_t)a * n2;
-                            if ((nv & 1) == 0) {
-                                const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-                                for (int q = tid; q < n2 / 4; q += nth) reinterpret_cast<float4 *>(dst)[q] = z;
-                            } else {
-                                const float2 z = make_float2(0.f, 0.f);
-                                for (int q = tid; q < nv; q += nth) reinterpret_cast<float2 *>(dst)[q] = z;
-                            }
-                        }
-                    }
-                }
-            }
-            __syncthreads();
-            // the box subapertures' slopes: scattered stores over the zeroed
-            // columns (MODE_FWD / MODE_TAN) or the VJP dot product
-            {
-                int seq = 0;
-                for (int w = 0; w < g.n_wfs; ++w) {
-                    const ItemWfs &s = s_info[w];
-                    if (s.group != gi) continue;
-                    const int pidx = d * g.n_wfs + w;
-                    const DevPair &P = pairs[pidx];
-                    if (MODE == MODE_VJP && !P.gim) continue;
-                    const DevWFS &WF = g.wfs[w];
-                    const int nv = WF.nv, n2 = 2 * nv;
-                    const int nsj = s.sj1 - s.sj0 + 1, nsub = (s.si1 - s.si0 + 1) * nsj;
-                    const int nq = s.empty ? 0 : 2 * nsub;
-                    const float *S = s_arena + s.arena + NV * (2 * s.nxc * s.nb + 2 * s.nyc * s.nbr);
-                    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-                    int q = tid - seq % nth;
-                    if (q < 0) q += nth;
-                    for (; q < nq; q += nth) {
-                        const int comp = q >= nsub ? 1 : 0, idx = q - comp * nsub;
-                        const int si = s.si0 + idx / nsj, sj = s.sj0 + idx % nsj;
-                        const int row = WF.vidx[si * WF.n_sub + sj];
-                        if (row < 0) continue;
-                        const float f = WF.fac[row];
-                        const size_t at = (size_t)a * n2 + comp * nv + row;
-                        if (MODE == MODE_VJP) {
-                            const float gv = P.gim[at];
-#pragma unroll
-                            for (int t = 0; t < 4; ++t) acc[t] = fmaf(gv, S[q * NV + t + 1] * f, acc[t]);
-                        } else {
-                            if (P.im) P.im[at] = S[q * NV] * f;
-                            if (MODE == MODE_TAN)
-#pragma unroll
-                                for (int t = 0; t < 4; ++t)
-                                    if (P.dim[t]) P.dim[t][at] = S[q * NV + t + 1] * f;
-                        }
-                    }
-                    seq += nq;
-                    if (MODE == MODE_VJP) {
-#pragma unroll
-                        for (int t = 0; t < 4; ++t) {
-                            float vsum = acc[t];
-                            for (int o = 16; o > 0; o >>= 1) vsum += __shfl_xor_sync(0xffffffffu, vsum, o);
-                            if (lane == 0 && vsum != 0.f) atomicAdd(&s_gp[pidx * 4 + t], (double)vsum);
-                        }
-                    }
-                }
-            }
-            __syncthreads();
+        for (int o = 0; o < NOUT; ++o) {
+            float *base = (o == 0) ? P.im : P.dim[o - 1];
+            cols[o] = base ? base + (size_t)a * n2 : nullptr;
+            if (!cols[o]) continue;
+            zero_rows(cols[o], 0, vr0, vec4, lane);
+            zero_rows(cols[o], vr1, nv + vr0, vec4, lane);
+            zero_rows(cols[o], nv + vr1, n2, vec4, lane);
         }
-        item = next_item;
+    }
+    if (s.empty) return;
+    const float *G = (MODE == MODE_VJP) ? P.gim + (size_t)a * n2 : nullptr;
+    float gacc[4] = {0.f, 0.f, 0.f, 0.f};
+    Eval<NV> ev;
+    ev.load(s, D.win + (size_t)a * D.win_stride, D.Wp, D.W, WF.M);
+    float *segx = wbuf;                                // [nsj + 1][2][NV]
+    float *sy0 = wbuf + (size_t)(nsj + 1) * 2 * NV;    // row boundary above the row: [nsj][2][NV]
+    float *sy1 = sy0 + (size_t)nsj * 2 * NV;           // row boundary below it
+    warp_segments<NV>(WF, s, ev, 1, s.si0, s.sj0, nsj, sy0, lane);
+    for (int si = s.si0; si <= s.si1; ++si) {
+        warp_segments<NV>(WF, s, ev, 0, si, s.sj0, nsj + 1, segx, lane);
+        warp_segments<NV>(WF, s, ev, 1, si + 1, s.sj0, nsj, sy1, lane);
+        __syncwarp();
+        // pupil-edge sums of the row's box subapertures that have edge pixels
+        // (the whole warp on each, both axes from one resample per pixel)
+        float *eb = wbuf + (size_t)(3 * nsj + 1) * 2 * NV;   // [nsj][2][NV], after both y rows
+        for (int c0 = 0; c0 < nsj; c0 += 32) {
+            // which of the next 32 box subapertures have edge pixels (one load each)
+            const int cl = c0 + lane;
+            bool has = false;
+            if (cl < nsj) {
+                const int q = si * WF.n_sub + s.sj0 + cl;
+                has = WF.irr_sub[q + 1] > WF.irr_sub[q];
+                if (!has)
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) {
+                        eb[(size_t)cl * 2 * NV + v] = 0.f;
+                        eb[(size_t)cl * 2 * NV + NV + v] = 0.f;
+                    }
+            }
+            unsigned m = __ballot_sync(0xffffffffu, has);
+            while (m) {
+                const int c = c0 + __ffs(m) - 1;
+                m &= m - 1;
+                float ax[NV], ay[NV];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) ax[v] = ay[v] = 0.f;
+                edge_sum<NV>(WF, s, ev, si, s.sj0 + c, lane, 32, ax, ay);
+#pragma unroll
+                for (int v = 0; v < NV; ++v)
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        ax[v] += __shfl_xor_sync(0xffffffffu, ax[v], o);
+                        ay[v] += __shfl_xor_sync(0xffffffffu, ay[v], o);
+                    }
+                if (lane == 0)
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) {
+                        eb[(size_t)c * 2 * NV + v] = ax[v];
+                        eb[(size_t)c * 2 * NV + NV + v] = ay[v];
+                    }
+            }
+        }
+        __syncwarp();
+        // slopes of the box subapertures (one lane each), zeros for the
+        // row's other valid subapertures: rows [vrow[si], vrow[si + 1])
+        int rlo = INT_MAX, rhi = -1;
+        for (int c = lane; c < nsj; c += 32) {
+            const int sj = s.sj0 + c;
+            const int r = WF.vidx[si * WF.n_sub + sj];
+            if (r < 0) continue;
+            rlo = min(rlo, r);
+            rhi = max(rhi, r);
+            float vx[NV], vy[NV];
+            const float f = WF.fac[r];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                vx[v] = (segx[(size_t)(c + 1) * 2 * NV + v] - segx[(size_t)c * 2 * NV + NV + v] +
+                         eb[(size_t)c * 2 * NV + v]) * f;
+                vy[v] = (sy1[(size_t)c * 2 * NV + v] - sy0[(size_t)c * 2 * NV + NV + v] +
+                         eb[(size_t)c * 2 * NV + NV + v]) * f;
+            }
+            if constexpr (MODE == MODE_VJP) {
+                const float gx = G[r], gy = G[nv + r];
+#pragma unroll
+                for (int k2 = 0; k2 < 4; ++k2) gacc[k2] = fmaf(gx, vx[1 + k2], fmaf(gy, vy[1 + k2], gacc[k2]));
+            } else {
+#pragma unroll
+                for (int o = 0; o < NOUT; ++o)
+                    if (cols[o]) {
+                        cols[o][r] = vx[o];
+                        cols[o][nv + r] = vy[o];
+                    }
+            }
+        }
+        if constexpr (MODE != MODE_VJP) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                rlo = min(rlo, __shfl_xor_sync(0xffffffffu, rlo, o));
+                rhi = max(rhi, __shfl_xor_sync(0xffffffffu, rhi, o));
+            }
+            const int ra = WF.vrow[si], rb = WF.vrow[si + 1];
+            const int za = rhi < 0 ? rb : rlo, zb = rhi < 0 ? rb : rhi + 1;   // box rows: [za, zb)
+#pragma unroll
+            for (int o = 0; o < NOUT; ++o)
+                if (cols[o]) {
+                    zero_rows(cols[o], ra, za, false, lane);
+                    zero_rows(cols[o], zb, rb, false, lane);
+                    zero_rows(cols[o], nv + ra, nv + za, false, lane);
+                    zero_rows(cols[o], nv + zb, nv + rb, false, lane);
+                }
+        }
+        __syncwarp();
+        float *t = sy0;
+        sy0 = sy1;
+        sy1 = t;
     }
     if (MODE == MODE_VJP) {
-        __syncthreads();
-        const int np = g.n_dm * g.n_wfs;
-        for (int q = tid; q < np * 4; q += nth)
-            if (s_gp[q] != 0.0) atomicAdd(&gp[q], s_gp[q]);
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) {
+            float vsum = gacc[k2];
+            for (int o = 16; o > 0; o >>= 1) vsum += __shfl_xor_sync(0xffffffffu, vsum, o);
+            if (lane == 0 && vsum != 0.f) atomicAdd(&gp[pidx * 4 + k2], (double)vsum);
+        }
     }
 }
 
-size_t im_smem_bytes(const Geo &g) {
-    return (size_t)g.max_win_floats * 4 + 16 + sizeof(ItemWfs) * SYNIM_MAX_WFS +
-           (size_t)g.arena_floats * 4;
+// One warp per (actuator, sensor) column, the columns of one actuator in
+// consecutive warps so that they share its window through L1.  Warps never
+// wait for one another.
+template <int MODE>
+__global__ void __launch_bounds__(256, (MODE == MODE_FWD) ? 4 : 2)
+k_im(const __grid_constant__ Geo g, const DevPair *__restrict__ pairs, int *__restrict__ counter,
+     int *__restrict__ err, double *__restrict__ gp) {
+    constexpr int NV = (MODE == MODE_FWD) ? 1 : 5;
+    extern __shared__ __align__(16) float smem_f[];
+    (void)counter;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    float *wbuf = smem_f + (size_t)warp * g.seg_floats;
+    const long n_units = (long)g.n_items * g.n_wfs;
+    for (long u = (long)blockIdx.x * nw + warp; u < n_units; u += (long)gridDim.x * nw) {
+        const int item = (int)(u / g.n_wfs), w = (int)(u - (long)item * g.n_wfs);
+        int d, a;
+        decode_item(g, item, d, a);
+        warp_column<MODE, NV>(g, pairs, d, a, w, wbuf, g.seg_floats, lane, err, gp);
+    }
 }
+
+size_t im_smem_bytes(const Geo &g) { return (size_t)8 * g.seg_floats * 4; }
 
 template <int MODE>
 static cudaError_t prepare_one(int threads, size_t smem, int *bps) {

@@ -443,10 +443,8 @@ extern "C" synim_status synim_im_compute_noalloc(const synim_dm_desc *dm, const 
     pair.pst = ptr(L.pst);
     pair.xcc = ptr(L.lines);
     pair.ycc = pair.xcc + (size_t)M * (n + 1);
-    const long long arena = (arena_need(Dh, Wh, pair.Ai, 1) + 31) / 32 * 32;
-    pair.arena_off = 0;
-    pair.arena_len = (int)arena;
-    pair.group = 0;
+    pair.vec4 = ((2 * nv) % 4 == 0 && (reinterpret_cast<uintptr_t>(im) & 15u) == 0) ? 1 : 0;
+    const long long seg = (seg_need(Dh, Wh, pair.Ai, 1) + 3) / 4 * 4;
     DevPair *d_pair = reinterpret_cast<DevPair *>(ptr(L.pair));
     // pageable source: the copy is staged before cudaMemcpyAsync returns
     if ((e = cudaMemcpyAsync(d_pair, &pair, sizeof(pair), cudaMemcpyHostToDevice, st)) != cudaSuccess)
@@ -462,26 +460,24 @@ extern "C" synim_status synim_im_compute_noalloc(const synim_dm_desc *dm, const 
     F.n_sub = n; F.M = M; F.k = k; F.nv = nv; F.CH = Wh.CH;
     g.n_dm = 1; g.n_wfs = 1; g.n_items = n_act;
     g.order_dm[0] = 0; g.order_start[0] = 0; g.order_start[1] = n_act;
-    g.max_win_floats = stride;
-    g.arena_floats = (int)arena;
-    g.n_groups[0] = 1;
+    g.seg_floats = (int)seg;
     const size_t smem = im_smem_bytes(g);
     int dev_max = 0, n_sm = 0, bps = 0;
     cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    if (smem + 8192 > (size_t)dev_max) return na_fail(SYNIM_ERR_SHAPE, "support window too large for shared memory");
-    if ((e = im_prepare(MODE_FWD, 512, smem, &bps)) != cudaSuccess || bps < 1)
+    if (smem > (size_t)dev_max) return na_fail(SYNIM_ERR_SHAPE, "boundary segments exceed the shared memory of a CTA");
+    if ((e = im_prepare(MODE_FWD, 256, smem, &bps)) != cudaSuccess || bps < 1)
         return na_fail(SYNIM_ERR_CUDA, "IM kernel attributes");
     const int grid = std::max(1, std::min(n_act, n_sm * bps));
     if ((e = cudaMemsetAsync(hdr, 0, 2 * sizeof(int), st)) != cudaSuccess ||
         (e = launch_pst(g, d_pair, M * M, M * (n + 1), st)) != cudaSuccess ||
-        (e = launch_im(MODE_FWD, g, d_pair, hdr + H_COUNTER, hdr + H_ERR, nullptr, grid, 512, smem, st)) != cudaSuccess)
+        (e = launch_im(MODE_FWD, g, d_pair, hdr + H_COUNTER, hdr + H_ERR, nullptr, grid, 256, smem, st)) != cudaSuccess)
         return na_fail(SYNIM_ERR_CUDA, cudaGetErrorString(e));
     int err_flag = 0;
     if ((e = cudaMemcpyAsync(&err_flag, hdr + H_ERR, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
         (e = cudaStreamSynchronize(st)) != cudaSuccess)
         return na_fail(SYNIM_ERR_CUDA, cudaGetErrorString(e));
     if (err_flag & ERR_TIMEOUT) return na_fail(SYNIM_ERR_TIMEOUT, "window staging wait timed out");
-    if (err_flag & ERR_ARENA) return na_fail(SYNIM_ERR_SHAPE, "subaperture accumulators exceeded the arena");
+    if (err_flag & ERR_ARENA) return na_fail(SYNIM_ERR_SHAPE, "slope values exceeded their shared-memory buffer");
     return SYNIM_OK;
 }
