@@ -38,9 +38,9 @@ METRIC = "IM actuator-columns/s at <=1e-5 rel err vs FP64 oracle; % of HBM roofl
 UNIT = "columns/s"
 
 # DRAM bytes (read + write) of one k_im launch on the MCAO workload, from the
-# ncu capture summarised in profiles/k_im_mcao.md; valid only for the kernel
-# source whose hash is recorded with it.
-TRAFFIC = {"kernel_sha1": None, "bytes_per_launch": None}
+# one-pass ncu capture summarised in profiles/k_im_mcao_dram_full.md; valid only
+# for the kernel source whose hash is recorded with it.
+TRAFFIC = {"kernel_sha1": "3b8134129102ae511dc451abb25d72bd088a7bde", "bytes_per_launch": 138.97e6 + 1.33e9}
 
 
 def kernel_sha1() -> str:
