@@ -292,7 +292,7 @@ def run_synim(args):
         t = torch.empty(dm.ifs.shape, dtype=torch.float32, pin_memory=True)
         t.numpy()[...] = dm.ifs
         dm.ifs = t
-    s = SynIM(wl.dms, wl.wfss, profile=True)
+    s = SynIM(wl.dms, wl.wfss, profile=True, autotune=True)
     outs = s.alloc_outputs()
     n_pairs = len(wl.dms) * len(wl.wfss)
     cols_per_step = sum(dm.n_act for dm in wl.dms) * len(wl.wfss)
@@ -304,7 +304,8 @@ def run_synim(args):
     for _ in range(args.warmup):
         s.compute(step_misregs(wl, rng), outs)
     s.check()
-    s.kernel_ms()  # drop warm-up launches
+    s.kernel_ms()  # drop warm-up launches (the first one also ran the autotuner)
+    tuned = s.tuning(0)
     mis = [step_misregs(wl, rng) for _ in range(args.steps)]
     clocks = ClockSampler(local)
     barrier()
@@ -359,7 +360,9 @@ def run_synim(args):
                    "n_dm": len(wl.dms), "n_wfs": len(wl.wfss), "n_pairs": n_pairs,
                    "columns_per_step": cols_per_step, "im_bytes_per_step": im_bytes,
                    "l2": "working set (1.4 GB written per step) exceeds L2; no flush",
-                   "parallelism": f"replicas x{world} (independent jobs, no collective on the data path)"},
+                   "parallelism": f"replicas x{world} (independent jobs, no collective on the data path)",
+                   "launch_shape": None if tuned is None else {"threads_per_cta": tuned[0], "lanes_per_segment": tuned[1],
+                                                               "picked_by": "autotuner (first call)"}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                      "kernel": "k_im<0>", "alg_bytes_per_launch": alg_bytes,

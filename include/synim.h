@@ -101,9 +101,11 @@ typedef struct {
 /* Creation options; pass NULL for defaults. */
 typedef struct {
     int32_t threads_per_cta; /* 0 = default (256); a multiple of 32 in 64..256 */
-    int32_t ctas_per_sm;     /* 0 = default / autotuned */
+    int32_t ctas_per_sm;     /* reserved, 0 (every column is one warp of one launch) */
     int32_t use_graph;       /* 1 = replay a CUDA graph per stream; 0 = plain launches */
-    int32_t autotune;        /* 1 = time candidate launch shapes at the first compute */
+    int32_t autotune;        /* 1 = at the first call of each mode, time the candidate launch
+                                shapes (128 or 256 threads x 2, 4 or 8 lanes per boundary
+                                segment) on that call's inputs and keep the fastest */
     int32_t profile;         /* 1 = record CUDA events around every IM-kernel launch
                                 (read back with synim_im_kernel_ms) */
 } synim_opts;
@@ -328,6 +330,13 @@ typedef struct {
  * Synchronous. */
 synim_status synim_cnn_train(synim_ctx *ctx, const double *params, int64_t n, const synim_train_opts *opts,
                              double *loss_out, void *cuda_stream);
+
+/* Launch shape chosen by the autotuner for mode 0 (IM), 1 (tangents) or 2
+ * (adjoint): threads per CTA, lanes per boundary segment, and the mean
+ * kernel time of the winner (ms).  SYNIM_ERR_NOT_CONVERGED (outputs hold the
+ * defaults) while that mode has not been tuned. */
+synim_status synim_im_tuning(const synim_ctx *ctx, int32_t mode, int32_t *threads, int32_t *seg_lanes,
+                             double *ms);
 
 /* Free all device memory of the context (waits for its streams). NULL is a no-op. */
 void synim_im_destroy(synim_ctx *ctx);

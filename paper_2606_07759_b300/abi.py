@@ -86,6 +86,8 @@ SIGNATURES = {
                                  ctypes.POINTER(c_float), c_void_p]),
     "synim_cnn_train": (c_int32, [c_void_p, c_void_p, c_int64, ctypes.POINTER(synim_train_opts),
                                   ctypes.POINTER(c_double), c_void_p]),
+    "synim_im_tuning": (c_int32, [c_void_p, c_int32, ctypes.POINTER(c_int32), ctypes.POINTER(c_int32),
+                                  ctypes.POINTER(c_double)]),
     "synim_im_destroy": (None, [c_void_p]),
     "synim_status_string": (ctypes.c_char_p, [c_int32]),
     "synim_last_error": (ctypes.c_char_p, [c_void_p]),

@@ -358,6 +358,7 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
         if (opts->threads_per_cta > 0) c->threads = opts->threads_per_cta;
         c->ctas_per_sm = std::max(0, opts->ctas_per_sm);
         c->use_graph = opts->use_graph != 0;
+        c->autotune = opts->autotune != 0;
         c->profile = opts->profile != 0;
     }
     if (c->threads % 32 != 0 || c->threads < 64 || c->threads > 256) {
@@ -674,17 +675,73 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
                         " bytes of shared memory per CTA; lower the grid or raise support_eps");
     c->seg_floats = (int)cap;
     g.seg_floats = c->seg_floats;
+    // launch shape: the tuned one once the autotuner has run for this mode
+    int threads = c->threads;
+    g.seg_lanes = 0;
+    if (c->tuned[mode]) {
+        threads = c->tune_threads[mode];
+        g.seg_lanes = c->tune_lanes[mode];
+    }
     const size_t smem = im_smem_bytes(g);
+    const long long units = (long long)c->geo.n_items * c->n_wfs;
+    auto grid_for = [&](int th) {
+        const long long warps = th / 32;
+        return (int)std::max<long long>(1, std::min<long long>((units + warps - 1) / warps, 1LL << 30));
+    };
     int bps = 0;
-    if ((e = im_prepare(mode, c->threads, smem, &bps)) != cudaSuccess) return cuda_fail(c, e, "kernel attributes");
+    if ((e = im_prepare(mode, threads, smem, &bps)) != cudaSuccess) return cuda_fail(c, e, "kernel attributes");
     if (bps < 1) return fail(c, SYNIM_ERR_SHAPE, "IM kernel does not fit on an SM");
-    const long long units = (long long)c->geo.n_items * c->n_wfs, warps = c->threads / 32;
-    const int grid = (int)std::max<long long>(1, std::min<long long>((units + warps - 1) / warps, 1LL << 30));
+    int grid = grid_for(threads);
     if ((e = cudaMemcpyAsync(c->d_pairs, hp, sizeof(DevPair) * np, cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return cuda_fail(c, e, "parameter upload");
     cudaEventRecord(c->slot_ev[slot], s);
     c->slot_used[slot] = true;
     c->slot = (slot + 1) % NSLOT;
+    if (c->autotune && !c->tuned[mode]) {
+        // autotuner: time each candidate launch shape on this call's inputs
+        // (three launches after a warm-up) and keep the fastest for the mode
+        static const int cand_threads[] = {128, 256};
+        static const int cand_lanes[] = {2, 4, 8};
+        cudaEvent_t t0 = nullptr, t1 = nullptr;
+        if ((e = cudaEventCreate(&t0)) != cudaSuccess || (e = cudaEventCreate(&t1)) != cudaSuccess)
+            return cuda_fail(c, e, "autotune events");
+        float best = 3e38f;
+        int best_th = threads, best_l = 0;
+        if ((e = launch_pst(g, c->d_pairs, c->max_mm, c->max_lines, s)) != cudaSuccess) return cuda_fail(c, e, "autotune");
+        for (int th : cand_threads)
+            for (int l : cand_lanes) {
+                Geo gt = g;
+                gt.seg_lanes = l;
+                int b2 = 0;
+                if ((e = im_prepare(mode, th, smem, &b2)) != cudaSuccess || b2 < 1) continue;
+                const int gr = grid_for(th);
+                float ms = 0.f;
+                e = launch_im(mode, gt, c->d_pairs, c->d_counter, c->d_err, c->d_gp, gr, th, smem, s);
+                if (e == cudaSuccess) e = cudaEventRecord(t0, s);
+                for (int r = 0; r < 3 && e == cudaSuccess; ++r)
+                    e = launch_im(mode, gt, c->d_pairs, c->d_counter, c->d_err, c->d_gp, gr, th, smem, s);
+                if (e == cudaSuccess) e = cudaEventRecord(t1, s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+                if (e != cudaSuccess) break;
+                if (ms < best) {
+                    best = ms;
+                    best_th = th;
+                    best_l = l;
+                }
+            }
+        cudaEventDestroy(t0);
+        cudaEventDestroy(t1);
+        if (e != cudaSuccess) return cuda_fail(c, e, "autotune");
+        c->tuned[mode] = true;
+        c->tune_threads[mode] = best_th;
+        c->tune_lanes[mode] = best_l;
+        c->tune_ms[mode] = best / 3.f;
+        threads = best_th;
+        g.seg_lanes = best_l;
+        if ((e = im_prepare(mode, threads, smem, &bps)) != cudaSuccess) return cuda_fail(c, e, "kernel attributes");
+        grid = grid_for(threads);
+    }
     if (mode == MODE_VJP && (e = cudaMemsetAsync(c->d_gp, 0, sizeof(double) * np * 4, s)) != cudaSuccess)
         return cuda_fail(c, e, "vjp clear");
     // profiling: pick the event pair of this launch (collect the oldest if the ring is full)
@@ -711,12 +768,12 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
         cudaError_t r = cudaMemsetAsync(c->d_counter, 0, sizeof(int), q);
         if (r == cudaSuccess) r = launch_pst(g, c->d_pairs, c->max_mm, c->max_lines, q);
         if (r == cudaSuccess && a0) r = cudaEventRecordWithFlags(a0, q, rf);
-        if (r == cudaSuccess) r = launch_im(mode, g, c->d_pairs, c->d_counter, c->d_err, c->d_gp, grid, c->threads, smem, q);
+        if (r == cudaSuccess) r = launch_im(mode, g, c->d_pairs, c->d_counter, c->d_err, c->d_gp, grid, threads, smem, q);
         if (r == cudaSuccess && b0) r = cudaEventRecordWithFlags(b0, q, rf);
         return r;
     };
     if (c->use_graph) {
-        const auto key = std::make_tuple(mode, smem, grid, c->threads);
+        const auto key = std::make_tuple(mode, smem, grid, threads * 16 + g.seg_lanes);
         auto it = c->graphs.find(key);
         if (it == c->graphs.end()) {
             GraphEntry ge;
@@ -773,6 +830,16 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
 }
 
 }  // namespace
+
+extern "C" synim_status synim_im_tuning(const synim_ctx *ctx, int32_t mode, int32_t *threads, int32_t *seg_lanes,
+                                        double *ms) {
+    if (!ctx || mode < 0 || mode > 2) return SYNIM_ERR_INVALID_ARG;
+    const bool t = ctx->tuned[mode];
+    if (threads) *threads = t ? ctx->tune_threads[mode] : ctx->threads;
+    if (seg_lanes) *seg_lanes = t ? ctx->tune_lanes[mode] : 0;
+    if (ms) *ms = t ? (double)ctx->tune_ms[mode] : 0.0;
+    return t ? SYNIM_OK : SYNIM_ERR_NOT_CONVERGED;
+}
 
 extern "C" synim_status synim_im_compute(synim_ctx *ctx, const synim_misreg *mis, float *const *im,
                                          void *cuda_stream) {

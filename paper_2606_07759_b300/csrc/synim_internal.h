@@ -83,6 +83,7 @@ struct Geo {
     int order_dm[SYNIM_MAX_DM];         // DM processed at each position (costliest first)
     int order_start[SYNIM_MAX_DM + 1];  // item prefix in processing order
     int seg_floats;      // per-warp shared-memory buffer of the IM kernel (floats)
+    int seg_lanes;       // lanes per boundary segment for k <= 32 (2, 4 or 8); 0 = by k
 };
 
 enum { ERR_TIMEOUT = 1, ERR_ARENA = 2 };
@@ -160,6 +161,10 @@ struct synim_ctx {
     uint8_t *d_pst = nullptr, *d_lines = nullptr;
     int max_mm = 0, max_lines = 0;
     int threads = 256, ctas_per_sm = 0;
+    bool autotune = false;
+    bool tuned[3] = {false, false, false};
+    int tune_threads[3] = {0, 0, 0}, tune_lanes[3] = {0, 0, 0};
+    float tune_ms[3] = {0.f, 0.f, 0.f};
     bool use_graph = true;
     int seg_floats = 0;
     std::map<std::tuple<int, size_t, int, int>, synim::GraphEntry> graphs;

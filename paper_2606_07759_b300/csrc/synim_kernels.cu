@@ -335,6 +335,17 @@ struct Eval {
         }
     }
 
+    // Bilinear value at padded-window coordinates (x, y) (no tangents).
+    __device__ __forceinline__ float bil_at(float x, float y) const {
+        if (!(x > 0.f && x < Wf1 && y > 0.f && y < Wf1)) return 0.f;
+        const float fx0 = floorf(x), fy0 = floorf(y);
+        const float fx = x - fx0, fy = y - fy0;
+        const float *q = win + (int)fy0 * Wp + (int)fx0;
+        const float v00 = q[0], v10 = q[1], v01 = q[Wp], v11 = q[Wp + 1];
+        const float top = fmaf(fx, v10 - v00, v00), bot = fmaf(fx, v11 - v01, v01);
+        return fmaf(fy, bot - top, top);
+    }
+
     // Edge repair step 3 (Sec. 2.3) at a ring pixel: mean over the valid
     // cardinal directions of 2 P1 - P2 (or P1); P1, P2 must be strict core.
     __device__ __forceinline__ void ring(int i, int j, float *v) const {
@@ -484,35 +495,71 @@ __device__ __forceinline__ void seg_compute(const DevWFS &WF, const SegRows &r, 
                                             int lane0, int lstep, float *A, float *B) {
     if (!r.inmask) return;
     const int n1 = WF.n_sub + 1, l0 = r.l0, inmask = r.inmask;
-    for (int u = r.ua + lane0; u <= r.ub; u += lstep) {
-        const int c = __ldg(r.cc + (long)u * n1);
-        const int cl0 = (inmask & 1) ? (c >> 4) & 3 : 0, cl1 = (inmask & 2) ? (c >> 6) & 3 : 0;
-        const float wa0 = (float)(c & 1), wb0 = (float)((c >> 1) & 1);
-        const float wa1 = (float)((c >> 2) & 1), wb1 = (float)((c >> 3) & 1);
-        float v0[NV], v1[NV];
-        if (cl0 == 2 || cl1 == 2) {
-#pragma unroll
-            for (int t = 0; t < NV; ++t) v0[t] = v1[t] = 0.f;
-            if (cl0 == 1) ev.bil(axis ? l0 : u, axis ? u : l0, v0);
-            else if (cl0 == 2) ev.ring(axis ? l0 : u, axis ? u : l0, v0);
-            if (cl1 == 1) ev.bil(axis ? l0 + 1 : u, axis ? u : l0 + 1, v1);
-            else if (cl1 == 2) ev.ring(axis ? l0 + 1 : u, axis ? u : l0 + 1, v1);
-        } else {
-            // both pixels core or zero: two independent gathers, zero weight
-            // for a zero-class pixel
-            ev.bil(axis ? l0 : u, axis ? u : l0, v0);
-            ev.bil(axis ? l0 + 1 : u, axis ? u : l0 + 1, v1);
-            if (cl0 == 0)
-#pragma unroll
-                for (int t = 0; t < NV; ++t) v0[t] = 0.f;
-            if (cl1 == 0)
-#pragma unroll
-                for (int t = 0; t < NV; ++t) v1[t] = 0.f;
+    const int u0 = r.ua + lane0;
+    if (u0 > r.ub) return;
+    const uint8_t *cp = r.cc + (long)u0 * n1;
+    const int cstep = lstep * n1;
+    if constexpr (NV == 1) {
+        // the sampled DM points move by a constant step along the line; the
+        // second line pixel is one sensor pixel across
+        const float di = (float)((axis ? l0 : u0) - ev.pi0), dj = (float)((axis ? u0 : l0) - ev.pj0);
+        const float x0 = fmaf(ev.a00, dj, fmaf(ev.a01, di, ev.xo));
+        const float y0 = fmaf(ev.a10, dj, fmaf(ev.a11, di, ev.yo));
+        // lstep is a power of two: the step is exact, each point one rounding
+        const float sx = (float)lstep * (axis ? ev.a00 : ev.a01), sy = (float)lstep * (axis ? ev.a10 : ev.a11);
+        const float ox = axis ? ev.a01 : ev.a00, oy = axis ? ev.a11 : ev.a10;
+        float qf = 0.f;
+        for (int u = u0; u <= r.ub; u += lstep, qf += 1.f, cp += cstep) {
+            const float x = fmaf(qf, sx, x0), y = fmaf(qf, sy, y0);
+            const int c = __ldg(cp);
+            const int cl0 = (inmask & 1) ? (c >> 4) & 3 : 0, cl1 = (inmask & 2) ? (c >> 6) & 3 : 0;
+            float v0, v1;
+            if (cl0 == 2 || cl1 == 2) {
+                float t0[1] = {0.f}, t1[1] = {0.f};
+                if (cl0 == 1) ev.bil(axis ? l0 : u, axis ? u : l0, t0);
+                else if (cl0 == 2) ev.ring(axis ? l0 : u, axis ? u : l0, t0);
+                if (cl1 == 1) ev.bil(axis ? l0 + 1 : u, axis ? u : l0 + 1, t1);
+                else if (cl1 == 2) ev.ring(axis ? l0 + 1 : u, axis ? u : l0 + 1, t1);
+                v0 = t0[0];
+                v1 = t1[0];
+            } else {
+                v0 = cl0 ? ev.bil_at(x, y) : 0.f;
+                v1 = cl1 ? ev.bil_at(x + ox, y + oy) : 0.f;
+            }
+            A[0] += ((c & 1) ? v0 : 0.f) + ((c & 4) ? v1 : 0.f);
+            B[0] += ((c & 2) ? v0 : 0.f) + ((c & 8) ? v1 : 0.f);
         }
+    } else {
+        for (int u = u0; u <= r.ub; u += lstep, cp += cstep) {
+            const int c = __ldg(cp);
+            const int cl0 = (inmask & 1) ? (c >> 4) & 3 : 0, cl1 = (inmask & 2) ? (c >> 6) & 3 : 0;
+            const float wa0 = (c & 1) ? 1.f : 0.f, wb0 = (c & 2) ? 1.f : 0.f;
+            const float wa1 = (c & 4) ? 1.f : 0.f, wb1 = (c & 8) ? 1.f : 0.f;
+            float v0[NV], v1[NV];
+            if (cl0 == 2 || cl1 == 2) {
 #pragma unroll
-        for (int t = 0; t < NV; ++t) {
-            A[t] = fmaf(wa0, v0[t], fmaf(wa1, v1[t], A[t]));
-            B[t] = fmaf(wb0, v0[t], fmaf(wb1, v1[t], B[t]));
+                for (int t = 0; t < NV; ++t) v0[t] = v1[t] = 0.f;
+                if (cl0 == 1) ev.bil(axis ? l0 : u, axis ? u : l0, v0);
+                else if (cl0 == 2) ev.ring(axis ? l0 : u, axis ? u : l0, v0);
+                if (cl1 == 1) ev.bil(axis ? l0 + 1 : u, axis ? u : l0 + 1, v1);
+                else if (cl1 == 2) ev.ring(axis ? l0 + 1 : u, axis ? u : l0 + 1, v1);
+            } else {
+                // both pixels core or zero: two independent gathers, zero
+                // weight for a zero-class pixel
+                ev.bil(axis ? l0 : u, axis ? u : l0, v0);
+                ev.bil(axis ? l0 + 1 : u, axis ? u : l0 + 1, v1);
+                if (cl0 == 0)
+#pragma unroll
+                    for (int t = 0; t < NV; ++t) v0[t] = 0.f;
+                if (cl1 == 0)
+#pragma unroll
+                    for (int t = 0; t < NV; ++t) v1[t] = 0.f;
+            }
+#pragma unroll
+            for (int t = 0; t < NV; ++t) {
+                A[t] = fmaf(wa0, v0[t], fmaf(wa1, v1[t], A[t]));
+                B[t] = fmaf(wb0, v0[t], fmaf(wb1, v1[t], B[t]));
+            }
         }
     }
 }
@@ -568,8 +615,9 @@ __device__ __forceinline__ void zero_rows(float *col, int r0, int r1, bool vec4,
 // seg[(q) * 2 NV + v] = A, seg[(q) * 2 NV + NV + v] = B of the q-th segment.
 template <int NV>
 __device__ __forceinline__ void warp_segments(const DevWFS &WF, const ItemWfs &s, const Eval<NV> &ev, int axis,
-                                              int fixed, int first, int count, float *seg, int lane) {
-    const int L = (WF.k > 32) ? 32 : (WF.k > 16 ? 8 : 4);   // lanes per segment
+                                              int fixed, int first, int count, float *seg, int lane, int lanes) {
+    // lanes per segment: a whole warp for large k, else the tuned or default count
+    const int L = (WF.k > 32) ? 32 : (lanes > 0 ? lanes : (WF.k > 16 ? 8 : 4));
     const int per = 32 / L;
     const int grp = lane / L, q = lane - grp * L;
     // x: boundary first + idx over subaperture row `fixed`; y: boundary
@@ -583,31 +631,12 @@ __device__ __forceinline__ void warp_segments(const DevWFS &WF, const ItemWfs &s
             const SegRows r = seg_rows(WF, s, axis, axis ? fixed : first + idx, axis ? first + idx : fixed);
             seg_compute<NV>(WF, r, ev, axis, q, L, A, B);
         }
-        if (L == 4) {
+        for (int o = L >> 1; o > 0; o >>= 1)
 #pragma unroll
-            for (int v = 0; v < NV; ++v)
-#pragma unroll
-                for (int o = 2; o > 0; o >>= 1) {
-                    A[v] += __shfl_xor_sync(0xffffffffu, A[v], o);
-                    B[v] += __shfl_xor_sync(0xffffffffu, B[v], o);
-                }
-        } else if (L == 8) {
-#pragma unroll
-            for (int v = 0; v < NV; ++v)
-#pragma unroll
-                for (int o = 4; o > 0; o >>= 1) {
-                    A[v] += __shfl_xor_sync(0xffffffffu, A[v], o);
-                    B[v] += __shfl_xor_sync(0xffffffffu, B[v], o);
-                }
-        } else {
-#pragma unroll
-            for (int v = 0; v < NV; ++v)
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    A[v] += __shfl_xor_sync(0xffffffffu, A[v], o);
-                    B[v] += __shfl_xor_sync(0xffffffffu, B[v], o);
-                }
-        }
+            for (int v = 0; v < NV; ++v) {
+                A[v] += __shfl_xor_sync(0xffffffffu, A[v], o);
+                B[v] += __shfl_xor_sync(0xffffffffu, B[v], o);
+            }
         if (q == 0 && idx < count)
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
@@ -660,10 +689,10 @@ __device__ __forceinline__ void warp_column(const Geo &g, const DevPair *__restr
     float *segx = wbuf;                                // [nsj + 1][2][NV]
     float *sy0 = wbuf + (size_t)(nsj + 1) * 2 * NV;    // row boundary above the row: [nsj][2][NV]
     float *sy1 = sy0 + (size_t)nsj * 2 * NV;           // row boundary below it
-    warp_segments<NV>(WF, s, ev, 1, s.si0, s.sj0, nsj, sy0, lane);
+    warp_segments<NV>(WF, s, ev, 1, s.si0, s.sj0, nsj, sy0, lane, g.seg_lanes);
     for (int si = s.si0; si <= s.si1; ++si) {
-        warp_segments<NV>(WF, s, ev, 0, si, s.sj0, nsj + 1, segx, lane);
-        warp_segments<NV>(WF, s, ev, 1, si + 1, s.sj0, nsj, sy1, lane);
+        warp_segments<NV>(WF, s, ev, 0, si, s.sj0, nsj + 1, segx, lane, g.seg_lanes);
+        warp_segments<NV>(WF, s, ev, 1, si + 1, s.sj0, nsj, sy1, lane, g.seg_lanes);
         __syncwarp();
         // pupil-edge sums of the row's box subapertures that have edge pixels
         // (the whole warp on each, both axes from one resample per pixel)

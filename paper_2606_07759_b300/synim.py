@@ -37,7 +37,8 @@ class SynIM:
     """
 
     def __init__(self, dms: Sequence, wfss: Sequence, threads_per_cta: int = 0, ctas_per_sm: int = 0,
-                 use_graph: bool = True, profile: bool = False, device: Optional[torch.device] = None):
+                 use_graph: bool = True, profile: bool = False, device: Optional[torch.device] = None,
+                 autotune: bool = False):
         self._L = abi.load()
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.n_dm, self.n_wfs = len(dms), len(wfss)
@@ -80,7 +81,7 @@ class SynIM:
             d.obstruction = float(getattr(w, "obstruction", 0.0))
             d.slope_scale = float(getattr(w, "slope_scale", 1.0))
             ww[q] = d
-        opts = abi.synim_opts(int(threads_per_cta), int(ctas_per_sm), 1 if use_graph else 0, 0,
+        opts = abi.synim_opts(int(threads_per_cta), int(ctas_per_sm), 1 if use_graph else 0, 1 if autotune else 0,
                               1 if profile else 0)
         ctx = ctypes.c_void_p()
         with torch.cuda.device(self.device):
@@ -114,6 +115,12 @@ class SynIM:
         W = ctypes.c_int32()
         abi.check(self._L.synim_dm_window(self._ctx, d, ctypes.byref(W)), self._ctx)
         return int(W.value)
+
+    def tuning(self, mode: int = 0):
+        """(threads per CTA, lanes per segment, kernel ms) chosen by the autotuner, or None."""
+        th, ln, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+        st = self._L.synim_im_tuning(self._ctx, mode, ctypes.byref(th), ctypes.byref(ln), ctypes.byref(ms))
+        return (int(th.value), int(ln.value), float(ms.value)) if st == 0 else None
 
     def kernel_ms(self):
         """(summed device ms, launches) of the IM kernel since the last call (profile=True)."""

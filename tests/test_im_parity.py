@@ -157,3 +157,30 @@ def test_profiling_events_count_kernel_launches():
         ms, n = s.kernel_ms()
         assert n == 0 and ms == 0.0
         s.close()
+
+
+def test_autotuned_launch_matches_default():
+    # the autotuner times launch shapes on the first call of each mode and
+    # keeps the fastest; any shape computes the same IM up to summation order
+    from paper_2606_07759_b300.synim import SynIM
+    wl = W.mcao_batched(seed=12, scale=0.15)
+    a = SynIM(wl.dms, wl.wfss)
+    b = SynIM(wl.dms, wl.wfss, autotune=True)
+    assert b.tuning(0) is None
+    ra, rb = a.compute(wl.misregs), b.compute(wl.misregs)
+    b.check()
+    t = b.tuning(0)
+    assert t is not None and t[0] in (128, 256) and t[1] in (2, 4, 8) and t[2] > 0
+    for x, y in zip(ra, rb):
+        x, y = x.cpu().numpy().astype(np.float64), y.cpu().numpy().astype(np.float64)
+        peak = np.maximum(np.abs(x).max(axis=1), 1e-2 * max(np.abs(x).max(), 1e-30))
+        assert np.all(np.abs(x - y).max(axis=1) <= TOL * peak)
+    # the second call reuses the tuned shape (and its captured graph)
+    rc = b.compute(wl.misregs)
+    for y, z in zip(rb, rc):
+        assert torch.equal(y, z)
+    b.sensitivity(wl.misregs)
+    b.check()
+    assert b.tuning(1) is not None
+    a.close()
+    b.close()
