@@ -10,13 +10,15 @@
 // t = ((sx - c0) / r0, (sy - c1) / r1, (rot - c2) / r2, (mag - c3) / r3).
 // Loss: mean over the batch and the 4 outputs of the squared error; Adam.
 //
-// Kernels (BF16 operands, FP32 accumulation, mma.sync m16n8k16):
-//   k_conv<FWD>    implicit GEMM out[m][co] = sum_k im2col(in)[m][k] W[co][k],
-//                  m = (sample, oy, ox), k = (ky, kx, ci); + bias, ReLU, BF16;
-//   k_conv<DGRAD>  implicit GEMM of the transposed convolution: gradient of
-//                  the layer input, masked by its ReLU, BF16;
-//   k_wgrad        dW[co][k] = sum_m dz[m][co] im2col(in)[m][k], split over
-//                  m into per-CTA partials summed in a fixed order;
+// Kernels (BF16 operands, FP32 accumulation):
+//   k_conv_tc<FWD>    implicit GEMM out[m][co] = sum_k im2col(in)[m][k] W[co][k],
+//                     m = (sample, oy, ox), k = (ky, kx, ci); + bias, ReLU,
+//                     BF16; tcgen05.mma with TMEM accumulators;
+//   k_conv_tc<DGRAD>  implicit GEMM of the transposed convolution: gradient
+//                     of the layer input, masked by its ReLU, BF16;
+//   k_wgrad           dW[co][k] = sum_m dz[m][co] im2col(in)[m][k] (mma.sync
+//                     m16n8k16), split over m into per-CTA partials summed in
+//                     a fixed order;
 //   small kernels for the head (dense layer, loss), bias sums, Adam.
 // Parameters live as FP32 masters (flat vector, order W1 b1 W2 b2 W3 b3 Wfc
 // bfc; W[co][ky][kx][ci], Wfc[j][y][x][c]) with BF16 copies for the GEMMs.
@@ -33,12 +35,12 @@
 
 #include "synim_internal.h"
 #include "synim_mma.cuh"
+#include "synim_tc.cuh"
 
 namespace synim {
 
 constexpr int CH = 64;               // hidden channels
-constexpr int BM = 128, BN = 64, BK = 32, LDA = BK + 8;
-constexpr int kConvThreads = 128;
+constexpr int BM = 128;                // GEMM rows per tile
 constexpr int kWgThreads = 128;
 constexpr int kBatchCap = 256;       // samples per training / inference pass
 
@@ -57,7 +59,7 @@ struct CnnState {
     bf16 *x = nullptr, *a1 = nullptr, *a2 = nullptr, *a3 = nullptr;
     bf16 *dz1 = nullptr, *dz2 = nullptr, *dz3 = nullptr;
     float *out = nullptr, *loss = nullptr, *dout = nullptr;
-    float *wpart = nullptr, *bpart = nullptr;
+    float *wpart = nullptr;   // weight-gradient partials [splits][64 K + 64]
     long long wpart_floats = 0;
     float *tgt = nullptr;   // [kBatchCap][4] targets of the current batch
     int *perm = nullptr;    // [n_data]
@@ -65,13 +67,14 @@ struct CnnState {
     float *targets = nullptr;  // [n_data][4]
     long long n_data = 0, data_cap = 0;
     float *h_loss = nullptr;   // pinned [kBatchCap]
+    int *d_err = nullptr;      // bit 0: a bounded wait of the tensor-core convolution gave up
 };
 
 void cnn_destroy(CnnState *s) {
     if (!s) return;
     void *p[] = {s->master, s->adam_m, s->adam_v, s->grad, s->w1, s->w2, s->w3, s->w2t, s->w3t, s->x,
                  s->a1, s->a2, s->a3, s->dz1, s->dz2, s->dz3, s->out, s->loss, s->dout,
-                 s->wpart, s->bpart, s->tgt, s->perm, s->data, s->targets};
+                 s->wpart, s->tgt, s->perm, s->data, s->targets, s->d_err};
     for (void *q : p) cudaFree(q);
     cudaFreeHost(s->h_loss);
     delete s;
@@ -93,129 +96,305 @@ struct ConvArgs {
     int B, Hi, Ho, stride;
 };
 
-template <bool DGRAD, int CIN>
-__global__ void __launch_bounds__(kConvThreads) k_conv(const ConvArgs a) {
-    __shared__ __align__(16) bf16 As[2][BM][LDA];
-    __shared__ __align__(16) bf16 Bs[2][BN][LDA];
-    constexpr int K = 9 * CIN;
-    constexpr int KT = K / BK;
-    const int Hr = DGRAD ? a.Hi : a.Ho;  // rows of the GEMM are pixels of this grid
-    const long long M = (long long)a.B * Hr * Hr;
-    const long long m0 = (long long)blockIdx.x * BM;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+// ---------------------------------------------------------------------------
+// The convolution and its transpose on the 5th-generation tensor cores
+// (tcgen05).
+//
+// One CTA walks 128-row tiles of the GEMM (rows = output pixels for the
+// forward pass, input pixels for the input gradient) with three warp roles:
+//   warps 0-3  gather, per 3x3 tap, each tile row's CIN channels (one pixel,
+//              zero outside the image) into a shared-memory stage laid out as
+//              K-major 8x16-byte core matrices; a stage holds one tap;
+//   warp 8     one lane issues tcgen05.mma 128 x 64 x 16 per 16 channels of
+//              the tap into a TMEM accumulator (two accumulators, so that the
+//              epilogue of one tile overlaps the MMAs of the next);
+//   warps 4-7  read the accumulator back (warp 4 + e owns TMEM lanes
+//              32 e .. 32 e + 31), add the bias and apply the ReLU (forward)
+//              or the ReLU mask of the layer input (input gradient), and
+//              store BF16 rows.
+// The weights (64 x 9 CIN, K-major) stay in shared memory for the whole
+// kernel.  Stages are handed over through mbarriers: full (128 producer
+// arrivals after their copies landed and were fenced for the async proxy),
+// empty (tcgen05.commit of the MMAs that read the stage); accumulators
+// through tfull (commit after a tile's last MMA) and tempty (128 epilogue
+// arrivals).  Every wait is bounded; a wait that gives up sets bit 1 of *err
+// and its role stops, so the kernel always ends.
+// ---------------------------------------------------------------------------
+constexpr int kTcThreads = 288;   // 4 producer warps, 4 epilogue warps, 1 MMA warp
+constexpr int kTcCols = 2 * CH;   // TMEM columns: two 64-column FP32 accumulators
 
-    // this thread loads GEMM row m0 + tid of A
-    const long long mrow = m0 + tid;
-    const bool row_ok = mrow < M;
-    int rb = 0, ry = 0, rx = 0;
-    if (row_ok) {
-        rb = (int)(mrow / ((long long)Hr * Hr));
-        const int r = (int)(mrow - (long long)rb * Hr * Hr);
-        ry = r / Hr;
-        rx = r - ry * Hr;
+template <int CIN>
+struct TcCfg {
+    static constexpr int K = 9 * CIN;
+    static constexpr int KG = CIN / 8;             // core-matrix columns per tap
+    static constexpr int A_BYTES = BM * CIN * 2;   // one tap of one 128-row tile
+    static constexpr int B_BYTES = CH * K * 2;     // all weights
+    static constexpr int STAGES = (CIN == 32) ? 6 : 4;
+    static constexpr int LAG = STAGES - 2;         // taps in flight per producer thread
+    static constexpr int N_BARS = 2 * STAGES + 4;
+    static constexpr size_t SMEM = 128 + B_BYTES + (size_t)STAGES * A_BYTES + 8 * N_BARS + 16;
+};
+
+// Tiles of the GEMM.  Forward: one class, rows m = (b, y, x) of the output
+// grid, all 9 taps.  Input gradient of a stride-2 convolution: the input
+// pixels fall by parity (cy, cx) into four classes, rows (b, py, px) with
+// (iy, ix) = (2 py + cy, 2 px + cx); only ky = 1 (cy = 0) or ky in {0, 2}
+// (cy = 1), and likewise kx, reach a pixel of the class, from the output
+// pixel oy = (iy + 1 - ky) / 2, ox = (ix + 1 - kx) / 2.  The classes hold
+// 1, 2, 2 and 4 taps, instead of 9 with mostly zero rows.
+struct TcTile {
+    long long m0, M;   // first row of the tile within its class, rows of the class
+    int cy, cx, ny, nx, ntap;
+};
+
+template <bool DGRAD>
+__host__ __device__ __forceinline__ int tc_tile(const ConvArgs &a, int tile, TcTile *t) {
+    if (!DGRAD) {
+        const long long M = (long long)a.B * a.Ho * a.Ho;
+        const int T = (int)((M + BM - 1) / BM);
+        if (t && tile < T) *t = TcTile{(long long)tile * BM, M, 0, 0, a.Ho, a.Ho, 9};
+        return T;
     }
-    const bf16 *src_img;
+    int first = 0;
+    for (int c = 0; c < 4; ++c) {
+        const int cy = c >> 1, cx = c & 1;
+        const int ny = (a.Hi - cy + 1) >> 1, nx = (a.Hi - cx + 1) >> 1;
+        const long long M = (long long)a.B * ny * nx;
+        const int T = (int)((M + BM - 1) / BM);
+        if (t && tile >= first && tile < first + T)
+            *t = TcTile{(long long)(tile - first) * BM, M, cy, cx, ny, nx, (cy + 1) * (cx + 1)};
+        first += T;
+    }
+    return first;   // the number of tiles
+}
+
+// Row m of a tile's class -> pixel (b, y, x) of the GEMM-row grid (output
+// grid forward, input grid for the input gradient).
+template <bool DGRAD>
+__device__ __forceinline__ void tc_row(const TcTile &t, long long m, int &b, int &y, int &x) {
+    const long long per = (long long)t.ny * t.nx;
+    b = (int)(m / per);
+    const int r = (int)(m - (long long)b * per);
+    const int py = r / t.nx, px = r - py * t.nx;
+    y = DGRAD ? 2 * py + t.cy : py;
+    x = DGRAD ? 2 * px + t.cx : px;
+}
+
+// Tap q of a tile -> (ky, kx).
+template <bool DGRAD>
+__device__ __forceinline__ void tc_tap(const TcTile &t, int q, int &ky, int &kx) {
     if (DGRAD) {
-        src_img = a.in + (size_t)rb * a.Ho * a.Ho * CH;
+        const int nkx = t.cx + 1;
+        ky = t.cy ? 2 * (q / nkx) : 1;
+        kx = t.cx ? 2 * (q % nkx) : 1;
     } else {
-        const long long sb = a.perm ? (long long)a.perm[a.b0 + rb] : a.b0 + rb;
-        src_img = a.in + (size_t)sb * a.Hi * a.Hi * CIN;
+        ky = q / 3;
+        kx = q - ky * 3;
     }
+}
 
-    auto load_tile = [&](int kt, int buf) {
-        const int k0 = kt * BK;
-        const int tap = k0 / CIN, c0 = k0 - tap * CIN;
-        const int ky = tap / 3, kx = tap - ky * 3;
-        bool ok = row_ok;
-        const bf16 *src = a.in;
-        if (DGRAD) {
-            const int ny = ry + 1 - ky, nx = rx + 1 - kx;
-            ok = ok && ny >= 0 && nx >= 0 && (ny % a.stride) == 0 && (nx % a.stride) == 0;
-            const int oy = ny / a.stride, ox = nx / a.stride;
-            ok = ok && oy < a.Ho && ox < a.Ho;
-            if (ok) src = src_img + ((size_t)oy * a.Ho + ox) * CH + c0;
-        } else {
-            const int iy = ry * a.stride + ky - 1, ix = rx * a.stride + kx - 1;
-            ok = ok && iy >= 0 && ix >= 0 && iy < a.Hi && ix < a.Hi;
-            if (ok) src = src_img + ((size_t)iy * a.Hi + ix) * CIN + c0;
-        }
-#pragma unroll
-        for (int c = 0; c < 4; ++c) cp_async16(&As[buf][tid][c * 8], ok ? src + c * 8 : a.in, ok);
-        // B: 64 rows x 4 chunks, two per thread
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int idx = tid * 2 + q, n = idx >> 2, c = idx & 3;
-            cp_async16(&Bs[buf][n][c * 8], a.w + (size_t)n * K + k0 + c * 8, true);
-        }
-        cp_async_commit();
-    };
+template <bool DGRAD, int CIN>
+__global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const ConvArgs a, int *__restrict__ err) {
+    using C = TcCfg<CIN>;
+    constexpr int S = C::STAGES;
+    extern __shared__ __align__(128) unsigned char tc_raw[];
+    unsigned char *base = tc_raw + ((128u - (tc_smem(tc_raw) & 127u)) & 127u);
+    unsigned char *Bs = base;
+    unsigned char *As = base + C::B_BYTES;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(As + (size_t)S * C::A_BYTES);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + C::N_BARS);
+    const uint32_t bar0 = tc_smem(bars);
+    // full[st] = bar0 + 8 st, empty[st] = bar0 + 8 (S + st),
+    // tfull[j] = bar0 + 8 (2 S + j), tempty[j] = bar0 + 8 (2 S + 2 + j)
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n_tiles = tc_tile<DGRAD>(a, 0, nullptr);
 
-    float acc[2][8][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-#pragma unroll
-            for (int t = 0; t < 4; ++t) acc[i][j][t] = 0.f;
-
-    load_tile(0, 0);
-    for (int kt = 0; kt < KT; ++kt) {
-        const int buf = kt & 1;
-        if (kt + 1 < KT) {
-            load_tile(kt + 1, buf ^ 1);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
+    if (tid == 0) {
+        for (int i = 0; i < S; ++i) {
+            tc_mbar_init(bar0 + 8 * i, 128);
+            tc_mbar_init(bar0 + 8 * (S + i), 1);
         }
-        __syncthreads();
-#pragma unroll
-        for (int ks = 0; ks < BK; ks += 16) {
-            uint32_t af[2][4];
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                const int r = warp * 32 + mt * 16 + (lane & 7) + ((lane >> 3) & 1) * 8;
-                const int c = ks + (lane >> 4) * 8;
-                ldsm_x4(af[mt], &As[buf][r][c]);
+        for (int j = 0; j < 2; ++j) {
+            tc_mbar_init(bar0 + 8 * (2 * S + j), 1);
+            tc_mbar_init(bar0 + 8 * (2 * S + 2 + j), 128);
+        }
+        tc_fence_mbar_init();
+    }
+    if (warp == 8) tc_alloc(tc_smem(tslot), kTcCols);
+    // weights: row n, 16-byte column kg -> core matrix (n / 8, kg), row n % 8
+    for (int q = tid; q < CH * C::K / 8; q += kTcThreads) {
+        const int n = q / (C::K / 8), kg = q - n * (C::K / 8);
+        cp_async16_ca(Bs + ((size_t)(n >> 3) * (C::K / 8) + kg) * 128 + (n & 7) * 16, a.w + (size_t)n * C::K + kg * 8,
+                      true);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    tc_fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp < 4) {
+        // ---- producers: thread tid gathers row tid of every tile
+        int g = 0;
+        bool run = true;
+        for (int tile = blockIdx.x; tile < n_tiles && run; tile += gridDim.x) {
+            TcTile t;
+            tc_tile<DGRAD>(a, tile, &t);
+            const long long m = t.m0 + tid;
+            const bool row_ok = m < t.M;
+            int rb = 0, ry = 0, rx = 0;
+            if (row_ok) tc_row<DGRAD>(t, m, rb, ry, rx);
+            const bf16 *img;
+            if (DGRAD) {
+                img = a.in + (size_t)rb * a.Ho * a.Ho * CH;
+            } else {
+                const long long sb = a.perm ? (long long)a.perm[a.b0 + rb] : a.b0 + rb;
+                img = a.in + (size_t)sb * a.Hi * a.Hi * CIN;
             }
-#pragma unroll
-            for (int np = 0; np < 4; ++np) {
-                uint32_t bfr[4];
-                const int n = np * 16 + (lane & 7) + (lane >> 4) * 8;
-                const int c = ks + ((lane >> 3) & 1) * 8;
-                ldsm_x4(bfr, &Bs[buf][n][c]);
-#pragma unroll
-                for (int mt = 0; mt < 2; ++mt) {
-                    mma_bf16(acc[mt][2 * np], af[mt], bfr[0], bfr[1]);
-                    mma_bf16(acc[mt][2 * np + 1], af[mt], bfr[2], bfr[3]);
+            unsigned char *dst0 = As + (size_t)(tid >> 3) * (C::KG * 128) + (tid & 7) * 16;
+            for (int q = 0; q < t.ntap; ++q) {
+                const int st = g % S;
+                if (!tc_mbar_wait(bar0 + 8 * (S + st), ((g / S) & 1) ^ 1)) {
+                    atomicOr(err, 1);
+                    run = false;
+                    break;
                 }
-            }
-        }
-        __syncthreads();
-    }
-
-    // epilogue
-    const int g = lane >> 2, tg = lane & 3;
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const long long m = m0 + warp * 32 + mt * 16 + g + h * 8;
-            if (m >= M) continue;
-#pragma unroll
-            for (int nt = 0; nt < 8; ++nt) {
-                const int n = nt * 8 + 2 * tg;
-                float v0 = acc[mt][nt][2 * h], v1 = acc[mt][nt][2 * h + 1];
+                int ky, kx;
+                tc_tap<DGRAD>(t, q, ky, kx);
+                bool ok = row_ok;
+                const bf16 *src = a.in;
                 if (DGRAD) {
-                    const __nv_bfloat162 am = *reinterpret_cast<const __nv_bfloat162 *>(a.act + m * CH + n);
-                    if (!(__bfloat162float(am.x) > 0.f)) v0 = 0.f;
-                    if (!(__bfloat162float(am.y) > 0.f)) v1 = 0.f;
+                    const int oy = (ry + 1 - ky) >> 1, ox = (rx + 1 - kx) >> 1;
+                    ok = ok && oy < a.Ho && ox < a.Ho;
+                    if (ok) src = img + ((size_t)oy * a.Ho + ox) * CH;
                 } else {
-                    v0 = fmaxf(v0 + a.bias[n], 0.f);
-                    v1 = fmaxf(v1 + a.bias[n + 1], 0.f);
+                    const int iy = ry * a.stride + ky - 1, ix = rx * a.stride + kx - 1;
+                    ok = ok && iy >= 0 && ix >= 0 && iy < a.Hi && ix < a.Hi;
+                    if (ok) src = img + ((size_t)iy * a.Hi + ix) * CIN;
                 }
-                *reinterpret_cast<__nv_bfloat162 *>(a.out + m * CH + n) = __floats2bfloat162_rn(v0, v1);
+                unsigned char *dst = dst0 + (size_t)st * C::A_BYTES;
+#pragma unroll
+                for (int c = 0; c < C::KG; ++c) cp_async16_ca(dst + c * 128, ok ? src + c * 8 : a.in, ok);
+                cp_async_commit();
+                if (g >= C::LAG) {
+                    cp_async_wait<C::LAG>();
+                    tc_fence_proxy_async();
+                    tc_mbar_arrive(bar0 + 8 * ((g - C::LAG) % S));
+                }
+                ++g;
             }
         }
+        cp_async_wait<0>();
+        tc_fence_proxy_async();
+        for (int q = (g > C::LAG ? g - C::LAG : 0); q < g; ++q) tc_mbar_arrive(bar0 + 8 * (q % S));
+    } else if (warp == 8) {
+        // ---- MMA issue: one lane
+        if (lane == 0) {
+            const uint32_t idesc = tc_idesc_bf16(BM, CH);
+            const uint32_t a_base = tc_smem(As), b_base = tc_smem(Bs);
+            int g = 0, i = 0;
+            bool run = true;
+            for (int tile = blockIdx.x; tile < n_tiles && run; tile += gridDim.x, ++i) {
+                TcTile t;
+                tc_tile<DGRAD>(a, tile, &t);
+                const int ab = i & 1;
+                if (!tc_mbar_wait(bar0 + 8 * (2 * S + 2 + ab), ((i >> 1) & 1) ^ 1)) {
+                    atomicOr(err, 1);
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(ab * CH);
+                for (int q = 0; q < t.ntap; ++q, ++g) {
+                    const int st = g % S;
+                    if (!tc_mbar_wait(bar0 + 8 * st, (g / S) & 1)) {
+                        atomicOr(err, 1);
+                        run = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    int ky, kx;
+                    tc_tap<DGRAD>(t, q, ky, kx);
+                    const uint32_t as = a_base + (uint32_t)(st * C::A_BYTES);
+                    const uint32_t bs = b_base + (uint32_t)((ky * 3 + kx) * C::KG * 128);
+#pragma unroll
+                    for (int j = 0; j < CIN / 16; ++j)
+                        tc_mma(d, tc_desc(as + j * 256, 128, C::KG * 128), tc_desc(bs + j * 256, 128, C::K * 16), idesc,
+                               (q | j) != 0);
+                    tc_commit(bar0 + 8 * (S + st));
+                }
+                if (run) tc_commit(bar0 + 8 * (2 * S + ab));
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---- epilogue: warp 4 + e reads TMEM lanes 32 e .. 32 e + 31 = tile rows
+        const int e = warp - 4;
+        const uint32_t lane_base = tmem + ((uint32_t)(32 * e) << 16);
+        int i = 0;
+        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++i) {
+            TcTile t;
+            tc_tile<DGRAD>(a, tile, &t);
+            const int ab = i & 1;
+            if (!tc_mbar_wait(bar0 + 8 * (2 * S + ab), (i >> 1) & 1)) {
+                atomicOr(err, 1);
+                break;
+            }
+            tc_fence_after();
+            const long long m = t.m0 + 32 * e + lane;
+            long long orow = 0;   // output row (pixel) of GEMM row m
+            if (m < t.M) {
+                int b, y, x;
+                tc_row<DGRAD>(t, m, b, y, x);
+                orow = DGRAD ? ((long long)b * a.Hi + y) * a.Hi + x : m;
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                float v[32];
+                tc_ld32(lane_base + (uint32_t)(ab * CH + 32 * h), v);
+                if (m < t.M) {
+                    uint4 o[4];
+                    uint32_t *ow = reinterpret_cast<uint32_t *>(o);
+                    if (DGRAD) {
+                        const uint4 *act = reinterpret_cast<const uint4 *>(a.act + orow * CH + 32 * h);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const uint4 av = act[q];
+                            const uint32_t aw[4] = {av.x, av.y, av.z, av.w};
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                __nv_bfloat162 am = *reinterpret_cast<const __nv_bfloat162 *>(&aw[u]);
+                                const float v0 = (__bfloat162float(am.x) > 0.f) ? v[8 * q + 2 * u] : 0.f;
+                                const float v1 = (__bfloat162float(am.y) > 0.f) ? v[8 * q + 2 * u + 1] : 0.f;
+                                __nv_bfloat162 r = __floats2bfloat162_rn(v0, v1);
+                                ow[4 * q + u] = *reinterpret_cast<uint32_t *>(&r);
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 16; ++u) {
+                            const int n = 32 * h + 2 * u;
+                            __nv_bfloat162 r = __floats2bfloat162_rn(fmaxf(v[2 * u] + a.bias[n], 0.f),
+                                                                     fmaxf(v[2 * u + 1] + a.bias[n + 1], 0.f));
+                            ow[u] = *reinterpret_cast<uint32_t *>(&r);
+                        }
+                    }
+                    uint4 *out = reinterpret_cast<uint4 *>(a.out + orow * CH + 32 * h);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) out[q] = o[q];
+                }
+            }
+            tc_fence_before();
+            tc_mbar_arrive(bar0 + 8 * (2 * S + 2 + ab));
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 8) {
+        tc_fence_after();
+        tc_dealloc(tmem, kTcCols);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -229,7 +408,7 @@ struct WgArgs {
     long long b0;
     int B, Hi, Ho, stride;
     long long rows_per_split;
-    float *part;         // [splits][64][9 CIN]
+    float *part;         // [splits][64 x 9 CIN + 64]: weight, then (CTAs of k-tile 0) bias partials
 };
 
 template <int CIN, int BKW>
@@ -283,6 +462,10 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad(const WgArgs a) {
     for (int j = 0; j < NT; ++j)
 #pragma unroll
         for (int t = 0; t < 4; ++t) acc[j][t] = 0.f;
+    // the CTAs of k-tile 0 also sum dz over their rows (bias gradient):
+    // thread tid sums channel tid % 64 over rows (tid / 64) * 16 .. + 15
+    const bool do_bias = blockIdx.x == 0;
+    float bsum = 0.f;
 
     if (r0 < r1) {
         load(r0, 0);
@@ -314,11 +497,22 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad(const WgArgs a) {
                     mma_bf16(acc[2 * np + 1], af, bfr[2], bfr[3]);
                 }
             }
+            if (do_bias) {
+                const int co = tid & (CH - 1), rh = (tid >> 6) * 16;
+#pragma unroll
+                for (int r = 0; r < 16; ++r) bsum += __bfloat162float(Zs[buf][rh + r][co]);
+            }
             __syncthreads();
         }
     }
+    float *dst = a.part + (size_t)blockIdx.y * (CH * K + CH);
+    if (do_bias) {
+        __shared__ float bred[kWgThreads];
+        bred[tid] = bsum;
+        __syncthreads();
+        if (tid < CH) dst[CH * K + tid] = bred[tid] + bred[tid + CH];
+    }
     const int g = lane >> 2, tg = lane & 3;
-    float *dst = a.part + (size_t)blockIdx.y * CH * K;
 #pragma unroll
     for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
@@ -330,27 +524,27 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad(const WgArgs a) {
         }
 }
 
-// Bias gradient partials: part[split][co] = sum over the split's rows of dz[m][co].
-__global__ void k_bias_part(const bf16 *__restrict__ dz, long long M, long long rows_per_split,
-                            float *__restrict__ part) {
-    __shared__ float sh[4][CH];
-    const int co = threadIdx.x & (CH - 1), lane4 = threadIdx.x >> 6;
-    const long long r0 = (long long)blockIdx.x * rows_per_split;
-    const long long r1 = (r0 + rows_per_split < M) ? r0 + rows_per_split : M;
-    float s = 0.f;
-    for (long long m = r0 + lane4; m < r1; m += 4) s += __bfloat162float(dz[m * CH + co]);
-    sh[lane4][co] = s;
+// grad[q] = sum over splits (in order) of part[split * stride + q], q < count.
+// A CTA owns 32 consecutive q (one per lane); warp w adds splits w, w + 8, ...
+// and the 8 warp sums are added in warp order.
+__global__ void __launch_bounds__(256) k_sum_parts(const float *__restrict__ part, int splits, int count,
+                                                   long long stride, float *__restrict__ grad) {
+    __shared__ float red[8][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int q = blockIdx.x * 32 + lane;
+    float sum = 0.f;
+    if (q < count) {
+#pragma unroll 4
+        for (int p = w; p < splits; p += 8) sum += part[(size_t)p * stride + q];
+    }
+    red[w][lane] = sum;
     __syncthreads();
-    if (threadIdx.x < CH) part[(size_t)blockIdx.x * CH + co] = sh[0][co] + sh[1][co] + sh[2][co] + sh[3][co];
-}
-
-// grad[off + q] = sum over splits (in order) of part[split][q], q < count.
-__global__ void k_sum_parts(const float *__restrict__ part, int splits, int count, float *__restrict__ grad) {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= count) return;
-    float s = 0.f;
-    for (int p = 0; p < splits; ++p) s += part[(size_t)p * count + q];
-    grad[q] = s;
+    if (w == 0 && q < count) {
+        float t = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) t += red[k][lane];
+        grad[q] = t;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -405,24 +599,53 @@ __global__ void k_head_dout(const float *__restrict__ out, const float *__restri
     if (q < 4 * B) dout[q] = 2.f / (4.f * (float)B) * (out[q] - tgt[q]);
 }
 
-// gfc[j][e] = sum_b dout[b][j] a3[b][e] (fixed order); thread e = 4 outputs.
-__global__ void k_head_wgrad(const bf16 *__restrict__ a3, const float *__restrict__ dout, int B, int F,
-                             float *__restrict__ gfc, float *__restrict__ gbfc) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < F) {
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int b = 0; b < B; ++b) {
-            const float v = __bfloat162float(a3[(size_t)b * F + e]);
+// gfc[j][e] = sum_b dout[b][j] a3[b][e], gbfc[j] = sum_b dout[b][j].  A CTA
+// owns 64 features (32 BF16 pairs, one per lane) and splits the samples over
+// its 8 warps (b = warp, warp + 8, ...); the 8 partial sums are added in warp
+// order.  F is a multiple of 64.
+__global__ void __launch_bounds__(256) k_head_wgrad(const bf16 *__restrict__ a3, const float *__restrict__ dout, int B,
+                                                    int F, float *__restrict__ gfc, float *__restrict__ gbfc) {
+    __shared__ float red[8][4][64];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int e = blockIdx.x * 64 + 2 * lane;
+    float acc[4][2] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll 8
+    for (int b = w; b < B; b += 8) {
+        const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162 *>(a3 + (size_t)b * F + e);
+        const float v0 = __low2float(v), v1 = __high2float(v);
+        const float4 d = *reinterpret_cast<const float4 *>(dout + 4 * b);
+        const float dj[4] = {d.x, d.y, d.z, d.w};
 #pragma unroll
-            for (int j = 0; j < 4; ++j) acc[j] = fmaf(dout[b * 4 + j], v, acc[j]);
+        for (int j = 0; j < 4; ++j) {
+            acc[j][0] = fmaf(dj[j], v0, acc[j][0]);
+            acc[j][1] = fmaf(dj[j], v1, acc[j][1]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        red[w][j][2 * lane] = acc[j][0];
+        red[w][j][2 * lane + 1] = acc[j][1];
+    }
+    __syncthreads();
+    const int j = threadIdx.x >> 6, c = threadIdx.x & 63;
+    float sum = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) sum += red[q][j][c];
+    gfc[(size_t)j * F + blockIdx.x * 64 + c] = sum;
+    if (blockIdx.x == 0 && w == 0) {
+        float sb[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int b = lane; b < B; b += 32) {
+            const float4 d = *reinterpret_cast<const float4 *>(dout + 4 * b);
+            sb[0] += d.x;
+            sb[1] += d.y;
+            sb[2] += d.z;
+            sb[3] += d.w;
         }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) gfc[(size_t)j * F + e] = acc[j];
-    }
-    if (blockIdx.x == 0 && threadIdx.x < 4) {
-        float sb = 0.f;
-        for (int b = 0; b < B; ++b) sb += dout[b * 4 + threadIdx.x];
-        gbfc[threadIdx.x] = sb;
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sb[q] += __shfl_xor_sync(0xffffffffu, sb[q], o);
+        if (lane < 4) gbfc[lane] = sb[lane];
     }
 }
 
@@ -469,24 +692,23 @@ __global__ void k_pack_w(const float *__restrict__ w, int cin, bf16 *__restrict_
     }
 }
 
-__global__ void k_targets(const double *__restrict__ p, long long n, const double4 center, const double4 range,
-                          float *__restrict__ t) {
+// Normalisation of the four misregistration parameters (centre, range).
+struct Norm4 {
+    double c[4], r[4];
+};
+
+__global__ void k_targets(const double *__restrict__ p, long long n, const Norm4 nm, float *__restrict__ t) {
     const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
-    t[4 * q + 0] = (float)((p[4 * q + 0] - center.x) / range.x);
-    t[4 * q + 1] = (float)((p[4 * q + 1] - center.y) / range.y);
-    t[4 * q + 2] = (float)((p[4 * q + 2] - center.z) / range.z);
-    t[4 * q + 3] = (float)((p[4 * q + 3] - center.w) / range.w);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) t[4 * q + k] = (float)((p[4 * q + k] - nm.c[k]) / nm.r[k]);
 }
 
-__global__ void k_denorm(const float *__restrict__ o, long long n, const double4 center, const double4 range,
-                         double *__restrict__ p) {
+__global__ void k_denorm(const float *__restrict__ o, long long n, const Norm4 nm, double *__restrict__ p) {
     const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
-    p[4 * q + 0] = center.x + range.x * (double)o[4 * q + 0];
-    p[4 * q + 1] = center.y + range.y * (double)o[4 * q + 1];
-    p[4 * q + 2] = center.z + range.z * (double)o[4 * q + 2];
-    p[4 * q + 3] = center.w + range.w * (double)o[4 * q + 3];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) p[4 * q + k] = nm.c[k] + nm.r[k] * (double)o[4 * q + k];
 }
 
 __global__ void k_gather_targets(const float *__restrict__ t, const int *__restrict__ perm, long long b0, int B,
@@ -514,6 +736,33 @@ cudaError_t dmalloc(T **p, size_t count) {
 
 unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// Persistent launch of the tcgen05 convolution: as many CTAs as fit on the
+// device at once (shared memory limits them to one or two per SM, so that
+// their TMEM columns always fit in the 512 of an SM), at most one per tile.
+template <bool DGRAD, int CIN>
+cudaError_t launch_tc(const ConvArgs &a, int *err, cudaStream_t st) {
+    static int per_sm = 0, n_sm = 0;
+    const size_t smem = TcCfg<CIN>::SMEM;
+    if (per_sm == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k_conv_tc<DGRAD, CIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        int dev = 0;
+        if (e == cudaSuccess) e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_tc<DGRAD, CIN>, kTcThreads, smem);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        if (per_sm * kTcCols > 512) per_sm = 512 / kTcCols;
+    }
+    if (DGRAD && a.stride != 2) return cudaErrorInvalidValue;   // parity classes assume stride 2
+    const long long tiles = tc_tile<DGRAD>(a, 0, nullptr);
+    if (tiles == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)std::min<long long>(tiles, (long long)n_sm * per_sm);
+    k_conv_tc<DGRAD, CIN><<<grid, kTcThreads, smem, st>>>(a, err);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_conv_fwd(const CnnState &S, int layer, const bf16 *in, const int *perm, long long b0, int B,
                             cudaStream_t st) {
     ConvArgs a{};
@@ -528,12 +777,8 @@ cudaError_t launch_conv_fwd(const CnnState &S, int layer, const bf16 *in, const 
     } else {
         a.w = S.w3; a.bias = S.master + S.off_b3; a.out = S.a3; a.Hi = S.H2; a.Ho = S.H3; a.stride = 2;
     }
-    const long long M = (long long)B * a.Ho * a.Ho;
-    const unsigned nb = blocks_for(M, BM);
-    if (layer == 1 && S.C0 == 32) k_conv<false, 32><<<nb, kConvThreads, 0, st>>>(a);
-    else if (layer == 1) k_conv<false, 64><<<nb, kConvThreads, 0, st>>>(a);
-    else k_conv<false, 64><<<nb, kConvThreads, 0, st>>>(a);
-    return cudaGetLastError();
+    if (layer == 1 && S.C0 == 32) return launch_tc<false, 32>(a, S.d_err, st);
+    return launch_tc<false, 64>(a, S.d_err, st);
 }
 
 // Input gradient of layer 3 (into dz2) or layer 2 (into dz1).
@@ -546,14 +791,12 @@ cudaError_t launch_conv_dgrad(const CnnState &S, int layer, int B, cudaStream_t 
     } else {
         a.in = S.dz2; a.w = S.w2t; a.act = S.a1; a.out = S.dz1; a.Hi = S.H1; a.Ho = S.H2;
     }
-    const long long M = (long long)B * a.Hi * a.Hi;
-    k_conv<true, 64><<<blocks_for(M, BM), kConvThreads, 0, st>>>(a);
-    return cudaGetLastError();
+    return launch_tc<true, 64>(a, S.d_err, st);
 }
 
 int n_splits(long long M) {
-    // enough CTAs for a few waves, at least 64 rows each
-    return (int)std::max<long long>(1, std::min<long long>(296, M / 64));
+    // enough CTAs for a few waves, at least 256 rows each
+    return (int)std::max<long long>(1, std::min<long long>(296, M / 256));
 }
 
 cudaError_t launch_wgrad(const CnnState &S, int layer, const bf16 *in, const int *perm, long long b0, int B,
@@ -565,13 +808,13 @@ cudaError_t launch_wgrad(const CnnState &S, int layer, const bf16 *in, const int
     a.B = B;
     a.part = S.wpart;
     int cin;
-    long long off_w, off_b;
+    long long off_w;
     if (layer == 1) {
-        a.dz = S.dz1; a.Hi = S.H0; a.Ho = S.H1; a.stride = 1; cin = S.C0; off_w = S.off_w1; off_b = S.off_b1;
+        a.dz = S.dz1; a.Hi = S.H0; a.Ho = S.H1; a.stride = 1; cin = S.C0; off_w = S.off_w1;
     } else if (layer == 2) {
-        a.dz = S.dz2; a.Hi = S.H1; a.Ho = S.H2; a.stride = 2; cin = CH; off_w = S.off_w2; off_b = S.off_b2;
+        a.dz = S.dz2; a.Hi = S.H1; a.Ho = S.H2; a.stride = 2; cin = CH; off_w = S.off_w2;
     } else {
-        a.dz = S.dz3; a.Hi = S.H2; a.Ho = S.H3; a.stride = 2; cin = CH; off_w = S.off_w3; off_b = S.off_b3;
+        a.dz = S.dz3; a.Hi = S.H2; a.Ho = S.H3; a.stride = 2; cin = CH; off_w = S.off_w3;
     }
     const long long M = (long long)B * a.Ho * a.Ho;
     const int splits = n_splits(M);
@@ -587,9 +830,9 @@ cudaError_t launch_wgrad(const CnnState &S, int layer, const bf16 *in, const int
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_sum_parts<<<blocks_for(CH * K, 256), 256, 0, st>>>(S.wpart, splits, CH * K, S.grad + off_w);
-    k_bias_part<<<splits, 256, 0, st>>>(a.dz, M, a.rows_per_split, S.bpart);
-    k_sum_parts<<<1, CH, 0, st>>>(S.bpart, splits, CH, S.grad + off_b);
+    // weights and bias are adjacent in the parameter vector (off_b = off_w + 64 K)
+    k_sum_parts<<<blocks_for(CH * K + CH, 32), 256, 0, st>>>(S.wpart, splits, CH * K + CH, (long long)CH * K + CH,
+                                                            S.grad + off_w);
     return cudaGetLastError();
 }
 
@@ -618,7 +861,7 @@ cudaError_t backward(CnnState &S, const bf16 *in, const int *perm, long long b0,
     cudaError_t e;
     const int F = S.H3 * S.H3 * CH;
     k_head_dout<<<blocks_for(4 * B, 256), 256, 0, st>>>(S.out, tgt, B, S.dout);
-    k_head_wgrad<<<blocks_for(F, 128), 128, 0, st>>>(S.a3, S.dout, B, F, S.grad + S.off_fc, S.grad + S.off_bfc);
+    k_head_wgrad<<<F / 64, 256, 0, st>>>(S.a3, S.dout, B, F, S.grad + S.off_fc, S.grad + S.off_bfc);
     k_head_dgrad<<<blocks_for((long long)B * F, 256), 256, 0, st>>>(S.a3, S.dout, S.master + S.off_fc, B, F, S.dz3);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = launch_wgrad(S, 3, S.a2, nullptr, 0, B, st)) != cudaSuccess) return e;
@@ -634,7 +877,7 @@ cudaError_t alloc_state(CnnState &S) {
     const size_t a1 = (size_t)kBatchCap * S.H1 * S.H1 * CH, a2 = (size_t)kBatchCap * S.H2 * S.H2 * CH,
                  a3 = (size_t)kBatchCap * S.H3 * S.H3 * CH;
     const int splits = 296;
-    S.wpart_floats = (long long)splits * CH * 9 * CH;
+    S.wpart_floats = (long long)splits * (CH * 9 * CH + CH);
 #define SYNIM_A(ptr, n) \
     if (e == cudaSuccess) e = dmalloc(&(ptr), (n))
     SYNIM_A(S.master, P);
@@ -658,8 +901,9 @@ cudaError_t alloc_state(CnnState &S) {
     SYNIM_A(S.dout, (size_t)kBatchCap * 4);
     SYNIM_A(S.tgt, (size_t)kBatchCap * 4);
     SYNIM_A(S.wpart, (size_t)S.wpart_floats);
-    SYNIM_A(S.bpart, (size_t)splits * CH);
+    SYNIM_A(S.d_err, 1);
 #undef SYNIM_A
+    if (e == cudaSuccess) e = cudaMemset(S.d_err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMallocHost(&S.h_loss, sizeof(float) * kBatchCap);
     return e;
 }
@@ -674,7 +918,25 @@ synim_status ccuda(synim_ctx *c, cudaError_t e, const char *what) {
                  std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-double4 d4(const double *v) { return make_double4(v[0], v[1], v[2], v[3]); }
+Norm4 norm4(const CnnState &S) {
+    Norm4 nm;
+    for (int k = 0; k < 4; ++k) {
+        nm.c[k] = S.center[k];
+        nm.r[k] = S.range[k];
+    }
+    return nm;
+}
+
+// After a synchronisation: SYNIM_ERR_TIMEOUT if a tensor-core convolution
+// flagged a bounded wait that gave up (the flag is cleared).
+synim_status check_tc(synim_ctx *c, CnnState &S, const char *what) {
+    int flag = 0;
+    cudaError_t e = cudaMemcpy(&flag, S.d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return ccuda(c, e, what);
+    if (flag == 0) return SYNIM_OK;
+    cudaMemset(S.d_err, 0, sizeof(int));
+    return cfail(c, SYNIM_ERR_TIMEOUT, std::string(what) + ": a tensor-core pipeline wait timed out");
+}
 
 }  // namespace
 
@@ -696,7 +958,7 @@ cudaError_t cnn_predict_slopes(synim_ctx *c, const float *y, long long n, double
         const int B = (int)std::min<long long>(kBatchCap, n - s0);
         k_to_bf16<<<blocks_for(B * per, 256), 256, 0, st>>>(y + s0 * per, B * per, S->x);
         if ((e = forward(*S, S->x, nullptr, 0, B, nullptr, st)) != cudaSuccess) break;
-        k_denorm<<<blocks_for(B, 128), 128, 0, st>>>(S->out, B, d4(S->center), d4(S->range), params_out + 4 * s0);
+        k_denorm<<<blocks_for(B, 128), 128, 0, st>>>(S->out, B, norm4(*S), params_out + 4 * s0);
         e = cudaGetLastError();
     }
     return e;
@@ -808,6 +1070,7 @@ synim_status synim_cnn_grad(synim_ctx *ctx, const uint16_t *x, const float *targ
         e = cudaMemcpyAsync(grad_out, S.grad, sizeof(float) * S.n_params, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return ccuda(ctx, e, "cnn_grad");
+    if (synim_status t = check_tc(ctx, S, "cnn_grad")) return t;
     if (loss_out) {
         double s = 0.0;
         for (float v : l) s += v;
@@ -847,7 +1110,7 @@ synim_status synim_cnn_train(synim_ctx *ctx, const double *params, int64_t n, co
     synim_status ss = synim_probe_generate(ctx, params, n, opts->seed, opts->sample0, opts->noise_rel,
                                            reinterpret_cast<uint16_t *>(S.data), cuda_stream);
     if (ss != SYNIM_OK) return ss;
-    k_targets<<<blocks_for(n, 128), 128, 0, st>>>(params, n, d4(S.center), d4(S.range), S.targets);
+    k_targets<<<blocks_for(n, 128), 128, 0, st>>>(params, n, norm4(S), S.targets);
     S.n_data = n;
     std::vector<int> perm((size_t)n);
     std::mt19937_64 rng(opts->seed ^ 0x5851F42D4C957F2DULL);
@@ -891,7 +1154,8 @@ synim_status synim_cnn_train(synim_ctx *ctx, const double *params, int64_t n, co
         if (loss_out) loss_out[ep] = ep_loss;
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    return e == cudaSuccess ? SYNIM_OK : ccuda(ctx, e, "cnn_train");
+    if (e != cudaSuccess) return ccuda(ctx, e, "cnn_train");
+    return check_tc(ctx, S, "cnn_train");
 }
 
 }  // extern "C"
