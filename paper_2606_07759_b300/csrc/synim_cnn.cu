@@ -121,7 +121,41 @@ struct ConvArgs {
 // and its role stops, so the kernel always ends.
 // ---------------------------------------------------------------------------
 constexpr int kTcThreads = 288;   // 4 producer warps, 4 epilogue warps, 1 MMA warp
-constexpr int kTcCols = 2 * CH;   // TMEM columns: two 64-column FP32 accumulators
+// MMAs that accumulate into one TMEM accumulator serialise (a dependent
+// chain costs ~173 cycles per tcgen05.mma on B300 whatever N is, against
+// ~79 cycles per MMA for 4 interleaved chains), so a tile's MMAs go round
+// robin into kTcParts partial accumulators that the epilogue adds.  Each
+// tile needs at least kTcParts MMAs (it has 4 to 36).
+constexpr int kTcParts = 4;
+constexpr int kTcCols = 2 * kTcParts * CH;   // double-buffered: all 512 TMEM columns (one CTA per SM)
+
+// Bias, ReLU, BF16 and the store of 32 channels (half h) of one output row.
+__device__ __forceinline__ void store_relu32(const float (&v)[32], const float *__restrict__ bias, int h,
+                                             bf16 *__restrict__ row) {
+    uint4 o[4];
+    uint32_t *ow = reinterpret_cast<uint32_t *>(o);
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        const int n = 32 * h + 2 * u;
+        __nv_bfloat162 r = __floats2bfloat162_rn(fmaxf(v[2 * u] + bias[n], 0.f), fmaxf(v[2 * u + 1] + bias[n + 1], 0.f));
+        ow[u] = *reinterpret_cast<uint32_t *>(&r);
+    }
+    uint4 *out = reinterpret_cast<uint4 *>(row + 32 * h);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) out[q] = o[q];
+}
+
+// v = sum over the kTcParts partial accumulators (64 columns apart, added in
+// order) of 32 columns starting at taddr.
+__device__ __forceinline__ void tc_ld_sum(uint32_t taddr, float (&v)[32]) {
+    static_assert(kTcParts == 4, "one load per partial accumulator");
+    uint32_t r[128];
+    tc_ld32x4(taddr, CH, r);
+#pragma unroll
+    for (int q = 0; q < 32; ++q)
+        v[q] = ((__uint_as_float(r[q]) + __uint_as_float(r[32 + q])) + __uint_as_float(r[64 + q])) +
+               __uint_as_float(r[96 + q]);
+}
 
 template <int CIN>
 struct TcCfg {
@@ -129,7 +163,7 @@ struct TcCfg {
     static constexpr int KG = CIN / 8;             // core-matrix columns per tap
     static constexpr int A_BYTES = BM * CIN * 2;   // one tap of one 128-row tile
     static constexpr int B_BYTES = CH * K * 2;     // all weights
-    static constexpr int STAGES = (CIN == 32) ? 6 : 4;
+    static constexpr int STAGES = (CIN == 32) ? 6 : 8;
     static constexpr int LAG = STAGES - 2;         // taps in flight per producer thread
     static constexpr int N_BARS = 2 * STAGES + 4;
     static constexpr size_t SMEM = 128 + B_BYTES + (size_t)STAGES * A_BYTES + 8 * N_BARS + 16;
@@ -208,6 +242,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const ConvArgs a, int
     // tfull[j] = bar0 + 8 (2 S + j), tempty[j] = bar0 + 8 (2 S + 2 + j)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int n_tiles = tc_tile<DGRAD>(a, 0, nullptr);
+    __shared__ float s_bias[CH];
+    if (!DGRAD && tid < CH) s_bias[tid] = a.bias[tid];
 
     if (tid == 0) {
         for (int i = 0; i < S; ++i) {
@@ -305,7 +341,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const ConvArgs a, int
                     break;
                 }
                 tc_fence_after();
-                const uint32_t d = tmem + (uint32_t)(ab * CH);
+                const uint32_t d = tmem + (uint32_t)(ab * kTcParts * CH);
+                int n_mma = 0;
                 for (int q = 0; q < t.ntap; ++q, ++g) {
                     const int st = g % S;
                     if (!tc_mbar_wait(bar0 + 8 * st, (g / S) & 1)) {
@@ -319,9 +356,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const ConvArgs a, int
                     const uint32_t as = a_base + (uint32_t)(st * C::A_BYTES);
                     const uint32_t bs = b_base + (uint32_t)((ky * 3 + kx) * C::KG * 128);
 #pragma unroll
-                    for (int j = 0; j < CIN / 16; ++j)
-                        tc_mma(d, tc_desc(as + j * 256, 128, C::KG * 128), tc_desc(bs + j * 256, 128, C::K * 16), idesc,
-                               (q | j) != 0);
+                    for (int j = 0; j < CIN / 16; ++j, ++n_mma)
+                        tc_mma(d + (uint32_t)((n_mma % kTcParts) * CH), tc_desc(as + j * 256, 128, C::KG * 128),
+                               tc_desc(bs + j * 256, 128, C::K * 16), idesc, n_mma >= kTcParts);
                     tc_commit(bar0 + 8 * (S + st));
                 }
                 if (run) tc_commit(bar0 + 8 * (2 * S + ab));
@@ -352,11 +389,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const ConvArgs a, int
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 float v[32];
-                tc_ld32(lane_base + (uint32_t)(ab * CH + 32 * h), v);
+                tc_ld_sum(lane_base + (uint32_t)(ab * kTcParts * CH + 32 * h), v);
                 if (m < t.M) {
-                    uint4 o[4];
-                    uint32_t *ow = reinterpret_cast<uint32_t *>(o);
                     if (DGRAD) {
+                        uint4 o[4];
+                        uint32_t *ow = reinterpret_cast<uint32_t *>(o);
                         const uint4 *act = reinterpret_cast<const uint4 *>(a.act + orow * CH + 32 * h);
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
@@ -371,19 +408,218 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const ConvArgs a, int
                                 ow[4 * q + u] = *reinterpret_cast<uint32_t *>(&r);
                             }
                         }
+                        uint4 *out = reinterpret_cast<uint4 *>(a.out + orow * CH + 32 * h);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) out[q] = o[q];
                     } else {
-#pragma unroll
-                        for (int u = 0; u < 16; ++u) {
-                            const int n = 32 * h + 2 * u;
-                            __nv_bfloat162 r = __floats2bfloat162_rn(fmaxf(v[2 * u] + a.bias[n], 0.f),
-                                                                     fmaxf(v[2 * u + 1] + a.bias[n + 1], 0.f));
-                            ow[u] = *reinterpret_cast<uint32_t *>(&r);
-                        }
+                        store_relu32(v, s_bias, h, a.out + orow * CH);
                     }
-                    uint4 *out = reinterpret_cast<uint4 *>(a.out + orow * CH + 32 * h);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) out[q] = o[q];
                 }
+            }
+            tc_fence_before();
+            tc_mbar_arrive(bar0 + 8 * (2 * S + 2 + ab));
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 8) {
+        tc_fence_after();
+        tc_dealloc(tmem, kTcCols);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Shifted-window kernels for the stride-1 layer (first convolution).
+//
+// GEMM rows are the pixels of a padded-pitch grid, r = y Wp + x with
+// Wp = H + 2 (x >= H: padding rows, computed and dropped), in tiles of 128
+// rows within one image.  Input pixel (y + ky - 1, x + kx - 1) of row r sits
+// at padded position r + ky Wp + kx, so one halo of NS = 128 + 2 Wp + 2
+// padded positions per tile serves all nine taps: tap (ky, kx) is the halo
+// read from offset ky Wp + kx.  The halo is stored as CIN / 8 planes of
+// 16-byte pixels (8 channels each), so that 8 consecutive rows of one plane
+// are one 8 x 16-byte core matrix: K-major for the forward GEMM (rows =
+// pixels, K = channels; the next 8 channels are the next plane) and
+// MN-major for the weight gradient (K = pixels, N = channels).
+// ---------------------------------------------------------------------------
+struct HaloGeo {
+    int H, Wp, NS, plane, per_img;   // side, pitch, halo positions, plane bytes, tiles per image
+};
+
+__host__ __device__ __forceinline__ HaloGeo halo_geo(int H) {
+    HaloGeo g;
+    g.H = H;
+    g.Wp = H + 2;
+    g.NS = (BM + 2 * g.Wp + 2 + 7) / 8 * 8;
+    g.plane = g.NS * 16;
+    g.per_img = (H * g.Wp + BM - 1) / BM;
+    return g;
+}
+
+// Halo of one tile (image img, first row r0) into the CIN / 8 planes at dst,
+// by the 128 producer threads; zero outside the image.
+template <int CIN>
+__device__ __forceinline__ void load_halo(unsigned char *dst, const bf16 *img, const HaloGeo &g, int r0, int tid,
+                                          const bf16 *any) {
+    constexpr int KG = CIN / 8;
+    // a thread per halo position; 8 consecutive threads fill 128 contiguous
+    // bytes of one plane (no bank conflicts)
+    for (int sp = tid; sp < g.NS; sp += 128) {
+        const int P = r0 + sp, py = P / g.Wp, px = P - py * g.Wp;
+        const int iy = py - 1, ix = px - 1;
+        const bool ok = iy >= 0 && iy < g.H && ix >= 0 && ix < g.H;
+        const bf16 *src = ok ? img + ((size_t)iy * g.H + ix) * CIN : any;
+#pragma unroll
+        for (int kg = 0; kg < KG; ++kg) cp_async16_ca(dst + kg * g.plane + sp * 16, ok ? src + kg * 8 : any, ok);
+    }
+}
+
+template <int CIN>
+struct HaloCfg {
+    static constexpr int K = 9 * CIN;
+    static constexpr int KG = CIN / 8;
+    static constexpr int B_BYTES = CH * K * 2;
+    static constexpr int STAGES = (CIN == 32) ? 8 : 4;   // also keeps one CTA per SM
+    static constexpr int N_BARS = 2 * STAGES + 4;
+    __host__ __device__ static size_t smem(const HaloGeo &g) {
+        return 128 + B_BYTES + (size_t)STAGES * KG * g.plane + 8 * N_BARS + 16;
+    }
+};
+
+// Forward convolution, stride 1, pad 1: out = ReLU(conv(in) + bias), same
+// warp roles, barriers and bounded waits as k_conv_tc; a stage holds one
+// tile's halo and feeds 9 taps x CIN / 16 MMAs.
+template <int CIN>
+__global__ void __launch_bounds__(kTcThreads, 1) k_conv_halo(const ConvArgs a, int *__restrict__ err) {
+    using C = HaloCfg<CIN>;
+    constexpr int S = C::STAGES;
+    const HaloGeo hg = halo_geo(a.Ho);
+    const int stage_bytes = C::KG * hg.plane;
+    extern __shared__ __align__(128) unsigned char tc_raw[];
+    unsigned char *base = tc_raw + ((128u - (tc_smem(tc_raw) & 127u)) & 127u);
+    unsigned char *Bs = base;
+    unsigned char *As = base + C::B_BYTES;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(As + (size_t)S * stage_bytes);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + C::N_BARS);
+    const uint32_t bar0 = tc_smem(bars);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n_tiles = a.B * hg.per_img;
+    __shared__ float s_bias[CH];
+
+    if (tid == 0) {
+        for (int i = 0; i < S; ++i) {
+            tc_mbar_init(bar0 + 8 * i, 128);
+            tc_mbar_init(bar0 + 8 * (S + i), 1);
+        }
+        for (int j = 0; j < 2; ++j) {
+            tc_mbar_init(bar0 + 8 * (2 * S + j), 1);
+            tc_mbar_init(bar0 + 8 * (2 * S + 2 + j), 128);
+        }
+        tc_fence_mbar_init();
+    }
+    if (tid < CH) s_bias[tid] = a.bias[tid];
+    if (warp == 8) tc_alloc(tc_smem(tslot), kTcCols);
+    for (int q = tid; q < CH * C::K / 8; q += kTcThreads) {
+        const int n = q / (C::K / 8), kg = q - n * (C::K / 8);
+        cp_async16_ca(Bs + ((size_t)(n >> 3) * (C::K / 8) + kg) * 128 + (n & 7) * 16, a.w + (size_t)n * C::K + kg * 8,
+                      true);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    tc_fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp < 4) {
+        constexpr int LAG = S - 2;
+        int g = 0;
+        // sample of the next tile, loaded one tile ahead
+        long long sb_next = 0;
+        if (blockIdx.x < n_tiles) {
+            const int b = blockIdx.x / hg.per_img;
+            sb_next = a.perm ? (long long)a.perm[a.b0 + b] : a.b0 + b;
+        }
+        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++g) {
+            const long long sb = sb_next;
+            if (tile + (int)gridDim.x < n_tiles) {
+                const int bn = (tile + (int)gridDim.x) / hg.per_img;
+                sb_next = a.perm ? (long long)a.perm[a.b0 + bn] : a.b0 + bn;
+            }
+            const int st = g % S;
+            if (!tc_mbar_wait(bar0 + 8 * (S + st), ((g / S) & 1) ^ 1)) {
+                atomicOr(err, 1);
+                break;
+            }
+            const int b = tile / hg.per_img, r0 = (tile - b * hg.per_img) * BM;
+            load_halo<CIN>(As + (size_t)st * stage_bytes, a.in + (size_t)sb * a.Hi * a.Hi * CIN, hg, r0, tid, a.in);
+            cp_async_commit();
+            if (g >= LAG) {
+                cp_async_wait<LAG>();
+                tc_fence_proxy_async();
+                tc_mbar_arrive(bar0 + 8 * ((g - LAG) % S));
+            }
+        }
+        cp_async_wait<0>();
+        tc_fence_proxy_async();
+        for (int q = (g > LAG ? g - LAG : 0); q < g; ++q) tc_mbar_arrive(bar0 + 8 * (q % S));
+    } else if (warp == 8) {
+        if (lane == 0) {
+            const uint32_t idesc = tc_idesc_bf16(BM, CH);
+            const uint32_t a_base = tc_smem(As), b_base = tc_smem(Bs);
+            int g = 0;
+            for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++g) {
+                const int ab = g & 1;
+                if (!tc_mbar_wait(bar0 + 8 * (2 * S + 2 + ab), ((g >> 1) & 1) ^ 1)) {
+                    atomicOr(err, 1);
+                    break;
+                }
+                const int st = g % S;
+                if (!tc_mbar_wait(bar0 + 8 * st, (g / S) & 1)) {
+                    atomicOr(err, 1);
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(ab * kTcParts * CH);
+                const uint32_t as = a_base + (uint32_t)(st * stage_bytes);
+                int n_mma = 0;
+#pragma unroll 1
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int ky = tap / 3, kx = tap - ky * 3;
+                    const uint32_t at = as + (uint32_t)((ky * hg.Wp + kx) * 16);
+                    const uint32_t bt = b_base + (uint32_t)(tap * C::KG * 128);
+#pragma unroll
+                    for (int j = 0; j < CIN / 16; ++j, ++n_mma)
+                        tc_mma(d + (uint32_t)((n_mma % kTcParts) * CH), tc_desc(at + 2 * j * hg.plane, hg.plane, 128),
+                               tc_desc(bt + j * 256, 128, C::K * 16), idesc, n_mma >= kTcParts);
+                }
+                tc_commit(bar0 + 8 * (S + st));
+                tc_commit(bar0 + 8 * (2 * S + ab));
+            }
+        }
+        __syncwarp();
+    } else {
+        const int e = warp - 4;
+        const uint32_t lane_base = tmem + ((uint32_t)(32 * e) << 16);
+        int g = 0;
+        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++g) {
+            const int ab = g & 1;
+            if (!tc_mbar_wait(bar0 + 8 * (2 * S + ab), (g >> 1) & 1)) {
+                atomicOr(err, 1);
+                break;
+            }
+            tc_fence_after();
+            const int b = tile / hg.per_img;
+            const int r = (tile - b * hg.per_img) * BM + 32 * e + lane;
+            const int y = r / hg.Wp, x = r - y * hg.Wp;
+            const bool keep = y < hg.H && x < hg.H;
+            bf16 *row = a.out + (((size_t)b * hg.H + y) * hg.H + x) * CH;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                float v[32];
+                tc_ld_sum(lane_base + (uint32_t)(ab * kTcParts * CH + 32 * h), v);
+                if (keep) store_relu32(v, s_bias, h, row);
             }
             tc_fence_before();
             tc_mbar_arrive(bar0 + 8 * (2 * S + 2 + ab));
@@ -522,6 +758,174 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad(const WgArgs a) {
             dst[(size_t)n * K + k] = acc[nt][2 * h];
             dst[(size_t)n * K + k + 1] = acc[nt][2 * h + 1];
         }
+}
+
+// ---------------------------------------------------------------------------
+// Weight and bias gradient of the stride-1 layer with CIN = 32 channels, on
+// the shifted windows: for each tile, the halo of the layer input and the
+// tile's 128 rows of dz (zero on padding rows) are staged once; tap (ky, kx)
+// contributes dz^T (64 x 128, MN-major) times the halo read from offset
+// ky Wp + kx (128 x 32, MN-major) through tcgen05.mma M=64 N=32 K=16 into
+// its own 32 TMEM columns, accumulated over all tiles of the CTA; a 10th
+// product with an all-ones operand (N = 8) gives the bias gradient.  The
+// epilogue writes part[cta][co][tap ci] and part[cta][64 K + co].  With
+// M = 64, accumulator row i sits in TMEM lane 32 (i / 16) + i % 16.
+// ---------------------------------------------------------------------------
+struct HaloWgArgs {
+    const bf16 *dz;      // [B][H][H][64]
+    const bf16 *in;      // layer input [.][H][H][32]
+    const int *perm;
+    long long b0;
+    int B, H;
+    float *part;         // [gridDim.x][64 x 288 + 64]
+};
+
+constexpr int kHwStages = 6;
+constexpr int kHwCols = 512;   // 9 x 32 + 8 columns, rounded up to a power of two
+
+__host__ __device__ __forceinline__ size_t wgrad_halo_smem(const HaloGeo &g) {
+    return 128 + 2048 + (size_t)kHwStages * (4 * g.plane + BM * CH * 2) + 8 * (2 * kHwStages + 1) + 16;
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_wgrad_halo(const HaloWgArgs a, int *__restrict__ err) {
+    constexpr int CIN = 32, K = 9 * CIN, KG = CIN / 8, S = kHwStages, LAG = S - 2;
+    const HaloGeo hg = halo_geo(a.H);
+    const int halo_bytes = KG * hg.plane, stage_bytes = halo_bytes + BM * CH * 2;
+    extern __shared__ __align__(128) unsigned char tc_raw[];
+    unsigned char *base = tc_raw + ((128u - (tc_smem(tc_raw) & 127u)) & 127u);
+    unsigned char *ones = base;            // 128 rows x 8 BF16 ones
+    unsigned char *St = base + 2048;       // stages: halo planes, then dz core matrices
+    uint64_t *bars = reinterpret_cast<uint64_t *>(St + (size_t)S * stage_bytes);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * S + 1);
+    const uint32_t bar0 = tc_smem(bars);
+    // full[st] = bar0 + 8 st, empty[st] = bar0 + 8 (S + st), done = bar0 + 16 S
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n_tiles = a.B * hg.per_img;
+
+    if (tid == 0) {
+        for (int i = 0; i < S; ++i) {
+            tc_mbar_init(bar0 + 8 * i, 128);
+            tc_mbar_init(bar0 + 8 * (S + i), 1);
+        }
+        tc_mbar_init(bar0 + 16 * S, 1);
+        tc_fence_mbar_init();
+    }
+    if (warp == 8) tc_alloc(tc_smem(tslot), kHwCols);
+    for (int q = tid; q < 2048 / 16; q += kTcThreads)
+        reinterpret_cast<uint4 *>(ones)[q] = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
+    tc_fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp < 4) {
+        int g = 0;
+        long long sb_next = 0;
+        if (blockIdx.x < n_tiles) {
+            const int b = blockIdx.x / hg.per_img;
+            sb_next = a.perm ? (long long)a.perm[a.b0 + b] : a.b0 + b;
+        }
+        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++g) {
+            const long long sb = sb_next;
+            if (tile + (int)gridDim.x < n_tiles) {
+                const int bn = (tile + (int)gridDim.x) / hg.per_img;
+                sb_next = a.perm ? (long long)a.perm[a.b0 + bn] : a.b0 + bn;
+            }
+            const int st = g % S;
+            if (!tc_mbar_wait(bar0 + 8 * (S + st), ((g / S) & 1) ^ 1)) {
+                atomicOr(err, 1);
+                break;
+            }
+            const int b = tile / hg.per_img, r0 = (tile - b * hg.per_img) * BM;
+            unsigned char *stage = St + (size_t)st * stage_bytes;
+            load_halo<CIN>(stage, a.in + (size_t)sb * a.H * a.H * CIN, hg, r0, tid, a.in);
+            unsigned char *dzs = stage + halo_bytes;
+            const bf16 *dzi = a.dz + (size_t)b * a.H * a.H * CH;
+            {
+                // a thread per row; 8 consecutive threads fill one core matrix
+                const int i = tid;
+                const int r = r0 + i, y = r / hg.Wp, x = r - y * hg.Wp;
+                const bool ok = y < a.H && x < a.H;
+                const bf16 *src = ok ? dzi + ((size_t)y * a.H + x) * CH : a.dz;
+#pragma unroll
+                for (int cg = 0; cg < 8; ++cg)
+                    cp_async16_ca(dzs + ((i >> 3) * 8 + cg) * 128 + (i & 7) * 16, ok ? src + cg * 8 : a.dz, ok);
+            }
+            cp_async_commit();
+            if (g >= LAG) {
+                cp_async_wait<LAG>();
+                tc_fence_proxy_async();
+                tc_mbar_arrive(bar0 + 8 * ((g - LAG) % S));
+            }
+        }
+        cp_async_wait<0>();
+        tc_fence_proxy_async();
+        for (int q = (g > LAG ? g - LAG : 0); q < g; ++q) tc_mbar_arrive(bar0 + 8 * (q % S));
+    } else if (warp == 8) {
+        if (lane == 0) {
+            const uint32_t id_w = tc_idesc_bf16(64, CIN) | (1u << 15) | (1u << 16);   // both operands MN-major
+            const uint32_t id_b = tc_idesc_bf16(64, 8) | (1u << 15) | (1u << 16);
+            const uint32_t st_base = tc_smem(St), ones_a = tc_smem(ones);
+            int g = 0;
+            bool run = true;
+            for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++g) {
+                const int st = g % S;
+                if (!tc_mbar_wait(bar0 + 8 * st, (g / S) & 1)) {
+                    atomicOr(err, 1);
+                    run = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t hs = st_base + (uint32_t)(st * stage_bytes), ds = hs + (uint32_t)halo_bytes;
+                // the ten accumulators are independent: issue them interleaved
+#pragma unroll 1
+                for (int j = 0; j < BM / 16; ++j) {
+                    const uint64_t adz = tc_desc(ds + j * 2048, 1024, 128);
+#pragma unroll
+                    for (int tap = 0; tap < 9; ++tap) {
+                        const int ky = tap / 3, kx = tap - ky * 3;
+                        const uint32_t ht = hs + (uint32_t)((ky * hg.Wp + kx + 16 * j) * 16);
+                        tc_mma(tmem + (uint32_t)(tap * CIN), adz, tc_desc(ht, 128, hg.plane), id_w, (g | j) != 0);
+                    }
+                    tc_mma(tmem + (uint32_t)K, adz, tc_desc(ones_a + j * 256, 128, 128), id_b, (g | j) != 0);
+                }
+                tc_commit(bar0 + 8 * (S + st));
+            }
+            if (run) tc_commit(bar0 + 16 * S);
+            else atomicOr(err, 1);
+        }
+        __syncwarp();
+    } else {
+        // epilogue: warp 4 + e holds rows co = 16 e + lane (lanes 0-15)
+        const int e = warp - 4;
+        if (tc_mbar_wait(bar0 + 16 * S, 0)) {
+            tc_fence_after();
+            const int co = 16 * e + lane;
+            float *dst = a.part + (size_t)blockIdx.x * (CH * K + CH);
+#pragma unroll 1
+            for (int c0 = 0; c0 < (K + 8 + 31) / 32; ++c0) {
+                float v[32];
+                tc_ld32(tmem + ((uint32_t)(32 * e) << 16) + (uint32_t)(32 * c0), v);
+                if (lane < 16) {
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) {
+                        const int k = 32 * c0 + q;
+                        if (k < K) dst[(size_t)co * K + k] = v[q];
+                        else if (k == K) dst[(size_t)CH * K + co] = v[q];
+                    }
+                }
+            }
+        } else {
+            atomicOr(err, 1);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 8) {
+        tc_fence_after();
+        tc_dealloc(tmem, kHwCols);
+    }
 }
 
 // grad[q] = sum over splits (in order) of part[split * stride + q], q < count.
@@ -736,21 +1140,44 @@ cudaError_t dmalloc(T **p, size_t count) {
 
 unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            n = 0;
+    }
+    return n;
+}
+
+// The tensor-core kernels allocate all 512 TMEM columns of an SM; asking for
+// more than half of an SM's shared memory keeps a second CTA off the SM
+// (it would only wait in tcgen05.alloc for the first to finish).
+constexpr size_t kExclusiveSmem = 116 * 1024;
+
+// Raise a kernel's dynamic shared-memory limit to at least `bytes` (once per size).
+template <typename F>
+cudaError_t smem_limit(F *k, size_t bytes, size_t &set_to) {
+    if (bytes <= set_to) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess) set_to = bytes;
+    return e;
+}
+
 // Persistent launch of the tcgen05 convolution: as many CTAs as fit on the
 // device at once (shared memory limits them to one or two per SM, so that
 // their TMEM columns always fit in the 512 of an SM), at most one per tile.
 template <bool DGRAD, int CIN>
 cudaError_t launch_tc(const ConvArgs &a, int *err, cudaStream_t st) {
-    static int per_sm = 0, n_sm = 0;
-    const size_t smem = TcCfg<CIN>::SMEM;
+    static size_t set_to = 0;
+    static int per_sm = 0;
+    const size_t smem = std::max(TcCfg<CIN>::SMEM, kExclusiveSmem);
+    cudaError_t e = smem_limit(k_conv_tc<DGRAD, CIN>, smem, set_to);
+    if (e != cudaSuccess) return e;
     if (per_sm == 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_conv_tc<DGRAD, CIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        int dev = 0;
-        if (e == cudaSuccess) e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_tc<DGRAD, CIN>, kTcThreads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_tc<DGRAD, CIN>, kTcThreads, smem);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
         if (per_sm * kTcCols > 512) per_sm = 512 / kTcCols;
@@ -758,8 +1185,34 @@ cudaError_t launch_tc(const ConvArgs &a, int *err, cudaStream_t st) {
     if (DGRAD && a.stride != 2) return cudaErrorInvalidValue;   // parity classes assume stride 2
     const long long tiles = tc_tile<DGRAD>(a, 0, nullptr);
     if (tiles == 0) return cudaSuccess;
-    const unsigned grid = (unsigned)std::min<long long>(tiles, (long long)n_sm * per_sm);
+    const unsigned grid = (unsigned)std::min<long long>(tiles, (long long)sm_count() * per_sm);
     k_conv_tc<DGRAD, CIN><<<grid, kTcThreads, smem, st>>>(a, err);
+    return cudaGetLastError();
+}
+
+// Stride-1 forward convolution on shifted windows: persistent, as many CTAs
+// as fit (shared memory limits them to one or two per SM, whose TMEM columns
+// then fit in the 512 of an SM), at most one per tile.
+template <int CIN>
+cudaError_t launch_halo_fwd(const ConvArgs &a, int *err, cudaStream_t st) {
+    static size_t set_to = 0;
+    static int per_sm = 0, per_sm_for = -1;
+    const HaloGeo hg = halo_geo(a.Ho);
+    const size_t smem = std::max(HaloCfg<CIN>::smem(hg), kExclusiveSmem);
+    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+    cudaError_t e = smem_limit(k_conv_halo<CIN>, smem, set_to);
+    if (e != cudaSuccess) return e;
+    if (per_sm_for != a.Ho) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_halo<CIN>, kTcThreads, smem);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        if (per_sm * kTcCols > 512) per_sm = 512 / kTcCols;
+        per_sm_for = a.Ho;
+    }
+    const long long tiles = (long long)a.B * hg.per_img;
+    if (tiles == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)std::min<long long>(tiles, (long long)sm_count() * per_sm);
+    k_conv_halo<CIN><<<grid, kTcThreads, smem, st>>>(a, err);
     return cudaGetLastError();
 }
 
@@ -777,7 +1230,7 @@ cudaError_t launch_conv_fwd(const CnnState &S, int layer, const bf16 *in, const 
     } else {
         a.w = S.w3; a.bias = S.master + S.off_b3; a.out = S.a3; a.Hi = S.H2; a.Ho = S.H3; a.stride = 2;
     }
-    if (layer == 1 && S.C0 == 32) return launch_tc<false, 32>(a, S.d_err, st);
+    if (layer == 1) return S.C0 == 32 ? launch_halo_fwd<32>(a, S.d_err, st) : launch_halo_fwd<64>(a, S.d_err, st);
     return launch_tc<false, 64>(a, S.d_err, st);
 }
 
@@ -815,6 +1268,32 @@ cudaError_t launch_wgrad(const CnnState &S, int layer, const bf16 *in, const int
         a.dz = S.dz2; a.Hi = S.H1; a.Ho = S.H2; a.stride = 2; cin = CH; off_w = S.off_w2;
     } else {
         a.dz = S.dz3; a.Hi = S.H2; a.Ho = S.H3; a.stride = 2; cin = CH; off_w = S.off_w3;
+    }
+    if (layer == 1 && cin == 32) {
+        // shifted windows on tcgen05, one CTA per SM
+        static size_t set_to = 0;
+        HaloWgArgs h{};
+        h.dz = a.dz;
+        h.in = in;
+        h.perm = perm;
+        h.b0 = b0;
+        h.B = B;
+        h.H = a.Ho;
+        h.part = S.wpart;
+        const HaloGeo hg = halo_geo(h.H);
+        const size_t smem = std::max(wgrad_halo_smem(hg), kExclusiveSmem);
+        if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+        cudaError_t e = smem_limit(k_wgrad_halo, smem, set_to);
+        if (e != cudaSuccess) return e;
+        const long long tiles = (long long)B * hg.per_img;
+        const int grid = (int)std::min<long long>(std::min<long long>(tiles, sm_count()), 296);
+        if (grid < 1) return cudaErrorInvalidConfiguration;
+        k_wgrad_halo<<<grid, kTcThreads, smem, st>>>(h, S.d_err);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        const int K = 9 * cin;
+        k_sum_parts<<<blocks_for(CH * K + CH, 32), 256, 0, st>>>(S.wpart, grid, CH * K + CH, (long long)CH * K + CH,
+                                                                S.grad + off_w);
+        return cudaGetLastError();
     }
     const long long M = (long long)B * a.Ho * a.Ho;
     const int splits = n_splits(M);
@@ -979,7 +1458,7 @@ synim_status synim_cnn_init(synim_ctx *ctx, const float *params, const double *n
     if (!params || !norm) return cfail(ctx, SYNIM_ERR_INVALID_ARG, "cnn_init: params and norm are required");
     int n_sub = 0, C = 0;
     synim_probe_query(ctx, &n_sub, &C, nullptr);
-    if (C % 32 != 0) return cfail(ctx, SYNIM_ERR_SHAPE, "cnn_init: 2 n_modes must be a multiple of 32");
+    if (C != 32 && C != 64) return cfail(ctx, SYNIM_ERR_SHAPE, "cnn_init: 2 n_modes must be 32 or 64");
     for (int k = 0; k < 4; ++k)
         if (!(norm[4 + k] > 0.0)) return cfail(ctx, SYNIM_ERR_INVALID_ARG, "cnn_init: ranges must be > 0");
     int prev = -1;
