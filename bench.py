@@ -40,7 +40,7 @@ UNIT = "columns/s"
 # DRAM bytes (read + write) of one k_im launch on the MCAO workload, from the
 # one-pass ncu capture summarised in profiles/k_im_mcao_dram_full.md; valid only
 # for the kernel source whose hash is recorded with it.
-TRAFFIC = {"kernel_sha1": "3b8134129102ae511dc451abb25d72bd088a7bde", "bytes_per_launch": 138.97e6 + 1.33e9}
+TRAFFIC = {"kernel_sha1": "0b9cdd00062ab39449a9366bb555785cc7090ab8", "bytes_per_launch": 138.47e6 + 1.33e9}
 
 
 def kernel_sha1() -> str:
@@ -76,18 +76,62 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+    """SM clocks and clock-event (throttle) reasons sampled during the timed
+    region: through NVML every 5 ms from a thread (read-only queries), else
+    nvidia-smi every 200 ms."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # NVML clock-event reason bits
+    REASONS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40}
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
         self.file = None
+        self.thread = None
+        self.samples = []
+        self.max_mhz = None
+        self.stop_flag = None
+        self.nvml_error = None
+
+    def _nvml_handle(self):
+        import pynvml
+        pynvml.nvmlInit()
+        try:
+            import torch
+            bus = torch.cuda.get_device_properties(self.gpu).pci_bus_id
+            dom = torch.cuda.get_device_properties(self.gpu).pci_domain_id
+            dev = torch.cuda.get_device_properties(self.gpu).pci_device_id
+            return pynvml, pynvml.nvmlDeviceGetHandleByPciBusId(f"{dom:08x}:{bus:02x}:{dev:02x}.0".encode())
+        except Exception:
+            return pynvml, pynvml.nvmlDeviceGetHandleByIndex(self.gpu)
 
     def start(self):
+        import threading
+        try:
+            nv, h = self._nvml_handle()
+            self.max_mhz = float(nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM))
+            get_reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                nv.nvmlDeviceGetCurrentClocksThrottleReasons
+            self.stop_flag = threading.Event()
+
+            def run():
+                while not self.stop_flag.is_set():
+                    try:
+                        self.samples.append((float(nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)), int(get_reasons(h))))
+                    except Exception:
+                        pass
+                    self.stop_flag.wait(0.005)
+
+            self.samples.append((float(nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)), int(get_reasons(h))))
+            self.thread = threading.Thread(target=run, daemon=True)
+            self.thread.start()
+            return
+        except Exception as e:
+            self.thread = None
+            self.nvml_error = f"{type(e).__name__}: {e}"[:120]
         try:
             self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(
@@ -97,6 +141,14 @@ class ClockSampler:
             self.proc = None
 
     def stop(self):
+        if self.thread is not None:
+            self.stop_flag.set()
+            self.thread.join(timeout=5)
+            if not self.samples:
+                return None
+            reasons = sorted(n for n, bit in self.REASONS.items() if any(r & bit for _, r in self.samples))
+            return {"sm_mhz": statistics.median(m for m, _ in self.samples), "sm_max_mhz": self.max_mhz,
+                    "reasons": reasons, "samples": len(self.samples), "source": "nvml, 5 ms"}
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -122,7 +174,7 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": "nvidia-smi, 200 ms", "nvml_unavailable": self.nvml_error}
 
 
 def cpu_oracle_sample(wl, seconds: float, seed: int = 0):
