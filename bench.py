@@ -264,6 +264,61 @@ def learned_flops_per_sample(h0: int = 40, c0: int = 32):
     return fwd, fwd + bwd
 
 
+def run_sensitivity(args):
+    """Throughput of the tangent (IM + 4 tangents) and adjoint passes on the ELT-scale single-WFS
+    geometry (81x81 DM on 480x480, 68x68 SH), against the HBM roofline."""
+    import torch
+    from paper_2606_07759_b300.synim import SynIM
+    wl = W.elt_single()
+    s = SynIM(wl.dms, wl.wfss, profile=True, autotune=True)
+    ims = s.alloc_outputs()
+    tans = [[torch.empty_like(t) for _ in range(4)] for t in ims]
+    mis = wl.misregs
+    im_bytes = sum(t.numel() * 4 for t in ims)
+    win_bytes = sum(dm.n_act * s.dm_window(d) ** 2 * 4 for d, dm in enumerate(wl.dms))
+    cols = sum(dm.n_act for dm in wl.dms) * len(wl.wfss)
+    steps = max(5, args.steps // 5)
+    stream = torch.cuda.current_stream()
+    peak, peak_kind = peaks()
+    out = {"workload": "elt_single: 81x81 DM on 480x480 (obstruction 0.28), 68x68 SH, M = 544",
+           "columns_per_step": cols, "steps": steps}
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        s.check()
+        s.kernel_ms()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        s.check()
+        k_ms, k_n = s.kernel_ms()
+        return e0.elapsed_time(e1) / steps, k_ms / max(k_n, 1)
+
+    # tangents: the IM and its 4 derivatives written per column
+    t_ms, k_ms = timed(lambda: s.sensitivity(mis, ims, tans))
+    alg = 5 * im_bytes + win_bytes
+    out["tangents"] = {"columns_per_s": cols / (t_ms / 1e3), "ms_per_step": t_ms, "kernel_ms": k_ms,
+                       "alg_bytes_per_launch": alg,
+                       "roofline": {"bound": "hbm", "achieved": alg / (k_ms / 1e3) / 1e9, "peak": peak,
+                                    "unit": "GB/s", "frac": alg / (k_ms / 1e3) / 1e9 / peak, "peak_kind": peak_kind}}
+    # adjoint: grad_p = sum(grad_IM * T_k), the cotangent IM read once per column
+    g = [torch.randn_like(t) for t in ims]
+    t_ms, k_ms = timed(lambda: s.vjp(mis, g))
+    alg = im_bytes + win_bytes
+    out["vjp"] = {"columns_per_s": cols / (t_ms / 1e3), "ms_per_step": t_ms, "kernel_ms": k_ms,
+                  "alg_bytes_per_launch": alg,
+                  "note": "each step returns grad_p to the host (one synchronisation)",
+                  "roofline": {"bound": "hbm", "achieved": alg / (k_ms / 1e3) / 1e9, "peak": peak,
+                               "unit": "GB/s", "frac": alg / (k_ms / 1e3) / 1e9 / peak, "peak_kind": peak_kind}}
+    s.close()
+    return out
+
+
 def run_learned(args):
     """Training throughput, accuracy and batch-1 latency of the misregistration estimators."""
     import torch
@@ -430,6 +485,8 @@ def run_synim(args):
                                 "sample": f"{cols} random columns over all {n_pairs} pairs, dense FP64 oracle, "
                                           f"{secs:.1f} s"}
     s.close()
+    if rank == 0 and world == 1 and not args.no_sensitivity:
+        line["sensitivity"] = run_sensitivity(args)
     if rank == 0 and world == 1 and not args.no_learned:
         line["learned"] = run_learned(args)
     if rank == 0:
@@ -454,7 +511,11 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-estimator measurements")
     ap.add_argument("--learned-train", type=int, default=200_000)
-    ap.add_argument("--learned-epochs", type=int, default=10)
+    ap.add_argument("--learned-epochs", type=int, default=40)
+    ap.add_argument("--no-sensitivity", action="store_true",
+                    help="skip the tangent / adjoint throughput measurements")
+    ap.add_argument("--sensitivity-only", action="store_true",
+                    help="diagnostic: run only the tangent / adjoint measurements and print them")
     ap.add_argument("--learned-only", action="store_true",
                     help="diagnostic: run only the learned-estimator measurements and print them")
     args = ap.parse_args(argv)
@@ -464,6 +525,9 @@ def main(argv=None):
         return run_reference(args)
     if args.learned_only:
         print(json.dumps({"learned": run_learned(args)}), flush=True)
+        return 0
+    if args.sensitivity_only:
+        print(json.dumps({"sensitivity": run_sensitivity(args)}), flush=True)
         return 0
     return run_synim(args)
 
