@@ -108,6 +108,9 @@ typedef struct {
                                 segment) on that call's inputs and keep the fastest */
     int32_t profile;         /* 1 = record CUDA events around every IM-kernel launch
                                 (read back with synim_im_kernel_ms) */
+    int64_t device_mem_cap;  /* bytes of device memory create may take (the context's
+                                holdings plus the temporary cube staging); 0 = no cap.
+                                Exceeding it fails create with SYNIM_ERR_OOM */
 } synim_opts;
 
 /*
@@ -176,6 +179,16 @@ synim_status synim_im_vjp(synim_ctx *ctx, const synim_misreg *mis, const float *
  * gave up).  Clears the flag.
  */
 synim_status synim_im_check(synim_ctx *ctx, void *cuda_stream);
+
+/*
+ * Self-test of the bounded device waits (the mbarrier waits of the
+ * tensor-core kernels use the same helper): one thread waits on an mbarrier
+ * that nothing arrives at, gives up after limit_clocks SM clocks (clamped to
+ * 1 .. 2^31), raises the context's error flag and returns; the call then
+ * synchronises `cuda_stream` and reports the flag like synim_im_check.
+ * Expected result: SYNIM_ERR_TIMEOUT, with the context still usable.
+ */
+synim_status synim_wait_selftest(synim_ctx *ctx, int64_t limit_clocks, void *cuda_stream);
 
 /*
  * With opts.profile = 1: wait for the IM-kernel launches recorded since the

@@ -40,7 +40,7 @@ class synim_misreg(ctypes.Structure):
 
 class synim_opts(ctypes.Structure):
     _fields_ = [("threads_per_cta", c_int32), ("ctas_per_sm", c_int32), ("use_graph", c_int32),
-                ("autotune", c_int32), ("profile", c_int32)]
+                ("autotune", c_int32), ("profile", c_int32), ("device_mem_cap", ctypes.c_int64)]
 
 
 class synim_train_opts(ctypes.Structure):
@@ -64,6 +64,7 @@ SIGNATURES = {
     "synim_im_vjp": (c_int32, [c_void_p, ctypes.POINTER(synim_misreg), ctypes.POINTER(c_void_p),
                                ctypes.POINTER(c_double), c_void_p]),
     "synim_im_check": (c_int32, [c_void_p, c_void_p]),
+    "synim_wait_selftest": (c_int32, [c_void_p, ctypes.c_int64, c_void_p]),
     "synim_dm_window": (c_int32, [c_void_p, c_int32, ctypes.POINTER(c_int32)]),
     "synim_im_kernel_ms": (c_int32, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int32)]),
     "synim_im_compute_noalloc": (c_int32, [ctypes.POINTER(synim_dm_desc), ctypes.POINTER(synim_wfs_desc),
@@ -124,6 +125,12 @@ class SynimError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
         self.status = status
+
+
+def last_error(ctx=None) -> str:
+    """Message of the context's last failure (of the last failed create with ctx = None)."""
+    msg = load().synim_last_error(ctx)
+    return (msg or b"").decode()
 
 
 def check(status: int, ctx=None):

@@ -17,6 +17,7 @@
 
 #include "synim.h"
 #include "synim_internal.h"
+#include "synim_tc.cuh"
 
 using namespace synim;
 
@@ -54,10 +55,18 @@ synim_status cuda_fail(synim_ctx *c, cudaError_t e, const char *what) {
     return fail(c, e == cudaErrorMemoryAllocation ? SYNIM_ERR_OOM : SYNIM_ERR_CUDA, m);
 }
 
+// Device allocation charged against the context's memory cap (if any).
+cudaError_t capped_malloc(synim_ctx *c, void **q, size_t bytes) {
+    if (c->mem_cap > 0 && c->mem_used + bytes > (size_t)c->mem_cap) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaMalloc(q, bytes);
+    if (e == cudaSuccess) c->mem_used += bytes;
+    return e;
+}
+
 template <typename T>
 cudaError_t dev_alloc(synim_ctx *c, T **p, size_t count) {
     void *q = nullptr;
-    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+    cudaError_t e = capped_malloc(c, &q, std::max<size_t>(count, 1) * sizeof(T));
     if (e == cudaSuccess) {
         c->dev_allocs.push_back(q);
         *p = static_cast<T *>(q);
@@ -283,6 +292,21 @@ namespace {
 // ---------------------------------------------------------------------------
 // ABI
 // ---------------------------------------------------------------------------
+namespace synim {
+// One warp; lane 0 waits on an mbarrier that nothing arrives at, through the
+// bounded wait of the tensor-core kernels, and raises ERR_TIMEOUT when it
+// gives up.
+__global__ void k_wait_selftest(long long limit, int *err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        tc_mbar_init(tc_smem(&bar), 1);
+        tc_fence_mbar_init();
+    }
+    __syncwarp();
+    if (threadIdx.x == 0 && !tc_mbar_wait(tc_smem(&bar), 0, limit)) atomicOr(err, ERR_TIMEOUT);
+}
+}  // namespace synim
+
 extern "C" {
 
 const char *synim_status_string(synim_status s) {
@@ -360,6 +384,7 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
         c->use_graph = opts->use_graph != 0;
         c->autotune = opts->autotune != 0;
         c->profile = opts->profile != 0;
+        c->mem_cap = std::max<int64_t>(0, opts->device_mem_cap);
     }
     if (c->threads % 32 != 0 || c->threads < 64 || c->threads > 256) {
         delete c;
@@ -381,14 +406,21 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
         const float *cube = Dd.ifs;
         float *staging = nullptr;
         if (!Dd.ifs_on_device) {
-            if ((e = cudaMalloc(&staging, cube_n * sizeof(float))) != cudaSuccess)
+            if ((e = capped_malloc(c, reinterpret_cast<void **>(&staging), cube_n * sizeof(float))) != cudaSuccess)
                 return bail(cuda_fail(c, e, "cube staging"));
             if ((e = cudaMemcpy(staging, Dd.ifs, cube_n * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess) {
                 cudaFree(staging);
+                c->mem_used -= cube_n * sizeof(float);
                 return bail(cuda_fail(c, e, "cube upload"));
             }
             cube = staging;
         }
+        auto free_staging = [&]() {
+            if (!staging) return;
+            cudaFree(staging);
+            c->mem_used -= cube_n * sizeof(float);
+            staging = nullptr;
+        };
         int *d_box = nullptr;
         std::vector<int> box(4 * (size_t)H.n_act);
         e = cudaMalloc(&d_box, (box.size() + 1) * sizeof(int));
@@ -396,7 +428,7 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
         if (e == cudaSuccess) e = cudaMemcpy(box.data(), d_box, box.size() * sizeof(int), cudaMemcpyDeviceToHost);
         cudaFree(d_box);
         if (e != cudaSuccess) {
-            cudaFree(staging);
+            free_staging();
             return bail(cuda_fail(c, e, "support scan"));
         }
         int W = 1;
@@ -424,7 +456,7 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
         if (e == cudaSuccess) e = dev_alloc(c, &d_win, (size_t)H.n_act * stride);
         if (e == cudaSuccess) e = launch_pack(cube, H.n_act, H.N, d_org, W, Wp, stride, d_win, 0);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
-        cudaFree(staging);
+        free_staging();
         if (e != cudaSuccess) return bail(cuda_fail(c, e, "window packing"));
         uint8_t *d_mask = nullptr;
         if (Dd.mask) {
@@ -605,9 +637,20 @@ synim_status synim_im_check(synim_ctx *ctx, void *cuda_stream) {
         return cuda_fail(ctx, e, "error flag read");
     const int flag = *ctx->h_err;
     cudaMemset(ctx->d_err, 0, sizeof(int));
-    if (flag & ERR_TIMEOUT) return fail(ctx, SYNIM_ERR_TIMEOUT, "window staging wait timed out");
+    if (flag & ERR_TIMEOUT) return fail(ctx, SYNIM_ERR_TIMEOUT, "a bounded device wait timed out");
     if (flag & ERR_ARENA) return fail(ctx, SYNIM_ERR_SHAPE, "slope values exceeded their shared-memory buffer");
     return SYNIM_OK;
+}
+
+synim_status synim_wait_selftest(synim_ctx *ctx, int64_t limit_clocks, void *cuda_stream) {
+    if (!ctx) return SYNIM_ERR_INVALID_ARG;
+    DeviceGuard guard(ctx->device);
+    const long long lim = std::min<long long>(std::max<long long>(limit_clocks, 1), 1LL << 31);
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    k_wait_selftest<<<1, 32, 0, s>>>(lim, ctx->d_err);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "wait self-test launch");
+    return synim_im_check(ctx, cuda_stream);
 }
 
 }  // extern "C"

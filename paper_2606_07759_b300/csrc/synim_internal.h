@@ -148,6 +148,8 @@ struct synim_ctx {
     synim::WfsHost wh[SYNIM_MAX_WFS];
     synim::Geo geo{};
     std::vector<void *> dev_allocs;
+    int64_t mem_cap = 0;      // device bytes create may take (0 = no cap)
+    size_t mem_used = 0;      // device bytes taken by create so far
     std::vector<void *> host_allocs;
     synim::DevPair *d_pairs = nullptr;
     synim::DevPair *h_pairs[synim::NSLOT] = {};

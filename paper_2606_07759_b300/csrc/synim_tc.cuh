@@ -59,11 +59,12 @@ __device__ __forceinline__ bool tc_mbar_try_wait(uint32_t bar, uint32_t parity) 
 __device__ __forceinline__ void tc_mbar_arrive(uint32_t bar) {
     asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(bar) : "memory");
 }
-// Bounded wait: gives up after ~2^31 clocks (about a second).
-__device__ __forceinline__ bool tc_mbar_wait(uint32_t bar, uint32_t parity) {
+// Bounded wait: gives up after `limit` SM clocks (default 2^31, about a
+// second) and returns false.
+__device__ __forceinline__ bool tc_mbar_wait(uint32_t bar, uint32_t parity, long long limit = 1LL << 31) {
     const long long t0 = clock64();
     while (!tc_mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > (1LL << 31)) return false;
+        if (clock64() - t0 > limit) return false;
     }
     return true;
 }

@@ -38,7 +38,7 @@ class SynIM:
 
     def __init__(self, dms: Sequence, wfss: Sequence, threads_per_cta: int = 0, ctas_per_sm: int = 0,
                  use_graph: bool = True, profile: bool = False, device: Optional[torch.device] = None,
-                 autotune: bool = False):
+                 autotune: bool = False, device_mem_cap: int = 0):
         self._L = abi.load()
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.n_dm, self.n_wfs = len(dms), len(wfss)
@@ -82,7 +82,7 @@ class SynIM:
             d.slope_scale = float(getattr(w, "slope_scale", 1.0))
             ww[q] = d
         opts = abi.synim_opts(int(threads_per_cta), int(ctas_per_sm), 1 if use_graph else 0, 1 if autotune else 0,
-                              1 if profile else 0)
+                              1 if profile else 0, int(device_mem_cap))
         ctx = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             abi.check(self._L.synim_im_create(dd, self.n_dm, ww, self.n_wfs, ctypes.byref(opts),
@@ -158,6 +158,10 @@ class SynIM:
 
     def check(self, stream=None):
         abi.check(self._L.synim_im_check(self._ctx, self._stream(stream)), self._ctx)
+
+    def wait_selftest(self, limit_clocks: int = 1 << 20, stream=None) -> int:
+        """Status of the bounded-wait self-test (SYNIM_ERR_TIMEOUT = 5 when the wait gave up)."""
+        return int(self._L.synim_wait_selftest(self._ctx, int(limit_clocks), self._stream(stream)))
 
     def sensitivity(self, misregs, out=None, d_out=None, stream=None):
         """IMs and their tangents dIM/dp_k, p = (shift_x_px, shift_y_px, rot_deg, mag).
