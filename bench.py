@@ -95,37 +95,78 @@ class ClockSampler:
         self.max_mhz = None
         self.stop_flag = None
         self.nvml_error = None
+        self.kind = None
 
-    def _nvml_handle(self):
-        import pynvml
-        pynvml.nvmlInit()
+    @staticmethod
+    def _nvml():
+        """(clock_sm(), reasons(), max_sm) readers: pynvml if importable, else the
+        driver's libnvidia-ml through ctypes (read-only queries)."""
         try:
-            import torch
-            bus = torch.cuda.get_device_properties(self.gpu).pci_bus_id
-            dom = torch.cuda.get_device_properties(self.gpu).pci_domain_id
-            dev = torch.cuda.get_device_properties(self.gpu).pci_device_id
-            return pynvml, pynvml.nvmlDeviceGetHandleByPciBusId(f"{dom:08x}:{bus:02x}:{dev:02x}.0".encode())
+            import pynvml as nv
+            nv.nvmlInit()
+            return "pynvml", nv
         except Exception:
-            return pynvml, pynvml.nvmlDeviceGetHandleByIndex(self.gpu)
+            pass
+        import ctypes
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit_v2 failed")
+        return "libnvidia-ml", lib
+
+    def _readers(self):
+        import ctypes
+        kind, nv = self._nvml()
+        import torch
+        pr = torch.cuda.get_device_properties(self.gpu)
+        bus = f"{pr.pci_domain_id:08x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0"
+        if kind == "pynvml":
+            try:
+                h = nv.nvmlDeviceGetHandleByPciBusId(bus.encode())
+            except Exception:
+                h = nv.nvmlDeviceGetHandleByIndex(self.gpu)
+            get_r = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                nv.nvmlDeviceGetCurrentClocksThrottleReasons
+            return (lambda: float(nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)), lambda: int(get_r(h)),
+                    float(nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)), kind)
+        h = ctypes.c_void_p()
+        if nv.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(h)) != 0 and \
+                nv.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.gpu), ctypes.byref(h)) != 0:
+            raise RuntimeError("no NVML handle for the device")
+        clk, mx, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        f_reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        SM = ctypes.c_int(1)   # NVML_CLOCK_SM
+
+        def clock():
+            if nv.nvmlDeviceGetClockInfo(h, SM, ctypes.byref(clk)) != 0:
+                raise RuntimeError("nvmlDeviceGetClockInfo")
+            return float(clk.value)
+
+        def reasons():
+            if f_reasons(h, ctypes.byref(rs)) != 0:
+                raise RuntimeError("clock event reasons")
+            return int(rs.value)
+
+        if nv.nvmlDeviceGetMaxClockInfo(h, SM, ctypes.byref(mx)) != 0:
+            raise RuntimeError("nvmlDeviceGetMaxClockInfo")
+        return clock, reasons, float(mx.value), kind
 
     def start(self):
         import threading
         try:
-            nv, h = self._nvml_handle()
-            self.max_mhz = float(nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM))
-            get_reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
-                nv.nvmlDeviceGetCurrentClocksThrottleReasons
+            clock, reasons, self.max_mhz, kind = self._readers()
+            self.kind = kind
             self.stop_flag = threading.Event()
 
             def run():
                 while not self.stop_flag.is_set():
                     try:
-                        self.samples.append((float(nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)), int(get_reasons(h))))
+                        self.samples.append((clock(), reasons()))
                     except Exception:
                         pass
                     self.stop_flag.wait(0.005)
 
-            self.samples.append((float(nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)), int(get_reasons(h))))
+            self.samples.append((clock(), reasons()))
             self.thread = threading.Thread(target=run, daemon=True)
             self.thread.start()
             return
@@ -148,7 +189,7 @@ class ClockSampler:
                 return None
             reasons = sorted(n for n, bit in self.REASONS.items() if any(r & bit for _, r in self.samples))
             return {"sm_mhz": statistics.median(m for m, _ in self.samples), "sm_max_mhz": self.max_mhz,
-                    "reasons": reasons, "samples": len(self.samples), "source": "nvml, 5 ms"}
+                    "reasons": reasons, "samples": len(self.samples), "source": f"NVML ({self.kind}), 5 ms"}
         if self.proc is None:
             return None
         self.proc.terminate()
