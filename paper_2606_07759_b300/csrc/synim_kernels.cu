@@ -594,6 +594,28 @@ __device__ __forceinline__ void edge_sum(const DevWFS &WF, const ItemWfs &s, con
     }
 }
 
+// Zero rows [r0, r1) of a 16-byte-aligned column: lanes store the unaligned
+// head and tail, lane 0 issues bulk copies (cp.async.bulk, at most 4 KB each)
+// of the CTA's shared zero buffer over the aligned middle.
+constexpr int kZeroFloats = 1024;
+__shared__ __align__(128) float4 s_zero[kZeroFloats / 4];   // zeroed by k_im at entry
+
+__device__ __forceinline__ void bulk_zero(float *col, int r0, int r1, int lane) {
+    if (r0 >= r1) return;
+    const int h = min(r1, (r0 + 3) & ~3), t = max(h, r1 & ~3);
+    if (lane < h - r0) col[r0 + lane] = 0.f;
+    if (lane < r1 - t) col[t + lane] = 0.f;
+    if (lane == 0 && h < t) {
+        const uint32_t zsrc = (uint32_t)__cvta_generic_to_shared(s_zero);
+        for (int q = h; q < t; q += kZeroFloats) {
+            const int n = min(kZeroFloats, t - q) * 4;
+            asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(col + q), "r"(zsrc), "r"(n)
+                         : "memory");
+        }
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    }
+}
+
 // Zero rows [r0, r1) of one output column (16-byte stores where aligned).
 __device__ __forceinline__ void zero_rows(float *col, int r0, int r1, bool vec4, int lane) {
     if (r0 >= r1) return;
@@ -676,9 +698,15 @@ __device__ __forceinline__ void warp_column(const Geo &g, const DevPair *__restr
             float *base = (o == 0) ? P.im : P.dim[o - 1];
             cols[o] = base ? base + (size_t)a * n2 : nullptr;
             if (!cols[o]) continue;
-            zero_rows(cols[o], 0, vr0, vec4, lane);
-            zero_rows(cols[o], vr1, nv + vr0, vec4, lane);
-            zero_rows(cols[o], nv + vr1, n2, vec4, lane);
+            if (vec4) {
+                bulk_zero(cols[o], 0, vr0, lane);
+                bulk_zero(cols[o], vr1, nv + vr0, lane);
+                bulk_zero(cols[o], nv + vr1, n2, lane);
+            } else {
+                zero_rows(cols[o], 0, vr0, false, lane);
+                zero_rows(cols[o], vr1, nv + vr0, false, lane);
+                zero_rows(cols[o], nv + vr1, n2, false, lane);
+            }
         }
     }
     if (s.empty) return;
@@ -800,7 +828,9 @@ __device__ __forceinline__ void warp_column(const Geo &g, const DevPair *__restr
 
 // One warp per (actuator, sensor) column, the columns of one actuator in
 // consecutive warps so that they share its window through L1.  Warps never
-// wait for one another.
+// wait for one another.  The long zero runs of a column are bulk copies of a
+// shared zero buffer (TMA engine), which each issuing lane waits to have been
+// read before the CTA exits.
 template <int MODE>
 __global__ void __launch_bounds__(256, (MODE == MODE_FWD) ? 4 : 2)
 k_im(const __grid_constant__ Geo g, const DevPair *__restrict__ pairs, int *__restrict__ counter,
@@ -810,6 +840,11 @@ k_im(const __grid_constant__ Geo g, const DevPair *__restrict__ pairs, int *__re
     (void)counter;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     float *wbuf = smem_f + (size_t)warp * g.seg_floats;
+    if constexpr (MODE != MODE_VJP) {
+        for (int q = threadIdx.x; q < kZeroFloats / 4; q += blockDim.x) s_zero[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic zeros -> bulk-copy reads
+        __syncthreads();
+    }
     const long n_units = (long)g.n_items * g.n_wfs;
     for (long u = (long)blockIdx.x * nw + warp; u < n_units; u += (long)gridDim.x * nw) {
         const int item = (int)(u / g.n_wfs), w = (int)(u - (long)item * g.n_wfs);
@@ -817,6 +852,8 @@ k_im(const __grid_constant__ Geo g, const DevPair *__restrict__ pairs, int *__re
         decode_item(g, item, d, a);
         warp_column<MODE, NV>(g, pairs, d, a, w, wbuf, g.seg_floats, lane, err, gp);
     }
+    // the zero buffer must outlive the bulk copies that read it
+    if (MODE != MODE_VJP && lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 
 size_t im_smem_bytes(const Geo &g) { return (size_t)8 * g.seg_floats * 4; }
