@@ -180,6 +180,73 @@ def elt_single(seed: int = 2, n_side: int = 81, grid_n: int = 480, n_sub: int = 
     return Workload("elt_single", [dm], [wfs], [_uniform_misreg(rng, 1.0, 1.0, 0.01)])
 
 
+def dense(wl: Workload) -> Workload:
+    """The same workload with support_eps = 0: every influence function is
+    resampled over its whole plane (the dense-cube accounting)."""
+    dms = [dataclasses.replace(dm, support_eps=0.0) for dm in wl.dms]
+    return Workload(wl.name + "_dense", dms, wl.wfss, wl.misregs)
+
+
+def cosine_modes(N: int, dd: float, D: float, mask: np.ndarray, n_modes: int) -> np.ndarray:
+    """The first n_modes 2-D cosines cos(pi n (x / D + 1/2)) cos(pi m (y / D + 1/2))
+    over the mask (pixel centres, x along columns), piston excluded, ordered by
+    n + m then n: float32 [n_modes, N, N]."""
+    c = (np.arange(N) + 0.5) * dd - D / 2.0
+    orders = sorted(((n, m) for n in range(2 * int(np.sqrt(n_modes)) + 4)
+                     for m in range(2 * int(np.sqrt(n_modes)) + 4) if n + m > 0), key=lambda t: (t[0] + t[1], t[0]))
+    orders = orders[:n_modes]
+    cube = np.empty((n_modes, N, N), np.float32)
+    mf = mask.astype(np.float32)
+    for q, (n, m) in enumerate(orders):
+        cx = np.cos(np.pi * n * (c / D + 0.5)).astype(np.float32)
+        cy = np.cos(np.pi * m * (c / D + 0.5)).astype(np.float32)
+        np.multiply(np.outer(cy, cx), mf, out=cube[q])
+    return cube
+
+
+def modal_elt(n_modes: int = 4519, seed: int = 8, grid_n: int = 480, n_sub: int = 68) -> Workload:
+    """A modal cube at ELT scale standing in for a mirror-mode set with global
+    support: n_modes 2-D cosine modes over the 480x480 pupil (obstruction
+    0.28), one 68x68 Shack-Hartmann (k = 8, M = 544), support_eps = 0."""
+    D, obs = 39.0, 0.28
+    N = grid_n
+    dd = D / N
+    mask = disc_mask(N, N / 2.0, obs * N / 2.0)
+    cube = cosine_modes(N, dd, D, mask, n_modes)
+    k = -(-N // n_sub)
+    M = k * n_sub
+    wfs = WFS(n_sub, M, D, 0.0, (0.0, 0.0), disc_mask(M, M / 2.0, obs * M / 2.0), obstruction=obs)
+    xy = np.tile([N / 2.0, N / 2.0], (n_modes, 1))
+    dm = DM(cube, mask, dd, 0.0, xy, float(N), support_eps=0.0)
+    rng = np.random.default_rng(seed)
+    return Workload("modal_elt", [dm], [wfs], [_uniform_misreg(rng, 1.0, 1.0, 0.01)])
+
+
+def modal_scao(n_max: int = 8, seed: int = 7) -> Workload:
+    """A modal cube on the SCAO small geometry: the 2-D cosine modes
+    cos(pi n (x / D + 1/2)) cos(pi m (y / D + 1/2)) over the DM mask, 0 <= n, m
+    <= n_max without piston, global support (support_eps = 0)."""
+    D, N, obs = 8.0, 80, 0.2
+    dd = D / N
+    mask = disc_mask(N, N / 2.0, obs * N / 2.0)
+    c = (np.arange(N) + 0.5) * dd - D / 2.0          # pixel centres in metres
+    X, Y = np.meshgrid(c, c)
+    modes, xy = [], []
+    for n in range(n_max + 1):
+        for m in range(n_max + 1):
+            if n == 0 and m == 0:
+                continue
+            modes.append((np.cos(np.pi * n * (X / D + 0.5)) * np.cos(np.pi * m * (Y / D + 0.5)) * mask)
+                         .astype(np.float32))
+            xy.append((N / 2.0, N / 2.0))
+    cube = np.stack(modes)
+    n_sub, M = 10, 80
+    wfs = WFS(n_sub, M, D, 0.0, (0.0, 0.0), disc_mask(M, M / 2.0, obs * M / 2.0), obstruction=obs)
+    dm = DM(cube, mask, dd, 0.0, np.array(xy), float(N), support_eps=0.0)
+    rng = np.random.default_rng(seed)
+    return Workload("modal_scao", [dm], [wfs], [_uniform_misreg(rng, 1.0, 1.0, 0.01)])
+
+
 def mcao_batched(seed: int = 3, scale: float = 1.0) -> Workload:
     """3 DMs (0, 4, 12.7 km) x (6 LGS 68x68 at 7.5" + 3 NGS 2x2 at 55"), 39 m pupil.
 
