@@ -118,7 +118,7 @@ typedef struct {
  * window (|IF| > support_eps * the DM's largest |IF|), packs the windows into device memory,
  * and builds the per-sensor subaperture tables (Sec. 2.2) and derivative
  * stencils.  The caller may free every input as soon as create returns.
- * dms[n_dm], wfs[n_wfs]: 1 <= n_dm <= 8, 1 <= n_wfs <= 16.
+ * dms[n_dm], wfs[n_wfs]: 1 <= n_dm <= 16, 1 <= n_wfs <= 16.
  * On success *out owns device memory until synim_im_destroy.
  */
 synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim_wfs_desc *wfs,

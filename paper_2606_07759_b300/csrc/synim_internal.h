@@ -28,7 +28,7 @@
 #include "synim.h"
 #include "synim_geom.h"
 
-#define SYNIM_MAX_DM 8
+#define SYNIM_MAX_DM 16
 #define SYNIM_MAX_WFS 16
 #define SYNIM_MAX_PAIRS (SYNIM_MAX_DM * SYNIM_MAX_WFS)
 

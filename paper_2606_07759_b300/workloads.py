@@ -292,6 +292,70 @@ def mcao_batched(seed: int = 3, scale: float = 1.0) -> Workload:
     return Workload("mcao_batched", dms, wfss, mis)
 
 
+def gaussian_cube_device(xy_px: np.ndarray, sigma_px: float, grid_n: int, mask: Optional[np.ndarray], device):
+    """gaussian_cube computed on a torch device (the same separable formula:
+    FP64 exponentials, FP32 outer product times the mask), for cubes too large
+    for host memory."""
+    import torch
+    ax = torch.arange(grid_n, dtype=torch.float64, device=device)
+    xy = torch.as_tensor(xy_px, dtype=torch.float64, device=device)
+    inv = 1.0 / (2.0 * sigma_px * sigma_px)
+    gx = torch.exp(-(ax[None, :] - xy[:, 0:1]) ** 2 * inv).float()
+    gy = torch.exp(-(ax[None, :] - xy[:, 1:2]) ** 2 * inv).float()
+    cube = torch.empty((xy.shape[0], grid_n, grid_n), dtype=torch.float32, device=device)
+    m = None if mask is None else torch.as_tensor(mask, dtype=torch.float32, device=device)
+    for a0 in range(0, xy.shape[0], 256):
+        a1 = min(xy.shape[0], a0 + 256)
+        blk = gy[a0:a1, :, None] * gx[a0:a1, None, :]
+        cube[a0:a1] = blk * m if m is not None else blk
+    return cube
+
+
+def mcao_dictionary(seed: int = 9, scale: float = 1.0, device=None) -> Workload:
+    """An LGS tomographic dictionary in the shape of the paper's MCAO run: 12
+    components (the 3 DMs of mcao_batched at 0, 4 and 12.7 km, plus 9 virtual
+    layers at 0.2-22 km on meta-pupils D + 2 h 80", i.e. 480-690 px grids, 70x70
+    actuator lattices) seen by the 6 LGS 68x68 sensors (7.5", 90 km): 72 IMs,
+    about 44,600 modes.  With ``device`` the cubes are generated there as torch
+    tensors (about 57 GB at full scale); otherwise as numpy arrays."""
+    D, obs, H_lgs = 39.0, 0.28, 90e3
+    N0 = max(16, int(round(480 * scale)))
+    dd = D / N0
+    lgs_field, meta_field = 7.5 * ARCSEC, 80.0 * ARCSEC
+    make = (lambda xy, sig, N, m: gaussian_cube_device(xy, sig, N, m, device)) if device is not None else gaussian_cube
+    dms = []
+    specs = [(0.0, 81), (4000.0, 49), (12700.0, 41)] + \
+            [(h, 70) for h in (200.0, 1000.0, 2000.0, 4500.0, 7000.0, 10000.0, 14000.0, 18000.0, 22000.0)]
+    for q, (h, n_side) in enumerate(specs):
+        n_side = max(5, int(round((n_side - 1) * scale)) + 1)
+        if q == 0:
+            mask = disc_mask(N0, N0 / 2.0, obs * N0 / 2.0)
+            xy, r, pitch_m = actuator_lattice(n_side, D, N0, dd)
+            xy = xy[r <= D / 2.0 + pitch_m + 1e-9]
+            pitch_px = pitch_m / dd
+            dms.append(DM(make(xy, coupling_sigma(pitch_px), N0, mask), mask, dd, 0.0, xy, pitch_px))
+            continue
+        d_meta = D + 2.0 * h * (55.0 * ARCSEC if q < 3 else meta_field)
+        N = int(math.ceil(d_meta / dd))
+        N += N % 2
+        mask = disc_mask(N, d_meta / (2.0 * dd))
+        xy, r, pitch_m = actuator_lattice(n_side, d_meta, N, dd)
+        xy = xy[r <= d_meta / 2.0 + pitch_m + 1e-9]
+        pitch_px = pitch_m / dd
+        dms.append(DM(make(xy, coupling_sigma(pitch_px), N, mask), mask, dd, h, xy, pitch_px))
+    wfss = []
+    n_lgs = max(2, int(round(68 * scale)))
+    k_lgs = -(-N0 // n_lgs)
+    M_lgs = k_lgs * n_lgs
+    for az in range(0, 360, 60):
+        a = math.radians(az)
+        wfss.append(WFS(n_lgs, M_lgs, D, H_lgs, (lgs_field * math.cos(a), lgs_field * math.sin(a)),
+                        disc_mask(M_lgs, M_lgs / 2.0, obs * M_lgs / 2.0), obstruction=obs))
+    rng = np.random.default_rng(seed)
+    mis = [_uniform_misreg(rng, 1.0, 1.0, 0.01) for _ in range(len(dms) * len(wfss))]
+    return Workload("mcao_dictionary", dms, wfss, mis)
+
+
 def probe_modes(dm: DM, D_m: float, n_modes: int = 16) -> np.ndarray:
     """Low-order 2-D cosine probe commands sampled at the actuator positions.
 
