@@ -180,6 +180,45 @@ synim_status synim_im_vjp(synim_ctx *ctx, const synim_misreg *mis, const float *
  */
 synim_status synim_im_check(synim_ctx *ctx, void *cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Tomographic projection (Sec. 3, tomographic projection matrices).
+ *
+ * The components of a context (its DMs and virtual layers) are seen from
+ * n_dir optimisation directions dirs_rad[j] = (theta_x, theta_y) by a
+ * source at infinity, on the pupil grid of sensor `wfs` (M x M, its pupil
+ * mask) binned bin x bin (M % bin == 0).  Entry (row, column) of a
+ * projection matrix P_X is the mean over the bin x bin fine pixels of the
+ * binned pixel of P(p) * bilinear(IF_a; A_j (p_col, p_row) + b_j), where:
+ *   - the columns are the actuators of the listed components, in order;
+ *   - the rows are direction-major, row = j (M / bin)^2 + binned pixel
+ *     (row-major);
+ *   - (A_j, b_j) is the composite affine with the direction's field angle,
+ *     no cone, no sensor rotation, magnification or shift, and no
+ *     misregistration (footprint shift h theta_j);
+ *   - there is no edge repair.
+ * ---------------------------------------------------------------------- */
+
+/* Rows of the projection matrices: n_dir (M / bin)^2. */
+synim_status synim_projection_rows(const synim_ctx *ctx, int32_t wfs, int32_t n_dir, int32_t bin, int64_t *rows);
+
+/* P_X of components comps[n_comp] into P (device, FP32, column-major
+ * [n_cols][rows]: each actuator's column contiguous).  Synchronises the
+ * stream before returning. */
+synim_status synim_projection_matrix(synim_ctx *ctx, int32_t wfs, int32_t n_dir, const double *dirs_rad, int32_t bin,
+                                     int32_t n_comp, const int32_t *comps, float *P, void *cuda_stream);
+
+/* P_opt = (P_DM^T P_DM + lambda I)^{-1} P_DM^T P_Layer for DM components
+ * dms[n_dm] and layer components layers[n_layer] (lambda >= 0, absolute):
+ * p_opt (device, FP32, column-major [n_layer_cols][n_dm_cols], i.e. column l
+ * holds the DM commands of layer mode l).  Builds both projection matrices
+ * in device scratch (rows x columns x 4 bytes each), forms the products with
+ * FP32-accurate tensor-core GEMMs, and factors and solves by Cholesky.
+ * Synchronises the stream before returning.  SYNIM_ERR_NOT_CONVERGED if the
+ * normal matrix is not positive definite. */
+synim_status synim_projection_opt(synim_ctx *ctx, int32_t wfs, int32_t n_dir, const double *dirs_rad, int32_t bin,
+                                  int32_t n_dm, const int32_t *dms, int32_t n_layer, const int32_t *layers,
+                                  double lambda, float *p_opt, void *cuda_stream);
+
 /*
  * Self-test of the bounded device waits (the mbarrier waits of the
  * tensor-core kernels use the same helper): one thread waits on an mbarrier

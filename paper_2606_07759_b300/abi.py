@@ -65,6 +65,12 @@ SIGNATURES = {
                                ctypes.POINTER(c_double), c_void_p]),
     "synim_im_check": (c_int32, [c_void_p, c_void_p]),
     "synim_wait_selftest": (c_int32, [c_void_p, ctypes.c_int64, c_void_p]),
+    "synim_projection_rows": (c_int32, [c_void_p, c_int32, c_int32, c_int32, ctypes.POINTER(ctypes.c_int64)]),
+    "synim_projection_matrix": (c_int32, [c_void_p, c_int32, c_int32, ctypes.POINTER(c_double), c_int32, c_int32,
+                                          ctypes.POINTER(c_int32), c_void_p, c_void_p]),
+    "synim_projection_opt": (c_int32, [c_void_p, c_int32, c_int32, ctypes.POINTER(c_double), c_int32, c_int32,
+                                       ctypes.POINTER(c_int32), c_int32, ctypes.POINTER(c_int32), c_double, c_void_p,
+                                       c_void_p]),
     "synim_dm_window": (c_int32, [c_void_p, c_int32, ctypes.POINTER(c_int32)]),
     "synim_im_kernel_ms": (c_int32, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int32)]),
     "synim_im_compute_noalloc": (c_int32, [ctypes.POINTER(synim_dm_desc), ctypes.POINTER(synim_wfs_desc),

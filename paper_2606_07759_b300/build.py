@@ -24,6 +24,7 @@ NVCC_FLAGS = [
     "-Xcompiler", "-fPIC", "-shared",
     "--cudart", "shared",
     "-Xlinker", "-rpath,/usr/local/cuda/lib64",
+    "-lcublas", "-lcusolver",
 ]
 
 

@@ -343,6 +343,7 @@ void synim_im_destroy(synim_ctx *ctx) {
     for (int s = 0; s < NSLOT; ++s)
         if (ctx->slot_ev[s]) cudaEventDestroy(ctx->slot_ev[s]);
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
+    projection_destroy(ctx);
     cnn_destroy(ctx->cnn);
     est_destroy(ctx->est);
     probe_destroy(ctx->probe);

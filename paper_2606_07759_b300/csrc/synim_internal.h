@@ -128,6 +128,7 @@ struct EstState;   // synim_estimate.cu
 void est_destroy(EstState *e);
 struct CnnState;   // synim_cnn.cu
 void cnn_destroy(CnnState *s);
+void projection_destroy(synim_ctx *c);   // library handles of the projection
 
 constexpr int NSLOT = 4;
 constexpr int NPROF = 256;
@@ -148,6 +149,7 @@ struct synim_ctx {
     synim::WfsHost wh[SYNIM_MAX_WFS];
     synim::Geo geo{};
     std::vector<void *> dev_allocs;
+    void *cublas = nullptr, *cusolver = nullptr;   // library handles of the projection (created on first use)
     int64_t mem_cap = 0;      // device bytes create may take (0 = no cap)
     size_t mem_used = 0;      // device bytes taken by create so far
     std::vector<void *> host_allocs;

@@ -188,6 +188,45 @@ class SynIM:
                   self._ctx)
         return np.array(gp[:]).reshape(np_, 4)
 
+    # ---- tomographic projection (Sec. 3) ----
+    def projection_rows(self, w: int, n_dir: int, bin: int) -> int:
+        r = ctypes.c_int64()
+        abi.check(self._L.synim_projection_rows(self._ctx, w, n_dir, bin, ctypes.byref(r)), self._ctx)
+        return int(r.value)
+
+    @staticmethod
+    def _dirs(dirs):
+        d = np.ascontiguousarray(np.asarray(dirs, np.float64).reshape(-1, 2))
+        return d, d.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), d.shape[0]
+
+    @staticmethod
+    def _ints(v):
+        a = np.ascontiguousarray(np.asarray(v, np.int32).ravel())
+        return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), a.size
+
+    def projection_matrix(self, w: int, dirs, bin: int, comps, stream=None):
+        """P_X of components comps as a tensor [n_cols, rows] (row c = actuator c's column)."""
+        d, dp, nd = self._dirs(dirs)
+        c, cp, nc = self._ints(comps)
+        rows = self.projection_rows(w, nd, bin)
+        ncols = sum(self.shapes[(int(q), 0)][1] for q in c)
+        out = torch.empty((ncols, rows), dtype=torch.float32, device=self.device)
+        abi.check(self._L.synim_projection_matrix(self._ctx, w, nd, dp, bin, nc, cp, ctypes.c_void_p(out.data_ptr()),
+                                                  self._stream(stream)), self._ctx)
+        return out
+
+    def projection_opt(self, w: int, dirs, bin: int, dms, layers, lam: float, stream=None):
+        """P_opt = (P_DM^T P_DM + lam I)^-1 P_DM^T P_Layer as a tensor [n_dm_cols, n_layer_cols]."""
+        d, dp, nd = self._dirs(dirs)
+        a, ap, na = self._ints(dms)
+        b, bp, nb = self._ints(layers)
+        nd_cols = sum(self.shapes[(int(q), 0)][1] for q in a)
+        nl_cols = sum(self.shapes[(int(q), 0)][1] for q in b)
+        out = torch.empty((nl_cols, nd_cols), dtype=torch.float32, device=self.device)
+        abi.check(self._L.synim_projection_opt(self._ctx, w, nd, dp, bin, na, ap, nb, bp, float(lam),
+                                               ctypes.c_void_p(out.data_ptr()), self._stream(stream)), self._ctx)
+        return out.t()
+
     # ---- probe responses (input of the misregistration estimators) ----
     def probe_attach(self, d: int, w: int, cmd):
         """Attach probe commands cmd [n_modes, n_act] (float64) to pair (d, w)."""
