@@ -211,8 +211,9 @@ synim_status synim_projection_matrix(synim_ctx *ctx, int32_t wfs, int32_t n_dir,
  * dms[n_dm] and layer components layers[n_layer] (lambda >= 0, absolute):
  * p_opt (device, FP32, column-major [n_layer_cols][n_dm_cols], i.e. column l
  * holds the DM commands of layer mode l).  Builds both projection matrices
- * in device scratch (rows x columns x 4 bytes each), forms the products with
- * FP32-accurate tensor-core GEMMs, and factors and solves by Cholesky.
+ * in device scratch (rows x columns x 4 bytes each), forms the products in
+ * FP32 (SSYRK / SGEMM), factors by Cholesky and solves with two triangular
+ * solves.
  * Synchronises the stream before returning.  SYNIM_ERR_NOT_CONVERGED if the
  * normal matrix is not positive definite. */
 synim_status synim_projection_opt(synim_ctx *ctx, int32_t wfs, int32_t n_dir, const double *dirs_rad, int32_t bin,

@@ -15,9 +15,12 @@
 //                      box from its packed window (zero border = zero outside),
 //                      zeros elsewhere;
 //   P_DM^T P_DM, P_DM^T P_Layer
-//                      FP32-accurate GEMMs on the tensor cores (cuBLAS with
-//                      BF16x9 emulation of FP32);
-//   + lambda I, Cholesky factor and solve (cuSOLVER, FP32).
+//                      FP32 products (cuBLAS SSYRK for the symmetric normal
+//                      matrix, SGEMM for the right-hand side); TF32 would
+//                      lose ~1e-3 relative per product, which the solve
+//                      multiplies by the condition number;
+//   + lambda I, Cholesky factor (cuSOLVER SPOTRF) and two triangular solves
+//                      (cuBLAS STRSM) for all layer columns.
 #include <algorithm>
 #include <cmath>
 #include <string>
@@ -265,7 +268,7 @@ synim_status synim_projection_opt(synim_ctx *ctx, int32_t wfs, int32_t n_dir, co
     if ((s = build_p(ctx, wfs, n_dir, dirs_rad, bin, n_layer, layers, Pl, K, d_pupil, d_dirs + (size_t)n_dm * n_dir,
                      st)) != SYNIM_OK)
         return s;
-    // normal matrix and right-hand side: FP32-accurate GEMMs on the tensor cores
+    // normal matrix (lower triangle) and right-hand side, FP32
     if (!ctx->cublas) {
         cublasHandle_t h = nullptr;
         if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) return pfail(ctx, SYNIM_ERR_CUDA, "cublasCreate failed");
@@ -280,19 +283,17 @@ synim_status synim_projection_opt(synim_ctx *ctx, int32_t wfs, int32_t n_dir, co
     cusolverDnHandle_t hs = static_cast<cusolverDnHandle_t>(ctx->cusolver);
     cublasSetStream(hb, st);
     cusolverDnSetStream(hs, st);
-    cublasSetEmulationStrategy(hb, CUBLAS_EMULATION_STRATEGY_EAGER);
+    cublasSetMathMode(hb, CUBLAS_PEDANTIC_MATH);   // no TF32 anywhere
     const float one = 1.f, zero = 0.f;
-    cublasStatus_t bs = cublasGemmEx(hb, CUBLAS_OP_T, CUBLAS_OP_N, (int)nd, (int)nd, (int)K, &one, Pd, CUDA_R_32F,
-                                     (int)K, Pd, CUDA_R_32F, (int)K, &zero, G, CUDA_R_32F, (int)nd,
-                                     CUBLAS_COMPUTE_32F_EMULATED_16BFX9, CUBLAS_GEMM_DEFAULT);
+    cublasStatus_t bs = cublasSsyrk(hb, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, (int)nd, (int)K, &one, Pd, (int)K, &zero,
+                                    G, (int)nd);
     if (bs == CUBLAS_STATUS_SUCCESS)
-        bs = cublasGemmEx(hb, CUBLAS_OP_T, CUBLAS_OP_N, (int)nd, (int)nl, (int)K, &one, Pd, CUDA_R_32F, (int)K, Pl,
-                          CUDA_R_32F, (int)K, &zero, p_opt, CUDA_R_32F, (int)nd, CUBLAS_COMPUTE_32F_EMULATED_16BFX9,
-                          CUBLAS_GEMM_DEFAULT);
+        bs = cublasSgemm(hb, CUBLAS_OP_T, CUBLAS_OP_N, (int)nd, (int)nl, (int)K, &one, Pd, (int)K, Pl, (int)K, &zero,
+                         p_opt, (int)nd);
     if (bs != CUBLAS_STATUS_SUCCESS)
-        return pfail(ctx, SYNIM_ERR_CUDA, "projection GEMM failed (cuBLAS status " + std::to_string((int)bs) + ")");
+        return pfail(ctx, SYNIM_ERR_CUDA, "projection products failed (cuBLAS status " + std::to_string((int)bs) + ")");
     k_add_diag<<<(unsigned)((nd + 255) / 256), 256, 0, st>>>(G, nd, (float)lambda);
-    // Cholesky factor of G + lambda I, then the solve for all layer columns
+    // G + lambda I = L L^T, then P_opt = L^-T (L^-1 R) for all layer columns
     int lwork = 0;
     if (cusolverDnSpotrf_bufferSize(hs, CUBLAS_FILL_MODE_LOWER, (int)nd, G, (int)nd, &lwork) != CUSOLVER_STATUS_SUCCESS)
         return pfail(ctx, SYNIM_ERR_CUDA, "cusolverDnSpotrf_bufferSize failed");
@@ -300,14 +301,18 @@ synim_status synim_projection_opt(synim_ctx *ctx, int32_t wfs, int32_t n_dir, co
         return pfail(ctx, SYNIM_ERR_OOM, "projection solver workspace");
     if (cusolverDnSpotrf(hs, CUBLAS_FILL_MODE_LOWER, (int)nd, G, (int)nd, work, lwork, info) != CUSOLVER_STATUS_SUCCESS)
         return pfail(ctx, SYNIM_ERR_CUDA, "cusolverDnSpotrf failed");
-    if (cusolverDnSpotrs(hs, CUBLAS_FILL_MODE_LOWER, (int)nd, (int)nl, G, (int)nd, p_opt, (int)nd, info + 1) !=
-        CUSOLVER_STATUS_SUCCESS)
-        return pfail(ctx, SYNIM_ERR_CUDA, "cusolverDnSpotrs failed");
+    bs = cublasStrsm(hb, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, (int)nd, (int)nl,
+                     &one, G, (int)nd, p_opt, (int)nd);
+    if (bs == CUBLAS_STATUS_SUCCESS)
+        bs = cublasStrsm(hb, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, CUBLAS_DIAG_NON_UNIT, (int)nd,
+                         (int)nl, &one, G, (int)nd, p_opt, (int)nd);
+    if (bs != CUBLAS_STATUS_SUCCESS)
+        return pfail(ctx, SYNIM_ERR_CUDA, "projection triangular solves failed (cuBLAS status " +
+                                              std::to_string((int)bs) + ")");
     int h_info[2] = {0, 0};
     if ((e = cudaMemcpyAsync(h_info, info, 2 * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
         (e = cudaStreamSynchronize(st)) != cudaSuccess)
         return pfail(ctx, SYNIM_ERR_CUDA, std::string("projection: ") + cudaGetErrorString(e));
-    if (h_info[1] != 0) return pfail(ctx, SYNIM_ERR_CUDA, "projection: cusolverDnSpotrs reported a bad argument");
     if (h_info[0] != 0)
         return pfail(ctx, SYNIM_ERR_NOT_CONVERGED,
                      "projection: P_DM^T P_DM + lambda I is not positive definite (raise lambda)");
