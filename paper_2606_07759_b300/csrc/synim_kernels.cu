@@ -272,7 +272,7 @@ cudaError_t launch_pst(const Geo &g, const DevPair *pairs, int max_mm, int max_l
 // ---------------------------------------------------------------------------
 // Per (actuator, sensor): the pixel box where the resampled, repaired IF can
 // be non-zero, the subaperture box whose slopes can be non-zero, and the
-// local coordinates of the box origin in the staged window.
+// local coordinates of the box origin in the packed window.
 struct ItemWfs {
     int pi0, pi1, pj0, pj1;  // pixel box (inclusive)
     int si0, si1, sj0, sj1;  // subaperture box (inclusive)
@@ -305,7 +305,7 @@ struct Eval {
         }
     }
 
-    // Bilinear resample of the staged window at sensor pixel (i, j) (Sec. 2.1);
+    // Bilinear resample of the packed window at sensor pixel (i, j) (Sec. 2.1);
     // v[0] = phi, v[1..4] = d phi / d p_k (chain rule through the floor cell).
     __device__ __forceinline__ void bil(int i, int j, float *v) const {
         const float di = (float)(i - pi0), dj = (float)(j - pj0);

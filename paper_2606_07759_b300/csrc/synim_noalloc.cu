@@ -477,7 +477,7 @@ extern "C" synim_status synim_im_compute_noalloc(const synim_dm_desc *dm, const 
     if ((e = cudaMemcpyAsync(&err_flag, hdr + H_ERR, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
         (e = cudaStreamSynchronize(st)) != cudaSuccess)
         return na_fail(SYNIM_ERR_CUDA, cudaGetErrorString(e));
-    if (err_flag & ERR_TIMEOUT) return na_fail(SYNIM_ERR_TIMEOUT, "window staging wait timed out");
+    if (err_flag & ERR_TIMEOUT) return na_fail(SYNIM_ERR_TIMEOUT, "a bounded device wait timed out");
     if (err_flag & ERR_ARENA) return na_fail(SYNIM_ERR_SHAPE, "slope values exceeded their shared-memory buffer");
     return SYNIM_OK;
 }
