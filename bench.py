@@ -619,7 +619,9 @@ def run_synim(args):
     k_avg_s = (k_ms / max(k_n, 1)) / 1000.0
     peak, peak_kind = peaks()
     achieved = alg_bytes / k_avg_s / 1e9
-    traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["kernel_sha1"] == kernel_sha1() else None
+    # the recorded traffic is of the full MCAO launch: only that workload may carry it
+    full_mcao = args.workload == "mcao" and args.scale == 1.0
+    traffic = TRAFFIC["bytes_per_launch"] if full_mcao and TRAFFIC["kernel_sha1"] == kernel_sha1() else None
 
     # end to end through the public API: host (pinned) IF cubes in, host (pinned) IMs out
     host_outs = [torch.empty(t.shape, dtype=torch.float32, pin_memory=True) for t in outs]
