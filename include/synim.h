@@ -210,9 +210,10 @@ synim_status synim_projection_matrix(synim_ctx *ctx, int32_t wfs, int32_t n_dir,
 /* P_opt = (P_DM^T P_DM + lambda I)^{-1} P_DM^T P_Layer for DM components
  * dms[n_dm] and layer components layers[n_layer] (lambda >= 0, absolute):
  * p_opt (device, FP32, column-major [n_layer_cols][n_dm_cols], i.e. column l
- * holds the DM commands of layer mode l).  Builds both projection matrices
- * in device scratch (rows x columns x 4 bytes each), forms the products in
- * FP32 (SSYRK / SGEMM), factors by Cholesky and solves with two triangular
+ * holds the DM commands of layer mode l).  Stores both projection matrices
+ * box by box in device scratch (each column is non-zero only on its footprint
+ * box per direction), forms P_DM^T P_DM and P_DM^T P_Layer from the box
+ * intersections (FP32), factors by Cholesky and solves with two triangular
  * solves.
  * Synchronises the stream before returning.  SYNIM_ERR_NOT_CONVERGED if the
  * normal matrix is not positive definite. */

@@ -10,18 +10,24 @@
 // repair (a phase projection, not a slope).  Rows are direction-major,
 // row = j (M / bin)^2 + q.
 //
-//   k_proj             one CTA per (actuator, direction) writes that column
-//                      segment: the binned pixels of the actuator's footprint
-//                      box from its packed window (zero border = zero outside),
-//                      zeros elsewhere;
-//   P_DM^T P_DM, P_DM^T P_Layer
-//                      FP32 products (cuBLAS SSYRK for the symmetric normal
-//                      matrix, SGEMM for the right-hand side); TF32 would
-//                      lose ~1e-3 relative per product, which the solve
-//                      multiplies by the condition number;
+//   k_proj             (synim_projection_matrix) one CTA per (actuator,
+//                      direction) writes that dense column segment: the binned
+//                      pixels of the actuator's footprint box from its packed
+//                      window (zero border = zero outside), zeros elsewhere;
+//   k_proj_boxes, k_proj_vals
+//                      (P_opt) the same values, stored box by box: a column
+//                      is non-zero only on its footprint box in each direction
+//                      (about 1 % of the rows at the bench size);
+//   k_box_dot          P_DM^T P_DM and P_DM^T P_Layer from the boxes: one CTA
+//                      per DM actuator; the candidates are the actuators whose
+//                      union box (over the directions) meets its own, found
+//                      through a bucket grid; each candidate's entry is the sum
+//                      over directions of the dot product over the two boxes'
+//                      intersection (FP32), everything else stays zero;
 //   + lambda I, Cholesky factor (cuSOLVER SPOTRF) and two triangular solves
-//                      (cuBLAS STRSM) for all layer columns.
+//                      (cuBLAS STRSM) for all layer columns, FP32.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -107,6 +113,145 @@ k_proj(const DevDM D, const ProjDir *__restrict__ dirs, const uint8_t *__restric
         }
         dst[q] = v;
     }
+}
+
+// Footprint box (binned pixels, inclusive; qi1 < qi0 when empty) of actuator
+// a seen from one direction, and the window-local coordinates (xr, yr) of fine
+// pixel (qi0 bin, qj0 bin), both from the FP64 affine.
+__device__ __forceinline__ int4 proj_box(const DevDM &D, const ProjDir &pd, int a, int M, int bin, float &xr,
+                                         float &yr) {
+    const int wx0 = D.org[2 * a], wy0 = D.org[2 * a + 1];
+    const double det = pd.A[0] * pd.A[3] - pd.A[1] * pd.A[2];
+    const double i00 = pd.A[3] / det, i01 = -pd.A[1] / det, i10 = -pd.A[2] / det, i11 = pd.A[0] / det;
+    double jmin = 1e300, jmax = -1e300, imin = 1e300, imax = -1e300;
+    for (int c = 0; c < 4; ++c) {
+        const double dx = ((c & 1) ? wx0 + D.W : wx0 - 1) - pd.b[0];
+        const double dy = ((c & 2) ? wy0 + D.W : wy0 - 1) - pd.b[1];
+        const double jj = i00 * dx + i01 * dy, ii = i10 * dx + i11 * dy;
+        jmin = fmin(jmin, jj); jmax = fmax(jmax, jj);
+        imin = fmin(imin, ii); imax = fmax(imax, ii);
+    }
+    const double lo = -2.0, hi = (double)M + 2.0;
+    jmin = fmax(jmin, lo); imin = fmax(imin, lo); jmax = fmin(jmax, hi); imax = fmin(imax, hi);
+    const int j0 = max(0, (int)floor(jmin) - 1), j1 = min(M - 1, (int)ceil(jmax) + 1);
+    const int i0 = max(0, (int)floor(imin) - 1), i1 = min(M - 1, (int)ceil(imax) + 1);
+    int4 box = make_int4(i0 / bin, i1 / bin, j0 / bin, j1 / bin);
+    if (j0 > j1 || i0 > i1) box = make_int4(0, -1, 0, -1);
+    const double jr = (double)(box.z * bin), ir = (double)(box.x * bin);
+    xr = (float)(pd.A[0] * jr + pd.A[1] * ir + pd.b[0] - (wx0 - 1));
+    yr = (float)(pd.A[2] * jr + pd.A[3] * ir + pd.b[1] - (wy0 - 1));
+    return box;
+}
+
+// Value of binned pixel (qi, qj) of a box whose first fine pixel has window
+// coordinates (xr, yr).
+__device__ __forceinline__ float proj_value(const DevDM &D, const float *__restrict__ win, const ProjDir &pd,
+                                            const uint8_t *__restrict__ pupil, int M, int bin, int4 box, float xr,
+                                            float yr, int qi, int qj) {
+    const float a00 = (float)pd.A[0], a01 = (float)pd.A[1], a10 = (float)pd.A[2], a11 = (float)pd.A[3];
+    const float Wf1 = (float)(D.W + 1);
+    float v = 0.f;
+    for (int u = 0; u < bin; ++u)
+        for (int w = 0; w < bin; ++w) {
+            const int i = qi * bin + u, jj = qj * bin + w;
+            if (!pupil[(size_t)i * M + jj]) continue;
+            const float di = (float)(i - box.x * bin), dj = (float)(jj - box.z * bin);
+            const float x = fmaf(a00, dj, fmaf(a01, di, xr));
+            const float y = fmaf(a10, dj, fmaf(a11, di, yr));
+            if (!(x > 0.f && x < Wf1 && y > 0.f && y < Wf1)) continue;
+            const float fx0 = floorf(x), fy0 = floorf(y);
+            const float fx = x - fx0, fy = y - fy0;
+            const float *t = win + (int)fy0 * D.Wp + (int)fx0;
+            const float top = fmaf(fx, t[1] - t[0], t[0]);
+            const float bot = fmaf(fx, t[D.Wp + 1] - t[D.Wp], t[D.Wp]);
+            v += fmaf(fy, bot - top, top);
+        }
+    return v * (1.f / (float)(bin * bin));
+}
+
+// Boxes of every (actuator, direction) of one component: boxes[(col0 + a) n_dir + j].
+__global__ void k_proj_boxes(const DevDM D, const ProjDir *__restrict__ dirs, int M, int bin, int n_act, int n_dir,
+                             long long col0, int4 *__restrict__ boxes) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)n_act * n_dir) return;
+    const int a = (int)(t / n_dir), j = (int)(t - (long long)a * n_dir);
+    float xr, yr;
+    boxes[(col0 + a) * n_dir + j] = proj_box(D, dirs[j], a, M, bin, xr, yr);
+}
+
+// Box values of actuator a (blockIdx.x), direction j (blockIdx.y), row-major
+// within the box, at vals[offs[(col0 + a) n_dir + j]].
+__global__ void __launch_bounds__(kProjThreads)
+k_proj_vals(const DevDM D, const ProjDir *__restrict__ dirs, const uint8_t *__restrict__ pupil, int M, int bin,
+            int n_dir, long long col0, const long long *__restrict__ offs, float *__restrict__ vals) {
+    const int a = blockIdx.x, j = blockIdx.y;
+    __shared__ int4 sbox;
+    __shared__ float sref[2];
+    if (threadIdx.x == 0) {
+        float xr, yr;
+        sbox = proj_box(D, dirs[j], a, M, bin, xr, yr);
+        sref[0] = xr;
+        sref[1] = yr;
+    }
+    __syncthreads();
+    const int4 box = sbox;
+    const int w = box.w - box.z + 1, area = (box.y - box.x + 1) * w;
+    if (box.y < box.x || area <= 0) return;
+    const ProjDir pd = dirs[j];
+    const float *win = D.win + (size_t)a * D.win_stride;
+    float *dst = vals + offs[(col0 + a) * n_dir + j];
+    for (int q = threadIdx.x; q < area; q += kProjThreads) {
+        const int qi = box.x + q / w, qj = box.z + q % w;
+        dst[q] = proj_value(D, win, pd, pupil, M, bin, box, sref[0], sref[1], qi, qj);
+    }
+}
+
+// Products of the box-stored columns: out[l ld + a] = sum_j <col a, col l>
+// over the intersection of their direction-j boxes, for every right column l
+// whose union box meets left column a's (the others stay zero).  Right
+// columns are bucketed by the top-left cell (cell x cell binned pixels) of
+// their union box; every candidate is visited once.
+struct BoxSet {
+    const int4 *box;        // [cols][n_dir]
+    const long long *off;   // [cols][n_dir] value offsets
+    const float *val;
+    const int4 *uni;        // [cols] union box over the directions (qi1 < qi0: empty)
+};
+
+__global__ void __launch_bounds__(kProjThreads)
+k_box_dot(const BoxSet L, const BoxSet R, int n_dir, const int *__restrict__ cell_start,
+          const int *__restrict__ cell_item, int cell, int n_cr, int n_cc, int max_h, int max_w, long long ld,
+          float *__restrict__ out) {
+    const int a = blockIdx.x;
+    const int4 ua = L.uni[a];
+    if (ua.y < ua.x) return;
+    const int r0 = max(0, (ua.x - max_h + 1) / cell), r1 = min(n_cr - 1, ua.y / cell);
+    const int c0 = max(0, (ua.z - max_w + 1) / cell), c1 = min(n_cc - 1, ua.w / cell);
+    for (int r = r0; r <= r1; ++r)
+        for (int c = c0; c <= c1; ++c) {
+            const int cid = r * n_cc + c;
+            for (int it = cell_start[cid] + threadIdx.x; it < cell_start[cid + 1]; it += kProjThreads) {
+                const int l = cell_item[it];
+                const int4 ul = R.uni[l];
+                if (ul.x > ua.y || ul.y < ua.x || ul.z > ua.w || ul.w < ua.z) continue;
+                float acc = 0.f;
+                bool any = false;
+                for (int j = 0; j < n_dir; ++j) {
+                    const int4 A = L.box[(size_t)a * n_dir + j], B = R.box[(size_t)l * n_dir + j];
+                    const int i0 = max(A.x, B.x), i1 = min(A.y, B.y), j0 = max(A.z, B.z), j1 = min(A.w, B.w);
+                    if (i0 > i1 || j0 > j1 || A.y < A.x || B.y < B.x) continue;
+                    any = true;
+                    const int wa = A.w - A.z + 1, wb = B.w - B.z + 1;
+                    const float *pa = L.val + L.off[(size_t)a * n_dir + j];
+                    const float *pb = R.val + R.off[(size_t)l * n_dir + j];
+                    for (int qi = i0; qi <= i1; ++qi) {
+                        const float *ra = pa + (size_t)(qi - A.x) * wa, *rb = pb + (size_t)(qi - B.x) * wb;
+                        for (int qj = j0; qj <= j1; ++qj) acc = fmaf(ra[qj - A.z], rb[qj - B.z], acc);
+                    }
+                }
+                if (any) out[(size_t)l * ld + a] = acc;
+            }
+        }
 }
 
 __global__ void k_add_diag(float *__restrict__ G, long long n, float lam) {
@@ -199,6 +344,132 @@ struct ProjScratch {
     }
 };
 
+// Directions of one component (composite affine of each) into d_dirs.
+cudaError_t upload_dirs(synim_ctx *ctx, int w, int d, int n_dir, const double *dirs, ProjDir *d_dirs,
+                        cudaStream_t st) {
+    std::vector<ProjDir> hd((size_t)n_dir);
+    WfsHost view = ctx->wh[w];
+    view.H = 0.0;
+    view.rot = 0.0;
+    view.mag[0] = view.mag[1] = 1.0;
+    view.shift[0] = view.shift[1] = 0.0;
+    for (int j = 0; j < n_dir; ++j) {
+        view.th[0] = dirs[2 * j];
+        view.th[1] = dirs[2 * j + 1];
+        const synim_misreg m{0.0, 0.0, 0.0, 1.0};
+        composite(ctx->dmh[d], view, m, hd[j].A, hd[j].b);
+    }
+    // pageable source: the copy is staged before the call returns
+    return cudaMemcpyAsync(d_dirs, hd.data(), sizeof(ProjDir) * n_dir, cudaMemcpyHostToDevice, st);
+}
+
+// Box-stored projection columns of the listed components (columns in order):
+// boxes, value offsets and values on the device, union boxes on both sides.
+struct BoxBuild {
+    BoxSet dev{};
+    std::vector<int4> uni;
+    long long cols = 0;
+};
+
+synim_status build_boxes(synim_ctx *ctx, int w, int n_dir, const double *dirs, int bin, int n_comp, const int *comps,
+                         const uint8_t *d_pupil, ProjScratch &sc, BoxBuild &out, cudaStream_t st) {
+    const int M = ctx->wh[w].M;
+    const long long ncols = n_cols(ctx, n_comp, comps);
+    out.cols = ncols;
+    int4 *d_box = nullptr, *d_uni = nullptr;
+    ProjDir *d_dirs = nullptr;
+    long long *d_off = nullptr;
+    float *d_val = nullptr;
+    cudaError_t e = sc.alloc(&d_box, (size_t)ncols * n_dir);
+    if (e == cudaSuccess) e = sc.alloc(&d_dirs, (size_t)n_comp * n_dir);
+    if (e != cudaSuccess) return pfail(ctx, SYNIM_ERR_OOM, "projection boxes");
+    long long col = 0;
+    for (int c = 0; c < n_comp; ++c) {
+        const int d = comps[c];
+        const int n_act = ctx->dmh[d].n_act;
+        if ((e = upload_dirs(ctx, w, d, n_dir, dirs, d_dirs + (size_t)c * n_dir, st)) != cudaSuccess) break;
+        const long long n = (long long)n_act * n_dir;
+        k_proj_boxes<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ctx->geo.dm[d], d_dirs + (size_t)c * n_dir, M, bin,
+                                                                  n_act, n_dir, col, d_box);
+        if ((e = cudaGetLastError()) != cudaSuccess) break;
+        col += n_act;
+    }
+    std::vector<int4> hbox((size_t)ncols * n_dir);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hbox.data(), d_box, sizeof(int4) * hbox.size(), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return pfail(ctx, SYNIM_ERR_CUDA, std::string("projection boxes: ") + cudaGetErrorString(e));
+    std::vector<long long> hoff(hbox.size());
+    out.uni.assign((size_t)ncols, make_int4(0, -1, 0, -1));
+    long long total = 0;
+    for (long long q = 0; q < ncols; ++q) {
+        int4 u = make_int4(INT_MAX, INT_MIN, INT_MAX, INT_MIN);
+        for (int j = 0; j < n_dir; ++j) {
+            const int4 b = hbox[(size_t)q * n_dir + j];
+            hoff[(size_t)q * n_dir + j] = total;
+            if (b.y < b.x || b.w < b.z) continue;
+            total += (long long)(b.y - b.x + 1) * (b.w - b.z + 1);
+            u = make_int4(std::min(u.x, b.x), std::max(u.y, b.y), std::min(u.z, b.z), std::max(u.w, b.w));
+        }
+        if (u.x <= u.y) out.uni[(size_t)q] = u;
+    }
+    e = sc.alloc(&d_off, hoff.size());
+    if (e == cudaSuccess) e = sc.alloc(&d_uni, (size_t)ncols);
+    if (e == cudaSuccess) e = sc.alloc(&d_val, (size_t)std::max<long long>(total, 1));
+    if (e != cudaSuccess) return pfail(ctx, SYNIM_ERR_OOM, "projection box values");
+    e = cudaMemcpyAsync(d_off, hoff.data(), sizeof(long long) * hoff.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_uni, out.uni.data(), sizeof(int4) * out.uni.size(), cudaMemcpyHostToDevice, st);
+    col = 0;
+    for (int c = 0; c < n_comp && e == cudaSuccess; ++c) {
+        const int d = comps[c];
+        dim3 grid((unsigned)ctx->dmh[d].n_act, (unsigned)n_dir);
+        k_proj_vals<<<grid, kProjThreads, 0, st>>>(ctx->geo.dm[d], d_dirs + (size_t)c * n_dir, d_pupil, M, bin, n_dir,
+                                                   col, d_off, d_val);
+        e = cudaGetLastError();
+        col += ctx->dmh[d].n_act;
+    }
+    // the host vectors above must outlive the copies that read them
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return pfail(ctx, SYNIM_ERR_CUDA, std::string("projection box values: ") + cudaGetErrorString(e));
+    out.dev = BoxSet{d_box, d_off, d_val, d_uni};
+    return SYNIM_OK;
+}
+
+// Bucket grid of a column set by the top-left cell of each union box.
+struct Buckets {
+    int cell = 16, n_cr = 0, n_cc = 0, max_h = 1, max_w = 1;
+    int *start = nullptr, *item = nullptr;
+};
+
+synim_status build_buckets(synim_ctx *ctx, const BoxBuild &bb, int Mb, ProjScratch &sc, Buckets &out,
+                           cudaStream_t st, std::vector<int> &hstart, std::vector<int> &hitem) {
+    out.n_cr = out.n_cc = (Mb + out.cell - 1) / out.cell;
+    const size_t n_cells = (size_t)out.n_cr * out.n_cc;
+    hstart.assign(n_cells + 1, 0);
+    for (const int4 &u : bb.uni) {
+        if (u.y < u.x) continue;
+        ++hstart[(size_t)(u.x / out.cell) * out.n_cc + u.z / out.cell + 1];
+        out.max_h = std::max(out.max_h, u.y - u.x + 1);
+        out.max_w = std::max(out.max_w, u.w - u.z + 1);
+    }
+    for (size_t q = 0; q < n_cells; ++q) hstart[q + 1] += hstart[q];
+    hitem.assign((size_t)std::max(hstart[n_cells], 1), 0);
+    std::vector<int> fill(hstart.begin(), hstart.end() - 1);
+    for (size_t l = 0; l < bb.uni.size(); ++l) {
+        const int4 u = bb.uni[l];
+        if (u.y < u.x) continue;
+        hitem[(size_t)fill[(size_t)(u.x / out.cell) * out.n_cc + u.z / out.cell]++] = (int)l;
+    }
+    cudaError_t e = sc.alloc(&out.start, hstart.size());
+    if (e == cudaSuccess) e = sc.alloc(&out.item, hitem.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out.start, hstart.data(), sizeof(int) * hstart.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out.item, hitem.data(), sizeof(int) * hitem.size(), cudaMemcpyHostToDevice, st);
+    return e == cudaSuccess ? SYNIM_OK : pfail(ctx, SYNIM_ERR_OOM, "projection buckets");
+}
+
 }  // namespace
 
 extern "C" {
@@ -251,24 +522,34 @@ synim_status synim_projection_opt(synim_ctx *ctx, int32_t wfs, int32_t n_dir, co
     const int M = ctx->wh[wfs].M;
     ProjScratch sc;
     uint8_t *d_pupil = nullptr;
-    ProjDir *d_dirs = nullptr;
-    float *Pd = nullptr, *Pl = nullptr, *G = nullptr, *work = nullptr;
+    float *G = nullptr, *work = nullptr;
     int *info = nullptr;
     cudaError_t e = sc.alloc(&d_pupil, (size_t)M * M);
-    if (e == cudaSuccess) e = sc.alloc(&d_dirs, (size_t)(n_dm + n_layer) * n_dir);
-    if (e == cudaSuccess) e = sc.alloc(&Pd, (size_t)nd * K);
-    if (e == cudaSuccess) e = sc.alloc(&Pl, (size_t)nl * K);
     if (e == cudaSuccess) e = sc.alloc(&G, (size_t)nd * nd);
     if (e == cudaSuccess) e = sc.alloc(&info, 2);
     if (e == cudaSuccess) e = cudaMemsetAsync(info, 0, 2 * sizeof(int), st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_pupil, ctx->pupil[wfs].data(), (size_t)M * M, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return pfail(ctx, SYNIM_ERR_OOM, std::string("projection scratch: ") + cudaGetErrorString(e));
-    if ((s = build_p(ctx, wfs, n_dir, dirs_rad, bin, n_dm, dms, Pd, K, d_pupil, d_dirs, st)) != SYNIM_OK) return s;
-    if ((s = build_p(ctx, wfs, n_dir, dirs_rad, bin, n_layer, layers, Pl, K, d_pupil, d_dirs + (size_t)n_dm * n_dir,
-                     st)) != SYNIM_OK)
-        return s;
-    // normal matrix (lower triangle) and right-hand side, FP32
+    // box-stored columns of both sets, bucket grids of the right-hand sets
+    BoxBuild bd, bl;
+    if ((s = build_boxes(ctx, wfs, n_dir, dirs_rad, bin, n_dm, dms, d_pupil, sc, bd, st)) != SYNIM_OK) return s;
+    if ((s = build_boxes(ctx, wfs, n_dir, dirs_rad, bin, n_layer, layers, d_pupil, sc, bl, st)) != SYNIM_OK) return s;
+    Buckets kd, kl;
+    std::vector<int> hs1, hi1, hs2, hi2;   // host copies outlive their uploads (synchronised below)
+    const int Mb = M / bin;
+    if ((s = build_buckets(ctx, bd, Mb, sc, kd, st, hs1, hi1)) != SYNIM_OK) return s;
+    if ((s = build_buckets(ctx, bl, Mb, sc, kl, st, hs2, hi2)) != SYNIM_OK) return s;
+    // R = P_DM^T P_Layer into p_opt, G = P_DM^T P_DM (both triangles)
+    e = cudaMemsetAsync(p_opt, 0, sizeof(float) * (size_t)nd * nl, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(G, 0, sizeof(float) * (size_t)nd * nd, st);
+    if (e != cudaSuccess) return pfail(ctx, SYNIM_ERR_CUDA, std::string("projection: ") + cudaGetErrorString(e));
+    k_box_dot<<<(unsigned)nd, kProjThreads, 0, st>>>(bd.dev, bl.dev, n_dir, kl.start, kl.item, kl.cell, kl.n_cr,
+                                                      kl.n_cc, kl.max_h, kl.max_w, nd, p_opt);
+    k_box_dot<<<(unsigned)nd, kProjThreads, 0, st>>>(bd.dev, bd.dev, n_dir, kd.start, kd.item, kd.cell, kd.n_cr,
+                                                      kd.n_cc, kd.max_h, kd.max_w, nd, G);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return pfail(ctx, SYNIM_ERR_CUDA, std::string("k_box_dot: ") + cudaGetErrorString(e));
     if (!ctx->cublas) {
         cublasHandle_t h = nullptr;
         if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) return pfail(ctx, SYNIM_ERR_CUDA, "cublasCreate failed");
@@ -284,14 +565,8 @@ synim_status synim_projection_opt(synim_ctx *ctx, int32_t wfs, int32_t n_dir, co
     cublasSetStream(hb, st);
     cusolverDnSetStream(hs, st);
     cublasSetMathMode(hb, CUBLAS_PEDANTIC_MATH);   // no TF32 anywhere
-    const float one = 1.f, zero = 0.f;
-    cublasStatus_t bs = cublasSsyrk(hb, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, (int)nd, (int)K, &one, Pd, (int)K, &zero,
-                                    G, (int)nd);
-    if (bs == CUBLAS_STATUS_SUCCESS)
-        bs = cublasSgemm(hb, CUBLAS_OP_T, CUBLAS_OP_N, (int)nd, (int)nl, (int)K, &one, Pd, (int)K, Pl, (int)K, &zero,
-                         p_opt, (int)nd);
-    if (bs != CUBLAS_STATUS_SUCCESS)
-        return pfail(ctx, SYNIM_ERR_CUDA, "projection products failed (cuBLAS status " + std::to_string((int)bs) + ")");
+    const float one = 1.f;
+    cublasStatus_t bs = CUBLAS_STATUS_SUCCESS;
     k_add_diag<<<(unsigned)((nd + 255) / 256), 256, 0, st>>>(G, nd, (float)lambda);
     // G + lambda I = L L^T, then P_opt = L^-T (L^-1 R) for all layer columns
     int lwork = 0;
