@@ -238,6 +238,16 @@ def cpu_oracle_sample(wl, seconds: float, seed: int = 0):
     return cols_done, t_used, threads
 
 
+def reference_config(wl):
+    """The workload keys of the main arm's config, for the oracle arm (no GPU launch shape)."""
+    import oracle  # test infrastructure: only the reference / CPU-baseline legs run it
+    nv = [oracle.valid_subaps(w.pupil_mask, w.n_sub, w.subap_valid)[2] for w in wl.wfss]
+    cols = int(sum(d.n_act for d in wl.dms) * len(wl.wfss))
+    return {"workload": wl.name, "n_dm": len(wl.dms), "n_wfs": len(wl.wfss), "n_pairs": len(wl.dms) * len(wl.wfss),
+            "columns_per_step": cols, "im_bytes_per_step": int(sum(d.n_act for d in wl.dms) * sum(8 * n for n in nv)),
+            "parallelism": "replicas x1 (the oracle on the host cores of rank 0)"}
+
+
 def run_reference(args):
     _, rank, _ = rank_env()
     if rank != 0:
@@ -259,7 +269,7 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": 1000 * secs / len(per_step), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": wl.name, "n_columns_per_job": int(sum(d.n_act for d in wl.dms) * len(wl.wfss))},
+            "config": reference_config(wl),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                              "sample": sample_desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
