@@ -16,9 +16,11 @@
 //                     BF16; tcgen05.mma with TMEM accumulators;
 //   k_conv_tc<DGRAD>  implicit GEMM of the transposed convolution: gradient
 //                     of the layer input, masked by its ReLU, BF16;
-//   k_wgrad           dW[co][k] = sum_m dz[m][co] im2col(in)[m][k] (mma.sync
-//                     m16n8k16), split over m into per-CTA partials summed in
-//                     a fixed order;
+//   k_wgrad_halo      weight and bias gradient of the first layer (32
+//                     channels) on the shifted windows, tcgen05;
+//   k_wgrad_tc        dW[co][k] = sum_m dz[m][co] im2col(in)[m][k] of the
+//                     64-channel layers, tcgen05; both write one partial per
+//                     CTA, summed in a fixed order;
 //   small kernels for the head (dense layer, loss), bias sums, Adam.
 // Parameters live as FP32 masters (flat vector, order W1 b1 W2 b2 W3 b3 Wfc
 // bfc; W[co][ky][kx][ci], Wfc[j][y][x][c]) with BF16 copies for the GEMMs.
@@ -34,14 +36,13 @@
 #include <cuda_bf16.h>
 
 #include "synim_internal.h"
-#include "synim_mma.cuh"
+#include "synim_cpasync.cuh"
 #include "synim_tc.cuh"
 
 namespace synim {
 
 constexpr int CH = 64;               // hidden channels
 constexpr int BM = 128;                // GEMM rows per tile
-constexpr int kWgThreads = 128;
 constexpr int kBatchCap = 256;       // samples per training / inference pass
 
 typedef __nv_bfloat16 bf16;
@@ -634,8 +635,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_halo(const ConvArgs a, i
 }
 
 // ---------------------------------------------------------------------------
-// Weight gradient: part[split][co][k] = sum over this split's rows m of
-// dz[m][co] im2col(in)[m][k], k in one tile of BKW columns.
+// Weight gradients: arguments shared by the 64-channel kernel below.
 // ---------------------------------------------------------------------------
 struct WgArgs {
     const bf16 *dz;      // [B][Ho][Ho][64]
@@ -643,122 +643,8 @@ struct WgArgs {
     const int *perm;
     long long b0;
     int B, Hi, Ho, stride;
-    long long rows_per_split;
-    float *part;         // [splits][64 x 9 CIN + 64]: weight, then (CTAs of k-tile 0) bias partials
+    float *part;         // [CTAs][64 x 9 CIN + 64]: weight, then bias partials
 };
-
-template <int CIN, int BKW>
-__global__ void __launch_bounds__(kWgThreads) k_wgrad(const WgArgs a) {
-    constexpr int K = 9 * CIN;
-    constexpr int LDZ = CH + 8, LDC = BKW + 8;
-    constexpr int NT = BKW / 8;
-    __shared__ __align__(16) bf16 Zs[2][32][LDZ];
-    __shared__ __align__(16) bf16 Cs[2][32][LDC];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int kbase = blockIdx.x * BKW;
-    const long long M = (long long)a.B * a.Ho * a.Ho;
-    const long long r0 = (long long)blockIdx.y * a.rows_per_split;
-    const long long r1 = (r0 + a.rows_per_split < M) ? r0 + a.rows_per_split : M;
-
-    auto load = [&](long long mb, int buf) {
-        // dz rows: 32 x 8 chunks
-        for (int q = tid; q < 32 * 8; q += kWgThreads) {
-            const int r = q >> 3, c = q & 7;
-            const long long m = mb + r;
-            const bool ok = m < r1;
-            cp_async16(&Zs[buf][r][c * 8], ok ? a.dz + m * CH + c * 8 : a.dz, ok);
-        }
-        // im2col rows: 32 x (BKW / 8) chunks
-        for (int q = tid; q < 32 * (BKW / 8); q += kWgThreads) {
-            const int r = q / (BKW / 8), c = q - r * (BKW / 8);
-            const long long m = mb + r;
-            bool ok = m < r1;
-            const bf16 *src = a.in;
-            if (ok) {
-                const int b = (int)(m / ((long long)a.Ho * a.Ho));
-                const int rr = (int)(m - (long long)b * a.Ho * a.Ho);
-                const int oy = rr / a.Ho, ox = rr - oy * a.Ho;
-                const int k = kbase + c * 8;
-                const int tap = k / CIN, ci = k - tap * CIN;
-                const int ky = tap / 3, kx = tap - ky * 3;
-                const int iy = oy * a.stride + ky - 1, ix = ox * a.stride + kx - 1;
-                ok = iy >= 0 && ix >= 0 && iy < a.Hi && ix < a.Hi;
-                if (ok) {
-                    const long long sb = a.perm ? (long long)a.perm[a.b0 + b] : a.b0 + b;
-                    src = a.in + (((size_t)sb * a.Hi + iy) * a.Hi + ix) * CIN + ci;
-                }
-            }
-            cp_async16(&Cs[buf][r][c * 8], src, ok);
-        }
-        cp_async_commit();
-    };
-
-    float acc[NT][4];
-#pragma unroll
-    for (int j = 0; j < NT; ++j)
-#pragma unroll
-        for (int t = 0; t < 4; ++t) acc[j][t] = 0.f;
-    // the CTAs of k-tile 0 also sum dz over their rows (bias gradient):
-    // thread tid sums channel tid % 64 over rows (tid / 64) * 16 .. + 15
-    const bool do_bias = blockIdx.x == 0;
-    float bsum = 0.f;
-
-    if (r0 < r1) {
-        load(r0, 0);
-        int buf = 0;
-        for (long long mb = r0; mb < r1; mb += 32, buf ^= 1) {
-            if (mb + 32 < r1) {
-                load(mb + 32, buf ^ 1);
-                cp_async_wait<1>();
-            } else {
-                cp_async_wait<0>();
-            }
-            __syncthreads();
-#pragma unroll
-            for (int ks = 0; ks < 32; ks += 16) {
-                uint32_t af[4];
-                {
-                    const int j = lane >> 3;
-                    const int r = ks + (lane & 7) + (j >> 1) * 8;
-                    const int c = warp * 16 + (j & 1) * 8;
-                    ldsm_x4_t(af, &Zs[buf][r][c]);
-                }
-#pragma unroll
-                for (int np = 0; np < NT / 2; ++np) {
-                    uint32_t bfr[4];
-                    const int r = ks + (lane & 7) + ((lane >> 3) & 1) * 8;
-                    const int c = (2 * np + (lane >> 4)) * 8;
-                    ldsm_x4_t(bfr, &Cs[buf][r][c]);
-                    mma_bf16(acc[2 * np], af, bfr[0], bfr[1]);
-                    mma_bf16(acc[2 * np + 1], af, bfr[2], bfr[3]);
-                }
-            }
-            if (do_bias) {
-                const int co = tid & (CH - 1), rh = (tid >> 6) * 16;
-#pragma unroll
-                for (int r = 0; r < 16; ++r) bsum += __bfloat162float(Zs[buf][rh + r][co]);
-            }
-            __syncthreads();
-        }
-    }
-    float *dst = a.part + (size_t)blockIdx.y * (CH * K + CH);
-    if (do_bias) {
-        __shared__ float bred[kWgThreads];
-        bred[tid] = bsum;
-        __syncthreads();
-        if (tid < CH) dst[CH * K + tid] = bred[tid] + bred[tid + CH];
-    }
-    const int g = lane >> 2, tg = lane & 3;
-#pragma unroll
-    for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int n = warp * 16 + g + h * 8;
-            const int k = kbase + nt * 8 + 2 * tg;
-            dst[(size_t)n * K + k] = acc[nt][2 * h];
-            dst[(size_t)n * K + k + 1] = acc[nt][2 * h + 1];
-        }
-}
 
 // ---------------------------------------------------------------------------
 // Weight and bias gradient of the stride-1 layer with CIN = 32 channels, on
@@ -925,6 +811,183 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_wgrad_halo(const HaloWgArgs a
     if (warp == 8) {
         tc_fence_after();
         tc_dealloc(tmem, kHwCols);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Weight and bias gradient of a 64-channel convolution (the stride-2 layers)
+// on tcgen05: D^T[k][co] = sum_m im2col(in)[m][k] dz[m][co], k = tap 64 + ci.
+// Each CTA takes chunks of 64 output pixels (m) and accumulates over all of
+// them in TMEM; its partial goes to part[cta] and k_sum_parts adds the CTAs
+// in order.
+//   stage (per chunk): 80 planes of 64 pixels x 16 bytes, one per 8-channel
+//     group k of the im2col: MN-major A operand, M = k, K = pixels.  Planes
+//     0-71 are gathered; plane 72 holds ones and planes 73-79 zeros, written
+//     once, so that M-tile 4 (planes 64-79) adds the bias gradient
+//     sum_m dz[m][co] as accumulator row 576.  dz is stored as 8-pixel x
+//     8-channel core matrices: MN-major B operand, N = co.
+//   MMA: per 16 pixels, 5 M-tiles of 128 x 64 x 16 into 5 TMEM accumulators
+//     (independent, interleaved).
+//   epilogue: warp 4 + e reads accumulator rows 32 e .. 32 e + 31 of each
+//     tile.
+// ---------------------------------------------------------------------------
+constexpr int kWt2Pix = 64;                      // pixels per chunk
+constexpr int kWt2Planes = 80;                   // 72 im2col groups + ones + 7 zero planes
+constexpr int kWt2PlaneBytes = kWt2Pix * 16;     // 1 KB
+constexpr int kWt2StageBytes = kWt2Planes * kWt2PlaneBytes + kWt2Pix * CH * 2;   // 80 KB + 8 KB
+constexpr int kWt2Stages = 2;
+constexpr int kWt2Cols = 512;                    // 5 x 64 accumulator columns, rounded up to a power of two
+constexpr size_t kWt2Smem = 128 + (size_t)kWt2Stages * kWt2StageBytes + 8 * (2 * kWt2Stages + 1) + 16;
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_wgrad_tc(const WgArgs a, int *__restrict__ err) {
+    constexpr int K = 9 * CH, S = kWt2Stages;
+    extern __shared__ __align__(128) unsigned char tc_raw[];
+    unsigned char *base = tc_raw + ((128u - (tc_smem(tc_raw) & 127u)) & 127u);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(base + (size_t)S * kWt2StageBytes);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * S + 1);
+    const uint32_t bar0 = tc_smem(bars);
+    // full[st] = bar0 + 8 st, empty[st] = bar0 + 8 (S + st), done = bar0 + 16 S
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long M = (long long)a.B * a.Ho * a.Ho;
+    const int n_chunks = (int)((M + kWt2Pix - 1) / kWt2Pix);
+
+    if (tid == 0) {
+        for (int i = 0; i < S; ++i) {
+            tc_mbar_init(bar0 + 8 * i, 128);
+            tc_mbar_init(bar0 + 8 * (S + i), 1);
+        }
+        tc_mbar_init(bar0 + 16 * S, 1);
+        tc_fence_mbar_init();
+    }
+    if (warp == 8) tc_alloc(tc_smem(tslot), kWt2Cols);
+    // constant planes 72-79 of both stages: ones, then zeros
+    for (int q = tid; q < S * 8 * kWt2PlaneBytes / 16; q += kTcThreads) {
+        const int st = q / (8 * kWt2PlaneBytes / 16), r = q - st * (8 * kWt2PlaneBytes / 16);
+        const uint32_t v = (r < kWt2PlaneBytes / 16) ? 0x3F803F80u : 0u;
+        reinterpret_cast<uint4 *>(base + (size_t)st * kWt2StageBytes + 72 * kWt2PlaneBytes)[r] = make_uint4(v, v, v, v);
+    }
+    tc_fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp < 4) {
+        // thread tid owns pixel p = tid % 64 of every chunk and the 8-channel
+        // groups kg = tid / 64 + 2 i (im2col) and cg = tid / 64 + 2 i (dz)
+        const int p = tid & 63, g0 = tid >> 6;
+        constexpr int LAG = S - 1;
+        int g = 0;
+        for (int chunk = blockIdx.x; chunk < n_chunks; chunk += gridDim.x, ++g) {
+            const int st = g % S;
+            if (!tc_mbar_wait(bar0 + 8 * (S + st), ((g / S) & 1) ^ 1)) {
+                atomicOr(err, 1);
+                break;
+            }
+            unsigned char *stage = base + (size_t)st * kWt2StageBytes;
+            const long long m = (long long)chunk * kWt2Pix + p;
+            const bool ok_m = m < M;
+            int b = 0, oy = 0, ox = 0;
+            if (ok_m) {
+                b = (int)(m / ((long long)a.Ho * a.Ho));
+                const int r = (int)(m - (long long)b * a.Ho * a.Ho);
+                oy = r / a.Ho;
+                ox = r - oy * a.Ho;
+            }
+            const long long sb = a.perm ? (long long)a.perm[a.b0 + b] : a.b0 + b;
+            const bf16 *img = a.in + (size_t)sb * a.Hi * a.Hi * CH;
+#pragma unroll 4
+            for (int i = 0; i < 36; ++i) {
+                const int kg = g0 + 2 * i, tap = kg >> 3, cgp = kg & 7;
+                const int ky = tap / 3, kx = tap - ky * 3;
+                const int iy = oy * a.stride + ky - 1, ix = ox * a.stride + kx - 1;
+                const bool ok = ok_m && iy >= 0 && ix >= 0 && iy < a.Hi && ix < a.Hi;
+                cp_async16_ca(stage + kg * kWt2PlaneBytes + p * 16,
+                              ok ? img + ((size_t)iy * a.Hi + ix) * CH + cgp * 8 : a.in, ok);
+            }
+            unsigned char *dzs = stage + kWt2Planes * kWt2PlaneBytes;
+            const bf16 *dzr = a.dz + (size_t)(ok_m ? m : 0) * CH;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int cg = g0 + 2 * i;
+                cp_async16_ca(dzs + ((p >> 3) * 8 + cg) * 128 + (p & 7) * 16, ok_m ? dzr + cg * 8 : a.dz, ok_m);
+            }
+            cp_async_commit();
+            if (g >= LAG) {
+                cp_async_wait<LAG>();
+                tc_fence_proxy_async();
+                tc_mbar_arrive(bar0 + 8 * ((g - LAG) % S));
+            }
+        }
+        cp_async_wait<0>();
+        tc_fence_proxy_async();
+        for (int q = (g > LAG ? g - LAG : 0); q < g; ++q) tc_mbar_arrive(bar0 + 8 * (q % S));
+    } else if (warp == 8) {
+        if (lane == 0) {
+            // both operands MN-major
+            const uint32_t idesc = tc_idesc_bf16(BM, CH) | (1u << 15) | (1u << 16);
+            const uint32_t base_a = tc_smem(base);
+            int g = 0;
+            bool run = true;
+            for (int chunk = blockIdx.x; chunk < n_chunks; chunk += gridDim.x, ++g) {
+                const int st = g % S;
+                if (!tc_mbar_wait(bar0 + 8 * st, (g / S) & 1)) {
+                    atomicOr(err, 1);
+                    run = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t sa = base_a + (uint32_t)(st * kWt2StageBytes);
+                const uint32_t sd = sa + (uint32_t)(kWt2Planes * kWt2PlaneBytes);
+#pragma unroll
+                for (int s4 = 0; s4 < kWt2Pix / 16; ++s4) {
+                    const uint64_t bdesc = tc_desc(sd + s4 * 2048, 1024, 128);
+#pragma unroll
+                    for (int t = 0; t < 5; ++t)
+                        tc_mma(tmem + (uint32_t)(t * CH), tc_desc(sa + t * 16 * kWt2PlaneBytes + s4 * 256, 128,
+                                                                  kWt2PlaneBytes),
+                               bdesc, idesc, (g | s4) != 0);
+                }
+                tc_commit(bar0 + 8 * (S + st));
+            }
+            if (run) tc_commit(bar0 + 16 * S);
+            else atomicOr(err, 1);
+        }
+        __syncwarp();
+    } else {
+        const int e = warp - 4;
+        float *dst = a.part + (size_t)blockIdx.x * (CH * K + CH);
+        const bool any = blockIdx.x < n_chunks;
+        if (!any || tc_mbar_wait(bar0 + 16 * S, 0)) {
+            tc_fence_after();
+#pragma unroll 1
+            for (int t = 0; t < 5; ++t) {
+                const int k = 128 * t + 32 * e + lane;   // accumulator row of this lane
+#pragma unroll 1
+                for (int h = 0; h < 2; ++h) {
+                    float v[32];
+                    tc_ld32(tmem + ((uint32_t)(32 * e) << 16) + (uint32_t)(t * CH + 32 * h), v);
+                    if (!any) {
+#pragma unroll
+                        for (int q = 0; q < 32; ++q) v[q] = 0.f;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) {
+                        const int co = 32 * h + q;
+                        if (k < K) dst[(size_t)co * K + k] = v[q];
+                        else if (k == K) dst[(size_t)CH * K + co] = v[q];
+                    }
+                }
+            }
+        } else {
+            atomicOr(err, 1);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 8) {
+        tc_fence_after();
+        tc_dealloc(tmem, kWt2Cols);
     }
 }
 
@@ -1247,11 +1310,6 @@ cudaError_t launch_conv_dgrad(const CnnState &S, int layer, int B, cudaStream_t 
     return launch_tc<true, 64>(a, S.d_err, st);
 }
 
-int n_splits(long long M) {
-    // enough CTAs for a few waves, at least 256 rows each
-    return (int)std::max<long long>(1, std::min<long long>(296, M / 256));
-}
-
 cudaError_t launch_wgrad(const CnnState &S, int layer, const bf16 *in, const int *perm, long long b0, int B,
                          cudaStream_t st) {
     WgArgs a{};
@@ -1295,24 +1353,23 @@ cudaError_t launch_wgrad(const CnnState &S, int layer, const bf16 *in, const int
                                                                 S.grad + off_w);
         return cudaGetLastError();
     }
-    const long long M = (long long)B * a.Ho * a.Ho;
-    const int splits = n_splits(M);
-    a.rows_per_split = (M + splits - 1) / splits;
-    a.rows_per_split = (a.rows_per_split + 31) / 32 * 32;
-    const int K = 9 * cin;
-    if (cin == 32) {
-        dim3 grid(K / 96, splits);
-        k_wgrad<32, 96><<<grid, kWgThreads, 0, st>>>(a);
-    } else {
-        dim3 grid(K / 64, splits);
-        k_wgrad<64, 64><<<grid, kWgThreads, 0, st>>>(a);
+    if (cin == CH) {
+        // 64-channel layers: tcgen05, one CTA per SM, one partial per CTA
+        static size_t set_to = 0;
+        const size_t smem = std::max(kWt2Smem, kExclusiveSmem);
+        cudaError_t e = smem_limit(k_wgrad_tc, smem, set_to);
+        if (e != cudaSuccess) return e;
+        const long long chunks = ((long long)B * a.Ho * a.Ho + kWt2Pix - 1) / kWt2Pix;
+        const int grid = (int)std::min<long long>(std::min<long long>(chunks, sm_count()), 296);
+        if (grid < 1) return cudaErrorInvalidConfiguration;
+        k_wgrad_tc<<<grid, kTcThreads, smem, st>>>(a, S.d_err);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        const int K = 9 * cin;
+        k_sum_parts<<<blocks_for(CH * K + CH, 32), 256, 0, st>>>(S.wpart, grid, CH * K + CH, (long long)CH * K + CH,
+                                                                S.grad + off_w);
+        return cudaGetLastError();
     }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    // weights and bias are adjacent in the parameter vector (off_b = off_w + 64 K)
-    k_sum_parts<<<blocks_for(CH * K + CH, 32), 256, 0, st>>>(S.wpart, splits, CH * K + CH, (long long)CH * K + CH,
-                                                            S.grad + off_w);
-    return cudaGetLastError();
+    return cudaErrorInvalidValue;   // layer 1 has 32 or 64 channels, layers 2-3 64
 }
 
 cudaError_t pack_weights(CnnState &S, cudaStream_t st) {
