@@ -111,7 +111,21 @@ typedef struct {
     int64_t device_mem_cap;  /* bytes of device memory create may take (the context's
                                 holdings plus the temporary cube staging); 0 = no cap.
                                 Exceeding it fails create with SYNIM_ERR_OOM */
+    int32_t slope_engine;    /* SYNIM_ENGINE_NUMERICAL (0, default): central-difference slopes
+                                with edge repair (Sec. 2.2-2.3).  SYNIM_ENGINE_TELESCOPING (1):
+                                the telescoping sum of Sec. 2.2, read as the gradient tilt over
+                                each valid subaperture's lit area,
+                                  s_x = slope_scale * sum_edges sign * phi(edge) / (dw * n_lit),
+                                over the half-pixel ends of every lit pixel run along x
+                                (sign -1 at the start, +1 at the end; y likewise along
+                                pixel columns), phi resampled at the edge point with no edge
+                                repair.  Sensor grids up to 16383 pixels.  With engine 1 only
+                                synim_im_compute is available (sensitivity and vjp return
+                                SYNIM_ERR_INVALID_ARG) */
 } synim_opts;
+
+#define SYNIM_ENGINE_NUMERICAL 0
+#define SYNIM_ENGINE_TELESCOPING 1
 
 /*
  * Create a context: uploads the IF cubes once, scans each IF's support

@@ -38,9 +38,14 @@ class synim_misreg(ctypes.Structure):
                 ("mag", c_double)]
 
 
+ENGINE_NUMERICAL = 0     # SYNIM_ENGINE_NUMERICAL
+ENGINE_TELESCOPING = 1   # SYNIM_ENGINE_TELESCOPING
+
+
 class synim_opts(ctypes.Structure):
     _fields_ = [("threads_per_cta", c_int32), ("ctas_per_sm", c_int32), ("use_graph", c_int32),
-                ("autotune", c_int32), ("profile", c_int32), ("device_mem_cap", ctypes.c_int64)]
+                ("autotune", c_int32), ("profile", c_int32), ("device_mem_cap", ctypes.c_int64),
+                ("slope_engine", c_int32)]
 
 
 class synim_train_opts(ctypes.Structure):

@@ -265,6 +265,56 @@ bool build_wfs_tables(const synim_wfs_desc &d, WfsTables &t, std::string &why) {
     return true;
 }
 
+// Edge tables of the telescoping-sum engine (Sec. 2.2): per valid row, the
+// half-pixel ends of the lit pixel runs inside the subaperture along x
+// (pixel rows) and along y (pixel columns), packed as DevTele describes,
+// and the scale slope_scale / (dw lit).
+struct TeleTables {
+    std::vector<int> xs, xe, ys, ye, vfirst;
+    std::vector<float> fac;
+};
+
+void build_tele_tables(const synim_wfs_desc &d, const WfsTables &t, TeleTables &e) {
+    const int M = d.grid_m, n = d.n_sub, k = M / n;
+    const double dw = d.pupil_diam_m / M;
+    auto Pv = [&](int i, int j) -> int {
+        return (i >= 0 && j >= 0 && i < M && j < M) ? t.P[(size_t)i * M + j] : 0;
+    };
+    auto pack = [](int end, int i2, int j2) { return (int)(((unsigned)end << 31) | ((unsigned)i2 << 16) | (unsigned)j2); };
+    e.xs.assign(1, 0);
+    e.ys.assign(1, 0);
+    e.xe.clear();
+    e.ye.clear();
+    e.fac.clear();
+    for (int r = 0; r < t.nv; ++r) {
+        const int si = t.vsub[r] >> 16, sj = t.vsub[r] & 0xffff;
+        const int i0 = si * k, j0 = sj * k;
+        int lit = 0;
+        for (int i = i0; i < i0 + k; ++i)
+            for (int j = j0; j < j0 + k; ++j) {
+                if (!Pv(i, j)) continue;
+                ++lit;
+                const int i2 = 2 * i + 1, j2 = 2 * j + 1;   // doubled, offset by one
+                if (j == j0 || !Pv(i, j - 1)) e.xe.push_back(pack(0, i2, j2 - 1));
+                if (j == j0 + k - 1 || !Pv(i, j + 1)) e.xe.push_back(pack(1, i2, j2 + 1));
+                if (i == i0 || !Pv(i - 1, j)) e.ye.push_back(pack(0, i2 - 1, j2));
+                if (i == i0 + k - 1 || !Pv(i + 1, j)) e.ye.push_back(pack(1, i2 + 1, j2));
+            }
+        e.xs.push_back((int)e.xe.size());
+        e.ys.push_back((int)e.ye.size());
+        e.fac.push_back((float)(d.slope_scale / (dw * lit)));
+    }
+    e.vfirst.assign((size_t)n * (n + 1), 0);
+    for (int si = 0; si < n; ++si) {
+        int r = t.vrow[si + 1];
+        e.vfirst[(size_t)si * (n + 1) + n] = r;
+        for (int sj = n - 1; sj >= 0; --sj) {
+            if (t.vidx[si * n + sj] >= 0) r = t.vidx[si * n + sj];
+            e.vfirst[(size_t)si * (n + 1) + sj] = r;
+        }
+    }
+}
+
 }  // namespace
 
 namespace synim {
@@ -386,7 +436,17 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
         c->autotune = opts->autotune != 0;
         c->profile = opts->profile != 0;
         c->mem_cap = std::max<int64_t>(0, opts->device_mem_cap);
+        c->slope_engine = opts->slope_engine;
     }
+    if (c->slope_engine != SYNIM_ENGINE_NUMERICAL && c->slope_engine != SYNIM_ENGINE_TELESCOPING) {
+        delete c;
+        return fail(nullptr, SYNIM_ERR_INVALID_ARG, "slope_engine must be 0 (numerical) or 1 (telescoping)");
+    }
+    for (int w = 0; w < n_wfs && c->slope_engine == SYNIM_ENGINE_TELESCOPING; ++w)
+        if (wfs[w].grid_m > 16383) {
+            delete c;
+            return fail(nullptr, SYNIM_ERR_SHAPE, "the telescoping engine takes sensor grids up to 16383 pixels");
+        }
     if (c->threads % 32 != 0 || c->threads < 64 || c->threads > 256) {
         delete c;
         return fail(nullptr, SYNIM_ERR_INVALID_ARG, "threads_per_cta must be a multiple of 32 in 64..256");
@@ -519,6 +579,26 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
         G.xcode = xc; G.ycode = yc; G.irr_pix = ip; G.irr_w = iw; G.irr_sub = is;
         G.fac = fa; G.vsub = vs; G.vrow = vr;
         G.n_sub = H.n_sub; G.M = H.M; G.k = H.k; G.nv = H.nv; G.CH = H.CH;
+        if (c->slope_engine == SYNIM_ENGINE_TELESCOPING) {
+            TeleTables TT;
+            build_tele_tables(Wd, T, TT);
+            DevTele &DT = c->tele.w[w];
+            int *xs = nullptr, *xe = nullptr, *ys = nullptr, *ye = nullptr;
+            float *tf = nullptr;
+            int *vf = nullptr;
+            e = dev_upload(c, &xs, TT.xs);
+            if (e == cudaSuccess) e = dev_upload(c, &vf, TT.vfirst);
+            if (e == cudaSuccess) e = dev_upload(c, &xe, TT.xe);
+            if (e == cudaSuccess) e = dev_upload(c, &ys, TT.ys);
+            if (e == cudaSuccess) e = dev_upload(c, &ye, TT.ye);
+            if (e == cudaSuccess) e = dev_upload(c, &tf, TT.fac);
+            if (e != cudaSuccess) return bail(cuda_fail(c, e, "telescoping edge tables"));
+            DT.xs = xs; DT.xe = xe; DT.ys = ys; DT.ye = ye; DT.fac = tf; DT.vfirst = vf;
+            // a full subaperture has 2 k events per axis: at most eight per lane
+            int L = 1;
+            while (L < 32 && 4 * L < H.k) L *= 2;
+            DT.lanes = L;
+        }
         c->max_mm = std::max(c->max_mm, H.M * H.M);
         c->max_lines = std::max(c->max_lines, H.M * (H.n_sub + 1));
     }
@@ -666,6 +746,9 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
     DeviceGuard guard(c->device);
     const int np = c->n_dm * c->n_wfs;
     const int NV = (mode == MODE_FWD) ? 1 : 5;
+    const bool tele = c->slope_engine == SYNIM_ENGINE_TELESCOPING;
+    if (tele && mode != MODE_FWD)
+        return fail(c, SYNIM_ERR_INVALID_ARG, "the telescoping-sum engine computes IMs only (no tangents or vjp)");
     cudaError_t e;
     // parameter slot (pinned); wait for its previous copy to finish
     const int slot = c->slot;
@@ -713,10 +796,11 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
     cap = std::max<long long>(cap, c->seg_floats);  // never shrink: keeps the captured graph
     int dev_max = 0;
     cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
-    if ((long long)8 * 4 * cap > dev_max)
+    if (!tele && (long long)8 * 4 * cap > dev_max)
         return fail(c, SYNIM_ERR_SHAPE,
                     "boundary segments need " + std::to_string(8 * 4 * cap) +
                         " bytes of shared memory per CTA; lower the grid or raise support_eps");
+    if (tele) cap = 4;   // the telescoping kernel keeps no per-warp buffer
     c->seg_floats = (int)cap;
     g.seg_floats = c->seg_floats;
     // launch shape: the tuned one once the autotuner has run for this mode
@@ -732,8 +816,9 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
         const long long warps = th / 32;
         return (int)std::max<long long>(1, std::min<long long>((units + warps - 1) / warps, 1LL << 30));
     };
-    int bps = 0;
-    if ((e = im_prepare(mode, threads, smem, &bps)) != cudaSuccess) return cuda_fail(c, e, "kernel attributes");
+    int bps = 1;
+    if (!tele && (e = im_prepare(mode, threads, smem, &bps)) != cudaSuccess)
+        return cuda_fail(c, e, "kernel attributes");
     if (bps < 1) return fail(c, SYNIM_ERR_SHAPE, "IM kernel does not fit on an SM");
     int grid = grid_for(threads);
     if ((e = cudaMemcpyAsync(c->d_pairs, hp, sizeof(DevPair) * np, cudaMemcpyHostToDevice, s)) != cudaSuccess)
@@ -741,7 +826,7 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
     cudaEventRecord(c->slot_ev[slot], s);
     c->slot_used[slot] = true;
     c->slot = (slot + 1) % NSLOT;
-    if (c->autotune && !c->tuned[mode]) {
+    if (c->autotune && !c->tuned[mode] && !tele) {
         // autotuner: time each candidate launch shape on this call's inputs
         // (three launches after a warm-up) and keep the fastest for the mode
         static const int cand_threads[] = {128, 256};
@@ -809,6 +894,13 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
     // (inside a capture, only an "external" record becomes an event-record node)
     auto enqueue = [&](cudaStream_t q, cudaEvent_t a0, cudaEvent_t b0, bool capturing) -> cudaError_t {
         const unsigned int rf = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+        if (tele) {
+            // telescoping sum: one kernel, no pixel classes
+            cudaError_t r = a0 ? cudaEventRecordWithFlags(a0, q, rf) : cudaSuccess;
+            if (r == cudaSuccess) r = launch_tele(g, c->tele, c->d_pairs, grid, threads, q);
+            if (r == cudaSuccess && b0) r = cudaEventRecordWithFlags(b0, q, rf);
+            return r;
+        }
         cudaError_t r = cudaMemsetAsync(c->d_counter, 0, sizeof(int), q);
         if (r == cudaSuccess) r = launch_pst(g, c->d_pairs, c->max_mm, c->max_lines, q);
         if (r == cudaSuccess && a0) r = cudaEventRecordWithFlags(a0, q, rf);

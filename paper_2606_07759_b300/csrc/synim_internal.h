@@ -61,6 +61,24 @@ struct DevWFS {
     int n_sub, M, k, nv, CH;
 };
 
+// Edge tables of the telescoping-sum engine (Sec. 2.2), per sensor.  Each
+// event is one half-pixel end of a lit pixel run inside a valid subaperture,
+// packed as (end << 31) | ((2 i + 1 + e_i) << 16) | (2 j + 1 + e_j) with
+// (e_i, e_j) the half-pixel offset doubled (-1, 0 or 1) and end = 1 for the
+// run's last pixel (+phi), 0 for its first (-phi); grouped by valid row.
+struct DevTele {
+    const int *xs, *xe;  // x events of valid row r: xe[xs[r] .. xs[r + 1])
+    const int *ys, *ye;  // y events likewise
+    const float *fac;    // [nv] slope_scale / (dw lit)
+    const int *vfirst;   // [n_sub][n_sub + 1] valid row of the first valid subaperture at
+                         // or right of column sj in row si (vrow[si + 1] if none)
+    int lanes;           // lanes that share one subaperture's events (1 .. 32, a power of 2)
+};
+
+struct TeleSet {
+    DevTele w[SYNIM_MAX_WFS];
+};
+
 // Per (DM, sensor) pair, rewritten by the host every call.
 struct DevPair {
     double A[4], b[2];   // DM pixel = A (j, i) + b
@@ -115,6 +133,9 @@ size_t im_smem_bytes(const Geo &g);
 cudaError_t im_prepare(int mode, int threads, size_t smem, int *blocks_per_sm);
 cudaError_t launch_im(int mode, const Geo &g, const DevPair *pairs, int *counter, int *err,
                       double *gp, int grid, int threads, size_t smem, cudaStream_t s);
+// The telescoping-sum IM kernel: one warp per (actuator, sensor) column.
+cudaError_t launch_tele(const Geo &g, const TeleSet &t, const DevPair *pairs, int grid, int threads,
+                        cudaStream_t s);
 
 struct ProbeSet;   // synim_probe.cu
 void probe_destroy(ProbeSet *p);
@@ -151,6 +172,8 @@ struct synim_ctx {
     std::vector<void *> dev_allocs;
     void *cublas = nullptr, *cusolver = nullptr;   // library handles of the projection (created on first use)
     int64_t mem_cap = 0;      // device bytes create may take (0 = no cap)
+    int slope_engine = 0;     // SYNIM_ENGINE_NUMERICAL or SYNIM_ENGINE_TELESCOPING
+    synim::TeleSet tele{};
     size_t mem_used = 0;      // device bytes taken by create so far
     std::vector<void *> host_allocs;
     synim::DevPair *d_pairs = nullptr;

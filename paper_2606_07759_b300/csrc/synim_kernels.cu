@@ -17,6 +17,11 @@
 //                     the subaperture means of the central differences (Sec.
 //                     2.2), and writes the column once (16-byte stores for the
 //                     zero runs).  No warp ever waits for another.
+// k_tele              (every call, telescoping-sum engine of Sec. 2.2) the same
+//                     one-warp-per-column launch; a slope is the signed sum of
+//                     the IF resampled at the half-pixel ends of the lit runs
+//                     of its subaperture (create-time event tables), without
+//                     pixel classes or edge repair.
 //
 // The subaperture sum of central differences is evaluated in telescoped
 // form: sum_{p in s} P(p) (phi(p+x) - phi(p-x)) = sum_q phi(q) w_s(q) where
@@ -854,6 +859,115 @@ k_im(const __grid_constant__ Geo g, const DevPair *__restrict__ pairs, int *__re
     }
     // the zero buffer must outlive the bulk copies that read it
     if (MODE != MODE_VJP && lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
+// The telescoping-sum engine (Sec. 2.2)
+// ---------------------------------------------------------------------------
+// Sum over one subaperture's events of sign * phi(edge point), this lane's
+// share (events e0 + q, e0 + q + L, ...).  The edge point's offset from the
+// box origin (pi0, pj0) is exact in FP32 (half-integers below 2^14).
+__device__ __forceinline__ float tele_events(const int *__restrict__ ev, int e0, int e1, const Eval<1> &E,
+                                             int bi, int bj, int q, int L) {
+    float acc = 0.f;
+    for (int e = e0 + q; e < e1; e += L) {
+        const int c = __ldg(ev + e);
+        const float di = 0.5f * (float)(((c >> 16) & 0x7fff) - bi);
+        const float dj = 0.5f * (float)((c & 0xffff) - bj);
+        const float x = fmaf(E.a00, dj, fmaf(E.a01, di, E.xo));
+        const float y = fmaf(E.a10, dj, fmaf(E.a11, di, E.yo));
+        const float v = E.bil_at(x, y);
+        acc += (c < 0) ? v : -v;
+    }
+    return acc;
+}
+
+// One telescoping-sum IM column by one warp: zeros outside the valid rows
+// of the subaperture box and in each box row's gaps (valid subapertures left
+// or right of the box), and for every box subaperture the two edge sums
+// (groups of L lanes share a subaperture, taken in box order across the
+// rows; fixed butterfly order) times slope_scale / (dw lit).  Every phase
+// value is one bilinear sample of the packed window; there is no
+// pixel-class map and no edge repair.
+__device__ __forceinline__ void tele_column(const Geo &g, const DevTele &T, const DevPair *__restrict__ pairs,
+                                            int d, int a, int w, int lane) {
+    const DevPair &P = pairs[d * g.n_wfs + w];
+    if (!P.im) return;
+    const DevWFS &WF = g.wfs[w];
+    const DevDM &D = g.dm[d];
+    ItemWfs s;
+    make_info<MODE_FWD, 1>(g, pairs, d, a, w, s, nullptr);
+    const int nv = WF.nv, n2 = 2 * nv;
+    float *col = P.im + (size_t)a * n2;
+    const int vr0 = s.empty ? 0 : WF.vrow[s.si0], vr1 = s.empty ? 0 : WF.vrow[s.si1 + 1];
+    if (P.vec4) {
+        bulk_zero(col, 0, vr0, lane);
+        bulk_zero(col, vr1, nv + vr0, lane);
+        bulk_zero(col, nv + vr1, n2, lane);
+    } else {
+        zero_rows(col, 0, vr0, false, lane);
+        zero_rows(col, vr1, nv + vr0, false, lane);
+        zero_rows(col, nv + vr1, n2, false, lane);
+    }
+    if (s.empty) return;
+    const int n1 = WF.n_sub + 1;
+    for (int si = s.si0; si <= s.si1; ++si) {
+        const int ra = WF.vrow[si], rb = WF.vrow[si + 1];
+        const int za = T.vfirst[si * n1 + s.sj0], zb = T.vfirst[si * n1 + s.sj1 + 1];
+        zero_rows(col, ra, za, false, lane);
+        zero_rows(col, zb, rb, false, lane);
+        zero_rows(col, nv + ra, nv + za, false, lane);
+        zero_rows(col, nv + zb, nv + rb, false, lane);
+    }
+    Eval<1> E;
+    E.load(s, D.win + (size_t)a * D.win_stride, D.Wp, D.W, WF.M);
+    const int L = T.lanes, per = 32 / L, grp = lane / L, q = lane - grp * L;
+    const int bi = 2 * s.pi0 + 1, bj = 2 * s.pj0 + 1;
+    const int nsj = s.nsj, nb = (s.si1 - s.si0 + 1) * nsj;
+    for (int base = 0; base < nb; base += per) {
+        const int t = base + grp;
+        int r = -1;
+        if (t < nb) {
+            const int ti = t / nsj;
+            r = WF.vidx[(s.si0 + ti) * WF.n_sub + s.sj0 + (t - ti * nsj)];
+        }
+        float sx = 0.f, sy = 0.f;
+        if (r >= 0) {
+            sx = tele_events(T.xe, T.xs[r], T.xs[r + 1], E, bi, bj, q, L);
+            sy = tele_events(T.ye, T.ys[r], T.ys[r + 1], E, bi, bj, q, L);
+        }
+        for (int o = L >> 1; o > 0; o >>= 1) {
+            sx += __shfl_xor_sync(0xffffffffu, sx, o);
+            sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        }
+        if (r >= 0 && q == 0) {
+            const float f = T.fac[r];
+            col[r] = sx * f;
+            col[nv + r] = sy * f;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_tele(const __grid_constant__ Geo g, const __grid_constant__ TeleSet t, const DevPair *__restrict__ pairs) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int q = threadIdx.x; q < kZeroFloats / 4; q += blockDim.x) s_zero[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic zeros -> bulk-copy reads
+    __syncthreads();
+    const long n_units = (long)g.n_items * g.n_wfs;
+    for (long u = (long)blockIdx.x * nw + warp; u < n_units; u += (long)gridDim.x * nw) {
+        const int item = (int)(u / g.n_wfs), w = (int)(u - (long)item * g.n_wfs);
+        int d, a;
+        decode_item(g, item, d, a);
+        tele_column(g, t.w[w], pairs, d, a, w, lane);
+    }
+    if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+cudaError_t launch_tele(const Geo &g, const TeleSet &t, const DevPair *pairs, int grid, int threads,
+                        cudaStream_t s) {
+    k_tele<<<grid, threads, 0, s>>>(g, t, pairs);
+    return cudaGetLastError();
 }
 
 size_t im_smem_bytes(const Geo &g) { return (size_t)8 * g.seg_floats * 4; }

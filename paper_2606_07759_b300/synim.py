@@ -33,12 +33,14 @@ class SynIM:
     tensor), mask (uint8 [N, N] or None), pixel_pitch_m, altitude_m and
     optionally support_eps.  ``wfss`` items need: n_sub, grid_m,
     pupil_diam_m, src_height_m, field_rad, rot_deg, mag, shift_m,
-    pupil_mask, subap_valid, obstruction, slope_scale.
+    pupil_mask, subap_valid, obstruction, slope_scale.  ``slope_engine`` is
+    "numerical" (central differences with edge repair) or "telescoping" (the
+    edge-sum engine of Sec. 2.2; ``compute`` only).
     """
 
     def __init__(self, dms: Sequence, wfss: Sequence, threads_per_cta: int = 0, ctas_per_sm: int = 0,
                  use_graph: bool = True, profile: bool = False, device: Optional[torch.device] = None,
-                 autotune: bool = False, device_mem_cap: int = 0):
+                 autotune: bool = False, device_mem_cap: int = 0, slope_engine: str = "numerical"):
         self._L = abi.load()
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.n_dm, self.n_wfs = len(dms), len(wfss)
@@ -81,8 +83,11 @@ class SynIM:
             d.obstruction = float(getattr(w, "obstruction", 0.0))
             d.slope_scale = float(getattr(w, "slope_scale", 1.0))
             ww[q] = d
+        engines = {"numerical": abi.ENGINE_NUMERICAL, "telescoping": abi.ENGINE_TELESCOPING}
+        if slope_engine not in engines:
+            raise ValueError(f"slope_engine must be one of {sorted(engines)}")
         opts = abi.synim_opts(int(threads_per_cta), int(ctas_per_sm), 1 if use_graph else 0, 1 if autotune else 0,
-                              1 if profile else 0, int(device_mem_cap))
+                              1 if profile else 0, int(device_mem_cap), engines[slope_engine])
         ctx = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             abi.check(self._L.synim_im_create(dd, self.n_dm, ww, self.n_wfs, ctypes.byref(opts),
