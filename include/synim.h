@@ -11,7 +11,9 @@
  *     once (bilinear) onto the sensor grid;
  *   - Sec. 2.2: the sensor grid is M = k * n_sub pixels so that every
  *     subaperture is an exact k x k block; slopes are central differences
- *     averaged over the lit pixels of each subaperture;
+ *     averaged over the lit pixels of each subaperture, or, with the
+ *     telescoping-sum engine (synim_opts.slope_engine), phase sums at the
+ *     ends of the lit pixel runs;
  *   - Sec. 2.3: edge repair (strict core of the interpolated DM mask at
  *     0.999999, ring = cross dilation minus core, ring value = mean over the
  *     valid cardinal directions of 2 P1 - P2 or P1);
@@ -105,7 +107,9 @@ typedef struct {
     int32_t use_graph;       /* 1 = replay a CUDA graph per stream; 0 = plain launches */
     int32_t autotune;        /* 1 = at the first call of each mode, time the candidate launch
                                 shapes (128 or 256 threads x 2, 4 or 8 lanes per boundary
-                                segment) on that call's inputs and keep the fastest */
+                                segment; telescoping engine: x 1/2, 1, 2 or 4 times the
+                                default lanes per subaperture) on that call's inputs and
+                                keep the fastest */
     int32_t profile;         /* 1 = record CUDA events around every IM-kernel launch
                                 (read back with synim_im_kernel_ms) */
     int64_t device_mem_cap;  /* bytes of device memory create may take (the context's
@@ -400,9 +404,10 @@ synim_status synim_cnn_train(synim_ctx *ctx, const double *params, int64_t n, co
                              double *loss_out, void *cuda_stream);
 
 /* Launch shape chosen by the autotuner for mode 0 (IM), 1 (tangents) or 2
- * (adjoint): threads per CTA, lanes per boundary segment, and the mean
- * kernel time of the winner (ms).  SYNIM_ERR_NOT_CONVERGED (outputs hold the
- * defaults) while that mode has not been tuned. */
+ * (adjoint): threads per CTA, lanes per boundary segment (telescoping
+ * engine: lanes per subaperture on sensor 0), and the mean kernel time of
+ * the winner (ms).  SYNIM_ERR_NOT_CONVERGED (outputs hold the defaults)
+ * while that mode has not been tuned. */
 synim_status synim_im_tuning(const synim_ctx *ctx, int32_t mode, int32_t *threads, int32_t *seg_lanes,
                              double *ms);
 

@@ -270,7 +270,7 @@ bool build_wfs_tables(const synim_wfs_desc &d, WfsTables &t, std::string &why) {
 // (pixel rows) and along y (pixel columns), packed as DevTele describes,
 // and the scale slope_scale / (dw lit).
 struct TeleTables {
-    std::vector<int> xs, xe, ys, ye, vfirst;
+    std::vector<int> es, ev, vfirst;
     std::vector<float> fac;
 };
 
@@ -280,11 +280,11 @@ void build_tele_tables(const synim_wfs_desc &d, const WfsTables &t, TeleTables &
     auto Pv = [&](int i, int j) -> int {
         return (i >= 0 && j >= 0 && i < M && j < M) ? t.P[(size_t)i * M + j] : 0;
     };
-    auto pack = [](int end, int i2, int j2) { return (int)(((unsigned)end << 31) | ((unsigned)i2 << 16) | (unsigned)j2); };
-    e.xs.assign(1, 0);
-    e.ys.assign(1, 0);
-    e.xe.clear();
-    e.ye.clear();
+    auto pack = [](int end, int axis, int i2, int j2) {
+        return (int)(((unsigned)end << 31) | ((unsigned)i2 << 16) | ((unsigned)axis << 15) | (unsigned)j2);
+    };
+    e.es.assign(1, 0);
+    e.ev.clear();
     e.fac.clear();
     for (int r = 0; r < t.nv; ++r) {
         const int si = t.vsub[r] >> 16, sj = t.vsub[r] & 0xffff;
@@ -295,13 +295,12 @@ void build_tele_tables(const synim_wfs_desc &d, const WfsTables &t, TeleTables &
                 if (!Pv(i, j)) continue;
                 ++lit;
                 const int i2 = 2 * i + 1, j2 = 2 * j + 1;   // doubled, offset by one
-                if (j == j0 || !Pv(i, j - 1)) e.xe.push_back(pack(0, i2, j2 - 1));
-                if (j == j0 + k - 1 || !Pv(i, j + 1)) e.xe.push_back(pack(1, i2, j2 + 1));
-                if (i == i0 || !Pv(i - 1, j)) e.ye.push_back(pack(0, i2 - 1, j2));
-                if (i == i0 + k - 1 || !Pv(i + 1, j)) e.ye.push_back(pack(1, i2 + 1, j2));
+                if (j == j0 || !Pv(i, j - 1)) e.ev.push_back(pack(0, 0, i2, j2 - 1));
+                if (j == j0 + k - 1 || !Pv(i, j + 1)) e.ev.push_back(pack(1, 0, i2, j2 + 1));
+                if (i == i0 || !Pv(i - 1, j)) e.ev.push_back(pack(0, 1, i2 - 1, j2));
+                if (i == i0 + k - 1 || !Pv(i + 1, j)) e.ev.push_back(pack(1, 1, i2 + 1, j2));
             }
-        e.xs.push_back((int)e.xe.size());
-        e.ys.push_back((int)e.ye.size());
+        e.es.push_back((int)e.ev.size());
         e.fac.push_back((float)(d.slope_scale / (dw * lit)));
     }
     e.vfirst.assign((size_t)n * (n + 1), 0);
@@ -583,18 +582,15 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
             TeleTables TT;
             build_tele_tables(Wd, T, TT);
             DevTele &DT = c->tele.w[w];
-            int *xs = nullptr, *xe = nullptr, *ys = nullptr, *ye = nullptr;
+            int *es = nullptr, *ev = nullptr, *vf = nullptr;
             float *tf = nullptr;
-            int *vf = nullptr;
-            e = dev_upload(c, &xs, TT.xs);
+            e = dev_upload(c, &es, TT.es);
+            if (e == cudaSuccess) e = dev_upload(c, &ev, TT.ev);
             if (e == cudaSuccess) e = dev_upload(c, &vf, TT.vfirst);
-            if (e == cudaSuccess) e = dev_upload(c, &xe, TT.xe);
-            if (e == cudaSuccess) e = dev_upload(c, &ys, TT.ys);
-            if (e == cudaSuccess) e = dev_upload(c, &ye, TT.ye);
             if (e == cudaSuccess) e = dev_upload(c, &tf, TT.fac);
             if (e != cudaSuccess) return bail(cuda_fail(c, e, "telescoping edge tables"));
-            DT.xs = xs; DT.xe = xe; DT.ys = ys; DT.ye = ye; DT.fac = tf; DT.vfirst = vf;
-            // a full subaperture has 2 k events per axis: at most eight per lane
+            DT.es = es; DT.ev = ev; DT.fac = tf; DT.vfirst = vf;
+            // a full subaperture has 4 k events: at most sixteen per lane
             int L = 1;
             while (L < 32 && 4 * L < H.k) L *= 2;
             DT.lanes = L;
@@ -826,6 +822,52 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
     cudaEventRecord(c->slot_ev[slot], s);
     c->slot_used[slot] = true;
     c->slot = (slot + 1) % NSLOT;
+    if (c->autotune && !c->tuned[mode] && tele) {
+        // autotuner of the telescoping kernel: lanes per subaperture (each
+        // sensor's create-time choice times 1/2, 1, 2 or 4, within 1..32) x
+        // 128 or 256 threads, timed like the IM kernel's candidates
+        static const int cand_threads[] = {128, 256};
+        static const int cand_shift[] = {-1, 0, 1, 2};
+        cudaEvent_t t0 = nullptr, t1 = nullptr;
+        if ((e = cudaEventCreate(&t0)) != cudaSuccess || (e = cudaEventCreate(&t1)) != cudaSuccess)
+            return cuda_fail(c, e, "autotune events");
+        const TeleSet base = c->tele;
+        TeleSet best_set = base;
+        float best = 3e38f;
+        int best_th = threads;
+        for (int th : cand_threads)
+            for (int sh : cand_shift) {
+                TeleSet t = base;
+                for (int w = 0; w < c->n_wfs; ++w) {
+                    const int L = base.w[w].lanes;
+                    t.w[w].lanes = std::min(32, std::max(1, sh < 0 ? (L >> -sh) : (L << sh)));
+                }
+                const int gr = grid_for(th);
+                float ms = 0.f;
+                e = launch_tele(g, t, c->d_pairs, gr, th, s);
+                if (e == cudaSuccess) e = cudaEventRecord(t0, s);
+                for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_tele(g, t, c->d_pairs, gr, th, s);
+                if (e == cudaSuccess) e = cudaEventRecord(t1, s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+                if (e != cudaSuccess) break;
+                if (ms < best) {
+                    best = ms;
+                    best_th = th;
+                    best_set = t;
+                }
+            }
+        cudaEventDestroy(t0);
+        cudaEventDestroy(t1);
+        if (e != cudaSuccess) return cuda_fail(c, e, "autotune");
+        c->tele = best_set;
+        c->tuned[mode] = true;
+        c->tune_threads[mode] = best_th;
+        c->tune_lanes[mode] = best_set.w[0].lanes;
+        c->tune_ms[mode] = best / 3.f;
+        threads = best_th;
+        grid = grid_for(threads);
+    }
     if (c->autotune && !c->tuned[mode] && !tele) {
         // autotuner: time each candidate launch shape on this call's inputs
         // (three launches after a warm-up) and keep the fastest for the mode

@@ -63,12 +63,14 @@ struct DevWFS {
 
 // Edge tables of the telescoping-sum engine (Sec. 2.2), per sensor.  Each
 // event is one half-pixel end of a lit pixel run inside a valid subaperture,
-// packed as (end << 31) | ((2 i + 1 + e_i) << 16) | (2 j + 1 + e_j) with
-// (e_i, e_j) the half-pixel offset doubled (-1, 0 or 1) and end = 1 for the
-// run's last pixel (+phi), 0 for its first (-phi); grouped by valid row.
+// packed as (end << 31) | ((2 i + 1 + e_i) << 16) | (axis << 15) |
+// (2 j + 1 + e_j), with (e_i, e_j) the half-pixel offset doubled (-1, 0 or
+// 1), axis 0 for runs along x (pixel rows) and 1 along y (pixel columns),
+// and end = 1 for the run's last pixel (+phi), 0 for its first (-phi);
+// grouped by valid row.
 struct DevTele {
-    const int *xs, *xe;  // x events of valid row r: xe[xs[r] .. xs[r + 1])
-    const int *ys, *ye;  // y events likewise
+    const int *es;       // [nv + 1] first event of each valid row
+    const int *ev;       // events
     const float *fac;    // [nv] slope_scale / (dw lit)
     const int *vfirst;   // [n_sub][n_sub + 1] valid row of the first valid subaperture at
                          // or right of column sj in row si (vrow[si + 1] if none)

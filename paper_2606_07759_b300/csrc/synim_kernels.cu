@@ -864,22 +864,23 @@ k_im(const __grid_constant__ Geo g, const DevPair *__restrict__ pairs, int *__re
 // ---------------------------------------------------------------------------
 // The telescoping-sum engine (Sec. 2.2)
 // ---------------------------------------------------------------------------
-// Sum over one subaperture's events of sign * phi(edge point), this lane's
-// share (events e0 + q, e0 + q + L, ...).  The edge point's offset from the
-// box origin (pi0, pj0) is exact in FP32 (half-integers below 2^14).
-__device__ __forceinline__ float tele_events(const int *__restrict__ ev, int e0, int e1, const Eval<1> &E,
-                                             int bi, int bj, int q, int L) {
-    float acc = 0.f;
+// Sums over one subaperture's events of sign * phi(edge point), x runs into
+// sx and y runs into sy, this lane's share (events e0 + q, e0 + q + L, ...).
+// The edge point's offset from the box origin (pi0, pj0) is exact in FP32
+// (half-integers below 2^14).
+__device__ __forceinline__ void tele_events(const int *__restrict__ ev, int e0, int e1, const Eval<1> &E,
+                                            int bi, int bj, int q, int L, float &sx, float &sy) {
     for (int e = e0 + q; e < e1; e += L) {
         const int c = __ldg(ev + e);
         const float di = 0.5f * (float)(((c >> 16) & 0x7fff) - bi);
-        const float dj = 0.5f * (float)((c & 0xffff) - bj);
+        const float dj = 0.5f * (float)((c & 0x7fff) - bj);
         const float x = fmaf(E.a00, dj, fmaf(E.a01, di, E.xo));
         const float y = fmaf(E.a10, dj, fmaf(E.a11, di, E.yo));
-        const float v = E.bil_at(x, y);
-        acc += (c < 0) ? v : -v;
+        float v = E.bil_at(x, y);
+        v = (c < 0) ? v : -v;
+        if (c & 0x8000) sy += v;
+        else sx += v;
     }
-    return acc;
 }
 
 // One telescoping-sum IM column by one warp: zeros outside the valid rows
@@ -932,10 +933,7 @@ __device__ __forceinline__ void tele_column(const Geo &g, const DevTele &T, cons
             r = WF.vidx[(s.si0 + ti) * WF.n_sub + s.sj0 + (t - ti * nsj)];
         }
         float sx = 0.f, sy = 0.f;
-        if (r >= 0) {
-            sx = tele_events(T.xe, T.xs[r], T.xs[r + 1], E, bi, bj, q, L);
-            sy = tele_events(T.ye, T.ys[r], T.ys[r + 1], E, bi, bj, q, L);
-        }
+        if (r >= 0) tele_events(T.ev, T.es[r], T.es[r + 1], E, bi, bj, q, L, sx, sy);
         for (int o = L >> 1; o > 0; o >>= 1) {
             sx += __shfl_xor_sync(0xffffffffu, sx, o);
             sy += __shfl_xor_sync(0xffffffffu, sy, o);
