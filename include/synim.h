@@ -123,7 +123,7 @@ typedef struct {
                                 over the half-pixel ends of every lit pixel run along x
                                 (sign -1 at the start, +1 at the end; y likewise along
                                 pixel columns), phi resampled at the edge point with no edge
-                                repair.  Sensor grids up to 16383 pixels.  With engine 1 only
+                                repair.  Sensor grids up to 8191 pixels.  With engine 1 only
                                 synim_im_compute is available (sensitivity and vjp return
                                 SYNIM_ERR_INVALID_ARG) */
 } synim_opts;

@@ -268,7 +268,11 @@ bool build_wfs_tables(const synim_wfs_desc &d, WfsTables &t, std::string &why) {
 // Edge tables of the telescoping-sum engine (Sec. 2.2): per valid row, the
 // half-pixel ends of the lit pixel runs inside the subaperture along x
 // (pixel rows) and along y (pixel columns), packed as DevTele describes,
-// and the scale slope_scale / (dw lit).
+// and the scale slope_scale / (dw lit).  A run end on the boundary between
+// two valid subapertures whose pixels on both sides are lit is the end of
+// one run and the start of the next: it is stored once, as the start event
+// of the right (x) or lower (y) subaperture, flagged to credit +phi to the
+// neighbour as well.
 struct TeleTables {
     std::vector<int> es, ev, vfirst;
     std::vector<float> fac;
@@ -280,8 +284,12 @@ void build_tele_tables(const synim_wfs_desc &d, const WfsTables &t, TeleTables &
     auto Pv = [&](int i, int j) -> int {
         return (i >= 0 && j >= 0 && i < M && j < M) ? t.P[(size_t)i * M + j] : 0;
     };
-    auto pack = [](int end, int axis, int i2, int j2) {
-        return (int)(((unsigned)end << 31) | ((unsigned)i2 << 16) | ((unsigned)axis << 15) | (unsigned)j2);
+    auto Vv = [&](int si, int sj) -> bool {
+        return si >= 0 && sj >= 0 && si < n && sj < n && t.vidx[si * n + sj] >= 0;
+    };
+    auto pack = [](int end, int axis, int credit, int i2, int j2) {
+        return (int)(((unsigned)end << 31) | ((unsigned)i2 << 16) | ((unsigned)axis << 15) |
+                     ((unsigned)credit << 14) | (unsigned)j2);
     };
     e.es.assign(1, 0);
     e.ev.clear();
@@ -289,16 +297,19 @@ void build_tele_tables(const synim_wfs_desc &d, const WfsTables &t, TeleTables &
     for (int r = 0; r < t.nv; ++r) {
         const int si = t.vsub[r] >> 16, sj = t.vsub[r] & 0xffff;
         const int i0 = si * k, j0 = sj * k;
+        const bool vl = Vv(si, sj - 1), vr = Vv(si, sj + 1), vt = Vv(si - 1, sj), vb = Vv(si + 1, sj);
         int lit = 0;
         for (int i = i0; i < i0 + k; ++i)
             for (int j = j0; j < j0 + k; ++j) {
                 if (!Pv(i, j)) continue;
                 ++lit;
                 const int i2 = 2 * i + 1, j2 = 2 * j + 1;   // doubled, offset by one
-                if (j == j0 || !Pv(i, j - 1)) e.ev.push_back(pack(0, 0, i2, j2 - 1));
-                if (j == j0 + k - 1 || !Pv(i, j + 1)) e.ev.push_back(pack(1, 0, i2, j2 + 1));
-                if (i == i0 || !Pv(i - 1, j)) e.ev.push_back(pack(0, 1, i2 - 1, j2));
-                if (i == i0 + k - 1 || !Pv(i + 1, j)) e.ev.push_back(pack(1, 1, i2 + 1, j2));
+                if (j == j0 || !Pv(i, j - 1)) e.ev.push_back(pack(0, 0, j == j0 && vl && Pv(i, j - 1), i2, j2 - 1));
+                if (j == j0 + k - 1 || !Pv(i, j + 1))
+                    if (!(j == j0 + k - 1 && vr && Pv(i, j + 1))) e.ev.push_back(pack(1, 0, 0, i2, j2 + 1));
+                if (i == i0 || !Pv(i - 1, j)) e.ev.push_back(pack(0, 1, i == i0 && vt && Pv(i - 1, j), i2 - 1, j2));
+                if (i == i0 + k - 1 || !Pv(i + 1, j))
+                    if (!(i == i0 + k - 1 && vb && Pv(i + 1, j))) e.ev.push_back(pack(1, 1, 0, i2 + 1, j2));
             }
         e.es.push_back((int)e.ev.size());
         e.fac.push_back((float)(d.slope_scale / (dw * lit)));
@@ -442,9 +453,9 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
         return fail(nullptr, SYNIM_ERR_INVALID_ARG, "slope_engine must be 0 (numerical) or 1 (telescoping)");
     }
     for (int w = 0; w < n_wfs && c->slope_engine == SYNIM_ENGINE_TELESCOPING; ++w)
-        if (wfs[w].grid_m > 16383) {
+        if (wfs[w].grid_m > 8191) {
             delete c;
-            return fail(nullptr, SYNIM_ERR_SHAPE, "the telescoping engine takes sensor grids up to 16383 pixels");
+            return fail(nullptr, SYNIM_ERR_SHAPE, "the telescoping engine takes sensor grids up to 8191 pixels");
         }
     if (c->threads % 32 != 0 || c->threads < 64 || c->threads > 256) {
         delete c;
@@ -796,7 +807,15 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
         return fail(c, SYNIM_ERR_SHAPE,
                     "boundary segments need " + std::to_string(8 * 4 * cap) +
                         " bytes of shared memory per CTA; lower the grid or raise support_eps");
-    if (tele) cap = 4;   // the telescoping kernel keeps no per-warp buffer
+    int tele_cap4 = 0;   // the telescoping kernel's per-warp buffer (float4 subaperture sums)
+    if (tele) {
+        // a chunk of box rows plus the carried row: at least two rows, 256 float4 by default
+        tele_cap4 = 256;
+        for (int w = 0; w < c->n_wfs; ++w) tele_cap4 = std::max(tele_cap4, 2 * c->wh[w].n_sub);
+        cap = 4;
+        if ((long long)tele_smem_bytes(256, tele_cap4) > dev_max)
+            return fail(c, SYNIM_ERR_SHAPE, "telescoping engine: too many subapertures per side for shared memory");
+    }
     c->seg_floats = (int)cap;
     g.seg_floats = c->seg_floats;
     // launch shape: the tuned one once the autotuner has run for this mode
@@ -844,9 +863,10 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
                 }
                 const int gr = grid_for(th);
                 float ms = 0.f;
-                e = launch_tele(g, t, c->d_pairs, gr, th, s);
+                e = launch_tele(g, t, c->d_pairs, tele_cap4, c->d_err, gr, th, s);
                 if (e == cudaSuccess) e = cudaEventRecord(t0, s);
-                for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_tele(g, t, c->d_pairs, gr, th, s);
+                for (int r = 0; r < 3 && e == cudaSuccess; ++r)
+                    e = launch_tele(g, t, c->d_pairs, tele_cap4, c->d_err, gr, th, s);
                 if (e == cudaSuccess) e = cudaEventRecord(t1, s);
                 if (e == cudaSuccess) e = cudaEventSynchronize(t1);
                 if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
@@ -939,7 +959,7 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
         if (tele) {
             // telescoping sum: one kernel, no pixel classes
             cudaError_t r = a0 ? cudaEventRecordWithFlags(a0, q, rf) : cudaSuccess;
-            if (r == cudaSuccess) r = launch_tele(g, c->tele, c->d_pairs, grid, threads, q);
+            if (r == cudaSuccess) r = launch_tele(g, c->tele, c->d_pairs, tele_cap4, c->d_err, grid, threads, q);
             if (r == cudaSuccess && b0) r = cudaEventRecordWithFlags(b0, q, rf);
             return r;
         }

@@ -64,10 +64,13 @@ struct DevWFS {
 // Edge tables of the telescoping-sum engine (Sec. 2.2), per sensor.  Each
 // event is one half-pixel end of a lit pixel run inside a valid subaperture,
 // packed as (end << 31) | ((2 i + 1 + e_i) << 16) | (axis << 15) |
-// (2 j + 1 + e_j), with (e_i, e_j) the half-pixel offset doubled (-1, 0 or
-// 1), axis 0 for runs along x (pixel rows) and 1 along y (pixel columns),
-// and end = 1 for the run's last pixel (+phi), 0 for its first (-phi);
-// grouped by valid row.
+// (credit << 14) | (2 j + 1 + e_j), with (e_i, e_j) the half-pixel offset
+// doubled (-1, 0 or 1), axis 0 for runs along x (pixel rows) and 1 along y
+// (pixel columns), end = 1 for the run's last pixel (+phi), 0 for its first
+// (-phi), and credit = 1 for a run start on the left (x) or upper (y)
+// boundary whose point is also the end of a run of the valid neighbour
+// there: that neighbour's event is not stored, and this one adds +phi to
+// the neighbour's sum.  Grouped by valid row.
 struct DevTele {
     const int *es;       // [nv + 1] first event of each valid row
     const int *ev;       // events
@@ -135,9 +138,12 @@ size_t im_smem_bytes(const Geo &g);
 cudaError_t im_prepare(int mode, int threads, size_t smem, int *blocks_per_sm);
 cudaError_t launch_im(int mode, const Geo &g, const DevPair *pairs, int *counter, int *err,
                       double *gp, int grid, int threads, size_t smem, cudaStream_t s);
-// The telescoping-sum IM kernel: one warp per (actuator, sensor) column.
-cudaError_t launch_tele(const Geo &g, const TeleSet &t, const DevPair *pairs, int grid, int threads,
-                        cudaStream_t s);
+// The telescoping-sum IM kernel: one warp per (actuator, sensor) column, a
+// per-warp buffer of cap4 float4 subaperture sums (a chunk of box rows and
+// the row above it; cap4 >= 2 n_sub).
+size_t tele_smem_bytes(int threads, int cap4);
+cudaError_t launch_tele(const Geo &g, const TeleSet &t, const DevPair *pairs, int cap4, int *err, int grid,
+                        int threads, cudaStream_t s);
 
 struct ProbeSet;   // synim_probe.cu
 void probe_destroy(ProbeSet *p);

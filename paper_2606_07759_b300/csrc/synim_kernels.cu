@@ -21,7 +21,8 @@
 //                     one-warp-per-column launch; a slope is the signed sum of
 //                     the IF resampled at the half-pixel ends of the lit runs
 //                     of its subaperture (create-time event tables), without
-//                     pixel classes or edge repair.
+//                     pixel classes or edge repair.  A run end shared by two
+//                     valid neighbours is resampled once and credited to both.
 //
 // The subaperture sum of central differences is evaluated in telescoped
 // form: sum_{p in s} P(p) (phi(p+x) - phi(p-x)) = sum_q phi(q) w_s(q) where
@@ -864,34 +865,52 @@ k_im(const __grid_constant__ Geo g, const DevPair *__restrict__ pairs, int *__re
 // ---------------------------------------------------------------------------
 // The telescoping-sum engine (Sec. 2.2)
 // ---------------------------------------------------------------------------
-// Sums over one subaperture's events of sign * phi(edge point), x runs into
-// sx and y runs into sy, this lane's share (events e0 + q, e0 + q + L, ...).
-// The edge point's offset from the box origin (pi0, pj0) is exact in FP32
-// (half-integers below 2^14).
+// Sums over one subaperture's events of sign * phi(edge point), this
+// lane's share (events e0 + q, e0 + q + L, ..., four loads in flight):
+// acc.x / acc.y the subaperture's own x / y sums, acc.z / acc.w the +phi
+// credited to its left / upper neighbour by shared run ends.  The edge point's offset from the
+// box origin (pi0, pj0) is exact in FP32 (half-integers below 2^13).
 __device__ __forceinline__ void tele_events(const int *__restrict__ ev, int e0, int e1, const Eval<1> &E,
-                                            int bi, int bj, int q, int L, float &sx, float &sy) {
-    for (int e = e0 + q; e < e1; e += L) {
-        const int c = __ldg(ev + e);
-        const float di = 0.5f * (float)(((c >> 16) & 0x7fff) - bi);
-        const float dj = 0.5f * (float)((c & 0x7fff) - bj);
-        const float x = fmaf(E.a00, dj, fmaf(E.a01, di, E.xo));
-        const float y = fmaf(E.a10, dj, fmaf(E.a11, di, E.yo));
-        float v = E.bil_at(x, y);
-        v = (c < 0) ? v : -v;
-        if (c & 0x8000) sy += v;
-        else sx += v;
+                                            int bi, int bj, int q, int L, float4 &acc) {
+    constexpr int U = 4;   // events loaded ahead of their interpolation
+    for (int e = e0 + q; e < e1; e += U * L) {
+        int cc[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) cc[u] = (e + u * L < e1) ? __ldg(ev + e + u * L) : 0;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int c = cc[u];
+            const float di = 0.5f * (float)(((c >> 16) & 0x7fff) - bi);
+            const float dj = 0.5f * (float)((c & 0x3fff) - bj);
+            const float x = fmaf(E.a00, dj, fmaf(E.a01, di, E.xo));
+            const float y = fmaf(E.a10, dj, fmaf(E.a11, di, E.yo));
+            const float phi = (e + u * L < e1) ? E.bil_at(x, y) : 0.f;
+            const float v = (c < 0) ? phi : -phi;
+            const float cr = (c & 0x4000) ? phi : 0.f;
+            if (c & 0x8000) {
+                acc.y += v;
+                acc.w += cr;
+            } else {
+                acc.x += v;
+                acc.z += cr;
+            }
+        }
     }
 }
 
 // One telescoping-sum IM column by one warp: zeros outside the valid rows
 // of the subaperture box and in each box row's gaps (valid subapertures left
-// or right of the box), and for every box subaperture the two edge sums
-// (groups of L lanes share a subaperture, taken in box order across the
-// rows; fixed butterfly order) times slope_scale / (dw lit).  Every phase
-// value is one bilinear sample of the packed window; there is no
+// or right of the box), then chunk by chunk of box rows: per box
+// subaperture (groups of L lanes over the whole chunk, fixed butterfly
+// order) the own sums and the credits to its left and upper neighbours, kept
+// in shared memory with the previous chunk's last row; the x slopes (own +
+// the right neighbour's credit) and the y slopes of the rows above (own +
+// the lower neighbour's credit) times slope_scale / (dw lit).  A neighbour outside the box contributes nothing:
+// its shared points lie beyond the pixel box, where the IF is zero.  Every
+// phase value is one bilinear sample of the packed window; there is no
 // pixel-class map and no edge repair.
 __device__ __forceinline__ void tele_column(const Geo &g, const DevTele &T, const DevPair *__restrict__ pairs,
-                                            int d, int a, int w, int lane) {
+                                            int d, int a, int w, float4 *wbuf, int cap4, int lane, int *err) {
     const DevPair &P = pairs[d * g.n_wfs + w];
     if (!P.im) return;
     const DevWFS &WF = g.wfs[w];
@@ -900,6 +919,10 @@ __device__ __forceinline__ void tele_column(const Geo &g, const DevTele &T, cons
     make_info<MODE_FWD, 1>(g, pairs, d, a, w, s, nullptr);
     const int nv = WF.nv, n2 = 2 * nv;
     float *col = P.im + (size_t)a * n2;
+    if (!s.empty && 2 * s.nsj > cap4) {   // the buffer holds at least two rows of n_sub: not reached
+        if (lane == 0) atomicOr(err, ERR_ARENA);
+        s.empty = 1;
+    }
     const int vr0 = s.empty ? 0 : WF.vrow[s.si0], vr1 = s.empty ? 0 : WF.vrow[s.si1 + 1];
     if (P.vec4) {
         bulk_zero(col, 0, vr0, lane);
@@ -924,47 +947,83 @@ __device__ __forceinline__ void tele_column(const Geo &g, const DevTele &T, cons
     E.load(s, D.win + (size_t)a * D.win_stride, D.Wp, D.W, WF.M);
     const int L = T.lanes, per = 32 / L, grp = lane / L, q = lane - grp * L;
     const int bi = 2 * s.pi0 + 1, bj = 2 * s.pj0 + 1;
-    const int nsj = s.nsj, nb = (s.si1 - s.si0 + 1) * nsj;
-    for (int base = 0; base < nb; base += per) {
-        const int t = base + grp;
-        int r = -1;
-        if (t < nb) {
-            const int ti = t / nsj;
-            r = WF.vidx[(s.si0 + ti) * WF.n_sub + s.sj0 + (t - ti * nsj)];
+    const int nsj = s.nsj, n = WF.n_sub;
+    // chunks of R box rows: buffer row 0 carries the previous chunk's last row
+    const int R = max(1, cap4 / nsj - 1);
+    for (int sc = s.si0; sc <= s.si1; sc += R) {
+        const int Rc = min(R, s.si1 - sc + 1), nb = Rc * nsj;
+        const int *vchunk = WF.vidx + sc * n + s.sj0;
+        for (int base = 0; base < nb; base += per) {
+            const int t = base + grp;
+            int r = -1;
+            if (t < nb) {
+                const int ri = t / nsj;
+                r = vchunk[ri * n + (t - ri * nsj)];
+            }
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (r >= 0) tele_events(T.ev, T.es[r], T.es[r + 1], E, bi, bj, q, L, acc);
+            for (int o = L >> 1; o > 0; o >>= 1) {
+                acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+                acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+                acc.z += __shfl_xor_sync(0xffffffffu, acc.z, o);
+                acc.w += __shfl_xor_sync(0xffffffffu, acc.w, o);
+            }
+            if (q == 0 && t < nb) wbuf[nsj + t] = acc;
         }
-        float sx = 0.f, sy = 0.f;
-        if (r >= 0) tele_events(T.ev, T.es[r], T.es[r + 1], E, bi, bj, q, L, sx, sy);
-        for (int o = L >> 1; o > 0; o >>= 1) {
-            sx += __shfl_xor_sync(0xffffffffu, sx, o);
-            sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        __syncwarp();
+        // x slopes of the chunk's rows, y slopes of the rows above them
+        for (int t = lane; t < nb; t += 32) {
+            const int ri = t / nsj, c = t - ri * nsj;
+            const float4 me = wbuf[nsj + t];
+            const int r = vchunk[ri * n + c];
+            if (r >= 0) col[r] = (me.x + (c + 1 < nsj ? wbuf[nsj + t + 1].z : 0.f)) * T.fac[r];
+            if (sc + ri > s.si0) {
+                const int rp = vchunk[(ri - 1) * n + c];
+                if (rp >= 0) col[nv + rp] = (wbuf[t].y + me.w) * T.fac[rp];
+            }
         }
-        if (r >= 0 && q == 0) {
-            const float f = T.fac[r];
-            col[r] = sx * f;
-            col[nv + r] = sy * f;
-        }
+        __syncwarp();
+        for (int c = lane; c < nsj; c += 32) wbuf[c] = wbuf[nb + c];   // carry the last row
+        __syncwarp();
     }
+    // y slopes of the last box row (its lower neighbours lie outside the box)
+    const int *vlast = WF.vidx + s.si1 * n + s.sj0;
+    for (int c = lane; c < nsj; c += 32) {
+        const int rp = vlast[c];
+        if (rp >= 0) col[nv + rp] = wbuf[c].y * T.fac[rp];
+    }
+    __syncwarp();
 }
 
 __global__ void __launch_bounds__(256)
-k_tele(const __grid_constant__ Geo g, const __grid_constant__ TeleSet t, const DevPair *__restrict__ pairs) {
+k_tele(const __grid_constant__ Geo g, const __grid_constant__ TeleSet t, const DevPair *__restrict__ pairs,
+       int cap4, int *__restrict__ err) {
+    extern __shared__ __align__(16) float4 tele_smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int q = threadIdx.x; q < kZeroFloats / 4; q += blockDim.x) s_zero[q] = make_float4(0.f, 0.f, 0.f, 0.f);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic zeros -> bulk-copy reads
     __syncthreads();
+    float4 *wbuf = tele_smem + (size_t)warp * cap4;
     const long n_units = (long)g.n_items * g.n_wfs;
     for (long u = (long)blockIdx.x * nw + warp; u < n_units; u += (long)gridDim.x * nw) {
         const int item = (int)(u / g.n_wfs), w = (int)(u - (long)item * g.n_wfs);
         int d, a;
         decode_item(g, item, d, a);
-        tele_column(g, t.w[w], pairs, d, a, w, lane);
+        tele_column(g, t.w[w], pairs, d, a, w, wbuf, cap4, lane, err);
     }
     if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 
-cudaError_t launch_tele(const Geo &g, const TeleSet &t, const DevPair *pairs, int grid, int threads,
-                        cudaStream_t s) {
-    k_tele<<<grid, threads, 0, s>>>(g, t, pairs);
+size_t tele_smem_bytes(int threads, int cap4) { return (size_t)(threads / 32) * cap4 * sizeof(float4); }
+
+cudaError_t launch_tele(const Geo &g, const TeleSet &t, const DevPair *pairs, int cap4, int *err, int grid,
+                        int threads, cudaStream_t s) {
+    const size_t smem = tele_smem_bytes(threads, cap4);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_tele, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_tele<<<grid, threads, smem, s>>>(g, t, pairs, cap4, err);
     return cudaGetLastError();
 }
 
