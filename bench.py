@@ -40,7 +40,7 @@ UNIT = "columns/s"
 # DRAM bytes (read + write) of one k_im launch on the MCAO workload, from the
 # one-pass ncu capture summarised in profiles/k_im_mcao_dram_full.md; valid only
 # for the kernel source whose hash is recorded with it.
-TRAFFIC = {"kernel_sha1": "54059784ba2a7f90966a6d9632634f750a376834", "bytes_per_launch": 143.52e6 + 1.34e9}
+TRAFFIC = {"kernel_sha1": "2cfacefbc10269e32f462c21863da294a28e3200", "bytes_per_launch": 143.55e6 + 1.34e9}
 
 
 def kernel_sha1() -> str:
