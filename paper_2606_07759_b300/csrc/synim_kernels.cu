@@ -1019,7 +1019,7 @@ size_t tele_smem_bytes(int threads, int cap4) { return (size_t)(threads / 32) * 
 cudaError_t launch_tele(const Geo &g, const TeleSet &t, const DevPair *pairs, int cap4, int *err, int grid,
                         int threads, cudaStream_t s) {
     const size_t smem = tele_smem_bytes(threads, cap4);
-    if (smem > 48 * 1024) {
+    if (smem + sizeof(s_zero) > 48 * 1024) {   // static + dynamic above the default limit
         cudaError_t e = cudaFuncSetAttribute(k_tele, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
