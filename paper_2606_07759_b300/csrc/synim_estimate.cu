@@ -23,6 +23,15 @@ namespace synim {
 
 constexpr int kRedThreads = 256;
 constexpr int kRed = 16;  // c, H (10), g (4), y.y
+// A few samples leave most SMs idle, and the FP64 sums of one sample on one
+// SM are slow: each sample's elements are split over `parts` blocks (about
+// two blocks per SM in all, at most 128 per sample), whose partial sums a
+// second kernel adds in a fixed order.  n * parts <= max(n, kPartRows).
+constexpr int kMaxParts = 128;
+constexpr int kPartRows = 320;
+inline int reduce_parts(long long n, int n_sm) {
+    return (int)std::max<long long>(1, std::min<long long>(kMaxParts, std::min<long long>(2LL * n_sm, kPartRows) / n));
+}
 
 enum : int { GN_DONE = 1, GN_CONV = 2, GN_FIRST = 4 };
 
@@ -39,6 +48,7 @@ struct EstState {
     float *maps = nullptr;      // [cap][per_sample]
     float *dmaps = nullptr;     // [4][cap][per_sample]
     double *red = nullptr;      // [cap][kRed]
+    double *red_part = nullptr; // [n * parts][kRed] partial sums (parts blocks per sample)
     double *pt = nullptr;       // [cap][4]
     GnState *st = nullptr;      // [cap]
     int *n_active = nullptr;    // device counter
@@ -54,6 +64,7 @@ void est_destroy(EstState *e) {
     cudaFree(e->maps);
     cudaFree(e->dmaps);
     cudaFree(e->red);
+    cudaFree(e->red_part);
     cudaFree(e->pt);
     cudaFree(e->st);
     cudaFree(e->n_active);
@@ -71,14 +82,16 @@ __host__ __device__ __forceinline__ int tri(int a, int b) {
 
 __global__ void __launch_bounds__(kRedThreads)
 k_gn_reduce(const float *__restrict__ y, const float *__restrict__ s, const float *__restrict__ ds,
-            long n, int per_sample, double *__restrict__ red) {
-    const long q = blockIdx.x;
+            long n, int per_sample, int parts, double *__restrict__ red_part) {
+    const long q = blockIdx.y;
+    const int part = blockIdx.x, seg = (per_sample + parts - 1) / parts;
+    const int e0 = part * seg, e1 = min(per_sample, e0 + seg);
     const float *yq = y + q * per_sample, *sq = s + q * per_sample;
     const size_t plane = (size_t)n * per_sample;
     double acc[kRed];
 #pragma unroll
     for (int t = 0; t < kRed; ++t) acc[t] = 0.0;
-    for (int e = threadIdx.x; e < per_sample; e += blockDim.x) {
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
         const double yv = yq[e];
         const double r = yv - (double)sq[e];
         double j[4];
@@ -108,17 +121,33 @@ k_gn_reduce(const float *__restrict__ y, const float *__restrict__ s, const floa
     if (threadIdx.x < kRed) {
         double v = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sh[w][threadIdx.x];
-        red[q * kRed + threadIdx.x] = v;
+        red_part[(q * parts + part) * kRed + threadIdx.x] = v;
     }
+}
+
+// out[q][t] = sum over the parts of sample q of part[q][b][t] (t < nq), one
+// warp per quantity, fixed order for a given number of parts.
+__global__ void k_red_combine(const double *__restrict__ part, int parts, int nq, double *__restrict__ out) {
+    const long q = blockIdx.x;
+    const int t = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (t >= nq) return;
+    double v = 0.0;
+    for (int b = lane; b < parts; b += 32) v += part[(q * parts + b) * nq + t];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) out[q * nq + t] = v;
 }
 
 // Residual sums only: red2[q] = (r.r, y.y) of sample q.
 __global__ void __launch_bounds__(kRedThreads)
-k_resid_reduce(const float *__restrict__ y, const float *__restrict__ s, int per_sample, double *__restrict__ red2) {
-    const long q = blockIdx.x;
+k_resid_reduce(const float *__restrict__ y, const float *__restrict__ s, int per_sample, int parts,
+               double *__restrict__ red2_part) {
+    const long q = blockIdx.y;
+    const int part = blockIdx.x, seg = (per_sample + parts - 1) / parts;
+    const int e0 = part * seg, e1 = min(per_sample, e0 + seg);
     const float *yq = y + q * per_sample, *sq = s + q * per_sample;
     double rr = 0.0, yy = 0.0;
-    for (int e = threadIdx.x; e < per_sample; e += blockDim.x) {
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
         const double yv = yq[e], r = yv - (double)sq[e];
         rr += r * r;
         yy += yv * yv;
@@ -137,7 +166,7 @@ k_resid_reduce(const float *__restrict__ y, const float *__restrict__ s, int per
     if (threadIdx.x < 2) {
         double v = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sh[w][threadIdx.x];
-        red2[2 * q + threadIdx.x] = v;
+        red2_part[(q * parts + part) * 2 + threadIdx.x] = v;
     }
 }
 
@@ -266,18 +295,21 @@ cudaError_t est_reserve(EstState *E, long long cap, int per_sample) {
     cudaFree(E->maps);
     cudaFree(E->dmaps);
     cudaFree(E->red);
+    cudaFree(E->red_part);
     cudaFree(E->pt);
     cudaFree(E->st);
     cudaFree(E->p0);
     cudaFreeHost(E->h_p);
     cudaFreeHost(E->h_r);
     E->maps = E->dmaps = nullptr;
-    E->red = E->pt = E->p0 = E->h_p = E->h_r = nullptr;
+    E->red = E->red_part = E->pt = E->p0 = E->h_p = E->h_r = nullptr;
     E->st = nullptr;
     E->cap = 0;
     if ((e = cudaMalloc(&E->maps, sizeof(float) * per_sample * cap)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&E->dmaps, sizeof(float) * 4 * per_sample * cap)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&E->red, sizeof(double) * kRed * cap)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&E->red_part, sizeof(double) * kRed * std::max<long long>(cap, kPartRows))) != cudaSuccess)
+        return e;
     if ((e = cudaMalloc(&E->pt, sizeof(double) * 4 * cap)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&E->st, sizeof(GnState) * cap)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&E->p0, sizeof(double) * 4 * cap)) != cudaSuccess) return e;
@@ -303,11 +335,14 @@ cudaError_t gn_fit(synim_ctx *c, const float *y, long long n, const double *p0, 
     cfg.tol = E->tol;
     for (int k = 0; k < 4; ++k) cfg.scale[k] = E->scale[k];
     const unsigned nb = (unsigned)((n + 63) / 64);
+    const int parts = reduce_parts(n, c->n_sm);
     k_gn_init<<<nb, 64, 0, st>>>(E->st, p0, n, E->pt);
     cudaError_t e = cudaGetLastError();
     for (int pass = 0; pass <= E->max_iter + 16 && e == cudaSuccess; ++pass) {
         if ((e = probe_launch(c, E->pt, n, E->maps, E->dmaps, nullptr, st)) != cudaSuccess) break;
-        k_gn_reduce<<<(unsigned)n, kRedThreads, 0, st>>>(y, E->maps, E->dmaps, n, per_sample, E->red);
+        k_gn_reduce<<<dim3((unsigned)parts, (unsigned)n), kRedThreads, 0, st>>>(y, E->maps, E->dmaps, n, per_sample,
+                                                                                parts, E->red_part);
+        k_red_combine<<<(unsigned)n, 32 * kRed, 0, st>>>(E->red_part, parts, kRed, E->red);
         if ((e = cudaMemsetAsync(E->n_active, 0, sizeof(int), st)) != cudaSuccess) break;
         k_gn_step<<<nb, 64, 0, st>>>(E->st, E->red, n, cfg, E->pt, E->n_active);
         if ((e = cudaMemcpyAsync(E->h_active, E->n_active, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
@@ -403,7 +438,10 @@ synim_status synim_misreg_estimate(synim_ctx *ctx, const float *probe_slopes, in
             if (residual_out) {
                 e = probe_launch(ctx, p0, b, E->maps, nullptr, nullptr, st);
                 if (e == cudaSuccess) {
-                    k_resid_reduce<<<(unsigned)b, kRedThreads, 0, st>>>(y, E->maps, per_sample, E->red);
+                    const int parts = reduce_parts(b, ctx->n_sm);
+                    k_resid_reduce<<<dim3((unsigned)parts, (unsigned)b), kRedThreads, 0, st>>>(y, E->maps, per_sample,
+                                                                                               parts, E->red_part);
+                    k_red_combine<<<(unsigned)b, 64, 0, st>>>(E->red_part, parts, 2, E->red);
                     e = cudaMemcpyAsync(E->h_r, E->red, sizeof(double) * 2 * b, cudaMemcpyDeviceToHost, st);
                 }
             }
