@@ -60,6 +60,7 @@ struct CnnState {
     bf16 *x = nullptr, *a1 = nullptr, *a2 = nullptr, *a3 = nullptr;
     bf16 *dz1 = nullptr, *dz2 = nullptr, *dz3 = nullptr;
     float *out = nullptr, *loss = nullptr, *dout = nullptr;
+    float *hpart = nullptr;   // head partial sums of small batches [kBatchCap][4]
     float *wpart = nullptr;   // weight-gradient partials [splits][64 K + 64]
     long long wpart_floats = 0;
     float *tgt = nullptr;   // [kBatchCap][4] targets of the current batch
@@ -74,7 +75,7 @@ struct CnnState {
 void cnn_destroy(CnnState *s) {
     if (!s) return;
     void *p[] = {s->master, s->adam_m, s->adam_v, s->grad, s->w1, s->w2, s->w3, s->w2t, s->w3t, s->x,
-                 s->a1, s->a2, s->a3, s->dz1, s->dz2, s->dz3, s->out, s->loss, s->dout,
+                 s->a1, s->a2, s->a3, s->dz1, s->dz2, s->dz3, s->out, s->loss, s->dout, s->hpart,
                  s->wpart, s->tgt, s->perm, s->data, s->targets, s->d_err};
     for (void *q : p) cudaFree(q);
     cudaFreeHost(s->h_loss);
@@ -1021,13 +1022,18 @@ __global__ void __launch_bounds__(256) k_sum_parts(const float *__restrict__ par
 constexpr int kHeadThreads = 256;
 
 // out[b][j] = bfc[j] + sum_e Wfc[j][e] a3[b][e]; loss[b] = sum_j (out - tgt)^2.
+// With parts > 1 (small batches: a lone block per sample leaves the GPU idle)
+// block (part, b) sums features [part seg, (part + 1) seg) into
+// part_out[b][part][4] and k_head_combine finishes.
 __global__ void __launch_bounds__(kHeadThreads)
 k_head_fwd(const bf16 *__restrict__ a3, int F, const float *__restrict__ wfc, const float *__restrict__ bfc,
-           const float *__restrict__ tgt, float *__restrict__ out, float *__restrict__ loss) {
-    const int b = blockIdx.x;
+           const float *__restrict__ tgt, float *__restrict__ out, float *__restrict__ loss, int parts,
+           float *__restrict__ part_out) {
+    const int b = blockIdx.y, part = blockIdx.x, seg = (F + parts - 1) / parts;
+    const int e0 = part * seg, e1 = min(F, e0 + seg);
     const bf16 *x = a3 + (size_t)b * F;
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int e = threadIdx.x; e < F; e += blockDim.x) {
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
         const float v = __bfloat162float(x[e]);
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[j] = fmaf(wfc[(size_t)j * F + e], v, acc[j]);
@@ -1044,6 +1050,14 @@ k_head_fwd(const bf16 *__restrict__ a3, int F, const float *__restrict__ wfc, co
 #pragma unroll
         for (int j = 0; j < 4; ++j) sh[threadIdx.x >> 5][j] = acc[j];
     __syncthreads();
+    if (parts > 1) {
+        if (threadIdx.x < 4) {
+            float o = 0.f;
+            for (int w = 0; w < kHeadThreads / 32; ++w) o += sh[w][threadIdx.x];
+            part_out[((size_t)b * parts + part) * 4 + threadIdx.x] = o;
+        }
+        return;
+    }
     if (threadIdx.x == 0) {
         float l = 0.f;
         for (int j = 0; j < 4; ++j) {
@@ -1057,6 +1071,24 @@ k_head_fwd(const bf16 *__restrict__ a3, int F, const float *__restrict__ wfc, co
         }
         if (tgt) loss[b] = l;
     }
+}
+
+// out[b][j] = bfc[j] + the parts' sums in part order; loss as in k_head_fwd.
+__global__ void k_head_combine(const float *__restrict__ part_out, int parts, int B, const float *__restrict__ bfc,
+                               const float *__restrict__ tgt, float *__restrict__ out, float *__restrict__ loss) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    float l = 0.f;
+    for (int j = 0; j < 4; ++j) {
+        float o = bfc[j];
+        for (int p = 0; p < parts; ++p) o += part_out[((size_t)b * parts + p) * 4 + j];
+        out[b * 4 + j] = o;
+        if (tgt) {
+            const float d = o - tgt[b * 4 + j];
+            l = fmaf(d, d, l);
+        }
+    }
+    if (tgt) loss[b] = l;
 }
 
 // dout = d(mean loss)/d out.
@@ -1387,8 +1419,13 @@ cudaError_t forward(CnnState &S, const bf16 *in, const int *perm, long long b0, 
     if ((e = launch_conv_fwd(S, 1, in, perm, b0, B, st)) != cudaSuccess) return e;
     if ((e = launch_conv_fwd(S, 2, S.a1, nullptr, 0, B, st)) != cudaSuccess) return e;
     if ((e = launch_conv_fwd(S, 3, S.a2, nullptr, 0, B, st)) != cudaSuccess) return e;
-    k_head_fwd<<<B, kHeadThreads, 0, st>>>(S.a3, S.H3 * S.H3 * CH, S.master + S.off_fc, S.master + S.off_bfc,
-                                           tgt, S.out, S.loss);
+    // split the head's features over blocks while B * parts fits the partial buffer
+    const int parts = std::max(1, std::min(32, kBatchCap / std::max(B, 1)));
+    k_head_fwd<<<dim3(parts, B), kHeadThreads, 0, st>>>(S.a3, S.H3 * S.H3 * CH, S.master + S.off_fc,
+                                                        S.master + S.off_bfc, tgt, S.out, S.loss, parts, S.hpart);
+    if (parts > 1)
+        k_head_combine<<<blocks_for(B, 64), 64, 0, st>>>(S.hpart, parts, B, S.master + S.off_bfc, tgt, S.out,
+                                                         S.loss);
     return cudaGetLastError();
 }
 
@@ -1435,6 +1472,7 @@ cudaError_t alloc_state(CnnState &S) {
     SYNIM_A(S.out, (size_t)kBatchCap * 4);
     SYNIM_A(S.loss, (size_t)kBatchCap);
     SYNIM_A(S.dout, (size_t)kBatchCap * 4);
+    SYNIM_A(S.hpart, (size_t)kBatchCap * 4);
     SYNIM_A(S.tgt, (size_t)kBatchCap * 4);
     SYNIM_A(S.wpart, (size_t)S.wpart_floats);
     SYNIM_A(S.d_err, 1);

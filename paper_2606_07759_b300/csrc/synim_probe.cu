@@ -117,7 +117,7 @@ __global__ void k_form_screens(const DevDM D, const double *__restrict__ cmd, in
 
 // Per-sample composite transform (Sec. 2.1) and its parameter derivatives.
 __global__ void k_probe_affine(const DmHost D, const WfsHost W, const double *__restrict__ params,
-                               long n, ProbeAff *__restrict__ out) {
+                               long n, int with_jac, ProbeAff *__restrict__ out) {
     const long s = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     synim_misreg m;
@@ -127,8 +127,10 @@ __global__ void k_probe_affine(const DmHost D, const WfsHost W, const double *__
     m.mag = params[4 * s + 3];
     ProbeAff P;
     composite(D, W, m, P.A, P.b);
-    double dA[16], db[8];
-    composite_jac(D, m, P.A, P.b, dA, db);
+    // the tangent terms only when tangents are asked for (another FP64 sine
+    // and cosine on a single thread per sample)
+    double dA[16] = {}, db[8] = {};
+    if (with_jac) composite_jac(D, m, P.A, P.b, dA, db);
     for (int q = 0; q < 4; ++q) {
         P.Ahi[q] = (float)P.A[q];
         P.Alo[q] = (float)(P.A[q] - (double)P.Ahi[q]);
@@ -515,7 +517,8 @@ cudaError_t probe_launch(synim_ctx *c, const double *params, long long n, float 
     cudaError_t e = ensure_aff(c, p, n);
     if (e != cudaSuccess) return e;
     const int d = p->dm, w = p->wfs;
-    k_probe_affine<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(c->dmh[d], c->wh[w], params, n, p->aff);
+    k_probe_affine<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(c->dmh[d], c->wh[w], params, n,
+                                                               dmaps != nullptr ? 1 : 0, p->aff);
     ProbeGeo G = p->geo;
     const bool tan = dmaps != nullptr;
     G.Cs = tan ? p->cs_tan : p->cs_fwd;
