@@ -141,8 +141,8 @@ def test_elt_single_full_size_sampled_columns():
 
 
 def test_mcao_full_size_sampled_columns():
-    # the batched MCAO workload in the launch configuration the benchmark times
-    check_workload(W.mcao_batched(seed=3), cols_per_dm=12)
+    # the batched MCAO workload in the launch configuration the benchmark times (autotuned)
+    check_workload(W.mcao_batched(seed=3), cols_per_dm=12, autotune=True)
 
 
 def test_profiling_events_count_kernel_launches():
