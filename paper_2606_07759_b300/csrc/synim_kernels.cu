@@ -515,9 +515,12 @@ __device__ __forceinline__ void seg_compute(const DevWFS &WF, const SegRows &r, 
         const float sx = (float)lstep * (axis ? ev.a00 : ev.a01), sy = (float)lstep * (axis ? ev.a10 : ev.a11);
         const float ox = axis ? ev.a01 : ev.a00, oy = axis ? ev.a11 : ev.a10;
         float qf = 0.f;
+        // the next pixel pair's byte is loaded before this one's resamples
+        int c_next = __ldg(cp);
         for (int u = u0; u <= r.ub; u += lstep, qf += 1.f, cp += cstep) {
             const float x = fmaf(qf, sx, x0), y = fmaf(qf, sy, y0);
-            const int c = __ldg(cp);
+            const int c = c_next;
+            if (u + lstep <= r.ub) c_next = __ldg(cp + cstep);
             const int cl0 = (inmask & 1) ? (c >> 4) & 3 : 0, cl1 = (inmask & 2) ? (c >> 6) & 3 : 0;
             float v0, v1;
             if (cl0 == 2 || cl1 == 2) {
