@@ -40,7 +40,7 @@ UNIT = "columns/s"
 # DRAM bytes (read + write) of one k_im launch on the MCAO workload, from the
 # one-pass ncu capture summarised in profiles/k_im_mcao_dram_full.md; valid only
 # for the kernel source whose hash (kernel_sha1) is recorded with it.
-TRAFFIC = {"kernel_sha1": "1caef629602af6617bafa389785e32c8f0a0c7a3", "bytes_per_launch": 148.60e6 + 1.36e9}
+TRAFFIC = {"kernel_sha1": "25c205469dbd4e672ab2a3c20cebf5fc934b942e", "bytes_per_launch": 138.84e6 + 1.3309e9}
 
 
 def kernel_sha1() -> str:
