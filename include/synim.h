@@ -160,8 +160,8 @@ synim_status synim_pair_affine(const synim_ctx *ctx, int32_t dm, int32_t wfs,
                                const synim_misreg *mis, double *A, double *b);
 
 /*
- * Compute every IM of the context in one persistent launch (Sec. 2.1-2.3,
- * Sec. 4.2).  mis[n_dm * n_wfs] (host) holds one misregistration per pair,
+ * Compute every IM of the context in one launch (Sec. 2.1-2.3, Sec. 4.2):
+ * one warp per (actuator, sensor) column over a grid-stride loop.  mis[n_dm * n_wfs] (host) holds one misregistration per pair,
  * pair index = dm * n_wfs + wfs; im[n_dm * n_wfs] (host array) holds device
  * pointers to the caller's FP32 output buffers (layout above); a NULL entry
  * skips that pair.  Asynchronous on cuda_stream.
@@ -199,7 +199,7 @@ synim_status synim_im_vjp(synim_ctx *ctx, const synim_misreg *mis, const float *
 synim_status synim_im_check(synim_ctx *ctx, void *cuda_stream);
 
 /* ------------------------------------------------------------------------
- * Tomographic projection (Sec. 3, tomographic projection matrices).
+ * Tomographic projection (Sec. 2.5, tomographic projection matrices).
  *
  * The components of a context (its DMs and virtual layers) are seen from
  * n_dir optimisation directions dirs_rad[j] = (theta_x, theta_y) by a

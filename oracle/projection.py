@@ -3,7 +3,7 @@
 Only ``tests/`` and the CPU legs of ``bench.py`` may use it; the product path
 never imports it.
 
-Sec. 3 (tomographic projection matrices) defines the projection as a
+Sec. 2.5 (tomographic projection matrices) defines the projection as a
 pseudo-inverse (P_DM^T P_DM + lambda I)^{-1} P_DM^T P_Layer.  P_DM and
 P_Layer map each influence function over the optimisation directions.  The
 readings taken here are written out in full:

@@ -24,9 +24,11 @@ only at the subaperture edges.  The reading taken here is written out:
 
 Pins (tests/test_oracle_telescoping.py):
 - a tilted plane gives its exact gradient, whatever the lit shape;
-- a quadratic gives the lit-area centroid law;
-- low-frequency influence functions agree with the numerical-derivative
-  engine to O((k dw / sigma)^2).
+- a quadratic (unit pixel scale, pure shift) gives the lit-pixel centroid
+  law exactly;
+- a low-frequency influence function converges to the continuous boundary
+  integral, and agrees with the numerical-derivative oracle on interior
+  subapertures to O((k dw / sigma)^2).
 """
 from __future__ import annotations
 

@@ -5,7 +5,7 @@
 //          derivative stencils (host), allocates the per-pair state maps.
 // compute: builds the composite affine of every pair (Sec. 2.1, FP64 host),
 //          copies the small per-pair block to the device and runs
-//          pixel classes -> persistent IM kernel, replayed from a CUDA graph.
+//          pixel classes -> the IM kernel, replayed from a CUDA graph.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -149,7 +149,10 @@ bool build_wfs_tables(const synim_wfs_desc &d, WfsTables &t, std::string &why) {
         const double c = (M - 1) * 0.5, ro = M * 0.5, ri = d.obstruction * M * 0.5;
         for (int i = 0; i < M; ++i)
             for (int j = 0; j < M; ++j) {
-                const double r = std::hypot(j - c, i - c);
+                // exact squares and sum of half-integer offsets, correctly
+                // rounded sqrt: the no-allocation path gives the same mask
+                const double dx = (double)j - c, dy = (double)i - c;
+                const double r = std::sqrt(dx * dx + dy * dy);
                 P[(size_t)i * M + j] = (r <= ro && r >= ri) ? 1 : 0;
             }
     }
@@ -622,7 +625,6 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
     e = dev_alloc(c, &c->d_pst, (size_t)tot);
     if (e == cudaSuccess) e = dev_alloc(c, &c->d_lines, (size_t)tot_lines);
     if (e == cudaSuccess) e = dev_alloc(c, &c->d_pairs, (size_t)np);
-    if (e == cudaSuccess) e = dev_alloc(c, &c->d_counter, 1);
     if (e == cudaSuccess) e = dev_alloc(c, &c->d_err, 1);
     if (e == cudaSuccess) e = dev_alloc(c, &c->d_gp, (size_t)np * 4);
     if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
@@ -664,6 +666,8 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
     }
     c->geo.order_start[n_dm] = acc;
     c->geo.n_items = acc;
+    if ((e = dev_alloc(c, &c->d_vjp_part, (size_t)acc * n_wfs * 4)) != cudaSuccess)
+        return bail(cuda_fail(c, e, "adjoint partials"));
     c->geo.n_dm = n_dm;
     c->geo.n_wfs = n_wfs;
     *out = c;
@@ -907,10 +911,10 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
                 if ((e = im_prepare(mode, th, smem, &b2)) != cudaSuccess || b2 < 1) continue;
                 const int gr = grid_for(th);
                 float ms = 0.f;
-                e = launch_im(mode, gt, c->d_pairs, c->d_counter, c->d_err, c->d_gp, gr, th, smem, s);
+                e = launch_im(mode, gt, c->d_pairs, c->d_err, c->d_vjp_part, gr, th, smem, s);
                 if (e == cudaSuccess) e = cudaEventRecord(t0, s);
                 for (int r = 0; r < 3 && e == cudaSuccess; ++r)
-                    e = launch_im(mode, gt, c->d_pairs, c->d_counter, c->d_err, c->d_gp, gr, th, smem, s);
+                    e = launch_im(mode, gt, c->d_pairs, c->d_err, c->d_vjp_part, gr, th, smem, s);
                 if (e == cudaSuccess) e = cudaEventRecord(t1, s);
                 if (e == cudaSuccess) e = cudaEventSynchronize(t1);
                 if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
@@ -933,8 +937,6 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
         if ((e = im_prepare(mode, threads, smem, &bps)) != cudaSuccess) return cuda_fail(c, e, "kernel attributes");
         grid = grid_for(threads);
     }
-    if (mode == MODE_VJP && (e = cudaMemsetAsync(c->d_gp, 0, sizeof(double) * np * 4, s)) != cudaSuccess)
-        return cuda_fail(c, e, "vjp clear");
     // profiling: pick the event pair of this launch (collect the oldest if the ring is full)
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
     if (c->profile) {
@@ -963,10 +965,10 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
             if (r == cudaSuccess && b0) r = cudaEventRecordWithFlags(b0, q, rf);
             return r;
         }
-        cudaError_t r = cudaMemsetAsync(c->d_counter, 0, sizeof(int), q);
-        if (r == cudaSuccess) r = launch_pst(g, c->d_pairs, c->max_mm, c->max_lines, q);
+        cudaError_t r = launch_pst(g, c->d_pairs, c->max_mm, c->max_lines, q);
         if (r == cudaSuccess && a0) r = cudaEventRecordWithFlags(a0, q, rf);
-        if (r == cudaSuccess) r = launch_im(mode, g, c->d_pairs, c->d_counter, c->d_err, c->d_gp, grid, threads, smem, q);
+        if (r == cudaSuccess) r = launch_im(mode, g, c->d_pairs, c->d_err, c->d_vjp_part, grid, threads, smem, q);
+        if (r == cudaSuccess && mode == MODE_VJP) r = launch_vjp_reduce(g, c->d_vjp_part, c->d_gp, q);
         if (r == cudaSuccess && b0) r = cudaEventRecordWithFlags(b0, q, rf);
         return r;
     };

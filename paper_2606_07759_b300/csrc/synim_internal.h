@@ -136,8 +136,11 @@ cudaError_t launch_mcls(const uint8_t *mask, int N, uint8_t *mcls, cudaStream_t 
 cudaError_t launch_pst(const Geo &g, const DevPair *pairs, int max_mm, int max_lines, cudaStream_t s);
 size_t im_smem_bytes(const Geo &g);
 cudaError_t im_prepare(int mode, int threads, size_t smem, int *blocks_per_sm);
-cudaError_t launch_im(int mode, const Geo &g, const DevPair *pairs, int *counter, int *err,
-                      double *gp, int grid, int threads, size_t smem, cudaStream_t s);
+// gp: MODE_VJP only, the per-column partials [n_items * n_wfs][4] that
+// launch_vjp_reduce sums per pair into grad_p [n_pairs][4].
+cudaError_t launch_im(int mode, const Geo &g, const DevPair *pairs, int *err, double *gp, int grid, int threads,
+                      size_t smem, cudaStream_t s);
+cudaError_t launch_vjp_reduce(const Geo &g, const double *part, double *gp, cudaStream_t s);
 // The telescoping-sum IM kernel: one warp per (actuator, sensor) column, a
 // per-warp buffer of cap4 float4 subaperture sums (a chunk of box rows and
 // the row above it; cap4 >= 2 n_sub).
@@ -189,8 +192,9 @@ struct synim_ctx {
     cudaEvent_t slot_ev[synim::NSLOT] = {};
     bool slot_used[synim::NSLOT] = {};
     int slot = 0;
-    int *d_counter = nullptr, *d_err = nullptr, *h_err = nullptr;
-    double *d_gp = nullptr;
+    int *d_err = nullptr, *h_err = nullptr;
+    double *d_gp = nullptr;     // grad_p [n_pairs][4] of the adjoint
+    double *d_vjp_part = nullptr;   // per-column adjoint partials [n_items * n_wfs][4]
     long long pst_off[SYNIM_MAX_PAIRS] = {};
     long long line_off[SYNIM_MAX_PAIRS] = {};
     uint8_t *d_pst = nullptr, *d_lines = nullptr;

@@ -683,7 +683,7 @@ __device__ __forceinline__ void warp_segments(const DevWFS &WF, const ItemWfs &s
 // slope_scale / (2 dw lit)) and their stores; or the cotangent dot products.
 template <int MODE, int NV>
 __device__ __forceinline__ void warp_column(const Geo &g, const DevPair *__restrict__ pairs, int d, int a, int w,
-                                            float *wbuf, int cap, int lane, int *err, double *gp) {
+                                            float *wbuf, int cap, int lane, int *err, double *gp, long unit) {
     const int pidx = d * g.n_wfs + w;
     const DevPair &P = pairs[pidx];
     if (!pair_active<MODE>(P)) return;
@@ -837,7 +837,9 @@ __device__ __forceinline__ void warp_column(const Geo &g, const DevPair *__restr
         for (int k2 = 0; k2 < 4; ++k2) {
             float vsum = gacc[k2];
             for (int o = 16; o > 0; o >>= 1) vsum += __shfl_xor_sync(0xffffffffu, vsum, o);
-            if (lane == 0 && vsum != 0.f) atomicAdd(&gp[pidx * 4 + k2], (double)vsum);
+            // this column's own slot (the caller zeroed it): summed per pair
+            // in a fixed order by k_vjp_reduce, so the result is reproducible
+            if (lane == 0) gp[4 * unit + k2] = (double)vsum;
         }
     }
 }
@@ -849,11 +851,10 @@ __device__ __forceinline__ void warp_column(const Geo &g, const DevPair *__restr
 // read before the CTA exits.
 template <int MODE>
 __global__ void __launch_bounds__(256, (MODE == MODE_FWD) ? 4 : 2)
-k_im(const __grid_constant__ Geo g, const DevPair *__restrict__ pairs, int *__restrict__ counter,
-     int *__restrict__ err, double *__restrict__ gp) {
+k_im(const __grid_constant__ Geo g, const DevPair *__restrict__ pairs, int *__restrict__ err,
+     double *__restrict__ gp) {
     constexpr int NV = (MODE == MODE_FWD) ? 1 : 5;
     extern __shared__ __align__(16) float smem_f[];
-    (void)counter;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     float *wbuf = smem_f + (size_t)warp * g.seg_floats;
     if constexpr (MODE != MODE_VJP) {
@@ -866,7 +867,8 @@ k_im(const __grid_constant__ Geo g, const DevPair *__restrict__ pairs, int *__re
         const int item = (int)(u / g.n_wfs), w = (int)(u - (long)item * g.n_wfs);
         int d, a;
         decode_item(g, item, d, a);
-        warp_column<MODE, NV>(g, pairs, d, a, w, wbuf, g.seg_floats, lane, err, gp);
+        if (MODE == MODE_VJP && lane < 4) gp[4 * u + lane] = 0.0;   // columns that return early add nothing
+        warp_column<MODE, NV>(g, pairs, d, a, w, wbuf, g.seg_floats, lane, err, gp, u);
     }
     // the zero buffer must outlive the bulk copies that read it
     if (MODE != MODE_VJP && lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
@@ -1055,12 +1057,48 @@ cudaError_t im_prepare(int mode, int threads, size_t smem, int *bps) {
     }
 }
 
-cudaError_t launch_im(int mode, const Geo &g, const DevPair *pairs, int *counter, int *err,
-                      double *gp, int grid, int threads, size_t smem, cudaStream_t s) {
+// Adjoint: grad_p[pair][k] = sum over the pair's actuators of the per-column
+// partials of k_im<MODE_VJP>, one block per pair, each thread a fixed
+// stride of actuators, then a fixed tree: the same order on every call.
+__global__ void __launch_bounds__(256)
+k_vjp_reduce(const __grid_constant__ Geo g, const double *__restrict__ part, double *__restrict__ gp) {
+    const int p = blockIdx.x;
+    const int d = p / g.n_wfs, w = p - d * g.n_wfs;
+    int pos = 0;
+    while (pos < g.n_dm && g.order_dm[pos] != d) ++pos;
+    __shared__ double red[4][256];
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    if (pos < g.n_dm) {
+        const long first = g.order_start[pos], n = g.order_start[pos + 1] - first;
+        for (long a = threadIdx.x; a < n; a += blockDim.x) {
+            const double *q = part + 4 * ((first + a) * g.n_wfs + w);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[k] += q[k];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) red[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) gp[4 * p + threadIdx.x] = red[threadIdx.x][0];
+}
+
+cudaError_t launch_vjp_reduce(const Geo &g, const double *part, double *gp, cudaStream_t s) {
+    k_vjp_reduce<<<g.n_dm * g.n_wfs, 256, 0, s>>>(g, part, gp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_im(int mode, const Geo &g, const DevPair *pairs, int *err, double *gp, int grid, int threads,
+                      size_t smem, cudaStream_t s) {
     switch (mode) {
-        case MODE_FWD: k_im<MODE_FWD><<<grid, threads, smem, s>>>(g, pairs, counter, err, gp); break;
-        case MODE_TAN: k_im<MODE_TAN><<<grid, threads, smem, s>>>(g, pairs, counter, err, gp); break;
-        default: k_im<MODE_VJP><<<grid, threads, smem, s>>>(g, pairs, counter, err, gp); break;
+        case MODE_FWD: k_im<MODE_FWD><<<grid, threads, smem, s>>>(g, pairs, err, gp); break;
+        case MODE_TAN: k_im<MODE_TAN><<<grid, threads, smem, s>>>(g, pairs, err, gp); break;
+        default: k_im<MODE_VJP><<<grid, threads, smem, s>>>(g, pairs, err, gp); break;
     }
     return cudaGetLastError();
 }

@@ -63,7 +63,7 @@ cudaError_t scratch_address(int dev, unsigned char **out) {
 size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 
 // Header words at the start of the scratch.
-enum { H_COUNTER = 0, H_ERR = 1, H_W = 2, H_NV = 3, H_NIRR = 4, H_WORDS = 64 };
+enum { H_RESERVED = 0, H_ERR = 1, H_W = 2, H_NV = 3, H_NIRR = 4, H_WORDS = 64 };
 
 struct Layout {
     size_t pair, box, org, dmmask, mcls, P, vin, lit, ros, vsub, vsj, fac, vrow, xcode, ycode, irrsr, irrsub,
@@ -109,8 +109,12 @@ __global__ void k_na_annulus(uint8_t *P, int M, double obstruction) {
     const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= (long)M * M) return;
     const int i = (int)(q / M), j = (int)(q - (long)i * M);
+    // the same FP64 expression as the context path: the squares of the
+    // half-integer offsets and their sum are exact, and sqrt is correctly
+    // rounded on host and device alike
     const double c = (M - 1) * 0.5, ro = M * 0.5, ri = obstruction * M * 0.5;
-    const double r = hypot((double)j - c, (double)i - c);
+    const double dx = (double)j - c, dy = (double)i - c;
+    const double r = sqrt(dx * dx + dy * dy);
     P[q] = (r <= ro && r >= ri) ? 1 : 0;
 }
 
@@ -393,6 +397,17 @@ extern "C" synim_status synim_im_compute_noalloc(const synim_dm_desc *dm, const 
     int4 *irrc = reinterpret_cast<int4 *>(ptr(L.irrc));
     int *irrcrow = reinterpret_cast<int *>(ptr(L.irrcrow));
     k_na_irr_cand<<<1, 32, 0, st>>>(irrsub, n, irrc, irrcrow);
+    int h[H_WORDS];
+    if (!im) {
+        // size query: the row count needs only the sensor tables
+        if ((e = cudaGetLastError()) != cudaSuccess ||
+            (e = cudaMemcpyAsync(h, hdr, sizeof(h), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess)
+            return na_fail(SYNIM_ERR_CUDA, cudaGetErrorString(e));
+        if (n_rows) *n_rows = 2LL * h[H_NV];
+        if (h[H_NV] == 0) return na_fail(SYNIM_ERR_SHAPE, "sensor has no valid subaperture");
+        return SYNIM_OK;
+    }
     uint8_t *mcls = ptr(L.mcls);
     if ((e = launch_mcls(dm->mask ? ptr(L.dmmask) : nullptr, N, mcls, st)) != cudaSuccess)
         return na_fail(SYNIM_ERR_CUDA, "mask interior map launch failed");
@@ -400,7 +415,6 @@ extern "C" synim_status synim_im_compute_noalloc(const synim_dm_desc *dm, const 
     if ((e = launch_support(dm->ifs, n_act, N, dm->support_eps, box, st)) != cudaSuccess)
         return na_fail(SYNIM_ERR_CUDA, "support scan launch failed");
     k_na_wmax<<<grid_for(n_act, 256), 256, 0, st>>>(box, n_act, hdr);
-    int h[H_WORDS];
     if ((e = cudaGetLastError()) != cudaSuccess ||
         (e = cudaMemcpyAsync(h, hdr, sizeof(h), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
         (e = cudaStreamSynchronize(st)) != cudaSuccess)
@@ -408,7 +422,6 @@ extern "C" synim_status synim_im_compute_noalloc(const synim_dm_desc *dm, const 
     const int nv = h[H_NV];
     if (n_rows) *n_rows = 2LL * nv;
     if (nv == 0) return na_fail(SYNIM_ERR_SHAPE, "sensor has no valid subaperture");
-    if (!im) return SYNIM_OK;  // size query only
     const int W = std::min(std::max(h[H_W], 1), N);
     int Wp = W + 2;
     if ((Wp & 1) == 0) ++Wp;
@@ -471,7 +484,7 @@ extern "C" synim_status synim_im_compute_noalloc(const synim_dm_desc *dm, const 
     const int grid = std::max(1, std::min(n_act, n_sm * bps));
     if ((e = cudaMemsetAsync(hdr, 0, 2 * sizeof(int), st)) != cudaSuccess ||
         (e = launch_pst(g, d_pair, M * M, M * (n + 1), st)) != cudaSuccess ||
-        (e = launch_im(MODE_FWD, g, d_pair, hdr + H_COUNTER, hdr + H_ERR, nullptr, grid, 256, smem, st)) != cudaSuccess)
+        (e = launch_im(MODE_FWD, g, d_pair, hdr + H_ERR, nullptr, grid, 256, smem, st)) != cudaSuccess)
         return na_fail(SYNIM_ERR_CUDA, cudaGetErrorString(e));
     int err_flag = 0;
     if ((e = cudaMemcpyAsync(&err_flag, hdr + H_ERR, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||

@@ -1,4 +1,4 @@
-// synim_projection.cu -- tomographic projection matrices and P_opt (Sec. 3,
+// synim_projection.cu -- tomographic projection matrices and P_opt (Sec. 2.5,
 // tomographic projection matrices).
 //
 // P_X[(j, q), a] is the mean over the bin x bin fine pixels p of binned pupil

@@ -193,7 +193,7 @@ class SynIM:
                   self._ctx)
         return np.array(gp[:]).reshape(np_, 4)
 
-    # ---- tomographic projection (Sec. 3) ----
+    # ---- tomographic projection (Sec. 2.5) ----
     def projection_rows(self, w: int, n_dir: int, bin: int) -> int:
         r = ctypes.c_int64()
         abi.check(self._L.synim_projection_rows(self._ctx, w, n_dir, bin, ctypes.byref(r)), self._ctx)
@@ -373,17 +373,18 @@ def cnn_init_params(n_channels: int, seed: int = 0, input_scale: float = 1.0, si
 class IMFunction(torch.autograd.Function):
     """IMs as a differentiable function of the misregistrations.
 
-    forward(params [n_pairs, 4] float64 CPU tensor, synim) -> tuple of IMs;
-    backward uses the library's adjoint kernel (synim_im_vjp).
+    forward(params [n_pairs, 4] tensor on any device, synim) -> tuple of IMs;
+    backward uses the library's adjoint kernel (synim_im_vjp) and returns the
+    parameter gradient on the device and with the dtype of ``params``.
     """
 
     @staticmethod
     def forward(ctx, params, synim):
         mis = params.detach().cpu().double().tolist()
-        ctx.synim, ctx.mis, ctx.pdtype = synim, mis, params.dtype
+        ctx.synim, ctx.mis, ctx.pdtype, ctx.pdevice = synim, mis, params.dtype, params.device
         return tuple(synim.compute(mis))
 
     @staticmethod
     def backward(ctx, *grads):
         gp = ctx.synim.vjp(ctx.mis, list(grads))
-        return torch.from_numpy(gp).to(ctx.pdtype), None
+        return torch.from_numpy(gp).to(device=ctx.pdevice, dtype=ctx.pdtype), None

@@ -375,12 +375,6 @@ def probe_modes(dm: DM, D_m: float, n_modes: int = 16) -> np.ndarray:
     return cmd
 
 
-def modal_screens(dm: DM, cmd: np.ndarray) -> np.ndarray:
-    """Sum_a cmd[m, a] * IF_a for every probe m: FP32 [n_modes, N, N]."""
-    flat = dm.ifs.reshape(dm.n_act, -1).astype(np.float64)
-    return (cmd @ flat).reshape(cmd.shape[0], dm.grid_n, dm.grid_n).astype(np.float32)
-
-
 def learned(seed: int = 5):
     """40x40 SH (k = 8, M = 320, no obstruction), 41x41 DM (p = 8 px), 16 probes.
 

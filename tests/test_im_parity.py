@@ -11,8 +11,21 @@ column whose net slopes cancel to below 1 % of the IM peak (an actuator well
 inside a 2x2 NGS subaperture, or barely reaching the sensor) is therefore
 compared at an absolute 1e-7 of the IM peak; every other column at 1e-5 of
 its own peak.  The 1e-9 support-window truncation moves slopes by ~1e-8 of
-the IM peak at most, inside the same bound.
+the IM peak at most, inside the same bound: columns whose oracle peak lies
+below that level (IFs that barely reach the sensor) are exactly zero on the
+GPU by the definition of the support window.
+
+Every workload reports (a ParityReport warning, listed in pytest's warnings
+summary) how many columns the floor holds, their worst error relative to
+their own peak and to the IM peak, and the worst own-peak error of the other
+columns, which the spec criterion (1e-5 of the column's peak) covers.
+
+Structure: every entry the oracle puts above twice its column's error bound
+is non-zero on the GPU (the GPU's support boxes miss no significant row);
+shapes and row order are those of the oracle (row by row comparison).
 """
+import warnings
+
 import numpy as np
 import pytest
 import torch
@@ -25,6 +38,20 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-5
 
 
+class ParityReport(UserWarning):
+    """Per-workload parity summary (shown in pytest's warnings summary)."""
+
+
+def report(what, stats):
+    """Warn with: columns checked, columns held by the floor, their worst
+    error relative to their own peak and to the IM peak, and the worst
+    strict (own-peak) error of the other columns."""
+    warnings.warn(ParityReport(
+        f"{what}: {stats['cols']} columns, {stats['floor']} under the 1e-2 floor "
+        f"(worst error {stats['floor_rel']:.2e} of their own peak, {stats['floor_abs']:.2e} of the IM peak); "
+        f"other columns worst {stats['strict']:.2e} of their own peak"))
+
+
 def gpu_ims(wl, misregs=None, **kw):
     from paper_2606_07759_b300.synim import SynIM
     s = SynIM(wl.dms, wl.wfss, **kw)
@@ -35,14 +62,30 @@ def gpu_ims(wl, misregs=None, **kw):
     return res
 
 
-def assert_columns(gpu, ref, tol=TOL, what="", floor_rel=1e-2):
+def assert_columns(gpu, ref, tol=TOL, what="", floor_rel=1e-2, stats=None):
     assert gpu.shape == ref.shape, (what, gpu.shape, ref.shape)
-    floor = floor_rel * max(np.abs(ref).max(), 1e-30)
-    peak = np.maximum(np.abs(ref).max(axis=1), floor)
-    err = np.abs(gpu.astype(np.float64) - ref).max(axis=1)
+    impeak = max(np.abs(ref).max(), 1e-30)
+    floor = floor_rel * impeak
+    cpeak = np.abs(ref).max(axis=1)
+    peak = np.maximum(cpeak, floor)
+    g64 = gpu.astype(np.float64)
+    err = np.abs(g64 - ref).max(axis=1)
     bad = np.nonzero(err > tol * peak)[0]
     assert bad.size == 0, (f"{what}: {bad.size} columns fail, worst rel {np.max(err / peak):.3e} at col "
                            f"{bad[:5]}, column peaks / IM peak {np.abs(ref[bad[:5]]).max(axis=1) / floor * floor_rel}")
+    # structure: every row the oracle puts above the error bound of its
+    # column is computed (non-zero) on the GPU, and the GPU's exact zeros
+    # sit where the oracle is inside the bound
+    sig = np.abs(ref) > 2.0 * tol * peak[:, None]
+    assert np.all(g64[sig] != 0.0), f"{what}: {int((g64[sig] == 0).sum())} significant entries are zero on the GPU"
+    if stats is not None:
+        under = cpeak < floor
+        own = err / np.maximum(cpeak, 1e-300)
+        stats["cols"] = stats.get("cols", 0) + len(cpeak)
+        stats["floor"] = stats.get("floor", 0) + int(under.sum())
+        stats["floor_rel"] = max(stats.get("floor_rel", 0.0), float(own[under].max()) if under.any() else 0.0)
+        stats["floor_abs"] = max(stats.get("floor_abs", 0.0), float(err[under].max() / impeak) if under.any() else 0.0)
+        stats["strict"] = max(stats.get("strict", 0.0), float(own[~under].max()) if (~under).any() else 0.0)
     return float(np.max(err / peak))
 
 
@@ -50,6 +93,7 @@ def check_workload(wl, cols_per_dm=None, misregs=None, seed=0, floor_rel=1e-2, *
     ims = gpu_ims(wl, misregs, **kw)
     rng = np.random.default_rng(seed)
     worst = 0.0
+    stats = {}
     for d, dm in enumerate(wl.dms):
         if cols_per_dm is None or cols_per_dm >= dm.n_act:
             cols = np.arange(dm.n_act)
@@ -61,7 +105,8 @@ def check_workload(wl, cols_per_dm=None, misregs=None, seed=0, floor_rel=1e-2, *
             mis = (misregs[p] if misregs is not None else wl.misregs[p])
             ref = oracle.pair_im(wl, d, w, cols=cols, misreg=mis)
             worst = max(worst, assert_columns(ims[p][cols], ref, what=f"{wl.name} dm{d} wfs{w}",
-                                              floor_rel=floor_rel))
+                                              floor_rel=floor_rel, stats=stats))
+    report(wl.name, stats)
     return worst
 
 

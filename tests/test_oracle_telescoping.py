@@ -6,7 +6,11 @@
   rotation).
 - A wide Gaussian: the edge sums converge to the boundary integral of the
   continuous phase over each subaperture (evaluated with Gauss-Legendre),
-  the same limit as the numerical-derivative engine.
+  the same limit as the numerical-derivative engine, and agree with that
+  engine's oracle on interior subapertures.
+- A quadratic phase x^2 at unit pixel scale under a pure shift: the x slope
+  is twice the lit-pixel centroid over dw (bilinear's error is the same
+  constant at every run end and cancels).
 """
 import numpy as np
 
@@ -67,3 +71,53 @@ def test_low_frequency_matches_the_continuous_boundary_integral():
             r = ros[si, sj]
             assert abs(out[r] - ex) < 2e-3 * peak
             assert abs(out[nv + r] - ey) < 2e-3 * peak
+
+
+def test_quadratic_gives_the_lit_centroid_law():
+    # phi = x^2 (DM pixel units), sensor pixel = DM pixel, pure shift: every
+    # run end has the same fractional position, so bilinear's error
+    # f (1 - f) is one constant that cancels between a run's two ends, and
+    # the x slope is 2 * mean over the lit pixels of x / dw exactly (the y
+    # slope vanishes)
+    N, M, n, dd = 96, 48, 6, 0.05
+    yy, xx = np.mgrid[0:N, 0:N].astype(np.float64)
+    quad = (xx ** 2)[None]
+    P = W.disc_mask(M, M / 2.0, 0.3 * M / 2.0)
+    mis = W.Misreg(0.37, -0.21, 0.0, 1.0)
+    wl = _setup(quad, P, mis, N=N, dd=dd, M=M, n=n, D=M * dd)
+    out = TS.im(wl, 0, 0)[0]
+    A, b = oracle.composite(oracle.pair_geom(wl.dms[0], wl.wfss[0]), mis.as_tuple())
+    assert abs(A[0] - 1.0) < 1e-12 and abs(A[1]) < 1e-12
+    ros, lit, nv = oracle.valid_subaps(P, n)
+    k, dw = M // n, dd
+    for si in range(n):
+        for sj in range(n):
+            r = ros[si, sj]
+            if r < 0:
+                continue
+            ii, jj = np.nonzero(P[si * k:(si + 1) * k, sj * k:(sj + 1) * k])
+            xbar = np.mean(A[0] * (jj + sj * k) + b[0])
+            np.testing.assert_allclose(out[r], 2.0 * xbar / dw, rtol=1e-11)
+            assert abs(out[nv + r]) <= 1e-9 * abs(out[r]) + 1e-9
+
+
+def test_low_frequency_matches_the_numerical_derivative_oracle():
+    # both engines approximate the same boundary integral: for a wide IF
+    # (sigma = 4 subapertures) they agree to O((k dw / sigma)^2) of the peak
+    # on interior subapertures (on the outermost ring the central difference
+    # reads phi = 0 beyond the grid edge, the run-end sums do not)
+    N, dd, M, n, D = 96, 0.05, 48, 6, 3.6
+    k, dw = M // n, D / M
+    s = 4 * k * dw
+    cN = (N - 1) / 2
+    yy, xx = np.mgrid[0:N, 0:N].astype(np.float64)
+    X, Y = (xx - cN) * dd, (yy - cN) * dd
+    f = np.exp(-((X - 0.3) ** 2 + (Y + 0.2) ** 2) / (2 * s * s))[None]
+    P = np.ones((M, M), np.uint8)
+    wl = _setup(f, P, W.Misreg(0.3, -0.45, 0.4, 1.002))
+    tele = TS.im(wl, 0, 0)[0]
+    num = oracle.pair_im(wl, 0, 0)[0]
+    ros, lit, nv = oracle.valid_subaps(P, n)
+    inner = np.array([ros[si, sj] for si in range(1, n - 1) for sj in range(1, n - 1)])
+    rows = np.concatenate([inner, nv + inner])
+    assert np.abs(tele[rows] - num[rows]).max() <= 2e-3 * np.abs(num).max()

@@ -7,8 +7,9 @@ Criteria:
     coordinates and bilinear resample against FP64, as the IM columns);
   - P_opt at lambda = 1e-2 x mean diag(P_DM^T P_DM) (condition number ~2e3):
     max |P_opt_gpu - P_opt_ref| <= 1e-3 x max |P_opt_ref|.  The normal
-    matrix is formed with FP32-accurate GEMMs and factored in FP32, so the
-    solution carries ~cond x 1e-7 relative error;
+    matrices come from box-sparse products (each column is non-zero only on
+    its actuator's footprint box per direction) and the system is factored
+    in FP32, so the solution carries ~cond x 1e-7 relative error;
   - the projection of a component onto itself at a vanishing lambda is the
     identity;
   - lambda = 0 with a component that no direction sees (zero columns) is

@@ -110,6 +110,12 @@ def test_tangents_mcao_reduced():
     check_tangents(W.mcao_batched(seed=9, scale=0.15), cols_per_dm=40)
 
 
+def test_tangents_elt_single_full_size_sampled_columns():
+    # the ELT-scale sensitivity workload (81 x 81 DM on 480 px, 68 x 68 SH) at
+    # its full size, sampled columns against the oracle's analytic tangents
+    check_tangents(W.elt_single(seed=4), cols_per_dm=16, seed=4)
+
+
 def test_tangents_match_oracle_central_differences():
     # GPU tangents against central differences of the FP64 oracle forward,
     # steps (1e-3 px, 1e-3 px, 1e-3 deg, 1e-5), on kink-free rows
@@ -149,6 +155,9 @@ def test_vjp_is_the_adjoint_of_the_tangents():
     grads[3] = None  # zero cotangent for one pair
     gp = s.vjp(wl.misregs, grads)
     s.check()
+    # per-column partials summed in a fixed order: a second call is bit-identical
+    gp2 = s.vjp(wl.misregs, grads)
+    assert np.array_equal(gp, gp2)
     for p in range(len(ims)):
         for k in range(4):
             if grads[p] is None:
@@ -175,4 +184,16 @@ def test_autograd_function_backward_uses_the_adjoint():
     ref = np.array([(w_np * T[k]).sum() for k in range(4)])
     mag = np.array([(np.abs(w_np) * np.abs(T[k])).sum() for k in range(4)])
     np.testing.assert_array_less(np.abs(params.grad.numpy()[0] - ref), 1e-4 * mag)
+    s.close()
+
+
+def test_autograd_gradient_follows_the_parameter_device():
+    from paper_2606_07759_b300.synim import SynIM, IMFunction
+    wl = W.scao_small()
+    s = SynIM(wl.dms, wl.wfss)
+    params = torch.tensor([wl.misregs[0].as_tuple()], dtype=torch.float32, device="cuda", requires_grad=True)
+    (im,) = IMFunction.apply(params, s)
+    im.sum().backward()
+    assert params.grad.device == params.device and params.grad.dtype == params.dtype
+    assert torch.isfinite(params.grad).all()
     s.close()

@@ -28,7 +28,7 @@ TOL, FLOOR = 1e-5, 1e-2  # same criterion as the parity tests
 
 def _descs(dm, wfs, ifs_dev, keep):
     mask = None if dm.mask is None else np.ascontiguousarray(dm.mask, np.uint8)
-    pm = np.ascontiguousarray(wfs.pupil_mask, np.uint8)
+    pm = None if wfs.pupil_mask is None else np.ascontiguousarray(wfs.pupil_mask, np.uint8)
     keep += [mask, pm]
     d = abi.synim_dm_desc(dm.n_act, dm.grid_n, dm.pixel_pitch_m, dm.altitude_m, ifs_dev.data_ptr(), 1,
                           None if mask is None else mask.ctypes.data, dm.support_eps)
@@ -37,7 +37,7 @@ def _descs(dm, wfs, ifs_dev, keep):
     w.field_rad[0], w.field_rad[1] = wfs.field_rad
     w.rot_deg, w.mag[0], w.mag[1] = wfs.rot_deg, wfs.mag[0], wfs.mag[1]
     w.shift_m[0], w.shift_m[1] = wfs.shift_m
-    w.pupil_mask, w.subap_valid = pm.ctypes.data, None
+    w.pupil_mask, w.subap_valid = (None if pm is None else pm.ctypes.data), None
     w.obstruction, w.slope_scale = wfs.obstruction, wfs.slope_scale
     return d, w
 
@@ -58,12 +58,18 @@ def _assert_close(got, ref, what):
     assert np.all(err <= TOL * peak), f"{what}: worst rel {np.max(err / peak):.3e}"
 
 
-@pytest.mark.parametrize("name", ["scao_small", "elt_reduced", "mcao_reduced_ngs"])
+@pytest.mark.parametrize("name", ["scao_small", "scao_default_pupil", "elt_reduced", "mcao_reduced_ngs"])
 def test_noalloc_matches_context_path_on_two_calls(name):
+    import dataclasses
     from paper_2606_07759_b300.synim import SynIM
     L = abi.load()
     if name == "scao_small":
         wl = W.scao_small()
+        d_i, w_i = 0, 0
+    elif name == "scao_default_pupil":
+        # no pupil mask: both paths build the default annulus themselves
+        wl = W.scao_small()
+        wl.wfss[0] = dataclasses.replace(wl.wfss[0], pupil_mask=None, obstruction=0.2)
         d_i, w_i = 0, 0
     elif name == "elt_reduced":
         wl = W.elt_single(seed=7, n_side=21, grid_n=120, n_sub=17)
