@@ -231,13 +231,43 @@ synim_status synim_projection_matrix(synim_ctx *ctx, int32_t wfs, int32_t n_dir,
  * holds the DM commands of layer mode l).  Stores both projection matrices
  * box by box in device scratch (each column is non-zero only on its footprint
  * box per direction), forms P_DM^T P_DM and P_DM^T P_Layer from the box
- * intersections (FP32), factors by Cholesky and solves with two triangular
- * solves.
+ * intersections (FP32), factors by a blocked Cholesky and solves with two
+ * block triangular sweeps, every block update a tensor-core GEMM with
+ * FP32-level accuracy (synim_linalg_gemm).
  * Synchronises the stream before returning.  SYNIM_ERR_NOT_CONVERGED if the
  * normal matrix is not positive definite. */
 synim_status synim_projection_opt(synim_ctx *ctx, int32_t wfs, int32_t n_dir, const double *dirs_rad, int32_t bin,
                                   int32_t n_dm, const int32_t *dms, int32_t n_layer, const int32_t *layers,
                                   double lambda, float *p_opt, void *cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Dense linear algebra of the tomographic operators (Sec. 2.4, Sec. 2.5)
+ *
+ * The projection P_opt and the MMSE reconstructor are dense contractions and
+ * symmetric positive definite solves.  The library runs them on the tensor
+ * cores (tcgen05, TF32 inputs) with every operand split into a TF32 part and
+ * its FP32 remainder and three products accumulated in FP32 (hi.hi + hi.lo +
+ * lo.hi), about 2^-21 relative error per product: FP32-level accuracy.
+ * Matrices are row-major FP32 device arrays with a leading dimension (in
+ * elements).  These calls need no context; errors are reported through
+ * synim_last_error(NULL).  They enqueue on cuda_stream and synchronise it
+ * before returning.
+ * ---------------------------------------------------------------------- */
+
+/* C = beta C + alpha A B.  A is M x K (lda); B is N x K (b_kn = 0: element
+ * (k, n) at B[n ldb + k]) or K x N (b_kn = 1: B[k ldb + n]); C is M x N (ldc).
+ * M, N, K >= 0.  SYNIM_ERR_TIMEOUT if a bounded tensor-core wait gave up. */
+synim_status synim_linalg_gemm(int32_t M, int32_t N, int32_t K, float alpha, const float *A, int64_t lda,
+                               const float *B, int64_t ldb, int32_t b_kn, float beta, float *C, int64_t ldc,
+                               void *cuda_stream);
+
+/* Y <- Y S^-1 for a symmetric positive definite S (n x n, lds): S is
+ * overwritten by its Cholesky factor L (lower triangle, S = L L^T, blocked
+ * right-looking, 128-row blocks); Y is m x n (ldy).  Allocates its scratch
+ * (the factor's diagonal-block inverses and one panel).  SYNIM_ERR_NOT_CONVERGED
+ * if S is not positive definite. */
+synim_status synim_linalg_spd_solve(float *S, int32_t n, int64_t lds, float *Y, int32_t m, int64_t ldy,
+                                    void *cuda_stream);
 
 /*
  * Self-test of the bounded device waits (the mbarrier waits of the

@@ -77,6 +77,9 @@ SIGNATURES = {
                                        ctypes.POINTER(c_int32), c_int32, ctypes.POINTER(c_int32), c_double, c_void_p,
                                        c_void_p]),
     "synim_dm_window": (c_int32, [c_void_p, c_int32, ctypes.POINTER(c_int32)]),
+    "synim_linalg_gemm": (c_int32, [c_int32, c_int32, c_int32, c_float, c_void_p, c_int64, c_void_p, c_int64,
+                                    c_int32, c_float, c_void_p, c_int64, c_void_p]),
+    "synim_linalg_spd_solve": (c_int32, [c_void_p, c_int32, c_int64, c_void_p, c_int32, c_int64, c_void_p]),
     "synim_im_kernel_ms": (c_int32, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int32)]),
     "synim_im_compute_noalloc": (c_int32, [ctypes.POINTER(synim_dm_desc), ctypes.POINTER(synim_wfs_desc),
                                            ctypes.POINTER(synim_misreg), c_void_p, ctypes.POINTER(c_int64),

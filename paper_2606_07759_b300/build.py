@@ -24,7 +24,6 @@ NVCC_FLAGS = [
     "-Xcompiler", "-fPIC", "-shared",
     "--cudart", "shared",
     "-Xlinker", "-rpath,/usr/local/cuda/lib64",
-    "-lcublas", "-lcusolver",
 ]
 
 

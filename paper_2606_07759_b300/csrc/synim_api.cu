@@ -86,6 +86,7 @@ cudaError_t dev_upload(synim_ctx *c, T **p, const std::vector<T> &v) {
 namespace synim {
 
 void clear_create_error() { g_create_error.clear(); }
+void set_global_error(const std::string &m) { g_create_error = m; }
 
 int ctx_valid_rows(const synim_ctx *ctx, int w, const int **vsub, int *n_sub) {
     *vsub = ctx->geo.wfs[w].vsub;
@@ -406,7 +407,6 @@ void synim_im_destroy(synim_ctx *ctx) {
     for (int s = 0; s < NSLOT; ++s)
         if (ctx->slot_ev[s]) cudaEventDestroy(ctx->slot_ev[s]);
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
-    projection_destroy(ctx);
     cnn_destroy(ctx->cnn);
     est_destroy(ctx->est);
     probe_destroy(ctx->probe);

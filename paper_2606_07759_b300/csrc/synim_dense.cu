@@ -1,0 +1,457 @@
+// synim_dense.cu -- FP32-accurate dense linear algebra on the 5th-generation
+// tensor cores, for the tomographic operators (Sec. 2.4 MMSE reconstructor,
+// Sec. 2.5 P_opt = (P_DM^T P_DM + lambda I)^-1 P_DM^T P_Layer).
+//
+// k_gemm3     C = beta C + alpha op(A) op(B) on tcgen05.mma .kind::tf32 with
+//             split operands: x = hi + lo, hi = x with its low 13 mantissa
+//             bits cleared (what the tensor core reads of x), lo = x - hi
+//             (exact in FP32).  C accumulates hi.hi + hi.lo + lo.hi in FP32
+//             TMEM (the lo.lo term is below FP32 rounding), so a product
+//             carries ~2^-21 relative error, against 2^-11 for one TF32 pass.
+// k_potrf_diag  unblocked Cholesky of one diagonal block and the inverse of
+//             its factor (one CTA, shared memory);
+// blocked     right-looking Cholesky S = L L^T whose panel and trailing
+//             updates are k_gemm3 calls, and the solve Y <- Y S^-1 as two
+//             block triangular sweeps whose updates are k_gemm3 calls.
+//
+// All matrices are row-major FP32 with a leading dimension.  GEMM operands:
+// A(m, k) = A[m lda + k]; B(k, n) = B[n ldb + k] ("N x K", K contiguous) or
+// B[k ldb + n] ("K x N", N contiguous); both are staged into shared memory
+// as K-major core-matrix tiles, so the tensor core always reads one layout.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "synim_internal.h"
+#include "synim_tc.cuh"
+
+namespace synim {
+
+namespace {
+
+constexpr int kGBM = 128;   // tile rows (TMEM lanes)
+constexpr int kGBN = 128;   // tile columns (TMEM columns)
+constexpr int kGBK = 32;    // K chunk (floats): 8 core matrices of 16 bytes
+constexpr int kGThreads = 128;
+constexpr int kTileBytes = kGBM * kGBK * 4;            // one operand tile, one part (16 KB)
+constexpr int kStageBytes = 4 * kTileBytes;            // A hi, A lo, B hi, B lo
+constexpr int kGemmSmem = 2 * kStageBytes + 2048;      // two stages, barriers, 1024-byte alignment slack
+
+// Instruction descriptor of tcgen05.mma .kind::tf32: D F32, A and B TF32,
+// both K-major, shape M x N.
+__host__ __device__ __forceinline__ uint32_t idesc_tf32(int M, int N) {
+    return (1u << 4)                     // D format F32
+           | (2u << 7)                   // A format TF32
+           | (2u << 10)                  // B format TF32
+           | ((uint32_t)(N >> 3) << 17)  // N / 8
+           | ((uint32_t)(M >> 4) << 24); // M / 16
+}
+
+__device__ __forceinline__ void tc_mma_tf32(uint32_t taddr, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(taddr),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Byte offset of element (r, k) of a 128 x 32 K-major tile: 8-row groups
+// 1024 bytes apart (SBO), core matrices along K 128 bytes apart (LBO), rows
+// of a core matrix 16 bytes apart.
+__device__ __forceinline__ uint32_t tile_off(int r, int k) {
+    return (uint32_t)((r >> 3) * 1024 + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4);
+}
+
+__device__ __forceinline__ void split_store(uint8_t *hi, uint8_t *lo, uint32_t off, float x) {
+    const float h = __uint_as_float(__float_as_uint(x) & 0xffffe000u);
+    *reinterpret_cast<float *>(hi + off) = h;
+    *reinterpret_cast<float *>(lo + off) = x - h;
+}
+
+struct GemmArgs {
+    const float *A, *B;
+    float *C;
+    long lda, ldb, ldc;
+    int M, N, K;
+    float alpha, beta;
+    int b_kn;    // 0: B(k, n) = B[n ldb + k]; 1: B(k, n) = B[k ldb + n]
+    int lower;   // 1: only tiles that touch the lower triangle (n <= m) of C
+};
+
+// Stage the K chunk k0 of one operand tile (rows r0.., 128 rows) into its
+// hi / lo tiles.  kcont: the operand's K index is contiguous in memory.
+__device__ __forceinline__ void stage_tile(const float *X, long ld, bool kcont, int rows, int r0, int K, int k0,
+                                           uint8_t *hi, uint8_t *lo) {
+    const int t = threadIdx.x;
+    if (kcont) {
+        // 128 rows x 32 floats: each thread loads one row in 8 float4s
+        const int r = t;
+        const long gr = r0 + r;
+        const float *src = X + gr * ld + k0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int k = q * 4;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (gr < rows) {
+                if (k0 + k + 3 < K && ((reinterpret_cast<uintptr_t>(src + k) & 15u) == 0)) {
+                    v = *reinterpret_cast<const float4 *>(src + k);
+                } else {
+                    v.x = (k0 + k + 0 < K) ? src[k + 0] : 0.f;
+                    v.y = (k0 + k + 1 < K) ? src[k + 1] : 0.f;
+                    v.z = (k0 + k + 2 < K) ? src[k + 2] : 0.f;
+                    v.w = (k0 + k + 3 < K) ? src[k + 3] : 0.f;
+                }
+            }
+            const uint32_t off = tile_off(r, k);
+            split_store(hi, lo, off, v.x);
+            split_store(hi, lo, off + 4, v.y);
+            split_store(hi, lo, off + 8, v.z);
+            split_store(hi, lo, off + 12, v.w);
+        }
+    } else {
+        // the row index is contiguous: each pass reads 128 consecutive rows at
+        // one k; all 32 loads are issued before the first store
+        float v[kGBK];
+        const long gr = r0 + t;
+#pragma unroll
+        for (int k = 0; k < kGBK; ++k) {
+            const long gk = k0 + k;
+            v[k] = (gk < K && gr < rows) ? X[gk * ld + gr] : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < kGBK; ++k) split_store(hi, lo, tile_off(t, k), v[k]);
+    }
+}
+
+// One 128 x 128 tile of C per CTA.  All threads stage K chunks (double
+// buffered); thread 0 issues the three split products of each chunk into one
+// TMEM accumulator and commits to the chunk's mbarrier; the four warps then
+// read their 32 TMEM lanes (rows) back and update C.  Waits are bounded: a
+// wait that gives up sets *err and the CTA stops issuing work.
+__global__ void __launch_bounds__(kGThreads, 1) k_gemm3(const GemmArgs g, int *err) {
+    extern __shared__ __align__(1024) uint8_t gsm[];
+    const int bm = blockIdx.y, bn = blockIdx.x;
+    const int m0 = bm * kGBM, n0 = bn * kGBN;
+    if (g.lower && n0 > m0 + kGBM - 1) return;   // tile wholly above the diagonal
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(gsm) + 1023) & ~uintptr_t(1023));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(base + 2 * kStageBytes);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        tc_mbar_init(tc_smem(&bars[0]), 1);
+        tc_mbar_init(tc_smem(&bars[1]), 1);
+        tc_fence_mbar_init();
+    }
+    if (warp == 0) tc_alloc(tc_smem(tslot), kGBN);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const int nch = (g.K + kGBK - 1) / kGBK;
+    const uint32_t idesc = idesc_tf32(kGBM, kGBN);
+    bool ok = true;
+    int committed = -1;   // last chunk whose MMAs were committed
+    for (int c = 0; c < nch; ++c) {
+        const int b = c & 1;
+        uint8_t *ah = base + b * kStageBytes, *al = ah + kTileBytes, *bh = al + kTileBytes, *bl = bh + kTileBytes;
+        if (c >= 2 && !tc_mbar_wait(tc_smem(&bars[b]), ((c - 2) >> 1) & 1)) ok = false;
+        if (!__syncthreads_and(ok)) break;
+        stage_tile(g.A, g.lda, true, g.M, m0, g.K, c * kGBK, ah, al);
+        stage_tile(g.B, g.ldb, g.b_kn == 0, g.N, n0, g.K, c * kGBK, bh, bl);
+        tc_fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t sah = tc_smem(ah), sal = tc_smem(al), sbh = tc_smem(bh), sbl = tc_smem(bl);
+#pragma unroll
+            for (int j = 0; j < kGBK / 8; ++j) {
+                const uint32_t o = (uint32_t)j * 256;
+                const uint64_t dah = tc_desc(sah + o, 128, 1024), dal = tc_desc(sal + o, 128, 1024);
+                const uint64_t dbh = tc_desc(sbh + o, 128, 1024), dbl = tc_desc(sbl + o, 128, 1024);
+                tc_mma_tf32(tmem, dah, dbh, idesc, (c | j) != 0);
+                tc_mma_tf32(tmem, dah, dbl, idesc, 1);
+                tc_mma_tf32(tmem, dal, dbh, idesc, 1);
+            }
+            tc_commit(tc_smem(&bars[b]));
+        }
+        committed = c;
+    }
+    // every issued MMA has completed before TMEM is read or freed (bounded)
+    if (committed >= 0 && !tc_mbar_wait(tc_smem(&bars[committed & 1]), (committed >> 1) & 1)) ok = false;
+    ok = __syncthreads_and(ok) != 0;
+    tc_fence_after();
+    if (!ok) {
+        if (tid == 0) atomicOr(err, ERR_TIMEOUT);
+    } else {
+        // epilogue: warp w owns TMEM lanes (rows) 32 w .. 32 w + 31.  Each
+        // 32-column slice goes through shared memory (the operand stages are
+        // free now) so that C is read and written a row at a time by a warp
+        // (coalesced), not a column at a time.
+        float *stile = reinterpret_cast<float *>(base);   // [128][33]
+#pragma unroll 1
+        for (int q = 0; q < kGBN / 32; ++q) {
+            float v[32];
+            tc_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(q * 32), v);
+            if (nch == 0)
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = 0.f;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) stile[(warp * 32 + lane) * 33 + j] = v[j];
+            __syncwarp();
+            const int n = n0 + q * 32 + lane;
+            for (int rr = 0; rr < 32; ++rr) {
+                const int r = m0 + warp * 32 + rr;
+                if (r < g.M && n < g.N && (!g.lower || n <= r)) {
+                    float *cp = g.C + (long)r * g.ldc + n;
+                    const float acc = stile[(warp * 32 + rr) * 33 + lane];
+                    *cp = g.beta != 0.f ? fmaf(g.alpha, acc, g.beta * *cp) : g.alpha * acc;
+                }
+            }
+            __syncwarp();
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tc_dealloc(tmem, kGBN);
+}
+
+// Unblocked Cholesky of the nb x nb diagonal block at S (row-major, lds) in
+// shared memory: L (lower) written back over S, the inverse of L into Linv
+// (nb x nb of a kNB x kNB row-major block, zero above the diagonal).  A
+// non-positive pivot sets *info = 1 (not positive definite).  One CTA of
+// kGThreads threads.
+constexpr int kNB = 128;
+
+__global__ void __launch_bounds__(kGThreads) k_potrf_diag(float *S, long lds, int nb, float *Linv, int *info) {
+    constexpr int ldl = kNB;
+    extern __shared__ float a[];   // [nb][nb + 1] factor, then [nb][nb + 1] its inverse
+    const int ld = nb + 1, t = threadIdx.x;
+    for (int q = t; q < nb * nb; q += blockDim.x) {
+        const int i = q / nb, j = q - i * nb;
+        a[i * ld + j] = j <= i ? S[(long)i * lds + j] : 0.f;
+    }
+    __syncthreads();
+    __shared__ int bad;
+    if (t == 0) bad = 0;
+    __syncthreads();
+    for (int k = 0; k < nb; ++k) {
+        // pivot
+        if (t == 0) {
+            const float d = a[k * ld + k];
+            if (!(d > 0.f)) bad = 1;
+            a[k * ld + k] = d > 0.f ? sqrtf(d) : 1.f;
+        }
+        __syncthreads();
+        const float piv = a[k * ld + k];
+        for (int i = k + 1 + t; i < nb; i += blockDim.x) a[i * ld + k] /= piv;
+        __syncthreads();
+        // trailing update of the lower triangle, one row per thread
+        for (int i = k + 1 + t; i < nb; i += blockDim.x) {
+            const float lik = a[i * ld + k];
+            for (int j = k + 1; j <= i; ++j) a[i * ld + j] = fmaf(-lik, a[j * ld + k], a[i * ld + j]);
+        }
+        __syncthreads();
+    }
+    // inverse of L by forward substitution in shared memory, one column per
+    // thread (column c of the inverse depends only on itself)
+    float *inv = a + nb * ld;   // [nb][nb + 1]
+    for (int c = t; c < nb; c += blockDim.x) {
+        for (int i = 0; i < nb; ++i) {
+            float s = (i == c) ? 1.f : 0.f;
+            if (i >= c)
+                for (int k = c; k < i; ++k) s = fmaf(-a[i * ld + k], inv[k * ld + c], s);
+            inv[i * ld + c] = i >= c ? s / a[i * ld + i] : 0.f;
+        }
+    }
+    __syncthreads();
+    for (int q = t; q < nb * nb; q += blockDim.x) {
+        const int i = q / nb, j = q - i * nb;
+        if (j <= i) S[(long)i * lds + j] = a[i * ld + j];
+        Linv[(long)i * ldl + j] = inv[i * ld + j];
+    }
+    if (t == 0 && bad) atomicOr(info, 1);
+}
+
+// Copy an r x c block (row-major, leading dimensions) from src to dst.
+__global__ void k_copy_block(const float *src, long lds, float *dst, long ldd, int r, int c) {
+    const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (long)r * c) return;
+    const int i = (int)(q / c), j = (int)(q - (long)i * c);
+    dst[(long)i * ldd + j] = src[(long)i * lds + j];
+}
+
+}  // namespace
+
+cudaError_t dense_gemm(const float *A, long lda, const float *B, long ldb, bool b_kn, float *C, long ldc, int M,
+                       int N, int K, float alpha, float beta, bool lower, int *err, cudaStream_t s) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    // per call: the attribute belongs to the current device
+    cudaError_t ea = cudaFuncSetAttribute(k_gemm3, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
+    if (ea != cudaSuccess) return ea;
+    GemmArgs g;
+    g.A = A; g.B = B; g.C = C; g.lda = lda; g.ldb = ldb; g.ldc = ldc; g.M = M; g.N = N; g.K = K;
+    g.alpha = alpha; g.beta = beta; g.b_kn = b_kn ? 1 : 0; g.lower = lower ? 1 : 0;
+    dim3 grid((unsigned)((N + kGBN - 1) / kGBN), (unsigned)((M + kGBM - 1) / kGBM));
+    k_gemm3<<<grid, kGThreads, kGemmSmem, s>>>(g, err);
+    return cudaGetLastError();
+}
+
+// S = L L^T in place (lower triangle), blocked right-looking: for each block
+// column j, factor the diagonal block and invert its factor into
+// linvs[j] (kNB x kNB), solve the panel below it (L_ij = S_ij L_jj^-T, a GEMM
+// into work and a copy back), and update the trailing lower triangle
+// (S -= L_panel L_panel^T).  linvs: dense_blocks(n) * kNB * kNB floats; work:
+// n * kNB floats.  *info = 1 if S is not positive definite.
+cudaError_t dense_potrf(float *S, long lds, int n, float *linvs, float *work, int *info, int *err, cudaStream_t s) {
+    const size_t dsm = 2 * (size_t)kNB * (kNB + 1) * sizeof(float);
+    cudaError_t ea = cudaFuncSetAttribute(k_potrf_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
+    if (ea != cudaSuccess) return ea;
+    float *panel = work;
+    for (int j0 = 0; j0 < n; j0 += kNB) {
+        const int nb = std::min(kNB, n - j0), rest = n - j0 - nb;
+        float *Linv = linvs + (size_t)(j0 / kNB) * kNB * kNB;
+        float *Sjj = S + (long)j0 * lds + j0;
+        k_potrf_diag<<<1, kGThreads, dsm, s>>>(Sjj, lds, nb, Linv, info);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess || rest == 0) {
+            if (e != cudaSuccess) return e;
+            continue;
+        }
+        float *Sij = S + (long)(j0 + nb) * lds + j0;
+        // panel: rows below, B(k, n) = L_jj^-T(k, n) = Linv[n][k] ("N x K")
+        if ((e = dense_gemm(Sij, lds, Linv, kNB, false, panel, nb, rest, nb, nb, 1.f, 0.f, false, err, s)) !=
+            cudaSuccess)
+            return e;
+        const long cnt = (long)rest * nb;
+        k_copy_block<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(panel, nb, Sij, lds, rest, nb);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        // trailing lower triangle: S_rr -= L_r L_r^T
+        float *Srr = S + (long)(j0 + nb) * lds + (j0 + nb);
+        if ((e = dense_gemm(Sij, lds, Sij, lds, false, Srr, lds, rest, rest, nb, -1.f, 1.f, true, err, s)) !=
+            cudaSuccess)
+            return e;
+    }
+    return cudaSuccess;
+}
+
+int dense_blocks(int n) { return (n + kNB - 1) / kNB; }
+
+// Y <- Y S^-1 for S = L L^T factored by dense_potrf (Y: m x n, row-major),
+// left-looking, so that each block's update is one long-K GEMM: first
+// Z = Y L^-T (block columns ascending: Y_j -= Z_{<j} L_{j,<j}^T, then
+// Z_j = Y_j Linv_jj^T), then W = Z L^-1 (descending: Z_j -= W_{>j} L_{>j,j},
+// then W_j = Z_j Linv_jj).  Every step is a k_gemm3 call; work: m * kNB
+// floats.
+cudaError_t dense_posolve_right(const float *S, long lds, int n, const float *linvs, float *Y, long ldy, int m,
+                                float *work, int *err, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    const int nblk = dense_blocks(n);
+    auto copy_back = [&](float *dst, int nb) {
+        const long cnt = (long)m * nb;
+        k_copy_block<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(work, kNB, dst, ldy, m, nb);
+        return cudaGetLastError();
+    };
+    for (int jb = 0; jb < nblk && e == cudaSuccess; ++jb) {
+        const int j0 = jb * kNB, nb = std::min(kNB, n - j0);
+        const float *Linv = linvs + (size_t)jb * kNB * kNB;
+        float *Yj = Y + j0;
+        if (j0 > 0)   // B(k, n) = L[j0 + n][k], k < j0
+            e = dense_gemm(Y, ldy, S + (long)j0 * lds, lds, false, Yj, ldy, m, nb, j0, -1.f, 1.f, false, err, s);
+        if (e == cudaSuccess) e = dense_gemm(Yj, ldy, Linv, kNB, false, work, kNB, m, nb, nb, 1.f, 0.f, false, err, s);
+        if (e == cudaSuccess) e = copy_back(Yj, nb);
+    }
+    for (int jb = nblk - 1; jb >= 0 && e == cudaSuccess; --jb) {
+        const int j0 = jb * kNB, nb = std::min(kNB, n - j0), rest = n - j0 - nb;
+        const float *Linv = linvs + (size_t)jb * kNB * kNB;
+        float *Yj = Y + j0;
+        if (rest > 0)   // B(k, n) = L[j0 + nb + k][j0 + n], k < rest
+            e = dense_gemm(Y + j0 + nb, ldy, S + (long)(j0 + nb) * lds + j0, lds, true, Yj, ldy, m, nb, rest, -1.f,
+                           1.f, false, err, s);
+        if (e == cudaSuccess) e = dense_gemm(Yj, ldy, Linv, kNB, true, work, kNB, m, nb, nb, 1.f, 0.f, false, err, s);
+        if (e == cudaSuccess) e = copy_back(Yj, nb);
+    }
+    return e;
+}
+
+}  // namespace synim
+
+// ---------------------------------------------------------------------------
+// C ABI (context-free)
+// ---------------------------------------------------------------------------
+namespace {
+
+synim_status la_fail(synim_status st, const std::string &m) {
+    synim::set_global_error(m);
+    return st;
+}
+
+// Device scratch freed on scope exit (after the caller's synchronisation).
+struct LaScratch {
+    std::vector<void *> p;
+    ~LaScratch() {
+        for (void *q : p) cudaFree(q);
+    }
+    template <typename T>
+    cudaError_t alloc(T **q, size_t n) {
+        void *v = nullptr;
+        cudaError_t e = cudaMalloc(&v, std::max<size_t>(n, 1) * sizeof(T));
+        if (e == cudaSuccess) {
+            p.push_back(v);
+            *q = static_cast<T *>(v);
+        }
+        return e;
+    }
+};
+
+}  // namespace
+
+extern "C" synim_status synim_linalg_gemm(int32_t M, int32_t N, int32_t K, float alpha, const float *A, int64_t lda,
+                                          const float *B, int64_t ldb, int32_t b_kn, float beta, float *C,
+                                          int64_t ldc, void *cuda_stream) {
+    synim::clear_create_error();
+    // operand leading dimensions matter only when there is something to read
+    if (M < 0 || N < 0 || K < 0 || (M > 0 && N > 0 && (!C || (K > 0 && (!A || !B)))) ||
+        (K > 0 && (lda < K || ldb < (b_kn ? N : K))) || ldc < N || (b_kn != 0 && b_kn != 1))
+        return la_fail(SYNIM_ERR_INVALID_ARG, "linalg_gemm: invalid sizes or pointers");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    LaScratch sc;
+    int *err = nullptr;
+    cudaError_t e = sc.alloc(&err, 1);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), st);
+    if (e == cudaSuccess)
+        e = synim::dense_gemm(A, lda, B, ldb, b_kn != 0, C, ldc, M, N, K, alpha, beta, false, err, st);
+    int h = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return la_fail(SYNIM_ERR_CUDA, std::string("linalg_gemm: ") + cudaGetErrorString(e));
+    if (h) return la_fail(SYNIM_ERR_TIMEOUT, "linalg_gemm: a tensor-core wait gave up");
+    return SYNIM_OK;
+}
+
+extern "C" synim_status synim_linalg_spd_solve(float *S, int32_t n, int64_t lds, float *Y, int32_t m, int64_t ldy,
+                                               void *cuda_stream) {
+    synim::clear_create_error();
+    if (n < 1 || m < 0 || !S || (m > 0 && !Y) || lds < n || ldy < n)
+        return la_fail(SYNIM_ERR_INVALID_ARG, "linalg_spd_solve: invalid sizes or pointers");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    LaScratch sc;
+    int *flags = nullptr;
+    float *linvs = nullptr, *work = nullptr;
+    cudaError_t e = sc.alloc(&flags, 2);
+    if (e == cudaSuccess) e = sc.alloc(&linvs, (size_t)synim::dense_blocks(n) * 128 * 128);
+    if (e == cudaSuccess) e = sc.alloc(&work, (size_t)std::max(n, m) * 128);
+    if (e != cudaSuccess) return la_fail(SYNIM_ERR_OOM, "linalg_spd_solve: scratch");
+    e = cudaMemsetAsync(flags, 0, 2 * sizeof(int), st);
+    if (e == cudaSuccess) e = synim::dense_potrf(S, lds, n, linvs, work, flags, flags + 1, st);
+    if (e == cudaSuccess && m > 0) e = synim::dense_posolve_right(S, lds, n, linvs, Y, ldy, m, work, flags + 1, st);
+    int h[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, flags, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return la_fail(SYNIM_ERR_CUDA, std::string("linalg_spd_solve: ") + cudaGetErrorString(e));
+    if (h[1]) return la_fail(SYNIM_ERR_TIMEOUT, "linalg_spd_solve: a tensor-core wait gave up");
+    if (h[0]) return la_fail(SYNIM_ERR_NOT_CONVERGED, "linalg_spd_solve: S is not positive definite");
+    return SYNIM_OK;
+}

@@ -121,6 +121,7 @@ int largest_divisor_le(int k, int cap);
 long long seg_need(const DmHost &D, const WfsHost &W, const double Ai[4], int NV);
 void split_pair(DevPair &P);  // float pairs of A, b and the float inverse
 void clear_create_error();         // synim_api.cu (no allocation)
+void set_global_error(const std::string &m);   // message of synim_last_error(NULL)
 // Valid-row tables of sensor w of a context (device pointers): vsub[r] =
 // (si << 16) | sj of valid row r; returns nv.
 int ctx_valid_rows(const synim_ctx *ctx, int w, const int **vsub, int *n_sub);
@@ -148,6 +149,18 @@ size_t tele_smem_bytes(int threads, int cap4);
 cudaError_t launch_tele(const Geo &g, const TeleSet &t, const DevPair *pairs, int cap4, int *err, int grid,
                         int threads, cudaStream_t s);
 
+// Dense FP32-accurate linear algebra on tcgen05 (synim_dense.cu); row-major
+// matrices with leading dimensions.  C = beta C + alpha A B with A(m, k) =
+// A[m lda + k], B(k, n) = B[n ldb + k] or, b_kn, B[k ldb + n]; lower: only
+// the lower triangle (n <= m) of C is written.  *err gets ERR_TIMEOUT if a
+// bounded tensor-core wait gives up.
+cudaError_t dense_gemm(const float *A, long lda, const float *B, long ldb, bool b_kn, float *C, long ldc, int M,
+                       int N, int K, float alpha, float beta, bool lower, int *err, cudaStream_t s);
+int dense_blocks(int n);   // diagonal blocks of the blocked factorization (128 rows each)
+cudaError_t dense_potrf(float *S, long lds, int n, float *linvs, float *work, int *info, int *err, cudaStream_t s);
+cudaError_t dense_posolve_right(const float *S, long lds, int n, const float *linvs, float *Y, long ldy, int m,
+                                float *work, int *err, cudaStream_t s);
+
 struct ProbeSet;   // synim_probe.cu
 void probe_destroy(ProbeSet *p);
 // Probe responses of n samples (params device [n][4]): maps [n][per_sample],
@@ -160,7 +173,6 @@ struct EstState;   // synim_estimate.cu
 void est_destroy(EstState *e);
 struct CnnState;   // synim_cnn.cu
 void cnn_destroy(CnnState *s);
-void projection_destroy(synim_ctx *c);   // library handles of the projection
 
 constexpr int NSLOT = 4;
 constexpr int NPROF = 256;
@@ -181,7 +193,6 @@ struct synim_ctx {
     synim::WfsHost wh[SYNIM_MAX_WFS];
     synim::Geo geo{};
     std::vector<void *> dev_allocs;
-    void *cublas = nullptr, *cusolver = nullptr;   // library handles of the projection (created on first use)
     int64_t mem_cap = 0;      // device bytes create may take (0 = no cap)
     int slope_engine = 0;     // SYNIM_ENGINE_NUMERICAL or SYNIM_ENGINE_TELESCOPING
     synim::TeleSet tele{};

@@ -24,16 +24,14 @@
 //                      through a bucket grid; each candidate's entry is the sum
 //                      over directions of the dot product over the two boxes'
 //                      intersection (FP32), everything else stays zero;
-//   + lambda I, Cholesky factor (cuSOLVER SPOTRF) and two triangular solves
-//                      (cuBLAS STRSM) for all layer columns, FP32.
+//   + lambda I, then the blocked Cholesky factor and the two block triangular
+//                      sweeps for all layer columns (synim_dense.cu: every
+//                      block update a 3xTF32 tcgen05 GEMM, FP32 accuracy).
 #include <algorithm>
 #include <climits>
 #include <cmath>
 #include <string>
 #include <vector>
-
-#include <cublas_v2.h>
-#include <cusolverDn.h>
 
 #include "synim.h"
 #include "synim_device.cuh"
@@ -257,13 +255,6 @@ k_box_dot(const BoxSet L, const BoxSet R, int n_dir, const int *__restrict__ cel
 __global__ void k_add_diag(float *__restrict__ G, long long n, float lam) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) G[i * n + i] += lam;
-}
-
-void projection_destroy(synim_ctx *c) {
-    if (c->cublas) cublasDestroy(static_cast<cublasHandle_t>(c->cublas));
-    if (c->cusolver) cusolverDnDestroy(static_cast<cusolverDnHandle_t>(c->cusolver));
-    c->cublas = nullptr;
-    c->cusolver = nullptr;
 }
 
 }  // namespace synim
@@ -522,7 +513,7 @@ synim_status synim_projection_opt(synim_ctx *ctx, int32_t wfs, int32_t n_dir, co
     const int M = ctx->wh[wfs].M;
     ProjScratch sc;
     uint8_t *d_pupil = nullptr;
-    float *G = nullptr, *work = nullptr;
+    float *G = nullptr;
     int *info = nullptr;
     cudaError_t e = sc.alloc(&d_pupil, (size_t)M * M);
     if (e == cudaSuccess) e = sc.alloc(&G, (size_t)nd * nd);
@@ -550,44 +541,23 @@ synim_status synim_projection_opt(synim_ctx *ctx, int32_t wfs, int32_t n_dir, co
                                                       kd.n_cc, kd.max_h, kd.max_w, nd, G);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return pfail(ctx, SYNIM_ERR_CUDA, std::string("k_box_dot: ") + cudaGetErrorString(e));
-    if (!ctx->cublas) {
-        cublasHandle_t h = nullptr;
-        if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) return pfail(ctx, SYNIM_ERR_CUDA, "cublasCreate failed");
-        ctx->cublas = h;
-    }
-    if (!ctx->cusolver) {
-        cusolverDnHandle_t h = nullptr;
-        if (cusolverDnCreate(&h) != CUSOLVER_STATUS_SUCCESS) return pfail(ctx, SYNIM_ERR_CUDA, "cusolverDnCreate failed");
-        ctx->cusolver = h;
-    }
-    cublasHandle_t hb = static_cast<cublasHandle_t>(ctx->cublas);
-    cusolverDnHandle_t hs = static_cast<cusolverDnHandle_t>(ctx->cusolver);
-    cublasSetStream(hb, st);
-    cusolverDnSetStream(hs, st);
-    cublasSetMathMode(hb, CUBLAS_PEDANTIC_MATH);   // no TF32 anywhere
-    const float one = 1.f;
-    cublasStatus_t bs = CUBLAS_STATUS_SUCCESS;
+    // G + lambda I = L L^T (blocked Cholesky on the tensor cores), then
+    // P_opt = (G + lambda I)^-1 R: p_opt is R column-major, i.e. R^T
+    // row-major (n_layer x n_dm), and R^T G^-1 = (G^-1 R)^T in place
     k_add_diag<<<(unsigned)((nd + 255) / 256), 256, 0, st>>>(G, nd, (float)lambda);
-    // G + lambda I = L L^T, then P_opt = L^-T (L^-1 R) for all layer columns
-    int lwork = 0;
-    if (cusolverDnSpotrf_bufferSize(hs, CUBLAS_FILL_MODE_LOWER, (int)nd, G, (int)nd, &lwork) != CUSOLVER_STATUS_SUCCESS)
-        return pfail(ctx, SYNIM_ERR_CUDA, "cusolverDnSpotrf_bufferSize failed");
-    if ((e = sc.alloc(&work, (size_t)std::max(lwork, 1))) != cudaSuccess)
+    float *linvs = nullptr, *work = nullptr;
+    const size_t wrows = (size_t)std::max<long long>(nd, nl);
+    if ((e = sc.alloc(&linvs, (size_t)dense_blocks((int)nd) * 128 * 128)) != cudaSuccess ||
+        (e = sc.alloc(&work, wrows * 128)) != cudaSuccess)
         return pfail(ctx, SYNIM_ERR_OOM, "projection solver workspace");
-    if (cusolverDnSpotrf(hs, CUBLAS_FILL_MODE_LOWER, (int)nd, G, (int)nd, work, lwork, info) != CUSOLVER_STATUS_SUCCESS)
-        return pfail(ctx, SYNIM_ERR_CUDA, "cusolverDnSpotrf failed");
-    bs = cublasStrsm(hb, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, (int)nd, (int)nl,
-                     &one, G, (int)nd, p_opt, (int)nd);
-    if (bs == CUBLAS_STATUS_SUCCESS)
-        bs = cublasStrsm(hb, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, CUBLAS_DIAG_NON_UNIT, (int)nd,
-                         (int)nl, &one, G, (int)nd, p_opt, (int)nd);
-    if (bs != CUBLAS_STATUS_SUCCESS)
-        return pfail(ctx, SYNIM_ERR_CUDA, "projection triangular solves failed (cuBLAS status " +
-                                              std::to_string((int)bs) + ")");
+    if ((e = dense_potrf(G, nd, (int)nd, linvs, work, info, info + 1, st)) != cudaSuccess ||
+        (e = dense_posolve_right(G, nd, (int)nd, linvs, p_opt, nd, (int)nl, work, info + 1, st)) != cudaSuccess)
+        return pfail(ctx, SYNIM_ERR_CUDA, std::string("projection solve: ") + cudaGetErrorString(e));
     int h_info[2] = {0, 0};
     if ((e = cudaMemcpyAsync(h_info, info, 2 * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
         (e = cudaStreamSynchronize(st)) != cudaSuccess)
         return pfail(ctx, SYNIM_ERR_CUDA, std::string("projection: ") + cudaGetErrorString(e));
+    if (h_info[1] != 0) return pfail(ctx, SYNIM_ERR_TIMEOUT, "projection: a tensor-core wait gave up");
     if (h_info[0] != 0)
         return pfail(ctx, SYNIM_ERR_NOT_CONVERGED,
                      "projection: P_DM^T P_DM + lambda I is not positive definite (raise lambda)");
