@@ -269,6 +269,64 @@ synim_status synim_linalg_gemm(int32_t M, int32_t N, int32_t K, float alpha, con
 synim_status synim_linalg_spd_solve(float *S, int32_t n, int64_t lds, float *Y, int32_t m, int64_t ldy,
                                     void *cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Tomographic covariances and the MMSE reconstructor (Sec. 2.4)
+ *
+ * The paper names the models without formulas; the readings are:
+ *   - von Karman phase covariance of a layer (phase in radians at the
+ *     wavelength r0 refers to), x = 2 pi r / L0:
+ *       B(r) = c (L0 / r0)^(5/3) x^(5/6) K_5/6(x),
+ *       c = Gamma(11/6) / (2^(5/6) pi^(8/3)) (24/5 Gamma(6/5))^(5/6);
+ *     a layer holding the fraction f of the C_n^2 profile has r0 f^(-3/5);
+ *   - projected onto the DM's basis: F = the influence functions averaged
+ *     over bin x bin pixel blocks, C_atm = G^-1 F^T C_phi F G^-1 with
+ *     G = F^T F (covariance of the least-squares coefficients);
+ *   - Shack-Hartmann centroid noise (photon and read-out terms) per valid
+ *     subaperture, with the LGS spot elongated along the direction from the
+ *     launch telescope;
+ *   - R = C_atm D^T (D C_atm D^T + C_n)^-1, D^T being the IM.
+ * Outputs are row-major FP32 device matrices; the calls synchronise the
+ * stream before returning.
+ * ---------------------------------------------------------------------- */
+
+/* Detector and guide-star parameters of one sensor's noise covariance. */
+typedef struct {
+    double n_photons;       /* photons per subaperture per frame, > 0 */
+    double ron_e;           /* read-out noise, electrons rms per pixel, >= 0 */
+    double pixel_scale_rad; /* detector pixel, radians on the sky, > 0 */
+    int32_t n_pix;          /* centroiding window width, pixels, >= 1 */
+    int32_t lgs;            /* 1 = laser guide star (spot elongation), 0 = natural */
+    double fwhm_rad;        /* spot FWHM without elongation, radians, > 0 */
+    double wavelength_m;    /* sensing wavelength, > 0 */
+    double llt_xy_m[2];     /* launch telescope position in the pupil plane (LGS) */
+    double na_altitude_m;   /* sodium layer altitude above the telescope (LGS), > 0 */
+    double na_thickness_m;  /* sodium layer thickness (LGS), >= 0 */
+    double zenith_rad;      /* zenith angle (LGS): both lengths scale by 1 / cos */
+} synim_noise_desc;
+
+/* C_atm [n_act][n_act] of DM dm's basis for a von Karman layer of Fried
+ * parameter r0_m and outer scale L0_m, on the DM grid binned by bin (grid_n
+ * a multiple of bin, at most 46340 binned pixels).  The FP32 result carries
+ * about cond(G)^2 2^-24 relative error: choose bin so that each influence
+ * function spans at least two binned pixels (cond(G) grows fast as the
+ * binned basis functions shrink below that; SYNIM_ERR_NOT_CONVERGED if G is
+ * singular).  Allocates scratch of (grid_n / bin)^4 floats plus a few
+ * n_act^2. */
+synim_status synim_atm_covariance(synim_ctx *ctx, int32_t dm, int32_t bin, double r0_m, double L0_m,
+                                  float *c_atm, void *cuda_stream);
+
+/* C_n [2 nv][2 nv] of sensor wfs (rows as the IM's: x slopes then y slopes of
+ * the valid subapertures), in the IM's slope units (radians of phase per
+ * metre times slope_scale). */
+synim_status synim_noise_covariance(synim_ctx *ctx, int32_t wfs, const synim_noise_desc *nd, float *c_noise,
+                                    void *cuda_stream);
+
+/* R [n_modes][n_slopes] = C_atm D^T (D C_atm D^T + C_n)^-1 for im = D^T
+ * [n_modes][n_slopes], c_atm [n_modes][n_modes], c_noise [n_slopes][n_slopes].
+ * Context-free (errors through synim_last_error(NULL)). */
+synim_status synim_mmse_reconstructor(int32_t n_modes, int32_t n_slopes, const float *im, const float *c_atm,
+                                      const float *c_noise, float *R, void *cuda_stream);
+
 /*
  * Self-test of the bounded device waits (the mbarrier waits of the
  * tensor-core kernels use the same helper): one thread waits on an mbarrier

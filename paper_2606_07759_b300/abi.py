@@ -42,6 +42,12 @@ ENGINE_NUMERICAL = 0     # SYNIM_ENGINE_NUMERICAL
 ENGINE_TELESCOPING = 1   # SYNIM_ENGINE_TELESCOPING
 
 
+class synim_noise_desc(ctypes.Structure):
+    _fields_ = [("n_photons", c_double), ("ron_e", c_double), ("pixel_scale_rad", c_double), ("n_pix", c_int32),
+                ("lgs", c_int32), ("fwhm_rad", c_double), ("wavelength_m", c_double), ("llt_xy_m", c_double * 2),
+                ("na_altitude_m", c_double), ("na_thickness_m", c_double), ("zenith_rad", c_double)]
+
+
 class synim_opts(ctypes.Structure):
     _fields_ = [("threads_per_cta", c_int32), ("ctas_per_sm", c_int32), ("use_graph", c_int32),
                 ("autotune", c_int32), ("profile", c_int32), ("device_mem_cap", ctypes.c_int64),
@@ -80,6 +86,9 @@ SIGNATURES = {
     "synim_linalg_gemm": (c_int32, [c_int32, c_int32, c_int32, c_float, c_void_p, c_int64, c_void_p, c_int64,
                                     c_int32, c_float, c_void_p, c_int64, c_void_p]),
     "synim_linalg_spd_solve": (c_int32, [c_void_p, c_int32, c_int64, c_void_p, c_int32, c_int64, c_void_p]),
+    "synim_atm_covariance": (c_int32, [c_void_p, c_int32, c_int32, c_double, c_double, c_void_p, c_void_p]),
+    "synim_noise_covariance": (c_int32, [c_void_p, c_int32, ctypes.POINTER(synim_noise_desc), c_void_p, c_void_p]),
+    "synim_mmse_reconstructor": (c_int32, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "synim_im_kernel_ms": (c_int32, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int32)]),
     "synim_im_compute_noalloc": (c_int32, [ctypes.POINTER(synim_dm_desc), ctypes.POINTER(synim_wfs_desc),
                                            ctypes.POINTER(synim_misreg), c_void_p, ctypes.POINTER(c_int64),

@@ -40,7 +40,8 @@ def test_library_exports_every_declared_function():
 def test_struct_layouts_match_the_header(tmp_path):
     probe = tmp_path / "probe.c"
     structs = {"synim_dm_desc": abi.synim_dm_desc, "synim_wfs_desc": abi.synim_wfs_desc,
-               "synim_misreg": abi.synim_misreg, "synim_opts": abi.synim_opts}
+               "synim_misreg": abi.synim_misreg, "synim_opts": abi.synim_opts,
+               "synim_noise_desc": abi.synim_noise_desc}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "synim.h"', "int main(void){"]
     for name, cls in structs.items():
         lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
