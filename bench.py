@@ -550,18 +550,84 @@ def run_projection(s, wl):
     del X
     torch.cuda.empty_cache()
     dense_flop = 1.0 * nd * nd * K + 2.0 * nd * nl * K   # what dense products over all rows would cost
-    solve_flop = nd ** 3 / 3.0 + 2.0 * nd * nd * nl      # SPOTRF + two STRSM (dense, FP32)
-    solve_rate = solve_flop / t_opt / 1e12              # as if the whole call were the solve (a lower bound)
+    solve_flop = nd ** 3 / 3.0 + 2.0 * nd * nd * nl      # Cholesky + the two triangular sweeps (dense, FP32)
+    # the solve runs on tcgen05 TF32 with three split products per FP32 product
+    tc_rate = 3.0 * solve_flop / t_opt / 1e12           # as if the whole call were the solve (a lower bound)
+    tpeak, tkind = tf32_peak(sustained=True)
     return {"directions": len(dirs), "binning": b, "rows": K, "dm_columns": nd, "layer_columns": nl,
             "lambda": lam, "projection_matrix_s_dm_only": t_pd, "p_opt_s": t_opt,
             "dense_products_tflop_avoided": dense_flop / 1e12, "solve_tflop": solve_flop / 1e12, "finite": finite,
-            "roofline": {"bound": "fp32", "achieved": solve_rate, "peak": 38.3, "unit": "TFLOP/s",
-                         "frac": solve_rate / 38.3,
-                         "peak_kind": "cuBLAS STRSM (FP32, 8583 x 8192 right-hand sides) measured on this B300; "
-                                      "achieved counts only the dense solve FLOPs over the whole call"},
+            "roofline": {"bound": "tensor", "achieved": tc_rate, "peak": tpeak, "unit": "TFLOP/s",
+                         "frac": tc_rate / tpeak, "peak_kind": tkind,
+                         "achieved_counts": "3 TF32 products per FP32 product of the dense solve, over the whole call"},
             "note": "one call after a small warm-up call: box-stored projection columns, box-sparse products "
-                    "(every pair of columns whose footprint boxes meet), dense Cholesky factor and two triangular "
-                    "solves; wall clock around the call"}
+                    "(every pair of columns whose footprint boxes meet), blocked Cholesky and two block triangular "
+                    "sweeps on the tensor cores (3xTF32); wall clock around the call"}
+
+
+def tf32_peak(sustained: bool):
+    """Dense TF32 tensor peak: the measured bf16 figure times NVIDIA's nominal TF32 : BF16 ratio (1.1 : 2.25)."""
+    mp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    key = "bf16_tflops_sustained" if sustained else "bf16_tflops"
+    if os.path.exists(mp):
+        with open(mp) as f:
+            v = json.load(f).get(key)
+        if v:
+            return float(v) * 1.1 / 2.25, f"measured {key} x 1.1 / 2.25 (nominal TF32 : BF16)"
+    return (1400.0 if sustained else 1800.0) * 1.1 / 2.25, "fallback bf16 x 1.1 / 2.25"
+
+
+def run_mmse(args):
+    """Tomographic covariances and the MMSE reconstructor (Sec. 2.4) on the learned-estimator geometry:
+    37 x 37 DM (1369 modes, every one inside the 352 px grid, so the basis is full rank) binned 4 x 4
+    (7744 pixels), 40 x 40 SH (2528 slopes).  (The ELT / MCAO DMs keep actuators outside the pupil
+    annulus whose masked influence functions vanish: their basis Gram matrix is singular.)"""
+    import ctypes
+    import torch
+    from paper_2606_07759_b300 import abi
+    from paper_2606_07759_b300.synim import SynIM
+    wl, _ = W.learned()
+    s = SynIM(wl.dms, wl.wfss)
+    im = s.compute(wl.misregs)[0]
+    nm, ns = im.shape
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    L = s._L
+    ca = torch.empty(nm, nm, device="cuda")
+    cn = torch.empty(ns, ns, device="cuda")
+    R = torch.empty(nm, ns, device="cuda")
+    nd = abi.synim_noise_desc(n_photons=500.0, ron_e=3.0, pixel_scale_rad=0.8e-6, n_pix=10, lgs=1, fwhm_rad=1.0e-6,
+                              wavelength_m=589e-9)
+    nd.llt_xy_m[0], nd.llt_xy_m[1] = 20.0, 0.0
+    nd.na_altitude_m, nd.na_thickness_m, nd.zenith_rad = 90e3, 10e3, 0.5
+    bin_, N = 4, wl.dms[0].grid_n
+    L.synim_atm_covariance(s._ctx, 0, 8, 0.15, 25.0, ca.data_ptr(), st)   # warm-up (smaller grid)
+    times = {}
+    for name, fn in (("atm_covariance_s", lambda: L.synim_atm_covariance(s._ctx, 0, bin_, 0.15, 25.0, ca.data_ptr(), st)),
+                     ("noise_covariance_s", lambda: L.synim_noise_covariance(s._ctx, 0, ctypes.byref(nd), cn.data_ptr(),
+                                                                             st)),
+                     ("mmse_s", lambda: L.synim_mmse_reconstructor(nm, ns, im.data_ptr(), ca.data_ptr(), cn.data_ptr(),
+                                                                   R.data_ptr(), st))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc = fn()
+        torch.cuda.synchronize()
+        times[name] = time.perf_counter() - t0
+        if rc != 0:
+            raise RuntimeError(f"{name}: {L.synim_last_error(s._ctx if 'mmse' not in name else None)}")
+    npix = (N // bin_) ** 2
+    atm_flop = 2.0 * npix * npix * nm + 2.0 * nm * nm * npix * 2 + 2.0 * nm ** 3 / 3 + 4.0 * nm ** 3
+    mmse_flop = 2.0 * nm * nm * ns + 2.0 * ns * ns * nm + ns ** 3 / 3.0 + 2.0 * nm * ns * ns
+    tpeak, tkind = tf32_peak(sustained=True)
+    rate = 3.0 * mmse_flop / times["mmse_s"] / 1e12
+    finite = bool(torch.isfinite(R).all()) and bool(torch.isfinite(ca).all())
+    s.close()
+    return {"workload": "learned geometry: 37 x 37 DM (1369 modes) on 352 px binned 4 x 4, 40 x 40 SH "
+                        "(2528 slopes), LGS noise with elongation", "modes": nm, "slopes": ns, "binned_pixels": npix,
+            **times, "atm_tflop": atm_flop / 1e12, "mmse_tflop": mmse_flop / 1e12, "finite": finite,
+            "roofline": {"bound": "tensor", "achieved": rate, "peak": tpeak, "unit": "TFLOP/s",
+                         "frac": rate / tpeak, "peak_kind": tkind,
+                         "achieved_counts": "3 TF32 products per FP32 product of the MMSE call, over the whole call"},
+            "note": "one call each, wall clock around the call (synchronising)"}
 
 
 def run_learned(args):
@@ -748,6 +814,8 @@ def run_synim(args):
         line["dictionary"] = run_dictionary(args)
     if rank == 0 and world == 1 and not args.no_learned:
         line["learned"] = run_learned(args)
+    if rank == 0 and world == 1 and not args.no_mmse:
+        line["mmse"] = run_mmse(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -769,6 +837,7 @@ def main(argv=None):
     ap.add_argument("--ref-seconds", type=float, default=4.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-estimator measurements")
+    ap.add_argument("--no-mmse", action="store_true", help="skip the covariance / MMSE reconstructor measurements")
     ap.add_argument("--learned-train", type=int, default=200_000)
     ap.add_argument("--learned-epochs", type=int, default=40)
     ap.add_argument("--no-sensitivity", action="store_true",

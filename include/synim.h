@@ -310,8 +310,9 @@ typedef struct {
  * about cond(G)^2 2^-24 relative error: choose bin so that each influence
  * function spans at least two binned pixels (cond(G) grows fast as the
  * binned basis functions shrink below that; SYNIM_ERR_NOT_CONVERGED if G is
- * singular).  Allocates scratch of (grid_n / bin)^4 floats plus a few
- * n_act^2. */
+ * singular, as it is whenever some influence function vanishes on the grid,
+ * e.g. actuators masked out by the DM mask: leave those out of the basis).
+ * Allocates scratch of (grid_n / bin)^4 floats plus a few n_act^2. */
 synim_status synim_atm_covariance(synim_ctx *ctx, int32_t dm, int32_t bin, double r0_m, double L0_m,
                                   float *c_atm, void *cuda_stream);
 
