@@ -1,5 +1,6 @@
-// synim_cpasync.cuh -- 16-byte asynchronous global -> shared copies
-// (cp.async) used by the producer warps of the tensor-core kernels.
+// synim_cpasync.cuh -- asynchronous global -> shared copies (cp.async): 16-byte
+// copies for the producer warps of the convolution kernels, 4-byte copies for
+// the operand tiles of the dense-linear-algebra GEMM.
 #pragma once
 
 #include <cstdint>
@@ -21,6 +22,12 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src, bool vali
 __device__ __forceinline__ void cp_async16_ca(void *dst, const void *src, bool valid) {
     const int n = valid ? 16 : 0;
     asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_addr(dst)), "l"(src), "r"(n));
+}
+// 4-byte asynchronous copy through L1 (any alignment of the source element);
+// src_bytes = 0 writes a zero.
+__device__ __forceinline__ void cp_async4(void *dst, const void *src, bool valid) {
+    const int n = valid ? 4 : 0;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(smem_addr(dst)), "l"(src), "r"(n));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>

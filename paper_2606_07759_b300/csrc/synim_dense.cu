@@ -4,10 +4,12 @@
 //
 // k_gemm3     C = beta C + alpha op(A) op(B) on tcgen05.mma .kind::tf32 with
 //             split operands: x = hi + lo, hi = x with its low 13 mantissa
-//             bits cleared (what the tensor core reads of x), lo = x - hi
-//             (exact in FP32).  C accumulates hi.hi + hi.lo + lo.hi in FP32
-//             TMEM (the lo.lo term is below FP32 rounding), so a product
-//             carries ~2^-21 relative error, against 2^-11 for one TF32 pass.
+//             bits cleared (a TF32 value), lo = x - hi (exact in FP32).  C
+//             accumulates hi.hi + hi.lo + lo.hi in FP32 TMEM (the lo.lo term
+//             is below FP32 rounding), so a product carries ~2^-21 relative
+//             error, against 2^-11 for one TF32 pass.  Operand tiles arrive
+//             by 4-byte cp.async two chunks ahead of their use (four raw
+//             stages) and are split in shared memory.
 // k_potrf_diag  unblocked Cholesky of one diagonal block and the inverse of
 //             its factor (one CTA, shared memory);
 // blocked     right-looking Cholesky S = L L^T whose panel and trailing
@@ -24,6 +26,7 @@
 #include <string>
 #include <vector>
 
+#include "synim_cpasync.cuh"
 #include "synim_internal.h"
 #include "synim_tc.cuh"
 
@@ -36,8 +39,10 @@ constexpr int kGBN = 128;   // tile columns (TMEM columns)
 constexpr int kGBK = 32;    // K chunk (floats): 8 core matrices of 16 bytes
 constexpr int kGThreads = 128;
 constexpr int kTileBytes = kGBM * kGBK * 4;            // one operand tile, one part (16 KB)
-constexpr int kStageBytes = 4 * kTileBytes;            // A hi, A lo, B hi, B lo
-constexpr int kGemmSmem = 2 * kStageBytes + 2048;      // two stages, barriers, 1024-byte alignment slack
+constexpr int kRawStages = 4;                          // raw (= hi) operand stages in flight
+constexpr int kRawBytes = 2 * kTileBytes;              // A raw, B raw
+constexpr int kLoBytes = 2 * kTileBytes;               // A lo, B lo
+constexpr int kGemmSmem = kRawStages * kRawBytes + 2 * kLoBytes + 2048;   // + barriers, 1024-byte alignment slack
 
 // Instruction descriptor of tcgen05.mma .kind::tf32: D F32, A and B TF32,
 // both K-major, shape M x N.
@@ -65,12 +70,6 @@ __device__ __forceinline__ uint32_t tile_off(int r, int k) {
     return (uint32_t)((r >> 3) * 1024 + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4);
 }
 
-__device__ __forceinline__ void split_store(uint8_t *hi, uint8_t *lo, uint32_t off, float x) {
-    const float h = __uint_as_float(__float_as_uint(x) & 0xffffe000u);
-    *reinterpret_cast<float *>(hi + off) = h;
-    *reinterpret_cast<float *>(lo + off) = x - h;
-}
-
 struct GemmArgs {
     const float *A, *B;
     float *C;
@@ -81,48 +80,53 @@ struct GemmArgs {
     int lower;   // 1: only tiles that touch the lower triangle (n <= m) of C
 };
 
-// Stage the K chunk k0 of one operand tile (rows r0.., 128 rows) into its
-// hi / lo tiles.  kcont: the operand's K index is contiguous in memory.
-__device__ __forceinline__ void stage_tile(const float *X, long ld, bool kcont, int rows, int r0, int K, int k0,
-                                           uint8_t *hi, uint8_t *lo) {
-    const int t = threadIdx.x;
+// Issue the asynchronous 4-byte copies of K chunk k0 of one operand tile
+// (128 rows from r0) into its raw tile (zero where out of range), any
+// alignment.  kcont (K contiguous in memory): a warp instruction copies 8
+// rows x 4 consecutive k, so the shared-memory writes are 32 consecutive
+// words of one core-matrix row group; otherwise a warp copies 32 consecutive
+// rows at one k (coalesced reads of the contiguous row index).
+__device__ __forceinline__ void issue_tile(const float *X, long ld, bool kcont, int rows, int r0, int K, int k0,
+                                           uint8_t *raw) {
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     if (kcont) {
-        // 128 rows x 32 floats: each thread loads one row in 8 float4s
-        const int r = t;
-        const long gr = r0 + r;
-        const float *src = X + gr * ld + k0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int k = q * 4;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (gr < rows) {
-                if (k0 + k + 3 < K && ((reinterpret_cast<uintptr_t>(src + k) & 15u) == 0)) {
-                    v = *reinterpret_cast<const float4 *>(src + k);
-                } else {
-                    v.x = (k0 + k + 0 < K) ? src[k + 0] : 0.f;
-                    v.y = (k0 + k + 1 < K) ? src[k + 1] : 0.f;
-                    v.z = (k0 + k + 2 < K) ? src[k + 2] : 0.f;
-                    v.w = (k0 + k + 3 < K) ? src[k + 3] : 0.f;
-                }
-            }
-            const uint32_t off = tile_off(r, k);
-            split_store(hi, lo, off, v.x);
-            split_store(hi, lo, off + 4, v.y);
-            split_store(hi, lo, off + 8, v.z);
-            split_store(hi, lo, off + 12, v.w);
+#pragma unroll 8
+        for (int it = 0; it < 32; ++it) {
+            const int pr = it * 4 + warp;                  // (row group, k group) pair, 0..127
+            const int r = (pr >> 3) * 8 + (lane & 7), k = (pr & 7) * 4 + (lane >> 3);
+            const bool ok = r0 + r < rows && k0 + k < K;
+            const float *src = ok ? X + (long)(r0 + r) * ld + (k0 + k) : X;
+            cp_async4(raw + tile_off(r, k), src, ok);
         }
     } else {
-        // the row index is contiguous: each pass reads 128 consecutive rows at
-        // one k; all 32 loads are issued before the first store
-        float v[kGBK];
-        const long gr = r0 + t;
-#pragma unroll
+#pragma unroll 8
         for (int k = 0; k < kGBK; ++k) {
-            const long gk = k0 + k;
-            v[k] = (gk < K && gr < rows) ? X[gk * ld + gr] : 0.f;
+            const int r = t;
+            const bool ok = r0 + r < rows && k0 + k < K;
+            const float *src = ok ? X + (long)(k0 + k) * ld + (r0 + r) : X;
+            cp_async4(raw + tile_off(r, k), src, ok);
         }
-#pragma unroll
-        for (int k = 0; k < kGBK; ++k) split_store(hi, lo, tile_off(t, k), v[k]);
+    }
+}
+
+// Split both raw tiles of a stage in place: hi = x with its low 13 mantissa
+// bits cleared (written back, so that hi + lo = x exactly whatever the tensor
+// core does with the bits below TF32), lo = x - hi; 16 bytes per step (raw
+// and lo tiles share the layout).
+__device__ __forceinline__ void make_lo(uint8_t *raw, uint8_t *lo) {
+    float4 *src = reinterpret_cast<float4 *>(raw);
+    float4 *dst = reinterpret_cast<float4 *>(lo);
+#pragma unroll 4
+    for (int q = threadIdx.x; q < kRawBytes / 16; q += kGThreads) {
+        const float4 v = src[q];
+        float4 h, l;
+        h.x = __uint_as_float(__float_as_uint(v.x) & 0xffffe000u);
+        h.y = __uint_as_float(__float_as_uint(v.y) & 0xffffe000u);
+        h.z = __uint_as_float(__float_as_uint(v.z) & 0xffffe000u);
+        h.w = __uint_as_float(__float_as_uint(v.w) & 0xffffe000u);
+        l.x = v.x - h.x; l.y = v.y - h.y; l.z = v.z - h.z; l.w = v.w - h.w;
+        src[q] = h;
+        dst[q] = l;
     }
 }
 
@@ -137,7 +141,8 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gemm3(const GemmArgs g, int *e
     const int m0 = bm * kGBM, n0 = bn * kGBN;
     if (g.lower && n0 > m0 + kGBM - 1) return;   // tile wholly above the diagonal
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(gsm) + 1023) & ~uintptr_t(1023));
-    uint64_t *bars = reinterpret_cast<uint64_t *>(base + 2 * kStageBytes);
+    uint8_t *lo_base = base + kRawStages * kRawBytes;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(lo_base + 2 * kLoBytes);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
@@ -152,20 +157,34 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gemm3(const GemmArgs g, int *e
     const uint32_t tmem = *tslot;
     const int nch = (g.K + kGBK - 1) / kGBK;
     const uint32_t idesc = idesc_tf32(kGBM, kGBN);
+    // chunk c: raw (= hi) tiles in stage c % 4, written by cp.async two chunks
+    // ahead; lo tiles in slot c % 2, written once the MMAs of chunk c - 2
+    // (which read that slot and raw stage (c + 2) % 4) have completed
+    auto issue = [&](int c) {
+        uint8_t *raw = base + (c % kRawStages) * kRawBytes;
+        issue_tile(g.A, g.lda, true, g.M, m0, g.K, c * kGBK, raw);
+        issue_tile(g.B, g.ldb, g.b_kn == 0, g.N, n0, g.K, c * kGBK, raw + kTileBytes);
+        cp_async_commit();
+    };
+    if (nch > 0) issue(0);
+    if (nch > 1) issue(1);
     bool ok = true;
     int committed = -1;   // last chunk whose MMAs were committed
     for (int c = 0; c < nch; ++c) {
         const int b = c & 1;
-        uint8_t *ah = base + b * kStageBytes, *al = ah + kTileBytes, *bh = al + kTileBytes, *bl = bh + kTileBytes;
+        uint8_t *raw = base + (c % kRawStages) * kRawBytes, *lo = lo_base + b * kLoBytes;
+        if (c + 1 < nch) cp_async_wait<1>();   // chunk c landed (chunk c + 1 may be in flight)
+        else cp_async_wait<0>();
         if (c >= 2 && !tc_mbar_wait(tc_smem(&bars[b]), ((c - 2) >> 1) & 1)) ok = false;
         if (!__syncthreads_and(ok)) break;
-        stage_tile(g.A, g.lda, true, g.M, m0, g.K, c * kGBK, ah, al);
-        stage_tile(g.B, g.ldb, g.b_kn == 0, g.N, n0, g.K, c * kGBK, bh, bl);
-        tc_fence_proxy_async();
+        if (c + 2 < nch) issue(c + 2);
+        make_lo(raw, lo);
+        tc_fence_proxy_async();   // this thread's cp.async and lo writes -> the tensor core's reads
         __syncthreads();
         if (tid == 0) {
             tc_fence_after();
-            const uint32_t sah = tc_smem(ah), sal = tc_smem(al), sbh = tc_smem(bh), sbl = tc_smem(bl);
+            const uint32_t sah = tc_smem(raw), sbh = tc_smem(raw + kTileBytes);
+            const uint32_t sal = tc_smem(lo), sbl = tc_smem(lo + kTileBytes);
 #pragma unroll
             for (int j = 0; j < kGBK / 8; ++j) {
                 const uint32_t o = (uint32_t)j * 256;
@@ -179,6 +198,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gemm3(const GemmArgs g, int *e
         }
         committed = c;
     }
+    cp_async_wait<0>();   // no copy may still target shared memory when the CTA leaves
     // every issued MMA has completed before TMEM is read or freed (bounded)
     if (committed >= 0 && !tc_mbar_wait(tc_smem(&bars[committed & 1]), (committed >> 1) & 1)) ok = false;
     ok = __syncthreads_and(ok) != 0;
