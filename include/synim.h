@@ -104,7 +104,8 @@ typedef struct {
 typedef struct {
     int32_t threads_per_cta; /* 0 = default (256); a multiple of 32 in 64..256 */
     int32_t ctas_per_sm;     /* reserved, 0 (every column is one warp of one launch) */
-    int32_t use_graph;       /* 1 = replay a CUDA graph per stream; 0 = plain launches */
+    int32_t use_graph;       /* 1 = replay a CUDA graph per stream (interaction matrices) and
+                                per small estimator batch; 0 = plain launches */
     int32_t autotune;        /* 1 = at the first call of each mode, time the candidate launch
                                 shapes (128 or 256 threads x 2, 4 or 8 lanes per boundary
                                 segment; telescoping engine: x 1/2, 1, 2 or 4 times the
@@ -411,7 +412,8 @@ synim_status synim_probe_generate(synim_ctx *ctx, const double *params, int64_t 
  * Misregistration of the probed pair from measured probe responses.
  *   probe_slopes: device [n][n_sub][n_sub][C] FP32 slope maps (layout above).
  *   method: 0 = Gauss-Newton fit from the initial guesses in inout;
- *           1 = the trained network alone (synim_cnn_train / synim_cnn_load);
+ *           1 = the network alone (synim_cnn_init, then synim_cnn_train or
+ *               trained parameters);
  *           2 = the network's estimate refined by the fit.
  *   inout: host [n]: initial guesses (method 0; ignored otherwise), then the
  *          estimates.
@@ -429,6 +431,13 @@ synim_status synim_probe_generate(synim_ctx *ctx, const double *params, int64_t 
  * identity when N = M): there every sample lies on a cell line and the
  * floor-cell Jacobian is one-sided.  SYNIM_ERR_NOT_TRAINED for methods 1-2
  * without a network.  Synchronous.
+ * Small batches (n <= 32) of method 1, and of method 2 with max_iter <= 4,
+ * run as one CUDA graph per (method, n, max_iter, residual wanted), captured
+ * at the first such call (unless the context was created with use_graph =
+ * 0): the network, the residual or the max_iter + 1 fit passes, and the
+ * readback, with one synchronisation per call.  The results are those of the
+ * plain launches with the same batch size.  A later probe attach, network
+ * init or fit setting recaptures.
  */
 synim_status synim_misreg_estimate(synim_ctx *ctx, const float *probe_slopes, int64_t n, int32_t method,
                                    synim_misreg *inout, double *residual_out, void *cuda_stream);

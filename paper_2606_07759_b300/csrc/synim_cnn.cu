@@ -1519,6 +1519,12 @@ int cnn_n_params(int C0, int H0) {
     return CH * 9 * C0 + CH + 2 * (CH * 9 * CH + CH) + 4 * H3 * H3 * CH + 4;
 }
 
+bool cnn_ready(const synim_ctx *c, std::string &why) {
+    if (c->cnn && c->cnn->ready) return true;
+    why = "the network has not been initialised (synim_cnn_init) or trained";
+    return false;
+}
+
 cudaError_t cnn_predict_slopes(synim_ctx *c, const float *y, long long n, double *params_out, cudaStream_t st,
                                std::string &why) {
     CnnState *S = c->cnn;
@@ -1561,6 +1567,7 @@ synim_status synim_cnn_init(synim_ctx *ctx, const float *params, const double *n
     if (prev != ctx->device) cudaSetDevice(ctx->device);
     cnn_destroy(ctx->cnn);
     ctx->cnn = nullptr;
+    ++ctx->est_gen;
     CnnState *S = new CnnState();
     S->H0 = n_sub;
     S->C0 = C;

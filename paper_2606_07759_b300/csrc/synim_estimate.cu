@@ -57,10 +57,32 @@ struct EstState {
     double *h_p = nullptr;      // pinned [cap][4]
     double *h_r = nullptr;      // pinned [cap][2] residual sums
     std::vector<int> iters, conv;  // of the last estimate
+    // small-batch path: one captured graph per (method, n, passes)
+    struct Graph {
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t x = nullptr;
+    };
+    std::map<std::tuple<int, long long, int>, Graph> graphs;
+    float *ybuf = nullptr;      // [cap][per_sample] the call's probe slopes (the graph's input)
+    GnState *h_st = nullptr;    // pinned [cap]
+    unsigned long long gen = 0; // synim_ctx::est_gen the graphs were captured at
+    cudaStream_t cap_st = nullptr;
 };
+
+void est_drop_graphs(EstState *e) {
+    for (auto &kv : e->graphs) {
+        if (kv.second.x) cudaGraphExecDestroy(kv.second.x);
+        if (kv.second.g) cudaGraphDestroy(kv.second.g);
+    }
+    e->graphs.clear();
+}
 
 void est_destroy(EstState *e) {
     if (!e) return;
+    est_drop_graphs(e);
+    if (e->cap_st) cudaStreamDestroy(e->cap_st);
+    cudaFree(e->ybuf);
+    cudaFreeHost(e->h_st);
     cudaFree(e->maps);
     cudaFree(e->dmaps);
     cudaFree(e->red);
@@ -126,8 +148,12 @@ k_gn_reduce(const float *__restrict__ y, const float *__restrict__ s, const floa
 }
 
 // out[q][t] = sum over the parts of sample q of part[q][b][t] (t < nq), one
-// warp per quantity, fixed order for a given number of parts.
-__global__ void k_red_combine(const double *__restrict__ part, int parts, int nq, double *__restrict__ out) {
+// warp per quantity, fixed order for a given number of parts.  Rows of out
+// are ostride apart, and the last quantity goes to slot last (nq - 1 for a
+// packed row; kRed - 1 puts a residual pair (r.r, y.y) where k_gn_step reads
+// them).
+__global__ void k_red_combine(const double *__restrict__ part, int parts, int nq, double *__restrict__ out,
+                              int ostride, int last) {
     const long q = blockIdx.x;
     const int t = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (t >= nq) return;
@@ -135,7 +161,7 @@ __global__ void k_red_combine(const double *__restrict__ part, int parts, int nq
     for (int b = lane; b < parts; b += 32) v += part[(q * parts + b) * nq + t];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) out[q * nq + t] = v;
+    if (lane == 0) out[q * ostride + (t == nq - 1 ? last : t)] = v;
 }
 
 // Residual sums only: red2[q] = (r.r, y.y) of sample q.
@@ -172,8 +198,10 @@ k_resid_reduce(const float *__restrict__ y, const float *__restrict__ s, int per
 
 // Cholesky solve of the 4x4 SPD system (packed upper triangle); false if a
 // pivot is not positive.
+// FP64 division and square root are long instruction sequences on the
+// narrow FP64 pipe, so each pivot is inverted once and the rest multiplies.
 __device__ bool chol_solve4(const double *Hp, const double *g, double mu, double *x) {
-    double L[4][4] = {};
+    double L[4][4] = {}, rl[4];
     for (int a = 0; a < 4; ++a)
         for (int b = 0; b <= a; ++b) {
             double v = Hp[tri(b, a)];
@@ -182,28 +210,37 @@ __device__ bool chol_solve4(const double *Hp, const double *g, double mu, double
             if (a == b) {
                 if (!(v > 0.0)) return false;
                 L[a][a] = sqrt(v);
+                rl[a] = 1.0 / L[a][a];
             } else {
-                L[a][b] = v / L[b][b];
+                L[a][b] = v * rl[b];
             }
         }
     double z[4];
     for (int a = 0; a < 4; ++a) {
         double v = g[a];
         for (int k = 0; k < a; ++k) v -= L[a][k] * z[k];
-        z[a] = v / L[a][a];
+        z[a] = v * rl[a];
     }
     for (int a = 3; a >= 0; --a) {
         double v = z[a];
         for (int k = a + 1; k < 4; ++k) v -= L[k][a] * x[k];
-        x[a] = v / L[a][a];
+        x[a] = v * rl[a];
     }
     return true;
 }
 
 struct GnCfg {
     int max_iter;
-    double tol, scale[4];
+    double tol, rscale[4];   // 1 / scale
 };
+
+GnCfg gn_cfg(const EstState *E) {
+    GnCfg cfg;
+    cfg.max_iter = E->max_iter;
+    cfg.tol = E->tol;
+    for (int k = 0; k < 4; ++k) cfg.rscale[k] = 1.0 / E->scale[k];
+    return cfg;
+}
 
 __global__ void k_gn_step(GnState *__restrict__ S, const double *__restrict__ red, long n, const GnCfg cfg,
                           double *__restrict__ pt, int *__restrict__ n_active) {
@@ -239,7 +276,7 @@ __global__ void k_gn_step(GnState *__restrict__ S, const double *__restrict__ re
                 double d2 = 0.0;
                 for (int k = 0; k < 4; ++k) {
                     s.pt[k] = s.p[k] + dp[k];
-                    const double u = dp[k] / cfg.scale[k];
+                    const double u = dp[k] * cfg.rscale[k];
                     d2 += u * u;
                 }
                 s.dnorm = sqrt(d2);
@@ -292,6 +329,11 @@ cudaError_t est_reserve(EstState *E, long long cap, int per_sample) {
     if (cap <= E->cap) return cudaSuccess;
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return e;
+    est_drop_graphs(E);   // they hold the old buffers' addresses
+    cudaFree(E->ybuf);
+    cudaFreeHost(E->h_st);
+    E->ybuf = nullptr;
+    E->h_st = nullptr;
     cudaFree(E->maps);
     cudaFree(E->dmaps);
     cudaFree(E->red);
@@ -315,6 +357,8 @@ cudaError_t est_reserve(EstState *E, long long cap, int per_sample) {
     if ((e = cudaMalloc(&E->p0, sizeof(double) * 4 * cap)) != cudaSuccess) return e;
     if ((e = cudaMallocHost(&E->h_p, sizeof(double) * 4 * cap)) != cudaSuccess) return e;
     if ((e = cudaMallocHost(&E->h_r, sizeof(double) * 2 * cap)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&E->ybuf, sizeof(float) * per_sample * cap)) != cudaSuccess) return e;
+    if ((e = cudaMallocHost(&E->h_st, sizeof(GnState) * cap)) != cudaSuccess) return e;
     if (!E->n_active && (e = cudaMalloc(&E->n_active, sizeof(int))) != cudaSuccess) return e;
     if (!E->h_active && (e = cudaMallocHost(&E->h_active, sizeof(int))) != cudaSuccess) return e;
     E->cap = cap;
@@ -323,28 +367,42 @@ cudaError_t est_reserve(EstState *E, long long cap, int per_sample) {
 
 }  // namespace
 
+// One fit pass over n samples whose probe slopes are y: responses (and,
+// unless this is the last pass, tangents) at the trial points, the sums,
+// the step.  On pass max_iter every sample still running only judges its
+// trial point and stops, so that pass regenerates values alone and sums
+// r.r and y.y (the slots k_gn_step reads then).
+cudaError_t fit_pass(synim_ctx *c, const float *y, long long n, int pass, const GnCfg &cfg, cudaStream_t st) {
+    EstState *E = c->est;
+    const int per_sample = probe_per_sample(c->probe);
+    const int parts = reduce_parts(n, c->n_sm);
+    const dim3 grid((unsigned)parts, (unsigned)n);
+    cudaError_t e;
+    if (pass >= cfg.max_iter) {
+        if ((e = probe_launch(c, E->pt, n, E->maps, nullptr, nullptr, st)) != cudaSuccess) return e;
+        k_resid_reduce<<<grid, kRedThreads, 0, st>>>(y, E->maps, per_sample, parts, E->red_part);
+        k_red_combine<<<(unsigned)n, 64, 0, st>>>(E->red_part, parts, 2, E->red, kRed, kRed - 1);
+    } else {
+        if ((e = probe_launch(c, E->pt, n, E->maps, E->dmaps, nullptr, st)) != cudaSuccess) return e;
+        k_gn_reduce<<<grid, kRedThreads, 0, st>>>(y, E->maps, E->dmaps, n, per_sample, parts, E->red_part);
+        k_red_combine<<<(unsigned)n, 32 * kRed, 0, st>>>(E->red_part, parts, kRed, E->red, kRed, kRed - 1);
+    }
+    k_gn_step<<<(unsigned)((n + 63) / 64), 64, 0, st>>>(E->st, E->red, n, cfg, E->pt, E->n_active);
+    return cudaGetLastError();
+}
+
 // Fit n samples (n <= E->cap) from initial points p0 (device [n][4]); writes
 // the estimates to p_out (host [n][4]), the relative residual to res (host
 // [n], may be null) and the per-sample statistics.
 cudaError_t gn_fit(synim_ctx *c, const float *y, long long n, const double *p0, double *p_out, double *res,
                    int *iters, int *conv, cudaStream_t st) {
     EstState *E = c->est;
-    const int per_sample = probe_per_sample(c->probe);
-    GnCfg cfg;
-    cfg.max_iter = E->max_iter;
-    cfg.tol = E->tol;
-    for (int k = 0; k < 4; ++k) cfg.scale[k] = E->scale[k];
-    const unsigned nb = (unsigned)((n + 63) / 64);
-    const int parts = reduce_parts(n, c->n_sm);
-    k_gn_init<<<nb, 64, 0, st>>>(E->st, p0, n, E->pt);
+    const GnCfg cfg = gn_cfg(E);
+    k_gn_init<<<(unsigned)((n + 63) / 64), 64, 0, st>>>(E->st, p0, n, E->pt);
     cudaError_t e = cudaGetLastError();
-    for (int pass = 0; pass <= E->max_iter + 16 && e == cudaSuccess; ++pass) {
-        if ((e = probe_launch(c, E->pt, n, E->maps, E->dmaps, nullptr, st)) != cudaSuccess) break;
-        k_gn_reduce<<<dim3((unsigned)parts, (unsigned)n), kRedThreads, 0, st>>>(y, E->maps, E->dmaps, n, per_sample,
-                                                                                parts, E->red_part);
-        k_red_combine<<<(unsigned)n, 32 * kRed, 0, st>>>(E->red_part, parts, kRed, E->red);
+    for (int pass = 0; pass <= E->max_iter && e == cudaSuccess; ++pass) {
         if ((e = cudaMemsetAsync(E->n_active, 0, sizeof(int), st)) != cudaSuccess) break;
-        k_gn_step<<<nb, 64, 0, st>>>(E->st, E->red, n, cfg, E->pt, E->n_active);
+        if ((e = fit_pass(c, y, n, pass, cfg, st)) != cudaSuccess) break;
         if ((e = cudaMemcpyAsync(E->h_active, E->n_active, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
             break;
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) break;
@@ -367,6 +425,104 @@ cudaError_t gn_fit(synim_ctx *c, const float *y, long long n, const double *p0, 
 // CNN estimate of n samples (synim_cnn.cu): params_out device [n][4].
 cudaError_t cnn_predict_slopes(synim_ctx *c, const float *y, long long n, double *params_out, cudaStream_t st,
                                std::string &why);
+bool cnn_ready(const synim_ctx *c, std::string &why);
+
+// Small batches (the latency regime of a single estimate) spend most of
+// their time in launch gaps and per-pass host synchronisation.  For the
+// network alone (method 1) and the network plus a few fit passes (method 2,
+// max_iter <= kGraphMaxIter), the whole device chain of one batch size is
+// captured once as a CUDA graph reading the batch from E->ybuf and leaving
+// its results in pinned host memory: a call is one device copy, one graph
+// launch and one synchronisation.  The fit runs its max_iter + 1 passes
+// unconditionally; k_gn_step leaves stopped samples untouched, so the result
+// equals the host-driven loop's, which stops once no sample is active.
+constexpr long long kGraphMaxN = 32;
+constexpr int kGraphMaxIter = 4;
+
+cudaError_t small_chain(synim_ctx *c, int method, bool resid, long long n, cudaStream_t st) {
+    EstState *E = c->est;
+    std::string why;
+    cudaError_t e = cnn_predict_slopes(c, E->ybuf, n, E->p0, st, why);
+    if (e != cudaSuccess) return e;
+    const int per_sample = probe_per_sample(c->probe);
+    const int parts = reduce_parts(n, c->n_sm);
+    if (method == 1) {
+        if (resid) {
+            if ((e = probe_launch(c, E->p0, n, E->maps, nullptr, nullptr, st)) != cudaSuccess) return e;
+            k_resid_reduce<<<dim3((unsigned)parts, (unsigned)n), kRedThreads, 0, st>>>(E->ybuf, E->maps, per_sample,
+                                                                                       parts, E->red_part);
+            k_red_combine<<<(unsigned)n, 64, 0, st>>>(E->red_part, parts, 2, E->red, 2, 1);
+            if ((e = cudaMemcpyAsync(E->h_r, E->red, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, st)) !=
+                cudaSuccess)
+                return e;
+        }
+        if ((e = cudaMemcpyAsync(E->h_p, E->p0, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return e;
+        return cudaGetLastError();
+    }
+    const GnCfg cfg = gn_cfg(E);
+    const unsigned nb = (unsigned)((n + 63) / 64);
+    k_gn_init<<<nb, 64, 0, st>>>(E->st, E->p0, n, E->pt);
+    if ((e = cudaMemsetAsync(E->n_active, 0, sizeof(int), st)) != cudaSuccess) return e;
+    for (int pass = 0; pass <= E->max_iter; ++pass)
+        if ((e = fit_pass(c, E->ybuf, n, pass, cfg, st)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(E->h_st, E->st, sizeof(GnState) * n, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return e;
+    return cudaGetLastError();
+}
+
+// Run one small batch (y: device [n][per_sample]) through its cached graph,
+// capturing it on first use.  Results: hout [n][4], res [n] (may be null),
+// iters / conv [n] (method 2).
+cudaError_t small_estimate(synim_ctx *c, const float *y, long long n, int method, double *hout, double *res,
+                           int *iters, int *conv, cudaStream_t st) {
+    EstState *E = c->est;
+    cudaError_t e;
+    if ((e = probe_reserve(c, n)) != cudaSuccess) return e;
+    if (E->gen != c->est_gen) {
+        est_drop_graphs(E);
+        E->gen = c->est_gen;
+    }
+    if (!E->cap_st && (e = cudaStreamCreateWithFlags(&E->cap_st, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    const bool resid = method == 1 && res != nullptr;
+    const auto key = std::make_tuple(2 * method + (resid ? 1 : 0), n, method == 2 ? E->max_iter : 0);
+    auto it = E->graphs.find(key);
+    if (it == E->graphs.end()) {
+        EstState::Graph g;
+        if ((e = cudaStreamBeginCapture(E->cap_st, cudaStreamCaptureModeRelaxed)) != cudaSuccess) return e;
+        cudaError_t e1 = small_chain(c, method, resid, n, E->cap_st);
+        e = cudaStreamEndCapture(E->cap_st, &g.g);
+        if (e1 != cudaSuccess || e != cudaSuccess) {
+            if (g.g) cudaGraphDestroy(g.g);
+            cudaGetLastError();
+            return e1 != cudaSuccess ? e1 : e;
+        }
+        if ((e = cudaGraphInstantiate(&g.x, g.g, 0)) != cudaSuccess) {
+            cudaGraphDestroy(g.g);
+            return e;
+        }
+        it = E->graphs.emplace(key, g).first;
+    }
+    const int per_sample = probe_per_sample(c->probe);
+    if ((e = cudaMemcpyAsync(E->ybuf, y, sizeof(float) * per_sample * n, cudaMemcpyDeviceToDevice, st)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaGraphLaunch(it->second.x, st)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+    for (long long q = 0; q < n; ++q) {
+        if (method == 1) {
+            for (int k = 0; k < 4; ++k) hout[4 * q + k] = E->h_p[4 * q + k];
+            if (res) res[q] = E->h_r[2 * q + 1] > 0 ? std::sqrt(E->h_r[2 * q] / E->h_r[2 * q + 1]) : 0.0;
+        } else {
+            const GnState &g = E->h_st[q];
+            for (int k = 0; k < 4; ++k) hout[4 * q + k] = g.p[k];
+            if (res) res[q] = g.yy > 0 ? std::sqrt(g.c / g.yy) : 0.0;
+            iters[q] = g.it;
+            conv[q] = (g.flags & GN_CONV) ? 1 : 0;
+        }
+    }
+    return cudaSuccess;
+}
 
 }  // namespace synim
 
@@ -380,6 +536,7 @@ synim_status synim_gn_config(synim_ctx *ctx, int32_t max_iter, double tol, const
     if (max_iter < 1 || max_iter > 1000 || !(tol > 0.0))
         return efail(ctx, SYNIM_ERR_INVALID_ARG, "gn_config: max_iter in 1..1000, tol > 0");
     EstState *E = est_get(ctx);
+    ++ctx->est_gen;   // the captured fits hold the settings by value
     E->max_iter = max_iter;
     E->tol = tol;
     if (scale)
@@ -408,6 +565,21 @@ synim_status synim_misreg_estimate(synim_ctx *ctx, const float *probe_slopes, in
     if (e != cudaSuccess) return ecuda(ctx, e, "misreg_estimate scratch");
     double *p0 = E->p0;
     std::vector<double> hout((size_t)4 * chunk);
+    if (ctx->use_graph && n <= kGraphMaxN && (method == 1 || (method == 2 && E->max_iter <= kGraphMaxIter))) {
+        std::string why;
+        if (!cnn_ready(ctx, why)) return efail(ctx, SYNIM_ERR_NOT_TRAINED, "misreg_estimate: " + why);
+        e = small_estimate(ctx, probe_slopes, n, method, hout.data(), residual_out, E->iters.data(), E->conv.data(),
+                           st);
+        if (e != cudaSuccess) return ecuda(ctx, e, "misreg_estimate (graph)");
+        for (long long q = 0; q < n; ++q) {
+            synim_misreg &m = inout[q];
+            m.shift_x_px = hout[4 * q + 0];
+            m.shift_y_px = hout[4 * q + 1];
+            m.rot_deg = hout[4 * q + 2];
+            m.mag = hout[4 * q + 3];
+        }
+        return SYNIM_OK;
+    }
     synim_status status = SYNIM_OK;
     for (long long s0 = 0; s0 < n && status == SYNIM_OK; s0 += chunk) {
         const long long b = std::min(chunk, n - s0);
@@ -441,7 +613,7 @@ synim_status synim_misreg_estimate(synim_ctx *ctx, const float *probe_slopes, in
                     const int parts = reduce_parts(b, ctx->n_sm);
                     k_resid_reduce<<<dim3((unsigned)parts, (unsigned)b), kRedThreads, 0, st>>>(y, E->maps, per_sample,
                                                                                                parts, E->red_part);
-                    k_red_combine<<<(unsigned)b, 64, 0, st>>>(E->red_part, parts, 2, E->red);
+                    k_red_combine<<<(unsigned)b, 64, 0, st>>>(E->red_part, parts, 2, E->red, 2, 1);
                     e = cudaMemcpyAsync(E->h_r, E->red, sizeof(double) * 2 * b, cudaMemcpyDeviceToHost, st);
                 }
             }

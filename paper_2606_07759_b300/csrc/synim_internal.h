@@ -169,6 +169,8 @@ void probe_destroy(ProbeSet *p);
 cudaError_t probe_launch(synim_ctx *c, const double *params, long long n, float *maps, float *dmaps,
                          unsigned *peak, cudaStream_t st);
 int probe_per_sample(const ProbeSet *p);   // n_sub^2 x channels
+// Grow the probe scratch for n samples outside any stream capture.
+cudaError_t probe_reserve(synim_ctx *c, long long n);
 struct EstState;   // synim_estimate.cu
 void est_destroy(EstState *e);
 struct CnnState;   // synim_cnn.cu
@@ -231,4 +233,7 @@ struct synim_ctx {
     synim::ProbeSet *probe = nullptr;
     synim::EstState *est = nullptr;
     synim::CnnState *cnn = nullptr;
+    // bumped whenever a buffer or setting the estimator's captured graphs
+    // hold changes (probe attach or scratch growth, network init, GN config)
+    unsigned long long est_gen = 0;
 };

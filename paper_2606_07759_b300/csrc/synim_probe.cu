@@ -115,22 +115,58 @@ __global__ void k_form_screens(const DevDM D, const double *__restrict__ cmd, in
         if (m < NMP) dst[m] = (float)acc[m];
 }
 
-// Per-sample composite transform (Sec. 2.1) and its parameter derivatives.
-__global__ void k_probe_affine(const DmHost D, const WfsHost W, const double *__restrict__ params,
-                               long n, int with_jac, ProbeAff *__restrict__ out) {
+// The parts of the composite transform (Sec. 2.1) that depend on the pair
+// alone, formed on the host: the sensor's rotation-magnification matrix X =
+// R(theta_w) diag(mag_w), the conjugation factor times the sensor pixel,
+// the pair's translation before the misregistration, and the grid centres.
+struct AffPre {
+    double X00, X01, X10, X11;   // X
+    double cdw;                  // (1 - h / H) D_w / M
+    double tx0, ty0;             // (1 - h / H) shift_w + h theta_w
+    double dd, cN, cM;           // DM pitch; (N - 1) / 2, (M - 1) / 2
+};
+
+AffPre aff_pre(const DmHost &D, const WfsHost &W) {
+    AffPre a;
+    const double cone = (W.H > 0.0 && std::isfinite(W.H)) ? 1.0 - D.h / W.H : 1.0;
+    const double tw = W.rot * kPi / 180.0, cw = std::cos(tw), sw = std::sin(tw);
+    a.X00 = cw * W.mag[0];
+    a.X01 = -sw * W.mag[1];
+    a.X10 = sw * W.mag[0];
+    a.X11 = cw * W.mag[1];
+    a.cdw = cone * (W.D / W.M);
+    a.tx0 = cone * W.shift[0] + D.h * W.th[0];
+    a.ty0 = cone * W.shift[1] + D.h * W.th[1];
+    a.dd = D.dd;
+    a.cN = (D.N - 1) * 0.5;
+    a.cM = (W.M - 1) * 0.5;
+    return a;
+}
+
+// Per-sample composite transform (Sec. 2.1) and, with with_jac, its
+// parameter derivatives in closed form: the shifts translate by -R(-td) e /
+// mag; the rotation turns the map about the DM centre (dA = -J A, db = -J (b
+// - cN), J = [[0, -1], [1, 0]], per radian); the magnification scales it
+// about the DM centre (dA = -A / mag, db = -(b - cN) / mag).  One FP64 sincos
+// and one reciprocal per sample: FP64 is a narrow pipe on this part and the
+// kernel runs once per fit pass.
+__global__ void k_probe_affine(const AffPre Q, const double *__restrict__ params, long n, int with_jac,
+                               ProbeAff *__restrict__ out) {
     const long s = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
-    synim_misreg m;
-    m.shift_x_px = params[4 * s + 0];
-    m.shift_y_px = params[4 * s + 1];
-    m.rot_deg = params[4 * s + 2];
-    m.mag = params[4 * s + 3];
+    const double sx = params[4 * s + 0], sy = params[4 * s + 1], rot = params[4 * s + 2], mag = params[4 * s + 3];
+    double st, ct;
+    sincos(rot * (kPi / 180.0), &st, &ct);
+    const double inv = 1.0 / (Q.dd * mag), sc = Q.cdw * inv;
     ProbeAff P;
-    composite(D, W, m, P.A, P.b);
-    // the tangent terms only when tangents are asked for (another FP64 sine
-    // and cosine on a single thread per sample)
-    double dA[16] = {}, db[8] = {};
-    if (with_jac) composite_jac(D, m, P.A, P.b, dA, db);
+    // A = sc R(-td) X, R(-td) = [[ct, st], [-st, ct]]
+    P.A[0] = sc * (ct * Q.X00 + st * Q.X10);
+    P.A[1] = sc * (ct * Q.X01 + st * Q.X11);
+    P.A[2] = sc * (-st * Q.X00 + ct * Q.X10);
+    P.A[3] = sc * (-st * Q.X01 + ct * Q.X11);
+    const double tx = Q.tx0 - sx * Q.dd, ty = Q.ty0 - sy * Q.dd;
+    P.b[0] = Q.cN + inv * (ct * tx + st * ty) - (P.A[0] + P.A[1]) * Q.cM;
+    P.b[1] = Q.cN + inv * (-st * tx + ct * ty) - (P.A[2] + P.A[3]) * Q.cM;
     for (int q = 0; q < 4; ++q) {
         P.Ahi[q] = (float)P.A[q];
         P.Alo[q] = (float)(P.A[q] - (double)P.Ahi[q]);
@@ -139,8 +175,24 @@ __global__ void k_probe_affine(const DmHost D, const WfsHost W, const double *__
         P.bhi[q] = (float)P.b[q];
         P.blo[q] = (float)(P.b[q] - (double)P.bhi[q]);
     }
-    for (int q = 0; q < 16; ++q) P.dA[q] = (float)dA[q];
-    for (int q = 0; q < 8; ++q) P.db[q] = (float)db[q];
+    for (int q = 0; q < 16; ++q) P.dA[q] = 0.f;
+    for (int q = 0; q < 8; ++q) P.db[q] = 0.f;
+    if (with_jac) {
+        const double rm = 1.0 / mag, rad = kPi / 180.0;
+        P.db[0] = (float)(-ct * rm);
+        P.db[1] = (float)(st * rm);
+        P.db[2] = (float)(-st * rm);
+        P.db[3] = (float)(-ct * rm);
+        P.dA[8] = (float)(rad * P.A[2]);
+        P.dA[9] = (float)(rad * P.A[3]);
+        P.dA[10] = (float)(-rad * P.A[0]);
+        P.dA[11] = (float)(-rad * P.A[1]);
+        P.db[4] = (float)(rad * (P.b[1] - Q.cN));
+        P.db[5] = (float)(-rad * (P.b[0] - Q.cN));
+        for (int q = 0; q < 4; ++q) P.dA[12 + q] = (float)(-P.A[q] * rm);
+        P.db[6] = (float)(-(P.b[0] - Q.cN) * rm);
+        P.db[7] = (float)(-(P.b[1] - Q.cN) * rm);
+    }
     out[s] = P;
 }
 
@@ -504,11 +556,13 @@ cudaError_t ensure_aff(synim_ctx *c, ProbeSet *p, long long n) {
     const long long cap = std::max<long long>(n, 1024);
     e = cudaMalloc(&p->aff, sizeof(ProbeAff) * cap);
     if (e == cudaSuccess) p->aff_cap = cap;
-    (void)c;
+    ++c->est_gen;
     return e;
 }
 
 }  // namespace
+
+cudaError_t probe_reserve(synim_ctx *c, long long n) { return ensure_aff(c, c->probe, n); }
 
 // Launch the per-sample transforms and the probe kernel for n samples.
 cudaError_t probe_launch(synim_ctx *c, const double *params, long long n, float *maps, float *dmaps,
@@ -517,15 +571,22 @@ cudaError_t probe_launch(synim_ctx *c, const double *params, long long n, float 
     cudaError_t e = ensure_aff(c, p, n);
     if (e != cudaSuccess) return e;
     const int d = p->dm, w = p->wfs;
-    k_probe_affine<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(c->dmh[d], c->wh[w], params, n,
+    k_probe_affine<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(aff_pre(c->dmh[d], c->wh[w]), params, n,
                                                                dmaps != nullptr ? 1 : 0, p->aff);
     ProbeGeo G = p->geo;
     const bool tan = dmaps != nullptr;
     G.Cs = tan ? p->cs_tan : p->cs_fwd;
+    // a few samples (a single estimate) would leave most SMs idle: narrower
+    // chunks until there are about two CTAs per SM
+    const long long rows = n * G.n_sub, target = 2LL * c->n_sm;
+    if (rows * ((G.n_sub + G.Cs - 1) / G.Cs) < target) {
+        const long long chunks = std::min<long long>(G.n_sub, (target + rows - 1) / rows);
+        G.Cs = std::min(G.Cs, (int)((G.n_sub + chunks - 1) / chunks));
+    }
     G.n_chunks = (G.n_sub + G.Cs - 1) / G.Cs;
     const long long blocks = n * G.n_sub * G.n_chunks;
     if (blocks > INT_MAX) return cudaErrorInvalidValue;
-    const size_t sm = tan ? p->smem_tan : p->smem_fwd;
+    const size_t sm = probe_smem(G.k, G.Cs, tan ? 5 : 1, G.NMP);
     const unsigned nb = (unsigned)blocks;
 #define SYNIM_PROBE_LAUNCH(NV_, NMP_) \
     k_probe<NV_, NMP_><<<nb, kProbeThreads, sm, st>>>(G, p->aff, n, maps, NV_ == 5 ? dmaps : nullptr, peak)
@@ -573,6 +634,7 @@ synim_status synim_probe_attach(synim_ctx *ctx, int32_t dm, int32_t wfs, const d
                                                std::to_string(W.k) + ") exceeds the shared-memory cap");
     probe_destroy(ctx->probe);
     ctx->probe = nullptr;
+    ++ctx->est_gen;
     ProbeSet *p = new ProbeSet();
     p->dm = dm;
     p->wfs = wfs;

@@ -286,22 +286,24 @@ class SynIM:
 
         Returns (params [n, 4] float64, relative residual [n], iterations [n], converged [n]).
         """
-        y = torch.as_tensor(slopes).to(self.device, torch.float32).contiguous()
+        y = torch.as_tensor(slopes)
+        if y.device != self.device or y.dtype != torch.float32 or not y.is_contiguous():
+            y = y.to(self.device, torch.float32).contiguous()
         n = y.shape[0]
-        arr = (abi.synim_misreg * n)()
-        # default start: the prior centre nudged off the exact grid alignment
-        init = (np.tile([1e-3, 1e-3, 1e-3, 1.0 + 1e-5], (n, 1)) if init is None
-                else np.asarray(init, np.float64).reshape(n, 4))
-        for q in range(n):
-            arr[q] = abi.synim_misreg(*[float(v) for v in init[q]])
-        res = (ctypes.c_double * max(n, 1))()
-        abi.check(self._L.synim_misreg_estimate(self._ctx, ctypes.c_void_p(y.data_ptr()), n,
-                                                self.METHODS[method], arr, res, self._stream(stream)), self._ctx)
-        it = (ctypes.c_int32 * max(n, 1))()
-        cv = (ctypes.c_int32 * max(n, 1))()
-        abi.check(self._L.synim_misreg_estimate_stats(self._ctx, it, cv), self._ctx)
-        p = np.array([[a.shift_x_px, a.shift_y_px, a.rot_deg, a.mag] for a in arr]).reshape(n, 4)
-        return p, np.array(res[:n]), np.array(it[:n]), np.array(cv[:n], bool)
+        # synim_misreg is four doubles: an [n, 4] float64 array is its array
+        # (default start: the prior centre nudged off the exact grid alignment)
+        p = np.empty((max(n, 1), 4), np.float64)
+        p[:n] = (1e-3, 1e-3, 1e-3, 1.0 + 1e-5) if init is None else np.asarray(init, np.float64).reshape(n, 4)
+        res = np.zeros(max(n, 1))
+        it = np.zeros(max(n, 1), np.int32)
+        cv = np.zeros(max(n, 1), np.int32)
+        abi.check(self._L.synim_misreg_estimate(self._ctx, ctypes.c_void_p(y.data_ptr()), n, self.METHODS[method],
+                                                p.ctypes.data_as(ctypes.POINTER(abi.synim_misreg)),
+                                                res.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                                self._stream(stream)), self._ctx)
+        abi.check(self._L.synim_misreg_estimate_stats(self._ctx, it.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                                      cv.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))), self._ctx)
+        return p[:n], res[:n], it[:n], cv[:n].astype(bool)
 
     # ---- the learned estimator ----
     def cnn_n_params(self) -> int:
