@@ -54,7 +54,9 @@ typedef enum {
     SYNIM_ERR_CUDA = 4,        /* a CUDA runtime call failed (see synim_last_error) */
     SYNIM_ERR_TIMEOUT = 5,     /* a bounded device wait gave up (kernel returned early) */
     SYNIM_ERR_NOT_CONVERGED = 6,
-    SYNIM_ERR_NOT_TRAINED = 7
+    SYNIM_ERR_NOT_TRAINED = 7,
+    SYNIM_ERR_BOUNDS = 8       /* bounds-checked build only: an IM kernel index left its buffer;
+                                  the access was skipped (see synim_debug_bounds) */
 } synim_status;
 
 typedef struct synim_ctx synim_ctx;
@@ -191,6 +193,13 @@ synim_status synim_im_sensitivity(synim_ctx *ctx, const synim_misreg *mis, float
  */
 synim_status synim_im_vjp(synim_ctx *ctx, const synim_misreg *mis, const float *const *grad_im,
                           double *grad_p, void *cuda_stream);
+
+/* 1 if the library was built with -DSYNIM_DEBUG_BOUNDS: every global and
+ * shared-memory index of the IM kernels (k_im, k_tele) is tested against
+ * its buffer; an index outside skips the access and makes the next
+ * synim_im_check (or the no-allocation entry point) return
+ * SYNIM_ERR_BOUNDS.  0 for the release build. */
+int32_t synim_debug_bounds(void);
 
 /*
  * Synchronise cuda_stream and report whether any kernel of this context has
@@ -500,6 +509,23 @@ typedef struct {
  * Synchronous. */
 synim_status synim_cnn_train(synim_ctx *ctx, const double *params, int64_t n, const synim_train_opts *opts,
                              double *loss_out, void *cuda_stream);
+
+/*
+ * Checkpoint / resume of the network and its optimiser.  Layout (little-
+ * endian): a 128-byte header {char magic[8] = "SYNIMCNN"; uint32 version =
+ * 1; int32 n_sub, channels, step (Adam steps taken); int64 n_params; double
+ * center[4], range[4]; zero padding}, then FP32 parameters, Adam first
+ * moments and Adam second moments, [n_params] each.
+ * save: *bytes = the checkpoint's size; with buf (host, cap bytes) also
+ * writes it there (SYNIM_ERR_INVALID_ARG if cap is smaller).  Synchronous.
+ * load: replaces the context's network with the checkpoint's (as
+ * synim_cnn_init, then the moments and the step count), so that a training
+ * run resumed from a checkpoint continues exactly as the uninterrupted one.
+ * SYNIM_ERR_INVALID_ARG for a foreign or truncated buffer; SYNIM_ERR_SHAPE
+ * if its map shape differs from the attached probes'.  Synchronous.
+ */
+synim_status synim_cnn_save(const synim_ctx *ctx, void *buf, int64_t cap, int64_t *bytes);
+synim_status synim_cnn_load(synim_ctx *ctx, const void *buf, int64_t bytes);
 
 /* Launch shape chosen by the autotuner for mode 0 (IM), 1 (tangents) or 2
  * (adjoint): threads per CTA, lanes per boundary segment (telescoping

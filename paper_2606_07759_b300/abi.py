@@ -17,7 +17,7 @@ c_int32, c_int64, c_double, c_float, c_void_p = (ctypes.c_int32, ctypes.c_int64,
 SYNIM_OK = 0
 STATUS_NAMES = {0: "SYNIM_OK", 1: "SYNIM_ERR_INVALID_ARG", 2: "SYNIM_ERR_SHAPE", 3: "SYNIM_ERR_OOM",
                 4: "SYNIM_ERR_CUDA", 5: "SYNIM_ERR_TIMEOUT", 6: "SYNIM_ERR_NOT_CONVERGED",
-                7: "SYNIM_ERR_NOT_TRAINED"}
+                7: "SYNIM_ERR_NOT_TRAINED", 8: "SYNIM_ERR_BOUNDS"}
 
 
 class synim_dm_desc(ctypes.Structure):
@@ -105,6 +105,9 @@ SIGNATURES = {
     "synim_cnn_n_params": (c_int32, [c_int32, c_int32]),
     "synim_cnn_init": (c_int32, [c_void_p, ctypes.POINTER(c_float), ctypes.POINTER(c_double)]),
     "synim_cnn_get": (c_int32, [c_void_p, ctypes.POINTER(c_float), ctypes.POINTER(c_double)]),
+    "synim_debug_bounds": (c_int32, []),
+    "synim_cnn_save": (c_int32, [c_void_p, c_void_p, c_int64, ctypes.POINTER(c_int64)]),
+    "synim_cnn_load": (c_int32, [c_void_p, c_void_p, c_int64]),
     "synim_cnn_forward": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
     "synim_cnn_grad": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, ctypes.POINTER(c_double),
                                  ctypes.POINTER(c_float), c_void_p]),
@@ -125,17 +128,21 @@ def lib_path() -> str:
 
 
 def load():
-    """Load libsynim.so (building it first if it is missing or stale and nvcc exists)."""
+    """Load libsynim.so (building it first if it is missing or stale and nvcc
+    exists); with SYNIM_DEBUG_BOUNDS=1 in the environment, the bounds-checked
+    build libsynim_bounds.so instead."""
     global _lib
     if _lib is not None:
         return _lib
-    if _build.stale():
+    bounds = os.environ.get("SYNIM_DEBUG_BOUNDS", "0") == "1"
+    lib = _build.lib_path(bounds)
+    if _build.stale(bounds):
         if shutil.which(_build.NVCC) or os.path.exists(_build.NVCC):
-            _build.build()
-        elif not os.path.exists(_build.LIB):
-            raise RuntimeError("libsynim.so is not built and nvcc is unavailable: the CUDA path "
+            _build.build(bounds=bounds)
+        elif not os.path.exists(lib):
+            raise RuntimeError(os.path.basename(lib) + " is not built and nvcc is unavailable: the CUDA path "
                                "cannot run (there is no CPU fallback)")
-    L = ctypes.CDLL(_build.LIB)
+    L = ctypes.CDLL(lib)
     for name, (res, args) in SIGNATURES.items():
         f = getattr(L, name)
         f.restype = res

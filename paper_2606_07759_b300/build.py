@@ -1,6 +1,9 @@
-"""Build libsynim.so (the sm_103a CUDA library behind include/synim.h) in-tree.
+"""Build libsynim.so (the sm_103a CUDA library behind include/synim.h) in-tree,
+and its bounds-checked twin libsynim_bounds.so (-DSYNIM_DEBUG_BOUNDS: every
+index of the IM kernels tested against its buffer; loaded instead of the
+release library when SYNIM_DEBUG_BOUNDS=1 is set in the environment).
 
-    python -m paper_2606_07759_b300.build [--force]
+    python -m paper_2606_07759_b300.build [--force] [--bounds]
 
 nvcc cross-compiles for compute_103a/sm_103a; no GPU is needed to build.
 """
@@ -16,6 +19,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libsynim.so")
+LIB_BOUNDS = os.path.join(PKG, "libsynim_bounds.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 
 NVCC_FLAGS = [
@@ -35,17 +39,24 @@ def _deps():
     return sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
-def stale() -> bool:
-    if not os.path.exists(LIB):
+def lib_path(bounds: bool = False) -> str:
+    return LIB_BOUNDS if bounds else LIB
+
+
+def stale(bounds: bool = False) -> bool:
+    lib = lib_path(bounds)
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not stale():
-        return LIB
-    cmd = [NVCC, *NVCC_FLAGS, "-I", INCLUDE, "-I", CSRC, "-o", LIB + ".tmp", *sources()]
+def build(force: bool = False, verbose: bool = False, bounds: bool = False) -> str:
+    lib = lib_path(bounds)
+    if not force and not stale(bounds):
+        return lib
+    flags = NVCC_FLAGS + (["-DSYNIM_DEBUG_BOUNDS"] if bounds else [])
+    cmd = [NVCC, *flags, "-I", INCLUDE, "-I", CSRC, "-o", lib + ".tmp", *sources()]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -53,10 +64,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
         raise RuntimeError("nvcc failed:\n" + r.stdout + r.stderr)
     if verbose:
         sys.stderr.write(r.stderr)
-    os.replace(LIB + ".tmp", LIB)
-    return LIB
+    os.replace(lib + ".tmp", lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose="-v" in sys.argv)
-    print(LIB)
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, bounds="--bounds" in sys.argv))

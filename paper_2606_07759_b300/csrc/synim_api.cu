@@ -592,6 +592,7 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
         G.xcode = xc; G.ycode = yc; G.irr_pix = ip; G.irr_w = iw; G.irr_sub = is;
         G.fac = fa; G.vsub = vs; G.vrow = vr;
         G.n_sub = H.n_sub; G.M = H.M; G.k = H.k; G.nv = H.nv; G.CH = H.CH;
+        G.n_irr = (int)T.irr_pix.size();
         if (c->slope_engine == SYNIM_ENGINE_TELESCOPING) {
             TeleTables TT;
             build_tele_tables(Wd, T, TT);
@@ -604,6 +605,7 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
             if (e == cudaSuccess) e = dev_upload(c, &tf, TT.fac);
             if (e != cudaSuccess) return bail(cuda_fail(c, e, "telescoping edge tables"));
             DT.es = es; DT.ev = ev; DT.fac = tf; DT.vfirst = vf;
+            DT.n_ev = (int)TT.ev.size();
             // a full subaperture has 4 k events: at most sixteen per lane
             int L = 1;
             while (L < 32 && 4 * L < H.k) L *= 2;
@@ -719,6 +721,14 @@ synim_status synim_pair_affine(const synim_ctx *ctx, int32_t dm, int32_t wfs,
     return SYNIM_OK;
 }
 
+int32_t synim_debug_bounds(void) {
+#ifdef SYNIM_DEBUG_BOUNDS
+    return 1;
+#else
+    return 0;
+#endif
+}
+
 synim_status synim_im_check(synim_ctx *ctx, void *cuda_stream) {
     if (!ctx) return SYNIM_ERR_INVALID_ARG;
     DeviceGuard guard(ctx->device);
@@ -731,6 +741,7 @@ synim_status synim_im_check(synim_ctx *ctx, void *cuda_stream) {
     cudaMemset(ctx->d_err, 0, sizeof(int));
     if (flag & ERR_TIMEOUT) return fail(ctx, SYNIM_ERR_TIMEOUT, "a bounded device wait timed out");
     if (flag & ERR_ARENA) return fail(ctx, SYNIM_ERR_SHAPE, "slope values exceeded their shared-memory buffer");
+    if (flag & ERR_BOUNDS) return fail(ctx, SYNIM_ERR_BOUNDS, "an IM kernel index left its buffer (access skipped)");
     return SYNIM_OK;
 }
 

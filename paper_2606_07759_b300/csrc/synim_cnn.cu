@@ -1616,6 +1616,85 @@ synim_status synim_cnn_get(const synim_ctx *ctx, float *params, double *norm) {
     return SYNIM_OK;
 }
 
+// Checkpoint: a 128-byte little-endian header, then the FP32 parameters,
+// Adam first and second moments ([n_params] each).
+struct CnnCkpt {
+    char magic[8];         // "SYNIMCNN"
+    uint32_t version;      // 1
+    int32_t n_sub, channels, step;
+    int64_t n_params;
+    double norm[8];        // center[4], range[4]
+    uint8_t reserved[128 - 8 - 4 - 12 - 8 - 64];
+};
+static_assert(sizeof(CnnCkpt) == 128, "checkpoint header is 128 bytes");
+constexpr char kCkptMagic[8] = {'S', 'Y', 'N', 'I', 'M', 'C', 'N', 'N'};
+
+synim_status synim_cnn_save(const synim_ctx *ctx, void *buf, int64_t cap, int64_t *bytes) {
+    if (!ctx || !ctx->cnn || !bytes) return SYNIM_ERR_INVALID_ARG;
+    const CnnState *S = ctx->cnn;
+    const int64_t total = (int64_t)sizeof(CnnCkpt) + 3 * (int64_t)sizeof(float) * S->n_params;
+    *bytes = total;
+    if (!buf) return SYNIM_OK;
+    if (cap < total) return SYNIM_ERR_INVALID_ARG;
+    CnnCkpt h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, kCkptMagic, 8);
+    h.version = 1;
+    h.n_sub = S->H0;
+    h.channels = S->C0;
+    h.step = S->step;
+    h.n_params = S->n_params;
+    for (int k = 0; k < 4; ++k) {
+        h.norm[k] = S->center[k];
+        h.norm[4 + k] = S->range[k];
+    }
+    unsigned char *out = static_cast<unsigned char *>(buf);
+    std::memcpy(out, &h, sizeof(h));
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != ctx->device) cudaSetDevice(ctx->device);
+    const size_t P = sizeof(float) * (size_t)S->n_params;
+    cudaError_t e = cudaMemcpy(out + sizeof(h), S->master, P, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(out + sizeof(h) + P, S->adam_m, P, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(out + sizeof(h) + 2 * P, S->adam_v, P, cudaMemcpyDeviceToHost);
+    if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
+    return e == cudaSuccess ? SYNIM_OK : SYNIM_ERR_CUDA;
+}
+
+synim_status synim_cnn_load(synim_ctx *ctx, const void *buf, int64_t bytes) {
+    if (!ctx) return SYNIM_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (!buf || bytes < (int64_t)sizeof(CnnCkpt))
+        return cfail(ctx, SYNIM_ERR_INVALID_ARG, "cnn_load: no buffer or shorter than the header");
+    CnnCkpt h;
+    std::memcpy(&h, buf, sizeof(h));
+    if (std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 1)
+        return cfail(ctx, SYNIM_ERR_INVALID_ARG, "cnn_load: not a version-1 network checkpoint");
+    if (!ctx->probe) return cfail(ctx, SYNIM_ERR_INVALID_ARG, "cnn_load: attach probes first");
+    int n_sub = 0, C = 0;
+    synim_probe_query(ctx, &n_sub, &C, nullptr);
+    if (h.n_sub != n_sub || h.channels != C || h.n_params != cnn_n_params(C, n_sub))
+        return cfail(ctx, SYNIM_ERR_SHAPE, "cnn_load: the checkpoint's map shape differs from the attached probes'");
+    if (h.step < 0 || bytes < (int64_t)sizeof(CnnCkpt) + 3 * (int64_t)sizeof(float) * h.n_params)
+        return cfail(ctx, SYNIM_ERR_INVALID_ARG, "cnn_load: truncated checkpoint");
+    const unsigned char *in = static_cast<const unsigned char *>(buf) + sizeof(CnnCkpt);
+    const size_t P = sizeof(float) * (size_t)h.n_params;
+    std::vector<float> w((size_t)h.n_params);
+    std::memcpy(w.data(), in, P);
+    synim_status st = synim_cnn_init(ctx, w.data(), h.norm);
+    if (st != SYNIM_OK) return st;
+    CnnState *S = ctx->cnn;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != ctx->device) cudaSetDevice(ctx->device);
+    cudaError_t e = cudaMemcpy(S->adam_m, in + P, P, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(S->adam_v, in + 2 * P, P, cudaMemcpyHostToDevice);
+    if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
+    if (e != cudaSuccess) return ccuda(ctx, e, "cnn_load");
+    S->step = h.step;
+    return SYNIM_OK;
+}
+
 synim_status synim_cnn_forward(synim_ctx *ctx, const uint16_t *x, int64_t n, float *out, void *cuda_stream) {
     if (!ctx) return SYNIM_ERR_INVALID_ARG;
     ctx->err.clear();

@@ -59,6 +59,7 @@ struct DevWFS {
     const int *vidx;       // [n_sub * n_sub] valid row of each subaperture, -1 if invalid
     const int *vrow;       // [n_sub + 1] first valid row of each subaperture row
     int n_sub, M, k, nv, CH;
+    int n_irr;             // entries of irr_pix (an upper bound where the tables are built on the device)
 };
 
 // Edge tables of the telescoping-sum engine (Sec. 2.2), per sensor.  Each
@@ -78,6 +79,7 @@ struct DevTele {
     const int *vfirst;   // [n_sub][n_sub + 1] valid row of the first valid subaperture at
                          // or right of column sj in row si (vrow[si + 1] if none)
     int lanes;           // lanes that share one subaperture's events (1 .. 32, a power of 2)
+    int n_ev;            // entries of ev
 };
 
 struct TeleSet {
@@ -109,7 +111,18 @@ struct Geo {
     int seg_lanes;       // lanes per boundary segment for k <= 32 (2, 4 or 8); 0 = by k
 };
 
-enum { ERR_TIMEOUT = 1, ERR_ARENA = 2 };
+enum { ERR_TIMEOUT = 1, ERR_ARENA = 2, ERR_BOUNDS = 4 };
+
+// Debug builds (-DSYNIM_DEBUG_BOUNDS) test the index of each global and
+// shared-memory access of the IM kernels against its buffer: an index
+// outside sets ERR_BOUNDS in the context's error flag (surfaced by
+// synim_im_check) and the access is skipped.  Release builds compile the
+// tests away (the error pointer is not even evaluated).
+#ifdef SYNIM_DEBUG_BOUNDS
+#define SYNIM_IDX_OK(cond, errp) ((cond) ? true : (atomicOr((errp), ERR_BOUNDS), false))
+#else
+#define SYNIM_IDX_OK(cond, errp) true
+#endif
 
 enum Mode { MODE_FWD = 0, MODE_TAN = 1, MODE_VJP = 2 };
 

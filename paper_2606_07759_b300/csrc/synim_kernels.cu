@@ -298,6 +298,10 @@ struct Eval {
     int Wp, M, pi0, pj0;
     float Wf1, xo, yo, a00, a01, a10, a11;
     float dxo[NT], dyo[NT], da[4 * NT];
+#ifdef SYNIM_DEBUG_BOUNDS
+    int *err;   // the context's error flag
+    long wn;    // floats of this actuator's packed window
+#endif
 
     __device__ __forceinline__ void load(const ItemWfs &s, const float *w, int wp, int W, int m) {
         win = w; pst = s.pst; Wp = wp; M = m; pi0 = s.pi0; pj0 = s.pj0;
@@ -325,6 +329,11 @@ struct Eval {
         const float fx0 = floorf(x), fy0 = floorf(y);
         const int ix = (int)fx0, iy = (int)fy0;
         const float fx = x - fx0, fy = y - fy0;
+        if (!SYNIM_IDX_OK(ix >= 0 && iy >= 0 && (long)iy * Wp + ix + Wp + 1 < wn, err)) {
+#pragma unroll
+            for (int t = 0; t < NV; ++t) v[t] = 0.f;
+            return;
+        }
         const float *q = win + iy * Wp + ix;
         const float v00 = q[0], v10 = q[1], v01 = q[Wp], v11 = q[Wp + 1];
         const float ex = v10 - v00, ex1 = v11 - v01;
@@ -346,6 +355,7 @@ struct Eval {
         if (!(x > 0.f && x < Wf1 && y > 0.f && y < Wf1)) return 0.f;
         const float fx0 = floorf(x), fy0 = floorf(y);
         const float fx = x - fx0, fy = y - fy0;
+        if (!SYNIM_IDX_OK(fx0 >= 0.f && fy0 >= 0.f && (long)fy0 * Wp + (long)fx0 + Wp + 1 < wn, err)) return 0.f;
         const float *q = win + (int)fy0 * Wp + (int)fx0;
         const float v00 = q[0], v10 = q[1], v01 = q[Wp], v11 = q[Wp + 1];
         const float top = fmaf(fx, v10 - v00, v00), bot = fmaf(fx, v11 - v01, v01);
@@ -478,7 +488,7 @@ __device__ void make_info(const Geo &g, const DevPair *__restrict__ pairs, int d
 // the one after (bits 1 and 3); the slope of subaperture s along x is then
 // A(b = sj + 1) - B(b = sj) plus its pupil-edge pixels.
 struct SegRows {
-    int ua, ub, l0, inmask;
+    int ua, ub, l0, inmask, b;
     const uint8_t *cc;
 };
 
@@ -492,6 +502,7 @@ __device__ __forceinline__ SegRows seg_rows(const DevWFS &WF, const ItemWfs &s, 
     const int c0 = axis ? s.pi0 : s.pj0, c1 = axis ? s.pi1 : s.pj1;
     r.inmask = ((r.l0 >= c0 && r.l0 <= c1) ? 1 : 0) | ((r.l0 + 1 >= c0 && r.l0 + 1 <= c1) ? 2 : 0);
     r.cc = (axis ? s.ycc : s.xcc) + b;
+    r.b = b;
     return r;
 }
 
@@ -501,6 +512,10 @@ __device__ __forceinline__ void seg_compute(const DevWFS &WF, const SegRows &r, 
                                             int lane0, int lstep, float *A, float *B) {
     if (!r.inmask) return;
     const int n1 = WF.n_sub + 1, l0 = r.l0, inmask = r.inmask;
+    // line bytes [u][b]: rows ua .. ub of the sensor, boundary b <= n_sub;
+    // line pixels l0, l0 + 1 inside the sensor where their class is read
+    if (!SYNIM_IDX_OK(r.ua >= 0 && r.ub < WF.M && r.b >= 0 && r.b < n1 && l0 >= -1 && l0 + 1 <= WF.M, ev.err))
+        return;
     const int u0 = r.ua + lane0;
     if (u0 > r.ub) return;
     const uint8_t *cp = r.cc + (long)u0 * n1;
@@ -583,11 +598,16 @@ __device__ __forceinline__ void edge_sum(const DevWFS &WF, const ItemWfs &s, con
     const int ra = max(si * k, s.pi0), rb = min(si * k + k - 1, s.pi1);
     if (ra > rb) return;
     const long sr = (long)(si * WF.n_sub + sj) * k - (long)si * k;
+    if (!SYNIM_IDX_OK(si >= 0 && sj >= 0 && si < WF.n_sub && sj < WF.n_sub && sr + ra >= 0 &&
+                      sr + rb + 1 <= (long)WF.n_sub * WF.n_sub * k, ev.err))
+        return;
     const int e0 = WF.irr_sr[sr + ra], e1 = WF.irr_sr[sr + rb + 1];
+    if (!SYNIM_IDX_OK(e0 >= 0 && e1 <= WF.n_irr, ev.err)) return;
     for (int e = e0 + lane0; e < e1; e += lstep) {
         const int pix = WF.irr_pix[e];
         const int i = pix >> 16, j = pix & 0xffff;
         if (j < s.pj0 || j > s.pj1) continue;
+        if (!SYNIM_IDX_OK(i >= 0 && i < WF.M && j < WF.M, ev.err)) continue;
         const float wx = WF.irr_w[2 * e], wy = WF.irr_w[2 * e + 1];
         float v[NV];
 #pragma unroll
@@ -705,7 +725,10 @@ __device__ __forceinline__ void warp_column(const Geo &g, const DevPair *__restr
         s.empty = 1;
     }
     const bool vec4 = P.vec4 != 0;
+    if (!s.empty && !SYNIM_IDX_OK(s.si0 >= 0 && s.si1 < WF.n_sub && s.sj0 >= 0 && s.sj1 < WF.n_sub, err))
+        return;
     const int vr0 = s.empty ? 0 : WF.vrow[s.si0], vr1 = s.empty ? 0 : WF.vrow[s.si1 + 1];
+    if (!SYNIM_IDX_OK(0 <= vr0 && vr0 <= vr1 && vr1 <= nv, err)) return;
     constexpr int NOUT = (MODE == MODE_FWD) ? 1 : (MODE == MODE_TAN ? 5 : 0);
     float *cols[NOUT > 0 ? NOUT : 1];
     if (MODE != MODE_VJP) {
@@ -730,6 +753,10 @@ __device__ __forceinline__ void warp_column(const Geo &g, const DevPair *__restr
     float gacc[4] = {0.f, 0.f, 0.f, 0.f};
     Eval<NV> ev;
     ev.load(s, D.win + (size_t)a * D.win_stride, D.Wp, D.W, WF.M);
+#ifdef SYNIM_DEBUG_BOUNDS
+    ev.err = err;
+    ev.wn = D.win_stride;
+#endif
     float *segx = wbuf;                                // [nsj + 1][2][NV]
     float *sy0 = wbuf + (size_t)(nsj + 1) * 2 * NV;    // row boundary above the row: [nsj][2][NV]
     float *sy1 = sy0 + (size_t)nsj * 2 * NV;           // row boundary below it
@@ -786,6 +813,7 @@ __device__ __forceinline__ void warp_column(const Geo &g, const DevPair *__restr
             const int sj = s.sj0 + c;
             const int r = WF.vidx[si * WF.n_sub + sj];
             if (r < 0) continue;
+            if (!SYNIM_IDX_OK(r < nv, err)) continue;
             rlo = min(rlo, r);
             rhi = max(rhi, r);
             float vx[NV], vy[NV];
@@ -935,7 +963,11 @@ __device__ __forceinline__ void tele_column(const Geo &g, const DevTele &T, cons
         if (lane == 0) atomicOr(err, ERR_ARENA);
         s.empty = 1;
     }
+    if (!s.empty && !SYNIM_IDX_OK(s.si0 >= 0 && s.si1 < WF.n_sub && s.sj0 >= 0 && s.sj1 < WF.n_sub &&
+                                  (long)(2 * s.nsj) <= cap4, err))
+        return;
     const int vr0 = s.empty ? 0 : WF.vrow[s.si0], vr1 = s.empty ? 0 : WF.vrow[s.si1 + 1];
+    if (!SYNIM_IDX_OK(0 <= vr0 && vr0 <= vr1 && vr1 <= nv, err)) return;
     if (P.vec4) {
         bulk_zero(col, 0, vr0, lane);
         bulk_zero(col, vr1, nv + vr0, lane);
@@ -957,6 +989,10 @@ __device__ __forceinline__ void tele_column(const Geo &g, const DevTele &T, cons
     }
     Eval<1> E;
     E.load(s, D.win + (size_t)a * D.win_stride, D.Wp, D.W, WF.M);
+#ifdef SYNIM_DEBUG_BOUNDS
+    E.err = err;
+    E.wn = D.win_stride;
+#endif
     const int L = T.lanes, per = 32 / L, grp = lane / L, q = lane - grp * L;
     const int bi = 2 * s.pi0 + 1, bj = 2 * s.pj0 + 1;
     const int nsj = s.nsj, n = WF.n_sub;
@@ -973,14 +1009,15 @@ __device__ __forceinline__ void tele_column(const Geo &g, const DevTele &T, cons
                 r = vchunk[ri * n + (t - ri * nsj)];
             }
             float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (r >= 0) tele_events(T.ev, T.es[r], T.es[r + 1], E, bi, bj, q, L, acc);
+            if (r >= 0 && SYNIM_IDX_OK(r < nv && T.es[r] >= 0 && T.es[r + 1] <= T.n_ev, err))
+                tele_events(T.ev, T.es[r], T.es[r + 1], E, bi, bj, q, L, acc);
             for (int o = L >> 1; o > 0; o >>= 1) {
                 acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
                 acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
                 acc.z += __shfl_xor_sync(0xffffffffu, acc.z, o);
                 acc.w += __shfl_xor_sync(0xffffffffu, acc.w, o);
             }
-            if (q == 0 && t < nb) wbuf[nsj + t] = acc;
+            if (q == 0 && t < nb && SYNIM_IDX_OK(nsj + t < cap4, err)) wbuf[nsj + t] = acc;
         }
         __syncwarp();
         // x slopes of the chunk's rows, y slopes of the rows above them
@@ -988,10 +1025,11 @@ __device__ __forceinline__ void tele_column(const Geo &g, const DevTele &T, cons
             const int ri = t / nsj, c = t - ri * nsj;
             const float4 me = wbuf[nsj + t];
             const int r = vchunk[ri * n + c];
-            if (r >= 0) col[r] = (me.x + (c + 1 < nsj ? wbuf[nsj + t + 1].z : 0.f)) * T.fac[r];
+            if (r >= 0 && SYNIM_IDX_OK(r < nv, err))
+                col[r] = (me.x + (c + 1 < nsj ? wbuf[nsj + t + 1].z : 0.f)) * T.fac[r];
             if (sc + ri > s.si0) {
                 const int rp = vchunk[(ri - 1) * n + c];
-                if (rp >= 0) col[nv + rp] = (wbuf[t].y + me.w) * T.fac[rp];
+                if (rp >= 0 && SYNIM_IDX_OK(rp < nv, err)) col[nv + rp] = (wbuf[t].y + me.w) * T.fac[rp];
             }
         }
         __syncwarp();
@@ -1002,7 +1040,7 @@ __device__ __forceinline__ void tele_column(const Geo &g, const DevTele &T, cons
     const int *vlast = WF.vidx + s.si1 * n + s.sj0;
     for (int c = lane; c < nsj; c += 32) {
         const int rp = vlast[c];
-        if (rp >= 0) col[nv + rp] = wbuf[c].y * T.fac[rp];
+        if (rp >= 0 && SYNIM_IDX_OK(rp < nv, err)) col[nv + rp] = wbuf[c].y * T.fac[rp];
     }
     __syncwarp();
 }

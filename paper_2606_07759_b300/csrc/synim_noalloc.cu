@@ -471,6 +471,7 @@ extern "C" synim_status synim_im_compute_noalloc(const synim_dm_desc *dm, const 
     F.xcode = xcode; F.ycode = ycode; F.irr_pix = irrpix; F.irr_w = irrw; F.irr_sub = irrsub;
     F.fac = fac; F.vsub = vsub; F.vrow = vrow; F.irrc = irrc; F.irrc_row = irrcrow; F.irr_sr = irrsr; F.vsj = vsj; F.vidx = ros;
     F.n_sub = n; F.M = M; F.k = k; F.nv = nv; F.CH = Wh.CH;
+    F.n_irr = M * M;   // the capacity of irr_pix in the layout
     g.n_dm = 1; g.n_wfs = 1; g.n_items = n_act;
     g.order_dm[0] = 0; g.order_start[0] = 0; g.order_start[1] = n_act;
     g.seg_floats = (int)seg;
@@ -492,5 +493,6 @@ extern "C" synim_status synim_im_compute_noalloc(const synim_dm_desc *dm, const 
         return na_fail(SYNIM_ERR_CUDA, cudaGetErrorString(e));
     if (err_flag & ERR_TIMEOUT) return na_fail(SYNIM_ERR_TIMEOUT, "a bounded device wait timed out");
     if (err_flag & ERR_ARENA) return na_fail(SYNIM_ERR_SHAPE, "slope values exceeded their shared-memory buffer");
+    if (err_flag & ERR_BOUNDS) return na_fail(SYNIM_ERR_BOUNDS, "an IM kernel index left its buffer (access skipped)");
     return SYNIM_OK;
 }

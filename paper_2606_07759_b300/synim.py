@@ -324,6 +324,28 @@ class SynIM:
                                         norm.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), self._ctx)
         return w, norm[:4], norm[4:]
 
+    def cnn_save(self, path=None) -> bytes:
+        """Checkpoint of the network and its Adam state (synim_cnn_save); written
+        to path when given.  Returns the bytes."""
+        n = ctypes.c_int64()
+        abi.check(self._L.synim_cnn_save(self._ctx, None, 0, ctypes.byref(n)), self._ctx)
+        buf = np.zeros(n.value, np.uint8)
+        abi.check(self._L.synim_cnn_save(self._ctx, buf.ctypes.data_as(ctypes.c_void_p), n.value, ctypes.byref(n)),
+                  self._ctx)
+        data = buf.tobytes()
+        if path is not None:
+            with open(path, "wb") as f:
+                f.write(data)
+        return data
+
+    def cnn_load(self, src):
+        """Restore a checkpoint (bytes, or a path to a file written by cnn_save)."""
+        if not isinstance(src, (bytes, bytearray)):
+            with open(src, "rb") as f:
+                src = f.read()
+        buf = np.frombuffer(bytes(src), np.uint8)
+        abi.check(self._L.synim_cnn_load(self._ctx, buf.ctypes.data_as(ctypes.c_void_p), buf.size), self._ctx)
+
     def cnn_forward(self, x, stream=None):
         """Normalised outputs [n, 4] for bfloat16 maps x [n, n_sub, n_sub, C]."""
         x = x.to(self.device, torch.bfloat16).contiguous()

@@ -108,3 +108,56 @@ def test_training_reduces_the_loss():
     w, c, r = s.cnn_get()
     assert np.isfinite(w).all()
     s.close()
+
+
+def test_checkpoint_resume_equals_uninterrupted(tmp_path):
+    """A run saved after its first training call and resumed in a fresh
+    context (parameters, Adam moments and step count restored) ends with
+    the same parameters, bit for bit, as the uninterrupted run; foreign,
+    truncated and wrong-shape checkpoints are refused."""
+    import struct
+    from paper_2606_07759_b300 import abi
+    from paper_2606_07759_b300.synim import SynIM, cnn_init_params
+    wl, cmd = W.learned()
+    P0 = cnn_init_params(32, seed=8, input_scale=0.2)
+    rng = np.random.default_rng(9)
+    p1 = W.random_misregs(rng, 1024, 8.0, 2.0, 0.02)
+    p2 = W.random_misregs(rng, 1024, 8.0, 2.0, 0.02)
+
+    def fresh():
+        s = SynIM(wl.dms, wl.wfss)
+        s.probe_attach(0, 0, cmd)
+        return s
+
+    a = fresh()
+    a.cnn_init(P0, NORM_C, NORM_R)
+    a.cnn_train(p1, epochs=1, batch=128, lr=2e-3, seed=6)
+    ck = a.cnn_save(tmp_path / "net.ckpt")
+    a.cnn_train(p2, epochs=1, batch=128, lr=2e-3, seed=7)
+    wa, ca, ra = a.cnn_get()
+    a.close()
+
+    magic, version, n_sub, ch, step, n_params = struct.unpack_from("<8sIiiiq", ck, 0)
+    assert (magic, version, n_sub, ch, step) == (b"SYNIMCNN", 1, 40, 32, 1024 // 128)
+    assert n_params == P0.size and len(ck) == 128 + 3 * 4 * P0.size
+    np.testing.assert_array_equal(np.frombuffer(ck, np.float64, 8, 32), list(NORM_C) + list(NORM_R))
+
+    b = fresh()
+    b.cnn_load(tmp_path / "net.ckpt")
+    assert b.cnn_save() == ck                       # the round trip is exact
+    b.cnn_train(p2, epochs=1, batch=128, lr=2e-3, seed=7)
+    wb, cb, rb = b.cnn_get()
+    np.testing.assert_array_equal(wb, wa)
+    np.testing.assert_array_equal(cb, ca)
+    np.testing.assert_array_equal(rb, ra)
+    for bad in (b"XXXXXXXX" + ck[8:], ck[:-4], ck[:100]):
+        with pytest.raises(abi.SynimError) as e:
+            b.cnn_load(bad)
+        assert e.value.status == 1
+    b.close()
+    c = SynIM(wl.dms, wl.wfss)
+    c.probe_attach(0, 0, np.vstack([cmd, cmd]))     # 32 modes: 64 channels
+    with pytest.raises(abi.SynimError) as e:
+        c.cnn_load(ck)
+    assert e.value.status == 2
+    c.close()
