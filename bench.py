@@ -37,10 +37,13 @@ from paper_2606_07759_b300 import workloads as W  # noqa: E402
 METRIC = "IM actuator-columns/s at <=1e-5 rel err vs FP64 oracle; % of HBM roofline"
 UNIT = "columns/s"
 
-# DRAM bytes (read + write) of one k_im launch on the MCAO workload, from the
-# one-pass ncu capture summarised in profiles/k_im_mcao_dram_full.md; valid only
-# for the kernel source whose hash (kernel_sha1) is recorded with it.
-TRAFFIC = {"kernel_sha1": "25c205469dbd4e672ab2a3c20cebf5fc934b942e", "bytes_per_launch": 138.84e6 + 1.3309e9}
+# DRAM bytes (read + write) of one k_im launch on the full MCAO workload:
+# the ncu counters of the scale-0.6 launch (50.23 MB read + 129.34 MB
+# written, profiles/k_im_mcao_scale06_dram.md) times the ratio of the two
+# launches' algorithmic bytes (1507.1 / 233.3 MB).  Valid only for the kernel
+# source whose hash (kernel_sha1) is recorded with it.
+TRAFFIC = {"kernel_sha1": "99ca001009ae8da969c6dfcad131d8f8b3338aee",
+           "bytes_per_launch": (50.232832e6 + 129.341696e6) * 1507126080 / 233336784}
 
 
 def kernel_sha1() -> str:
@@ -785,7 +788,8 @@ def run_synim(args):
         "config": {"workload": wl.name if args.scale == 1.0 else f"{wl.name} (scale {args.scale}, profiling)",
                    "n_dm": len(wl.dms), "n_wfs": len(wl.wfss), "n_pairs": n_pairs,
                    "columns_per_step": cols_per_step, "im_bytes_per_step": im_bytes,
-                   "l2": "working set (1.4 GB written per step) exceeds L2; no flush",
+                   "l2": (f"working set ({im_bytes / 1e9:.2f} GB written per step) exceeds the 126 MB L2; no flush"
+                          if im_bytes > 126e6 else "outputs below the L2 size (profiling case); no flush"),
                    "parallelism": f"replicas x{world} (independent jobs, no collective on the data path)",
                    "launch_shape": None if tuned is None else {"threads_per_cta": tuned[0], "lanes_per_segment": tuned[1],
                                                                "picked_by": "autotuner (first call)"}},
