@@ -60,7 +60,7 @@ struct CnnState {
     bf16 *x = nullptr, *a1 = nullptr, *a2 = nullptr, *a3 = nullptr;
     bf16 *dz1 = nullptr, *dz2 = nullptr, *dz3 = nullptr;
     float *out = nullptr, *loss = nullptr, *dout = nullptr;
-    float *hpart = nullptr;   // head partial sums of small batches [kBatchCap][4]
+    float *hpart = nullptr;   // head partial sums [b][part][4], b * part <= kBatchCap * 32
     float *wpart = nullptr;   // weight-gradient partials [splits][64 K + 64]
     long long wpart_floats = 0;
     float *tgt = nullptr;   // [kBatchCap][4] targets of the current batch
@@ -1015,67 +1015,102 @@ __global__ void __launch_bounds__(256) k_sum_parts(const float *__restrict__ par
     }
 }
 
+// The same sums four consecutive q per lane (16-byte loads and stores; count,
+// stride and both base addresses multiples of 4 floats): a CTA owns 128 q.
+// Each q is added in the same order as by k_sum_parts.
+__global__ void __launch_bounds__(256) k_sum_parts4(const float4 *__restrict__ part, int splits, int count4,
+                                                    long long stride4, float4 *__restrict__ grad) {
+    __shared__ float4 red[8][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int q = blockIdx.x * 32 + lane;
+    float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (q < count4) {
+#pragma unroll 4
+        for (int p = w; p < splits; p += 8) {
+            const float4 v = part[(size_t)p * stride4 + q];
+            sum.x += v.x;
+            sum.y += v.y;
+            sum.z += v.z;
+            sum.w += v.w;
+        }
+    }
+    red[w][lane] = sum;
+    __syncthreads();
+    if (w == 0 && q < count4) {
+        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            t.x += red[k][lane].x;
+            t.y += red[k][lane].y;
+            t.z += red[k][lane].z;
+            t.w += red[k][lane].w;
+        }
+        grad[q] = t;
+    }
+}
+
+
 // ---------------------------------------------------------------------------
 // Head: dense layer from the flattened last feature map (F = H3 H3 64 values
 // per sample, NHWC order) to the 4 outputs; loss; and their backward.
 // ---------------------------------------------------------------------------
 constexpr int kHeadThreads = 256;
 
-// out[b][j] = bfc[j] + sum_e Wfc[j][e] a3[b][e]; loss[b] = sum_j (out - tgt)^2.
-// With parts > 1 (small batches: a lone block per sample leaves the GPU idle)
-// block (part, b) sums features [part seg, (part + 1) seg) into
-// part_out[b][part][4] and k_head_combine finishes.
+// part_out[b][part][j] = sum over features e of part `part` of Wfc[j][e]
+// a3[b][e].  Block (part, g) takes samples 8 g .. 8 g + 7 (so that each
+// weight loaded serves eight samples) and features [part seg, (part + 1)
+// seg); k_head_combine adds the parts in order.
+constexpr int kHeadSamples = 8;
 __global__ void __launch_bounds__(kHeadThreads)
-k_head_fwd(const bf16 *__restrict__ a3, int F, const float *__restrict__ wfc, const float *__restrict__ bfc,
-           const float *__restrict__ tgt, float *__restrict__ out, float *__restrict__ loss, int parts,
+k_head_fwd(const bf16 *__restrict__ a3, int F, int B, const float *__restrict__ wfc, int parts,
            float *__restrict__ part_out) {
-    const int b = blockIdx.y, part = blockIdx.x, seg = (F + parts - 1) / parts;
+    const int part = blockIdx.x, b0 = blockIdx.y * kHeadSamples, seg = (F + parts - 1) / parts;
     const int e0 = part * seg, e1 = min(F, e0 + seg);
-    const bf16 *x = a3 + (size_t)b * F;
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    const int nb = min(kHeadSamples, B - b0);
+    float acc[kHeadSamples][4];
+#pragma unroll
+    for (int s = 0; s < kHeadSamples; ++s)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[s][j] = 0.f;
     for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-        const float v = __bfloat162float(x[e]);
+        float w[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[j] = fmaf(wfc[(size_t)j * F + e], v, acc[j]);
-    }
-    __shared__ float sh[kHeadThreads / 32][4];
+        for (int j = 0; j < 4; ++j) w[j] = wfc[(size_t)j * F + e];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        float v = acc[j];
+        for (int s = 0; s < kHeadSamples; ++s) {
+            if (s < nb) {
+                const float v = __bfloat162float(a3[(size_t)(b0 + s) * F + e]);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        acc[j] = v;
-    }
-    if ((threadIdx.x & 31) == 0)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) sh[threadIdx.x >> 5][j] = acc[j];
-    __syncthreads();
-    if (parts > 1) {
-        if (threadIdx.x < 4) {
-            float o = 0.f;
-            for (int w = 0; w < kHeadThreads / 32; ++w) o += sh[w][threadIdx.x];
-            part_out[((size_t)b * parts + part) * 4 + threadIdx.x] = o;
-        }
-        return;
-    }
-    if (threadIdx.x == 0) {
-        float l = 0.f;
-        for (int j = 0; j < 4; ++j) {
-            float o = bfc[j];
-            for (int w = 0; w < kHeadThreads / 32; ++w) o += sh[w][j];
-            out[b * 4 + j] = o;
-            if (tgt) {
-                const float d = o - tgt[b * 4 + j];
-                l = fmaf(d, d, l);
+                for (int j = 0; j < 4; ++j) acc[s][j] = fmaf(w[j], v, acc[s][j]);
             }
         }
-        if (tgt) loss[b] = l;
+    }
+    __shared__ float sh[kHeadThreads / 32][kHeadSamples * 4];
+#pragma unroll
+    for (int s = 0; s < kHeadSamples; ++s)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float v = acc[s][j];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5][s * 4 + j] = v;
+        }
+    __syncthreads();
+    if (threadIdx.x < kHeadSamples * 4) {
+        const int s = threadIdx.x >> 2, j = threadIdx.x & 3;
+        if (s < nb) {
+            float o = 0.f;
+            for (int w = 0; w < kHeadThreads / 32; ++w) o += sh[w][threadIdx.x];
+            part_out[((size_t)(b0 + s) * parts + part) * 4 + j] = o;
+        }
     }
 }
 
-// out[b][j] = bfc[j] + the parts' sums in part order; loss as in k_head_fwd.
+// out[b][j] = bfc[j] + the parts' sums in part order; with targets, loss[b]
+// = sum_j (out - tgt)^2 and dout = d(mean loss)/d out.
 __global__ void k_head_combine(const float *__restrict__ part_out, int parts, int B, const float *__restrict__ bfc,
-                               const float *__restrict__ tgt, float *__restrict__ out, float *__restrict__ loss) {
+                               const float *__restrict__ tgt, float *__restrict__ out, float *__restrict__ loss,
+                               float *__restrict__ dout) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
     float l = 0.f;
@@ -1086,39 +1121,50 @@ __global__ void k_head_combine(const float *__restrict__ part_out, int parts, in
         if (tgt) {
             const float d = o - tgt[b * 4 + j];
             l = fmaf(d, d, l);
+            dout[b * 4 + j] = 2.f / (4.f * (float)B) * d;
         }
     }
     if (tgt) loss[b] = l;
 }
 
-// dout = d(mean loss)/d out.
-__global__ void k_head_dout(const float *__restrict__ out, const float *__restrict__ tgt, int B,
-                            float *__restrict__ dout) {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q < 4 * B) dout[q] = 2.f / (4.f * (float)B) * (out[q] - tgt[q]);
-}
-
-// gfc[j][e] = sum_b dout[b][j] a3[b][e], gbfc[j] = sum_b dout[b][j].  A CTA
-// owns 64 features (32 BF16 pairs, one per lane) and splits the samples over
-// its 8 warps (b = warp, warp + 8, ...); the 8 partial sums are added in warp
-// order.  F is a multiple of 64.
-__global__ void __launch_bounds__(256) k_head_wgrad(const bf16 *__restrict__ a3, const float *__restrict__ dout, int B,
-                                                    int F, float *__restrict__ gfc, float *__restrict__ gbfc) {
+// Head backward in one pass over a3: dz3[b][e] = (a3 > 0) sum_j dout[b][j]
+// Wfc[j][e], and the weight / bias gradient partials of sample group
+// blockIdx.y: part[g][j * F + e] = sum_{b in g} dout[b][j] a3[b][e],
+// part[g][4 F + j] = sum_{b in g} dout[b][j] (k_sum_parts adds the groups in
+// order).  A CTA owns 64 features (two per lane) and its 8 warps split the
+// group's samples (b = warp, warp + 8, ...), their sums added in warp order.
+// F is a multiple of 64.
+constexpr int kHeadGroups = 8;
+__global__ void __launch_bounds__(256) k_head_bwd(const bf16 *__restrict__ a3, const float *__restrict__ dout,
+                                                  const float *__restrict__ wfc, int B, int F, int per_group,
+                                                  bf16 *__restrict__ dz3, float *__restrict__ part) {
     __shared__ float red[8][4][64];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int e = blockIdx.x * 64 + 2 * lane;
+    const int g = blockIdx.y, bs = g * per_group, be = min(B, bs + per_group);
+    float wf[4][2];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        wf[j][0] = wfc[(size_t)j * F + e];
+        wf[j][1] = wfc[(size_t)j * F + e + 1];
+    }
     float acc[4][2] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-#pragma unroll 8
-    for (int b = w; b < B; b += 8) {
+#pragma unroll 4
+    for (int b = bs + w; b < be; b += 8) {
         const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162 *>(a3 + (size_t)b * F + e);
         const float v0 = __low2float(v), v1 = __high2float(v);
         const float4 d = *reinterpret_cast<const float4 *>(dout + 4 * b);
         const float dj[4] = {d.x, d.y, d.z, d.w};
+        float g0 = 0.f, g1 = 0.f;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             acc[j][0] = fmaf(dj[j], v0, acc[j][0]);
             acc[j][1] = fmaf(dj[j], v1, acc[j][1]);
+            g0 = fmaf(dj[j], wf[j][0], g0);
+            g1 = fmaf(dj[j], wf[j][1], g1);
         }
+        *reinterpret_cast<__nv_bfloat162 *>(dz3 + (size_t)b * F + e) =
+            __floats2bfloat162_rn(v0 > 0.f ? g0 : 0.f, v1 > 0.f ? g1 : 0.f);
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -1126,14 +1172,15 @@ __global__ void __launch_bounds__(256) k_head_wgrad(const bf16 *__restrict__ a3,
         red[w][j][2 * lane + 1] = acc[j][1];
     }
     __syncthreads();
+    float *pg = part + (size_t)g * (4 * (size_t)F + 4);
     const int j = threadIdx.x >> 6, c = threadIdx.x & 63;
     float sum = 0.f;
 #pragma unroll
     for (int q = 0; q < 8; ++q) sum += red[q][j][c];
-    gfc[(size_t)j * F + blockIdx.x * 64 + c] = sum;
+    pg[(size_t)j * F + blockIdx.x * 64 + c] = sum;
     if (blockIdx.x == 0 && w == 0) {
         float sb[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int b = lane; b < B; b += 32) {
+        for (int b = bs + lane; b < be; b += 32) {
             const float4 d = *reinterpret_cast<const float4 *>(dout + 4 * b);
             sb[0] += d.x;
             sb[1] += d.y;
@@ -1144,29 +1191,27 @@ __global__ void __launch_bounds__(256) k_head_wgrad(const bf16 *__restrict__ a3,
         for (int q = 0; q < 4; ++q)
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) sb[q] += __shfl_xor_sync(0xffffffffu, sb[q], o);
-        if (lane < 4) gbfc[lane] = sb[lane];
+        if (lane < 4) pg[4 * (size_t)F + lane] = sb[lane];
     }
-}
-
-// dz3[b][e] = (a3 > 0) sum_j dout[b][j] Wfc[j][e].
-__global__ void k_head_dgrad(const bf16 *__restrict__ a3, const float *__restrict__ dout,
-                             const float *__restrict__ wfc, int B, int F, bf16 *__restrict__ dz3) {
-    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= (long long)B * F) return;
-    const int b = (int)(q / F), e = (int)(q - (long long)b * F);
-    const float *d = dout + b * 4;
-    const float g = d[0] * wfc[e] + d[1] * wfc[(size_t)F + e] + d[2] * wfc[2 * (size_t)F + e] +
-                    d[3] * wfc[3 * (size_t)F + e];
-    dz3[q] = __float2bfloat16_rn(__bfloat162float(a3[q]) > 0.f ? g : 0.f);
 }
 
 // ---------------------------------------------------------------------------
 // Parameters: Adam, BF16 copies (and the transposed copies for the input
 // gradient), normalisation of targets and outputs.
 // ---------------------------------------------------------------------------
-__global__ void k_adam(float *__restrict__ w, float *__restrict__ m, float *__restrict__ v,
-                       const float *__restrict__ g, long long n, float lr, float b1, float b2, float eps,
-                       float c1, float c2) {
+// Where the three convolutions' weights sit in the parameter vector, and
+// their BF16 copies (wt: the transposed copy of a 64-channel layer).
+struct PackDst {
+    long long off[3];
+    int cin[3];
+    bf16 *wb[3], *wt[3];
+};
+
+// One Adam step (as k_adam) that also refreshes the BF16 copies of the
+// updated convolution weights (as k_pack_w): one pass over the parameters.
+__global__ void k_adam_pack(float *__restrict__ w, float *__restrict__ m, float *__restrict__ v,
+                            const float *__restrict__ g, long long n, float lr, float b1, float b2, float eps,
+                            float c1, float c2, const PackDst pd) {
     const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
     const float gq = g[q];
@@ -1174,7 +1219,21 @@ __global__ void k_adam(float *__restrict__ w, float *__restrict__ m, float *__re
     const float vq = b2 * v[q] + (1.f - b2) * gq * gq;
     m[q] = mq;
     v[q] = vq;
-    w[q] -= lr * (mq / c1) / (sqrtf(vq / c2) + eps);
+    const float wq = w[q] - lr * (mq / c1) / (sqrtf(vq / c2) + eps);
+    w[q] = wq;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+        const long long r = q - pd.off[l], K = 9LL * pd.cin[l];
+        if (r >= 0 && r < CH * K) {
+            const bf16 b = __float2bfloat16_rn(wq);
+            pd.wb[l][r] = b;
+            if (pd.wt[l]) {
+                const int co = (int)(r / K), k = (int)(r - co * K);
+                const int tap = k / pd.cin[l], ci = k - tap * pd.cin[l];
+                pd.wt[l][(size_t)ci * (9 * CH) + tap * CH + co] = b;
+            }
+        }
+    }
 }
 
 // w_bf16[co][k] = w[co][k]; wt[ci][tap * 64 + co] = w[co][tap * cin + ci] (cin = 64 only).
@@ -1234,6 +1293,17 @@ cudaError_t dmalloc(T **p, size_t count) {
 }
 
 unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+cudaError_t sum_parts(const float *part, int splits, int count, long long stride, float *grad, cudaStream_t st) {
+    const bool v4 = count % 4 == 0 && stride % 4 == 0 && (reinterpret_cast<uintptr_t>(part) & 15) == 0 &&
+                    (reinterpret_cast<uintptr_t>(grad) & 15) == 0;
+    if (v4)
+        k_sum_parts4<<<blocks_for(count / 4, 32), 256, 0, st>>>(reinterpret_cast<const float4 *>(part), splits,
+                                                               count / 4, stride / 4, reinterpret_cast<float4 *>(grad));
+    else
+        k_sum_parts<<<blocks_for(count, 32), 256, 0, st>>>(part, splits, count, stride, grad);
+    return cudaGetLastError();
+}
 
 int sm_count() {
     static int n = 0;
@@ -1381,9 +1451,7 @@ cudaError_t launch_wgrad(const CnnState &S, int layer, const bf16 *in, const int
         k_wgrad_halo<<<grid, kTcThreads, smem, st>>>(h, S.d_err);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         const int K = 9 * cin;
-        k_sum_parts<<<blocks_for(CH * K + CH, 32), 256, 0, st>>>(S.wpart, grid, CH * K + CH, (long long)CH * K + CH,
-                                                                S.grad + off_w);
-        return cudaGetLastError();
+        return sum_parts(S.wpart, grid, CH * K + CH, (long long)CH * K + CH, S.grad + off_w, st);
     }
     if (cin == CH) {
         // 64-channel layers: tcgen05, one CTA per SM, one partial per CTA
@@ -1397,11 +1465,18 @@ cudaError_t launch_wgrad(const CnnState &S, int layer, const bf16 *in, const int
         k_wgrad_tc<<<grid, kTcThreads, smem, st>>>(a, S.d_err);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         const int K = 9 * cin;
-        k_sum_parts<<<blocks_for(CH * K + CH, 32), 256, 0, st>>>(S.wpart, grid, CH * K + CH, (long long)CH * K + CH,
-                                                                S.grad + off_w);
-        return cudaGetLastError();
+        return sum_parts(S.wpart, grid, CH * K + CH, (long long)CH * K + CH, S.grad + off_w, st);
     }
     return cudaErrorInvalidValue;   // layer 1 has 32 or 64 channels, layers 2-3 64
+}
+
+PackDst pack_dst(const CnnState &S) {
+    PackDst d;
+    d.off[0] = S.off_w1; d.off[1] = S.off_w2; d.off[2] = S.off_w3;
+    d.cin[0] = S.C0; d.cin[1] = CH; d.cin[2] = CH;
+    d.wb[0] = S.w1; d.wb[1] = S.w2; d.wb[2] = S.w3;
+    d.wt[0] = nullptr; d.wt[1] = S.w2t; d.wt[2] = S.w3t;
+    return d;
 }
 
 cudaError_t pack_weights(CnnState &S, cudaStream_t st) {
@@ -1419,13 +1494,14 @@ cudaError_t forward(CnnState &S, const bf16 *in, const int *perm, long long b0, 
     if ((e = launch_conv_fwd(S, 1, in, perm, b0, B, st)) != cudaSuccess) return e;
     if ((e = launch_conv_fwd(S, 2, S.a1, nullptr, 0, B, st)) != cudaSuccess) return e;
     if ((e = launch_conv_fwd(S, 3, S.a2, nullptr, 0, B, st)) != cudaSuccess) return e;
-    // split the head's features over blocks while B * parts fits the partial buffer
-    const int parts = std::max(1, std::min(32, kBatchCap / std::max(B, 1)));
-    k_head_fwd<<<dim3(parts, B), kHeadThreads, 0, st>>>(S.a3, S.H3 * S.H3 * CH, S.master + S.off_fc,
-                                                        S.master + S.off_bfc, tgt, S.out, S.loss, parts, S.hpart);
-    if (parts > 1)
-        k_head_combine<<<blocks_for(B, 64), 64, 0, st>>>(S.hpart, parts, B, S.master + S.off_bfc, tgt, S.out,
-                                                         S.loss);
+    // the head: blocks of 8 samples x a share of the features, about 256
+    // blocks in all (32 feature parts for one group of 8, 8 for 32 groups)
+    const int groups = (B + kHeadSamples - 1) / kHeadSamples;
+    const int parts = std::max(1, std::min(32, kBatchCap / groups));
+    k_head_fwd<<<dim3(parts, groups), kHeadThreads, 0, st>>>(S.a3, S.H3 * S.H3 * CH, B, S.master + S.off_fc, parts,
+                                                             S.hpart);
+    k_head_combine<<<blocks_for(B, 64), 64, 0, st>>>(S.hpart, parts, B, S.master + S.off_bfc, tgt, S.out, S.loss,
+                                                     S.dout);
     return cudaGetLastError();
 }
 
@@ -1433,10 +1509,14 @@ cudaError_t backward(CnnState &S, const bf16 *in, const int *perm, long long b0,
                      cudaStream_t st) {
     cudaError_t e;
     const int F = S.H3 * S.H3 * CH;
-    k_head_dout<<<blocks_for(4 * B, 256), 256, 0, st>>>(S.out, tgt, B, S.dout);
-    k_head_wgrad<<<F / 64, 256, 0, st>>>(S.a3, S.dout, B, F, S.grad + S.off_fc, S.grad + S.off_bfc);
-    k_head_dgrad<<<blocks_for((long long)B * F, 256), 256, 0, st>>>(S.a3, S.dout, S.master + S.off_fc, B, F, S.dz3);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    (void)tgt;   // dout was formed by the forward pass
+    // head: dz3 and the dense layer's gradient partials of up to 8 sample
+    // groups in one pass over a3, then the groups added in order
+    const int per_group = (B + kHeadGroups - 1) / kHeadGroups;
+    const int groups = (B + per_group - 1) / per_group;
+    k_head_bwd<<<dim3(F / 64, groups), 256, 0, st>>>(S.a3, S.dout, S.master + S.off_fc, B, F, per_group, S.dz3,
+                                                     S.wpart);
+    if ((e = sum_parts(S.wpart, groups, 4 * F + 4, 4LL * F + 4, S.grad + S.off_fc, st)) != cudaSuccess) return e;
     if ((e = launch_wgrad(S, 3, S.a2, nullptr, 0, B, st)) != cudaSuccess) return e;
     if ((e = launch_conv_dgrad(S, 3, B, st)) != cudaSuccess) return e;
     if ((e = launch_wgrad(S, 2, S.a1, nullptr, 0, B, st)) != cudaSuccess) return e;
@@ -1472,7 +1552,7 @@ cudaError_t alloc_state(CnnState &S) {
     SYNIM_A(S.out, (size_t)kBatchCap * 4);
     SYNIM_A(S.loss, (size_t)kBatchCap);
     SYNIM_A(S.dout, (size_t)kBatchCap * 4);
-    SYNIM_A(S.hpart, (size_t)kBatchCap * 4);
+    SYNIM_A(S.hpart, (size_t)kBatchCap * 32 * 4);
     SYNIM_A(S.tgt, (size_t)kBatchCap * 4);
     SYNIM_A(S.wpart, (size_t)S.wpart_floats);
     SYNIM_A(S.d_err, 1);
@@ -1799,9 +1879,9 @@ synim_status synim_cnn_train(synim_ctx *ctx, const double *params, int64_t n, co
             if ((e = backward(S, S.data, S.perm, b0, B, S.tgt, st)) != cudaSuccess) break;
             ++S.step;
             const float c1 = 1.f - std::pow(b1, (float)S.step), c2 = 1.f - std::pow(b2, (float)S.step);
-            k_adam<<<blocks_for(S.n_params, 256), 256, 0, st>>>(S.master, S.adam_m, S.adam_v, S.grad, S.n_params,
-                                                               lr, b1, b2, eps, c1, c2);
-            if ((e = pack_weights(S, st)) != cudaSuccess) break;
+            k_adam_pack<<<blocks_for(S.n_params, 256), 256, 0, st>>>(S.master, S.adam_m, S.adam_v, S.grad,
+                                                                    S.n_params, lr, b1, b2, eps, c1, c2, pack_dst(S));
+            if ((e = cudaGetLastError()) != cudaSuccess) break;
             if (loss_out && (bi % 64 == 0 || bi == nb - 1)) {
                 if ((e = cudaMemcpyAsync(S.h_loss, S.loss, sizeof(float) * B, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
                     break;
