@@ -8,7 +8,7 @@
 //            Gamma(6/5))^(5/6); K_5/6 from its integral representation
 //            K_nu(x) = int_0^inf exp(-x cosh t) cosh(nu t) dt by the
 //            trapezoidal rule (exponentially convergent for this integrand),
-//            evaluated once per distinct pixel separation on the host (FP64).
+//            evaluated once per distinct pixel separation on the device (FP64).
 //   C_atm  = G^-1 F^T C_phi F G^-1, F the DM basis averaged over bin x bin
 //            pixel blocks (columns = modes), G = F^T F: the covariance of the
 //            least-squares coefficients of the layer phase sampled at the
@@ -36,20 +36,31 @@ namespace synim {
 
 namespace {
 
-// x^nu K_nu(x) for x >= 0, nu in (0, 1): trapezoidal rule on
+// x^nu K_nu(x) (x >= 0, nu in (0, 1)) by the trapezoidal rule on
 // int_0^inf exp(-x cosh t) cosh(nu t) dt with step h, up to where the
-// integrand is below 1e-300 of its value at t = 0.
-double xnu_knu(double nu, double x) {
-    if (x <= 0.0) return std::tgamma(nu) * std::pow(2.0, nu - 1.0);
-    const double h = 0.02;
-    double s = 0.5 * std::exp(-x);
-    for (int i = 1; i < 200000; ++i) {
-        const double t = i * h;
-        const double e = -x * std::cosh(t) + nu * t;   // log of the integrand, up to cosh(nu t) ~ e^(nu t) / 2
-        if (e + x < -700.0 && t > 1.0) break;
-        s += std::exp(-x * std::cosh(t)) * std::cosh(nu * t);
+// integrand is below 1e-300 of its value at t = 0; one thread per pixel separation
+// (dx, dy) of the binned grid: tab[dy Nb + dx] = amp x^nu K_nu(x), x = 2 pi
+// pitch |(dx, dy)| / L0, in FP64.
+__global__ void k_vk_table(int Nb, double pitch, double L0, double amp, double nu, float *__restrict__ tab) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= Nb * Nb) return;
+    const int dy = q / Nb, dx = q - dy * Nb;
+    const double x = 2.0 * 3.14159265358979323846 * pitch * sqrt((double)dx * dx + (double)dy * dy) / L0;
+    double v;
+    if (x <= 0.0) {
+        v = tgamma(nu) * pow(2.0, nu - 1.0);
+    } else {
+        const double h = 0.02;
+        double s = 0.5 * exp(-x);
+        for (int i = 1; i < 200000; ++i) {
+            const double t = i * h;
+            const double ct = cosh(t);
+            if (-x * ct + nu * t + x < -700.0 && t > 1.0) break;
+            s += exp(-x * ct) * cosh(nu * t);
+        }
+        v = pow(x, nu) * h * s;
     }
-    return std::pow(x, nu) * h * s;
+    tab[q] = (float)(amp * v);
 }
 
 double vk_const() {
@@ -179,22 +190,15 @@ extern "C" synim_status synim_atm_covariance(synim_ctx *ctx, int32_t dm, int32_t
     const long npix = (long)Nb * Nb;
     if (npix > 46340) return cv_fail(ctx, SYNIM_ERR_SHAPE, "atm_covariance: more than 46340 binned pixels (raise bin)");
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    // separation table (host, FP64): B at (dx, dy) pixel offsets of pitch dd bin
-    const double pi = 3.14159265358979323846, c = vk_const();
+    // separation table (device, FP64): B at (dx, dy) pixel offsets of pitch dd bin
+    const double c = vk_const();
     const double amp = c * std::pow(L0_m / r0_m, 5.0 / 3.0), pitch = H.dd * bin;
-    std::vector<float> tab((size_t)Nb * Nb);
-    for (int dy = 0; dy < Nb; ++dy)
-        for (int dx = 0; dx <= dy; ++dx) {
-            const double r = pitch * std::sqrt((double)dx * dx + (double)dy * dy);
-            const float v = (float)(amp * xnu_knu(5.0 / 6.0, 2.0 * pi * r / L0_m));
-            tab[(size_t)dy * Nb + dx] = v;
-            tab[(size_t)dx * Nb + dy] = v;
-        }
+    const size_t ntab = (size_t)Nb * Nb;
     CvScratch sc;
     float *d_tab = nullptr, *Ft = nullptr, *C = nullptr, *W = nullptr, *T = nullptr, *G = nullptr, *X = nullptr;
     float *linvs = nullptr, *work = nullptr;
     int *flags = nullptr;
-    cudaError_t e = sc.alloc(&d_tab, tab.size());
+    cudaError_t e = sc.alloc(&d_tab, ntab);
     if (e == cudaSuccess) e = sc.alloc(&Ft, (size_t)na * npix);
     if (e == cudaSuccess) e = sc.alloc(&C, (size_t)npix * npix);
     if (e == cudaSuccess) e = sc.alloc(&W, (size_t)npix * na);
@@ -205,9 +209,9 @@ extern "C" synim_status synim_atm_covariance(synim_ctx *ctx, int32_t dm, int32_t
     if (e == cudaSuccess) e = sc.alloc(&work, (size_t)na * 128);
     if (e == cudaSuccess) e = sc.alloc(&flags, 2);
     if (e != cudaSuccess) return cv_fail(ctx, SYNIM_ERR_OOM, "atm_covariance: scratch");
-    e = cudaMemcpyAsync(d_tab, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, 2 * sizeof(int), st);
+    e = cudaMemsetAsync(flags, 0, 2 * sizeof(int), st);
     if (e == cudaSuccess) {
+        k_vk_table<<<blocks_for((long)ntab, 128), 128, 0, st>>>(Nb, pitch, L0_m, amp, 5.0 / 6.0, d_tab);
         k_bin_basis<<<blocks_for((long)na * npix, 256), 256, 0, st>>>(D, bin, Nb, Ft);
         k_vk_fill<<<blocks_for(npix * npix, 256), 256, 0, st>>>(d_tab, Nb, C);
         e = cudaGetLastError();

@@ -23,6 +23,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -78,6 +80,8 @@ struct GemmArgs {
     float alpha, beta;
     int b_kn;    // 0: B(k, n) = B[n ldb + k]; 1: B(k, n) = B[k ldb + n]
     int lower;   // 1: only tiles that touch the lower triangle (n <= m) of C
+    int ksplit;  // K per blockIdx.z (K when gridDim.z = 1)
+    long zstride;   // C offset of blockIdx.z's partial (0 when gridDim.z = 1)
 };
 
 // Issue the asynchronous 4-byte copies of K chunk k0 of one operand tile
@@ -140,6 +144,11 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gemm3(const GemmArgs g, int *e
     const int bm = blockIdx.y, bn = blockIdx.x;
     const int m0 = bm * kGBM, n0 = bn * kGBN;
     if (g.lower && n0 > m0 + kGBM - 1) return;   // tile wholly above the diagonal
+    // split K: this CTA's share [kbeg, kbeg + Kz) of the sum, into its own partial
+    const int kbeg = blockIdx.z * g.ksplit, Kz = max(0, min(g.K, kbeg + g.ksplit) - kbeg);
+    const float *Ag = g.A + kbeg;
+    const float *Bg = g.b_kn ? g.B + (long)kbeg * g.ldb : g.B + kbeg;
+    float *Cg = g.C + (long)blockIdx.z * g.zstride;
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(gsm) + 1023) & ~uintptr_t(1023));
     uint8_t *lo_base = base + kRawStages * kRawBytes;
     uint64_t *bars = reinterpret_cast<uint64_t *>(lo_base + 2 * kLoBytes);
@@ -155,15 +164,15 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gemm3(const GemmArgs g, int *e
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-    const int nch = (g.K + kGBK - 1) / kGBK;
+    const int nch = (Kz + kGBK - 1) / kGBK;
     const uint32_t idesc = idesc_tf32(kGBM, kGBN);
     // chunk c: raw (= hi) tiles in stage c % 4, written by cp.async two chunks
     // ahead; lo tiles in slot c % 2, written once the MMAs of chunk c - 2
     // (which read that slot and raw stage (c + 2) % 4) have completed
     auto issue = [&](int c) {
         uint8_t *raw = base + (c % kRawStages) * kRawBytes;
-        issue_tile(g.A, g.lda, true, g.M, m0, g.K, c * kGBK, raw);
-        issue_tile(g.B, g.ldb, g.b_kn == 0, g.N, n0, g.K, c * kGBK, raw + kTileBytes);
+        issue_tile(Ag, g.lda, true, g.M, m0, Kz, c * kGBK, raw);
+        issue_tile(Bg, g.ldb, g.b_kn == 0, g.N, n0, Kz, c * kGBK, raw + kTileBytes);
         cp_async_commit();
     };
     if (nch > 0) issue(0);
@@ -225,7 +234,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gemm3(const GemmArgs g, int *e
             for (int rr = 0; rr < 32; ++rr) {
                 const int r = m0 + warp * 32 + rr;
                 if (r < g.M && n < g.N && (!g.lower || n <= r)) {
-                    float *cp = g.C + (long)r * g.ldc + n;
+                    float *cp = Cg + (long)r * g.ldc + n;
                     const float acc = stile[(warp * 32 + rr) * 33 + lane];
                     *cp = g.beta != 0.f ? fmaf(g.alpha, acc, g.beta * *cp) : g.alpha * acc;
                 }
@@ -238,61 +247,178 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gemm3(const GemmArgs g, int *e
     if (warp == 0) tc_dealloc(tmem, kGBN);
 }
 
-// Unblocked Cholesky of the nb x nb diagonal block at S (row-major, lds) in
-// shared memory: L (lower) written back over S, the inverse of L into Linv
-// (nb x nb of a kNB x kNB row-major block, zero above the diagonal).  A
-// non-positive pivot sets *info = 1 (not positive definite).  One CTA of
-// kGThreads threads.
+// Unblocked Cholesky of the nb x nb diagonal block at S (row-major, lds):
+// L (lower) written back over S, the inverse of L into Linv (nb x nb of a
+// kNB x kNB row-major block, zero above the diagonal).  A non-positive pivot
+// sets *info = 1 (not positive definite).  One CTA of 512 threads as 16 x 32:
+// thread (ty, tx) holds elements (ty + 16 a, tx + 32 b), a < 8, b < 4, of the
+// block in registers, so that a step's update is 32 register FMAs per
+// thread fed by 12 shared-memory loads of the published column / row.  Both
+// loops are right-looking:
+//   factor:  for k: L_kk = sqrt(a_kk); L_ik = a_ik / L_kk (i > k);
+//            a_ij -= L_ik L_jk (k < j <= i);
+//   inverse: X = I; for k: X_k. /= L_kk; X_i. -= L_ik X_k. (i > k), where
+//            only X_kc, c <= k, are non-zero.
+// The owners of column k (row k of X) publish it unscaled and keep their
+// registers unscaled; every thread applies 1 / L_kk as it reads, and the
+// final values are scaled on the way out (L_ij = a_ij / L_jj, X_ic =
+// x_ic / L_ii), so no register is selected by a run-time index inside the
+// step.
 constexpr int kNB = 128;
+constexpr int kPotrfThreads = 512;
 
-__global__ void __launch_bounds__(kGThreads) k_potrf_diag(float *S, long lds, int nb, float *Linv, int *info) {
+__global__ void __launch_bounds__(kPotrfThreads) k_potrf_diag(float *S, long lds, int nb, float *Linv, int *info) {
     constexpr int ldl = kNB;
-    extern __shared__ float a[];   // [nb][nb + 1] factor, then [nb][nb + 1] its inverse
-    const int ld = nb + 1, t = threadIdx.x;
-    for (int q = t; q < nb * nb; q += blockDim.x) {
-        const int i = q / nb, j = q - i * nb;
-        a[i * ld + j] = j <= i ? S[(long)i * lds + j] : 0.f;
-    }
-    __syncthreads();
+    extern __shared__ float a[];   // [kNB][kNB + 1]: L once factored
+    constexpr int ld = kNB + 1;
+    __shared__ float colk[kNB], pivv[kNB], rpv[kNB];
     __shared__ int bad;
+    const int t = threadIdx.x, ty = t >> 5, tx = t & 31;
+    float r[8][4];
+#pragma unroll
+    for (int ai = 0; ai < 8; ++ai)
+#pragma unroll
+        for (int bi = 0; bi < 4; ++bi) {
+            const int i = ty + 16 * ai, j = tx + 32 * bi;
+            r[ai][bi] = (i < nb && j <= i) ? S[(long)i * lds + j] : 0.f;
+        }
     if (t == 0) bad = 0;
+    for (int k = 0; k < nb; ++k) {
+        const int bk = k >> 5;
+        // the owners of column k publish it (rows k .. nb - 1, unscaled)
+        if (tx == (k & 31)) {
+#pragma unroll
+            for (int bi = 0; bi < 4; ++bi)
+                if (bi == bk)
+#pragma unroll
+                    for (int ai = 0; ai < 8; ++ai) {
+                        const int i = ty + 16 * ai;
+                        if (i >= k && i < nb) colk[i] = r[ai][bi];
+                    }
+        }
+        __syncthreads();
+        const float d = colk[k];
+        const float piv = d > 0.f ? sqrtf(d) : 1.f, rp = 1.f / piv;
+        if (t == 0) {
+            pivv[k] = piv;
+            rpv[k] = rp;
+            if (!(d > 0.f)) bad = 1;
+        }
+        float ci[8], cj[4];
+#pragma unroll
+        for (int ai = 0; ai < 8; ++ai) {
+            const int i = ty + 16 * ai;
+            ci[ai] = (i > k && i < nb) ? colk[i] * rp : 0.f;
+        }
+#pragma unroll
+        for (int bi = 0; bi < 4; ++bi) {
+            const int j = tx + 32 * bi;
+            cj[bi] = (j > k && j < nb) ? colk[j] * rp : 0.f;
+        }
+#pragma unroll
+        for (int ai = 0; ai < 8; ++ai)
+#pragma unroll
+            for (int bi = 0; bi < 4; ++bi) r[ai][bi] = fmaf(-ci[ai], cj[bi], r[ai][bi]);
+        __syncthreads();   // column k read by all before column k + 1 is published
+    }
+    // L to shared memory (and back to S); the upper triangle reads as zero
+#pragma unroll
+    for (int ai = 0; ai < 8; ++ai)
+#pragma unroll
+        for (int bi = 0; bi < 4; ++bi) {
+            const int i = ty + 16 * ai, j = tx + 32 * bi;
+            if (i < nb && j < nb) {
+                const float l = i == j ? pivv[j] : (j < i ? r[ai][bi] * rpv[j] : 0.f);
+                a[i * ld + j] = l;
+                if (j <= i) S[(long)i * lds + j] = l;
+            }
+        }
+    // inverse: X (unscaled rows) in the same registers, row k published through colk
+#pragma unroll
+    for (int ai = 0; ai < 8; ++ai)
+#pragma unroll
+        for (int bi = 0; bi < 4; ++bi) r[ai][bi] = (ty + 16 * ai == tx + 32 * bi) ? 1.f : 0.f;
     __syncthreads();
     for (int k = 0; k < nb; ++k) {
-        // pivot
-        if (t == 0) {
-            const float d = a[k * ld + k];
-            if (!(d > 0.f)) bad = 1;
-            a[k * ld + k] = d > 0.f ? sqrtf(d) : 1.f;
+        const int ak = k >> 4;
+        if (ty == (k & 15)) {
+#pragma unroll
+            for (int ai = 0; ai < 8; ++ai)
+                if (ai == ak)
+#pragma unroll
+                    for (int bi = 0; bi < 4; ++bi) {
+                        const int c = tx + 32 * bi;
+                        if (c <= k) colk[c] = r[ai][bi];
+                    }
         }
         __syncthreads();
-        const float piv = a[k * ld + k];
-        for (int i = k + 1 + t; i < nb; i += blockDim.x) a[i * ld + k] /= piv;
-        __syncthreads();
-        // trailing update of the lower triangle, one row per thread
-        for (int i = k + 1 + t; i < nb; i += blockDim.x) {
-            const float lik = a[i * ld + k];
-            for (int j = k + 1; j <= i; ++j) a[i * ld + j] = fmaf(-lik, a[j * ld + k], a[i * ld + j]);
+        const float rp = rpv[k];
+        float li[8], xk[4];
+#pragma unroll
+        for (int ai = 0; ai < 8; ++ai) {
+            const int i = ty + 16 * ai;
+            li[ai] = (i > k && i < nb) ? a[i * ld + k] : 0.f;
         }
-        __syncthreads();
-    }
-    // inverse of L by forward substitution in shared memory, one column per
-    // thread (column c of the inverse depends only on itself)
-    float *inv = a + nb * ld;   // [nb][nb + 1]
-    for (int c = t; c < nb; c += blockDim.x) {
-        for (int i = 0; i < nb; ++i) {
-            float s = (i == c) ? 1.f : 0.f;
-            if (i >= c)
-                for (int k = c; k < i; ++k) s = fmaf(-a[i * ld + k], inv[k * ld + c], s);
-            inv[i * ld + c] = i >= c ? s / a[i * ld + i] : 0.f;
+#pragma unroll
+        for (int bi = 0; bi < 4; ++bi) {
+            const int c = tx + 32 * bi;
+            xk[bi] = c <= k ? colk[c] * rp : 0.f;
         }
+#pragma unroll
+        for (int ai = 0; ai < 8; ++ai)
+#pragma unroll
+            for (int bi = 0; bi < 4; ++bi) r[ai][bi] = fmaf(-li[ai], xk[bi], r[ai][bi]);
+        __syncthreads();   // row k read by all before row k + 1 is published
     }
-    __syncthreads();
-    for (int q = t; q < nb * nb; q += blockDim.x) {
-        const int i = q / nb, j = q - i * nb;
-        if (j <= i) S[(long)i * lds + j] = a[i * ld + j];
-        Linv[(long)i * ldl + j] = inv[i * ld + j];
-    }
+#pragma unroll
+    for (int ai = 0; ai < 8; ++ai)
+#pragma unroll
+        for (int bi = 0; bi < 4; ++bi) {
+            const int i = ty + 16 * ai, j = tx + 32 * bi;
+            if (i < nb && j < nb) Linv[(long)i * ldl + j] = j <= i ? r[ai][bi] * rpv[i] : 0.f;
+        }
     if (t == 0 && bad) atomicOr(info, 1);
+}
+
+// C[r][n] = alpha sum_z part[z][r][n] + beta C[r][n] (z in order; beta = 0
+// reads nothing): the split-K partials of k_gemm3 added.
+__global__ void k_splitk_reduce(const float *__restrict__ part, int splits, int M, int N, float alpha, float beta,
+                                float *__restrict__ C, long ldc) {
+    const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (long)M * N) return;
+    const int r = (int)(q / N), n = (int)(q - (long)r * N);
+    float acc = 0.f;
+    for (int z = 0; z < splits; ++z) acc += part[(long)z * M * N + q];
+    float *cp = C + (long)r * ldc + n;
+    *cp = beta != 0.f ? fmaf(alpha, acc, beta * *cp) : alpha * acc;
+}
+
+// Split-K workspace, one per device, grown on demand.  The dense routines
+// are synchronous host calls; cudaFree of a smaller buffer waits for the
+// device, so no launch still reads it.
+float *splitk_ws(size_t floats) {
+    static std::mutex mu;
+    static std::map<int, std::pair<float *, size_t>> ws;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    auto &w = ws[dev];
+    if (w.second >= floats) return w.first;
+    if (w.first) cudaFree(w.first);
+    w.first = nullptr;
+    w.second = 0;
+    if (cudaMalloc(&w.first, floats * sizeof(float)) != cudaSuccess) {
+        w.first = nullptr;
+        return nullptr;
+    }
+    w.second = floats;
+    return w.first;
+}
+
+int device_sms() {
+    int dev = 0, n = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n;
 }
 
 // Copy an r x c block (row-major, leading dimensions) from src to dst.
@@ -314,8 +440,37 @@ cudaError_t dense_gemm(const float *A, long lda, const float *B, long ldb, bool 
     GemmArgs g;
     g.A = A; g.B = B; g.C = C; g.lda = lda; g.ldb = ldb; g.ldc = ldc; g.M = M; g.N = N; g.K = K;
     g.alpha = alpha; g.beta = beta; g.b_kn = b_kn ? 1 : 0; g.lower = lower ? 1 : 0;
+    g.ksplit = K;
+    g.zstride = 0;
     dim3 grid((unsigned)((N + kGBN - 1) / kGBN), (unsigned)((M + kGBM - 1) / kGBM));
+    // Few tiles and a long K (the panel updates of the blocked solves, m x 128
+    // with K up to n) would leave most SMs idle: split K over blockIdx.z into
+    // partials and add them in order.
+    const long tiles = (long)grid.x * grid.y;
+    const int n_sm = device_sms();
+    int splits = 1;
+    if (!lower && K >= 256 && 2 * tiles <= n_sm)
+        splits = (int)std::min<long>(std::min<long>((n_sm + tiles - 1) / tiles, K / 128), 16);
+    float *ws = nullptr;
+    if (splits > 1) {
+        const int ks = ((K + splits - 1) / splits + kGBK - 1) / kGBK * kGBK;
+        splits = (K + ks - 1) / ks;
+        ws = splitk_ws((size_t)splits * M * N);
+        if (ws) {
+            g.ksplit = ks;
+            g.C = ws;
+            g.ldc = N;
+            g.zstride = (long)M * N;
+            g.alpha = 1.f;
+            g.beta = 0.f;
+            grid.z = (unsigned)splits;
+        }
+    }
     k_gemm3<<<grid, kGThreads, kGemmSmem, s>>>(g, err);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || grid.z == 1) return e;
+    const long cnt = (long)M * N;
+    k_splitk_reduce<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(ws, (int)grid.z, M, N, alpha, beta, C, ldc);
     return cudaGetLastError();
 }
 
@@ -326,7 +481,7 @@ cudaError_t dense_gemm(const float *A, long lda, const float *B, long ldb, bool 
 // (S -= L_panel L_panel^T).  linvs: dense_blocks(n) * kNB * kNB floats; work:
 // n * kNB floats.  *info = 1 if S is not positive definite.
 cudaError_t dense_potrf(float *S, long lds, int n, float *linvs, float *work, int *info, int *err, cudaStream_t s) {
-    const size_t dsm = 2 * (size_t)kNB * (kNB + 1) * sizeof(float);
+    const size_t dsm = (size_t)kNB * (kNB + 1) * sizeof(float);
     cudaError_t ea = cudaFuncSetAttribute(k_potrf_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
     if (ea != cudaSuccess) return ea;
     float *panel = work;
@@ -334,7 +489,7 @@ cudaError_t dense_potrf(float *S, long lds, int n, float *linvs, float *work, in
         const int nb = std::min(kNB, n - j0), rest = n - j0 - nb;
         float *Linv = linvs + (size_t)(j0 / kNB) * kNB * kNB;
         float *Sjj = S + (long)j0 * lds + j0;
-        k_potrf_diag<<<1, kGThreads, dsm, s>>>(Sjj, lds, nb, Linv, info);
+        k_potrf_diag<<<1, kPotrfThreads, dsm, s>>>(Sjj, lds, nb, Linv, info);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess || rest == 0) {
             if (e != cudaSuccess) return e;

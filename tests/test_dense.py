@@ -5,7 +5,8 @@ GEMM criterion: |C - C_64| <= 2e-6 * (|A| |B|)_{mn} + 1e-6 |beta C0|_{mn}
 elementwise: three TF32 products (hi.hi + hi.lo + lo.hi) carry ~2^-21 of each
 product, FP32 accumulation ~K 2^-24 of the absolute sum.  Shapes cover several
 128 x 128 tiles, ragged edges in M, N and K (not multiples of 128 / 32), both
-layouts of B, alpha / beta, and K = 0.
+layouts of B, alpha / beta, K = 0, and few tiles with a long K (the split-K
+path).
 
 SPD solve criterion: Y S^-1 within 1e-4 relative (Frobenius) of FP64 for a
 well-conditioned S (cond ~ 1e2) at sizes spanning several 128-row blocks and
@@ -31,7 +32,10 @@ def _gemm(A, B, C, alpha, beta, b_kn):
     assert st == 0, L.synim_last_error(None)
 
 
-@pytest.mark.parametrize("M,N,K", [(256, 384, 256), (300, 170, 77), (129, 1, 33), (64, 200, 0), (517, 263, 1000)])
+# (300, 128, 3000) and (1369, 100, 2411) have few output tiles and a long K:
+# they take the split-K path (partials over blockIdx.z, added in order)
+@pytest.mark.parametrize("M,N,K", [(256, 384, 256), (300, 170, 77), (129, 1, 33), (64, 200, 0), (517, 263, 1000),
+                                   (300, 128, 3000), (1369, 100, 2411)])
 @pytest.mark.parametrize("b_kn", [0, 1])
 def test_gemm_matches_fp64(M, N, K, b_kn):
     g = torch.Generator().manual_seed(M * 1000 + N + K)
