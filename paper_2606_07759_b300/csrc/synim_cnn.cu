@@ -11,9 +11,11 @@
 // Loss: mean over the batch and the 4 outputs of the squared error; Adam.
 //
 // Kernels (BF16 operands, FP32 accumulation):
-//   k_conv_tc<FWD>    implicit GEMM out[m][co] = sum_k im2col(in)[m][k] W[co][k],
-//                     m = (sample, oy, ox), k = (ky, kx, ci); + bias, ReLU,
-//                     BF16; tcgen05.mma with TMEM accumulators;
+//   k_conv_halo       stride-1 forward (first layer) on shifted windows of one
+//                     halo per tile; + bias, ReLU, BF16; tcgen05.mma with
+//                     TMEM accumulators;
+//   k_conv_parity     stride-2 forwards (layers 2-3) on the four parity planes
+//                     of the input, each input pixel staged once per tile;
 //   k_conv_tc<DGRAD>  implicit GEMM of the transposed convolution: gradient
 //                     of the layer input, masked by its ReLU, BF16;
 //   k_wgrad_halo      weight and bias gradient of the first layer (32
@@ -617,6 +619,218 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_halo(const ConvArgs a, i
             const int y = r / hg.Wp, x = r - y * hg.Wp;
             const bool keep = y < hg.H && x < hg.H;
             bf16 *row = a.out + (((size_t)b * hg.H + y) * hg.H + x) * CH;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                float v[32];
+                tc_ld_sum(lane_base + (uint32_t)(ab * kTcParts * CH + 32 * h), v);
+                if (keep) store_relu32(v, s_bias, h, row);
+            }
+            tc_fence_before();
+            tc_mbar_arrive(bar0 + 8 * (2 * S + 2 + ab));
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 8) {
+        tc_fence_after();
+        tc_dealloc(tmem, kTcCols);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Parity-plane kernel for the stride-2 forward convolutions (64 channels).
+//
+// Input pixel (2 oy - 1 + ky, 2 ox - 1 + kx) of output (oy, ox) lies in the
+// parity plane (py, px) = (ky != 1, kx != 1) of the input, P_pq(Y, X) =
+// in(2 Y + p, 2 X + q), at (Y, X) = (oy - (ky == 0), ox - (kx == 0)).  With
+// GEMM rows r = oy Wq + ox on a padded pitch Wq = Ho + 1 (x = Ho: padding
+// rows, computed and dropped) and each plane stored at padded positions
+// R = (Y + 1) Wq + (X + 1) (zero outside the input), tap (ky, kx) of row r is
+// plane (py, px) at R = r + (ky != 0) Wq + (kx != 0): one halo of
+// NS2 = 128 + Wq + 2 positions per plane and tile serves all nine taps, and
+// every input pixel is staged once per tile instead of once per tap.  A
+// stage holds the four planes of one tile for half of the 64 input channels
+// (4 planes x 4 eight-channel groups of 16-byte pixels), so that three
+// stages and the resident weights fit one SM; a tile is two stages, 18 MMAs
+// each.
+// ---------------------------------------------------------------------------
+struct ParGeo {
+    int Hi, Ho, Wq, NS, plane, per_img;   // plane: bytes of one 8-channel group of one parity plane
+};
+
+__host__ __device__ __forceinline__ ParGeo par_geo(int Hi, int Ho) {
+    ParGeo g;
+    g.Hi = Hi;
+    g.Ho = Ho;
+    g.Wq = Ho + 1;
+    g.NS = (BM + g.Wq + 2 + 7) / 8 * 8;
+    g.plane = g.NS * 16;
+    g.per_img = (Ho * g.Wq + BM - 1) / BM;
+    return g;
+}
+
+struct ParCfg {
+    static constexpr int K = 9 * CH;
+    static constexpr int B_BYTES = CH * K * 2;
+    static constexpr int STAGES = 3;              // (tile, channel half) units in flight
+    static constexpr int N_BARS = 2 * STAGES + 4;
+    __host__ __device__ static size_t stage_bytes(const ParGeo &g) { return (size_t)16 * g.plane; }
+    __host__ __device__ static size_t smem(const ParGeo &g) {
+        return 128 + B_BYTES + (size_t)STAGES * stage_bytes(g) + 8 * N_BARS + 16;
+    }
+};
+
+// Half h of the channels of the four parity planes of one tile (image img,
+// first row r0) into the stage at dst: plane (p, q) group gg at
+// dst + (4 (2 p + q) + gg) plane + position * 16; zero outside the input.
+__device__ __forceinline__ void load_parity(unsigned char *dst, const bf16 *img, const ParGeo &g, int r0, int h,
+                                            int tid, const bf16 *any) {
+    for (int sp = tid; sp < g.NS; sp += 128) {
+        const int R = r0 + sp, PY = R / g.Wq, PX = R - PY * g.Wq;
+        const int Y = PY - 1, X = PX - 1;
+#pragma unroll
+        for (int pq = 0; pq < 4; ++pq) {
+            const int iy = 2 * Y + (pq >> 1), ix = 2 * X + (pq & 1);
+            const bool ok = Y >= 0 && X >= 0 && iy < g.Hi && ix < g.Hi;
+            const bf16 *src = ok ? img + ((size_t)iy * g.Hi + ix) * CH + h * 32 : any;
+#pragma unroll
+            for (int gg = 0; gg < 4; ++gg)
+                cp_async16_ca(dst + (size_t)(4 * pq + gg) * g.plane + sp * 16, ok ? src + gg * 8 : any, ok);
+        }
+    }
+}
+
+// Forward convolution, stride 2, pad 1, 64 -> 64 channels: out = ReLU(conv +
+// bias); warp roles, barriers and bounded waits as k_conv_halo, with the
+// stages counted in (tile, channel half) units.
+__global__ void __launch_bounds__(kTcThreads, 1) k_conv_parity(const ConvArgs a, int *__restrict__ err) {
+    using C = ParCfg;
+    constexpr int S = C::STAGES;
+    const ParGeo pg = par_geo(a.Hi, a.Ho);
+    const int stage_bytes = (int)C::stage_bytes(pg);
+    extern __shared__ __align__(128) unsigned char tc_raw[];
+    unsigned char *base = tc_raw + ((128u - (tc_smem(tc_raw) & 127u)) & 127u);
+    unsigned char *Bs = base;
+    unsigned char *As = base + C::B_BYTES;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(As + (size_t)S * stage_bytes);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + C::N_BARS);
+    const uint32_t bar0 = tc_smem(bars);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n_tiles = a.B * pg.per_img;
+    __shared__ float s_bias[CH];
+
+    if (tid == 0) {
+        for (int i = 0; i < S; ++i) {
+            tc_mbar_init(bar0 + 8 * i, 128);
+            tc_mbar_init(bar0 + 8 * (S + i), 1);
+        }
+        for (int j = 0; j < 2; ++j) {
+            tc_mbar_init(bar0 + 8 * (2 * S + j), 1);
+            tc_mbar_init(bar0 + 8 * (2 * S + 2 + j), 128);
+        }
+        tc_fence_mbar_init();
+    }
+    if (tid < CH) s_bias[tid] = a.bias[tid];
+    if (warp == 8) tc_alloc(tc_smem(tslot), kTcCols);
+    for (int q = tid; q < CH * C::K / 8; q += kTcThreads) {
+        const int n = q / (C::K / 8), kg = q - n * (C::K / 8);
+        cp_async16_ca(Bs + ((size_t)(n >> 3) * (C::K / 8) + kg) * 128 + (n & 7) * 16, a.w + (size_t)n * C::K + kg * 8,
+                      true);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    tc_fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp < 4) {
+        constexpr int LAG = S - 2;
+        int u = 0;   // units issued: u = 2 g + h
+        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+            const int b = tile / pg.per_img, r0 = (tile - b * pg.per_img) * BM;
+            const bf16 *img = a.in + (size_t)(a.b0 + b) * a.Hi * a.Hi * CH;
+            bool ok = true;
+            for (int h = 0; h < 2; ++h, ++u) {
+                const int st = u % S;
+                if (!tc_mbar_wait(bar0 + 8 * (S + st), ((u / S) & 1) ^ 1)) {
+                    atomicOr(err, 1);
+                    ok = false;
+                    break;
+                }
+                load_parity(As + (size_t)st * stage_bytes, img, pg, r0, h, tid, a.in);
+                cp_async_commit();
+                if (u >= LAG) {
+                    cp_async_wait<LAG>();
+                    tc_fence_proxy_async();
+                    tc_mbar_arrive(bar0 + 8 * ((u - LAG) % S));
+                }
+            }
+            if (!ok) break;
+        }
+        cp_async_wait<0>();
+        tc_fence_proxy_async();
+        for (int q = (u > LAG ? u - LAG : 0); q < u; ++q) tc_mbar_arrive(bar0 + 8 * (q % S));
+    } else if (warp == 8) {
+        if (lane == 0) {
+            const uint32_t idesc = tc_idesc_bf16(BM, CH);
+            const uint32_t a_base = tc_smem(As), b_base = tc_smem(Bs);
+            int g = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++g) {
+                const int ab = g & 1;
+                if (!tc_mbar_wait(bar0 + 8 * (2 * S + 2 + ab), ((g >> 1) & 1) ^ 1)) {
+                    atomicOr(err, 1);
+                    break;
+                }
+                const uint32_t d = tmem + (uint32_t)(ab * kTcParts * CH);
+                int n_mma = 0;
+                for (int h = 0; h < 2; ++h) {
+                    const int u = 2 * g + h, st = u % S;
+                    if (!tc_mbar_wait(bar0 + 8 * st, (u / S) & 1)) {
+                        atomicOr(err, 1);
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t as = a_base + (uint32_t)(st * stage_bytes);
+#pragma unroll 1
+                    for (int tap = 0; tap < 9; ++tap) {
+                        const int ky = tap / 3, kx = tap - ky * 3;
+                        const int pq = 2 * (ky != 1) + (kx != 1);
+                        const uint32_t at =
+                            as + (uint32_t)(4 * pq * pg.plane) + (uint32_t)(((ky != 0) * pg.Wq + (kx != 0)) * 16);
+                        const uint32_t bt = b_base + (uint32_t)((tap * 8 + 4 * h) * 128);
+#pragma unroll
+                        for (int j = 0; j < 2; ++j, ++n_mma)
+                            tc_mma(d + (uint32_t)((n_mma % kTcParts) * CH),
+                                   tc_desc(at + 2 * j * pg.plane, pg.plane, 128), tc_desc(bt + j * 256, 128, C::K * 16),
+                                   idesc, n_mma >= kTcParts);
+                    }
+                    tc_commit(bar0 + 8 * (S + st));
+                }
+                if (!ok) break;
+                tc_commit(bar0 + 8 * (2 * S + ab));
+            }
+        }
+        __syncwarp();
+    } else {
+        const int e = warp - 4;
+        const uint32_t lane_base = tmem + ((uint32_t)(32 * e) << 16);
+        int g = 0;
+        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++g) {
+            const int ab = g & 1;
+            if (!tc_mbar_wait(bar0 + 8 * (2 * S + ab), (g >> 1) & 1)) {
+                atomicOr(err, 1);
+                break;
+            }
+            tc_fence_after();
+            const int b = tile / pg.per_img;
+            const int r = (tile - b * pg.per_img) * BM + 32 * e + lane;
+            const int y = r / pg.Wq, x = r - y * pg.Wq;
+            const bool keep = y < pg.Ho && x < pg.Ho;
+            bf16 *row = a.out + (((size_t)b * pg.Ho + y) * pg.Ho + x) * CH;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 float v[32];
@@ -1381,6 +1595,22 @@ cudaError_t launch_halo_fwd(const ConvArgs &a, int *err, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Stride-2 forward convolution on parity planes: persistent, one CTA per SM
+// (shared memory), at most one per tile.
+cudaError_t launch_parity_fwd(const ConvArgs &a, int *err, cudaStream_t st) {
+    static size_t set_to = 0;
+    const ParGeo pg = par_geo(a.Hi, a.Ho);
+    const size_t smem = std::max(ParCfg::smem(pg), kExclusiveSmem);
+    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+    cudaError_t e = smem_limit(k_conv_parity, smem, set_to);
+    if (e != cudaSuccess) return e;
+    const long long tiles = (long long)a.B * pg.per_img;
+    if (tiles == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)std::min<long long>(tiles, (long long)sm_count());
+    k_conv_parity<<<grid, kTcThreads, smem, st>>>(a, err);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_conv_fwd(const CnnState &S, int layer, const bf16 *in, const int *perm, long long b0, int B,
                             cudaStream_t st) {
     ConvArgs a{};
@@ -1396,7 +1626,7 @@ cudaError_t launch_conv_fwd(const CnnState &S, int layer, const bf16 *in, const 
         a.w = S.w3; a.bias = S.master + S.off_b3; a.out = S.a3; a.Hi = S.H2; a.Ho = S.H3; a.stride = 2;
     }
     if (layer == 1) return S.C0 == 32 ? launch_halo_fwd<32>(a, S.d_err, st) : launch_halo_fwd<64>(a, S.d_err, st);
-    return launch_tc<false, 64>(a, S.d_err, st);
+    return launch_parity_fwd(a, S.d_err, st);
 }
 
 // Input gradient of layer 3 (into dz2) or layer 2 (into dz1).

@@ -64,7 +64,7 @@ def test_gemm_on_strided_operands():
     assert float((C.double() - ref).abs().max()) <= 2e-6 * float((A.double().abs() @ B.double().abs().t()).max())
 
 
-@pytest.mark.parametrize("n,m", [(128, 64), (300, 257), (650, 1000)])
+@pytest.mark.parametrize("n,m", [(128, 64), (300, 257), (650, 1000), (1300, 40)])
 def test_spd_solve_matches_fp64(n, m):
     L = abi.load()
     rng = np.random.default_rng(n + m)
