@@ -35,7 +35,9 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 
 #include "synim_internal.h"
 #include "synim_cpasync.cuh"
@@ -72,6 +74,7 @@ struct CnnState {
     long long n_data = 0, data_cap = 0;
     float *h_loss = nullptr;   // pinned [kBatchCap]
     int *d_err = nullptr;      // bit 0: a bounded wait of the tensor-core convolution gave up
+    CUtensorMap map_a1, map_a2;   // a1 / a2 as [kBatchCap][H][H][64] BF16, parity-plane boxes (k_conv_parity)
 };
 
 void cnn_destroy(CnnState *s) {
@@ -655,7 +658,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_halo(const ConvArgs a, i
 // each.
 // ---------------------------------------------------------------------------
 struct ParGeo {
-    int Hi, Ho, Wq, NS, plane, per_img;   // plane: bytes of one 8-channel group of one parity plane
+    int Hi, Ho, Wq, NR, plane, per_img;   // NR: plane rows per tile; plane: bytes of one 8-channel group
 };
 
 __host__ __device__ __forceinline__ ParGeo par_geo(int Hi, int Ho) {
@@ -663,8 +666,9 @@ __host__ __device__ __forceinline__ ParGeo par_geo(int Hi, int Ho) {
     g.Hi = Hi;
     g.Ho = Ho;
     g.Wq = Ho + 1;
-    g.NS = (BM + g.Wq + 2 + 7) / 8 * 8;
-    g.plane = g.NS * 16;
+    // a tile's rows r0 .. r0 + 127 read positions up to r0 + 128 + Wq, from plane row r0 / Wq on
+    g.NR = (BM + g.Wq) / g.Wq + 2;
+    g.plane = (g.NR * g.Wq * 16 + 127) / 128 * 128;
     g.per_img = (Ho * g.Wq + BM - 1) / BM;
     return g;
 }
@@ -680,30 +684,30 @@ struct ParCfg {
     }
 };
 
-// Half h of the channels of the four parity planes of one tile (image img,
-// first row r0) into the stage at dst: plane (p, q) group gg at
-// dst + (4 (2 p + q) + gg) plane + position * 16; zero outside the input.
-__device__ __forceinline__ void load_parity(unsigned char *dst, const bf16 *img, const ParGeo &g, int r0, int h,
-                                            int tid, const bf16 *any) {
-    for (int sp = tid; sp < g.NS; sp += 128) {
-        const int R = r0 + sp, PY = R / g.Wq, PX = R - PY * g.Wq;
-        const int Y = PY - 1, X = PX - 1;
-#pragma unroll
-        for (int pq = 0; pq < 4; ++pq) {
-            const int iy = 2 * Y + (pq >> 1), ix = 2 * X + (pq & 1);
-            const bool ok = Y >= 0 && X >= 0 && iy < g.Hi && ix < g.Hi;
-            const bf16 *src = ok ? img + ((size_t)iy * g.Hi + ix) * CH + h * 32 : any;
-#pragma unroll
-            for (int gg = 0; gg < 4; ++gg)
-                cp_async16_ca(dst + (size_t)(4 * pq + gg) * g.plane + sp * 16, ok ? src + gg * 8 : any, ok);
-        }
-    }
+// One 4-D tensor-map tile load (TMA) into shared memory, completing on mbar.
+__device__ __forceinline__ void tma_load4(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                          uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(mbar)
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
 // Forward convolution, stride 2, pad 1, 64 -> 64 channels: out = ReLU(conv +
 // bias); warp roles, barriers and bounded waits as k_conv_halo, with the
-// stages counted in (tile, channel half) units.
-__global__ void __launch_bounds__(kTcThreads, 1) k_conv_parity(const ConvArgs a, int *__restrict__ err) {
+// stages counted in (tile, channel half) units.  One producer thread fills a
+// stage with 16 tensor-map loads (4 planes x 4 eight-channel groups): the
+// map's element strides of 2 along x and y pick one parity plane, its box
+// covers NR plane rows x Wq columns from plane position (r0 / Wq) Wq, and
+// coordinates outside the input (the zero padding) are filled with zeros.
+__global__ void __launch_bounds__(kTcThreads, 1) k_conv_parity(const ConvArgs a,
+                                                               const __grid_constant__ CUtensorMap in_map,
+                                                               int *__restrict__ err) {
     using C = ParCfg;
     constexpr int S = C::STAGES;
     const ParGeo pg = par_geo(a.Hi, a.Ho);
@@ -721,7 +725,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_parity(const ConvArgs a,
 
     if (tid == 0) {
         for (int i = 0; i < S; ++i) {
-            tc_mbar_init(bar0 + 8 * i, 128);
+            tc_mbar_init(bar0 + 8 * i, 1);
             tc_mbar_init(bar0 + 8 * (S + i), 1);
         }
         for (int j = 0; j < 2; ++j) {
@@ -745,33 +749,36 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_parity(const ConvArgs a,
     tc_fence_after();
     const uint32_t tmem = *tslot;
 
-    if (warp < 4) {
-        constexpr int LAG = S - 2;
-        int u = 0;   // units issued: u = 2 g + h
-        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-            const int b = tile / pg.per_img, r0 = (tile - b * pg.per_img) * BM;
-            const bf16 *img = a.in + (size_t)(a.b0 + b) * a.Hi * a.Hi * CH;
+    if (warp == 0) {
+        if (lane == 0) {
+            const uint32_t box_bytes = (uint32_t)(pg.NR * pg.Wq * 16);
+            int u = 0;   // units issued: u = 2 g + h
             bool ok = true;
-            for (int h = 0; h < 2; ++h, ++u) {
-                const int st = u % S;
-                if (!tc_mbar_wait(bar0 + 8 * (S + st), ((u / S) & 1) ^ 1)) {
-                    atomicOr(err, 1);
-                    ok = false;
-                    break;
-                }
-                load_parity(As + (size_t)st * stage_bytes, img, pg, r0, h, tid, a.in);
-                cp_async_commit();
-                if (u >= LAG) {
-                    cp_async_wait<LAG>();
-                    tc_fence_proxy_async();
-                    tc_mbar_arrive(bar0 + 8 * ((u - LAG) % S));
+            for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+                const int b = tile / pg.per_img, r0 = (tile - b * pg.per_img) * BM;
+                const int py0 = r0 / pg.Wq;
+                for (int h = 0; h < 2; ++h, ++u) {
+                    const int st = u % S;
+                    if (!tc_mbar_wait(bar0 + 8 * (S + st), ((u / S) & 1) ^ 1)) {
+                        atomicOr(err, 1);
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t full = bar0 + 8 * st;
+                    mbar_expect_tx(full, 16 * box_bytes);
+                    const uint32_t dst = tc_smem(As + (size_t)st * stage_bytes);
+#pragma unroll 1
+                    for (int pq = 0; pq < 4; ++pq)
+#pragma unroll
+                        for (int gg = 0; gg < 4; ++gg)
+                            tma_load4(dst + (uint32_t)((4 * pq + gg) * pg.plane), &in_map, h * 32 + gg * 8,
+                                      (pq & 1) - 2, 2 * (py0 - 1) + (pq >> 1), (int)(a.b0 + b), full);
                 }
             }
-            if (!ok) break;
         }
-        cp_async_wait<0>();
-        tc_fence_proxy_async();
-        for (int q = (u > LAG ? u - LAG : 0); q < u; ++q) tc_mbar_arrive(bar0 + 8 * (q % S));
+        __syncwarp();
+    } else if (warp < 4) {
+        // the other producer warps have nothing to stage
     } else if (warp == 8) {
         if (lane == 0) {
             const uint32_t idesc = tc_idesc_bf16(BM, CH);
@@ -785,6 +792,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_parity(const ConvArgs a,
                     break;
                 }
                 const uint32_t d = tmem + (uint32_t)(ab * kTcParts * CH);
+                const int r0 = (tile - (tile / pg.per_img) * pg.per_img) * BM;
+                const int rel = r0 - (r0 / pg.Wq) * pg.Wq;   // the tile's first row within the loaded box
                 int n_mma = 0;
                 for (int h = 0; h < 2; ++h) {
                     const int u = 2 * g + h, st = u % S;
@@ -799,8 +808,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_parity(const ConvArgs a,
                     for (int tap = 0; tap < 9; ++tap) {
                         const int ky = tap / 3, kx = tap - ky * 3;
                         const int pq = 2 * (ky != 1) + (kx != 1);
-                        const uint32_t at =
-                            as + (uint32_t)(4 * pq * pg.plane) + (uint32_t)(((ky != 0) * pg.Wq + (kx != 0)) * 16);
+                        const uint32_t at = as + (uint32_t)(4 * pq * pg.plane) +
+                                            (uint32_t)((rel + (ky != 0) * pg.Wq + (kx != 0)) * 16);
                         const uint32_t bt = b_base + (uint32_t)((tap * 8 + 4 * h) * 128);
 #pragma unroll
                         for (int j = 0; j < 2; ++j, ++n_mma)
@@ -1595,9 +1604,33 @@ cudaError_t launch_halo_fwd(const ConvArgs &a, int *err, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Tensor map of a [kBatchCap][H][H][64] BF16 activation for k_conv_parity:
+// boxes of 8 channels x Wq columns x NR rows of one parity plane (element
+// strides 2 along x and y), zero fill outside.
+cudaError_t make_parity_map(CUtensorMap *map, const bf16 *act, int H) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess) return e;
+        if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const ParGeo pg = par_geo(H, conv_out(H, 2));
+    const cuuint64_t dims[4] = {(cuuint64_t)CH, (cuuint64_t)H, (cuuint64_t)H, (cuuint64_t)kBatchCap};
+    const cuuint64_t strides[3] = {(cuuint64_t)CH * 2, (cuuint64_t)H * CH * 2, (cuuint64_t)H * H * CH * 2};
+    const cuuint32_t box[4] = {8, (cuuint32_t)(2 * pg.Wq), (cuuint32_t)(2 * pg.NR), 1};
+    const cuuint32_t estr[4] = {1, 2, 2, 1};
+    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(act), dims, strides, box,
+                              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 // Stride-2 forward convolution on parity planes: persistent, one CTA per SM
 // (shared memory), at most one per tile.
-cudaError_t launch_parity_fwd(const ConvArgs &a, int *err, cudaStream_t st) {
+cudaError_t launch_parity_fwd(const ConvArgs &a, const CUtensorMap &map, int *err, cudaStream_t st) {
     static size_t set_to = 0;
     const ParGeo pg = par_geo(a.Hi, a.Ho);
     const size_t smem = std::max(ParCfg::smem(pg), kExclusiveSmem);
@@ -1607,7 +1640,7 @@ cudaError_t launch_parity_fwd(const ConvArgs &a, int *err, cudaStream_t st) {
     const long long tiles = (long long)a.B * pg.per_img;
     if (tiles == 0) return cudaSuccess;
     const unsigned grid = (unsigned)std::min<long long>(tiles, (long long)sm_count());
-    k_conv_parity<<<grid, kTcThreads, smem, st>>>(a, err);
+    k_conv_parity<<<grid, kTcThreads, smem, st>>>(a, map, err);
     return cudaGetLastError();
 }
 
@@ -1626,7 +1659,7 @@ cudaError_t launch_conv_fwd(const CnnState &S, int layer, const bf16 *in, const 
         a.w = S.w3; a.bias = S.master + S.off_b3; a.out = S.a3; a.Hi = S.H2; a.Ho = S.H3; a.stride = 2;
     }
     if (layer == 1) return S.C0 == 32 ? launch_halo_fwd<32>(a, S.d_err, st) : launch_halo_fwd<64>(a, S.d_err, st);
-    return launch_parity_fwd(a, S.d_err, st);
+    return launch_parity_fwd(a, layer == 2 ? S.map_a1 : S.map_a2, S.d_err, st);
 }
 
 // Input gradient of layer 3 (into dz2) or layer 2 (into dz1).
@@ -1789,6 +1822,8 @@ cudaError_t alloc_state(CnnState &S) {
 #undef SYNIM_A
     if (e == cudaSuccess) e = cudaMemset(S.d_err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMallocHost(&S.h_loss, sizeof(float) * kBatchCap);
+    if (e == cudaSuccess) e = make_parity_map(&S.map_a1, S.a1, S.H1);
+    if (e == cudaSuccess) e = make_parity_map(&S.map_a2, S.a2, S.H2);
     return e;
 }
 
