@@ -481,10 +481,13 @@ synim_status synim_cnn_init(synim_ctx *ctx, const float *params, const double *n
 /* Copy the current parameters (host [n_params]) and normalisation (host [8]); either may be NULL. */
 synim_status synim_cnn_get(const synim_ctx *ctx, float *params, double *norm);
 
-/* Normalised outputs (device [n][4] FP32) for bfloat16 maps x (device [n][n_sub][n_sub][C]). */
+/* Normalised outputs (device [n][4] FP32) for bfloat16 maps x (device [n][n_sub][n_sub][C],
+ * 16-byte aligned: the first layer reads it through a TMA tensor map; SYNIM_ERR_INVALID_ARG
+ * otherwise). */
 synim_status synim_cnn_forward(synim_ctx *ctx, const uint16_t *x, int64_t n, float *out, void *cuda_stream);
 
-/* One forward and backward pass without an update, 1 <= n <= 256: loss_out
+/* One forward and backward pass without an update, 1 <= n <= 256 (x 16-byte aligned, as
+ * for synim_cnn_forward): loss_out
  * (host, may be NULL) = mean squared error over the n x 4 outputs against
  * target (device [n][4], normalised); grad_out (host [n_params], may be
  * NULL) = its gradient.  Synchronous. */

@@ -75,6 +75,7 @@ struct CnnState {
     float *h_loss = nullptr;   // pinned [kBatchCap]
     int *d_err = nullptr;      // bit 0: a bounded wait of the tensor-core convolution gave up
     CUtensorMap map_a1, map_a2;   // a1 / a2 as [kBatchCap][H][H][64] BF16, parity-plane boxes (k_conv_parity)
+    CUtensorMap map_x, map_data;  // x [kBatchCap] and data [data_cap] inputs, halo boxes (k_conv_halo)
 };
 
 void cnn_destroy(CnnState *s) {
@@ -493,15 +494,62 @@ struct HaloCfg {
     }
 };
 
+// One 4-D tensor-map tile load (TMA) into shared memory, completing on mbar.
+__device__ __forceinline__ void tma_load4(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                          uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(mbar)
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// The forward halo as tensor-map boxes: whole padded rows from row r0 / Wp,
+// NR of them (rows r0 .. r0 + 127 read positions up to r0 + 127 + 2 Wp + 2),
+// one box of 8 channels x Wp columns x NR rows per 8-channel group; a group's
+// region is rounded up to 128 bytes.
+struct HaloTma {
+    int NR, plane;
+};
+
+__host__ __device__ __forceinline__ HaloTma halo_tma(const HaloGeo &g) {
+    HaloTma t;
+    t.NR = (BM + 2 * g.Wp + 2) / g.Wp + 2;
+    t.plane = (t.NR * g.Wp * 16 + 127) / 128 * 128;
+    return t;
+}
+
+template <int CIN>
+struct HaloTmaCfg {
+    static constexpr int K = 9 * CIN;
+    static constexpr int KG = CIN / 8;
+    static constexpr int B_BYTES = CH * K * 2;
+    static constexpr int STAGES = (CIN == 32) ? 8 : 3;
+    static constexpr int N_BARS = 2 * STAGES + 4;
+    __host__ __device__ static size_t smem(const HaloTma &t) {
+        return 128 + B_BYTES + (size_t)STAGES * KG * t.plane + 8 * N_BARS + 16;
+    }
+};
+
 // Forward convolution, stride 1, pad 1: out = ReLU(conv(in) + bias), same
 // warp roles, barriers and bounded waits as k_conv_tc; a stage holds one
 // tile's halo and feeds 9 taps x CIN / 16 MMAs.
+// The halo comes from the layer input's tensor map (4-D [samples][H][H][CIN]
+// BF16, boxes as halo_tma): one producer thread issues the CIN / 8 box loads
+// of a tile, starting at column -1 and row r0 / Wp - 1 of the image (zero
+// fill outside it gives the padding).
 template <int CIN>
-__global__ void __launch_bounds__(kTcThreads, 1) k_conv_halo(const ConvArgs a, int *__restrict__ err) {
-    using C = HaloCfg<CIN>;
+__global__ void __launch_bounds__(kTcThreads, 1) k_conv_halo(const ConvArgs a, const __grid_constant__ CUtensorMap in_map,
+                                                             int *__restrict__ err) {
+    using C = HaloTmaCfg<CIN>;
     constexpr int S = C::STAGES;
     const HaloGeo hg = halo_geo(a.Ho);
-    const int stage_bytes = C::KG * hg.plane;
+    const HaloTma ht = halo_tma(hg);
+    const int stage_bytes = C::KG * ht.plane;
     extern __shared__ __align__(128) unsigned char tc_raw[];
     unsigned char *base = tc_raw + ((128u - (tc_smem(tc_raw) & 127u)) & 127u);
     unsigned char *Bs = base;
@@ -515,7 +563,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_halo(const ConvArgs a, i
 
     if (tid == 0) {
         for (int i = 0; i < S; ++i) {
-            tc_mbar_init(bar0 + 8 * i, 128);
+            tc_mbar_init(bar0 + 8 * i, 1);
             tc_mbar_init(bar0 + 8 * (S + i), 1);
         }
         for (int j = 0; j < 2; ++j) {
@@ -539,38 +587,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_halo(const ConvArgs a, i
     tc_fence_after();
     const uint32_t tmem = *tslot;
 
-    if (warp < 4) {
-        constexpr int LAG = S - 2;
-        int g = 0;
-        // sample of the next tile, loaded one tile ahead
-        long long sb_next = 0;
-        if (blockIdx.x < n_tiles) {
-            const int b = blockIdx.x / hg.per_img;
-            sb_next = a.perm ? (long long)a.perm[a.b0 + b] : a.b0 + b;
-        }
-        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++g) {
-            const long long sb = sb_next;
-            if (tile + (int)gridDim.x < n_tiles) {
-                const int bn = (tile + (int)gridDim.x) / hg.per_img;
-                sb_next = a.perm ? (long long)a.perm[a.b0 + bn] : a.b0 + bn;
-            }
-            const int st = g % S;
-            if (!tc_mbar_wait(bar0 + 8 * (S + st), ((g / S) & 1) ^ 1)) {
-                atomicOr(err, 1);
-                break;
-            }
-            const int b = tile / hg.per_img, r0 = (tile - b * hg.per_img) * BM;
-            load_halo<CIN>(As + (size_t)st * stage_bytes, a.in + (size_t)sb * a.Hi * a.Hi * CIN, hg, r0, tid, a.in);
-            cp_async_commit();
-            if (g >= LAG) {
-                cp_async_wait<LAG>();
-                tc_fence_proxy_async();
-                tc_mbar_arrive(bar0 + 8 * ((g - LAG) % S));
+    if (warp == 0) {
+        if (lane == 0) {
+            const uint32_t box_bytes = (uint32_t)(ht.NR * hg.Wp * 16);
+            int g = 0;
+            for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++g) {
+                const int b = tile / hg.per_img, r0 = (tile - b * hg.per_img) * BM;
+                const int sb = a.perm ? a.perm[a.b0 + b] : (int)(a.b0 + b);
+                const int st = g % S;
+                if (!tc_mbar_wait(bar0 + 8 * (S + st), ((g / S) & 1) ^ 1)) {
+                    atomicOr(err, 1);
+                    break;
+                }
+                const uint32_t full = bar0 + 8 * st;
+                mbar_expect_tx(full, C::KG * box_bytes);
+                const uint32_t dst = tc_smem(As + (size_t)st * stage_bytes);
+#pragma unroll
+                for (int gg = 0; gg < C::KG; ++gg)
+                    tma_load4(dst + (uint32_t)(gg * ht.plane), &in_map, gg * 8, -1, r0 / hg.Wp - 1, sb, full);
             }
         }
-        cp_async_wait<0>();
-        tc_fence_proxy_async();
-        for (int q = (g > LAG ? g - LAG : 0); q < g; ++q) tc_mbar_arrive(bar0 + 8 * (q % S));
+        __syncwarp();
+    } else if (warp < 4) {
+        // the other producer warps have nothing to stage
     } else if (warp == 8) {
         if (lane == 0) {
             const uint32_t idesc = tc_idesc_bf16(BM, CH);
@@ -590,15 +629,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_halo(const ConvArgs a, i
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(ab * kTcParts * CH);
                 const uint32_t as = a_base + (uint32_t)(st * stage_bytes);
+                const int r0 = (tile - (tile / hg.per_img) * hg.per_img) * BM;
+                const int rel = r0 - (r0 / hg.Wp) * hg.Wp;   // the tile's first row within the loaded rows
                 int n_mma = 0;
 #pragma unroll 1
                 for (int tap = 0; tap < 9; ++tap) {
                     const int ky = tap / 3, kx = tap - ky * 3;
-                    const uint32_t at = as + (uint32_t)((ky * hg.Wp + kx) * 16);
+                    const uint32_t at = as + (uint32_t)((rel + ky * hg.Wp + kx) * 16);
                     const uint32_t bt = b_base + (uint32_t)(tap * C::KG * 128);
 #pragma unroll
                     for (int j = 0; j < CIN / 16; ++j, ++n_mma)
-                        tc_mma(d + (uint32_t)((n_mma % kTcParts) * CH), tc_desc(at + 2 * j * hg.plane, hg.plane, 128),
+                        tc_mma(d + (uint32_t)((n_mma % kTcParts) * CH), tc_desc(at + 2 * j * ht.plane, ht.plane, 128),
                                tc_desc(bt + j * 256, 128, C::K * 16), idesc, n_mma >= kTcParts);
                 }
                 tc_commit(bar0 + 8 * (S + st));
@@ -684,19 +725,6 @@ struct ParCfg {
     }
 };
 
-// One 4-D tensor-map tile load (TMA) into shared memory, completing on mbar.
-__device__ __forceinline__ void tma_load4(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
-                                          uint32_t mbar) {
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
-        "[%6];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(mbar)
-        : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
 
 // Forward convolution, stride 2, pad 1, 64 -> 64 channels: out = ReLU(conv +
 // bias); warp roles, barriers and bounded waits as k_conv_halo, with the
@@ -1582,11 +1610,11 @@ cudaError_t launch_tc(const ConvArgs &a, int *err, cudaStream_t st) {
 // as fit (shared memory limits them to one or two per SM, whose TMEM columns
 // then fit in the 512 of an SM), at most one per tile.
 template <int CIN>
-cudaError_t launch_halo_fwd(const ConvArgs &a, int *err, cudaStream_t st) {
+cudaError_t launch_halo_fwd(const ConvArgs &a, const CUtensorMap &map, int *err, cudaStream_t st) {
     static size_t set_to = 0;
     static int per_sm = 0, per_sm_for = -1;
     const HaloGeo hg = halo_geo(a.Ho);
-    const size_t smem = std::max(HaloCfg<CIN>::smem(hg), kExclusiveSmem);
+    const size_t smem = std::max(HaloTmaCfg<CIN>::smem(halo_tma(hg)), kExclusiveSmem);
     if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
     cudaError_t e = smem_limit(k_conv_halo<CIN>, smem, set_to);
     if (e != cudaSuccess) return e;
@@ -1600,14 +1628,14 @@ cudaError_t launch_halo_fwd(const ConvArgs &a, int *err, cudaStream_t st) {
     const long long tiles = (long long)a.B * hg.per_img;
     if (tiles == 0) return cudaSuccess;
     const unsigned grid = (unsigned)std::min<long long>(tiles, (long long)sm_count() * per_sm);
-    k_conv_halo<CIN><<<grid, kTcThreads, smem, st>>>(a, err);
+    k_conv_halo<CIN><<<grid, kTcThreads, smem, st>>>(a, map, err);
     return cudaGetLastError();
 }
 
-// Tensor map of a [kBatchCap][H][H][64] BF16 activation for k_conv_parity:
-// boxes of 8 channels x Wq columns x NR rows of one parity plane (element
-// strides 2 along x and y), zero fill outside.
-cudaError_t make_parity_map(CUtensorMap *map, const bf16 *act, int H) {
+// Tensor map of n samples of a [n][H][H][C] BF16 activation (16-byte
+// aligned): boxes of 8 channels x bx columns x by rows, element stride es
+// along x and y, zero fill outside.
+cudaError_t make_act_map(CUtensorMap *map, const bf16 *act, long long n, int H, int C, int bx, int by, int es) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
         void *fn = nullptr;
@@ -1617,15 +1645,27 @@ cudaError_t make_parity_map(CUtensorMap *map, const bf16 *act, int H) {
         if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
         encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }
-    const ParGeo pg = par_geo(H, conv_out(H, 2));
-    const cuuint64_t dims[4] = {(cuuint64_t)CH, (cuuint64_t)H, (cuuint64_t)H, (cuuint64_t)kBatchCap};
-    const cuuint64_t strides[3] = {(cuuint64_t)CH * 2, (cuuint64_t)H * CH * 2, (cuuint64_t)H * H * CH * 2};
-    const cuuint32_t box[4] = {8, (cuuint32_t)(2 * pg.Wq), (cuuint32_t)(2 * pg.NR), 1};
-    const cuuint32_t estr[4] = {1, 2, 2, 1};
+    if ((reinterpret_cast<uintptr_t>(act) & 15) != 0 || n < 1) return cudaErrorInvalidValue;
+    const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)H, (cuuint64_t)H, (cuuint64_t)n};
+    const cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)H * C * 2, (cuuint64_t)H * H * C * 2};
+    const cuuint32_t box[4] = {8, (cuuint32_t)(es * bx), (cuuint32_t)(es * by), 1};
+    const cuuint32_t estr[4] = {1, (cuuint32_t)es, (cuuint32_t)es, 1};
     const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(act), dims, strides, box,
                               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// k_conv_parity's map of a 64-channel activation ([kBatchCap][H][H][64]).
+cudaError_t make_parity_map(CUtensorMap *map, const bf16 *act, int H) {
+    const ParGeo pg = par_geo(H, conv_out(H, 2));
+    return make_act_map(map, act, kBatchCap, H, CH, pg.Wq, pg.NR, 2);
+}
+
+// k_conv_halo's map of n network inputs ([n][H0][H0][C0]).
+cudaError_t make_input_map(CUtensorMap *map, const bf16 *x, long long n, int H, int C) {
+    const HaloGeo hg = halo_geo(H);
+    return make_act_map(map, x, n, H, C, hg.Wp, halo_tma(hg).NR, 1);
 }
 
 // Stride-2 forward convolution on parity planes: persistent, one CTA per SM
@@ -1644,8 +1684,8 @@ cudaError_t launch_parity_fwd(const ConvArgs &a, const CUtensorMap &map, int *er
     return cudaGetLastError();
 }
 
-cudaError_t launch_conv_fwd(const CnnState &S, int layer, const bf16 *in, const int *perm, long long b0, int B,
-                            cudaStream_t st) {
+cudaError_t launch_conv_fwd(const CnnState &S, int layer, const bf16 *in, const CUtensorMap &map, const int *perm,
+                            long long b0, int B, cudaStream_t st) {
     ConvArgs a{};
     a.in = in;
     a.perm = perm;
@@ -1658,8 +1698,9 @@ cudaError_t launch_conv_fwd(const CnnState &S, int layer, const bf16 *in, const 
     } else {
         a.w = S.w3; a.bias = S.master + S.off_b3; a.out = S.a3; a.Hi = S.H2; a.Ho = S.H3; a.stride = 2;
     }
-    if (layer == 1) return S.C0 == 32 ? launch_halo_fwd<32>(a, S.d_err, st) : launch_halo_fwd<64>(a, S.d_err, st);
-    return launch_parity_fwd(a, layer == 2 ? S.map_a1 : S.map_a2, S.d_err, st);
+    if (layer == 1)
+        return S.C0 == 32 ? launch_halo_fwd<32>(a, map, S.d_err, st) : launch_halo_fwd<64>(a, map, S.d_err, st);
+    return launch_parity_fwd(a, map, S.d_err, st);
 }
 
 // Input gradient of layer 3 (into dz2) or layer 2 (into dz1).
@@ -1751,12 +1792,12 @@ cudaError_t pack_weights(CnnState &S, cudaStream_t st) {
 
 // Forward of B <= kBatchCap samples (inputs at in / perm / b0); with targets,
 // the per-sample squared errors go to S.loss.
-cudaError_t forward(CnnState &S, const bf16 *in, const int *perm, long long b0, int B, const float *tgt,
-                    cudaStream_t st) {
+cudaError_t forward(CnnState &S, const bf16 *in, const CUtensorMap &in_map, const int *perm, long long b0, int B,
+                    const float *tgt, cudaStream_t st) {
     cudaError_t e;
-    if ((e = launch_conv_fwd(S, 1, in, perm, b0, B, st)) != cudaSuccess) return e;
-    if ((e = launch_conv_fwd(S, 2, S.a1, nullptr, 0, B, st)) != cudaSuccess) return e;
-    if ((e = launch_conv_fwd(S, 3, S.a2, nullptr, 0, B, st)) != cudaSuccess) return e;
+    if ((e = launch_conv_fwd(S, 1, in, in_map, perm, b0, B, st)) != cudaSuccess) return e;
+    if ((e = launch_conv_fwd(S, 2, S.a1, S.map_a1, nullptr, 0, B, st)) != cudaSuccess) return e;
+    if ((e = launch_conv_fwd(S, 3, S.a2, S.map_a2, nullptr, 0, B, st)) != cudaSuccess) return e;
     // the head: blocks of 8 samples x a share of the features, about 256
     // blocks in all (32 feature parts for one group of 8, 8 for 32 groups)
     const int groups = (B + kHeadSamples - 1) / kHeadSamples;
@@ -1824,6 +1865,7 @@ cudaError_t alloc_state(CnnState &S) {
     if (e == cudaSuccess) e = cudaMallocHost(&S.h_loss, sizeof(float) * kBatchCap);
     if (e == cudaSuccess) e = make_parity_map(&S.map_a1, S.a1, S.H1);
     if (e == cudaSuccess) e = make_parity_map(&S.map_a2, S.a2, S.H2);
+    if (e == cudaSuccess) e = make_input_map(&S.map_x, S.x, kBatchCap, S.H0, S.C0);
     return e;
 }
 
@@ -1882,7 +1924,7 @@ cudaError_t cnn_predict_slopes(synim_ctx *c, const float *y, long long n, double
     for (long long s0 = 0; s0 < n && e == cudaSuccess; s0 += kBatchCap) {
         const int B = (int)std::min<long long>(kBatchCap, n - s0);
         k_to_bf16<<<blocks_for(B * per, 256), 256, 0, st>>>(y + s0 * per, B * per, S->x);
-        if ((e = forward(*S, S->x, nullptr, 0, B, nullptr, st)) != cudaSuccess) break;
+        if ((e = forward(*S, S->x, S->map_x, nullptr, 0, B, nullptr, st)) != cudaSuccess) break;
         k_denorm<<<blocks_for(B, 128), 128, 0, st>>>(S->out, B, norm4(*S), params_out + 4 * s0);
         e = cudaGetLastError();
     }
@@ -2049,9 +2091,13 @@ synim_status synim_cnn_forward(synim_ctx *ctx, const uint16_t *x, int64_t n, flo
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     cudaError_t e = cudaSuccess;
     const bf16 *xb = reinterpret_cast<const bf16 *>(x);
+    CUtensorMap xmap;
+    if (n > 0 && (e = make_input_map(&xmap, xb, n, S.H0, S.C0)) != cudaSuccess)
+        return e == cudaErrorInvalidValue ? cfail(ctx, SYNIM_ERR_INVALID_ARG, "cnn_forward: x must be 16-byte aligned")
+                                          : ccuda(ctx, e, "cnn_forward");
     for (long long s0 = 0; s0 < n && e == cudaSuccess; s0 += kBatchCap) {
         const int B = (int)std::min<long long>(kBatchCap, n - s0);
-        if ((e = forward(S, xb, nullptr, s0, B, nullptr, st)) != cudaSuccess) break;
+        if ((e = forward(S, xb, xmap, nullptr, s0, B, nullptr, st)) != cudaSuccess) break;
         e = cudaMemcpyAsync(out + 4 * s0, S.out, sizeof(float) * 4 * B, cudaMemcpyDeviceToDevice, st);
     }
     return e == cudaSuccess ? SYNIM_OK : ccuda(ctx, e, "cnn_forward");
@@ -2067,7 +2113,10 @@ synim_status synim_cnn_grad(synim_ctx *ctx, const uint16_t *x, const float *targ
     CnnState &S = *ctx->cnn;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const bf16 *xb = reinterpret_cast<const bf16 *>(x);
-    cudaError_t e = forward(S, xb, nullptr, 0, (int)n, target, st);
+    CUtensorMap xmap;
+    cudaError_t e = make_input_map(&xmap, xb, n, S.H0, S.C0);
+    if (e == cudaErrorInvalidValue) return cfail(ctx, SYNIM_ERR_INVALID_ARG, "cnn_grad: x must be 16-byte aligned");
+    if (e == cudaSuccess) e = forward(S, xb, xmap, nullptr, 0, (int)n, target, st);
     if (e == cudaSuccess) e = backward(S, xb, nullptr, 0, (int)n, target, st);
     std::vector<float> l((size_t)n);
     if (e == cudaSuccess) e = cudaMemcpyAsync(l.data(), S.loss, sizeof(float) * n, cudaMemcpyDeviceToHost, st);
@@ -2110,6 +2159,7 @@ synim_status synim_cnn_train(synim_ctx *ctx, const double *params, int64_t n, co
         if (e == cudaSuccess) e = dmalloc(&S.perm, (size_t)n);
         if (e != cudaSuccess) return ccuda(ctx, e, "cnn_train data");
         S.data_cap = n;
+        if ((e = make_input_map(&S.map_data, S.data, n, S.H0, S.C0)) != cudaSuccess) return ccuda(ctx, e, "cnn_train data map");
     }
     // training inputs: one noisy bfloat16 response per sample, generated here
     synim_status ss = synim_probe_generate(ctx, params, n, opts->seed, opts->sample0, opts->noise_rel,
@@ -2140,7 +2190,7 @@ synim_status synim_cnn_train(synim_ctx *ctx, const double *params, int64_t n, co
             const long long b0 = bi * B;
             // this batch's targets in permuted order
             k_gather_targets<<<blocks_for(B, 128), 128, 0, st>>>(S.targets, S.perm, b0, B, S.tgt);
-            if ((e = forward(S, S.data, S.perm, b0, B, S.tgt, st)) != cudaSuccess) break;
+            if ((e = forward(S, S.data, S.map_data, S.perm, b0, B, S.tgt, st)) != cudaSuccess) break;
             if ((e = backward(S, S.data, S.perm, b0, B, S.tgt, st)) != cudaSuccess) break;
             ++S.step;
             const float c1 = 1.f - std::pow(b1, (float)S.step), c2 = 1.f - std::pow(b2, (float)S.step);
