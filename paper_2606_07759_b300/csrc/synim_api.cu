@@ -470,81 +470,64 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
         g_create_error = m;
         return s;
     };
-    cudaError_t e;
-    // ---- DMs: support scan + window packing ----
-    for (int d = 0; d < n_dm; ++d) {
-        const synim_dm_desc &Dd = dms[d];
-        DmHost &H = c->dmh[d];
-        H.n_act = Dd.n_act; H.N = Dd.grid_n; H.dd = Dd.pixel_pitch_m; H.h = Dd.altitude_m;
-        const size_t NN = (size_t)H.N * H.N, cube_n = NN * H.n_act;
-        const float *cube = Dd.ifs;
-        float *staging = nullptr;
-        if (!Dd.ifs_on_device) {
-            if ((e = capped_malloc(c, reinterpret_cast<void **>(&staging), cube_n * sizeof(float))) != cudaSuccess)
-                return bail(cuda_fail(c, e, "cube staging"));
-            if ((e = cudaMemcpy(staging, Dd.ifs, cube_n * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess) {
-                cudaFree(staging);
-                c->mem_used -= cube_n * sizeof(float);
-                return bail(cuda_fail(c, e, "cube upload"));
+    // ---- DMs, part 1: the host cubes start their way to the device ----
+    // Two staging buffers in turn: the copy of cube d + 1 (copy stream) runs
+    // while cube d is scanned and packed (work stream), and both overlap the
+    // host-side sensor tables below.  A buffer is refilled once the packing
+    // that read it has finished.
+    struct Upload {
+        cudaStream_t cs = nullptr, ks = nullptr;
+        cudaEvent_t copied[SYNIM_MAX_DM] = {}, packed[SYNIM_MAX_DM] = {};
+        float *buf[2] = {nullptr, nullptr};
+        size_t bytes = 0;
+        // (a failed create has destroyed the context by the time this runs:
+        // the successful path returns the buffers' bytes to its count itself)
+        ~Upload() {
+            if (cs) cudaStreamSynchronize(cs);
+            if (ks) cudaStreamSynchronize(ks);
+            for (int q = 0; q < 2; ++q)
+                if (buf[q]) cudaFree(buf[q]);
+            for (int d = 0; d < SYNIM_MAX_DM; ++d) {
+                if (copied[d]) cudaEventDestroy(copied[d]);
+                if (packed[d]) cudaEventDestroy(packed[d]);
             }
-            cube = staging;
+            if (cs) cudaStreamDestroy(cs);
+            if (ks) cudaStreamDestroy(ks);
         }
-        auto free_staging = [&]() {
-            if (!staging) return;
-            cudaFree(staging);
-            c->mem_used -= cube_n * sizeof(float);
-            staging = nullptr;
-        };
-        int *d_box = nullptr;
-        std::vector<int> box(4 * (size_t)H.n_act);
-        e = cudaMalloc(&d_box, (box.size() + 1) * sizeof(int));
-        if (e == cudaSuccess) e = launch_support(cube, H.n_act, H.N, Dd.support_eps, d_box, 0);
-        if (e == cudaSuccess) e = cudaMemcpy(box.data(), d_box, box.size() * sizeof(int), cudaMemcpyDeviceToHost);
-        cudaFree(d_box);
-        if (e != cudaSuccess) {
-            free_staging();
-            return bail(cuda_fail(c, e, "support scan"));
+    } up;
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&up.cs, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&up.ks, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail(cuda_fail(c, e, "upload streams"));
+    int n_host = 0;
+    for (int d = 0; d < n_dm; ++d) {
+        if ((e = cudaEventCreateWithFlags(&up.copied[d], cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&up.packed[d], cudaEventDisableTiming)) != cudaSuccess)
+            return bail(cuda_fail(c, e, "upload events"));
+        if (!dms[d].ifs_on_device) {
+            up.bytes = std::max(up.bytes, (size_t)dms[d].grid_n * dms[d].grid_n * dms[d].n_act * sizeof(float));
+            ++n_host;
         }
-        int W = 1;
-        for (int a = 0; a < H.n_act; ++a) {
-            const int *bx = &box[4 * (size_t)a];
-            if (bx[1] < bx[0]) continue;
-            W = std::max(W, std::max(bx[1] - bx[0] + 1, bx[3] - bx[2] + 1));
-        }
-        W = std::min(W, H.N);
-        int Wp = W + 2;
-        if ((Wp & 1) == 0) ++Wp;  // odd pitch: rows of the window fall in distinct banks
-        const int stride = (Wp * Wp + 3) / 4 * 4;
-        H.W = W; H.Wp = Wp;
-        std::vector<int> org(2 * (size_t)H.n_act, 0);
-        for (int a = 0; a < H.n_act; ++a) {
-            const int *bx = &box[4 * (size_t)a];
-            if (bx[1] < bx[0]) continue;
-            org[2 * a] = std::max(0, std::min(bx[0], H.N - W));
-            org[2 * a + 1] = std::max(0, std::min(bx[2], H.N - W));
-        }
-        DevDM &G = c->geo.dm[d];
-        int *d_org = nullptr;
-        float *d_win = nullptr;
-        e = dev_upload(c, &d_org, org);
-        if (e == cudaSuccess) e = dev_alloc(c, &d_win, (size_t)H.n_act * stride);
-        if (e == cudaSuccess) e = launch_pack(cube, H.n_act, H.N, d_org, W, Wp, stride, d_win, 0);
-        if (e == cudaSuccess) e = cudaDeviceSynchronize();
-        free_staging();
-        if (e != cudaSuccess) return bail(cuda_fail(c, e, "window packing"));
-        uint8_t *d_mask = nullptr;
-        if (Dd.mask) {
-            std::vector<uint8_t> m(NN);
-            for (size_t q = 0; q < NN; ++q) m[q] = Dd.mask[q] ? 1 : 0;
-            if ((e = dev_upload(c, &d_mask, m)) != cudaSuccess) return bail(cuda_fail(c, e, "mask upload"));
-        }
-        uint8_t *d_mcls = nullptr;
-        e = dev_alloc(c, &d_mcls, (size_t)(H.N + 1) * (H.N + 1));
-        if (e == cudaSuccess) e = launch_mcls(d_mask, H.N, d_mcls, 0);
-        if (e != cudaSuccess) return bail(cuda_fail(c, e, "mask interior map"));
-        G.win = d_win; G.org = d_org; G.mask = d_mask; G.mcls = d_mcls;
-        G.n_act = H.n_act; G.N = H.N; G.W = W; G.Wp = Wp; G.win_stride = stride;
     }
+    for (int q = 0; q < std::min(n_host, 2); ++q)
+        if ((e = capped_malloc(c, reinterpret_cast<void **>(&up.buf[q]), up.bytes)) != cudaSuccess)
+            return bail(cuda_fail(c, e, "cube staging"));
+    // host cube d goes to staging buffer slot[d] (host cubes alternate between the two)
+    int slot[SYNIM_MAX_DM];
+    for (int d = 0, h = 0; d < n_dm; ++d) slot[d] = dms[d].ifs_on_device ? -1 : (h++ & 1);
+    auto issue_copy = [&](int d) -> cudaError_t {
+        const size_t nb = (size_t)dms[d].grid_n * dms[d].grid_n * dms[d].n_act * sizeof(float);
+        cudaError_t ec = cudaMemcpyAsync(up.buf[slot[d]], dms[d].ifs, nb, cudaMemcpyHostToDevice, up.cs);
+        if (ec == cudaSuccess) ec = cudaEventRecord(up.copied[d], up.cs);
+        return ec;
+    };
+    // the first two host cubes now; each later one after the packing of the cube two before it
+    int next_copy = 0, issued = 0;
+    for (; next_copy < n_dm && issued < 2; ++next_copy)
+        if (slot[next_copy] >= 0) {
+            if ((e = issue_copy(next_copy)) != cudaSuccess) return bail(cuda_fail(c, e, "cube upload"));
+            ++issued;
+        }
     // ---- sensors: tables ----
     for (int w = 0; w < n_wfs; ++w) {
         const synim_wfs_desc &Wd = wfs[w];
@@ -614,6 +597,83 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
         c->max_mm = std::max(c->max_mm, H.M * H.M);
         c->max_lines = std::max(c->max_lines, H.M * (H.n_sub + 1));
     }
+    // ---- DMs, part 2: support scan + window packing ----
+    for (int d = 0; d < n_dm; ++d) {
+        const synim_dm_desc &Dd = dms[d];
+        DmHost &H = c->dmh[d];
+        H.n_act = Dd.n_act; H.N = Dd.grid_n; H.dd = Dd.pixel_pitch_m; H.h = Dd.altitude_m;
+        const size_t NN = (size_t)H.N * H.N;
+        const float *cube = Dd.ifs;
+        if (slot[d] >= 0) {
+            if ((e = cudaStreamWaitEvent(up.ks, up.copied[d], 0)) != cudaSuccess)
+                return bail(cuda_fail(c, e, "cube upload"));
+            cube = up.buf[slot[d]];
+        }
+        int *d_box = nullptr;
+        std::vector<int> box(4 * (size_t)H.n_act);
+        e = cudaMalloc(&d_box, (box.size() + 1) * sizeof(int));
+        if (e == cudaSuccess) e = launch_support(cube, H.n_act, H.N, Dd.support_eps, d_box, up.ks);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(box.data(), d_box, box.size() * sizeof(int), cudaMemcpyDeviceToHost, up.ks);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(up.ks);
+        cudaFree(d_box);
+        if (e != cudaSuccess) return bail(cuda_fail(c, e, "support scan"));
+        int W = 1;
+        for (int a = 0; a < H.n_act; ++a) {
+            const int *bx = &box[4 * (size_t)a];
+            if (bx[1] < bx[0]) continue;
+            W = std::max(W, std::max(bx[1] - bx[0] + 1, bx[3] - bx[2] + 1));
+        }
+        W = std::min(W, H.N);
+        int Wp = W + 2;
+        if ((Wp & 1) == 0) ++Wp;  // odd pitch: rows of the window fall in distinct banks
+        const int stride = (Wp * Wp + 3) / 4 * 4;
+        H.W = W; H.Wp = Wp;
+        std::vector<int> org(2 * (size_t)H.n_act, 0);
+        for (int a = 0; a < H.n_act; ++a) {
+            const int *bx = &box[4 * (size_t)a];
+            if (bx[1] < bx[0]) continue;
+            org[2 * a] = std::max(0, std::min(bx[0], H.N - W));
+            org[2 * a + 1] = std::max(0, std::min(bx[2], H.N - W));
+        }
+        DevDM &G = c->geo.dm[d];
+        int *d_org = nullptr;
+        float *d_win = nullptr;
+        e = dev_upload(c, &d_org, org);
+        if (e == cudaSuccess) e = dev_alloc(c, &d_win, (size_t)H.n_act * stride);
+        if (e == cudaSuccess) e = launch_pack(cube, H.n_act, H.N, d_org, W, Wp, stride, d_win, up.ks);
+        if (e == cudaSuccess) e = cudaEventRecord(up.packed[d], up.ks);
+        if (e != cudaSuccess) return bail(cuda_fail(c, e, "window packing"));
+        // the staging buffer of cube d takes the next host cube once the packing has read it
+        if (slot[d] >= 0) {
+            while (next_copy < n_dm && slot[next_copy] < 0) ++next_copy;
+            if (next_copy < n_dm) {
+                if ((e = cudaStreamWaitEvent(up.cs, up.packed[d], 0)) != cudaSuccess ||
+                    (e = issue_copy(next_copy)) != cudaSuccess)
+                    return bail(cuda_fail(c, e, "cube upload"));
+                ++next_copy;
+            }
+        }
+        uint8_t *d_mask = nullptr;
+        if (Dd.mask) {
+            std::vector<uint8_t> m(NN);
+            for (size_t q = 0; q < NN; ++q) m[q] = Dd.mask[q] ? 1 : 0;
+            if ((e = dev_upload(c, &d_mask, m)) != cudaSuccess) return bail(cuda_fail(c, e, "mask upload"));
+        }
+        uint8_t *d_mcls = nullptr;
+        e = dev_alloc(c, &d_mcls, (size_t)(H.N + 1) * (H.N + 1));
+        if (e == cudaSuccess) e = launch_mcls(d_mask, H.N, d_mcls, up.ks);
+        if (e != cudaSuccess) return bail(cuda_fail(c, e, "mask interior map"));
+        G.win = d_win; G.org = d_org; G.mask = d_mask; G.mcls = d_mcls;
+        G.n_act = H.n_act; G.N = H.N; G.W = W; G.Wp = Wp; G.win_stride = stride;
+    }
+    if ((e = cudaStreamSynchronize(up.ks)) != cudaSuccess) return bail(cuda_fail(c, e, "window packing"));
+    for (int q = 0; q < 2; ++q)
+        if (up.buf[q]) {
+            cudaFree(up.buf[q]);
+            up.buf[q] = nullptr;
+            c->mem_used -= up.bytes;
+        }
     // ---- per-pair state maps, parameter blocks, counters ----
     long long tot = 0, tot_lines = 0;
     for (int d = 0; d < n_dm; ++d)
