@@ -642,6 +642,21 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
         e = dev_upload(c, &d_org, org);
         if (e == cudaSuccess) e = dev_alloc(c, &d_win, (size_t)H.n_act * stride);
         if (e == cudaSuccess) e = launch_pack(cube, H.n_act, H.N, d_org, W, Wp, stride, d_win, up.ks);
+        // the same windows with a KPAD-pixel zero border for the boundary-segment
+        // weight boxes, when a sensor has subapertures small enough for them
+        bool want_k = false;
+        for (int w = 0; w < n_wfs; ++w)
+            want_k |= c->wh[w].k <= KF_MAX_K && (long)c->wh[w].n_sub * (c->wh[w].n_sub + 1) <= KPS;
+        float *d_wink = nullptr;
+        int WpK = 0, strideK = 0;
+        if (want_k && e == cudaSuccess) {
+            WpK = W + 2 * KPAD;
+            if ((WpK & 1) == 0) ++WpK;
+            strideK = (WpK * WpK + 3) / 4 * 4;
+            e = dev_alloc(c, &d_wink, (size_t)H.n_act * strideK);
+            if (e == cudaSuccess)
+                e = launch_pack(cube, H.n_act, H.N, d_org, W, WpK, strideK, d_wink, up.ks, KPAD);
+        }
         if (e == cudaSuccess) e = cudaEventRecord(up.packed[d], up.ks);
         if (e != cudaSuccess) return bail(cuda_fail(c, e, "window packing"));
         // the staging buffer of cube d takes the next host cube once the packing has read it
@@ -666,6 +681,7 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
         if (e != cudaSuccess) return bail(cuda_fail(c, e, "mask interior map"));
         G.win = d_win; G.org = d_org; G.mask = d_mask; G.mcls = d_mcls;
         G.n_act = H.n_act; G.N = H.N; G.W = W; G.Wp = Wp; G.win_stride = stride;
+        G.winK = d_wink; G.WpK = WpK; G.strideK = strideK;
     }
     if ((e = cudaStreamSynchronize(up.ks)) != cudaSuccess) return bail(cuda_fail(c, e, "window packing"));
     for (int q = 0; q < 2; ++q)
@@ -686,6 +702,15 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
     const int np = n_dm * n_wfs;
     e = dev_alloc(c, &c->d_pst, (size_t)tot);
     if (e == cudaSuccess) e = dev_alloc(c, &c->d_lines, (size_t)tot_lines);
+    for (int d = 0; d < n_dm && e == cudaSuccess; ++d)
+        for (int w = 0; w < n_wfs && e == cudaSuccess; ++w) {
+            const WfsHost &H = c->wh[w];
+            if (H.k > KF_MAX_K || (long)H.n_sub * (H.n_sub + 1) > KPS || !c->geo.dm[d].winK) continue;
+            const int p = d * n_wfs + w;
+            e = dev_alloc(c, &c->k_org[p], (size_t)2 * KPS);
+            if (e == cudaSuccess) e = dev_alloc(c, &c->k_w[p], (size_t)2 * KTAPS * KPS);
+            if (e == cudaSuccess) e = dev_alloc(c, &c->k_wb[p], (size_t)2 * KTAPS * KPS);
+        }
     if (e == cudaSuccess) e = dev_alloc(c, &c->d_pairs, (size_t)np);
     if (e == cudaSuccess) e = dev_alloc(c, &c->d_err, 1);
     if (e == cudaSuccess) e = dev_alloc(c, &c->d_gp, (size_t)np * 4);
@@ -838,6 +863,7 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
         return cuda_fail(c, e, "slot wait");
     DevPair *hp = c->h_pairs[slot];
     std::vector<long long> need((size_t)np);
+    int max_seg = 0;   // segments per axis of the largest sensor with weight boxes this call
     for (int d = 0; d < c->n_dm; ++d)
         for (int w = 0; w < c->n_wfs; ++w) {
             const int p = d * c->n_wfs + w;
@@ -860,6 +886,20 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
                 for (int q = 0; q < 4; ++q) P.dim[q] = dim ? dim[4 * p + q] : nullptr;
             }
             if (mode == MODE_VJP) P.gim = gim ? gim[p] : nullptr;
+            // forward IMs of the numerical engine: the boundary-segment weight boxes
+            if (mode == MODE_FWD && !tele && c->k_org[p]) {
+                const int s0 = kseg_shape(P.A, c->wh[w].k, 0), s1 = kseg_shape(P.A, c->wh[w].k, 1);
+                if (s0 >= 0 && s1 >= 0) {
+                    P.kf = 1;
+                    P.kshape[0] = s0;
+                    P.kshape[1] = s1;
+                    for (int ax = 0; ax < 2; ++ax) {
+                        P.korg[ax] = c->k_org[p] + (size_t)ax * KPS;
+                        P.kw[ax] = c->k_w[p] + (size_t)ax * KTAPS * KPS;
+                        P.kwb[ax] = c->k_wb[p] + (size_t)ax * KTAPS * KPS;
+                    }
+                }
+            }
             {
                 // 16-byte column stores need aligned outputs and 2 nv % 4 == 0
                 auto al = [](const void *q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; };
@@ -870,6 +910,12 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
                 P.vec4 = v4 ? 1 : 0;
             }
             need[p] = (seg_need(c->dmh[d], c->wh[w], P.Ai, NV) + 3) / 4 * 4;
+            if (P.kf) {
+                // chunks of four box rows: X, Y, E of four rows and the carried Y row
+                const long long nsj = (need[p] / (2 * NV) - 1) / 4;
+                need[p] = std::max(need[p], (26 * nsj + 8 + 3) / 4 * 4);
+                max_seg = std::max(max_seg, c->wh[w].n_sub * (c->wh[w].n_sub + 1));
+            }
         }
     // Per-warp segment buffer (one warp per column): the largest need over the pairs.
     Geo g = c->geo;
@@ -911,6 +957,16 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
         return cuda_fail(c, e, "kernel attributes");
     if (bps < 1) return fail(c, SYNIM_ERR_SHAPE, "IM kernel does not fit on an SM");
     int grid = grid_for(threads);
+    // forward IMs: k_im for the pairs without weight boxes, k_imk for those with them
+    bool any_plain = mode != MODE_FWD, any_k = false;
+    for (int p = 0; p < np; ++p) {
+        if (mode == MODE_FWD && hp[p].im && !hp[p].kf) any_plain = true;
+        if (mode == MODE_FWD && hp[p].im && hp[p].kf) any_k = true;
+    }
+    auto grids = [&](int th, int &g0, int &g1) {
+        g0 = any_plain ? grid_for(th) : 0;
+        g1 = any_k ? grid_for(th) : 0;
+    };
     if ((e = cudaMemcpyAsync(c->d_pairs, hp, sizeof(DevPair) * np, cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return cuda_fail(c, e, "parameter upload");
     cudaEventRecord(c->slot_ev[slot], s);
@@ -973,19 +1029,22 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
             return cuda_fail(c, e, "autotune events");
         float best = 3e38f;
         int best_th = threads, best_l = 0;
-        if ((e = launch_pst(g, c->d_pairs, c->max_mm, c->max_lines, s)) != cudaSuccess) return cuda_fail(c, e, "autotune");
+        if ((e = launch_pst(g, c->d_pairs, c->max_mm, c->max_lines, s)) != cudaSuccess ||
+            (e = launch_kseg(g, c->d_pairs, max_seg, s)) != cudaSuccess)
+            return cuda_fail(c, e, "autotune");
         for (int th : cand_threads)
             for (int l : cand_lanes) {
                 Geo gt = g;
                 gt.seg_lanes = l;
                 int b2 = 0;
                 if ((e = im_prepare(mode, th, smem, &b2)) != cudaSuccess || b2 < 1) continue;
-                const int gr = grid_for(th);
+                int gr = 0, gk = 0;
+                grids(th, gr, gk);
                 float ms = 0.f;
-                e = launch_im(mode, gt, c->d_pairs, c->d_err, c->d_vjp_part, gr, th, smem, s);
+                e = launch_im(mode, gt, c->d_pairs, c->d_err, c->d_vjp_part, gr, th, smem, s, gk);
                 if (e == cudaSuccess) e = cudaEventRecord(t0, s);
                 for (int r = 0; r < 3 && e == cudaSuccess; ++r)
-                    e = launch_im(mode, gt, c->d_pairs, c->d_err, c->d_vjp_part, gr, th, smem, s);
+                    e = launch_im(mode, gt, c->d_pairs, c->d_err, c->d_vjp_part, gr, th, smem, s, gk);
                 if (e == cudaSuccess) e = cudaEventRecord(t1, s);
                 if (e == cudaSuccess) e = cudaEventSynchronize(t1);
                 if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
@@ -1037,14 +1096,19 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
             return r;
         }
         cudaError_t r = launch_pst(g, c->d_pairs, c->max_mm, c->max_lines, q);
+        if (r == cudaSuccess) r = launch_kseg(g, c->d_pairs, max_seg, q);
         if (r == cudaSuccess && a0) r = cudaEventRecordWithFlags(a0, q, rf);
-        if (r == cudaSuccess) r = launch_im(mode, g, c->d_pairs, c->d_err, c->d_vjp_part, grid, threads, smem, q);
+        int g0 = 0, g1 = 0;
+        grids(threads, g0, g1);
+        if (r == cudaSuccess) r = launch_im(mode, g, c->d_pairs, c->d_err, c->d_vjp_part, g0, threads, smem, q, g1);
         if (r == cudaSuccess && mode == MODE_VJP) r = launch_vjp_reduce(g, c->d_vjp_part, c->d_gp, q);
         if (r == cudaSuccess && b0) r = cudaEventRecordWithFlags(b0, q, rf);
         return r;
     };
     if (c->use_graph) {
-        const auto key = std::make_tuple(mode, smem, grid, threads * 16 + g.seg_lanes);
+        // the weight-box kernel's grid (max_seg) is part of the captured launches
+        const auto key = std::make_tuple(mode * 4 + (any_plain ? 1 : 0) + (any_k ? 2 : 0), smem, grid,
+                                         threads * 16 + g.seg_lanes + max_seg * 65536);
         auto it = c->graphs.find(key);
         if (it == c->graphs.end()) {
             GraphEntry ge;

@@ -34,6 +34,17 @@
 
 namespace synim {
 
+// Boundary-segment weight boxes (the IM kernel's dot-product form of the
+// telescoped segment sums, see k_kseg): windows for them carry a KPAD-pixel
+// zero border so that any box that touches an IF's support lies inside its
+// window; a box spans at most KBA_MAX DM pixels along the segment and
+// KBC_MAX across it; the weight tables are [KTAPS][KPS] planes per axis.
+constexpr int KPAD = 9;
+constexpr int KBA_MAX = 10, KBC_MAX = 4, KTAPS = KBA_MAX * KBC_MAX;
+constexpr int KPS = 8192;    // plane stride (floats): n_sub (n_sub + 1) <= KPS
+constexpr int KF_MAX_K = 12; // largest subaperture side (pixels) given weight tables
+enum { KF_NONE = 1, KF_ASYM = 2, KF_FALLBACK = 4 };   // segment flags (bits 24-31 of the origin word)
+
 struct DevDM {
     const float *win;     // [n_act][win_stride]
     const int *org;       // [n_act][2] window origin (wx0, wy0), DM pixels
@@ -42,6 +53,8 @@ struct DevDM {
                           // 0 all zero, 1 all one, 2 mixed (interior test of the core)
     int n_act, N, W, Wp;
     int win_stride;       // floats per packed window, multiple of 4 (16-byte bulk copies)
+    const float *winK;    // [n_act][strideK] the same windows with a KPAD-pixel zero border, or nullptr
+    int WpK, strideK;
 };
 
 struct DevWFS {
@@ -99,6 +112,17 @@ struct DevPair {
     float *dim[4];       // tangent outputs or nullptr
     const float *gim;    // VJP input [n_act][2 nv] or nullptr
     uint8_t *pst;        // [M][M] strict core (0/1)
+    // Boundary-segment weight boxes, per axis (0: x segments, index si (n_sub + 1) + b;
+    // 1: y segments, index b n_sub + sj), rebuilt every call by k_kseg when kf != 0:
+    // korg = box origin (gx, gy) in DM pixels as signed 12-bit fields (bits 0-11,
+    // 12-23) and the segment flags (bits 24-31); kw / kwb = [KTAPS][KPS] weights of
+    // the A / B sums (kwb only for KF_ASYM segments), tap (along a, across c) at
+    // a KBC_MAX + c; kshape = (ori << 8) | (BA << 4) | BC: box of BA x BC taps,
+    // along the DM's y (ori 0) or x (ori 1) axis.
+    int kf;
+    int kshape[2];
+    int *korg[2];
+    float *kw[2], *kwb[2];
 };
 
 struct Geo {
@@ -144,16 +168,23 @@ const char *noalloc_last_error();  // synim_noalloc.cu
 // box: 4 * n_act + 1 ints (the extra one is scratch for the DM peak)
 cudaError_t launch_support(const float *cube, int n_act, int N, float eps, int *box,
                            cudaStream_t s);
+// pad: zero border of the packed windows (1, or KPAD for the weight-box windows)
 cudaError_t launch_pack(const float *cube, int n_act, int N, const int *org, int W, int Wp,
-                        int stride, float *win, cudaStream_t s);
+                        int stride, float *win, cudaStream_t s, int pad = 1);
 cudaError_t launch_mcls(const uint8_t *mask, int N, uint8_t *mcls, cudaStream_t s);
 cudaError_t launch_pst(const Geo &g, const DevPair *pairs, int max_mm, int max_lines, cudaStream_t s);
+// Boundary-segment weight boxes of the pairs with kf != 0 (after launch_pst).
+cudaError_t launch_kseg(const Geo &g, const DevPair *pairs, int max_seg, cudaStream_t s);
+// Box shape code of one axis for the composite A and subaperture side k, or -1.
+int kseg_shape(const double A[4], int k, int axis);
 size_t im_smem_bytes(const Geo &g);
 cudaError_t im_prepare(int mode, int threads, size_t smem, int *blocks_per_sm);
 // gp: MODE_VJP only, the per-column partials [n_items * n_wfs][4] that
 // launch_vjp_reduce sums per pair into grad_p [n_pairs][4].
+// MODE_FWD: k_im over the pairs without weight boxes (grid CTAs, none if 0),
+// then k_imk over those with them (kgrid CTAs, none if 0).
 cudaError_t launch_im(int mode, const Geo &g, const DevPair *pairs, int *err, double *gp, int grid, int threads,
-                      size_t smem, cudaStream_t s);
+                      size_t smem, cudaStream_t s, int kgrid = 0);
 cudaError_t launch_vjp_reduce(const Geo &g, const double *part, double *gp, cudaStream_t s);
 // The telescoping-sum IM kernel: one warp per (actuator, sensor) column, a
 // per-warp buffer of cap4 float4 subaperture sums (a chunk of box rows and
@@ -224,6 +255,11 @@ struct synim_ctx {
     long long pst_off[SYNIM_MAX_PAIRS] = {};
     long long line_off[SYNIM_MAX_PAIRS] = {};
     uint8_t *d_pst = nullptr, *d_lines = nullptr;
+    // boundary-segment weight boxes per pair (nullptr where the sensor's
+    // subapertures are too large for them): origins [2][KPS], weights
+    // [2][KTAPS][KPS] for A and for B
+    int *k_org[SYNIM_MAX_PAIRS] = {};
+    float *k_w[SYNIM_MAX_PAIRS] = {}, *k_wb[SYNIM_MAX_PAIRS] = {};
     int max_mm = 0, max_lines = 0;
     int threads = 256, ctas_per_sm = 0;
     bool autotune = false;

@@ -101,9 +101,10 @@ __global__ void k_support(const float *__restrict__ cube, int N, float eps, cons
     }
 }
 
-// win[a][r][c] = IF_a(wy0 + r - 1, wx0 + c - 1) for 1 <= r, c <= W, zero elsewhere.
+// win[a][r][c] = IF_a(wy0 + r - pad, wx0 + c - pad) for pad <= r, c < pad + W,
+// zero elsewhere (a zero border of pad pixels).
 __global__ void k_pack(const float *__restrict__ cube, int N, const int *__restrict__ org, int W,
-                       int Wp, int stride, float *__restrict__ win) {
+                       int Wp, int stride, float *__restrict__ win, int pad) {
     const int a = blockIdx.x;
     const int wx0 = org[2 * a], wy0 = org[2 * a + 1];
     const float *img = cube + (size_t)a * N * N;
@@ -111,8 +112,8 @@ __global__ void k_pack(const float *__restrict__ cube, int N, const int *__restr
     for (int idx = threadIdx.x; idx < stride; idx += blockDim.x) {
         float v = 0.f;
         const int r = idx / Wp, c = idx - r * Wp;
-        if (idx < Wp * Wp && r >= 1 && r <= W && c >= 1 && c <= W) {
-            const int x = wx0 + c - 1, y = wy0 + r - 1;
+        if (idx < Wp * Wp && r >= pad && r < pad + W && c >= pad && c < pad + W) {
+            const int x = wx0 + c - pad, y = wy0 + r - pad;
             if (x >= 0 && x < N && y >= 0 && y < N) v = img[(size_t)y * N + x];
         }
         dst[idx] = v;
@@ -131,8 +132,8 @@ cudaError_t launch_support(const float *cube, int n_act, int N, float eps, int *
 }
 
 cudaError_t launch_pack(const float *cube, int n_act, int N, const int *org, int W, int Wp,
-                        int stride, float *win, cudaStream_t s) {
-    k_pack<<<n_act, 256, 0, s>>>(cube, N, org, W, Wp, stride, win);
+                        int stride, float *win, cudaStream_t s, int pad) {
+    k_pack<<<n_act, 256, 0, s>>>(cube, N, org, W, Wp, stride, win, pad);
     return cudaGetLastError();
 }
 
@@ -274,6 +275,146 @@ cudaError_t launch_pst(const Geo &g, const DevPair *pairs, int max_mm, int max_l
 }
 
 // ---------------------------------------------------------------------------
+// Every call: boundary-segment weight boxes
+// ---------------------------------------------------------------------------
+// A boundary segment is the two pixel lines at a subaperture boundary (pixels
+// b k - 1 and b k) over one subaperture row (x) or column (y).  Its
+// telescoped sums (Sec. 2.2) A (credited to the subaperture before the
+// boundary) and B (after) add the bilinear resamples (Sec. 2.1) of its core
+// pixels, selected by the sensor's pupil bits.  A window origin is a whole DM
+// pixel, so the fractional sample positions, the pixel classes (Sec. 2.3)
+// and the bits belong to the (DM, sensor) pair, not to the actuator: A and B
+// are dot products of one box of DM-pixel weights with any actuator's packed
+// window.  k_kseg builds those boxes once per call; the IM kernel then reads
+// BA x BC taps per segment instead of resampling 2 k pixels.  Segments with a
+// ring pixel (its repair reaches beyond the box) or whose samples do not fit
+// the pair's box are flagged KF_FALLBACK and keep the per-sample path.
+
+// Shape code (ori << 8) | (BA << 4) | BC of one axis, or -1.  The samples of a
+// segment are 2 pixels across by k along (x segments: along the sensor rows);
+// their DM extents bound the taps per axis by floor(extent) + 3.  The box
+// takes floor(extent + 0.9) + 2 (segments that need the last tap fall back)
+// rounded up to a supported size.
+int kseg_shape(const double A[4], int k, int axis) {
+    const double jx = std::fabs(A[0]), ix = std::fabs(A[1]), jy = std::fabs(A[2]), iy = std::fabs(A[3]);
+    const double dx = axis == 0 ? jx + (k - 1) * ix : ix + (k - 1) * jx;
+    const double dy = axis == 0 ? jy + (k - 1) * iy : iy + (k - 1) * jy;
+    const int ori = dy >= dx ? 0 : 1;                 // along the larger DM extent
+    const double dl = ori ? dx : dy, dc = ori ? dy : dx;
+    int BA = (int)std::floor(dl + 0.9) + 2, BC = (int)std::floor(dc + 0.9) + 2;
+    if (BA <= 4) BA = 4;
+    else if (BA <= 6) BA = 6;
+    else if (BA <= 8) BA = 8;
+    else if (BA > KBA_MAX) return -1;
+    if (BC <= 3) BC = 3;
+    else if (BC > KBC_MAX) return -1;
+    return (ori << 8) | (BA << 4) | BC;
+}
+
+__global__ void __launch_bounds__(128) k_kseg(const __grid_constant__ Geo g, const DevPair *__restrict__ pairs) {
+    __shared__ float acc[128][2 * KTAPS + 1];
+    const int p = blockIdx.y;
+    const DevPair &P = pairs[p];
+    if (!P.kf) return;
+    const DevWFS &WF = g.wfs[p % g.n_wfs];
+    const int n = WF.n_sub, n1 = n + 1, k = WF.k;
+    const int nseg = n * n1;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 2 * nseg) return;
+    const int ax = idx >= nseg ? 1 : 0, sid = idx - ax * nseg;
+    int row, b;   // x: subaperture row, boundary (sid = row n1 + b); y: boundary, subaperture column (sid = b n + row)
+    if (ax == 0) { row = sid / n1; b = sid - row * n1; }
+    else { b = sid / n; row = sid - b * n; }
+    const uint8_t *cc = (ax ? P.ycc : P.xcc) + b;    // byte of line pixel pair u at cc[u n1]
+    const int shape = P.kshape[ax];
+    const int ori = shape >> 8, BA = (shape >> 4) & 15, BC = shape & 15;
+    const int ex = ori ? BA : BC, ey = ori ? BC : BA;  // box extents along DM x and y
+    const int u0 = row * k, l0 = b * k - 1;
+    // sample (q, t) = line pixel t of pair u0 + q: sensor pixel (i, j)
+    auto pix = [&](int q, int t, int &i, int &j) {
+        if (ax == 0) { i = u0 + q; j = l0 + t; }
+        else { i = l0 + t; j = u0 + q; }
+    };
+    int i, j;
+    pix(0, 0, i, j);
+    const float xf = fmaf(P.Ahi[0], (float)j, fmaf(P.Ahi[1], (float)i, P.bhi[0]));
+    const float yf = fmaf(P.Ahi[2], (float)j, fmaf(P.Ahi[3], (float)i, P.bhi[1]));
+    int flags = 0;
+    bool any = false, asym = false;
+    int ox = 0, oy = 0, cx0 = INT_MAX, cx1 = INT_MIN, cy0 = INT_MAX, cy1 = INT_MIN;
+    if (!(fabsf(xf) < 1e5f && fabsf(yf) < 1e5f)) {
+        flags = KF_FALLBACK;
+    } else {
+        ox = (int)floorf(xf) - 1;
+        oy = (int)floorf(yf) - 1;
+        for (int q = 0; q < k; ++q) {
+            const int c = cc[(long)(u0 + q) * n1];
+            for (int t = 0; t < 2; ++t) {
+                const int cl = (c >> (4 + 2 * t)) & 3;
+                const int ba = c & (t ? 4 : 1), bb = c & (t ? 8 : 2);
+                if (!(ba || bb) || cl == 0) continue;
+                if (cl == 2) { flags |= KF_FALLBACK; continue; }
+                pix(q, t, i, j);
+                const float xl = exact_affine(P.Ahi[0], P.Alo[0], P.Ahi[1], P.Alo[1], P.bhi[0], P.blo[0], j, i, ox);
+                const float yl = exact_affine(P.Ahi[2], P.Alo[2], P.Ahi[3], P.Alo[3], P.bhi[1], P.blo[1], j, i, oy);
+                const int cx = (int)floorf(xl), cy = (int)floorf(yl);
+                cx0 = min(cx0, cx); cx1 = max(cx1, cx); cy0 = min(cy0, cy); cy1 = max(cy1, cy);
+                any = true;
+                if ((ba != 0) != (bb != 0)) asym = true;
+            }
+        }
+    }
+    int gx = 0, gy = 0;
+    if (!(flags & KF_FALLBACK) && any) {
+        gx = ox + cx0;
+        gy = oy + cy0;
+        if (cx1 - cx0 + 2 > ex || cy1 - cy0 + 2 > ey || gx < -2048 || gx > 2047 || gy < -2048 || gy > 2047)
+            flags |= KF_FALLBACK;
+    }
+    if (!any && !(flags & KF_FALLBACK)) flags |= KF_NONE;
+    if (!(flags & (KF_FALLBACK | KF_NONE))) {
+        if (asym) flags |= KF_ASYM;
+        float *wa = acc[threadIdx.x], *wb = wa + KTAPS;
+        for (int q = 0; q < 2 * KTAPS; ++q) wa[q] = 0.f;
+        for (int q = 0; q < k; ++q) {
+            const int c = cc[(long)(u0 + q) * n1];
+            for (int t = 0; t < 2; ++t) {
+                const int cl = (c >> (4 + 2 * t)) & 3;
+                const int ba = c & (t ? 4 : 1), bb = c & (t ? 8 : 2);
+                if (!(ba || bb) || cl != 1) continue;
+                pix(q, t, i, j);
+                // the same local coordinates as the first pass, so the cells agree with its extents
+                const float xl = exact_affine(P.Ahi[0], P.Alo[0], P.Ahi[1], P.Alo[1], P.bhi[0], P.blo[0], j, i, ox);
+                const float yl = exact_affine(P.Ahi[2], P.Alo[2], P.Ahi[3], P.Alo[3], P.bhi[1], P.blo[1], j, i, oy);
+                const float fx0 = floorf(xl), fy0 = floorf(yl);
+                const int cx = (int)fx0 - cx0, cy = (int)fy0 - cy0;
+                const float fx = xl - fx0, fy = yl - fy0, hx = 1.f - fx, hy = 1.f - fy;
+                const float wq[4] = {hx * hy, fx * hy, hx * fy, fx * fy};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int tx = cx + (e & 1), ty = cy + (e >> 1);
+                    const int tap = ori ? tx * KBC_MAX + ty : ty * KBC_MAX + tx;
+                    if (ba) wa[tap] += wq[e];
+                    if (bb) wb[tap] += wq[e];
+                }
+            }
+        }
+        float *ka = P.kw[ax] + sid, *kb = P.kwb[ax] + sid;
+        for (int q = 0; q < KTAPS; ++q) ka[(long)q * KPS] = wa[q];
+        if (asym)
+            for (int q = 0; q < KTAPS; ++q) kb[(long)q * KPS] = wb[q];
+    }
+    P.korg[ax][sid] = (gx & 0xfff) | ((gy & 0xfff) << 12) | (flags << 24);
+}
+
+cudaError_t launch_kseg(const Geo &g, const DevPair *pairs, int max_seg, cudaStream_t s) {
+    if (max_seg <= 0) return cudaSuccess;
+    dim3 grid((2 * max_seg + 127) / 128, g.n_dm * g.n_wfs);
+    k_kseg<<<grid, 128, 0, s>>>(g, pairs);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // The IM kernel
 // ---------------------------------------------------------------------------
 // Per (actuator, sensor): the pixel box where the resampled, repaired IF can
@@ -296,16 +437,17 @@ struct Eval {
     const float *win;
     const uint8_t *pst;
     int Wp, M, pi0, pj0;
-    float Wf1, xo, yo, a00, a01, a10, a11;
+    float xlo, xhi, xo, yo, a00, a01, a10, a11;   // window data at padded coordinates (xlo, xhi)
     float dxo[NT], dyo[NT], da[4 * NT];
 #ifdef SYNIM_DEBUG_BOUNDS
     int *err;   // the context's error flag
     long wn;    // floats of this actuator's packed window
 #endif
 
-    __device__ __forceinline__ void load(const ItemWfs &s, const float *w, int wp, int W, int m) {
+    // w: the actuator's packed window, pitch wp, data W x W after a zero border of pad pixels
+    __device__ __forceinline__ void load(const ItemWfs &s, const float *w, int wp, int W, int m, int pad = 1) {
         win = w; pst = s.pst; Wp = wp; M = m; pi0 = s.pi0; pj0 = s.pj0;
-        Wf1 = (float)(W + 1); xo = s.xo; yo = s.yo;
+        xlo = (float)(pad - 1); xhi = (float)(W + pad); xo = s.xo; yo = s.yo;
         a00 = s.a00; a01 = s.a01; a10 = s.a10; a11 = s.a11;
         if (NV == 5) {
 #pragma unroll
@@ -321,7 +463,7 @@ struct Eval {
         const float di = (float)(i - pi0), dj = (float)(j - pj0);
         const float x = fmaf(a00, dj, fmaf(a01, di, xo));
         const float y = fmaf(a10, dj, fmaf(a11, di, yo));
-        if (!(x > 0.f && x < Wf1 && y > 0.f && y < Wf1)) {
+        if (!(x > xlo && x < xhi && y > xlo && y < xhi)) {
 #pragma unroll
             for (int t = 0; t < NV; ++t) v[t] = 0.f;
             return;
@@ -352,7 +494,7 @@ struct Eval {
 
     // Bilinear value at padded-window coordinates (x, y) (no tangents).
     __device__ __forceinline__ float bil_at(float x, float y) const {
-        if (!(x > 0.f && x < Wf1 && y > 0.f && y < Wf1)) return 0.f;
+        if (!(x > xlo && x < xhi && y > xlo && y < xhi)) return 0.f;
         const float fx0 = floorf(x), fy0 = floorf(y);
         const float fx = x - fx0, fy = y - fy0;
         if (!SYNIM_IDX_OK(fx0 >= 0.f && fy0 >= 0.f && (long)fy0 * Wp + (long)fx0 + Wp + 1 < wn, err)) return 0.f;
@@ -423,9 +565,11 @@ __device__ __forceinline__ bool pair_active(const DevPair &P) {
 }
 
 // Pixel and subaperture boxes of actuator a on sensor w, local coordinates.
+// pad: zero border of the window the column reads (the local coordinates xo,
+// yo are relative to DM pixel (wx0 - pad, wy0 - pad)).
 template <int MODE, int NV>
 __device__ void make_info(const Geo &g, const DevPair *__restrict__ pairs, int d, int a, int w,
-                          ItemWfs &s, int *err) {
+                          ItemWfs &s, int *err, int pad = 1) {
     const DevPair &P = pairs[d * g.n_wfs + w];
     const DevWFS &WF = g.wfs[w];
     const DevDM &D = g.dm[d];
@@ -469,8 +613,8 @@ __device__ void make_info(const Geo &g, const DevPair *__restrict__ pairs, int d
     s.si0 = si0; s.si1 = si1; s.sj0 = sj0; s.sj1 = sj1;
     s.nsj = nsj;
     s.nsub = nsub;
-    s.xo = exact_affine(P.Ahi[0], P.Alo[0], P.Ahi[1], P.Alo[1], P.bhi[0], P.blo[0], pj0, pi0, wx0 - 1);
-    s.yo = exact_affine(P.Ahi[2], P.Alo[2], P.Ahi[3], P.Alo[3], P.bhi[1], P.blo[1], pj0, pi0, wy0 - 1);
+    s.xo = exact_affine(P.Ahi[0], P.Alo[0], P.Ahi[1], P.Alo[1], P.bhi[0], P.blo[0], pj0, pi0, wx0 - pad);
+    s.yo = exact_affine(P.Ahi[2], P.Alo[2], P.Ahi[3], P.Alo[3], P.bhi[1], P.blo[1], pj0, pi0, wy0 - pad);
     s.a00 = P.Ahi[0]; s.a01 = P.Ahi[1]; s.a10 = P.Ahi[2]; s.a11 = P.Ahi[3];
     if (NV == 5) {
         for (int q = 0; q < 4; ++q) {
@@ -697,6 +841,245 @@ __device__ __forceinline__ void warp_segments(const DevWFS &WF, const ItemWfs &s
     }
 }
 
+// ---------------------------------------------------------------------------
+// IM columns from the boundary-segment weight boxes (forward IMs)
+// ---------------------------------------------------------------------------
+// A = sum over the box of kw[tap] * window, B likewise with kwb (TWO) or A.
+// wb: the window at the box origin; ka / kb: tap 0 of the segment's planes.
+template <int BA, int BC, int ORI, bool TWO>
+__device__ __forceinline__ void kf_dot(const float *__restrict__ wb, int Wp, const float *__restrict__ ka,
+                                       const float *__restrict__ kb, float &A, float &B) {
+    float sa = 0.f, sb = 0.f;
+    if constexpr (ORI == 0) {   // along the window's rows (stride Wp), across its columns
+#pragma unroll
+        for (int a = 0; a < BA; ++a) {
+            const float *wr = wb + a * Wp;
+#pragma unroll
+            for (int c = 0; c < BC; ++c) {
+                const float v = __ldg(wr + c);
+                sa = fmaf(__ldg(ka + (a * KBC_MAX + c) * KPS), v, sa);
+                if (TWO) sb = fmaf(__ldg(kb + (a * KBC_MAX + c) * KPS), v, sb);
+            }
+        }
+    } else {                    // along the window's columns, across its rows
+#pragma unroll
+        for (int c = 0; c < BC; ++c) {
+            const float *wr = wb + c * Wp;
+#pragma unroll
+            for (int a = 0; a < BA; ++a) {
+                const float v = __ldg(wr + a);
+                sa = fmaf(__ldg(ka + (a * KBC_MAX + c) * KPS), v, sa);
+                if (TWO) sb = fmaf(__ldg(kb + (a * KBC_MAX + c) * KPS), v, sb);
+            }
+        }
+    }
+    A = sa;
+    B = TWO ? sb : sa;
+}
+
+template <int ORI, bool TWO>
+__device__ __forceinline__ void kf_dot_ba(int BA, int BC, const float *wb, int Wp, const float *ka,
+                                          const float *kb, float &A, float &B) {
+#define SYNIM_KF(ba, bc) \
+    if (BA == ba && BC == bc) { kf_dot<ba, bc, ORI, TWO>(wb, Wp, ka, kb, A, B); return; }
+    SYNIM_KF(9, 3) SYNIM_KF(8, 3) SYNIM_KF(10, 3) SYNIM_KF(6, 3) SYNIM_KF(4, 3)
+    SYNIM_KF(9, 4) SYNIM_KF(8, 4) SYNIM_KF(10, 4) SYNIM_KF(6, 4) SYNIM_KF(4, 4)
+#undef SYNIM_KF
+    A = B = 0.f;
+}
+
+// One pass over cnt segments of axis ax: t = r ncol + c is x segment
+// (row0 + r, boundary col0 + c) or y segment (boundary row0 + r, column col0
+// + c); out[2 t], out[2 t + 1] = A, B.  Lanes take one segment each; flagged
+// segments are resampled pixel by pixel afterwards by the whole warp.
+__device__ void kf_pass(const DevWFS &WF, const DevPair &P, const ItemWfs &s, const Eval<1> &ev,
+                        const float *__restrict__ win, int Wp, int W, int wx0, int wy0, int ax, int row0,
+                        int ncol, int col0, int cnt, float *out, int lane, int *err) {
+    const int n = WF.n_sub, n1 = n + 1;
+    const int shape = P.kshape[ax];
+    const int ori = shape >> 8, BA = (shape >> 4) & 15, BC = shape & 15;
+    const int ex = ori ? BA : BC, ey = ori ? BC : BA;
+    const int *__restrict__ org = P.korg[ax];
+    const float *kwa = P.kw[ax], *kwb = P.kwb[ax];
+    const int lx0 = wx0 - KPAD, ly0 = wy0 - KPAD;
+    (void)err;
+    for (int base = 0; base < cnt; base += 32) {
+        const int t = base + lane;
+        int sid = 0, fl = 0;
+        bool act = false, fb = false;
+        const float *wb = win;
+        if (t < cnt) {
+            const int r = t / ncol, c = t - r * ncol;
+            sid = ax ? (row0 + r) * n + (col0 + c) : (row0 + r) * n1 + (col0 + c);
+            const int word = __ldg(org + sid);
+            fl = (int)((unsigned)word >> 24);
+            const int gx = (word << 20) >> 20, gy = (word << 8) >> 20;
+            const int lx = gx - lx0, ly = gy - ly0;
+            // the box touches the window's data (padded coordinates [KPAD, KPAD + W))
+            const bool hit = lx + ex > KPAD && lx < KPAD + W && ly + ey > KPAD && ly < KPAD + W;
+            if (fl & KF_FALLBACK) {
+                fb = true;
+            } else if (!(fl & KF_NONE) && hit &&
+                       SYNIM_IDX_OK(lx >= 0 && ly >= 0 && (long)(ly + ey - 1) * Wp + lx + ex - 1 < ev.wn, err)) {
+                act = true;
+                wb = win + ly * Wp + lx;
+            }
+        }
+        const bool two = __any_sync(0xffffffffu, act && (fl & KF_ASYM));
+        float A = 0.f, B = 0.f;
+        if (act) {
+            if (ori == 0) {
+                if (two) kf_dot_ba<0, true>(BA, BC, wb, Wp, kwa + sid, kwb + sid, A, B);
+                else kf_dot_ba<0, false>(BA, BC, wb, Wp, kwa + sid, kwb + sid, A, B);
+            } else {
+                if (two) kf_dot_ba<1, true>(BA, BC, wb, Wp, kwa + sid, kwb + sid, A, B);
+                else kf_dot_ba<1, false>(BA, BC, wb, Wp, kwa + sid, kwb + sid, A, B);
+            }
+            if (!(fl & KF_ASYM)) B = A;   // kwb holds only the asymmetric segments' weights
+        }
+        if (t < cnt && !fb) {
+            out[2 * t] = A;
+            out[2 * t + 1] = B;
+        }
+        unsigned m = __ballot_sync(0xffffffffu, fb);
+        while (m) {
+            const int tt = base + __ffs(m) - 1;
+            m &= m - 1;
+            const int r = tt / ncol, c = tt - r * ncol;
+            const SegRows sr = ax ? seg_rows(WF, s, 1, row0 + r, col0 + c) : seg_rows(WF, s, 0, col0 + c, row0 + r);
+            float fa[1] = {0.f}, fbv[1] = {0.f};
+            seg_compute<1>(WF, sr, ev, ax, lane, 32, fa, fbv);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                fa[0] += __shfl_xor_sync(0xffffffffu, fa[0], o);
+                fbv[0] += __shfl_xor_sync(0xffffffffu, fbv[0], o);
+            }
+            if (lane == 0) {
+                out[2 * tt] = fa[0];
+                out[2 * tt + 1] = fbv[0];
+            }
+        }
+    }
+}
+
+// One forward IM column from the weight boxes.  The same column as
+// warp_column: zeros outside the rows of the subaperture box; then, in
+// chunks of R box rows, every x segment of the chunk's rows and every y
+// segment of the boundaries below them (the boundary above carried), the
+// pupil-edge sums of the chunk's box subapertures, and one in-order pass over
+// the chunk's valid rows (slopes in the box, zeros elsewhere).  Buffer
+// (floats): X [R][nsj + 1][2], Y [R + 1][nsj][2], E [R][nsj][2].
+__device__ __forceinline__ void warp_column_kf(const Geo &g, const DevPair *__restrict__ pairs, int d, int a,
+                                               int w, float *wbuf, int cap, int lane, int *err) {
+    const DevPair &P = pairs[d * g.n_wfs + w];
+    const DevWFS &WF = g.wfs[w];
+    const DevDM &D = g.dm[d];
+    __shared__ ItemWfs s_item[8];
+    ItemWfs &s = s_item[threadIdx.x >> 5];
+    __syncwarp();
+    make_info<MODE_FWD, 1>(g, pairs, d, a, w, s, err, KPAD);
+    __syncwarp();
+    const int nv = WF.nv, n2 = 2 * nv;
+    const int nsj = s.empty ? 0 : s.nsj;
+    // at least one box row: X, two Y rows and E
+    if (!s.empty && 2 * (4 * nsj + 1) > cap) {
+        if (lane == 0) atomicOr(err, ERR_ARENA);
+        s.empty = 1;
+    }
+    if (!s.empty && !SYNIM_IDX_OK(s.si0 >= 0 && s.si1 < WF.n_sub && s.sj0 >= 0 && s.sj1 < WF.n_sub, err)) return;
+    const int vr0 = s.empty ? 0 : WF.vrow[s.si0], vr1 = s.empty ? 0 : WF.vrow[s.si1 + 1];
+    if (!SYNIM_IDX_OK(0 <= vr0 && vr0 <= vr1 && vr1 <= nv, err)) return;
+    float *col = P.im + (size_t)a * n2;
+    if (P.vec4) {
+        bulk_zero(col, 0, vr0, lane);
+        bulk_zero(col, vr1, nv + vr0, lane);
+        bulk_zero(col, nv + vr1, n2, lane);
+    } else {
+        zero_rows(col, 0, vr0, false, lane);
+        zero_rows(col, vr1, nv + vr0, false, lane);
+        zero_rows(col, nv + vr1, n2, false, lane);
+    }
+    if (s.empty) return;
+    const float *win = D.winK + (size_t)a * D.strideK;
+    const int wx0 = D.org[2 * a], wy0 = D.org[2 * a + 1];
+    Eval<1> ev;
+    ev.load(s, win, D.WpK, D.W, WF.M, KPAD);
+#ifdef SYNIM_DEBUG_BOUNDS
+    ev.err = err;
+    ev.wn = D.strideK;
+#endif
+    const int nrows = s.si1 - s.si0 + 1;
+    // chunk rows: X, Y and E of R rows plus the carried Y row
+    const int R = max(1, min(nrows, (cap / 2 - nsj) / (3 * nsj + 1)));
+    float *X = wbuf;
+    float *Y = X + (size_t)R * (nsj + 1) * 2;
+    float *E = Y + (size_t)(R + 1) * nsj * 2;
+    // the boundary above the box
+    kf_pass(WF, P, s, ev, win, D.WpK, D.W, wx0, wy0, 1, s.si0, nsj, s.sj0, nsj, Y, lane, err);
+    for (int r0 = s.si0; r0 <= s.si1; r0 += R) {
+        const int Rc = min(R, s.si1 - r0 + 1), nb = Rc * nsj;
+        kf_pass(WF, P, s, ev, win, D.WpK, D.W, wx0, wy0, 0, r0, nsj + 1, s.sj0, Rc * (nsj + 1), X, lane, err);
+        kf_pass(WF, P, s, ev, win, D.WpK, D.W, wx0, wy0, 1, r0 + 1, nsj, s.sj0, nb, Y + 2 * nsj, lane, err);
+        // pupil-edge sums of the chunk's box subapertures (the whole warp on
+        // each that has edge pixels, both axes from one resample per pixel)
+        for (int t0 = 0; t0 < nb; t0 += 32) {
+            const int t = t0 + lane;
+            bool has = false;
+            if (t < nb) {
+                const int q = t / nsj, c = t - q * nsj;
+                const int qq = (r0 + q) * WF.n_sub + s.sj0 + c;
+                has = WF.irr_sub[qq + 1] > WF.irr_sub[qq];
+                if (!has) {
+                    E[2 * t] = 0.f;
+                    E[2 * t + 1] = 0.f;
+                }
+            }
+            unsigned m = __ballot_sync(0xffffffffu, has);
+            while (m) {
+                const int tt = t0 + __ffs(m) - 1;
+                m &= m - 1;
+                const int q = tt / nsj, c = tt - q * nsj;
+                float ax_[1] = {0.f}, ay_[1] = {0.f};
+                edge_sum<1>(WF, s, ev, r0 + q, s.sj0 + c, lane, 32, ax_, ay_);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    ax_[0] += __shfl_xor_sync(0xffffffffu, ax_[0], o);
+                    ay_[0] += __shfl_xor_sync(0xffffffffu, ay_[0], o);
+                }
+                if (lane == 0) {
+                    E[2 * tt] = ax_[0];
+                    E[2 * tt + 1] = ay_[0];
+                }
+            }
+        }
+        __syncwarp();
+        // every valid row of the chunk's subaperture rows, in order: the
+        // slope of a box subaperture (segment differences plus pupil-edge
+        // sums, times slope_scale / (2 dw lit)), zero for the others
+        const int ra = WF.vrow[r0], rb = WF.vrow[r0 + Rc];
+        if (!SYNIM_IDX_OK(0 <= ra && ra <= rb && rb <= nv, err)) return;
+        for (int r = ra + lane; r < rb; r += 32) {
+            const int vs = __ldg(WF.vsub + r);
+            const int q = (vs >> 16) - r0, c = (vs & 0xffff) - s.sj0;
+            float vx = 0.f, vy = 0.f;
+            if (c >= 0 && c < nsj) {
+                const float f = __ldg(WF.fac + r);
+                const float *segx = X + (size_t)q * (nsj + 1) * 2;
+                const float *sy0 = Y + (size_t)q * nsj * 2, *sy1 = sy0 + 2 * nsj;
+                const float *eq = E + (size_t)q * nsj * 2;
+                vx = (segx[2 * (c + 1)] - segx[2 * c + 1] + eq[2 * c]) * f;
+                vy = (sy1[2 * c] - sy0[2 * c + 1] + eq[2 * c + 1]) * f;
+            }
+            col[r] = vx;
+            col[nv + r] = vy;
+        }
+        __syncwarp();
+        // carry the last boundary row of the chunk
+        for (int c = lane; c < 2 * nsj; c += 32) Y[c] = Y[(size_t)Rc * nsj * 2 + c];
+        __syncwarp();
+    }
+}
+
 // One IM column (actuator a of DM d on sensor w) by one warp: zeros outside
 // the rows of the subaperture box, and, box row by box row, the boundary
 // segments, the slopes (segment differences plus pupil-edge pixels, times
@@ -707,6 +1090,7 @@ __device__ __forceinline__ void warp_column(const Geo &g, const DevPair *__restr
     const int pidx = d * g.n_wfs + w;
     const DevPair &P = pairs[pidx];
     if (!pair_active<MODE>(P)) return;
+    if (MODE == MODE_FWD && P.kf) return;   // k_imk's column
     const DevWFS &WF = g.wfs[w];
     const DevDM &D = g.dm[d];
     // The column's pixel and subaperture boxes live in shared memory, one
@@ -1064,6 +1448,28 @@ k_tele(const __grid_constant__ Geo g, const __grid_constant__ TeleSet t, const D
     if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 
+// Forward IM columns of the pairs with boundary-segment weight boxes (kf),
+// one warp per column as in k_im; k_im skips these pairs.
+__global__ void __launch_bounds__(256, 3)
+k_imk(const __grid_constant__ Geo g, const DevPair *__restrict__ pairs, int *__restrict__ err) {
+    extern __shared__ __align__(16) float smem_f[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    float *wbuf = smem_f + (size_t)warp * g.seg_floats;
+    for (int q = threadIdx.x; q < kZeroFloats / 4; q += blockDim.x) s_zero[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic zeros -> bulk-copy reads
+    __syncthreads();
+    const long n_units = (long)g.n_items * g.n_wfs;
+    for (long u = (long)blockIdx.x * nw + warp; u < n_units; u += (long)gridDim.x * nw) {
+        const int item = (int)(u / g.n_wfs), w = (int)(u - (long)item * g.n_wfs);
+        int d, a;
+        decode_item(g, item, d, a);
+        const DevPair &P = pairs[d * g.n_wfs + w];
+        if (!P.kf || !P.im) continue;
+        warp_column_kf(g, pairs, d, a, w, wbuf, g.seg_floats, lane, err);
+    }
+    if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
 size_t tele_smem_bytes(int threads, int cap4) { return (size_t)(threads / 32) * cap4 * sizeof(float4); }
 
 cudaError_t launch_tele(const Geo &g, const TeleSet &t, const DevPair *pairs, int cap4, int *err, int grid,
@@ -1084,6 +1490,9 @@ static cudaError_t prepare_one(int threads, size_t smem, int *bps) {
     cudaError_t e = cudaFuncSetAttribute(k_im<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
+    if (MODE == MODE_FWD &&
+        (e = cudaFuncSetAttribute(k_imk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+        return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_im<MODE>, threads, smem);
 }
 
@@ -1132,9 +1541,12 @@ cudaError_t launch_vjp_reduce(const Geo &g, const double *part, double *gp, cuda
 }
 
 cudaError_t launch_im(int mode, const Geo &g, const DevPair *pairs, int *err, double *gp, int grid, int threads,
-                      size_t smem, cudaStream_t s) {
+                      size_t smem, cudaStream_t s, int kgrid) {
     switch (mode) {
-        case MODE_FWD: k_im<MODE_FWD><<<grid, threads, smem, s>>>(g, pairs, err, gp); break;
+        case MODE_FWD:
+            if (grid > 0) k_im<MODE_FWD><<<grid, threads, smem, s>>>(g, pairs, err, gp);
+            if (kgrid > 0) k_imk<<<kgrid, threads, smem, s>>>(g, pairs, err);
+            break;
         case MODE_TAN: k_im<MODE_TAN><<<grid, threads, smem, s>>>(g, pairs, err, gp); break;
         default: k_im<MODE_VJP><<<grid, threads, smem, s>>>(g, pairs, err, gp); break;
     }

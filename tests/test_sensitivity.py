@@ -82,9 +82,15 @@ def check_tangents(wl, cols_per_dm=None, seed=0):
             p = d * len(wl.wfss) + w
             mis = wl.misregs[p].as_tuple()
             ref = oracle.pair_tangent(wl, d, w, cols=cols, misreg=mis)
-            # the IM written by the tangent pass equals the forward pass
+            # the IM written by the tangent pass equals the forward pass to FP32
+            # rounding: the forward pass forms each boundary segment as a dot
+            # product of precomputed bilinear weights, the tangent pass
+            # resamples pixel by pixel, so their sums round differently; each
+            # is held to the parity bar against the oracle elsewhere, so the
+            # two agree within twice that bar per column
             a, b_ = ims[p].cpu().numpy(), fwd[p].cpu().numpy()
-            assert np.abs(a - b_).max() <= 1e-6 * max(np.abs(b_).max(), 1e-30)
+            cpk = np.maximum(np.abs(b_).max(axis=1), 1e-2 * max(np.abs(b_).max(), 1e-30))
+            assert np.all(np.abs(a - b_).max(axis=1) <= 2e-5 * cpk)
             bad = kink_rows(wl, d, w, [mis])
             assert bad.mean() < (0.25 if wl.wfss[w].n_sub > 4 else 0.8)
             for k in range(4):
