@@ -707,7 +707,7 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
             const WfsHost &H = c->wh[w];
             if (H.k > KF_MAX_K || (long)H.n_sub * (H.n_sub + 1) > KPS || !c->geo.dm[d].winK) continue;
             const int p = d * n_wfs + w;
-            e = dev_alloc(c, &c->k_org[p], (size_t)2 * KPS);
+            e = dev_alloc(c, &c->k_org[p], (size_t)4 * KPS);
             if (e == cudaSuccess) e = dev_alloc(c, &c->k_w[p], (size_t)2 * KTAPS * KPS);
             if (e == cudaSuccess) e = dev_alloc(c, &c->k_wb[p], (size_t)2 * KTAPS * KPS);
         }
@@ -895,6 +895,7 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
                     P.kshape[1] = s1;
                     for (int ax = 0; ax < 2; ++ax) {
                         P.korg[ax] = c->k_org[p] + (size_t)ax * KPS;
+                        P.kring[ax] = c->k_org[p] + (size_t)(2 + ax) * KPS;
                         P.kw[ax] = c->k_w[p] + (size_t)ax * KTAPS * KPS;
                         P.kwb[ax] = c->k_wb[p] + (size_t)ax * KTAPS * KPS;
                     }

@@ -43,7 +43,10 @@ constexpr int KPAD = 9;
 constexpr int KBA_MAX = 10, KBC_MAX = 4, KTAPS = KBA_MAX * KBC_MAX;
 constexpr int KPS = 8192;    // plane stride (floats): n_sub (n_sub + 1) <= KPS
 constexpr int KF_MAX_K = 12; // largest subaperture side (pixels) given weight tables
-enum { KF_NONE = 1, KF_ASYM = 2, KF_FALLBACK = 4 };   // segment flags (bits 24-31 of the origin word)
+// segment flags (bits 24-31 of the origin word): no core sample in the box,
+// A and B differ (kwb holds B), resample pixel by pixel, ring pixels listed
+// in kring (repaired by the lane that takes the segment)
+enum { KF_NOCORE = 1, KF_ASYM = 2, KF_FALLBACK = 4, KF_RING = 8 };
 
 struct DevDM {
     const float *win;     // [n_act][win_stride]
@@ -119,9 +122,11 @@ struct DevPair {
     // the A / B sums (kwb only for KF_ASYM segments), tap (along a, across c) at
     // a KBC_MAX + c; kshape = (ori << 8) | (BA << 4) | BC: box of BA x BC taps,
     // along the DM's y (ori 0) or x (ori 1) axis.
+    // kring: bit 2 q + t set when line pixel t of pair q of the segment is a
+    // ring pixel with a stencil bit (KF_RING segments only)
     int kf;
     int kshape[2];
-    int *korg[2];
+    int *korg[2], *kring[2];
     float *kw[2], *kwb[2];
 };
 
@@ -256,7 +261,7 @@ struct synim_ctx {
     long long line_off[SYNIM_MAX_PAIRS] = {};
     uint8_t *d_pst = nullptr, *d_lines = nullptr;
     // boundary-segment weight boxes per pair (nullptr where the sensor's
-    // subapertures are too large for them): origins [2][KPS], weights
+    // subapertures are too large for them): origins and ring lists [2][2][KPS], weights
     // [2][KTAPS][KPS] for A and for B
     int *k_org[SYNIM_MAX_PAIRS] = {};
     float *k_w[SYNIM_MAX_PAIRS] = {}, *k_wb[SYNIM_MAX_PAIRS] = {};

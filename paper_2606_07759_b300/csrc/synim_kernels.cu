@@ -286,9 +286,10 @@ cudaError_t launch_pst(const Geo &g, const DevPair *pairs, int max_mm, int max_l
 // and the bits belong to the (DM, sensor) pair, not to the actuator: A and B
 // are dot products of one box of DM-pixel weights with any actuator's packed
 // window.  k_kseg builds those boxes once per call; the IM kernel then reads
-// BA x BC taps per segment instead of resampling 2 k pixels.  Segments with a
-// ring pixel (its repair reaches beyond the box) or whose samples do not fit
-// the pair's box are flagged KF_FALLBACK and keep the per-sample path.
+// BA x BC taps per segment instead of resampling 2 k pixels.  A ring pixel's
+// repair reaches beyond the box: it is left out of the box and listed, and the
+// IM kernel repairs it from its core neighbours.  Segments whose samples do not
+// fit the pair's box are flagged KF_FALLBACK and keep the per-sample path.
 
 // Shape code (ori << 8) | (BA << 4) | BC of one axis, or -1.  The samples of a
 // segment are 2 pixels across by k along (x segments: along the sensor rows);
@@ -339,7 +340,7 @@ __global__ void __launch_bounds__(128) k_kseg(const __grid_constant__ Geo g, con
     pix(0, 0, i, j);
     const float xf = fmaf(P.Ahi[0], (float)j, fmaf(P.Ahi[1], (float)i, P.bhi[0]));
     const float yf = fmaf(P.Ahi[2], (float)j, fmaf(P.Ahi[3], (float)i, P.bhi[1]));
-    int flags = 0;
+    int flags = 0, ring = 0;
     bool any = false, asym = false;
     int ox = 0, oy = 0, cx0 = INT_MAX, cx1 = INT_MIN, cy0 = INT_MAX, cy1 = INT_MIN;
     if (!(fabsf(xf) < 1e5f && fabsf(yf) < 1e5f)) {
@@ -353,7 +354,10 @@ __global__ void __launch_bounds__(128) k_kseg(const __grid_constant__ Geo g, con
                 const int cl = (c >> (4 + 2 * t)) & 3;
                 const int ba = c & (t ? 4 : 1), bb = c & (t ? 8 : 2);
                 if (!(ba || bb) || cl == 0) continue;
-                if (cl == 2) { flags |= KF_FALLBACK; continue; }
+                if (cl == 2) {   // repaired by the IM kernel from its core neighbours
+                    ring |= 1 << (2 * q + t);
+                    continue;
+                }
                 pix(q, t, i, j);
                 const float xl = exact_affine(P.Ahi[0], P.Alo[0], P.Ahi[1], P.Alo[1], P.bhi[0], P.blo[0], j, i, ox);
                 const float yl = exact_affine(P.Ahi[2], P.Alo[2], P.Ahi[3], P.Alo[3], P.bhi[1], P.blo[1], j, i, oy);
@@ -371,8 +375,12 @@ __global__ void __launch_bounds__(128) k_kseg(const __grid_constant__ Geo g, con
         if (cx1 - cx0 + 2 > ex || cy1 - cy0 + 2 > ey || gx < -2048 || gx > 2047 || gy < -2048 || gy > 2047)
             flags |= KF_FALLBACK;
     }
-    if (!any && !(flags & KF_FALLBACK)) flags |= KF_NONE;
-    if (!(flags & (KF_FALLBACK | KF_NONE))) {
+    if (!any) flags |= KF_NOCORE;
+    if (ring && !(flags & KF_FALLBACK)) {
+        flags |= KF_RING;
+        P.kring[ax][sid] = ring;
+    }
+    if (!(flags & (KF_FALLBACK | KF_NOCORE))) {
         if (asym) flags |= KF_ASYM;
         float *wa = acc[threadIdx.x], *wb = wa + KTAPS;
         for (int q = 0; q < 2 * KTAPS; ++q) wa[q] = 0.f;
@@ -919,7 +927,7 @@ __device__ void kf_pass(const DevWFS &WF, const DevPair &P, const ItemWfs &s, co
             const bool hit = lx + ex > KPAD && lx < KPAD + W && ly + ey > KPAD && ly < KPAD + W;
             if (fl & KF_FALLBACK) {
                 fb = true;
-            } else if (!(fl & KF_NONE) && hit &&
+            } else if (!(fl & KF_NOCORE) && hit &&
                        SYNIM_IDX_OK(lx >= 0 && ly >= 0 && (long)(ly + ey - 1) * Wp + lx + ex - 1 < ev.wn, err)) {
                 act = true;
                 wb = win + ly * Wp + lx;
@@ -936,6 +944,24 @@ __device__ void kf_pass(const DevWFS &WF, const DevPair &P, const ItemWfs &s, co
                 else kf_dot_ba<1, false>(BA, BC, wb, Wp, kwa + sid, kwb + sid, A, B);
             }
             if (!(fl & KF_ASYM)) B = A;   // kwb holds only the asymmetric segments' weights
+        }
+        if (t < cnt && (fl & KF_RING)) {
+            // ring pixels of the segment (Sec. 2.3 step 3), with their stencil bits
+            const int r = t / ncol, c = t - r * ncol;
+            const int sq = ax ? col0 + c : row0 + r, b = ax ? row0 + r : col0 + c;
+            const int u0 = sq * WF.k, l0 = b * WF.k - 1;
+            const uint8_t *cc = (ax ? P.ycc : P.xcc) + b;
+            int rm = __ldg(P.kring[ax] + sid);
+            while (rm) {
+                const int bit = __ffs(rm) - 1;
+                rm &= rm - 1;
+                const int q = bit >> 1, tt = bit & 1;
+                const int cb = __ldg(cc + (long)(u0 + q) * n1);
+                float v[1];
+                ev.ring(ax ? l0 + tt : u0 + q, ax ? u0 + q : l0 + tt, v);
+                if (cb & (tt ? 4 : 1)) A += v[0];
+                if (cb & (tt ? 8 : 2)) B += v[0];
+            }
         }
         if (t < cnt && !fb) {
             out[2 * t] = A;
@@ -1020,8 +1046,9 @@ __device__ __forceinline__ void warp_column_kf(const Geo &g, const DevPair *__re
         const int Rc = min(R, s.si1 - r0 + 1), nb = Rc * nsj;
         kf_pass(WF, P, s, ev, win, D.WpK, D.W, wx0, wy0, 0, r0, nsj + 1, s.sj0, Rc * (nsj + 1), X, lane, err);
         kf_pass(WF, P, s, ev, win, D.WpK, D.W, wx0, wy0, 1, r0 + 1, nsj, s.sj0, nb, Y + 2 * nsj, lane, err);
-        // pupil-edge sums of the chunk's box subapertures (the whole warp on
-        // each that has edge pixels, both axes from one resample per pixel)
+        // pupil-edge sums of the chunk's box subapertures that have edge
+        // pixels: four at a time, eight lanes each (both axes from one
+        // resample per pixel, fixed butterfly order within the group)
         for (int t0 = 0; t0 < nb; t0 += 32) {
             const int t = t0 + lane;
             bool has = false;
@@ -1035,18 +1062,24 @@ __device__ __forceinline__ void warp_column_kf(const Geo &g, const DevPair *__re
                 }
             }
             unsigned m = __ballot_sync(0xffffffffu, has);
+            const int grp = lane >> 3, gl = lane & 7;
             while (m) {
-                const int tt = t0 + __ffs(m) - 1;
-                m &= m - 1;
-                const int q = tt / nsj, c = tt - q * nsj;
+                // the group's subaperture: the grp-th lowest remaining one
+                unsigned mm = m;
+                for (int g2 = 0; g2 < grp && mm; ++g2) mm &= mm - 1;
+                for (int g2 = 0; g2 < 4 && m; ++g2) m &= m - 1;
+                const int tt = mm ? t0 + __ffs(mm) - 1 : -1;
                 float ax_[1] = {0.f}, ay_[1] = {0.f};
-                edge_sum<1>(WF, s, ev, r0 + q, s.sj0 + c, lane, 32, ax_, ay_);
+                if (tt >= 0) {
+                    const int q = tt / nsj, c = tt - q * nsj;
+                    edge_sum<1>(WF, s, ev, r0 + q, s.sj0 + c, gl, 8, ax_, ay_);
+                }
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
+                for (int o = 4; o > 0; o >>= 1) {
                     ax_[0] += __shfl_xor_sync(0xffffffffu, ax_[0], o);
                     ay_[0] += __shfl_xor_sync(0xffffffffu, ay_[0], o);
                 }
-                if (lane == 0) {
+                if (gl == 0 && tt >= 0) {
                     E[2 * tt] = ax_[0];
                     E[2 * tt + 1] = ay_[0];
                 }
