@@ -914,7 +914,7 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
             if (P.kf) {
                 // chunks of four box rows: X, Y, E of four rows and the carried Y row
                 const long long nsj = (need[p] / (2 * NV) - 1) / 4;
-                need[p] = std::max(need[p], (26 * nsj + 8 + 3) / 4 * 4);
+                need[p] = std::max(need[p], (26 * nsj + 8 + 64 + 3) / 4 * 4);   // + the ring buffer
                 max_seg = std::max(max_seg, c->wh[w].n_sub * (c->wh[w].n_sub + 1));
             }
         }
@@ -964,8 +964,9 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
         if (mode == MODE_FWD && hp[p].im && !hp[p].kf) any_plain = true;
         if (mode == MODE_FWD && hp[p].im && hp[p].kf) any_k = true;
     }
+    // one launch: k_imk takes every forward column when some pair has weight boxes
     auto grids = [&](int th, int &g0, int &g1) {
-        g0 = any_plain ? grid_for(th) : 0;
+        g0 = (any_plain && !any_k) ? grid_for(th) : 0;
         g1 = any_k ? grid_for(th) : 0;
     };
     if ((e = cudaMemcpyAsync(c->d_pairs, hp, sizeof(DevPair) * np, cudaMemcpyHostToDevice, s)) != cudaSuccess)

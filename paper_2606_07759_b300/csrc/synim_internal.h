@@ -186,8 +186,8 @@ size_t im_smem_bytes(const Geo &g);
 cudaError_t im_prepare(int mode, int threads, size_t smem, int *blocks_per_sm);
 // gp: MODE_VJP only, the per-column partials [n_items * n_wfs][4] that
 // launch_vjp_reduce sums per pair into grad_p [n_pairs][4].
-// MODE_FWD: k_im over the pairs without weight boxes (grid CTAs, none if 0),
-// then k_imk over those with them (kgrid CTAs, none if 0).
+// MODE_FWD: k_im (grid CTAs, none if 0) when no pair has weight boxes, else
+// k_imk over every column (kgrid CTAs).
 cudaError_t launch_im(int mode, const Geo &g, const DevPair *pairs, int *err, double *gp, int grid, int threads,
                       size_t smem, cudaStream_t s, int kgrid = 0);
 cudaError_t launch_vjp_reduce(const Geo &g, const double *part, double *gp, cudaStream_t s);

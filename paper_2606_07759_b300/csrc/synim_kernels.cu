@@ -229,10 +229,11 @@ __global__ void k_pst_core(const __grid_constant__ Geo g, const DevPair *__restr
 // a non-core pixel with a core 4-neighbour), 0 otherwise.
 __device__ __forceinline__ int pixel_class(const uint8_t *__restrict__ pst, int M, int i, int j) {
     const long q = (long)i * M + j;
-    if (pst[q]) return 1;
-    const bool ring = (j + 1 < M && pst[q + 1]) || (j >= 1 && pst[q - 1]) ||
-                      (i + 1 < M && pst[q + M]) || (i >= 1 && pst[q - M]);
-    return ring ? 2 : 0;
+    // five independent byte loads (no short-circuit chain)
+    const int c = pst[q];
+    const int nb = (j + 1 < M ? pst[q + 1] : 0) | (j >= 1 ? pst[q - 1] : 0) | (i + 1 < M ? pst[q + M] : 0) |
+                   (i >= 1 ? pst[q - M] : 0);
+    return c ? 1 : (nb ? 2 : 0);
 }
 
 // Boundary-line bytes: for boundary b and pixel row i (x) / column j (y):
@@ -765,8 +766,16 @@ __device__ __forceinline__ void edge_sum(const DevWFS &WF, const ItemWfs &s, con
 #pragma unroll
         for (int t = 0; t < NV; ++t) v[t] = 0.f;
         const int c = pixel_class(s.pst, WF.M, i, j);
-        if (c == 1) ev.bil(i, j, v);
-        else if (c == 2) ev.ring(i, j, v);
+        if constexpr (NV == 1) {
+            // resample while the class loads; keep it for a core pixel
+            float b1[1];
+            ev.bil(i, j, b1);
+            if (c == 1) v[0] = b1[0];
+            else if (c == 2) ev.ring(i, j, v);
+        } else {
+            if (c == 1) ev.bil(i, j, v);
+            else if (c == 2) ev.ring(i, j, v);
+        }
 #pragma unroll
         for (int t = 0; t < NV; ++t) {
             ax[t] = fmaf(wx, v[t], ax[t]);
@@ -899,10 +908,11 @@ __device__ __forceinline__ void kf_dot_ba(int BA, int BC, const float *wb, int W
 // One pass over cnt segments of axis ax: t = r ncol + c is x segment
 // (row0 + r, boundary col0 + c) or y segment (boundary row0 + r, column col0
 // + c); out[2 t], out[2 t + 1] = A, B.  Lanes take one segment each; flagged
-// segments are resampled pixel by pixel afterwards by the whole warp.
+// segments are resampled pixel by pixel afterwards by the whole warp.  rbuf:
+// 64 floats of the warp's buffer for the ring pixels.
 __device__ void kf_pass(const DevWFS &WF, const DevPair &P, const ItemWfs &s, const Eval<1> &ev,
                         const float *__restrict__ win, int Wp, int W, int wx0, int wy0, int ax, int row0,
-                        int ncol, int col0, int cnt, float *out, int lane, int *err) {
+                        int ncol, int col0, int cnt, float *out, float *rbuf, int lane, int *err) {
     const int n = WF.n_sub, n1 = n + 1;
     const int shape = P.kshape[ax];
     const int ori = shape >> 8, BA = (shape >> 4) & 15, BC = shape & 15;
@@ -945,23 +955,48 @@ __device__ void kf_pass(const DevWFS &WF, const DevPair &P, const ItemWfs &s, co
             }
             if (!(fl & KF_ASYM)) B = A;   // kwb holds only the asymmetric segments' weights
         }
-        if (t < cnt && (fl & KF_RING)) {
-            // ring pixels of the segment (Sec. 2.3 step 3), with their stencil bits
-            const int r = t / ncol, c = t - r * ncol;
-            const int sq = ax ? col0 + c : row0 + r, b = ax ? row0 + r : col0 + c;
-            const int u0 = sq * WF.k, l0 = b * WF.k - 1;
-            const uint8_t *cc = (ax ? P.ycc : P.xcc) + b;
-            int rm = __ldg(P.kring[ax] + sid);
-            while (rm) {
-                const int bit = __ffs(rm) - 1;
-                rm &= rm - 1;
-                const int q = bit >> 1, tt = bit & 1;
-                const int cb = __ldg(cc + (long)(u0 + q) * n1);
+        // ring pixels of the pass's segments (Sec. 2.3 step 3) with their
+        // stencil bits, spread over the lanes: the j-th one is repaired by lane
+        // j % 32 into rbuf, then each segment's lane adds its own in order
+        const int rm = (t < cnt && (fl & KF_RING)) ? __ldg(P.kring[ax] + sid) : 0;
+        const int nr = __popc(rm);
+        int pre = nr;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, pre, o);
+            if (lane >= o) pre += v;
+        }
+        const int total = __shfl_sync(0xffffffffu, pre, 31), excl = pre - nr;
+        for (int j0 = 0; j0 < total; j0 += 32) {
+            const int j = j0 + lane;
+            int own = 0;   // the last lane whose first ring pixel is at or before j
+#pragma unroll
+            for (int st = 16; st > 0; st >>= 1)
+                if (__shfl_sync(0xffffffffu, excl, own + st) <= j) own += st;
+            const int orm = __shfl_sync(0xffffffffu, rm, own), oex = __shfl_sync(0xffffffffu, excl, own);
+            float va = 0.f, vb = 0.f;
+            if (j < total) {
+                int mm = orm;
+                for (int q = j - oex; q > 0; --q) mm &= mm - 1;
+                const int bit = __ffs(mm) - 1, q = bit >> 1, tt = bit & 1;
+                const int to = base + own, r = to / ncol, c = to - r * ncol;
+                const int sq = ax ? col0 + c : row0 + r, b = ax ? row0 + r : col0 + c;
+                const int u0 = sq * WF.k, l0 = b * WF.k - 1;
+                const int cb = __ldg((ax ? P.ycc : P.xcc) + b + (long)(u0 + q) * n1);
                 float v[1];
                 ev.ring(ax ? l0 + tt : u0 + q, ax ? u0 + q : l0 + tt, v);
-                if (cb & (tt ? 4 : 1)) A += v[0];
-                if (cb & (tt ? 8 : 2)) B += v[0];
+                va = (cb & (tt ? 4 : 1)) ? v[0] : 0.f;
+                vb = (cb & (tt ? 8 : 2)) ? v[0] : 0.f;
             }
+            rbuf[2 * lane] = va;
+            rbuf[2 * lane + 1] = vb;
+            __syncwarp();
+            const int q1 = min(excl + nr, j0 + 32);
+            for (int q = max(excl, j0); q < q1; ++q) {
+                A += rbuf[2 * (q - j0)];
+                B += rbuf[2 * (q - j0) + 1];
+            }
+            __syncwarp();
         }
         if (t < cnt && !fb) {
             out[2 * t] = A;
@@ -1007,8 +1042,8 @@ __device__ __forceinline__ void warp_column_kf(const Geo &g, const DevPair *__re
     __syncwarp();
     const int nv = WF.nv, n2 = 2 * nv;
     const int nsj = s.empty ? 0 : s.nsj;
-    // at least one box row: X, two Y rows and E
-    if (!s.empty && 2 * (4 * nsj + 1) > cap) {
+    // at least one box row: X, two Y rows and E, and the ring buffer
+    if (!s.empty && 2 * (4 * nsj + 1) + 64 > cap) {
         if (lane == 0) atomicOr(err, ERR_ARENA);
         s.empty = 1;
     }
@@ -1036,16 +1071,17 @@ __device__ __forceinline__ void warp_column_kf(const Geo &g, const DevPair *__re
 #endif
     const int nrows = s.si1 - s.si0 + 1;
     // chunk rows: X, Y and E of R rows plus the carried Y row
-    const int R = max(1, min(nrows, (cap / 2 - nsj) / (3 * nsj + 1)));
+    const int R = max(1, min(nrows, ((cap - 64) / 2 - nsj) / (3 * nsj + 1)));
+    float *rbuf = wbuf + cap - 64;
     float *X = wbuf;
     float *Y = X + (size_t)R * (nsj + 1) * 2;
     float *E = Y + (size_t)(R + 1) * nsj * 2;
     // the boundary above the box
-    kf_pass(WF, P, s, ev, win, D.WpK, D.W, wx0, wy0, 1, s.si0, nsj, s.sj0, nsj, Y, lane, err);
+    kf_pass(WF, P, s, ev, win, D.WpK, D.W, wx0, wy0, 1, s.si0, nsj, s.sj0, nsj, Y, rbuf, lane, err);
     for (int r0 = s.si0; r0 <= s.si1; r0 += R) {
         const int Rc = min(R, s.si1 - r0 + 1), nb = Rc * nsj;
-        kf_pass(WF, P, s, ev, win, D.WpK, D.W, wx0, wy0, 0, r0, nsj + 1, s.sj0, Rc * (nsj + 1), X, lane, err);
-        kf_pass(WF, P, s, ev, win, D.WpK, D.W, wx0, wy0, 1, r0 + 1, nsj, s.sj0, nb, Y + 2 * nsj, lane, err);
+        kf_pass(WF, P, s, ev, win, D.WpK, D.W, wx0, wy0, 0, r0, nsj + 1, s.sj0, Rc * (nsj + 1), X, rbuf, lane, err);
+        kf_pass(WF, P, s, ev, win, D.WpK, D.W, wx0, wy0, 1, r0 + 1, nsj, s.sj0, nb, Y + 2 * nsj, rbuf, lane, err);
         // pupil-edge sums of the chunk's box subapertures that have edge
         // pixels: four at a time, eight lanes each (both axes from one
         // resample per pixel, fixed butterfly order within the group)
@@ -1123,7 +1159,10 @@ __device__ __forceinline__ void warp_column(const Geo &g, const DevPair *__restr
     const int pidx = d * g.n_wfs + w;
     const DevPair &P = pairs[pidx];
     if (!pair_active<MODE>(P)) return;
-    if (MODE == MODE_FWD && P.kf) return;   // k_imk's column
+    if (MODE == MODE_FWD && P.kf) {   // a weight-box column: k_imk's
+        if (lane == 0) atomicOr(err, ERR_ARENA);
+        return;
+    }
     const DevWFS &WF = g.wfs[w];
     const DevDM &D = g.dm[d];
     // The column's pixel and subaperture boxes live in shared memory, one
@@ -1481,8 +1520,9 @@ k_tele(const __grid_constant__ Geo g, const __grid_constant__ TeleSet t, const D
     if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 
-// Forward IM columns of the pairs with boundary-segment weight boxes (kf),
-// one warp per column as in k_im; k_im skips these pairs.
+// Forward IM columns when some pair has boundary-segment weight boxes: one
+// warp per column as in k_im, the weight boxes for those pairs (kf) and
+// k_im's per-sample path for the others, all in one launch.
 __global__ void __launch_bounds__(256, 3)
 k_imk(const __grid_constant__ Geo g, const DevPair *__restrict__ pairs, int *__restrict__ err) {
     extern __shared__ __align__(16) float smem_f[];
@@ -1497,8 +1537,9 @@ k_imk(const __grid_constant__ Geo g, const DevPair *__restrict__ pairs, int *__r
         int d, a;
         decode_item(g, item, d, a);
         const DevPair &P = pairs[d * g.n_wfs + w];
-        if (!P.kf || !P.im) continue;
-        warp_column_kf(g, pairs, d, a, w, wbuf, g.seg_floats, lane, err);
+        if (!P.im) continue;
+        if (P.kf) warp_column_kf(g, pairs, d, a, w, wbuf, g.seg_floats, lane, err);
+        else warp_column<MODE_FWD, 1>(g, pairs, d, a, w, wbuf, g.seg_floats, lane, err, nullptr, u);
     }
     if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
