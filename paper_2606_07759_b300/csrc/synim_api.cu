@@ -912,9 +912,14 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
             }
             need[p] = (seg_need(c->dmh[d], c->wh[w], P.Ai, NV) + 3) / 4 * 4;
             if (P.kf) {
-                // chunks of four box rows: X, Y, E of four rows and the carried Y row
+                // chunks of box rows (X, Y, E of the rows, the carried Y row and the
+                // ring buffer) in at most 768 floats, and at least four rows: small
+                // boxes take one chunk, large ones several, and the per-warp buffer
+                // stays small enough for the occupancy the registers allow
                 const long long nsj = (need[p] / (2 * NV) - 1) / 4;
-                need[p] = std::max(need[p], (26 * nsj + 8 + 64 + 3) / 4 * 4);   // + the ring buffer
+                const long long whole = 2 * ((nsj + 1) * (3 * nsj + 1) + nsj) + 64;
+                const long long four = 2 * (4 * (3 * nsj + 1) + nsj) + 64;
+                need[p] = std::max(need[p], (std::max(four, std::min(whole, 768LL)) + 3) / 4 * 4);
                 max_seg = std::max(max_seg, c->wh[w].n_sub * (c->wh[w].n_sub + 1));
             }
         }
@@ -947,7 +952,7 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
         threads = c->tune_threads[mode];
         g.seg_lanes = c->tune_lanes[mode];
     }
-    const size_t smem = im_smem_bytes(g);
+    size_t smem = im_smem_bytes(g, threads);
     const long long units = (long long)c->geo.n_items * c->n_wfs;
     auto grid_for = [&](int th) {
         const long long warps = th / 32;
@@ -1039,14 +1044,15 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
                 Geo gt = g;
                 gt.seg_lanes = l;
                 int b2 = 0;
-                if ((e = im_prepare(mode, th, smem, &b2)) != cudaSuccess || b2 < 1) continue;
+                const size_t sm = im_smem_bytes(g, th);
+                if ((e = im_prepare(mode, th, sm, &b2)) != cudaSuccess || b2 < 1) continue;
                 int gr = 0, gk = 0;
                 grids(th, gr, gk);
                 float ms = 0.f;
-                e = launch_im(mode, gt, c->d_pairs, c->d_err, c->d_vjp_part, gr, th, smem, s, gk);
+                e = launch_im(mode, gt, c->d_pairs, c->d_err, c->d_vjp_part, gr, th, sm, s, gk);
                 if (e == cudaSuccess) e = cudaEventRecord(t0, s);
                 for (int r = 0; r < 3 && e == cudaSuccess; ++r)
-                    e = launch_im(mode, gt, c->d_pairs, c->d_err, c->d_vjp_part, gr, th, smem, s, gk);
+                    e = launch_im(mode, gt, c->d_pairs, c->d_err, c->d_vjp_part, gr, th, sm, s, gk);
                 if (e == cudaSuccess) e = cudaEventRecord(t1, s);
                 if (e == cudaSuccess) e = cudaEventSynchronize(t1);
                 if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
@@ -1066,6 +1072,7 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
         c->tune_ms[mode] = best / 3.f;
         threads = best_th;
         g.seg_lanes = best_l;
+        smem = im_smem_bytes(g, threads);
         if ((e = im_prepare(mode, threads, smem, &bps)) != cudaSuccess) return cuda_fail(c, e, "kernel attributes");
         grid = grid_for(threads);
     }

@@ -182,7 +182,8 @@ cudaError_t launch_pst(const Geo &g, const DevPair *pairs, int max_mm, int max_l
 cudaError_t launch_kseg(const Geo &g, const DevPair *pairs, int max_seg, cudaStream_t s);
 // Box shape code of one axis for the composite A and subaperture side k, or -1.
 int kseg_shape(const double A[4], int k, int axis);
-size_t im_smem_bytes(const Geo &g);
+// dynamic shared memory of the IM kernels: one seg_floats buffer per warp
+size_t im_smem_bytes(const Geo &g, int threads);
 cudaError_t im_prepare(int mode, int threads, size_t smem, int *blocks_per_sm);
 // gp: MODE_VJP only, the per-column partials [n_items * n_wfs][4] that
 // launch_vjp_reduce sums per pair into grad_p [n_pairs][4].

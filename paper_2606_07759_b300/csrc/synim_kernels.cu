@@ -861,6 +861,14 @@ __device__ __forceinline__ void warp_segments(const DevWFS &WF, const ItemWfs &s
 // ---------------------------------------------------------------------------
 // IM columns from the boundary-segment weight boxes (forward IMs)
 // ---------------------------------------------------------------------------
+// t / n for 0 <= t < 2^20 and 0 < n, from inv = 1 / n (one correction step).
+__device__ __forceinline__ int fast_div(int t, float inv, int n) {
+    int q = (int)(((float)t + 0.5f) * inv);
+    if (q * n > t) --q;
+    else if ((q + 1) * n <= t) ++q;
+    return q;
+}
+
 // A = sum over the box of kw[tap] * window, B likewise with kwb (TWO) or A.
 // wb: the window at the box origin; ka / kb: tap 0 of the segment's planes.
 template <int BA, int BC, int ORI, bool TWO>
@@ -920,6 +928,7 @@ __device__ void kf_pass(const DevWFS &WF, const DevPair &P, const ItemWfs &s, co
     const int *__restrict__ org = P.korg[ax];
     const float *kwa = P.kw[ax], *kwb = P.kwb[ax];
     const int lx0 = wx0 - KPAD, ly0 = wy0 - KPAD;
+    const float inv = 1.f / (float)ncol;
     (void)err;
     for (int base = 0; base < cnt; base += 32) {
         const int t = base + lane;
@@ -927,7 +936,7 @@ __device__ void kf_pass(const DevWFS &WF, const DevPair &P, const ItemWfs &s, co
         bool act = false, fb = false;
         const float *wb = win;
         if (t < cnt) {
-            const int r = t / ncol, c = t - r * ncol;
+            const int r = fast_div(t, inv, ncol), c = t - r * ncol;
             sid = ax ? (row0 + r) * n + (col0 + c) : (row0 + r) * n1 + (col0 + c);
             const int word = __ldg(org + sid);
             fl = (int)((unsigned)word >> 24);
@@ -960,6 +969,7 @@ __device__ void kf_pass(const DevWFS &WF, const DevPair &P, const ItemWfs &s, co
         // j % 32 into rbuf, then each segment's lane adds its own in order
         const int rm = (t < cnt && (fl & KF_RING)) ? __ldg(P.kring[ax] + sid) : 0;
         const int nr = __popc(rm);
+        if (__any_sync(0xffffffffu, rm != 0)) {
         int pre = nr;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -979,7 +989,7 @@ __device__ void kf_pass(const DevWFS &WF, const DevPair &P, const ItemWfs &s, co
                 int mm = orm;
                 for (int q = j - oex; q > 0; --q) mm &= mm - 1;
                 const int bit = __ffs(mm) - 1, q = bit >> 1, tt = bit & 1;
-                const int to = base + own, r = to / ncol, c = to - r * ncol;
+                const int to = base + own, r = fast_div(to, inv, ncol), c = to - r * ncol;
                 const int sq = ax ? col0 + c : row0 + r, b = ax ? row0 + r : col0 + c;
                 const int u0 = sq * WF.k, l0 = b * WF.k - 1;
                 const int cb = __ldg((ax ? P.ycc : P.xcc) + b + (long)(u0 + q) * n1);
@@ -998,6 +1008,7 @@ __device__ void kf_pass(const DevWFS &WF, const DevPair &P, const ItemWfs &s, co
             }
             __syncwarp();
         }
+        }
         if (t < cnt && !fb) {
             out[2 * t] = A;
             out[2 * t + 1] = B;
@@ -1006,7 +1017,7 @@ __device__ void kf_pass(const DevWFS &WF, const DevPair &P, const ItemWfs &s, co
         while (m) {
             const int tt = base + __ffs(m) - 1;
             m &= m - 1;
-            const int r = tt / ncol, c = tt - r * ncol;
+            const int r = fast_div(tt, inv, ncol), c = tt - r * ncol;
             const SegRows sr = ax ? seg_rows(WF, s, 1, row0 + r, col0 + c) : seg_rows(WF, s, 0, col0 + c, row0 + r);
             float fa[1] = {0.f}, fbv[1] = {0.f};
             seg_compute<1>(WF, sr, ev, ax, lane, 32, fa, fbv);
@@ -1085,11 +1096,12 @@ __device__ __forceinline__ void warp_column_kf(const Geo &g, const DevPair *__re
         // pupil-edge sums of the chunk's box subapertures that have edge
         // pixels: four at a time, eight lanes each (both axes from one
         // resample per pixel, fixed butterfly order within the group)
+        const float inv_nsj = 1.f / (float)nsj;
         for (int t0 = 0; t0 < nb; t0 += 32) {
             const int t = t0 + lane;
             bool has = false;
             if (t < nb) {
-                const int q = t / nsj, c = t - q * nsj;
+                const int q = fast_div(t, inv_nsj, nsj), c = t - q * nsj;
                 const int qq = (r0 + q) * WF.n_sub + s.sj0 + c;
                 has = WF.irr_sub[qq + 1] > WF.irr_sub[qq];
                 if (!has) {
@@ -1107,7 +1119,7 @@ __device__ __forceinline__ void warp_column_kf(const Geo &g, const DevPair *__re
                 const int tt = mm ? t0 + __ffs(mm) - 1 : -1;
                 float ax_[1] = {0.f}, ay_[1] = {0.f};
                 if (tt >= 0) {
-                    const int q = tt / nsj, c = tt - q * nsj;
+                    const int q = fast_div(tt, inv_nsj, nsj), c = tt - q * nsj;
                     edge_sum<1>(WF, s, ev, r0 + q, s.sj0 + c, gl, 8, ax_, ay_);
                 }
 #pragma unroll
@@ -1127,6 +1139,7 @@ __device__ __forceinline__ void warp_column_kf(const Geo &g, const DevPair *__re
         // sums, times slope_scale / (2 dw lit)), zero for the others
         const int ra = WF.vrow[r0], rb = WF.vrow[r0 + Rc];
         if (!SYNIM_IDX_OK(0 <= ra && ra <= rb && rb <= nv, err)) return;
+#pragma unroll 2
         for (int r = ra + lane; r < rb; r += 32) {
             const int vs = __ldg(WF.vsub + r);
             const int q = (vs >> 16) - r0, c = (vs & 0xffff) - s.sj0;
@@ -1557,7 +1570,7 @@ cudaError_t launch_tele(const Geo &g, const TeleSet &t, const DevPair *pairs, in
     return cudaGetLastError();
 }
 
-size_t im_smem_bytes(const Geo &g) { return (size_t)8 * g.seg_floats * 4; }
+size_t im_smem_bytes(const Geo &g, int threads) { return (size_t)(threads / 32) * g.seg_floats * 4; }
 
 template <int MODE>
 static cudaError_t prepare_one(int threads, size_t smem, int *bps) {

@@ -475,7 +475,7 @@ extern "C" synim_status synim_im_compute_noalloc(const synim_dm_desc *dm, const 
     g.n_dm = 1; g.n_wfs = 1; g.n_items = n_act;
     g.order_dm[0] = 0; g.order_start[0] = 0; g.order_start[1] = n_act;
     g.seg_floats = (int)seg;
-    const size_t smem = im_smem_bytes(g);
+    const size_t smem = im_smem_bytes(g, 256);
     int dev_max = 0, n_sm = 0, bps = 0;
     cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
