@@ -795,7 +795,7 @@ def run_synim(args):
                                                                "picked_by": "autotuner (first call)"}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": "k_im<0>", "alg_bytes_per_launch": alg_bytes,
+                     "kernel": "k_imk", "alg_bytes_per_launch": alg_bytes,
                      "kernel_ms_avg": 1000 * k_avg_s},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "what": "create from pinned host IF cubes + compute + IMs to pinned host memory"},

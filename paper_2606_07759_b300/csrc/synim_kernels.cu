@@ -172,18 +172,8 @@ __device__ __forceinline__ int mask_tap(const uint8_t *__restrict__ mask, int N,
 // FP32 pre-tests settle every pixel whose neighbourhood of mask taps is
 // uniform, and every pixel whose four taps agree and whose fractional position
 // is far from an integer, so FP64 runs only at mask edges near cell lines.
-__global__ void k_pst_core(const __grid_constant__ Geo g, const DevPair *__restrict__ pairs) {
-    const int p = blockIdx.y;
-    const int d = p / g.n_wfs, w = p - d * g.n_wfs;
-    const int M = g.wfs[w].M;
-    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long)M * M) return;
-    const DevPair &P = pairs[p];
-    uint8_t *pst = P.pst;
-    if (!pst) return;
-    const int i = (int)(idx / M), j = (int)(idx - (long)i * M);
-    const int N = g.dm[d].N;
-    const uint8_t *mask = g.dm[d].mask;
+__device__ __forceinline__ int core_at(const DevPair &P, const uint8_t *__restrict__ mask,
+                                       const uint8_t *__restrict__ mcls, int N, int i, int j) {
     const float xf = fmaf(P.Ahi[0], (float)j, fmaf(P.Ahi[1], (float)i, P.bhi[0]));
     const float yf = fmaf(P.Ahi[2], (float)j, fmaf(P.Ahi[3], (float)i, P.bhi[1]));
     int core = -1;
@@ -195,7 +185,7 @@ __global__ void k_pst_core(const __grid_constant__ Geo g, const DevPair *__restr
         if (ix < -2 || iy < -2 || ix > N || iy > N) {
             core = 0;  // every tap of every candidate cell is off the grid
         } else if (ix >= -1 && iy >= -1 && ix <= N - 1 && iy <= N - 1) {
-            const int c = g.dm[d].mcls[(long)(iy + 1) * (N + 1) + (ix + 1)];
+            const int c = mcls[(long)(iy + 1) * (N + 1) + (ix + 1)];
             if (c != 2) core = c;
         }
         if (core < 0) {
@@ -222,7 +212,41 @@ __global__ void k_pst_core(const __grid_constant__ Geo g, const DevPair *__restr
         m = __dadd_rn(m, __dmul_rn(__dmul_rn(fx, fy), (double)mask_tap(mask, N, ix + 1, iy + 1)));
         core = (m >= 0.999999) ? 1 : 0;
     }
-    pst[idx] = (uint8_t)core;
+    return core;
+}
+
+// Four consecutive pixels (row-major over the M x M grid) per thread, stored
+// as one 32-bit word where aligned.
+__global__ void k_pst_core(const __grid_constant__ Geo g, const DevPair *__restrict__ pairs) {
+    const int p = blockIdx.y;
+    const int d = p / g.n_wfs, w = p - d * g.n_wfs;
+    const int M = g.wfs[w].M;
+    const long MM = (long)M * M;
+    const long q0 = 4 * ((long)blockIdx.x * blockDim.x + threadIdx.x);
+    if (q0 >= MM) return;
+    const DevPair &P = pairs[p];
+    uint8_t *pst = P.pst;
+    if (!pst) return;
+    const int N = g.dm[d].N;
+    const uint8_t *mask = g.dm[d].mask, *mcls = g.dm[d].mcls;
+    int c[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const long q = q0 + e;
+        c[e] = 0;
+        if (q < MM) {
+            const int i = (int)(q / M), j = (int)(q - (long)i * M);
+            c[e] = core_at(P, mask, mcls, N, i, j);
+        }
+    }
+    if (q0 + 3 < MM && (reinterpret_cast<uintptr_t>(pst + q0) & 3u) == 0) {
+        *reinterpret_cast<uint32_t *>(pst + q0) = (uint32_t)c[0] | ((uint32_t)c[1] << 8) | ((uint32_t)c[2] << 16) |
+                                                  ((uint32_t)c[3] << 24);
+    } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (q0 + e < MM) pst[q0 + e] = (uint8_t)c[e];
+    }
 }
 
 // Class of a sensor pixel from the core map: 1 core, 2 ring (Sec. 2.3 step 2:
@@ -234,6 +258,16 @@ __device__ __forceinline__ int pixel_class(const uint8_t *__restrict__ pst, int 
     const int nb = (j + 1 < M ? pst[q + 1] : 0) | (j >= 1 ? pst[q - 1] : 0) | (i + 1 < M ? pst[q + M] : 0) |
                    (i >= 1 ? pst[q - M] : 0);
     return c ? 1 : (nb ? 2 : 0);
+}
+
+// The same class with the neighbour tests short-circuited (fewer loads where
+// most pixels are core: the whole-grid class kernel).
+__device__ __forceinline__ int pixel_class_sc(const uint8_t *__restrict__ pst, int M, int i, int j) {
+    const long q = (long)i * M + j;
+    if (pst[q]) return 1;
+    const bool ring = (j + 1 < M && pst[q + 1]) || (j >= 1 && pst[q - 1]) ||
+                      (i + 1 < M && pst[q + M]) || (i >= 1 && pst[q - M]);
+    return ring ? 2 : 0;
 }
 
 // Boundary-line bytes: for boundary b and pixel row i (x) / column j (y):
@@ -256,19 +290,19 @@ __global__ void k_pst_codes(const __grid_constant__ Geo g, const DevPair *__rest
     int code;
     if (dir == 0) {
         code = WF.xcode[(long)b * M + x];
-        const int k0 = (c0 >= 0) ? pixel_class(P.pst, M, x, c0) : 0;
-        const int k1 = (c1 < M) ? pixel_class(P.pst, M, x, c1) : 0;
+        const int k0 = (c0 >= 0) ? pixel_class_sc(P.pst, M, x, c0) : 0;
+        const int k1 = (c1 < M) ? pixel_class_sc(P.pst, M, x, c1) : 0;
         P.xcc[r] = (uint8_t)(code | (k0 << 4) | (k1 << 6));
     } else {
         code = WF.ycode[(long)b * M + x];
-        const int k0 = (c0 >= 0) ? pixel_class(P.pst, M, c0, x) : 0;
-        const int k1 = (c1 < M) ? pixel_class(P.pst, M, c1, x) : 0;
+        const int k0 = (c0 >= 0) ? pixel_class_sc(P.pst, M, c0, x) : 0;
+        const int k1 = (c1 < M) ? pixel_class_sc(P.pst, M, c1, x) : 0;
         P.ycc[r] = (uint8_t)(code | (k0 << 4) | (k1 << 6));
     }
 }
 
 cudaError_t launch_pst(const Geo &g, const DevPair *pairs, int max_mm, int max_lines, cudaStream_t s) {
-    dim3 grid((max_mm + 255) / 256, g.n_dm * g.n_wfs);
+    dim3 grid((max_mm + 1023) / 1024, g.n_dm * g.n_wfs);
     k_pst_core<<<grid, 256, 0, s>>>(g, pairs);
     dim3 grid2((2 * max_lines + 255) / 256, g.n_dm * g.n_wfs);
     k_pst_codes<<<grid2, 256, 0, s>>>(g, pairs);
@@ -344,13 +378,19 @@ __global__ void __launch_bounds__(128) k_kseg(const __grid_constant__ Geo g, con
     int flags = 0, ring = 0;
     bool any = false, asym = false;
     int ox = 0, oy = 0, cx0 = INT_MAX, cx1 = INT_MIN, cy0 = INT_MAX, cy1 = INT_MIN;
+    // the segment's class bytes, loaded together (k <= KF_MAX_K)
+    int cb[KF_MAX_K];
+#pragma unroll
+    for (int q = 0; q < KF_MAX_K; ++q) cb[q] = q < k ? cc[(long)(u0 + q) * n1] : 0;
     if (!(fabsf(xf) < 1e5f && fabsf(yf) < 1e5f)) {
         flags = KF_FALLBACK;
     } else {
         ox = (int)floorf(xf) - 1;
         oy = (int)floorf(yf) - 1;
-        for (int q = 0; q < k; ++q) {
-            const int c = cc[(long)(u0 + q) * n1];
+#pragma unroll
+        for (int q = 0; q < KF_MAX_K; ++q) {
+            if (q >= k) break;
+            const int c = cb[q];
             for (int t = 0; t < 2; ++t) {
                 const int cl = (c >> (4 + 2 * t)) & 3;
                 const int ba = c & (t ? 4 : 1), bb = c & (t ? 8 : 2);
@@ -385,8 +425,10 @@ __global__ void __launch_bounds__(128) k_kseg(const __grid_constant__ Geo g, con
         if (asym) flags |= KF_ASYM;
         float *wa = acc[threadIdx.x], *wb = wa + KTAPS;
         for (int q = 0; q < 2 * KTAPS; ++q) wa[q] = 0.f;
-        for (int q = 0; q < k; ++q) {
-            const int c = cc[(long)(u0 + q) * n1];
+#pragma unroll
+        for (int q = 0; q < KF_MAX_K; ++q) {
+            if (q >= k) break;
+            const int c = cb[q];
             for (int t = 0; t < 2; ++t) {
                 const int cl = (c >> (4 + 2 * t)) & 3;
                 const int ba = c & (t ? 4 : 1), bb = c & (t ? 8 : 2);
