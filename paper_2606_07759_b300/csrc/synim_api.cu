@@ -753,6 +753,14 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
     }
     c->geo.order_start[n_dm] = acc;
     c->geo.n_items = acc;
+    {
+        int q = 0;
+        for (int w = 0; w < n_wfs; ++w)
+            if (c->wh[w].k <= 32) c->geo.wfs_order[q++] = w;
+        c->geo.n_wfs_a = q;
+        for (int w = 0; w < n_wfs; ++w)
+            if (c->wh[w].k > 32) c->geo.wfs_order[q++] = w;
+    }
     if ((e = dev_alloc(c, &c->d_vjp_part, (size_t)acc * n_wfs * 4)) != cudaSuccess)
         return bail(cuda_fail(c, e, "adjoint partials"));
     c->geo.n_dm = n_dm;

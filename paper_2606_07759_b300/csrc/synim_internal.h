@@ -136,6 +136,11 @@ struct Geo {
     int n_dm, n_wfs, n_items;
     int order_dm[SYNIM_MAX_DM];         // DM processed at each position (costliest first)
     int order_start[SYNIM_MAX_DM + 1];  // item prefix in processing order
+    // k_imk's column order within each DM: the actuators on the sensors
+    // wfs_order[0 .. n_wfs_a) (subapertures of at most 32 pixels), then the
+    // actuators on the others, so that a CTA's warps take columns of one kind
+    int wfs_order[SYNIM_MAX_WFS];
+    int n_wfs_a;
     int seg_floats;      // per-warp shared-memory buffer of the IM kernel (floats)
     int seg_lanes;       // lanes per boundary segment for k <= 32 (2, 4 or 8); 0 = by k
 };

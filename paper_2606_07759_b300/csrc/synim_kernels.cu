@@ -1588,9 +1588,23 @@ k_imk(const __grid_constant__ Geo g, const DevPair *__restrict__ pairs, int *__r
     __syncthreads();
     const long n_units = (long)g.n_items * g.n_wfs;
     for (long u = (long)blockIdx.x * nw + warp; u < n_units; u += (long)gridDim.x * nw) {
-        const int item = (int)(u / g.n_wfs), w = (int)(u - (long)item * g.n_wfs);
-        int d, a;
-        decode_item(g, item, d, a);
+        // within each DM: the actuators on the small-subaperture sensors,
+        // then on the others (one kind of column per CTA, mostly)
+        int pos = 0;
+        while (pos + 1 < g.n_dm && u >= (long)g.order_start[pos + 1] * g.n_wfs) ++pos;
+        const int n_act = g.order_start[pos + 1] - g.order_start[pos];
+        const int na = g.n_wfs_a, nb = g.n_wfs - na;
+        long r = u - (long)g.order_start[pos] * g.n_wfs;
+        int a, w;
+        if (r < (long)n_act * na) {
+            a = (int)(r / na);
+            w = g.wfs_order[r - (long)a * na];
+        } else {
+            r -= (long)n_act * na;
+            a = (int)(r / nb);
+            w = g.wfs_order[na + (r - (long)a * nb)];
+        }
+        const int d = g.order_dm[pos];
         const DevPair &P = pairs[d * g.n_wfs + w];
         if (!P.im) continue;
         if (P.kf) warp_column_kf(g, pairs, d, a, w, wbuf, g.seg_floats, lane, err);
