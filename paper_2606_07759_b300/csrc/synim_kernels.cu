@@ -1129,12 +1129,15 @@ __device__ __forceinline__ void warp_column_kf(const Geo &g, const DevPair *__re
     float *X = wbuf;
     float *Y = X + (size_t)R * (nsj + 1) * 2;
     float *E = Y + (size_t)(R + 1) * nsj * 2;
-    // the boundary above the box
-    kf_pass(WF, P, s, ev, win, D.WpK, D.W, wx0, wy0, 1, s.si0, nsj, s.sj0, nsj, Y, rbuf, lane, err);
     for (int r0 = s.si0; r0 <= s.si1; r0 += R) {
         const int Rc = min(R, s.si1 - r0 + 1), nb = Rc * nsj;
         kf_pass(WF, P, s, ev, win, D.WpK, D.W, wx0, wy0, 0, r0, nsj + 1, s.sj0, Rc * (nsj + 1), X, rbuf, lane, err);
-        kf_pass(WF, P, s, ev, win, D.WpK, D.W, wx0, wy0, 1, r0 + 1, nsj, s.sj0, nb, Y + 2 * nsj, rbuf, lane, err);
+        // the y boundaries below the chunk's rows; the first chunk also takes
+        // the one above the box (later chunks carry it)
+        if (r0 == s.si0)
+            kf_pass(WF, P, s, ev, win, D.WpK, D.W, wx0, wy0, 1, r0, nsj, s.sj0, nb + nsj, Y, rbuf, lane, err);
+        else
+            kf_pass(WF, P, s, ev, win, D.WpK, D.W, wx0, wy0, 1, r0 + 1, nsj, s.sj0, nb, Y + 2 * nsj, rbuf, lane, err);
         // pupil-edge sums of the chunk's box subapertures that have edge
         // pixels: four at a time, eight lanes each (both axes from one
         // resample per pixel, fixed butterfly order within the group)
