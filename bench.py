@@ -37,17 +37,17 @@ from paper_2606_07759_b300 import workloads as W  # noqa: E402
 METRIC = "IM actuator-columns/s at <=1e-5 rel err vs FP64 oracle; % of HBM roofline"
 UNIT = "columns/s"
 
-# DRAM bytes (read + write) of one k_im launch on the full MCAO workload:
-# the ncu counters of the scale-0.6 launch (50.23 MB read + 129.34 MB
-# written, profiles/k_im_mcao_scale06_dram.md) times the ratio of the two
-# launches' algorithmic bytes (1507.1 / 233.3 MB).  Valid only for the kernel
-# source whose hash (kernel_sha1) is recorded with it.
-TRAFFIC = {"kernel_sha1": "99ca001009ae8da969c6dfcad131d8f8b3338aee",
-           "bytes_per_launch": (50.232832e6 + 129.341696e6) * 1507126080 / 233336784}
+# DRAM bytes (read + write) of one IM-kernel launch (k_imk) on the full MCAO
+# workload: the ncu counters of the scale-0.6 launch (105.14 MB read +
+# 133.93 MB written, profiles/k_imk_mcao_scale06_dram.md) times the ratio of
+# the two launches' algorithmic bytes (1507.1 / 233.3 MB).  Valid only for
+# the kernel source whose hash (kernel_sha1) is recorded with it.
+TRAFFIC = {"kernel_sha1": "b85a6631eed75fe7b94cc7d0f5a0e6e505d1948d",
+           "bytes_per_launch": (105.135104e6 + 133.932800e6) * 1507126080 / 233336784}
 
 
 def kernel_sha1() -> str:
-    """sha1 of the k_im source: synim_kernels.cu without its telescoping-sum section (another kernel)."""
+    """sha1 of the IM kernels' source: synim_kernels.cu without its telescoping-sum section (another kernel)."""
     with open(os.path.join(ROOT, "paper_2606_07759_b300", "csrc", "synim_kernels.cu"), "rb") as fh:
         text = fh.read()
     a = text.find(b"// The telescoping-sum engine (Sec. 2.2)")
