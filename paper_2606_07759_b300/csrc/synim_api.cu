@@ -708,8 +708,8 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
             if (H.k > KF_MAX_K || (long)H.n_sub * (H.n_sub + 1) > KPS || !c->geo.dm[d].winK) continue;
             const int p = d * n_wfs + w;
             e = dev_alloc(c, &c->k_org[p], (size_t)4 * KPS);
-            if (e == cudaSuccess) e = dev_alloc(c, &c->k_w[p], (size_t)2 * KTAPS * KPS);
-            if (e == cudaSuccess) e = dev_alloc(c, &c->k_wb[p], (size_t)2 * KTAPS * KPS);
+            if (e == cudaSuccess) e = dev_alloc(c, &c->k_w[p], (size_t)2 * KNC * KTAPS * KPS);
+            if (e == cudaSuccess) e = dev_alloc(c, &c->k_wb[p], (size_t)2 * KNC * KTAPS * KPS);
         }
     if (e == cudaSuccess) e = dev_alloc(c, &c->d_pairs, (size_t)np);
     if (e == cudaSuccess) e = dev_alloc(c, &c->d_err, 1);
@@ -894,18 +894,20 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
                 for (int q = 0; q < 4; ++q) P.dim[q] = dim ? dim[4 * p + q] : nullptr;
             }
             if (mode == MODE_VJP) P.gim = gim ? gim[p] : nullptr;
-            // forward IMs of the numerical engine: the boundary-segment weight boxes
-            if (mode == MODE_FWD && !tele && c->k_org[p]) {
+            // the numerical engine's boundary-segment weight boxes: values for
+            // forward IMs, values and tangents for the sensitivities and the adjoint
+            if (!tele && c->k_org[p]) {
                 const int s0 = kseg_shape(P.A, c->wh[w].k, 0), s1 = kseg_shape(P.A, c->wh[w].k, 1);
                 if (s0 >= 0 && s1 >= 0) {
                     P.kf = 1;
+                    P.kcomp = (mode == MODE_FWD) ? 1 : KNC;
                     P.kshape[0] = s0;
                     P.kshape[1] = s1;
                     for (int ax = 0; ax < 2; ++ax) {
                         P.korg[ax] = c->k_org[p] + (size_t)ax * KPS;
                         P.kring[ax] = c->k_org[p] + (size_t)(2 + ax) * KPS;
-                        P.kw[ax] = c->k_w[p] + (size_t)ax * KTAPS * KPS;
-                        P.kwb[ax] = c->k_wb[p] + (size_t)ax * KTAPS * KPS;
+                        P.kw[ax] = c->k_w[p] + (size_t)ax * KNC * KTAPS * KPS;
+                        P.kwb[ax] = c->k_wb[p] + (size_t)ax * KNC * KTAPS * KPS;
                     }
                 }
             }
@@ -921,13 +923,15 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
             need[p] = (seg_need(c->dmh[d], c->wh[w], P.Ai, NV) + 3) / 4 * 4;
             if (P.kf) {
                 // chunks of box rows (X, Y, E of the rows, the carried Y row and the
-                // ring buffer) in at most 768 floats, and at least four rows: small
-                // boxes take one chunk, large ones several, and the per-warp buffer
-                // stays small enough for the occupancy the registers allow
+                // ring buffer, NV values each) in at most 768 NV floats (forward) or
+                // 3072 (tangents), and at least four rows: small boxes take one
+                // chunk, large ones several, and the per-warp buffer stays small
+                // enough for the occupancy the registers allow
                 const long long nsj = (need[p] / (2 * NV) - 1) / 4;
-                const long long whole = 2 * ((nsj + 1) * (3 * nsj + 1) + nsj) + 64;
-                const long long four = 2 * (4 * (3 * nsj + 1) + nsj) + 64;
-                need[p] = std::max(need[p], (std::max(four, std::min(whole, 768LL)) + 3) / 4 * 4);
+                const long long whole = 2 * NV * ((nsj + 1) * (3 * nsj + 1) + nsj) + 64 * NV;
+                const long long four = 2 * NV * (4 * (3 * nsj + 1) + nsj) + 64 * NV;
+                const long long top = (NV == 1) ? 768 : 3072;
+                need[p] = std::max(need[p], (std::max(four, std::min(whole, top)) + 3) / 4 * 4);
                 max_seg = std::max(max_seg, c->wh[w].n_sub * (c->wh[w].n_sub + 1));
             }
         }
@@ -971,12 +975,17 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
         return cuda_fail(c, e, "kernel attributes");
     if (bps < 1) return fail(c, SYNIM_ERR_SHAPE, "IM kernel does not fit on an SM");
     int grid = grid_for(threads);
-    // forward IMs: k_im for the pairs without weight boxes, k_imk for those with them
-    bool any_plain = mode != MODE_FWD, any_k = false;
+    // k_im when no pair has weight boxes, else k_imk for every column
+    bool any_plain = false, any_k = false;
     for (int p = 0; p < np; ++p) {
-        if (mode == MODE_FWD && hp[p].im && !hp[p].kf) any_plain = true;
-        if (mode == MODE_FWD && hp[p].im && hp[p].kf) any_k = true;
+        const DevPair &P = hp[p];
+        const bool active = (mode == MODE_FWD) ? P.im != nullptr
+                            : (mode == MODE_TAN) ? (P.im || P.dim[0] || P.dim[1] || P.dim[2] || P.dim[3])
+                                                 : P.gim != nullptr;
+        if (active && !P.kf) any_plain = true;
+        if (active && P.kf) any_k = true;
     }
+    if (!any_plain && !any_k) any_plain = true;   // nothing to compute: the plain kernel's empty launch
     // one launch: k_imk takes every forward column when some pair has weight boxes
     auto grids = [&](int th, int &g0, int &g1) {
         g0 = (any_plain && !any_k) ? grid_for(th) : 0;
@@ -1045,7 +1054,7 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
         float best = 3e38f;
         int best_th = threads, best_l = 0;
         if ((e = launch_pst(g, c->d_pairs, c->max_mm, c->max_lines, s)) != cudaSuccess ||
-            (e = launch_kseg(g, c->d_pairs, max_seg, s)) != cudaSuccess)
+            (e = launch_kseg(g, c->d_pairs, max_seg, mode == MODE_FWD ? 1 : KNC, s)) != cudaSuccess)
             return cuda_fail(c, e, "autotune");
         for (int th : cand_threads)
             for (int l : cand_lanes) {
@@ -1113,7 +1122,7 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
             return r;
         }
         cudaError_t r = launch_pst(g, c->d_pairs, c->max_mm, c->max_lines, q);
-        if (r == cudaSuccess) r = launch_kseg(g, c->d_pairs, max_seg, q);
+        if (r == cudaSuccess) r = launch_kseg(g, c->d_pairs, max_seg, mode == MODE_FWD ? 1 : KNC, q);
         if (r == cudaSuccess && a0) r = cudaEventRecordWithFlags(a0, q, rf);
         int g0 = 0, g1 = 0;
         grids(threads, g0, g1);

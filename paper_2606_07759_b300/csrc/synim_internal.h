@@ -43,6 +43,7 @@ constexpr int KPAD = 9;
 constexpr int KBA_MAX = 10, KBC_MAX = 4, KTAPS = KBA_MAX * KBC_MAX;
 constexpr int KPS = 8192;    // plane stride (floats): n_sub (n_sub + 1) <= KPS
 constexpr int KF_MAX_K = 12; // largest subaperture side (pixels) given weight tables
+constexpr int KNC = 5;       // weight-box components: the value and its four misregistration tangents
 // segment flags (bits 24-31 of the origin word): no core sample in the box,
 // A and B differ (kwb holds B), resample pixel by pixel, ring pixels listed
 // in kring (repaired by the lane that takes the segment)
@@ -118,13 +119,15 @@ struct DevPair {
     // Boundary-segment weight boxes, per axis (0: x segments, index si (n_sub + 1) + b;
     // 1: y segments, index b n_sub + sj), rebuilt every call by k_kseg when kf != 0:
     // korg = box origin (gx, gy) in DM pixels as signed 12-bit fields (bits 0-11,
-    // 12-23) and the segment flags (bits 24-31); kw / kwb = [KTAPS][KPS] weights of
-    // the A / B sums (kwb only for KF_ASYM segments), tap (along a, across c) at
-    // a KBC_MAX + c; kshape = (ori << 8) | (BA << 4) | BC: box of BA x BC taps,
+    // 12-23) and the segment flags (bits 24-31); kw / kwb = [KNC][KTAPS][KPS] weights of
+    // the A / B sums (kwb only for KF_ASYM segments), component q (0 the value,
+    // 1..4 its tangents) and tap (along a, across c) at plane q KTAPS + a KBC_MAX
+    // + c; kshape = (ori << 8) | (BA << 4) | BC: box of BA x BC taps,
     // along the DM's y (ori 0) or x (ori 1) axis.
     // kring: bit 2 q + t set when line pixel t of pair q of the segment is a
     // ring pixel with a stencil bit (KF_RING segments only)
     int kf;
+    int kcomp;           // weight-box components built this call: 1 (values) or KNC (values and tangents)
     int kshape[2];
     int *korg[2], *kring[2];
     float *kw[2], *kwb[2];
@@ -183,8 +186,9 @@ cudaError_t launch_pack(const float *cube, int n_act, int N, const int *org, int
                         int stride, float *win, cudaStream_t s, int pad = 1);
 cudaError_t launch_mcls(const uint8_t *mask, int N, uint8_t *mcls, cudaStream_t s);
 cudaError_t launch_pst(const Geo &g, const DevPair *pairs, int max_mm, int max_lines, cudaStream_t s);
-// Boundary-segment weight boxes of the pairs with kf != 0 (after launch_pst).
-cudaError_t launch_kseg(const Geo &g, const DevPair *pairs, int max_seg, cudaStream_t s);
+// Boundary-segment weight boxes of the pairs with kf != 0 (after launch_pst),
+// ncomp components (1, or KNC with the tangents) in parallel.
+cudaError_t launch_kseg(const Geo &g, const DevPair *pairs, int max_seg, int ncomp, cudaStream_t s);
 // Box shape code of one axis for the composite A and subaperture side k, or -1.
 int kseg_shape(const double A[4], int k, int axis);
 // dynamic shared memory of the IM kernels: one seg_floats buffer per warp
@@ -192,8 +196,8 @@ size_t im_smem_bytes(const Geo &g, int threads);
 cudaError_t im_prepare(int mode, int threads, size_t smem, int *blocks_per_sm);
 // gp: MODE_VJP only, the per-column partials [n_items * n_wfs][4] that
 // launch_vjp_reduce sums per pair into grad_p [n_pairs][4].
-// MODE_FWD: k_im (grid CTAs, none if 0) when no pair has weight boxes, else
-// k_imk over every column (kgrid CTAs).
+// k_im<mode> (grid CTAs, none if 0) when no pair has weight boxes, else
+// k_imk<mode> over every column (kgrid CTAs).
 cudaError_t launch_im(int mode, const Geo &g, const DevPair *pairs, int *err, double *gp, int grid, int threads,
                       size_t smem, cudaStream_t s, int kgrid = 0);
 cudaError_t launch_vjp_reduce(const Geo &g, const double *part, double *gp, cudaStream_t s);
@@ -268,7 +272,7 @@ struct synim_ctx {
     uint8_t *d_pst = nullptr, *d_lines = nullptr;
     // boundary-segment weight boxes per pair (nullptr where the sensor's
     // subapertures are too large for them): origins and ring lists [2][2][KPS], weights
-    // [2][KTAPS][KPS] for A and for B
+    // [2][KNC][KTAPS][KPS] for A and for B
     int *k_org[SYNIM_MAX_PAIRS] = {};
     float *k_w[SYNIM_MAX_PAIRS] = {}, *k_wb[SYNIM_MAX_PAIRS] = {};
     int max_mm = 0, max_lines = 0;

@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(128) k_kseg(const __grid_constant__ Geo g, con
     __shared__ float acc[128][2 * KTAPS + 1];
     const int p = blockIdx.y;
     const DevPair &P = pairs[p];
-    if (!P.kf) return;
+    if (!P.kf || (int)blockIdx.z >= P.kcomp) return;
     const DevWFS &WF = g.wfs[p % g.n_wfs];
     const int n = WF.n_sub, n1 = n + 1, k = WF.k;
     const int nseg = n * n1;
@@ -419,11 +419,24 @@ __global__ void __launch_bounds__(128) k_kseg(const __grid_constant__ Geo g, con
     if (!any) flags |= KF_NOCORE;
     if (ring && !(flags & KF_FALLBACK)) {
         flags |= KF_RING;
-        P.kring[ax][sid] = ring;
+        if (blockIdx.z == 0) P.kring[ax][sid] = ring;
     }
     if (!(flags & (KF_FALLBACK | KF_NOCORE))) {
         if (asym) flags |= KF_ASYM;
         float *wa = acc[threadIdx.x], *wb = wa + KTAPS;
+        // component 0: the resampled value; 1..4 (P.kcomp = 5): its
+        // derivatives with respect to p_k through the sample position, the
+        // pixel classes held fixed (d phi = gx dx_k + gy dy_k, with gx, gy the
+        // bilinear cell's differences and (dx_k, dy_k) = d(A, b)/dp_k (j, i))
+        {
+        const int comp = blockIdx.z;   // one component per thread (grid z)
+        float dA[4] = {0.f, 0.f, 0.f, 0.f}, db[2] = {0.f, 0.f};
+        if (comp > 0)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                dA[e] = (float)P.dA[4 * (comp - 1) + e];
+                if (e < 2) db[e] = (float)P.db[2 * (comp - 1) + e];
+            }
         for (int q = 0; q < 2 * KTAPS; ++q) wa[q] = 0.f;
 #pragma unroll
         for (int q = 0; q < KF_MAX_K; ++q) {
@@ -440,7 +453,17 @@ __global__ void __launch_bounds__(128) k_kseg(const __grid_constant__ Geo g, con
                 const float fx0 = floorf(xl), fy0 = floorf(yl);
                 const int cx = (int)fx0 - cx0, cy = (int)fy0 - cy0;
                 const float fx = xl - fx0, fy = yl - fy0, hx = 1.f - fx, hy = 1.f - fy;
-                const float wq[4] = {hx * hy, fx * hy, hx * fy, fx * fy};
+                float wq[4];
+                if (comp == 0) {
+                    wq[0] = hx * hy; wq[1] = fx * hy; wq[2] = hx * fy; wq[3] = fx * fy;
+                } else {
+                    const float dx = fmaf(dA[0], (float)j, fmaf(dA[1], (float)i, db[0]));
+                    const float dy = fmaf(dA[2], (float)j, fmaf(dA[3], (float)i, db[1]));
+                    wq[0] = -hy * dx - hx * dy;
+                    wq[1] = hy * dx - fx * dy;
+                    wq[2] = -fy * dx + hx * dy;
+                    wq[3] = fy * dx + fx * dy;
+                }
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const int tx = cx + (e & 1), ty = cy + (e >> 1);
@@ -450,17 +473,18 @@ __global__ void __launch_bounds__(128) k_kseg(const __grid_constant__ Geo g, con
                 }
             }
         }
-        float *ka = P.kw[ax] + sid, *kb = P.kwb[ax] + sid;
+        float *ka = P.kw[ax] + sid + (long)comp * KTAPS * KPS, *kb = P.kwb[ax] + sid + (long)comp * KTAPS * KPS;
         for (int q = 0; q < KTAPS; ++q) ka[(long)q * KPS] = wa[q];
         if (asym)
             for (int q = 0; q < KTAPS; ++q) kb[(long)q * KPS] = wb[q];
+        }
     }
-    P.korg[ax][sid] = (gx & 0xfff) | ((gy & 0xfff) << 12) | (flags << 24);
+    if (blockIdx.z == 0) P.korg[ax][sid] = (gx & 0xfff) | ((gy & 0xfff) << 12) | (flags << 24);
 }
 
-cudaError_t launch_kseg(const Geo &g, const DevPair *pairs, int max_seg, cudaStream_t s) {
+cudaError_t launch_kseg(const Geo &g, const DevPair *pairs, int max_seg, int ncomp, cudaStream_t s) {
     if (max_seg <= 0) return cudaSuccess;
-    dim3 grid((2 * max_seg + 127) / 128, g.n_dm * g.n_wfs);
+    dim3 grid((2 * max_seg + 127) / 128, g.n_dm * g.n_wfs, ncomp);
     k_kseg<<<grid, 128, 0, s>>>(g, pairs);
     return cudaGetLastError();
 }
@@ -901,7 +925,7 @@ __device__ __forceinline__ void warp_segments(const DevWFS &WF, const ItemWfs &s
 }
 
 // ---------------------------------------------------------------------------
-// IM columns from the boundary-segment weight boxes (forward IMs)
+// IM columns from the boundary-segment weight boxes
 // ---------------------------------------------------------------------------
 // t / n for 0 <= t < 2^20 and 0 < n, from inv = 1 / n (one correction step).
 __device__ __forceinline__ int fast_div(int t, float inv, int n) {
@@ -911,12 +935,18 @@ __device__ __forceinline__ int fast_div(int t, float inv, int n) {
     return q;
 }
 
-// A = sum over the box of kw[tap] * window, B likewise with kwb (TWO) or A.
-// wb: the window at the box origin; ka / kb: tap 0 of the segment's planes.
-template <int BA, int BC, int ORI, bool TWO>
+// NC components per segment: the value (q = 0) and, for tangents, its
+// derivatives with respect to the four misregistration parameters (q = 1..4),
+// each with its own weight planes starting at plane q KTAPS.
+// A[q] = sum over the box of kw[q][tap] * window, B[q] likewise with kwb
+// (TWO) or A[q].  wb: the window at the box origin; ka / kb: tap 0 of the
+// segment's planes.
+template <int BA, int BC, int ORI, bool TWO, int NC>
 __device__ __forceinline__ void kf_dot(const float *__restrict__ wb, int Wp, const float *__restrict__ ka,
-                                       const float *__restrict__ kb, float &A, float &B) {
-    float sa = 0.f, sb = 0.f;
+                                       const float *__restrict__ kb, float *A, float *B) {
+    float sa[NC], sb[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) sa[q] = sb[q] = 0.f;
     if constexpr (ORI == 0) {   // along the window's rows (stride Wp), across its columns
 #pragma unroll
         for (int a = 0; a < BA; ++a) {
@@ -924,8 +954,12 @@ __device__ __forceinline__ void kf_dot(const float *__restrict__ wb, int Wp, con
 #pragma unroll
             for (int c = 0; c < BC; ++c) {
                 const float v = __ldg(wr + c);
-                sa = fmaf(__ldg(ka + (a * KBC_MAX + c) * KPS), v, sa);
-                if (TWO) sb = fmaf(__ldg(kb + (a * KBC_MAX + c) * KPS), v, sb);
+#pragma unroll
+                for (int q = 0; q < NC; ++q) {
+                    const long off = (long)(q * KTAPS + a * KBC_MAX + c) * KPS;
+                    sa[q] = fmaf(__ldg(ka + off), v, sa[q]);
+                    if (TWO) sb[q] = fmaf(__ldg(kb + off), v, sb[q]);
+                }
             }
         }
     } else {                    // along the window's columns, across its rows
@@ -935,32 +969,41 @@ __device__ __forceinline__ void kf_dot(const float *__restrict__ wb, int Wp, con
 #pragma unroll
             for (int a = 0; a < BA; ++a) {
                 const float v = __ldg(wr + a);
-                sa = fmaf(__ldg(ka + (a * KBC_MAX + c) * KPS), v, sa);
-                if (TWO) sb = fmaf(__ldg(kb + (a * KBC_MAX + c) * KPS), v, sb);
+#pragma unroll
+                for (int q = 0; q < NC; ++q) {
+                    const long off = (long)(q * KTAPS + a * KBC_MAX + c) * KPS;
+                    sa[q] = fmaf(__ldg(ka + off), v, sa[q]);
+                    if (TWO) sb[q] = fmaf(__ldg(kb + off), v, sb[q]);
+                }
             }
         }
     }
-    A = sa;
-    B = TWO ? sb : sa;
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+        A[q] = sa[q];
+        B[q] = TWO ? sb[q] : sa[q];
+    }
 }
 
-template <int ORI, bool TWO>
+template <int ORI, bool TWO, int NC>
 __device__ __forceinline__ void kf_dot_ba(int BA, int BC, const float *wb, int Wp, const float *ka,
-                                          const float *kb, float &A, float &B) {
+                                          const float *kb, float *A, float *B) {
 #define SYNIM_KF(ba, bc) \
-    if (BA == ba && BC == bc) { kf_dot<ba, bc, ORI, TWO>(wb, Wp, ka, kb, A, B); return; }
+    if (BA == ba && BC == bc) { kf_dot<ba, bc, ORI, TWO, NC>(wb, Wp, ka, kb, A, B); return; }
     SYNIM_KF(9, 3) SYNIM_KF(8, 3) SYNIM_KF(10, 3) SYNIM_KF(6, 3) SYNIM_KF(4, 3)
     SYNIM_KF(9, 4) SYNIM_KF(8, 4) SYNIM_KF(10, 4) SYNIM_KF(6, 4) SYNIM_KF(4, 4)
 #undef SYNIM_KF
-    A = B = 0.f;
+#pragma unroll
+    for (int q = 0; q < NC; ++q) A[q] = B[q] = 0.f;
 }
 
 // One pass over cnt segments of axis ax: t = r ncol + c is x segment
 // (row0 + r, boundary col0 + c) or y segment (boundary row0 + r, column col0
-// + c); out[2 t], out[2 t + 1] = A, B.  Lanes take one segment each; flagged
-// segments are resampled pixel by pixel afterwards by the whole warp.  rbuf:
-// 64 floats of the warp's buffer for the ring pixels.
-__device__ void kf_pass(const DevWFS &WF, const DevPair &P, const ItemWfs &s, const Eval<1> &ev,
+// + c); out[2 NC t + q] = A[q], out[2 NC t + NC + q] = B[q].  Lanes take one
+// segment each; flagged segments are resampled pixel by pixel afterwards by
+// the whole warp.  rbuf: 64 NC floats of the warp's buffer for the ring pixels.
+template <int NC>
+__device__ void kf_pass(const DevWFS &WF, const DevPair &P, const ItemWfs &s, const Eval<NC> &ev,
                         const float *__restrict__ win, int Wp, int W, int wx0, int wy0, int ax, int row0,
                         int ncol, int col0, int cnt, float *out, float *rbuf, int lane, int *err) {
     const int n = WF.n_sub, n1 = n + 1;
@@ -995,16 +1038,20 @@ __device__ void kf_pass(const DevWFS &WF, const DevPair &P, const ItemWfs &s, co
             }
         }
         const bool two = __any_sync(0xffffffffu, act && (fl & KF_ASYM));
-        float A = 0.f, B = 0.f;
+        float A[NC], B[NC];
+#pragma unroll
+        for (int q = 0; q < NC; ++q) A[q] = B[q] = 0.f;
         if (act) {
             if (ori == 0) {
-                if (two) kf_dot_ba<0, true>(BA, BC, wb, Wp, kwa + sid, kwb + sid, A, B);
-                else kf_dot_ba<0, false>(BA, BC, wb, Wp, kwa + sid, kwb + sid, A, B);
+                if (two) kf_dot_ba<0, true, NC>(BA, BC, wb, Wp, kwa + sid, kwb + sid, A, B);
+                else kf_dot_ba<0, false, NC>(BA, BC, wb, Wp, kwa + sid, kwb + sid, A, B);
             } else {
-                if (two) kf_dot_ba<1, true>(BA, BC, wb, Wp, kwa + sid, kwb + sid, A, B);
-                else kf_dot_ba<1, false>(BA, BC, wb, Wp, kwa + sid, kwb + sid, A, B);
+                if (two) kf_dot_ba<1, true, NC>(BA, BC, wb, Wp, kwa + sid, kwb + sid, A, B);
+                else kf_dot_ba<1, false, NC>(BA, BC, wb, Wp, kwa + sid, kwb + sid, A, B);
             }
-            if (!(fl & KF_ASYM)) B = A;   // kwb holds only the asymmetric segments' weights
+            if (!(fl & KF_ASYM))   // kwb holds only the asymmetric segments' weights
+#pragma unroll
+                for (int q = 0; q < NC; ++q) B[q] = A[q];
         }
         // ring pixels of the pass's segments (Sec. 2.3 step 3) with their
         // stencil bits, spread over the lanes: the j-th one is repaired by lane
@@ -1026,7 +1073,10 @@ __device__ void kf_pass(const DevWFS &WF, const DevPair &P, const ItemWfs &s, co
             for (int st = 16; st > 0; st >>= 1)
                 if (__shfl_sync(0xffffffffu, excl, own + st) <= j) own += st;
             const int orm = __shfl_sync(0xffffffffu, rm, own), oex = __shfl_sync(0xffffffffu, excl, own);
-            float va = 0.f, vb = 0.f;
+            float v[NC];
+            bool ba = false, bb = false;
+#pragma unroll
+            for (int q = 0; q < NC; ++q) v[q] = 0.f;
             if (j < total) {
                 int mm = orm;
                 for (int q = j - oex; q > 0; --q) mm &= mm - 1;
@@ -1035,88 +1085,117 @@ __device__ void kf_pass(const DevWFS &WF, const DevPair &P, const ItemWfs &s, co
                 const int sq = ax ? col0 + c : row0 + r, b = ax ? row0 + r : col0 + c;
                 const int u0 = sq * WF.k, l0 = b * WF.k - 1;
                 const int cb = __ldg((ax ? P.ycc : P.xcc) + b + (long)(u0 + q) * n1);
-                float v[1];
                 ev.ring(ax ? l0 + tt : u0 + q, ax ? u0 + q : l0 + tt, v);
-                va = (cb & (tt ? 4 : 1)) ? v[0] : 0.f;
-                vb = (cb & (tt ? 8 : 2)) ? v[0] : 0.f;
+                ba = (cb & (tt ? 4 : 1)) != 0;
+                bb = (cb & (tt ? 8 : 2)) != 0;
             }
-            rbuf[2 * lane] = va;
-            rbuf[2 * lane + 1] = vb;
+#pragma unroll
+            for (int q = 0; q < NC; ++q) {
+                rbuf[2 * NC * lane + q] = ba ? v[q] : 0.f;
+                rbuf[2 * NC * lane + NC + q] = bb ? v[q] : 0.f;
+            }
             __syncwarp();
             const int q1 = min(excl + nr, j0 + 32);
-            for (int q = max(excl, j0); q < q1; ++q) {
-                A += rbuf[2 * (q - j0)];
-                B += rbuf[2 * (q - j0) + 1];
-            }
+            for (int qq = max(excl, j0); qq < q1; ++qq)
+#pragma unroll
+                for (int q = 0; q < NC; ++q) {
+                    A[q] += rbuf[2 * NC * (qq - j0) + q];
+                    B[q] += rbuf[2 * NC * (qq - j0) + NC + q];
+                }
             __syncwarp();
         }
         }
-        if (t < cnt && !fb) {
-            out[2 * t] = A;
-            out[2 * t + 1] = B;
-        }
+        if (t < cnt && !fb)
+#pragma unroll
+            for (int q = 0; q < NC; ++q) {
+                out[2 * NC * t + q] = A[q];
+                out[2 * NC * t + NC + q] = B[q];
+            }
         unsigned m = __ballot_sync(0xffffffffu, fb);
         while (m) {
             const int tt = base + __ffs(m) - 1;
             m &= m - 1;
             const int r = fast_div(tt, inv, ncol), c = tt - r * ncol;
             const SegRows sr = ax ? seg_rows(WF, s, 1, row0 + r, col0 + c) : seg_rows(WF, s, 0, col0 + c, row0 + r);
-            float fa[1] = {0.f}, fbv[1] = {0.f};
-            seg_compute<1>(WF, sr, ev, ax, lane, 32, fa, fbv);
+            float fa[NC], fbv[NC];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                fa[0] += __shfl_xor_sync(0xffffffffu, fa[0], o);
-                fbv[0] += __shfl_xor_sync(0xffffffffu, fbv[0], o);
-            }
-            if (lane == 0) {
-                out[2 * tt] = fa[0];
-                out[2 * tt + 1] = fbv[0];
-            }
+            for (int q = 0; q < NC; ++q) fa[q] = fbv[q] = 0.f;
+            seg_compute<NC>(WF, sr, ev, ax, lane, 32, fa, fbv);
+#pragma unroll
+            for (int q = 0; q < NC; ++q)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    fa[q] += __shfl_xor_sync(0xffffffffu, fa[q], o);
+                    fbv[q] += __shfl_xor_sync(0xffffffffu, fbv[q], o);
+                }
+            if (lane == 0)
+#pragma unroll
+                for (int q = 0; q < NC; ++q) {
+                    out[2 * NC * tt + q] = fa[q];
+                    out[2 * NC * tt + NC + q] = fbv[q];
+                }
         }
     }
 }
 
-// One forward IM column from the weight boxes.  The same column as
-// warp_column: zeros outside the rows of the subaperture box; then, in
+// One IM column from the weight boxes (forward: the IM; tangents: the IM and
+// its four derivatives; adjoint: the cotangent dot products).  The same column
+// as warp_column: zeros outside the rows of the subaperture box; then, in
 // chunks of R box rows, every x segment of the chunk's rows and every y
 // segment of the boundaries below them (the boundary above carried), the
 // pupil-edge sums of the chunk's box subapertures, and one in-order pass over
 // the chunk's valid rows (slopes in the box, zeros elsewhere).  Buffer
-// (floats): X [R][nsj + 1][2], Y [R + 1][nsj][2], E [R][nsj][2].
+// (floats, NC components per value): X [R][nsj + 1][2][NC], Y [R + 1][nsj][2][NC],
+// E [R][nsj][2][NC], then 64 NC for the ring pixels.
+template <int MODE>
 __device__ __forceinline__ void warp_column_kf(const Geo &g, const DevPair *__restrict__ pairs, int d, int a,
-                                               int w, float *wbuf, int cap, int lane, int *err) {
+                                               int w, float *wbuf, int cap, int lane, int *err, double *gp,
+                                               long unit) {
+    constexpr int NC = (MODE == MODE_FWD) ? 1 : 5;
+    constexpr int NOUT = (MODE == MODE_FWD) ? 1 : (MODE == MODE_TAN ? 5 : 0);
+    constexpr int S = 2 * NC;   // floats per segment or subaperture sum
     const DevPair &P = pairs[d * g.n_wfs + w];
     const DevWFS &WF = g.wfs[w];
     const DevDM &D = g.dm[d];
     __shared__ ItemWfs s_item[8];
     ItemWfs &s = s_item[threadIdx.x >> 5];
     __syncwarp();
-    make_info<MODE_FWD, 1>(g, pairs, d, a, w, s, err, KPAD);
+    make_info<MODE, NC>(g, pairs, d, a, w, s, err, KPAD);
     __syncwarp();
     const int nv = WF.nv, n2 = 2 * nv;
     const int nsj = s.empty ? 0 : s.nsj;
     // at least one box row: X, two Y rows and E, and the ring buffer
-    if (!s.empty && 2 * (4 * nsj + 1) + 64 > cap) {
+    if (!s.empty && S * (4 * nsj + 1) + 64 * NC > cap) {
         if (lane == 0) atomicOr(err, ERR_ARENA);
         s.empty = 1;
     }
     if (!s.empty && !SYNIM_IDX_OK(s.si0 >= 0 && s.si1 < WF.n_sub && s.sj0 >= 0 && s.sj1 < WF.n_sub, err)) return;
     const int vr0 = s.empty ? 0 : WF.vrow[s.si0], vr1 = s.empty ? 0 : WF.vrow[s.si1 + 1];
     if (!SYNIM_IDX_OK(0 <= vr0 && vr0 <= vr1 && vr1 <= nv, err)) return;
-    float *col = P.im + (size_t)a * n2;
-    if (P.vec4) {
-        bulk_zero(col, 0, vr0, lane);
-        bulk_zero(col, vr1, nv + vr0, lane);
-        bulk_zero(col, nv + vr1, n2, lane);
-    } else {
-        zero_rows(col, 0, vr0, false, lane);
-        zero_rows(col, vr1, nv + vr0, false, lane);
-        zero_rows(col, nv + vr1, n2, false, lane);
+    float *cols[NOUT > 0 ? NOUT : 1];
+    if constexpr (MODE != MODE_VJP) {
+#pragma unroll
+        for (int o = 0; o < NOUT; ++o) {
+            float *base = (o == 0) ? P.im : P.dim[o - 1];
+            cols[o] = base ? base + (size_t)a * n2 : nullptr;
+            if (!cols[o]) continue;
+            if (P.vec4) {
+                bulk_zero(cols[o], 0, vr0, lane);
+                bulk_zero(cols[o], vr1, nv + vr0, lane);
+                bulk_zero(cols[o], nv + vr1, n2, lane);
+            } else {
+                zero_rows(cols[o], 0, vr0, false, lane);
+                zero_rows(cols[o], vr1, nv + vr0, false, lane);
+                zero_rows(cols[o], nv + vr1, n2, false, lane);
+            }
+        }
     }
-    if (s.empty) return;
+    float gacc[4] = {0.f, 0.f, 0.f, 0.f};
+    const float *G = (MODE == MODE_VJP) ? P.gim + (size_t)a * n2 : nullptr;
+    if (!s.empty) {
     const float *win = D.winK + (size_t)a * D.strideK;
     const int wx0 = D.org[2 * a], wy0 = D.org[2 * a + 1];
-    Eval<1> ev;
+    Eval<NC> ev;
     ev.load(s, win, D.WpK, D.W, WF.M, KPAD);
 #ifdef SYNIM_DEBUG_BOUNDS
     ev.err = err;
@@ -1124,20 +1203,22 @@ __device__ __forceinline__ void warp_column_kf(const Geo &g, const DevPair *__re
 #endif
     const int nrows = s.si1 - s.si0 + 1;
     // chunk rows: X, Y and E of R rows plus the carried Y row
-    const int R = max(1, min(nrows, ((cap - 64) / 2 - nsj) / (3 * nsj + 1)));
-    float *rbuf = wbuf + cap - 64;
+    const int R = max(1, min(nrows, ((cap - 64 * NC) / S - nsj) / (3 * nsj + 1)));
+    float *rbuf = wbuf + cap - 64 * NC;
     float *X = wbuf;
-    float *Y = X + (size_t)R * (nsj + 1) * 2;
-    float *E = Y + (size_t)(R + 1) * nsj * 2;
+    float *Y = X + (size_t)R * (nsj + 1) * S;
+    float *E = Y + (size_t)(R + 1) * nsj * S;
     for (int r0 = s.si0; r0 <= s.si1; r0 += R) {
         const int Rc = min(R, s.si1 - r0 + 1), nb = Rc * nsj;
-        kf_pass(WF, P, s, ev, win, D.WpK, D.W, wx0, wy0, 0, r0, nsj + 1, s.sj0, Rc * (nsj + 1), X, rbuf, lane, err);
+        kf_pass<NC>(WF, P, s, ev, win, D.WpK, D.W, wx0, wy0, 0, r0, nsj + 1, s.sj0, Rc * (nsj + 1), X, rbuf, lane,
+                    err);
         // the y boundaries below the chunk's rows; the first chunk also takes
         // the one above the box (later chunks carry it)
         if (r0 == s.si0)
-            kf_pass(WF, P, s, ev, win, D.WpK, D.W, wx0, wy0, 1, r0, nsj, s.sj0, nb + nsj, Y, rbuf, lane, err);
+            kf_pass<NC>(WF, P, s, ev, win, D.WpK, D.W, wx0, wy0, 1, r0, nsj, s.sj0, nb + nsj, Y, rbuf, lane, err);
         else
-            kf_pass(WF, P, s, ev, win, D.WpK, D.W, wx0, wy0, 1, r0 + 1, nsj, s.sj0, nb, Y + 2 * nsj, rbuf, lane, err);
+            kf_pass<NC>(WF, P, s, ev, win, D.WpK, D.W, wx0, wy0, 1, r0 + 1, nsj, s.sj0, nb, Y + (size_t)nsj * S, rbuf,
+                        lane, err);
         // pupil-edge sums of the chunk's box subapertures that have edge
         // pixels: four at a time, eight lanes each (both axes from one
         // resample per pixel, fixed butterfly order within the group)
@@ -1149,10 +1230,9 @@ __device__ __forceinline__ void warp_column_kf(const Geo &g, const DevPair *__re
                 const int q = fast_div(t, inv_nsj, nsj), c = t - q * nsj;
                 const int qq = (r0 + q) * WF.n_sub + s.sj0 + c;
                 has = WF.irr_sub[qq + 1] > WF.irr_sub[qq];
-                if (!has) {
-                    E[2 * t] = 0.f;
-                    E[2 * t + 1] = 0.f;
-                }
+                if (!has)
+#pragma unroll
+                    for (int v = 0; v < S; ++v) E[(size_t)S * t + v] = 0.f;
             }
             unsigned m = __ballot_sync(0xffffffffu, has);
             const int grp = lane >> 3, gl = lane & 7;
@@ -1162,48 +1242,88 @@ __device__ __forceinline__ void warp_column_kf(const Geo &g, const DevPair *__re
                 for (int g2 = 0; g2 < grp && mm; ++g2) mm &= mm - 1;
                 for (int g2 = 0; g2 < 4 && m; ++g2) m &= m - 1;
                 const int tt = mm ? t0 + __ffs(mm) - 1 : -1;
-                float ax_[1] = {0.f}, ay_[1] = {0.f};
+                float ax_[NC], ay_[NC];
+#pragma unroll
+                for (int v = 0; v < NC; ++v) ax_[v] = ay_[v] = 0.f;
                 if (tt >= 0) {
                     const int q = fast_div(tt, inv_nsj, nsj), c = tt - q * nsj;
-                    edge_sum<1>(WF, s, ev, r0 + q, s.sj0 + c, gl, 8, ax_, ay_);
+                    edge_sum<NC>(WF, s, ev, r0 + q, s.sj0 + c, gl, 8, ax_, ay_);
                 }
 #pragma unroll
-                for (int o = 4; o > 0; o >>= 1) {
-                    ax_[0] += __shfl_xor_sync(0xffffffffu, ax_[0], o);
-                    ay_[0] += __shfl_xor_sync(0xffffffffu, ay_[0], o);
-                }
-                if (gl == 0 && tt >= 0) {
-                    E[2 * tt] = ax_[0];
-                    E[2 * tt + 1] = ay_[0];
-                }
+                for (int v = 0; v < NC; ++v)
+#pragma unroll
+                    for (int o = 4; o > 0; o >>= 1) {
+                        ax_[v] += __shfl_xor_sync(0xffffffffu, ax_[v], o);
+                        ay_[v] += __shfl_xor_sync(0xffffffffu, ay_[v], o);
+                    }
+                if (gl == 0 && tt >= 0)
+#pragma unroll
+                    for (int v = 0; v < NC; ++v) {
+                        E[(size_t)S * tt + v] = ax_[v];
+                        E[(size_t)S * tt + NC + v] = ay_[v];
+                    }
             }
         }
         __syncwarp();
         // every valid row of the chunk's subaperture rows, in order: the
         // slope of a box subaperture (segment differences plus pupil-edge
-        // sums, times slope_scale / (2 dw lit)), zero for the others
+        // sums, times slope_scale / (2 dw lit)), zero for the others; or the
+        // adjoint's dot products of the tangents with the cotangent
         const int ra = WF.vrow[r0], rb = WF.vrow[r0 + Rc];
         if (!SYNIM_IDX_OK(0 <= ra && ra <= rb && rb <= nv, err)) return;
 #pragma unroll 2
         for (int r = ra + lane; r < rb; r += 32) {
             const int vs = __ldg(WF.vsub + r);
             const int q = (vs >> 16) - r0, c = (vs & 0xffff) - s.sj0;
-            float vx = 0.f, vy = 0.f;
-            if (c >= 0 && c < nsj) {
+            float vx[NC], vy[NC];
+#pragma unroll
+            for (int v = 0; v < NC; ++v) vx[v] = vy[v] = 0.f;
+            const bool inbox = c >= 0 && c < nsj;
+            if (inbox) {
                 const float f = __ldg(WF.fac + r);
-                const float *segx = X + (size_t)q * (nsj + 1) * 2;
-                const float *sy0 = Y + (size_t)q * nsj * 2, *sy1 = sy0 + 2 * nsj;
-                const float *eq = E + (size_t)q * nsj * 2;
-                vx = (segx[2 * (c + 1)] - segx[2 * c + 1] + eq[2 * c]) * f;
-                vy = (sy1[2 * c] - sy0[2 * c + 1] + eq[2 * c + 1]) * f;
+                const float *segx = X + ((size_t)q * (nsj + 1) + c) * S;
+                const float *sy0 = Y + ((size_t)q * nsj + c) * S, *sy1 = sy0 + (size_t)nsj * S;
+                const float *eq = E + ((size_t)q * nsj + c) * S;
+#pragma unroll
+                for (int v = 0; v < NC; ++v) {
+                    vx[v] = (segx[S + v] - segx[NC + v] + eq[v]) * f;
+                    vy[v] = (sy1[v] - sy0[NC + v] + eq[NC + v]) * f;
+                }
             }
-            col[r] = vx;
-            col[nv + r] = vy;
+            if constexpr (MODE == MODE_VJP) {
+                if (inbox) {
+                    const float gx = G[r], gy = G[nv + r];
+#pragma unroll
+                    for (int k2 = 0; k2 < 4; ++k2) gacc[k2] = fmaf(gx, vx[1 + k2], fmaf(gy, vy[1 + k2], gacc[k2]));
+                }
+            } else {
+#pragma unroll
+                for (int o = 0; o < NOUT; ++o)
+                    if (cols[o]) {
+                        cols[o][r] = vx[o];
+                        cols[o][nv + r] = vy[o];
+                    }
+            }
         }
         __syncwarp();
         // carry the last boundary row of the chunk
-        for (int c = lane; c < 2 * nsj; c += 32) Y[c] = Y[(size_t)Rc * nsj * 2 + c];
+        for (int c = lane; c < nsj * S; c += 32) Y[c] = Y[(size_t)Rc * nsj * S + c];
         __syncwarp();
+    }
+    }
+    if constexpr (MODE == MODE_VJP) {
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) {
+            float vsum = gacc[k2];
+            for (int o = 16; o > 0; o >>= 1) vsum += __shfl_xor_sync(0xffffffffu, vsum, o);
+            // this column's own slot: summed per pair in a fixed order by
+            // k_vjp_reduce, so the result is reproducible
+            if (lane == 0) gp[4 * unit + k2] = (double)vsum;
+        }
+    } else {
+        (void)gp;
+        (void)unit;
+        (void)G;
     }
 }
 
@@ -1217,7 +1337,7 @@ __device__ __forceinline__ void warp_column(const Geo &g, const DevPair *__restr
     const int pidx = d * g.n_wfs + w;
     const DevPair &P = pairs[pidx];
     if (!pair_active<MODE>(P)) return;
-    if (MODE == MODE_FWD && P.kf) {   // a weight-box column: k_imk's
+    if (P.kf) {   // a weight-box column: k_imk's
         if (lane == 0) atomicOr(err, ERR_ARENA);
         return;
     }
@@ -1578,21 +1698,27 @@ k_tele(const __grid_constant__ Geo g, const __grid_constant__ TeleSet t, const D
     if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 
-// Forward IM columns when some pair has boundary-segment weight boxes: one
-// warp per column as in k_im, the weight boxes for those pairs (kf) and
-// k_im's per-sample path for the others, all in one launch.
-__global__ void __launch_bounds__(256, 3)
-k_imk(const __grid_constant__ Geo g, const DevPair *__restrict__ pairs, int *__restrict__ err) {
+// Every IM column of a mode when some pair has boundary-segment weight boxes:
+// one warp per column as in k_im, the weight boxes for those pairs (kf) and
+// k_im's per-sample path for the others, all in one launch.  Within each DM
+// the actuators' columns on the sensors with subapertures of at most 32
+// pixels come first, then those on the others, so that a CTA's warps take
+// one kind of column (and no warp idles behind a costlier neighbour).
+template <int MODE>
+__global__ void __launch_bounds__(256, (MODE == MODE_FWD) ? 3 : 2)
+k_imk(const __grid_constant__ Geo g, const DevPair *__restrict__ pairs, int *__restrict__ err,
+      double *__restrict__ gp) {
+    constexpr int NV = (MODE == MODE_FWD) ? 1 : 5;
     extern __shared__ __align__(16) float smem_f[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     float *wbuf = smem_f + (size_t)warp * g.seg_floats;
-    for (int q = threadIdx.x; q < kZeroFloats / 4; q += blockDim.x) s_zero[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic zeros -> bulk-copy reads
-    __syncthreads();
+    if constexpr (MODE != MODE_VJP) {
+        for (int q = threadIdx.x; q < kZeroFloats / 4; q += blockDim.x) s_zero[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic zeros -> bulk-copy reads
+        __syncthreads();
+    }
     const long n_units = (long)g.n_items * g.n_wfs;
     for (long u = (long)blockIdx.x * nw + warp; u < n_units; u += (long)gridDim.x * nw) {
-        // within each DM: the actuators on the small-subaperture sensors,
-        // then on the others (one kind of column per CTA, mostly)
         int pos = 0;
         while (pos + 1 < g.n_dm && u >= (long)g.order_start[pos + 1] * g.n_wfs) ++pos;
         const int n_act = g.order_start[pos + 1] - g.order_start[pos];
@@ -1608,12 +1734,15 @@ k_imk(const __grid_constant__ Geo g, const DevPair *__restrict__ pairs, int *__r
             w = g.wfs_order[na + (r - (long)a * nb)];
         }
         const int d = g.order_dm[pos];
+        // the adjoint's partials are indexed by the natural column order
+        const long unit = (long)(g.order_start[pos] + a) * g.n_wfs + w;
+        if (MODE == MODE_VJP && lane < 4) gp[4 * unit + lane] = 0.0;   // columns that return early add nothing
         const DevPair &P = pairs[d * g.n_wfs + w];
-        if (!P.im) continue;
-        if (P.kf) warp_column_kf(g, pairs, d, a, w, wbuf, g.seg_floats, lane, err);
-        else warp_column<MODE_FWD, 1>(g, pairs, d, a, w, wbuf, g.seg_floats, lane, err, nullptr, u);
+        if (!pair_active<MODE>(P)) continue;
+        if (P.kf) warp_column_kf<MODE>(g, pairs, d, a, w, wbuf, g.seg_floats, lane, err, gp, unit);
+        else warp_column<MODE, NV>(g, pairs, d, a, w, wbuf, g.seg_floats, lane, err, gp, unit);
     }
-    if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+    if (MODE != MODE_VJP && lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 
 size_t tele_smem_bytes(int threads, int cap4) { return (size_t)(threads / 32) * cap4 * sizeof(float4); }
@@ -1636,8 +1765,8 @@ static cudaError_t prepare_one(int threads, size_t smem, int *bps) {
     cudaError_t e = cudaFuncSetAttribute(k_im<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    if (MODE == MODE_FWD &&
-        (e = cudaFuncSetAttribute(k_imk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+    if ((e = cudaFuncSetAttribute(k_imk<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        cudaSuccess)
         return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_im<MODE>, threads, smem);
 }
@@ -1690,11 +1819,17 @@ cudaError_t launch_im(int mode, const Geo &g, const DevPair *pairs, int *err, do
                       size_t smem, cudaStream_t s, int kgrid) {
     switch (mode) {
         case MODE_FWD:
-            if (grid > 0) k_im<MODE_FWD><<<grid, threads, smem, s>>>(g, pairs, err, gp);
-            if (kgrid > 0) k_imk<<<kgrid, threads, smem, s>>>(g, pairs, err);
+            if (kgrid > 0) k_imk<MODE_FWD><<<kgrid, threads, smem, s>>>(g, pairs, err, gp);
+            else if (grid > 0) k_im<MODE_FWD><<<grid, threads, smem, s>>>(g, pairs, err, gp);
             break;
-        case MODE_TAN: k_im<MODE_TAN><<<grid, threads, smem, s>>>(g, pairs, err, gp); break;
-        default: k_im<MODE_VJP><<<grid, threads, smem, s>>>(g, pairs, err, gp); break;
+        case MODE_TAN:
+            if (kgrid > 0) k_imk<MODE_TAN><<<kgrid, threads, smem, s>>>(g, pairs, err, gp);
+            else if (grid > 0) k_im<MODE_TAN><<<grid, threads, smem, s>>>(g, pairs, err, gp);
+            break;
+        default:
+            if (kgrid > 0) k_imk<MODE_VJP><<<kgrid, threads, smem, s>>>(g, pairs, err, gp);
+            else if (grid > 0) k_im<MODE_VJP><<<grid, threads, smem, s>>>(g, pairs, err, gp);
+            break;
     }
     return cudaGetLastError();
 }
