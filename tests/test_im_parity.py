@@ -170,6 +170,20 @@ def test_edge_cases_shift_rotation_k2_and_odd_rows():
     assert nv % 2 == 1 or True
 
 
+def test_weight_box_orientations_and_widths():
+    # The weight-box path (sensors with subapertures of at most 12 pixels):
+    # 5 deg and -3 deg rotations with magnifications 1.03 / 0.97 need boxes four
+    # DM pixels wide (and some segments overflow them into the per-sample
+    # path); 90.5 and 180 deg turn the boxes across the other DM axis and flip
+    # the signs of the transform.  Every column against the oracle.
+    wl = W.scao_small()
+    dm, wfs = wl.dms[0], wl.wfss[0]
+    mis = [W.Misreg(0.3, -0.2, 5.0, 1.03), W.Misreg(-0.6, 0.45, -3.0, 0.97),
+           W.Misreg(0.2, 0.7, 90.5, 1.0), W.Misreg(-0.35, -0.15, 180.0, 1.01)]
+    for m in mis:
+        check_workload(W.Workload("boxes", [dm], [wfs], [m]))
+
+
 def test_explicit_subap_valid_and_single_actuator():
     wl = W.scao_small()
     dm = wl.dms[0]
