@@ -230,13 +230,15 @@ __global__ void k_pst_core(const __grid_constant__ Geo g, const DevPair *__restr
     const int N = g.dm[d].N;
     const uint8_t *mask = g.dm[d].mask, *mcls = g.dm[d].mcls;
     int c[4];
+    // M * M < 2^31: 32-bit index arithmetic, the row advanced as j wraps
+    int i = (int)q0 / M, j = (int)q0 - i * M;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-        const long q = q0 + e;
         c[e] = 0;
-        if (q < MM) {
-            const int i = (int)(q / M), j = (int)(q - (long)i * M);
-            c[e] = core_at(P, mask, mcls, N, i, j);
+        if (q0 + e < MM) c[e] = core_at(P, mask, mcls, N, i, j);
+        if (++j == M) {
+            j = 0;
+            ++i;
         }
     }
     if (q0 + 3 < MM && (reinterpret_cast<uintptr_t>(pst + q0) & 3u) == 0) {
@@ -279,13 +281,13 @@ __global__ void k_pst_codes(const __grid_constant__ Geo g, const DevPair *__rest
     const int w = p % g.n_wfs;
     const DevWFS &WF = g.wfs[w];
     const int M = WF.M, n1 = WF.n_sub + 1, k = WF.k;
-    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= 2L * M * n1) return;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;   // 2 M (n_sub + 1) < 2^31
+    if (idx >= 2 * M * n1) return;
     const DevPair &P = pairs[p];
     if (!P.pst) return;
-    const int dir = (int)(idx / ((long)M * n1));
-    const long r = idx - (long)dir * M * n1;
-    const int x = (int)(r / n1), b = (int)(r - (long)x * n1);
+    const int dir = idx >= M * n1 ? 1 : 0;
+    const int r = idx - dir * M * n1;
+    const int x = r / n1, b = r - x * n1;
     const int c0 = b * k - 1, c1 = b * k;
     int code;
     if (dir == 0) {
@@ -378,6 +380,7 @@ __global__ void __launch_bounds__(128) k_kseg(const __grid_constant__ Geo g, con
     int flags = 0, ring = 0;
     bool any = false, asym = false;
     int ox = 0, oy = 0, cx0 = INT_MAX, cx1 = INT_MIN, cy0 = INT_MAX, cy1 = INT_MIN;
+    int qa = KF_MAX_K, qb = -1, ta = 1, tb = 0;   // rectangle of the core samples with stencil bits
     // the segment's class bytes, loaded together (k <= KF_MAX_K)
     int cb[KF_MAX_K];
 #pragma unroll
@@ -399,15 +402,21 @@ __global__ void __launch_bounds__(128) k_kseg(const __grid_constant__ Geo g, con
                     ring |= 1 << (2 * q + t);
                     continue;
                 }
-                pix(q, t, i, j);
-                const float xl = exact_affine(P.Ahi[0], P.Alo[0], P.Ahi[1], P.Alo[1], P.bhi[0], P.blo[0], j, i, ox);
-                const float yl = exact_affine(P.Ahi[2], P.Alo[2], P.Ahi[3], P.Alo[3], P.bhi[1], P.blo[1], j, i, oy);
-                const int cx = (int)floorf(xl), cy = (int)floorf(yl);
-                cx0 = min(cx0, cx); cx1 = max(cx1, cx); cy0 = min(cy0, cy); cy1 = max(cy1, cy);
+                qa = min(qa, q); qb = max(qb, q); ta = min(ta, t); tb = max(tb, t);
                 any = true;
                 if ((ba != 0) != (bb != 0)) asym = true;
             }
         }
+        // the map is affine: the extreme cells of the core samples lie at the
+        // corners of their (q, t) rectangle (the second pass checks each sample)
+        if (any)
+            for (int e = 0; e < 4; ++e) {
+                pix((e & 1) ? qb : qa, (e & 2) ? tb : ta, i, j);
+                const float xl = exact_affine(P.Ahi[0], P.Alo[0], P.Ahi[1], P.Alo[1], P.bhi[0], P.blo[0], j, i, ox);
+                const float yl = exact_affine(P.Ahi[2], P.Alo[2], P.Ahi[3], P.Alo[3], P.bhi[1], P.blo[1], j, i, oy);
+                const int cx = (int)floorf(xl), cy = (int)floorf(yl);
+                cx0 = min(cx0, cx); cx1 = max(cx1, cx); cy0 = min(cy0, cy); cy1 = max(cy1, cy);
+            }
     }
     int gx = 0, gy = 0;
     if (!(flags & KF_FALLBACK) && any) {
@@ -424,6 +433,7 @@ __global__ void __launch_bounds__(128) k_kseg(const __grid_constant__ Geo g, con
     if (!(flags & (KF_FALLBACK | KF_NOCORE))) {
         if (asym) flags |= KF_ASYM;
         float *wa = acc[threadIdx.x], *wb = wa + KTAPS;
+        bool overflow = false;
         // component 0: the resampled value; 1..4 (P.kcomp = 5): its
         // derivatives with respect to p_k through the sample position, the
         // pixel classes held fixed (d phi = gx dx_k + gy dy_k, with gx, gy the
@@ -452,6 +462,10 @@ __global__ void __launch_bounds__(128) k_kseg(const __grid_constant__ Geo g, con
                 const float yl = exact_affine(P.Ahi[2], P.Alo[2], P.Ahi[3], P.Alo[3], P.bhi[1], P.blo[1], j, i, oy);
                 const float fx0 = floorf(xl), fy0 = floorf(yl);
                 const int cx = (int)fx0 - cx0, cy = (int)fy0 - cy0;
+                if (cx < 0 || cy < 0 || cx + 1 >= ex || cy + 1 >= ey) {
+                    overflow = true;   // a rounding past the corners' cells: per-sample path
+                    continue;
+                }
                 const float fx = xl - fx0, fy = yl - fy0, hx = 1.f - fx, hy = 1.f - fy;
                 float wq[4];
                 if (comp == 0) {
@@ -473,10 +487,14 @@ __global__ void __launch_bounds__(128) k_kseg(const __grid_constant__ Geo g, con
                 }
             }
         }
-        float *ka = P.kw[ax] + sid + (long)comp * KTAPS * KPS, *kb = P.kwb[ax] + sid + (long)comp * KTAPS * KPS;
-        for (int q = 0; q < KTAPS; ++q) ka[(long)q * KPS] = wa[q];
-        if (asym)
-            for (int q = 0; q < KTAPS; ++q) kb[(long)q * KPS] = wb[q];
+        if (overflow) {
+            flags |= KF_FALLBACK;
+        } else {
+            float *ka = P.kw[ax] + sid + (long)comp * KTAPS * KPS, *kb = P.kwb[ax] + sid + (long)comp * KTAPS * KPS;
+            for (int q = 0; q < KTAPS; ++q) ka[(long)q * KPS] = wa[q];
+            if (asym)
+                for (int q = 0; q < KTAPS; ++q) kb[(long)q * KPS] = wb[q];
+        }
         }
     }
     if (blockIdx.z == 0) P.korg[ax][sid] = (gx & 0xfff) | ((gy & 0xfff) << 12) | (flags << 24);
