@@ -133,6 +133,12 @@ namespace {
 struct WfsTables {
     std::vector<uint8_t> xcode, ycode;
     std::vector<int> irr_pix, irr_sub, irr_sr, vsub, vrow, irrc_row, vidx;
+    // the same pupil-edge entries bucketed by 16 x 16 pixel tiles of each
+    // subaperture (sensors with k > 32): first entry of each tile, then pixels
+    // and weights in tile order
+    std::vector<int> tl_start, tl_pix;
+    std::vector<int8_t> tl_w;
+    int tl_n = 0;
     std::vector<int4> irrc;
     std::vector<int8_t> irr_w;
     std::vector<short> vsj;
@@ -265,6 +271,30 @@ bool build_wfs_tables(const synim_wfs_desc &d, WfsTables &t, std::string &why) {
         }
     }
     t.irrc_row[n] = (int)t.irrc.size();
+    if (k > 32) {
+        const int T = (k + 15) / 16;
+        t.tl_n = T;
+        const size_t nt = (size_t)n * n * T * T;
+        std::vector<int> cnt(nt + 1, 0), tile_of(t.irr_pix.size());
+        for (size_t e = 0; e < t.irr_pix.size(); ++e) {
+            const int i = t.irr_pix[e] >> 16, j = t.irr_pix[e] & 0xffff;
+            const int si = i / k, sj = j / k;
+            const int q = ((si * n + sj) * T + (i - si * k) / 16) * T + (j - sj * k) / 16;
+            tile_of[e] = q;
+            ++cnt[q + 1];
+        }
+        for (size_t q = 0; q < nt; ++q) cnt[q + 1] += cnt[q];
+        t.tl_start = cnt;
+        t.tl_pix.assign(t.irr_pix.size(), 0);
+        t.tl_w.assign(t.irr_w.size(), 0);
+        std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+        for (size_t e = 0; e < t.irr_pix.size(); ++e) {   // stable: entry order within a tile
+            const int d = fill[tile_of[e]]++;
+            t.tl_pix[d] = t.irr_pix[e];
+            t.tl_w[2 * d] = t.irr_w[2 * e];
+            t.tl_w[2 * d + 1] = t.irr_w[2 * e + 1];
+        }
+    }
     t.P = std::move(P);
     return true;
 }
@@ -570,7 +600,15 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
         if (e == cudaSuccess) e = dev_upload(c, &sr, T.irr_sr);
         if (e == cudaSuccess) e = dev_upload(c, &cd, T.irrc);
         if (e == cudaSuccess) e = dev_upload(c, &cr, T.irrc_row);
+        int *ts = nullptr, *tp = nullptr;
+        int8_t *tw = nullptr;
+        if (T.tl_n > 0) {
+            if (e == cudaSuccess) e = dev_upload(c, &ts, T.tl_start);
+            if (e == cudaSuccess && !T.tl_pix.empty()) e = dev_upload(c, &tp, T.tl_pix);
+            if (e == cudaSuccess && !T.tl_w.empty()) e = dev_upload(c, &tw, T.tl_w);
+        }
         if (e != cudaSuccess) return bail(cuda_fail(c, e, "sensor tables"));
+        G.tl_start = ts; G.tl_pix = tp; G.tl_w = tw; G.tl_n = tp ? T.tl_n : 0;
         G.irrc = cd; G.irrc_row = cr; G.irr_sr = sr; G.vsj = vj; G.vidx = vx;
         G.xcode = xc; G.ycode = yc; G.irr_pix = ip; G.irr_w = iw; G.irr_sub = is;
         G.fac = fa; G.vsub = vs; G.vrow = vr;

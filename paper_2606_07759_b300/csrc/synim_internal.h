@@ -75,6 +75,13 @@ struct DevWFS {
     const short *vsj;      // [nv + 4] sj of each valid row (padded with -1: 4-row loads)
     const int *vidx;       // [n_sub * n_sub] valid row of each subaperture, -1 if invalid
     const int *vrow;       // [n_sub + 1] first valid row of each subaperture row
+    // the pupil-edge entries by 16 x 16 pixel tiles of each subaperture (k > 32 only):
+    // tile (si, sj, ti, tj) at ((si n_sub + sj) tl_n + ti) tl_n + tj, its entries
+    // [tl_start[tile], tl_start[tile + 1]) of tl_pix / tl_w (as irr_pix / irr_w)
+    const int *tl_start;
+    const int *tl_pix;
+    const int8_t *tl_w;
+    int tl_n;              // tiles per subaperture side, 0 = no tiles
     int n_sub, M, k, nv, CH;
     int n_irr;             // entries of irr_pix (an upper bound where the tables are built on the device)
 };

@@ -868,6 +868,68 @@ __device__ __forceinline__ void edge_sum(const DevWFS &WF, const ItemWfs &s, con
     }
 }
 
+// The same sums for large subapertures (k > 32) from the create-time tiles:
+// only the 16 x 16 pixel tiles that the pixel box overlaps are read, their
+// entries spread over the lanes (entries outside the box are skipped, as in
+// edge_sum).  Each lane accumulates its entries in a fixed order.
+template <int NV>
+__device__ __forceinline__ void edge_sum_tiles(const DevWFS &WF, const ItemWfs &s, const Eval<NV> &ev, int si,
+                                               int sj, int lane, float *ax, float *ay) {
+    const int k = WF.k, T = WF.tl_n;
+    const int i0 = max(si * k, s.pi0), i1 = min(si * k + k - 1, s.pi1);
+    const int j0 = max(sj * k, s.pj0), j1 = min(sj * k + k - 1, s.pj1);
+    if (i0 > i1 || j0 > j1) return;
+    const int ti0 = (i0 - si * k) >> 4, ti1 = (i1 - si * k) >> 4;
+    const int tj0 = (j0 - sj * k) >> 4, tj1 = (j1 - sj * k) >> 4;
+    const int ntj = tj1 - tj0 + 1, ntiles = (ti1 - ti0 + 1) * ntj;
+    const int base = (si * WF.n_sub + sj) * T * T;
+    for (int g0 = 0; g0 < ntiles; g0 += 32) {
+        const int tq = g0 + lane;
+        int st = 0, cnt = 0;
+        if (tq < ntiles) {
+            const int a = tq / ntj, b = tq - a * ntj;
+            const int tile = base + (ti0 + a) * T + tj0 + b;
+            if (SYNIM_IDX_OK(tile >= 0 && tile < WF.n_sub * WF.n_sub * T * T, ev.err)) {
+                st = WF.tl_start[tile];
+                cnt = WF.tl_start[tile + 1] - st;
+            }
+        }
+        int pre = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, pre, o);
+            if (lane >= o) pre += v;
+        }
+        const int total = __shfl_sync(0xffffffffu, pre, 31), excl = pre - cnt;
+        for (int e0 = 0; e0 < total; e0 += 32) {
+            const int jj = e0 + lane;
+            int own = 0;   // the last lane whose first entry is at or before jj
+#pragma unroll
+            for (int st2 = 16; st2 > 0; st2 >>= 1)
+                if (__shfl_sync(0xffffffffu, excl, own + st2) <= jj) own += st2;
+            const int ost = __shfl_sync(0xffffffffu, st, own), oex = __shfl_sync(0xffffffffu, excl, own);
+            if (jj >= total) continue;
+            const int e = ost + (jj - oex);
+            if (!SYNIM_IDX_OK(e >= 0 && e < WF.n_irr, ev.err)) continue;
+            const int pix = WF.tl_pix[e];
+            const int i = pix >> 16, j = pix & 0xffff;
+            if (i < i0 || i > i1 || j < j0 || j > j1) continue;
+            const float wx = WF.tl_w[2 * e], wy = WF.tl_w[2 * e + 1];
+            float v[NV];
+#pragma unroll
+            for (int t = 0; t < NV; ++t) v[t] = 0.f;
+            const int c = pixel_class(s.pst, WF.M, i, j);
+            if (c == 1) ev.bil(i, j, v);
+            else if (c == 2) ev.ring(i, j, v);
+#pragma unroll
+            for (int t = 0; t < NV; ++t) {
+                ax[t] = fmaf(wx, v[t], ax[t]);
+                ay[t] = fmaf(wy, v[t], ay[t]);
+            }
+        }
+    }
+}
+
 // Zero rows [r0, r1) of a 16-byte-aligned column: lanes store the unaligned
 // head and tail, lane 0 issues bulk copies (cp.async.bulk, at most 4 KB each)
 // of the CTA's shared zero buffer over the aligned middle.
@@ -1441,7 +1503,8 @@ __device__ __forceinline__ void warp_column(const Geo &g, const DevPair *__restr
                 float ax[NV], ay[NV];
 #pragma unroll
                 for (int v = 0; v < NV; ++v) ax[v] = ay[v] = 0.f;
-                edge_sum<NV>(WF, s, ev, si, s.sj0 + c, lane, 32, ax, ay);
+                if (WF.tl_n > 0) edge_sum_tiles<NV>(WF, s, ev, si, s.sj0 + c, lane, ax, ay);
+                else edge_sum<NV>(WF, s, ev, si, s.sj0 + c, lane, 32, ax, ay);
 #pragma unroll
                 for (int v = 0; v < NV; ++v)
 #pragma unroll
