@@ -167,7 +167,12 @@ synim_status synim_pair_affine(const synim_ctx *ctx, int32_t dm, int32_t wfs,
  * one warp per (actuator, sensor) column over a grid-stride loop.  mis[n_dm * n_wfs] (host) holds one misregistration per pair,
  * pair index = dm * n_wfs + wfs; im[n_dm * n_wfs] (host array) holds device
  * pointers to the caller's FP32 output buffers (layout above); a NULL entry
- * skips that pair.  Asynchronous on cuda_stream.
+ * skips that pair.  Asynchronous on cuda_stream.  With the numerical slope
+ * engine, the call's per-pair pixel classes and weight boxes are built on a
+ * stream the context owns, ordered before the IM launch on cuda_stream; the
+ * context alternates two sets of these tables, so the next call's tables are
+ * built while this call's IM kernel runs.  One host thread at a time per
+ * context.
  */
 synim_status synim_im_compute(synim_ctx *ctx, const synim_misreg *mis, float *const *im,
                               void *cuda_stream);

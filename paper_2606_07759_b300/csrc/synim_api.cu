@@ -437,6 +437,11 @@ void synim_im_destroy(synim_ctx *ctx) {
     for (int s = 0; s < NSLOT; ++s)
         if (ctx->slot_ev[s]) cudaEventDestroy(ctx->slot_ev[s]);
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
+    if (ctx->prep) cudaStreamDestroy(ctx->prep);
+    for (int t = 0; t < 2; ++t) {
+        if (ctx->ev_prep[t]) cudaEventDestroy(ctx->ev_prep[t]);
+        if (ctx->ev_im[t]) cudaEventDestroy(ctx->ev_im[t]);
+    }
     cnn_destroy(ctx->cnn);
     est_destroy(ctx->est);
     probe_destroy(ctx->probe);
@@ -738,18 +743,23 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
             tot_lines += 2LL * c->wh[w].M * (c->wh[w].n_sub + 1);
         }
     const int np = n_dm * n_wfs;
-    e = dev_alloc(c, &c->d_pst, (size_t)tot);
-    if (e == cudaSuccess) e = dev_alloc(c, &c->d_lines, (size_t)tot_lines);
-    for (int d = 0; d < n_dm && e == cudaSuccess; ++d)
-        for (int w = 0; w < n_wfs && e == cudaSuccess; ++w) {
-            const WfsHost &H = c->wh[w];
-            if (H.k > KF_MAX_K || (long)H.n_sub * (H.n_sub + 1) > KPS || !c->geo.dm[d].winK) continue;
-            const int p = d * n_wfs + w;
-            e = dev_alloc(c, &c->k_org[p], (size_t)4 * KPS);
-            if (e == cudaSuccess) e = dev_alloc(c, &c->k_w[p], (size_t)2 * KNC * KTAPS * KPS);
-            if (e == cudaSuccess) e = dev_alloc(c, &c->k_wb[p], (size_t)2 * KNC * KTAPS * KPS);
-        }
-    if (e == cudaSuccess) e = dev_alloc(c, &c->d_pairs, (size_t)np);
+    // two table sets (alternate calls); the telescoping engine takes set 0 only
+    const int n_sets = c->slope_engine == SYNIM_ENGINE_TELESCOPING ? 1 : 2;
+    e = cudaSuccess;
+    for (int t = 0; t < n_sets && e == cudaSuccess; ++t) {
+        e = dev_alloc(c, &c->d_pst[t], (size_t)tot);
+        if (e == cudaSuccess) e = dev_alloc(c, &c->d_lines[t], (size_t)tot_lines);
+        for (int d = 0; d < n_dm && e == cudaSuccess; ++d)
+            for (int w = 0; w < n_wfs && e == cudaSuccess; ++w) {
+                const WfsHost &H = c->wh[w];
+                if (H.k > KF_MAX_K || (long)H.n_sub * (H.n_sub + 1) > KPS || !c->geo.dm[d].winK) continue;
+                const int p = d * n_wfs + w;
+                e = dev_alloc(c, &c->k_org[t][p], (size_t)4 * KPS);
+                if (e == cudaSuccess) e = dev_alloc(c, &c->k_w[t][p], (size_t)2 * KNC * KTAPS * KPS);
+                if (e == cudaSuccess) e = dev_alloc(c, &c->k_wb[t][p], (size_t)2 * KNC * KTAPS * KPS);
+            }
+        if (e == cudaSuccess) e = dev_alloc(c, &c->d_pairs[t], (size_t)np);
+    }
     if (e == cudaSuccess) e = dev_alloc(c, &c->d_err, 1);
     if (e == cudaSuccess) e = dev_alloc(c, &c->d_gp, (size_t)np * 4);
     if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
@@ -772,6 +782,12 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
     }
     if ((e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking)) != cudaSuccess)
         return bail(cuda_fail(c, e, "capture stream"));
+    if ((e = cudaStreamCreateWithFlags(&c->prep, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail(cuda_fail(c, e, "prep stream"));
+    for (int t = 0; t < 2; ++t)
+        if ((e = cudaEventCreateWithFlags(&c->ev_prep[t], cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&c->ev_im[t], cudaEventDisableTiming)) != cudaSuccess)
+            return bail(cuda_fail(c, e, "event"));
     if (c->profile)
         for (int q = 0; q < NPROF; ++q)
             if ((e = cudaEventCreate(&c->prof_a[q])) != cudaSuccess ||
@@ -908,6 +924,9 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
     if (c->slot_used[slot] && (e = cudaEventSynchronize(c->slot_ev[slot])) != cudaSuccess)
         return cuda_fail(c, e, "slot wait");
     DevPair *hp = c->h_pairs[slot];
+    // this call's table set (alternate calls take the other one)
+    const int ts = tele ? 0 : c->tset;
+    DevPair *dp = c->d_pairs[ts];
     std::vector<long long> need((size_t)np);
     int max_seg = 0;   // segments per axis of the largest sensor with weight boxes this call
     for (int d = 0; d < c->n_dm; ++d)
@@ -923,8 +942,8 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
             if (!invert2(P.A, P.Ai)) return fail(c, SYNIM_ERR_INVALID_ARG, "singular composite affine");
             composite_jac(c->dmh[d], m, P.A, P.b, P.dA, P.db);
             split_pair(P);
-            P.pst = c->d_pst + c->pst_off[p];
-            P.xcc = c->d_lines + c->line_off[p];
+            P.pst = c->d_pst[ts] + c->pst_off[p];
+            P.xcc = c->d_lines[ts] + c->line_off[p];
             P.ycc = P.xcc + (size_t)c->wh[w].M * (c->wh[w].n_sub + 1);
             if (mode == MODE_FWD) P.im = im ? im[p] : nullptr;
             if (mode == MODE_TAN) {
@@ -934,7 +953,7 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
             if (mode == MODE_VJP) P.gim = gim ? gim[p] : nullptr;
             // the numerical engine's boundary-segment weight boxes: values for
             // forward IMs, values and tangents for the sensitivities and the adjoint
-            if (!tele && c->k_org[p]) {
+            if (!tele && c->k_org[ts][p]) {
                 const int s0 = kseg_shape(P.A, c->wh[w].k, 0), s1 = kseg_shape(P.A, c->wh[w].k, 1);
                 if (s0 >= 0 && s1 >= 0) {
                     P.kf = 1;
@@ -942,10 +961,10 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
                     P.kshape[0] = s0;
                     P.kshape[1] = s1;
                     for (int ax = 0; ax < 2; ++ax) {
-                        P.korg[ax] = c->k_org[p] + (size_t)ax * KPS;
-                        P.kring[ax] = c->k_org[p] + (size_t)(2 + ax) * KPS;
-                        P.kw[ax] = c->k_w[p] + (size_t)ax * KNC * KTAPS * KPS;
-                        P.kwb[ax] = c->k_wb[p] + (size_t)ax * KNC * KTAPS * KPS;
+                        P.korg[ax] = c->k_org[ts][p] + (size_t)ax * KPS;
+                        P.kring[ax] = c->k_org[ts][p] + (size_t)(2 + ax) * KPS;
+                        P.kw[ax] = c->k_w[ts][p] + (size_t)ax * KNC * KTAPS * KPS;
+                        P.kwb[ax] = c->k_wb[ts][p] + (size_t)ax * KNC * KTAPS * KPS;
                     }
                 }
             }
@@ -1029,10 +1048,25 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
         g0 = (any_plain && !any_k) ? grid_for(th) : 0;
         g1 = any_k ? grid_for(th) : 0;
     };
-    if ((e = cudaMemcpyAsync(c->d_pairs, hp, sizeof(DevPair) * np, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    // forward IMs and tangents build this call's tables on the prep stream,
+    // once the IM launch that last read the set has finished; the adjoint
+    // (which synchronises at the end of each call) builds them on the
+    // caller's stream, and the telescoping engine has no tables to build
+    const bool overlap = !tele && mode != MODE_VJP;
+    cudaStream_t up = overlap ? c->prep : s;
+    if (!tele && c->im_used[ts] && (e = cudaStreamWaitEvent(up, c->ev_im[ts], 0)) != cudaSuccess)
+        return cuda_fail(c, e, "table set wait");
+    if ((e = cudaMemcpyAsync(dp, hp, sizeof(DevPair) * np, cudaMemcpyHostToDevice, up)) != cudaSuccess)
         return cuda_fail(c, e, "parameter upload");
-    cudaEventRecord(c->slot_ev[slot], s);
+    cudaEventRecord(c->slot_ev[slot], up);
     c->slot_used[slot] = true;
+    if (overlap && c->autotune && !c->tuned[mode]) {
+        // the autotuner runs on the caller's stream: after the upload, and the
+        // prep stream after it
+        if ((e = cudaEventRecord(c->ev_prep[ts], up)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(s, c->ev_prep[ts], 0)) != cudaSuccess)
+            return cuda_fail(c, e, "autotune order");
+    }
     c->slot = (slot + 1) % NSLOT;
     if (c->autotune && !c->tuned[mode] && tele) {
         // autotuner of the telescoping kernel: lanes per subaperture (each
@@ -1056,10 +1090,10 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
                 }
                 const int gr = grid_for(th);
                 float ms = 0.f;
-                e = launch_tele(g, t, c->d_pairs, tele_cap4, c->d_err, gr, th, s);
+                e = launch_tele(g, t, dp, tele_cap4, c->d_err, gr, th, s);
                 if (e == cudaSuccess) e = cudaEventRecord(t0, s);
                 for (int r = 0; r < 3 && e == cudaSuccess; ++r)
-                    e = launch_tele(g, t, c->d_pairs, tele_cap4, c->d_err, gr, th, s);
+                    e = launch_tele(g, t, dp, tele_cap4, c->d_err, gr, th, s);
                 if (e == cudaSuccess) e = cudaEventRecord(t1, s);
                 if (e == cudaSuccess) e = cudaEventSynchronize(t1);
                 if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
@@ -1081,7 +1115,9 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
         threads = best_th;
         grid = grid_for(threads);
     }
+    bool ran_tuner = false;
     if (c->autotune && !c->tuned[mode] && !tele) {
+        ran_tuner = true;
         // autotuner: time each candidate launch shape on this call's inputs
         // (three launches after a warm-up) and keep the fastest for the mode
         static const int cand_threads[] = {128, 256};
@@ -1091,8 +1127,8 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
             return cuda_fail(c, e, "autotune events");
         float best = 3e38f;
         int best_th = threads, best_l = 0;
-        if ((e = launch_pst(g, c->d_pairs, c->max_mm, c->max_lines, s)) != cudaSuccess ||
-            (e = launch_kseg(g, c->d_pairs, max_seg, mode == MODE_FWD ? 1 : KNC, s)) != cudaSuccess)
+        if ((e = launch_pst(g, dp, c->max_mm, c->max_lines, s)) != cudaSuccess ||
+            (e = launch_kseg(g, dp, max_seg, mode == MODE_FWD ? 1 : KNC, s)) != cudaSuccess)
             return cuda_fail(c, e, "autotune");
         for (int th : cand_threads)
             for (int l : cand_lanes) {
@@ -1104,10 +1140,10 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
                 int gr = 0, gk = 0;
                 grids(th, gr, gk);
                 float ms = 0.f;
-                e = launch_im(mode, gt, c->d_pairs, c->d_err, c->d_vjp_part, gr, th, sm, s, gk);
+                e = launch_im(mode, gt, dp, c->d_err, c->d_vjp_part, gr, th, sm, s, gk);
                 if (e == cudaSuccess) e = cudaEventRecord(t0, s);
                 for (int r = 0; r < 3 && e == cudaSuccess; ++r)
-                    e = launch_im(mode, gt, c->d_pairs, c->d_err, c->d_vjp_part, gr, th, sm, s, gk);
+                    e = launch_im(mode, gt, dp, c->d_err, c->d_vjp_part, gr, th, sm, s, gk);
                 if (e == cudaSuccess) e = cudaEventRecord(t1, s);
                 if (e == cudaSuccess) e = cudaEventSynchronize(t1);
                 if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
@@ -1150,43 +1186,52 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
         ev_b = c->prof_b[q];
     }
     // (inside a capture, only an "external" record becomes an event-record node)
-    auto enqueue = [&](cudaStream_t q, cudaEvent_t a0, cudaEvent_t b0, bool capturing) -> cudaError_t {
+    // part 0: the IM kernel (or the telescoping kernel), on the caller's
+    // stream; part 1: the class kernels and weight boxes, on the prep stream
+    auto enqueue = [&](int part, cudaStream_t q, cudaEvent_t a0, cudaEvent_t b0, bool capturing) -> cudaError_t {
         const unsigned int rf = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
-        if (tele) {
-            // telescoping sum: one kernel, no pixel classes
-            cudaError_t r = a0 ? cudaEventRecordWithFlags(a0, q, rf) : cudaSuccess;
-            if (r == cudaSuccess) r = launch_tele(g, c->tele, c->d_pairs, tele_cap4, c->d_err, grid, threads, q);
-            if (r == cudaSuccess && b0) r = cudaEventRecordWithFlags(b0, q, rf);
+        if (part == 1) {
+            cudaError_t r = launch_pst(g, dp, c->max_mm, c->max_lines, q);
+            if (r == cudaSuccess) r = launch_kseg(g, dp, max_seg, mode == MODE_FWD ? 1 : KNC, q);
             return r;
         }
-        cudaError_t r = launch_pst(g, c->d_pairs, c->max_mm, c->max_lines, q);
-        if (r == cudaSuccess) r = launch_kseg(g, c->d_pairs, max_seg, mode == MODE_FWD ? 1 : KNC, q);
-        if (r == cudaSuccess && a0) r = cudaEventRecordWithFlags(a0, q, rf);
-        int g0 = 0, g1 = 0;
-        grids(threads, g0, g1);
-        if (r == cudaSuccess) r = launch_im(mode, g, c->d_pairs, c->d_err, c->d_vjp_part, g0, threads, smem, q, g1);
-        if (r == cudaSuccess && mode == MODE_VJP) r = launch_vjp_reduce(g, c->d_vjp_part, c->d_gp, q);
+        cudaError_t r = a0 ? cudaEventRecordWithFlags(a0, q, rf) : cudaSuccess;
+        if (tele) {
+            // telescoping sum: one kernel, no pixel classes
+            if (r == cudaSuccess) r = launch_tele(g, c->tele, dp, tele_cap4, c->d_err, grid, threads, q);
+        } else {
+            int g0 = 0, g1 = 0;
+            grids(threads, g0, g1);
+            if (r == cudaSuccess) r = launch_im(mode, g, dp, c->d_err, c->d_vjp_part, g0, threads, smem, q, g1);
+            if (r == cudaSuccess && mode == MODE_VJP) r = launch_vjp_reduce(g, c->d_vjp_part, c->d_gp, q);
+        }
         if (r == cudaSuccess && b0) r = cudaEventRecordWithFlags(b0, q, rf);
         return r;
     };
-    if (c->use_graph) {
+    // one part, from its captured graph where graphs are on (one graph per
+    // part, table set and launch shape)
+    auto launch_part = [&](int part, cudaStream_t q) -> synim_status {
+        const bool prof = c->profile && part == 0;
+        if (!c->use_graph) {
+            const cudaError_t r = enqueue(part, q, prof ? ev_a : nullptr, prof ? ev_b : nullptr, false);
+            return r == cudaSuccess ? SYNIM_OK : cuda_fail(c, r, "launch");
+        }
         // the weight-box kernel's grid (max_seg) is part of the captured launches
-        const auto key = std::make_tuple(mode * 4 + (any_plain ? 1 : 0) + (any_k ? 2 : 0), smem, grid,
-                                         threads * 16 + g.seg_lanes + max_seg * 65536);
+        const auto key = std::make_tuple(mode * 4 + (any_plain ? 1 : 0) + (any_k ? 2 : 0) + 16 * ts + 64 * part,
+                                         smem, grid, threads * 16 + g.seg_lanes + max_seg * 65536);
         auto it = c->graphs.find(key);
         if (it == c->graphs.end()) {
             GraphEntry ge;
             if ((e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
                 return cuda_fail(c, e, "graph capture begin");
-            cudaError_t e1 = enqueue(c->cap, c->profile ? c->prof_a[0] : nullptr,
-                                     c->profile ? c->prof_b[0] : nullptr, true);
+            cudaError_t e1 = enqueue(part, c->cap, prof ? c->prof_a[0] : nullptr, prof ? c->prof_b[0] : nullptr, true);
             e = cudaStreamEndCapture(c->cap, &ge.graph);
             if (e1 != cudaSuccess) {
                 if (ge.graph) cudaGraphDestroy(ge.graph);
                 return cuda_fail(c, e1, "graph capture");
             }
             if (e != cudaSuccess) return cuda_fail(c, e, "graph capture end");
-            if (c->profile) {
+            if (prof) {
                 size_t nn = 0;
                 cudaGraphGetNodes(ge.graph, nullptr, &nn);
                 std::vector<cudaGraphNode_t> nodes(nn);
@@ -1207,16 +1252,34 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
             }
             it = c->graphs.emplace(key, ge).first;
         }
-        if (c->profile) {
+        if (prof) {
             if (!it->second.ev_start || !it->second.ev_stop)
                 return fail(c, SYNIM_ERR_CUDA, "profiling: event nodes missing from the captured graph");
             if ((e = cudaGraphExecEventRecordNodeSetEvent(it->second.exec, it->second.ev_start, ev_a)) != cudaSuccess ||
                 (e = cudaGraphExecEventRecordNodeSetEvent(it->second.exec, it->second.ev_stop, ev_b)) != cudaSuccess)
                 return cuda_fail(c, e, "profiling: event node update");
         }
-        if ((e = cudaGraphLaunch(it->second.exec, s)) != cudaSuccess) return cuda_fail(c, e, "graph launch");
+        if ((e = cudaGraphLaunch(it->second.exec, q)) != cudaSuccess) return cuda_fail(c, e, "graph launch");
+        return SYNIM_OK;
+    };
+    synim_status st = SYNIM_OK;
+    if (tele) {
+        if ((st = launch_part(0, s)) != SYNIM_OK) return st;
     } else {
-        if ((e = enqueue(s, ev_a, ev_b, false)) != cudaSuccess) return cuda_fail(c, e, "launch");
+        // the autotuner's launches (caller's stream) read this set: the prep
+        // stream rebuilds it after them
+        if (overlap && ran_tuner &&
+            ((e = cudaEventRecord(c->ev_im[ts], s)) != cudaSuccess ||
+             (e = cudaStreamWaitEvent(c->prep, c->ev_im[ts], 0)) != cudaSuccess))
+            return cuda_fail(c, e, "autotune order");
+        if ((st = launch_part(1, up)) != SYNIM_OK) return st;
+        if (overlap && ((e = cudaEventRecord(c->ev_prep[ts], up)) != cudaSuccess ||
+                        (e = cudaStreamWaitEvent(s, c->ev_prep[ts], 0)) != cudaSuccess))
+            return cuda_fail(c, e, "table set order");
+        if ((st = launch_part(0, s)) != SYNIM_OK) return st;
+        if ((e = cudaEventRecord(c->ev_im[ts], s)) != cudaSuccess) return cuda_fail(c, e, "table set release");
+        c->im_used[ts] = true;
+        c->tset = ts ^ 1;
     }
     if (mode == MODE_VJP) {
         std::vector<double> tmp((size_t)np * 4);

@@ -266,7 +266,16 @@ struct synim_ctx {
     synim::TeleSet tele{};
     size_t mem_used = 0;      // device bytes taken by create so far
     std::vector<void *> host_allocs;
-    synim::DevPair *d_pairs = nullptr;
+    // Two sets of per-call tables (pair records, core maps, boundary-line
+    // classes, weight boxes), taken by alternate calls: a call's class kernels
+    // and weight boxes run on the context's prep stream and overlap the
+    // previous call's IM kernel on the caller's stream.  ev_prep[t]: set t is
+    // built; ev_im[t]: the IM launch that read set t has finished.
+    synim::DevPair *d_pairs[2] = {};
+    int tset = 0;
+    cudaStream_t prep = nullptr;
+    cudaEvent_t ev_prep[2] = {}, ev_im[2] = {};
+    bool im_used[2] = {};
     synim::DevPair *h_pairs[synim::NSLOT] = {};
     cudaEvent_t slot_ev[synim::NSLOT] = {};
     bool slot_used[synim::NSLOT] = {};
@@ -276,12 +285,12 @@ struct synim_ctx {
     double *d_vjp_part = nullptr;   // per-column adjoint partials [n_items * n_wfs][4]
     long long pst_off[SYNIM_MAX_PAIRS] = {};
     long long line_off[SYNIM_MAX_PAIRS] = {};
-    uint8_t *d_pst = nullptr, *d_lines = nullptr;
-    // boundary-segment weight boxes per pair (nullptr where the sensor's
-    // subapertures are too large for them): origins and ring lists [2][2][KPS], weights
-    // [2][KNC][KTAPS][KPS] for A and for B
-    int *k_org[SYNIM_MAX_PAIRS] = {};
-    float *k_w[SYNIM_MAX_PAIRS] = {}, *k_wb[SYNIM_MAX_PAIRS] = {};
+    uint8_t *d_pst[2] = {}, *d_lines[2] = {};
+    // boundary-segment weight boxes per table set and pair (nullptr where the
+    // sensor's subapertures are too large for them): origins and ring lists
+    // [2][2][KPS], weights [2][KNC][KTAPS][KPS] for A and for B
+    int *k_org[2][SYNIM_MAX_PAIRS] = {};
+    float *k_w[2][SYNIM_MAX_PAIRS] = {}, *k_wb[2][SYNIM_MAX_PAIRS] = {};
     int max_mm = 0, max_lines = 0;
     int threads = 256, ctas_per_sm = 0;
     bool autotune = false;
