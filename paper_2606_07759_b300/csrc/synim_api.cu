@@ -401,6 +401,26 @@ __global__ void k_wait_selftest(long long limit, int *err) {
 }
 }  // namespace synim
 
+namespace {
+
+// Window origin of each actuator from its support box (x0, x1, y0, y1): the
+// box corner clamped so that the W x W window stays on the N x N grid; (0, 0)
+// for an empty box.
+__global__ void k_org_from_box(const int *__restrict__ box, int n_act, int N, int W, int *__restrict__ org) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= n_act) return;
+    const int *bx = box + 4 * (size_t)a;
+    int ox = 0, oy = 0;
+    if (bx[1] >= bx[0]) {
+        ox = max(0, min(bx[0], N - W));
+        oy = max(0, min(bx[2], N - W));
+    }
+    org[2 * (size_t)a] = ox;
+    org[2 * (size_t)a + 1] = oy;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char *synim_status_string(synim_status s) {
@@ -514,6 +534,7 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
         cudaStream_t cs = nullptr, ks = nullptr;
         cudaEvent_t copied[SYNIM_MAX_DM] = {}, packed[SYNIM_MAX_DM] = {};
         float *buf[2] = {nullptr, nullptr};
+        int *box = nullptr;   // support boxes of one DM (the largest n_act)
         size_t bytes = 0;
         // (a failed create has destroyed the context by the time this runs:
         // the successful path returns the buffers' bytes to its count itself)
@@ -522,6 +543,7 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
             if (ks) cudaStreamSynchronize(ks);
             for (int q = 0; q < 2; ++q)
                 if (buf[q]) cudaFree(buf[q]);
+            if (box) cudaFree(box);
             for (int d = 0; d < SYNIM_MAX_DM; ++d) {
                 if (copied[d]) cudaEventDestroy(copied[d]);
                 if (packed[d]) cudaEventDestroy(packed[d]);
@@ -547,6 +569,22 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
     for (int q = 0; q < std::min(n_host, 2); ++q)
         if ((e = capped_malloc(c, reinterpret_cast<void **>(&up.buf[q]), up.bytes)) != cudaSuccess)
             return bail(cuda_fail(c, e, "cube staging"));
+    // Nothing below waits on the copy stream until the last cube is packed:
+    // the masks go up before the cubes, the support boxes stay in one scratch
+    // (no cudaFree, which would wait for the copies), the window origins are
+    // computed on the device, and the sensor tables are uploaded afterwards.
+    uint8_t *d_masks[SYNIM_MAX_DM] = {};
+    int max_act = 1;
+    for (int d = 0; d < n_dm; ++d) {
+        max_act = std::max(max_act, dms[d].n_act);
+        if (!dms[d].mask) continue;
+        const size_t NN = (size_t)dms[d].grid_n * dms[d].grid_n;
+        std::vector<uint8_t> m(NN);
+        for (size_t q = 0; q < NN; ++q) m[q] = dms[d].mask[q] ? 1 : 0;
+        if ((e = dev_upload(c, &d_masks[d], m)) != cudaSuccess) return bail(cuda_fail(c, e, "mask upload"));
+    }
+    if ((e = cudaMalloc(&up.box, (4 * (size_t)max_act + 1) * sizeof(int))) != cudaSuccess)
+        return bail(cuda_fail(c, e, "support boxes"));
     // host cube d goes to staging buffer slot[d] (host cubes alternate between the two)
     int slot[SYNIM_MAX_DM];
     for (int d = 0, h = 0; d < n_dm; ++d) slot[d] = dms[d].ifs_on_device ? -1 : (h++ & 1);
@@ -563,7 +601,8 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
             if ((e = issue_copy(next_copy)) != cudaSuccess) return bail(cuda_fail(c, e, "cube upload"));
             ++issued;
         }
-    // ---- sensors: tables ----
+    // ---- sensors: tables, built on the host while the cubes travel (uploaded after the DMs) ----
+    std::vector<WfsTables> tabs((size_t)n_wfs);
     for (int w = 0; w < n_wfs; ++w) {
         const synim_wfs_desc &Wd = wfs[w];
         WfsHost &H = c->wh[w];
@@ -573,7 +612,7 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
         H.th[0] = Wd.field_rad[0]; H.th[1] = Wd.field_rad[1];
         H.rot = Wd.rot_deg; H.mag[0] = Wd.mag[0]; H.mag[1] = Wd.mag[1];
         H.shift[0] = Wd.shift_m[0]; H.shift[1] = Wd.shift_m[1]; H.scale = Wd.slope_scale;
-        WfsTables T;
+        WfsTables &T = tabs[w];
         std::string why;
         if (!build_wfs_tables(Wd, T, why)) {
             fail(c, SYNIM_ERR_SHAPE, "sensor " + std::to_string(w) + ": " + why);
@@ -582,6 +621,161 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
         H.nv = T.nv;
         c->pupil[w] = T.P;
         c->vidx_h[w] = T.vidx;
+        c->max_mm = std::max(c->max_mm, H.M * H.M);
+        c->max_lines = std::max(c->max_lines, H.M * (H.n_sub + 1));
+    }
+    // (a DM gets the 9-pixel-bordered windows when some sensor has subapertures
+    // small enough for the weight boxes; the DM loop below builds them)
+    bool want_k_any = false;
+    for (int w = 0; w < n_wfs; ++w)
+        want_k_any |= c->wh[w].k <= KF_MAX_K && (long)c->wh[w].n_sub * (c->wh[w].n_sub + 1) <= KPS;
+    // ---- per-pair state maps, parameter blocks, counters ----
+    long long tot = 0, tot_lines = 0;
+    for (int d = 0; d < n_dm; ++d)
+        for (int w = 0; w < n_wfs; ++w) {
+            c->pst_off[d * n_wfs + w] = tot;
+            tot += (long long)c->wh[w].M * c->wh[w].M;
+            c->line_off[d * n_wfs + w] = tot_lines;
+            tot_lines += 2LL * c->wh[w].M * (c->wh[w].n_sub + 1);
+        }
+    const int np = n_dm * n_wfs;
+    // two table sets (alternate calls); the telescoping engine takes set 0 only
+    const int n_sets = c->slope_engine == SYNIM_ENGINE_TELESCOPING ? 1 : 2;
+    e = cudaSuccess;
+    for (int t = 0; t < n_sets && e == cudaSuccess; ++t) {
+        e = dev_alloc(c, &c->d_pst[t], (size_t)tot);
+        if (e == cudaSuccess) e = dev_alloc(c, &c->d_lines[t], (size_t)tot_lines);
+        for (int d = 0; d < n_dm && e == cudaSuccess; ++d)
+            for (int w = 0; w < n_wfs && e == cudaSuccess; ++w) {
+                const WfsHost &H = c->wh[w];
+                if (H.k > KF_MAX_K || (long)H.n_sub * (H.n_sub + 1) > KPS || !want_k_any) continue;
+                const int p = d * n_wfs + w;
+                e = dev_alloc(c, &c->k_org[t][p], (size_t)4 * KPS);
+                if (e == cudaSuccess) e = dev_alloc(c, &c->k_w[t][p], (size_t)2 * KNC * KTAPS * KPS);
+                if (e == cudaSuccess) e = dev_alloc(c, &c->k_wb[t][p], (size_t)2 * KNC * KTAPS * KPS);
+            }
+        if (e == cudaSuccess) e = dev_alloc(c, &c->d_pairs[t], (size_t)np);
+    }
+    if (e == cudaSuccess) e = dev_alloc(c, &c->d_err, 1);
+    if (e == cudaSuccess) e = dev_alloc(c, &c->d_gp, (size_t)np * 4);
+    if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "context buffers"));
+    for (int s = 0; s < NSLOT; ++s) {
+        void *h = nullptr;
+        if ((e = cudaMallocHost(&h, sizeof(DevPair) * np)) != cudaSuccess)
+            return bail(cuda_fail(c, e, "pinned parameter block"));
+        c->host_allocs.push_back(h);
+        c->h_pairs[s] = static_cast<DevPair *>(h);
+        std::memset(h, 0, sizeof(DevPair) * np);
+        if ((e = cudaEventCreateWithFlags(&c->slot_ev[s], cudaEventDisableTiming)) != cudaSuccess)
+            return bail(cuda_fail(c, e, "event"));
+    }
+    {
+        void *h = nullptr;
+        if ((e = cudaMallocHost(&h, sizeof(int))) != cudaSuccess) return bail(cuda_fail(c, e, "pinned flag"));
+        c->host_allocs.push_back(h);
+        c->h_err = static_cast<int *>(h);
+    }
+    if ((e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail(cuda_fail(c, e, "capture stream"));
+    if ((e = cudaStreamCreateWithFlags(&c->prep, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail(cuda_fail(c, e, "prep stream"));
+    for (int t = 0; t < 2; ++t)
+        if ((e = cudaEventCreateWithFlags(&c->ev_prep[t], cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&c->ev_im[t], cudaEventDisableTiming)) != cudaSuccess)
+            return bail(cuda_fail(c, e, "event"));
+    if (c->profile)
+        for (int q = 0; q < NPROF; ++q)
+            if ((e = cudaEventCreate(&c->prof_a[q])) != cudaSuccess ||
+                (e = cudaEventCreate(&c->prof_b[q])) != cudaSuccess)
+                return bail(cuda_fail(c, e, "profiling events"));
+    // ---- DMs, part 2: support scan + window packing ----
+    for (int d = 0; d < n_dm; ++d) {
+        const synim_dm_desc &Dd = dms[d];
+        DmHost &H = c->dmh[d];
+        H.n_act = Dd.n_act; H.N = Dd.grid_n; H.dd = Dd.pixel_pitch_m; H.h = Dd.altitude_m;
+        const float *cube = Dd.ifs;
+        if (slot[d] >= 0) {
+            if ((e = cudaStreamWaitEvent(up.ks, up.copied[d], 0)) != cudaSuccess)
+                return bail(cuda_fail(c, e, "cube upload"));
+            cube = up.buf[slot[d]];
+        }
+        int *d_box = up.box;
+        std::vector<int> box(4 * (size_t)H.n_act);
+        e = launch_support(cube, H.n_act, H.N, Dd.support_eps, d_box, up.ks);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(box.data(), d_box, box.size() * sizeof(int), cudaMemcpyDeviceToHost, up.ks);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(up.ks);
+        if (e != cudaSuccess) return bail(cuda_fail(c, e, "support scan"));
+        int W = 1;
+        for (int a = 0; a < H.n_act; ++a) {
+            const int *bx = &box[4 * (size_t)a];
+            if (bx[1] < bx[0]) continue;
+            W = std::max(W, std::max(bx[1] - bx[0] + 1, bx[3] - bx[2] + 1));
+        }
+        W = std::min(W, H.N);
+        int Wp = W + 2;
+        if ((Wp & 1) == 0) ++Wp;  // odd pitch: rows of the window fall in distinct banks
+        const int stride = (Wp * Wp + 3) / 4 * 4;
+        H.W = W; H.Wp = Wp;
+        DevDM &G = c->geo.dm[d];
+        int *d_org = nullptr;
+        float *d_win = nullptr;
+        e = dev_alloc(c, &d_org, 2 * (size_t)H.n_act);
+        if (e == cudaSuccess) {
+            k_org_from_box<<<(H.n_act + 255) / 256, 256, 0, up.ks>>>(d_box, H.n_act, H.N, W, d_org);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = dev_alloc(c, &d_win, (size_t)H.n_act * stride);
+        if (e == cudaSuccess) e = launch_pack(cube, H.n_act, H.N, d_org, W, Wp, stride, d_win, up.ks);
+        // the same windows with a KPAD-pixel zero border for the boundary-segment
+        // weight boxes, when a sensor has subapertures small enough for them
+        bool want_k = false;
+        for (int w = 0; w < n_wfs; ++w)
+            want_k |= c->wh[w].k <= KF_MAX_K && (long)c->wh[w].n_sub * (c->wh[w].n_sub + 1) <= KPS;
+        float *d_wink = nullptr;
+        int WpK = 0, strideK = 0;
+        if (want_k && e == cudaSuccess) {
+            WpK = W + 2 * KPAD;
+            if ((WpK & 1) == 0) ++WpK;
+            strideK = (WpK * WpK + 3) / 4 * 4;
+            e = dev_alloc(c, &d_wink, (size_t)H.n_act * strideK);
+            if (e == cudaSuccess)
+                e = launch_pack(cube, H.n_act, H.N, d_org, W, WpK, strideK, d_wink, up.ks, KPAD);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(up.packed[d], up.ks);
+        if (e != cudaSuccess) return bail(cuda_fail(c, e, "window packing"));
+        // the staging buffer of cube d takes the next host cube once the packing has read it
+        if (slot[d] >= 0) {
+            while (next_copy < n_dm && slot[next_copy] < 0) ++next_copy;
+            if (next_copy < n_dm) {
+                if ((e = cudaStreamWaitEvent(up.cs, up.packed[d], 0)) != cudaSuccess ||
+                    (e = issue_copy(next_copy)) != cudaSuccess)
+                    return bail(cuda_fail(c, e, "cube upload"));
+                ++next_copy;
+            }
+        }
+        uint8_t *d_mask = d_masks[d];
+        uint8_t *d_mcls = nullptr;
+        e = dev_alloc(c, &d_mcls, (size_t)(H.N + 1) * (H.N + 1));
+        if (e == cudaSuccess) e = launch_mcls(d_mask, H.N, d_mcls, up.ks);
+        if (e != cudaSuccess) return bail(cuda_fail(c, e, "mask interior map"));
+        G.win = d_win; G.org = d_org; G.mask = d_mask; G.mcls = d_mcls;
+        G.n_act = H.n_act; G.N = H.N; G.W = W; G.Wp = Wp; G.win_stride = stride;
+        G.winK = d_wink; G.WpK = WpK; G.strideK = strideK;
+    }
+    if ((e = cudaStreamSynchronize(up.ks)) != cudaSuccess) return bail(cuda_fail(c, e, "window packing"));
+    for (int q = 0; q < 2; ++q)
+        if (up.buf[q]) {
+            cudaFree(up.buf[q]);
+            up.buf[q] = nullptr;
+            c->mem_used -= up.bytes;
+        }
+    // ---- sensors: device tables (the copy engine is idle now) ----
+    for (int w = 0; w < n_wfs; ++w) {
+        const synim_wfs_desc &Wd = wfs[w];
+        const WfsHost &H = c->wh[w];
+        const WfsTables &T = tabs[w];
         DevWFS &G = c->geo.wfs[w];
         uint8_t *xc, *yc;
         int *ip, *is, *vs, *vr;
@@ -637,162 +831,8 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
             while (L < 32 && 4 * L < H.k) L *= 2;
             DT.lanes = L;
         }
-        c->max_mm = std::max(c->max_mm, H.M * H.M);
-        c->max_lines = std::max(c->max_lines, H.M * (H.n_sub + 1));
     }
-    // ---- DMs, part 2: support scan + window packing ----
-    for (int d = 0; d < n_dm; ++d) {
-        const synim_dm_desc &Dd = dms[d];
-        DmHost &H = c->dmh[d];
-        H.n_act = Dd.n_act; H.N = Dd.grid_n; H.dd = Dd.pixel_pitch_m; H.h = Dd.altitude_m;
-        const size_t NN = (size_t)H.N * H.N;
-        const float *cube = Dd.ifs;
-        if (slot[d] >= 0) {
-            if ((e = cudaStreamWaitEvent(up.ks, up.copied[d], 0)) != cudaSuccess)
-                return bail(cuda_fail(c, e, "cube upload"));
-            cube = up.buf[slot[d]];
-        }
-        int *d_box = nullptr;
-        std::vector<int> box(4 * (size_t)H.n_act);
-        e = cudaMalloc(&d_box, (box.size() + 1) * sizeof(int));
-        if (e == cudaSuccess) e = launch_support(cube, H.n_act, H.N, Dd.support_eps, d_box, up.ks);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(box.data(), d_box, box.size() * sizeof(int), cudaMemcpyDeviceToHost, up.ks);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(up.ks);
-        cudaFree(d_box);
-        if (e != cudaSuccess) return bail(cuda_fail(c, e, "support scan"));
-        int W = 1;
-        for (int a = 0; a < H.n_act; ++a) {
-            const int *bx = &box[4 * (size_t)a];
-            if (bx[1] < bx[0]) continue;
-            W = std::max(W, std::max(bx[1] - bx[0] + 1, bx[3] - bx[2] + 1));
-        }
-        W = std::min(W, H.N);
-        int Wp = W + 2;
-        if ((Wp & 1) == 0) ++Wp;  // odd pitch: rows of the window fall in distinct banks
-        const int stride = (Wp * Wp + 3) / 4 * 4;
-        H.W = W; H.Wp = Wp;
-        std::vector<int> org(2 * (size_t)H.n_act, 0);
-        for (int a = 0; a < H.n_act; ++a) {
-            const int *bx = &box[4 * (size_t)a];
-            if (bx[1] < bx[0]) continue;
-            org[2 * a] = std::max(0, std::min(bx[0], H.N - W));
-            org[2 * a + 1] = std::max(0, std::min(bx[2], H.N - W));
-        }
-        DevDM &G = c->geo.dm[d];
-        int *d_org = nullptr;
-        float *d_win = nullptr;
-        e = dev_upload(c, &d_org, org);
-        if (e == cudaSuccess) e = dev_alloc(c, &d_win, (size_t)H.n_act * stride);
-        if (e == cudaSuccess) e = launch_pack(cube, H.n_act, H.N, d_org, W, Wp, stride, d_win, up.ks);
-        // the same windows with a KPAD-pixel zero border for the boundary-segment
-        // weight boxes, when a sensor has subapertures small enough for them
-        bool want_k = false;
-        for (int w = 0; w < n_wfs; ++w)
-            want_k |= c->wh[w].k <= KF_MAX_K && (long)c->wh[w].n_sub * (c->wh[w].n_sub + 1) <= KPS;
-        float *d_wink = nullptr;
-        int WpK = 0, strideK = 0;
-        if (want_k && e == cudaSuccess) {
-            WpK = W + 2 * KPAD;
-            if ((WpK & 1) == 0) ++WpK;
-            strideK = (WpK * WpK + 3) / 4 * 4;
-            e = dev_alloc(c, &d_wink, (size_t)H.n_act * strideK);
-            if (e == cudaSuccess)
-                e = launch_pack(cube, H.n_act, H.N, d_org, W, WpK, strideK, d_wink, up.ks, KPAD);
-        }
-        if (e == cudaSuccess) e = cudaEventRecord(up.packed[d], up.ks);
-        if (e != cudaSuccess) return bail(cuda_fail(c, e, "window packing"));
-        // the staging buffer of cube d takes the next host cube once the packing has read it
-        if (slot[d] >= 0) {
-            while (next_copy < n_dm && slot[next_copy] < 0) ++next_copy;
-            if (next_copy < n_dm) {
-                if ((e = cudaStreamWaitEvent(up.cs, up.packed[d], 0)) != cudaSuccess ||
-                    (e = issue_copy(next_copy)) != cudaSuccess)
-                    return bail(cuda_fail(c, e, "cube upload"));
-                ++next_copy;
-            }
-        }
-        uint8_t *d_mask = nullptr;
-        if (Dd.mask) {
-            std::vector<uint8_t> m(NN);
-            for (size_t q = 0; q < NN; ++q) m[q] = Dd.mask[q] ? 1 : 0;
-            if ((e = dev_upload(c, &d_mask, m)) != cudaSuccess) return bail(cuda_fail(c, e, "mask upload"));
-        }
-        uint8_t *d_mcls = nullptr;
-        e = dev_alloc(c, &d_mcls, (size_t)(H.N + 1) * (H.N + 1));
-        if (e == cudaSuccess) e = launch_mcls(d_mask, H.N, d_mcls, up.ks);
-        if (e != cudaSuccess) return bail(cuda_fail(c, e, "mask interior map"));
-        G.win = d_win; G.org = d_org; G.mask = d_mask; G.mcls = d_mcls;
-        G.n_act = H.n_act; G.N = H.N; G.W = W; G.Wp = Wp; G.win_stride = stride;
-        G.winK = d_wink; G.WpK = WpK; G.strideK = strideK;
-    }
-    if ((e = cudaStreamSynchronize(up.ks)) != cudaSuccess) return bail(cuda_fail(c, e, "window packing"));
-    for (int q = 0; q < 2; ++q)
-        if (up.buf[q]) {
-            cudaFree(up.buf[q]);
-            up.buf[q] = nullptr;
-            c->mem_used -= up.bytes;
-        }
-    // ---- per-pair state maps, parameter blocks, counters ----
-    long long tot = 0, tot_lines = 0;
-    for (int d = 0; d < n_dm; ++d)
-        for (int w = 0; w < n_wfs; ++w) {
-            c->pst_off[d * n_wfs + w] = tot;
-            tot += (long long)c->wh[w].M * c->wh[w].M;
-            c->line_off[d * n_wfs + w] = tot_lines;
-            tot_lines += 2LL * c->wh[w].M * (c->wh[w].n_sub + 1);
-        }
-    const int np = n_dm * n_wfs;
-    // two table sets (alternate calls); the telescoping engine takes set 0 only
-    const int n_sets = c->slope_engine == SYNIM_ENGINE_TELESCOPING ? 1 : 2;
-    e = cudaSuccess;
-    for (int t = 0; t < n_sets && e == cudaSuccess; ++t) {
-        e = dev_alloc(c, &c->d_pst[t], (size_t)tot);
-        if (e == cudaSuccess) e = dev_alloc(c, &c->d_lines[t], (size_t)tot_lines);
-        for (int d = 0; d < n_dm && e == cudaSuccess; ++d)
-            for (int w = 0; w < n_wfs && e == cudaSuccess; ++w) {
-                const WfsHost &H = c->wh[w];
-                if (H.k > KF_MAX_K || (long)H.n_sub * (H.n_sub + 1) > KPS || !c->geo.dm[d].winK) continue;
-                const int p = d * n_wfs + w;
-                e = dev_alloc(c, &c->k_org[t][p], (size_t)4 * KPS);
-                if (e == cudaSuccess) e = dev_alloc(c, &c->k_w[t][p], (size_t)2 * KNC * KTAPS * KPS);
-                if (e == cudaSuccess) e = dev_alloc(c, &c->k_wb[t][p], (size_t)2 * KNC * KTAPS * KPS);
-            }
-        if (e == cudaSuccess) e = dev_alloc(c, &c->d_pairs[t], (size_t)np);
-    }
-    if (e == cudaSuccess) e = dev_alloc(c, &c->d_err, 1);
-    if (e == cudaSuccess) e = dev_alloc(c, &c->d_gp, (size_t)np * 4);
-    if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
-    if (e != cudaSuccess) return bail(cuda_fail(c, e, "context buffers"));
-    for (int s = 0; s < NSLOT; ++s) {
-        void *h = nullptr;
-        if ((e = cudaMallocHost(&h, sizeof(DevPair) * np)) != cudaSuccess)
-            return bail(cuda_fail(c, e, "pinned parameter block"));
-        c->host_allocs.push_back(h);
-        c->h_pairs[s] = static_cast<DevPair *>(h);
-        std::memset(h, 0, sizeof(DevPair) * np);
-        if ((e = cudaEventCreateWithFlags(&c->slot_ev[s], cudaEventDisableTiming)) != cudaSuccess)
-            return bail(cuda_fail(c, e, "event"));
-    }
-    {
-        void *h = nullptr;
-        if ((e = cudaMallocHost(&h, sizeof(int))) != cudaSuccess) return bail(cuda_fail(c, e, "pinned flag"));
-        c->host_allocs.push_back(h);
-        c->h_err = static_cast<int *>(h);
-    }
-    if ((e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking)) != cudaSuccess)
-        return bail(cuda_fail(c, e, "capture stream"));
-    if ((e = cudaStreamCreateWithFlags(&c->prep, cudaStreamNonBlocking)) != cudaSuccess)
-        return bail(cuda_fail(c, e, "prep stream"));
-    for (int t = 0; t < 2; ++t)
-        if ((e = cudaEventCreateWithFlags(&c->ev_prep[t], cudaEventDisableTiming)) != cudaSuccess ||
-            (e = cudaEventCreateWithFlags(&c->ev_im[t], cudaEventDisableTiming)) != cudaSuccess)
-            return bail(cuda_fail(c, e, "event"));
-    if (c->profile)
-        for (int q = 0; q < NPROF; ++q)
-            if ((e = cudaEventCreate(&c->prof_a[q])) != cudaSuccess ||
-                (e = cudaEventCreate(&c->prof_b[q])) != cudaSuccess)
-                return bail(cuda_fail(c, e, "profiling events"));
+    tabs.clear();
     // processing order: largest windows first (longest items scheduled early)
     std::vector<int> order(n_dm);
     for (int d = 0; d < n_dm; ++d) order[d] = d;
