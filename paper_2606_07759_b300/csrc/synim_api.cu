@@ -642,19 +642,40 @@ synim_status synim_im_create(const synim_dm_desc *dms, int32_t n_dm, const synim
     // two table sets (alternate calls); the telescoping engine takes set 0 only
     const int n_sets = c->slope_engine == SYNIM_ENGINE_TELESCOPING ? 1 : 2;
     e = cudaSuccess;
+    // one allocation per set, carved at 256-byte boundaries (a hundred-odd
+    // separate buffers cost milliseconds to allocate and free)
+    auto carve = [](size_t &off, size_t bytes) {
+        const size_t at = off;
+        off += (bytes + 255) / 256 * 256;
+        return at;
+    };
     for (int t = 0; t < n_sets && e == cudaSuccess; ++t) {
-        e = dev_alloc(c, &c->d_pst[t], (size_t)tot);
-        if (e == cudaSuccess) e = dev_alloc(c, &c->d_lines[t], (size_t)tot_lines);
-        for (int d = 0; d < n_dm && e == cudaSuccess; ++d)
-            for (int w = 0; w < n_wfs && e == cudaSuccess; ++w) {
+        size_t off = 0;
+        const size_t o_pst = carve(off, (size_t)tot), o_lines = carve(off, (size_t)tot_lines);
+        const size_t o_pairs = carve(off, sizeof(DevPair) * np);
+        size_t o_k[SYNIM_MAX_PAIRS][3] = {};
+        bool has_k[SYNIM_MAX_PAIRS] = {};
+        for (int d = 0; d < n_dm; ++d)
+            for (int w = 0; w < n_wfs; ++w) {
                 const WfsHost &H = c->wh[w];
                 if (H.k > KF_MAX_K || (long)H.n_sub * (H.n_sub + 1) > KPS || !want_k_any) continue;
                 const int p = d * n_wfs + w;
-                e = dev_alloc(c, &c->k_org[t][p], (size_t)4 * KPS);
-                if (e == cudaSuccess) e = dev_alloc(c, &c->k_w[t][p], (size_t)2 * KNC * KTAPS * KPS);
-                if (e == cudaSuccess) e = dev_alloc(c, &c->k_wb[t][p], (size_t)2 * KNC * KTAPS * KPS);
+                has_k[p] = true;
+                o_k[p][0] = carve(off, sizeof(int) * 4 * KPS);
+                o_k[p][1] = carve(off, sizeof(float) * 2 * KNC * KTAPS * KPS);
+                o_k[p][2] = carve(off, sizeof(float) * 2 * KNC * KTAPS * KPS);
             }
-        if (e == cudaSuccess) e = dev_alloc(c, &c->d_pairs[t], (size_t)np);
+        uint8_t *blk = nullptr;
+        if ((e = dev_alloc(c, &blk, off)) != cudaSuccess) break;
+        c->d_pst[t] = blk + o_pst;
+        c->d_lines[t] = blk + o_lines;
+        c->d_pairs[t] = reinterpret_cast<DevPair *>(blk + o_pairs);
+        for (int p = 0; p < np; ++p)
+            if (has_k[p]) {
+                c->k_org[t][p] = reinterpret_cast<int *>(blk + o_k[p][0]);
+                c->k_w[t][p] = reinterpret_cast<float *>(blk + o_k[p][1]);
+                c->k_wb[t][p] = reinterpret_cast<float *>(blk + o_k[p][2]);
+            }
     }
     if (e == cudaSuccess) e = dev_alloc(c, &c->d_err, 1);
     if (e == cudaSuccess) e = dev_alloc(c, &c->d_gp, (size_t)np * 4);
