@@ -985,8 +985,10 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
     if (c->slot_used[slot] && (e = cudaEventSynchronize(c->slot_ev[slot])) != cudaSuccess)
         return cuda_fail(c, e, "slot wait");
     DevPair *hp = c->h_pairs[slot];
-    // this call's table set (alternate calls take the other one)
-    const int ts = tele ? 0 : c->tset;
+    // this call's table set: forward and tangent calls alternate between the
+    // two; the adjoint, which synchronises at the end of each call, always
+    // takes set 0 (alternating sets measured slower for it)
+    const int ts = (tele || mode == MODE_VJP) ? 0 : c->tset;
     DevPair *dp = c->d_pairs[ts];
     std::vector<long long> need((size_t)np);
     int max_seg = 0;   // segments per axis of the largest sensor with weight boxes this call
@@ -1340,7 +1342,7 @@ synim_status run(synim_ctx *c, int mode, const synim_misreg *mis, float *const *
         if ((st = launch_part(0, s)) != SYNIM_OK) return st;
         if ((e = cudaEventRecord(c->ev_im[ts], s)) != cudaSuccess) return cuda_fail(c, e, "table set release");
         c->im_used[ts] = true;
-        c->tset = ts ^ 1;
+        if (mode != MODE_VJP) c->tset = ts ^ 1;
     }
     if (mode == MODE_VJP) {
         std::vector<double> tmp((size_t)np * 4);
