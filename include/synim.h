@@ -432,7 +432,7 @@ synim_status synim_probe_generate(synim_ctx *ctx, const double *params, int64_t 
  *   inout: host [n]: initial guesses (method 0; ignored otherwise), then the
  *          estimates.
  *   residual_out: host [n] or NULL: ||y - s(p)|| / ||y|| at the estimate, with
- *          s regenerated by Sec. 2.1-2.3 (the judge of the estimate).
+ *          s regenerated by Sec. 2.1-2.3 (the check on the estimate).
  * Fit: r = y - s(p) over all map entries, Jacobian J from the probe tangents,
  * step (J^T J + mu diag(J^T J)) dp = J^T r solved in FP64 (Cholesky); mu = 0
  * at first, x10 when the cost rises (the step is rejected), /10 after an

@@ -369,7 +369,7 @@ cudaError_t est_reserve(EstState *E, long long cap, int per_sample) {
 
 // One fit pass over n samples whose probe slopes are y: responses (and,
 // unless this is the last pass, tangents) at the trial points, the sums,
-// the step.  On pass max_iter every sample still running only judges its
+// the step.  On pass max_iter every sample still running only evaluates its
 // trial point and stops, so that pass regenerates values alone and sums
 // r.r and y.y (the slots k_gn_step reads then).
 cudaError_t fit_pass(synim_ctx *c, const float *y, long long n, int pass, const GnCfg &cfg, cudaStream_t st) {
@@ -606,7 +606,7 @@ synim_status synim_misreg_estimate(synim_ctx *ctx, const float *probe_slopes, in
             break;
         }
         if (method == 1) {
-            // network only; the judge is the residual of the regenerated responses
+            // network only; the estimate is checked by the residual of the regenerated responses
             if (residual_out) {
                 e = probe_launch(ctx, p0, b, E->maps, nullptr, nullptr, st);
                 if (e == cudaSuccess) {
