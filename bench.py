@@ -799,7 +799,8 @@ def run_synim(args):
                      "kernel_ms_avg": 1000 * k_avg_s},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "what": "create from pinned host IF cubes + compute + IMs to pinned host memory"},
-        "gpu_launches": 3 * args.steps,
+        # per step: k_pst_core, k_pst_codes and k_kseg (overlapping the previous step's k_imk), k_imk
+        "gpu_launches": 4 * args.steps,
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
